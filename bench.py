@@ -1,0 +1,425 @@
+"""Benchmark of the inpainting hot path on GB300.
+
+Default workload (one GPU): the BF16 precision form, 4 frames of 512x512, d256 h8,
+8 blocks, MLP ratio 4; masks of 1-6 random polygons covering 5-40 % of each frame.
+A step is one full forward pass (patch embed -> 8 blocks -> decoder -> composite) of
+one batch.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`value` is frames/s of the BF16 path with inputs resident in HBM, timed per step with
+CUDA events (L2 flushed by a 256 MiB write between steps); `e2e` is the same metric
+through the host-buffer entry point (pinned host -> device copies and the device ->
+host read of the output inside the timed region).  Beside it: the plain FP32 form on
+the same GPU, p50/p99 step latency, attention TFLOP/s, the roofline of the dominant
+kernel from per-launch CUDA events, and the FP64 oracle timed on the host cores.
+With N > 1 every rank runs an independent replica (frames are independent).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & p99 latency at 512² (BF16 vs FP32 plain, same GPU); attn TFLOP/s"
+UNIT = "frames/s"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=None, help="override the batch (small ncu captures)")
+    ap.add_argument("--size", type=int, default=None, help="override H = W (small ncu captures)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2509_10466_gb300.config import WORKLOAD_B
+    w = WORKLOAD_B
+    B = args.batch or w.batch
+    H = W = args.size or w.height
+    return w, B, H, W
+
+
+def workload_name(w, B, H, W):
+    m = w.model
+    return (f"{w.name}: {B}x{H}x{W} frames, d{m.dim} h{m.heads} L{m.blocks} r{m.mlp_ratio}, "
+            f"window 8x8 (shifted on odd blocks), {w.mask_kind} holes 5-40%")
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        loaded = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- roofline numbers
+
+def flops_per_frame(m, H, W):
+    """Algorithmic FLOPs of one frame, by kernel class (dense-window attention)."""
+    Hp, Wp = -(-H // 32) * 32, -(-W // 32) * 32
+    N = (Hp // 4) * (Wp // 4)
+    d, r, L = m.dim, m.mlp_ratio, m.blocks
+    c1, c2 = m.c1, m.c2
+    return {
+        "qkv_gemm": 2 * N * d * 3 * d * L,
+        "attention": 4 * N * 64 * d * L,
+        "proj_gemm": 2 * N * d * d * L,
+        "fc1_gemm": 2 * N * d * r * d * L,
+        "fc2_gemm": 2 * N * r * d * d * L,
+        "decoder1": 2 * (4 * N) * 9 * d * c1,
+        "decoder2": 2 * (16 * N) * 9 * c1 * c2,
+        "head_composite": 2 * (16 * N) * 9 * c2 * 3,
+        "embed": 2 * N * 64 * d,
+    }
+
+
+def bytes_per_frame(m, H, W, act_bytes=2):
+    """Algorithmic (compulsory) HBM bytes of one frame, by kernel class."""
+    Hp, Wp = -(-H // 32) * 32, -(-W // 32) * 32
+    N = (Hp // 4) * (Wp // 4)
+    d, r, L = m.dim, m.mlp_ratio, m.blocks
+    a = act_bytes
+    return {
+        "embed": 13 * H * W + N * d * 4 + N,
+        "layernorm": (2 * L + 1) * N * d * (4 + a),
+        "qkv_gemm": L * N * (d * a + 3 * d * a),
+        "attention": L * N * (3 * d * a + d * a + 2),
+        "proj_gemm": L * N * (d * a + 2 * d * 4),
+        "fc1_gemm": L * N * (d * a + r * d * a),
+        "fc2_gemm": L * N * (r * d * a + 2 * d * 4),
+        "decoder1": N * d * a + 4 * N * m.c1 * a,
+        "decoder2": 4 * N * m.c1 * a + 16 * N * m.c2 * a,
+        "head_composite": 16 * N * m.c2 * a + 25 * H * W,
+    }
+
+
+def read_traffic():
+    """Per-launch DRAM bytes of each kernel class from the committed ncu summary, if current."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return {}
+    out = {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        kv = dict(p.split("=", 1) for p in line.split())
+        src = os.path.join(ROOT, "paper_2509_10466_gb300", "csrc", kv["source"])
+        if not os.path.exists(src):
+            continue
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h == kv.get("sha"):
+            out[kv["class"]] = float(kv["bytes_per_launch"])
+    return out
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 oracle as the reference arm, on the host cores, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    from oracle import inpaint_oracle as O
+    from paper_2509_10466_gb300 import synthetic as S
+    w, B, H, W = workload(args)
+    cfg = w.model
+    weights = S.make_weights(cfg, seed=0).astype(np.float64)
+    x = S.make_frames(1, H, W, seed=1)
+    hole = S.make_hole(1, H, W, w.mask_kind, seed=1)
+    wt = torch.from_numpy(weights)
+    times = []
+    with torch.no_grad():
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            O.forward(torch.from_numpy(x), torch.from_numpy(hole), wt, cfg)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w, 1, H, W), "global_batch": 1, "seq_len": (H // 4) * (W // 4),
+                   "parallelism": "none (host CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": f"1 frame of {H}x{W} per step (the workload's model), FP64 oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2509_10466_gb300 import binding, build as Bld, synthetic as S
+    from paper_2509_10466_gb300.config import FP32
+    if rank == 0:
+        Bld.build()
+    if dist:
+        dist.barrier()
+    binding.load()
+
+    w, B, H, W = workload(args)
+    cfg = w.model
+    weights = S.make_weights(cfg, seed=0)
+    x_np = S.make_frames(B, H, W, seed=1 + 1000 * rank)
+    hole_np = S.make_hole(B, H, W, w.mask_kind, seed=1 + 1000 * rank)
+    dev = torch.device("cuda", local)
+    x = torch.from_numpy(x_np).to(dev)
+    hole = torch.from_numpy(hole_np).to(dev)
+    out = torch.empty_like(x)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    inp = binding.Inpainter(cfg, weights)
+    ctx = inp.ctx
+
+    def step():
+        binding.inpaint_batch(ctx, x, hole, out, None, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-step events, per-launch events (roofline), L2 flush between steps
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = binding.inpaint_launch_count(ctx)
+    binding.inpaint_profile_read(ctx)  # clear
+    binding.inpaint_profile_enable(ctx, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    binding.inpaint_profile_enable(ctx, False)
+    launches = binding.inpaint_launch_count(ctx) - n0
+    clk = clocks.stop()
+    prof = binding.inpaint_profile_read(ctx)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+    value = world * B * args.steps / (total_ms / 1000.0)
+    ms_per_step = total_ms / args.steps
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    xh = torch.from_numpy(x_np).pin_memory()
+    hh = torch.from_numpy(hole_np).pin_memory()
+    oh = torch.empty(x_np.shape, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        binding.inpaint_batch_host(ctx, xh, hh, oh, stream)
+    e2e_s = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binding.inpaint_batch_host(ctx, xh, hh, oh, stream)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_s)
+    if dist:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t)
+    e2e_value = world * B * args.steps / e2e_total
+    assert np.array_equal(oh.numpy(), out.cpu().numpy()), "host path result differs from the device path"
+
+    # ---- plain FP32 form on the same GPU and workload
+    fp32 = None
+    if not args.no_fp32:
+        inp32 = binding.Inpainter(cfg.with_precision(FP32), weights)
+        out32 = torch.empty_like(x)
+        for _ in range(2):
+            binding.inpaint_batch(inp32.ctx, x, hole, out32, None, stream)
+        k32 = max(3, min(args.steps, 8))
+        ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k32)]
+        for k in range(k32):
+            flush.fill_(float(k))
+            ev32[k][0].record(stream)
+            binding.inpaint_batch(inp32.ctx, x, hole, out32, None, stream)
+            ev32[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms32 = sum(a.elapsed_time(b) for a, b in ev32) / k32
+        fp32 = {"value": B / (ms32 / 1000.0), "unit": UNIT, "ms_per_step": ms32,
+                "bf16_speedup": (B / (ms_per_step / 1000.0)) / (B / (ms32 / 1000.0))}
+        inp32.close()
+
+    # ---- roofline of the dominant kernel class (per-launch CUDA events in the timed region)
+    from json import load as _jl
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _jl(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    tc_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    peak_src = "measured" if peaks else "fallback"
+    fl = flops_per_frame(cfg, H, W)
+    by = bytes_per_frame(cfg, H, W)
+    kernels = {}
+    for name, (ms, n) in prof.items():
+        if n == 0:
+            continue
+        kernels[name] = {"ms_total": ms, "launches": n, "ms_per_launch": ms / n}
+    prof_total = sum(v["ms_total"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms_total"] / prof_total
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    launches_per_step = {k: v["launches"] / args.steps for k, v in kernels.items()}
+    traffic = read_traffic()
+
+    def roof(name):
+        per_step_launches = launches_per_step[name]
+        avg_s = kernels[name]["ms_per_launch"] / 1000.0
+        if name.endswith("_gemm") or name == "decoder1":
+            work = fl[name] * B / per_step_launches
+            ach = work / avg_s / 1e12
+            return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,
+                    "peak_source": f"{peak_src} bf16 sustained", "kernel": name,
+                    "traffic": traffic.get(name)}
+        work = by[name] * B / per_step_launches
+        ach = work / avg_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                "peak_source": f"{peak_src} hbm copy", "kernel": name, "traffic": traffic.get(name)}
+
+    roofline = roof(dom)
+    per_kernel = {k: dict(v, **{"roofline_frac": roof(k)["frac"]}) for k, v in kernels.items()
+                  if k in fl or k in by}
+    attn = kernels.get("attention")
+    attn_tflops = (fl["attention"] * B * args.steps / (attn["ms_total"] / 1000.0) / 1e12) if attn else None
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import inpaint_oracle as O
+        t0 = time.perf_counter()
+        with torch.no_grad():
+            O.forward(torch.from_numpy(x_np[:1]), torch.from_numpy(hole_np[:1]),
+                      torch.from_numpy(weights.astype(np.float64)), cfg)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": f"1 of the {B} frames ({H}x{W}), full model, FP64, {dt:.1f} s"}
+
+    inp.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": workload_name(w, B, H, W), "global_batch": B * world,
+                       "seq_len": (-(-H // 32) * 8) * (-(-W // 32) * 8), "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "latency_ms": {"p50": p50, "p99": p99, "per": f"batch of {B} frames"},
+            "fp32_plain": fp32,
+            "attn_tflops": attn_tflops,
+            "roofline": roofline,
+            "kernels": per_kernel,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_np.nbytes + hole_np.nbytes),
+                    "d2h_bytes_per_step": int(x_np.nbytes)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

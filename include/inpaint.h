@@ -1,0 +1,199 @@
+/*
+ * inpaint.h - C ABI of the GB300 mask-aware windowed-transformer inpainting library.
+ *
+ * The library runs the per-frame inpainting pass of the privacy pipeline of arXiv
+ * 2509.10466: the model receives a frame whose private (masked) regions are set to 0
+ * and returns the completed frame ("Inpainting Manager" section).  The network is a
+ * hybrid CNN/transformer derived from DSTT ("Real-time Digital Inpainting"), with
+ * scaled-dot-product attention ("Inpainting Model", item "Distinct Transformer Blocks")
+ * and a convolutional reconstruction with a final crop (item "Modified Vec2Patch").
+ *
+ * The pass, per frame (H, W padded internally to multiples of 32 with x = 0, hole = 1):
+ *   1. m = 1 - hole; input = [x*m (RGB), m]; 4x4 stride-4 conv patch embedding to
+ *      tokens [N, dim]; token mask v0[t] = 1 if any pixel of the patch is known.
+ *   2. `blocks` pre-LN transformer blocks.  Block l: LN -> QKV -> multi-head attention
+ *      inside 8x8-token windows (offset by 4 tokens on odd blocks when shift = 1; slots
+ *      outside the grid are void).  Keys are the tokens with v_l = 1; a window with no
+ *      such key outputs 0.  v_{l+1}[t] = OR of v_l over t's window (bit-exact).  Then
+ *      proj + residual, LN -> MLP (exact-erf GELU) -> residual.
+ *   3. Final LN; two stages of nearest x2 upsample + 3x3 conv + GELU (dim/4, dim/8
+ *      channels); 3x3 conv to RGB = pred.
+ *   4. out = hole ? pred : x, cropped to H x W (known pixels copied exactly).
+ *
+ * Conventions
+ *   - Every device pointer is caller-owned and must stay valid until the work queued
+ *     on `stream` has finished.  x, out, pred, target, grad_out: float32 NCHW
+ *     [B, 3, H, W], contiguous.  hole: uint8 [B, H, W], nonzero = private pixel.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only enqueue
+ *     work unless stated otherwise; completion is stream-ordered.
+ *   - Every function returns INPAINT_OK (0) or an error code; nothing throws across
+ *     the ABI.  A failed call leaves caller buffers in an unspecified state.
+ *   - One context may be used by one host thread at a time.  Calls that use the
+ *     context's internal workspace (inpaint_frame/batch/batch_host/backward) must not
+ *     overlap on different streams; inpaint_batch_ws takes a caller workspace and may
+ *     run concurrently on different streams with different workspaces.
+ *   - Requirements: window = 8, patch = 4, dim / heads = 32; dim % 64 == 0 for BF16.
+ */
+#ifndef INPAINT_H
+#define INPAINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define INPAINT_API __attribute__((visibility("default")))
+#else
+#define INPAINT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  INPAINT_OK = 0,
+  INPAINT_E_INVAL = 1,    /* bad argument or unsupported configuration            */
+  INPAINT_E_NOMEM = 2,    /* device allocation failed or exceeds hbm_budget_bytes */
+  INPAINT_E_CUDA = 3,     /* a CUDA runtime call failed                           */
+  INPAINT_E_TIMEOUT = 4,  /* inpaint_sync deadline passed before the work finished */
+  INPAINT_E_STATE = 5,    /* call not valid in the context's current state        */
+  INPAINT_E_DEVICE = 6    /* a kernel reported an error (e.g. a bounded wait ran out) */
+};
+
+enum { INPAINT_FP32 = 0, INPAINT_BF16 = 1 };
+
+typedef struct inpaint_config {
+  int32_t dim;        /* token channels d                                   */
+  int32_t heads;      /* attention heads (dim / heads must be 32)           */
+  int32_t window;     /* window side in tokens (must be 8)                  */
+  int32_t blocks;     /* transformer blocks L                               */
+  int32_t mlp_ratio;  /* MLP hidden = mlp_ratio * dim                       */
+  int32_t patch;      /* patch-embedding stride (must be 4)                 */
+  int32_t dec_c1;     /* decoder stage-1 channels, 0 = dim / 4              */
+  int32_t dec_c2;     /* decoder stage-2 channels, 0 = dim / 8              */
+  int32_t precision;  /* INPAINT_FP32 (SIMT FP32) or INPAINT_BF16 (tensor cores,
+                         FP32 accumulation, softmax statistics and LayerNorms) */
+  int32_t shift;      /* 1 = odd blocks use windows offset by half a window  */
+  uint64_t seed;      /* recorded only; weights always come from the caller  */
+  size_t hbm_budget_bytes; /* cap on the context's device memory, 0 = none   */
+} inpaint_config;
+
+typedef struct inpaint_ctx inpaint_ctx;
+
+/* Number of float32 values in the weight blob for `cfg`.  Blob order (each tensor
+ * row-major): embed.w [d,4,4,4] (out, in = R,G,B,mask, ky, kx), embed.b [d]; per block:
+ * ln1.g, ln1.b [d], qkv.w [d,3d] (in, out; out = q | k | v, head h at columns
+ * 32h.. of each third), qkv.b [3d], proj.w [d,d], proj.b [d], ln2.g, ln2.b [d],
+ * fc1.w [d, r*d], fc1.b [r*d], fc2.w [r*d, d], fc2.b [d]; then lnf.g, lnf.b [d],
+ * dec1.w [c1,d,3,3], dec1.b [c1], dec2.w [c2,c1,3,3], dec2.b [c2], head.w [3,c2,3,3],
+ * head.b [3].  Errors: E_INVAL for a NULL or unsupported config. */
+INPAINT_API int inpaint_num_params(const inpaint_config* cfg, size_t* n_params);
+
+/* Create a context on the current CUDA device and upload `weights` (host float32,
+ * `n_weights` values in blob order; must equal inpaint_num_params).  The context
+ * owns its copy of the weights and a device workspace that grows on demand up to
+ * hbm_budget_bytes.  Blocks until the upload is done.  Errors: E_INVAL (config,
+ * NULL weights, count mismatch), E_NOMEM, E_CUDA.  *out is NULL on error. */
+INPAINT_API int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weights,
+                 inpaint_ctx** out);
+
+/* Replace the weights (float32 blob).  weights_on_device = 1: `weights` is a device
+ * pointer and the update is enqueued on `stream`; 0: host pointer, copied before
+ * returning.  Used by fine-tuning after an optimizer step. */
+INPAINT_API int inpaint_set_weights(inpaint_ctx* ctx, const float* weights, int weights_on_device,
+                        void* stream);
+
+/* Copy the context's float32 weight blob to host memory (num_params values). Blocking. */
+INPAINT_API int inpaint_get_weights(inpaint_ctx* ctx, float* host_out);
+
+/* Device workspace bytes one forward call of this shape needs (inpaint_batch_ws). */
+INPAINT_API int inpaint_workspace_bytes(inpaint_ctx* ctx, int B, int H, int W, size_t* bytes);
+
+/* Forward pass of one frame (B = 1); see inpaint_batch. */
+INPAINT_API int inpaint_frame(inpaint_ctx* ctx, const float* x, const uint8_t* hole, int H, int W,
+                  float* out, void* stream);
+
+/* Forward pass of B frames of equal size (steps 1-4 above).  Device pointers:
+ * x [B,3,H,W], hole [B,H,W], out [B,3,H,W]; pred_or_null, if not NULL, receives the
+ * decoder output (before compositing) [B,3,H,W].  Uses the context's workspace
+ * (grown if needed: E_NOMEM beyond the budget).  Errors: E_INVAL for B < 1, H or
+ * W < 1, NULL pointers; E_CUDA on a launch failure. */
+INPAINT_API int inpaint_batch(inpaint_ctx* ctx, const float* x, const uint8_t* hole, int B, int H,
+                  int W, float* out, float* pred_or_null, void* stream);
+
+/* Same as inpaint_batch but every intermediate lives in the caller's device
+ * `workspace` (256-byte aligned, >= inpaint_workspace_bytes).  Calls with distinct
+ * workspaces may run concurrently on distinct streams; the weights are shared
+ * read-only.  Token masks of such calls are not kept for inpaint_token_masks. */
+INPAINT_API int inpaint_batch_ws(inpaint_ctx* ctx, void* workspace, size_t workspace_bytes,
+                     const float* x, const uint8_t* hole, int B, int H, int W, float* out,
+                     float* pred_or_null, void* stream);
+
+/* End-to-end form with HOST buffers: copies x and hole host->device, runs
+ * inpaint_batch, copies out device->host and waits for completion.  Pinned host
+ * memory gives asynchronous copies; pageable memory works but is slower. */
+INPAINT_API int inpaint_batch_host(inpaint_ctx* ctx, const float* x_host, const uint8_t* hole_host,
+                       int B, int H, int W, float* out_host, void* stream);
+
+/* Token masks v0 ... vL of the last inpaint_frame/inpaint_batch call, copied to host:
+ * uint8 [(L+1), B, Ht*Wt] (Ht = H_pad/4, Wt = W_pad/4, row-major tokens).  `n` is
+ * the capacity of `host_out` in bytes; E_INVAL if too small, E_STATE if no forward
+ * call has run.  Blocking. */
+INPAINT_API int inpaint_token_masks(inpaint_ctx* ctx, uint8_t* host_out, size_t n);
+
+/* Hole-L1 fine-tuning loss (the paper trains with a per-pixel L1 loss weighted
+ * towards the masked region, "Training structure"; this path keeps the hole term):
+ * loss = sum over hole pixels and channels |out - target| / (3 * n_hole), 0 when
+ * there are no hole pixels; grad_out = dloss/dout (sign(0) = 0, 0 on known pixels).
+ * loss_dev: one device float; grad_out_dev: device [B,3,H,W] or NULL.  The sum is
+ * reduced in a fixed order (deterministic). */
+INPAINT_API int inpaint_l1_hole_loss(inpaint_ctx* ctx, const float* out, const float* target,
+                         const uint8_t* hole, int B, int H, int W, float* loss_dev,
+                         float* grad_out_dev, void* stream);
+
+/* Gradient of sum(out * grad_out) with respect to the weight blob, written to
+ * grad_weights (device float32, num_params values, overwritten).  Recomputes the
+ * forward, keeping only each block's input, and recomputes each block again during
+ * the reverse sweep (per-block activation recomputation).  The token masks carry no
+ * gradient.  FP32 arithmetic in either precision setting. */
+INPAINT_API int inpaint_backward(inpaint_ctx* ctx, const float* x, const uint8_t* hole,
+                     const float* grad_out, int B, int H, int W, float* grad_weights,
+                     void* stream);
+
+/* Wait for `stream` with a host deadline (timeout_ms < 0: wait forever), then check
+ * the context's device error flag.  E_TIMEOUT if the deadline passed (the work keeps
+ * running), E_DEVICE if a kernel raised the flag (the flag is then cleared). */
+INPAINT_API int inpaint_sync(inpaint_ctx* ctx, void* stream, int timeout_ms);
+
+/* Per-kernel-class timing with CUDA events on the launching stream.  While enabled,
+ * each kernel launch of the context is bracketed by an event pair.  Classes:
+ * 0 embed, 1 layernorm, 2 qkv gemm, 3 attention, 4 proj gemm, 5 fc1 gemm, 6 fc2 gemm,
+ * 7 decoder stage 1, 8 decoder stage 2, 9 head + composite, 10 other.
+ * inpaint_profile_read synchronizes and returns total milliseconds and launch
+ * counts per class (arrays of INPAINT_PROFILE_CLASSES), then clears them. */
+#define INPAINT_PROFILE_CLASSES 11
+INPAINT_API int inpaint_profile_enable(inpaint_ctx* ctx, int on);
+INPAINT_API int inpaint_profile_read(inpaint_ctx* ctx, float* ms, int64_t* launches);
+
+/* Number of kernels this context has launched since creation. */
+INPAINT_API int inpaint_launch_count(inpaint_ctx* ctx, int64_t* count);
+
+/* Release every device resource of the context.  Waits for its work to finish. */
+INPAINT_API void inpaint_destroy(inpaint_ctx* ctx);
+
+/* Static description of an error code. */
+INPAINT_API const char* inpaint_strerror(int code);
+
+/* --- unit-test hooks for single kernels (used by the test suite) ---------------- */
+
+/* C[M,N] = A[M,K] . B[K,N] on the BF16 tensor-core GEMM (tcgen05, FP32 accumulate).
+ * A: bf16 row-major [M,K]; Bt: bf16 row-major [N,K] (B transposed, K contiguous);
+ * C: float32 row-major [M,N].  M % 128 == 0, N % 64 == 0, K % 64 == 0. */
+INPAINT_API int inpaint_test_gemm_bf16(const void* A, const void* Bt, float* C, int M, int N, int K,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INPAINT_H */

@@ -1,0 +1,268 @@
+"""ctypes binding of ``libinpaint.so`` (the C ABI declared in ``include/inpaint.h``).
+
+Argument marshalling only: every step of the inpainting pass runs in the library's
+CUDA kernels.  Functions keep the C names; tensors are passed as raw pointers
+(``tensor.data_ptr()``) and the current torch CUDA stream is used unless one is given.
+Loading fails loudly if the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .config import ModelConfig
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libinpaint.so")
+_lib = None
+
+INPAINT_OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE, E_DEVICE = range(7)
+PROFILE_CLASSES = 11
+PROFILE_NAMES = ("embed", "layernorm", "qkv_gemm", "attention", "proj_gemm", "fc1_gemm", "fc2_gemm",
+                 "decoder1", "decoder2", "head_composite", "other")
+
+
+class InpaintError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+
+
+class InpaintConfig(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("heads", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("mlp_ratio", ctypes.c_int32), ("patch", ctypes.c_int32),
+                ("dec_c1", ctypes.c_int32), ("dec_c2", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("shift", ctypes.c_int32), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_size_t)]
+
+    @classmethod
+    def from_model(cls, cfg: ModelConfig, seed: int = 0, hbm_budget_bytes: int = 0) -> "InpaintConfig":
+        return cls(cfg.dim, cfg.heads, cfg.window, cfg.blocks, cfg.mlp_ratio, cfg.patch, cfg.dec_c1, cfg.dec_c2,
+                   cfg.precision, cfg.shift, seed, hbm_budget_bytes)
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "inpaint_strerror": (ctypes.c_char_p, [_I]),
+    "inpaint_num_params": (_I, [ctypes.POINTER(InpaintConfig), ctypes.POINTER(ctypes.c_size_t)]),
+    "inpaint_init": (_I, [ctypes.POINTER(InpaintConfig), _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "inpaint_set_weights": (_I, [_P, _P, _I, _P]),
+    "inpaint_get_weights": (_I, [_P, _P]),
+    "inpaint_workspace_bytes": (_I, [_P, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "inpaint_frame": (_I, [_P, _P, _P, _I, _I, _P, _P]),
+    "inpaint_batch": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "inpaint_batch_ws": (_I, [_P, _P, ctypes.c_size_t, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "inpaint_batch_host": (_I, [_P, _P, _P, _I, _I, _I, _P, _P]),
+    "inpaint_token_masks": (_I, [_P, _P, ctypes.c_size_t]),
+    "inpaint_l1_hole_loss": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "inpaint_backward": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P]),
+    "inpaint_sync": (_I, [_P, _P, _I]),
+    "inpaint_profile_enable": (_I, [_P, _I]),
+    "inpaint_profile_read": (_I, [_P, _P, _P]),
+    "inpaint_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "inpaint_destroy": (None, [_P]),
+    "inpaint_test_gemm_bf16": (_I, [_P, _P, _P, _I, _I, _I, _P]),
+}
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libinpaint.so and declare its signatures (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_2509_10466_gb300.build.build()")
+        lib = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def strerror(code: int) -> str:
+    return load().inpaint_strerror(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != INPAINT_OK:
+        raise InpaintError(code, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------------- same-name wrappers
+
+def inpaint_num_params(cfg: ModelConfig) -> int:
+    n = ctypes.c_size_t()
+    c = InpaintConfig.from_model(cfg)
+    _check(load().inpaint_num_params(ctypes.byref(c), ctypes.byref(n)), "inpaint_num_params")
+    return n.value
+
+
+def inpaint_init(cfg: ModelConfig, weights: np.ndarray, seed: int = 0, hbm_budget_bytes: int = 0):
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    c = InpaintConfig.from_model(cfg, seed, hbm_budget_bytes)
+    ctx = ctypes.c_void_p()
+    _check(load().inpaint_init(ctypes.byref(c), w.ctypes.data_as(ctypes.c_void_p), w.size, ctypes.byref(ctx)),
+           "inpaint_init")
+    return ctx
+
+
+def inpaint_destroy(ctx):
+    load().inpaint_destroy(ctx)
+
+
+def inpaint_set_weights(ctx, weights, stream=None):
+    """weights: a CUDA float32 tensor (device update on the stream) or a numpy array (host)."""
+    if isinstance(weights, np.ndarray):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        _check(load().inpaint_set_weights(ctx, w.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)),
+               "inpaint_set_weights")
+    else:
+        _check(load().inpaint_set_weights(ctx, _ptr(weights), 1, _stream(stream)), "inpaint_set_weights")
+
+
+def inpaint_get_weights(ctx, n: int) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    _check(load().inpaint_get_weights(ctx, out.ctypes.data_as(ctypes.c_void_p)), "inpaint_get_weights")
+    return out
+
+
+def inpaint_workspace_bytes(ctx, B: int, H: int, W: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load().inpaint_workspace_bytes(ctx, B, H, W, ctypes.byref(n)), "inpaint_workspace_bytes")
+    return n.value
+
+
+def inpaint_frame(ctx, x, hole, out, stream=None):
+    _, H, W = hole.shape
+    _check(load().inpaint_frame(ctx, _ptr(x), _ptr(hole), H, W, _ptr(out), _stream(stream)), "inpaint_frame")
+
+
+def inpaint_batch(ctx, x, hole, out, pred=None, stream=None):
+    B, H, W = hole.shape
+    _check(load().inpaint_batch(ctx, _ptr(x), _ptr(hole), B, H, W, _ptr(out), _ptr(pred), _stream(stream)),
+           "inpaint_batch")
+
+
+def inpaint_batch_ws(ctx, workspace, x, hole, out, pred=None, stream=None):
+    B, H, W = hole.shape
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().inpaint_batch_ws(ctx, _ptr(workspace), nbytes, _ptr(x), _ptr(hole), B, H, W, _ptr(out),
+                                   _ptr(pred), _stream(stream)), "inpaint_batch_ws")
+
+
+def inpaint_batch_host(ctx, x: np.ndarray | object, hole, out, stream=None):
+    """Host buffers (pinned torch CPU tensors or numpy arrays); blocks until `out` is filled."""
+    B, H, W = hole.shape
+
+    def hp(a):
+        return ctypes.c_void_p(a.ctypes.data) if isinstance(a, np.ndarray) else ctypes.c_void_p(a.data_ptr())
+
+    _check(load().inpaint_batch_host(ctx, hp(x), hp(hole), B, H, W, hp(out), _stream(stream)), "inpaint_batch_host")
+
+
+def inpaint_token_masks(ctx, blocks: int, B: int, Ntok: int) -> np.ndarray:
+    out = np.empty(((blocks + 1), B, Ntok), np.uint8)
+    _check(load().inpaint_token_masks(ctx, out.ctypes.data_as(ctypes.c_void_p), out.size), "inpaint_token_masks")
+    return out
+
+
+def inpaint_l1_hole_loss(ctx, out, target, hole, loss, grad_out=None, stream=None):
+    B, H, W = hole.shape
+    _check(load().inpaint_l1_hole_loss(ctx, _ptr(out), _ptr(target), _ptr(hole), B, H, W, _ptr(loss),
+                                       _ptr(grad_out), _stream(stream)), "inpaint_l1_hole_loss")
+
+
+def inpaint_backward(ctx, x, hole, grad_out, grad_weights, stream=None):
+    B, H, W = hole.shape
+    _check(load().inpaint_backward(ctx, _ptr(x), _ptr(hole), _ptr(grad_out), B, H, W, _ptr(grad_weights),
+                                   _stream(stream)), "inpaint_backward")
+
+
+def inpaint_sync(ctx, stream=None, timeout_ms: int = -1) -> int:
+    """Returns the status code (0, E_TIMEOUT or E_DEVICE) instead of raising for those two."""
+    code = load().inpaint_sync(ctx, _stream(stream), timeout_ms)
+    if code not in (INPAINT_OK, E_TIMEOUT, E_DEVICE):
+        _check(code, "inpaint_sync")
+    return code
+
+
+def inpaint_profile_enable(ctx, on: bool):
+    _check(load().inpaint_profile_enable(ctx, 1 if on else 0), "inpaint_profile_enable")
+
+
+def inpaint_profile_read(ctx):
+    ms = (ctypes.c_float * PROFILE_CLASSES)()
+    n = (ctypes.c_int64 * PROFILE_CLASSES)()
+    _check(load().inpaint_profile_read(ctx, ms, n), "inpaint_profile_read")
+    return {PROFILE_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(PROFILE_CLASSES)}
+
+
+def inpaint_launch_count(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(load().inpaint_launch_count(ctx, ctypes.byref(n)), "inpaint_launch_count")
+    return n.value
+
+
+def inpaint_test_gemm_bf16(A, Bt, C, stream=None):
+    M, K = A.shape
+    N = Bt.shape[0]
+    _check(load().inpaint_test_gemm_bf16(_ptr(A), _ptr(Bt), _ptr(C), M, N, K, _stream(stream)),
+           "inpaint_test_gemm_bf16")
+
+
+# ----------------------------------------------------------------------------- convenience object
+
+class Inpainter:
+    """Owns one library context; methods take torch CUDA tensors."""
+
+    def __init__(self, cfg: ModelConfig, weights: np.ndarray, hbm_budget_bytes: int = 0):
+        self.cfg = cfg
+        self.n_params = inpaint_num_params(cfg)
+        self.ctx = inpaint_init(cfg, weights, hbm_budget_bytes=hbm_budget_bytes)
+
+    def close(self):
+        if self.ctx is not None:
+            inpaint_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __call__(self, x, hole, want_pred: bool = False, stream=None):
+        import torch
+        out = torch.empty_like(x)
+        pred = torch.empty_like(x) if want_pred else None
+        inpaint_batch(self.ctx, x, hole, out, pred, stream)
+        return (out, pred) if want_pred else out
+
+    def token_masks(self, B: int, H: int, W: int) -> np.ndarray:
+        mult = self.cfg.patch * self.cfg.window
+        Ht = -(-H // mult) * mult // self.cfg.patch
+        Wt = -(-W // mult) * mult // self.cfg.patch
+        return inpaint_token_masks(self.ctx, self.cfg.blocks, B, Ht * Wt)

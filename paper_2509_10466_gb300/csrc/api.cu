@@ -1,0 +1,583 @@
+// C ABI and runtime of the inpainting library: context, weight layouts, workspace
+// planning, the forward sequence and event-based per-kernel timing.
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+
+namespace inpaint {
+cudaError_t launch_gemm_f32_ex(bool ta, bool tb, const float* A, int lda, const float* Bm, int ldb, float* C, int ldc,
+                               int M, int N, int K, int splits, int epi, const float* bias, const float* resid,
+                               cudaStream_t st);
+int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* grad_out, int B, int H, int W,
+                  float* grad_w, cudaStream_t st);
+}  // namespace inpaint
+
+using namespace inpaint;
+
+// ------------------------------------------------------------------------- layout
+
+namespace {
+
+// Offsets (in floats) of every tensor of the weight blob, in blob order.
+struct BlockOff {
+  size_t ln1g, ln1b, qkvw, qkvb, projw, projb, ln2g, ln2b, fc1w, fc1b, fc2w, fc2b;
+};
+struct Offsets {
+  size_t embw, embb;
+  std::vector<BlockOff> blk;
+  size_t lnfg, lnfb, d1w, d1b, d2w, d2b, hw, hb;
+  size_t total;
+};
+
+bool check_cfg(const inpaint_config* c) {
+  if (!c) return false;
+  if (c->window != 8 || c->patch != 4) return false;
+  if (c->dim <= 0 || c->dim % 32 || c->heads <= 0 || c->dim != c->heads * 32) return false;
+  if (c->precision == INPAINT_BF16 && c->dim % 64) return false;  // tensor-core tiles are 64 wide
+  if (c->blocks < 0 || c->blocks > 64 || c->mlp_ratio <= 0 || c->mlp_ratio > 16) return false;
+  if (c->precision != INPAINT_FP32 && c->precision != INPAINT_BF16) return false;
+  const int c1 = c->dec_c1 ? c->dec_c1 : c->dim / 4;
+  const int c2 = c->dec_c2 ? c->dec_c2 : c->dim / 8;
+  if (c1 <= 0 || c2 <= 0 || c1 % 4 || c2 % 4 || c1 > 4096 || c2 > 1024) return false;
+  return true;
+}
+
+Offsets make_offsets(const inpaint_config& c) {
+  const size_t d = c.dim, r = c.mlp_ratio;
+  const size_t c1 = c.dec_c1 ? c.dec_c1 : d / 4, c2 = c.dec_c2 ? c.dec_c2 : d / 8;
+  Offsets o;
+  size_t p = 0;
+  auto take = [&](size_t n) { size_t at = p; p += n; return at; };
+  o.embw = take(d * 64);
+  o.embb = take(d);
+  for (int l = 0; l < c.blocks; ++l) {
+    BlockOff b;
+    b.ln1g = take(d); b.ln1b = take(d);
+    b.qkvw = take(d * 3 * d); b.qkvb = take(3 * d);
+    b.projw = take(d * d); b.projb = take(d);
+    b.ln2g = take(d); b.ln2b = take(d);
+    b.fc1w = take(d * r * d); b.fc1b = take(r * d);
+    b.fc2w = take(r * d * d); b.fc2b = take(d);
+    o.blk.push_back(b);
+  }
+  o.lnfg = take(d); o.lnfb = take(d);
+  o.d1w = take(c1 * d * 9); o.d1b = take(c1);
+  o.d2w = take(c2 * c1 * 9); o.d2b = take(c2);
+  o.hw = take(3 * c2 * 9); o.hb = take(3);
+  o.total = p;
+  return o;
+}
+
+// out[n*K + k] = bf16(in[k*N + n])  (linear weight [in=K, out=N] -> K-major B operand)
+__global__ void transpose_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, int K, int N) {
+  __shared__ float t[32][33];
+  const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int k = k0 + i, n = n0 + threadIdx.x;
+    t[i][threadIdx.x] = (k < K && n < N) ? in[(size_t)k * N + n] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int n = n0 + i, k = k0 + threadIdx.x;
+    if (n < N && k < K) out[(size_t)n * K + k] = __float2bfloat16_rn(t[threadIdx.x][i]);
+  }
+}
+
+// conv weight [Cout][Cin][9] -> [9][Cin][Cout]
+__global__ void conv_w_to_tap_major(const float* __restrict__ in, float* __restrict__ out, int Cout, int Cin) {
+  const size_t n = (size_t)Cout * Cin * 9;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int tap = (int)(e % 9);
+    const size_t rest = e / 9;
+    const int ci = (int)(rest % Cin), co = (int)(rest / Cin);
+    out[((size_t)tap * Cin + ci) * Cout + co] = in[e];
+  }
+}
+
+// [d][64] -> [64][d]
+__global__ void transpose_f32(const float* __restrict__ in, float* __restrict__ out, int R, int C) {
+  const size_t n = (size_t)R * C;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / C), c = (int)(e % C);
+    out[(size_t)c * R + r] = in[e];
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------- context
+
+struct Plan {
+  int B, H, W, Hp, Wp, Ht, Wt, Nt, M;
+  size_t tok, ln, qkv, o, hid, masks, f1, f2, err, end;
+};
+
+struct EventPair {
+  cudaEvent_t a, b;
+  int cls;
+};
+
+struct inpaint_ctx {
+  inpaint_config cfg;
+  int d, heads, L, r, c1, c2, hid;
+  bool use_bf16;
+  Offsets off;
+  size_t nparams;
+  float* w32 = nullptr;        // float32 blob (device)
+  float* embed_wt = nullptr;   // [64][d]
+  float* dec1_wt = nullptr;    // [9][d][c1]
+  float* dec2_wt = nullptr;    // [9][c1][c2]
+  bf16* lin_bf16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
+  size_t lin_block_elems = 0;
+  size_t weight_bytes = 0;
+  int* dev_err = nullptr;
+  uint8_t* arena = nullptr;
+  size_t arena_bytes = 0;
+  // last internal-workspace forward, for inpaint_token_masks
+  bool have_masks = false;
+  Plan last{};
+  // host e2e staging
+  uint8_t* stage = nullptr;
+  size_t stage_bytes = 0;
+  // backward scratch
+  uint8_t* bws = nullptr;
+  size_t bws_bytes = 0;
+  // profiling
+  bool prof = false;
+  std::vector<EventPair> events;
+  size_t ev_used = 0;
+  int64_t launches = 0;
+};
+
+namespace inpaint {
+
+// Bracket one kernel launch with events when profiling is on; counts launches.
+struct LaunchScope {
+  inpaint_ctx* c;
+  cudaStream_t st;
+  int cls;
+  EventPair* ep = nullptr;
+  LaunchScope(inpaint_ctx* c_, cudaStream_t s, int k) : c(c_), st(s), cls(k) {
+    c->launches++;
+    if (!c->prof) return;
+    if (c->ev_used == c->events.size()) {
+      EventPair p;
+      if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return;
+      c->events.push_back(p);
+    }
+    ep = &c->events[c->ev_used++];
+    ep->cls = k;
+    cudaEventRecord(ep->a, st);
+  }
+  ~LaunchScope() {
+    if (ep) cudaEventRecord(ep->b, st);
+  }
+};
+
+int grow(uint8_t** buf, size_t* cap, size_t need, const inpaint_ctx* c, size_t other_bytes) {
+  if (need <= *cap) return INPAINT_OK;
+  if (c->cfg.hbm_budget_bytes && c->weight_bytes + other_bytes + need > c->cfg.hbm_budget_bytes) return INPAINT_E_NOMEM;
+  if (*buf) {
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+  }
+  if (cudaMalloc(buf, need) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return INPAINT_E_NOMEM;
+  }
+  *cap = need;
+  return INPAINT_OK;
+}
+
+}  // namespace inpaint
+
+namespace {
+
+Plan make_plan(const inpaint_ctx* c, int B, int H, int W) {
+  Plan p;
+  p.B = B; p.H = H; p.W = W;
+  p.Hp = (H + 31) / 32 * 32;
+  p.Wp = (W + 31) / 32 * 32;
+  p.Ht = p.Hp / 4;
+  p.Wt = p.Wp / 4;
+  p.Nt = p.Ht * p.Wt;
+  p.M = B * p.Nt;
+  const size_t es = c->use_bf16 ? 2 : 4;
+  const size_t M = p.M, d = c->d;
+  size_t q = 0;
+  auto take = [&](size_t bytes) { size_t at = q; q = align_up(q + bytes, 256); return at; };
+  p.tok = take(M * d * 4);
+  p.ln = take(M * d * es);
+  p.qkv = take(M * 3 * d * es);
+  p.o = take(M * d * es);
+  p.hid = take(M * (size_t)c->hid * es);
+  p.masks = take((size_t)(c->L + 1) * M);
+  p.f1 = take((size_t)B * (2 * p.Ht) * (2 * p.Wt) * c->c1 * es);
+  p.f2 = take((size_t)B * p.Hp * p.Wp * c->c2 * es);
+  p.err = take(256);
+  p.end = q;
+  return p;
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? INPAINT_OK : INPAINT_E_CUDA; }
+
+#define TRY(call)                          \
+  do {                                     \
+    int rc_ = (call);                      \
+    if (rc_ != INPAINT_OK) return rc_;     \
+  } while (0)
+
+int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
+  const Offsets& o = c->off;
+  transpose_f32<<<64, 256, 0, st>>>(c->w32 + o.embw, c->embed_wt, c->d, 64);
+  conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d1w, c->dec1_wt, c->c1, c->d);
+  conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d2w, c->dec2_wt, c->c2, c->c1);
+  if (c->use_bf16) {
+    const int d = c->d, h = c->hid;
+    for (int l = 0; l < c->L; ++l) {
+      bf16* base = c->lin_bf16 + (size_t)l * c->lin_block_elems;
+      struct { size_t src; int K, N; size_t dst; } mats[4] = {
+          {o.blk[l].qkvw, d, 3 * d, 0},
+          {o.blk[l].projw, d, d, (size_t)3 * d * d},
+          {o.blk[l].fc1w, d, h, (size_t)4 * d * d},
+          {o.blk[l].fc2w, h, d, (size_t)4 * d * d + (size_t)h * d}};
+      for (auto& m : mats) {
+        dim3 grid(cdiv(m.N, 32), cdiv(m.K, 32));
+        transpose_to_bf16<<<grid, dim3(32, 8), 0, st>>>(c->w32 + m.src, base + m.dst, m.K, m.N);
+      }
+    }
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+// The whole forward pass into workspace `ws` laid out by plan `p`.
+int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, const uint8_t* hole, float* out,
+                float* pred, cudaStream_t st) {
+  const Offsets& o = c->off;
+  const int d = c->d, M = p.M;
+  float* tok = reinterpret_cast<float*>(ws + p.tok);
+  uint8_t* masks = ws + p.masks;
+  int* err = c->dev_err;
+  {
+    LaunchScope ls(c, st, K_EMBED);
+    TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st)));
+  }
+  for (int l = 0; l < c->L; ++l) {
+    const BlockOff& b = o.blk[l];
+    const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
+    uint8_t* v_in = masks + (size_t)l * M;
+    uint8_t* v_out = masks + (size_t)(l + 1) * M;
+    if (c->use_bf16) {
+      bf16* ln = reinterpret_cast<bf16*>(ws + p.ln);
+      bf16* qkv = reinterpret_cast<bf16*>(ws + p.qkv);
+      bf16* ao = reinterpret_cast<bf16*>(ws + p.o);
+      bf16* hid = reinterpret_cast<bf16*>(ws + p.hid);
+      const bf16* wl = c->lin_bf16 + (size_t)l * c->lin_block_elems;
+      const bf16* wqkv = wl;
+      const bf16* wproj = wl + (size_t)3 * d * d;
+      const bf16* wfc1 = wl + (size_t)4 * d * d;
+      const bf16* wfc2 = wfc1 + (size_t)c->hid * d;
+      { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
+      { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, err, st))); }
+      { LaunchScope ls(c, st, K_ATTN); TRY(cuda_err(launch_attention<bf16>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st))); }
+      { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_tc(ao, wproj, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, err, st))); }
+      { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
+      { LaunchScope ls(c, st, K_FC1); TRY(cuda_err(launch_gemm_tc(ln, wfc1, hid, c->hid, M, c->hid, d, EPI_BIAS_GELU, c->w32 + b.fc1b, nullptr, err, st))); }
+      { LaunchScope ls(c, st, K_FC2); TRY(cuda_err(launch_gemm_tc(hid, wfc2, tok, d, M, d, c->hid, EPI_BIAS_RESID, c->w32 + b.fc2b, tok, err, st))); }
+    } else {
+      float* ln = reinterpret_cast<float*>(ws + p.ln);
+      float* qkv = reinterpret_cast<float*>(ws + p.qkv);
+      float* ao = reinterpret_cast<float*>(ws + p.o);
+      float* hid = reinterpret_cast<float*>(ws + p.hid);
+      { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<float>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
+      { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_f32(ln, d, c->w32 + b.qkvw, 3 * d, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, st))); }
+      { LaunchScope ls(c, st, K_ATTN); TRY(cuda_err(launch_attention<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st))); }
+      { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_f32(ao, d, c->w32 + b.projw, d, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, st))); }
+      { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<float>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
+      { LaunchScope ls(c, st, K_FC1); TRY(cuda_err(launch_gemm_f32(ln, d, c->w32 + b.fc1w, c->hid, hid, c->hid, M, c->hid, d, EPI_BIAS_GELU, c->w32 + b.fc1b, nullptr, st))); }
+      { LaunchScope ls(c, st, K_FC2); TRY(cuda_err(launch_gemm_f32(hid, c->hid, c->w32 + b.fc2w, d, tok, d, M, d, c->hid, EPI_BIAS_RESID, c->w32 + b.fc2b, tok, st))); }
+    }
+  }
+  if (c->use_bf16) {
+    bf16* ln = reinterpret_cast<bf16*>(ws + p.ln);
+    bf16* f1 = reinterpret_cast<bf16*>(ws + p.f1);
+    bf16* f2 = reinterpret_cast<bf16*>(ws + p.f2);
+    { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
+    { LaunchScope ls(c, st, K_DEC1); TRY(cuda_err(launch_upconv<bf16>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st))); }
+    { LaunchScope ls(c, st, K_DEC2); TRY(cuda_err(launch_upconv<bf16>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st))); }
+    { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<bf16>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
+  } else {
+    float* ln = reinterpret_cast<float*>(ws + p.ln);
+    float* f1 = reinterpret_cast<float*>(ws + p.f1);
+    float* f2 = reinterpret_cast<float*>(ws + p.f2);
+    { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<float>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
+    { LaunchScope ls(c, st, K_DEC1); TRY(cuda_err(launch_upconv<float>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st))); }
+    { LaunchScope ls(c, st, K_DEC2); TRY(cuda_err(launch_upconv<float>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st))); }
+    { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<float>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
+  }
+  return INPAINT_OK;
+}
+
+bool bad_shape(int B, int H, int W) {
+  return B < 1 || H < 1 || W < 1 || H > 16384 || W > 16384 || (size_t)B * H * W > ((size_t)1 << 34);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* inpaint_strerror(int code) {
+  switch (code) {
+    case INPAINT_OK: return "ok";
+    case INPAINT_E_INVAL: return "invalid argument or unsupported configuration";
+    case INPAINT_E_NOMEM: return "device memory allocation failed or exceeds the context's HBM budget";
+    case INPAINT_E_CUDA: return "CUDA runtime error";
+    case INPAINT_E_TIMEOUT: return "deadline passed before the stream finished";
+    case INPAINT_E_STATE: return "call not valid in the current state";
+    case INPAINT_E_DEVICE: return "a kernel reported a device-side error (bounded wait expired)";
+    default: return "unknown error code";
+  }
+}
+
+int inpaint_num_params(const inpaint_config* cfg, size_t* n) {
+  if (!check_cfg(cfg) || !n) return INPAINT_E_INVAL;
+  *n = make_offsets(*cfg).total;
+  return INPAINT_OK;
+}
+
+void inpaint_destroy(inpaint_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  cudaFree(c->w32);
+  cudaFree(c->embed_wt);
+  cudaFree(c->dec1_wt);
+  cudaFree(c->dec2_wt);
+  cudaFree(c->lin_bf16);
+  cudaFree(c->dev_err);
+  cudaFree(c->arena);
+  cudaFree(c->stage);
+  cudaFree(c->bws);
+  for (auto& e : c->events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  delete c;
+}
+
+int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weights, inpaint_ctx** out) {
+  if (!out) return INPAINT_E_INVAL;
+  *out = nullptr;
+  if (!check_cfg(cfg) || !weights) return INPAINT_E_INVAL;
+  inpaint_ctx* c = new (std::nothrow) inpaint_ctx();
+  if (!c) return INPAINT_E_NOMEM;
+  c->cfg = *cfg;
+  c->d = cfg->dim;
+  c->heads = cfg->heads;
+  c->L = cfg->blocks;
+  c->r = cfg->mlp_ratio;
+  c->hid = cfg->dim * cfg->mlp_ratio;
+  c->c1 = cfg->dec_c1 ? cfg->dec_c1 : cfg->dim / 4;
+  c->c2 = cfg->dec_c2 ? cfg->dec_c2 : cfg->dim / 8;
+  c->use_bf16 = cfg->precision == INPAINT_BF16;
+  c->off = make_offsets(*cfg);
+  c->nparams = c->off.total;
+  if (n_weights != c->nparams) {
+    delete c;
+    return INPAINT_E_INVAL;
+  }
+  const size_t d = c->d, h = c->hid;
+  c->lin_block_elems = 4 * d * d + 2 * h * d;
+  c->weight_bytes = c->nparams * 4 + 64 * d * 4 + 9 * d * c->c1 * 4 + 9 * (size_t)c->c1 * c->c2 * 4 +
+                    (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 : 0) + 256;
+  if (cfg->hbm_budget_bytes && c->weight_bytes > cfg->hbm_budget_bytes) {
+    delete c;
+    return INPAINT_E_NOMEM;
+  }
+  bool ok = cudaMalloc(&c->w32, c->nparams * 4) == cudaSuccess &&
+            cudaMalloc(&c->embed_wt, 64 * d * 4) == cudaSuccess &&
+            cudaMalloc(&c->dec1_wt, 9 * d * c->c1 * 4) == cudaSuccess &&
+            cudaMalloc(&c->dec2_wt, 9 * (size_t)c->c1 * c->c2 * 4) == cudaSuccess &&
+            cudaMalloc(&c->dev_err, 256) == cudaSuccess &&
+            (!c->use_bf16 || cudaMalloc(&c->lin_bf16, (size_t)c->L * c->lin_block_elems * 2) == cudaSuccess);
+  if (!ok) {
+    cudaGetLastError();
+    inpaint_destroy(c);
+    return INPAINT_E_NOMEM;
+  }
+  if (cudaMemcpy(c->w32, weights, c->nparams * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->dev_err, 0, 256) != cudaSuccess || prepare_layouts(c, 0) != INPAINT_OK ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    inpaint_destroy(c);
+    return INPAINT_E_CUDA;
+  }
+  *out = c;
+  return INPAINT_OK;
+}
+
+int inpaint_set_weights(inpaint_ctx* c, const float* w, int on_device, void* stream) {
+  if (!c || !w) return INPAINT_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (on_device) {
+    if (cudaMemcpyAsync(c->w32, w, c->nparams * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return INPAINT_E_CUDA;
+    return prepare_layouts(c, st);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return INPAINT_E_CUDA;
+  if (cudaMemcpy(c->w32, w, c->nparams * 4, cudaMemcpyHostToDevice) != cudaSuccess) return INPAINT_E_CUDA;
+  TRY(prepare_layouts(c, st));
+  return cuda_err(cudaStreamSynchronize(st));
+}
+
+int inpaint_get_weights(inpaint_ctx* c, float* host) {
+  if (!c || !host) return INPAINT_E_INVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return INPAINT_E_CUDA;
+  return cuda_err(cudaMemcpy(host, c->w32, c->nparams * 4, cudaMemcpyDeviceToHost));
+}
+
+int inpaint_workspace_bytes(inpaint_ctx* c, int B, int H, int W, size_t* bytes) {
+  if (!c || !bytes || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  *bytes = make_plan(c, B, H, W).end;
+  return INPAINT_OK;
+}
+
+int inpaint_batch(inpaint_ctx* c, const float* x, const uint8_t* hole, int B, int H, int W, float* out, float* pred,
+                  void* stream) {
+  if (!c || !x || !hole || !out || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  const Plan p = make_plan(c, B, H, W);
+  TRY(grow(&c->arena, &c->arena_bytes, p.end, c, c->stage_bytes + c->bws_bytes));
+  c->have_masks = false;
+  TRY(run_forward(c, c->arena, p, x, hole, out, pred, (cudaStream_t)stream));
+  c->last = p;
+  c->have_masks = true;
+  return INPAINT_OK;
+}
+
+int inpaint_frame(inpaint_ctx* c, const float* x, const uint8_t* hole, int H, int W, float* out, void* stream) {
+  return inpaint_batch(c, x, hole, 1, H, W, out, nullptr, stream);
+}
+
+int inpaint_batch_ws(inpaint_ctx* c, void* workspace, size_t ws_bytes, const float* x, const uint8_t* hole, int B,
+                     int H, int W, float* out, float* pred, void* stream) {
+  if (!c || !workspace || !x || !hole || !out || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) & 255) return INPAINT_E_INVAL;
+  const Plan p = make_plan(c, B, H, W);
+  if (ws_bytes < p.end) return INPAINT_E_INVAL;
+  return run_forward(c, static_cast<uint8_t*>(workspace), p, x, hole, out, pred, (cudaStream_t)stream);
+}
+
+int inpaint_batch_host(inpaint_ctx* c, const float* xh, const uint8_t* hh, int B, int H, int W, float* oh,
+                       void* stream) {
+  if (!c || !xh || !hh || !oh || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nx = (size_t)B * 3 * H * W, nh = (size_t)B * H * W;
+  const size_t bx = align_up(nx * 4, 256), bh = align_up(nh, 256);
+  TRY(grow(&c->stage, &c->stage_bytes, 2 * bx + bh, c, c->arena_bytes + c->bws_bytes));
+  float* xd = reinterpret_cast<float*>(c->stage);
+  float* od = reinterpret_cast<float*>(c->stage + bx);
+  uint8_t* hd = c->stage + 2 * bx;
+  if (cudaMemcpyAsync(xd, xh, nx * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(hd, hh, nh, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return INPAINT_E_CUDA;
+  TRY(inpaint_batch(c, xd, hd, B, H, W, od, nullptr, stream));
+  if (cudaMemcpyAsync(oh, od, nx * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return INPAINT_E_CUDA;
+  return cuda_err(cudaStreamSynchronize(st));
+}
+
+int inpaint_token_masks(inpaint_ctx* c, uint8_t* host, size_t n) {
+  if (!c || !host) return INPAINT_E_INVAL;
+  if (!c->have_masks) return INPAINT_E_STATE;
+  const size_t need = (size_t)(c->L + 1) * c->last.M;
+  if (n < need) return INPAINT_E_INVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return INPAINT_E_CUDA;
+  return cuda_err(cudaMemcpy(host, c->arena + c->last.masks, need, cudaMemcpyDeviceToHost));
+}
+
+int inpaint_l1_hole_loss(inpaint_ctx* c, const float* out, const float* target, const uint8_t* hole, int B, int H,
+                         int W, float* loss, float* grad, void* stream) {
+  if (!c || !out || !target || !hole || !loss || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  const int nb = loss_partials(B, H, W);
+  // partial sums live in the backward scratch area (separate from the forward arena)
+  const size_t need = align_up((size_t)nb * 4, 256) * 2;
+  TRY(grow(&c->bws, &c->bws_bytes, need, c, c->arena_bytes + c->stage_bytes));
+  float* partials = reinterpret_cast<float*>(c->bws);
+  unsigned* counts = reinterpret_cast<unsigned*>(c->bws + align_up((size_t)nb * 4, 256));
+  LaunchScope ls(c, (cudaStream_t)stream, K_OTHER);
+  return cuda_err(launch_l1_hole_loss(out, target, hole, B, H, W, partials, counts, loss, grad, (cudaStream_t)stream));
+}
+
+int inpaint_backward(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* grad_out, int B, int H, int W,
+                     float* grad_w, void* stream) {
+  if (!c || !x || !hole || !grad_out || !grad_w || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  return backward_impl(c, x, hole, grad_out, B, H, W, grad_w, (cudaStream_t)stream);
+}
+
+int inpaint_sync(inpaint_ctx* c, void* stream, int timeout_ms) {
+  if (!c) return INPAINT_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaStreamQuery(st);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return INPAINT_E_CUDA;
+    if (timeout_ms >= 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+      return INPAINT_E_TIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  int flag = 0;
+  if (cudaMemcpy(&flag, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return INPAINT_E_CUDA;
+  if (flag) {
+    cudaMemset(c->dev_err, 0, sizeof(int));
+    return INPAINT_E_DEVICE;
+  }
+  return INPAINT_OK;
+}
+
+int inpaint_profile_enable(inpaint_ctx* c, int on) {
+  if (!c) return INPAINT_E_INVAL;
+  c->prof = on != 0;
+  return INPAINT_OK;
+}
+
+int inpaint_profile_read(inpaint_ctx* c, float* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return INPAINT_E_INVAL;
+  for (int k = 0; k < INPAINT_PROFILE_CLASSES; ++k) {
+    ms[k] = 0.f;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < c->ev_used; ++i) {
+    EventPair& e = c->events[i];
+    if (cudaEventSynchronize(e.b) != cudaSuccess) return INPAINT_E_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.a, e.b) != cudaSuccess) return INPAINT_E_CUDA;
+    ms[e.cls] += t;
+    launches[e.cls] += 1;
+  }
+  c->ev_used = 0;
+  return INPAINT_OK;
+}
+
+int inpaint_launch_count(inpaint_ctx* c, int64_t* n) {
+  if (!c || !n) return INPAINT_E_INVAL;
+  *n = c->launches;
+  return INPAINT_OK;
+}
+
+int inpaint_test_gemm_bf16(const void* A, const void* Bt, float* C, int M, int N, int K, void* stream) {
+  if (!A || !Bt || !C || M <= 0 || N <= 0 || K <= 0 || N % 64 || K % 64) return INPAINT_E_INVAL;
+  static int* err = nullptr;
+  if (!err) {
+    if (cudaMalloc(&err, 256) != cudaSuccess) return INPAINT_E_NOMEM;
+    cudaMemset(err, 0, 256);
+  }
+  return cuda_err(launch_gemm_tc(static_cast<const bf16*>(A), static_cast<const bf16*>(Bt), C, N, M, N, K, EPI_NONE,
+                                 nullptr, nullptr, err, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "inpaint.h"
+
+namespace inpaint {
+
+typedef __nv_bfloat16 bf16;
+
+// Kernel-class ids for event timing (match INPAINT_PROFILE_CLASSES in inpaint.h).
+enum KClass {
+  K_EMBED = 0, K_LN = 1, K_QKV = 2, K_ATTN = 3, K_PROJ = 4, K_FC1 = 5, K_FC2 = 6,
+  K_DEC1 = 7, K_DEC2 = 8, K_HEAD = 9, K_OTHER = 10
+};
+
+// Device-side error codes written into the context's error word.
+enum DevErr { DEV_OK = 0, DEV_MBAR_TIMEOUT = 1, DEV_BAD_SHAPE = 2 };
+
+// GEMM epilogues.
+enum Epi {
+  EPI_BIAS = 0,        // C = acc + bias                     (output type T)
+  EPI_BIAS_GELU = 1,   // C = gelu(acc + bias)               (output type T)
+  EPI_BIAS_RESID = 2,  // C(f32) = resid(f32) + acc + bias   (C may alias resid)
+  EPI_NONE = 3         // C(f32) = acc
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ float gelu_erf(float x) {
+  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752440f));
+}
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(bf16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ bf16 from_f32<bf16>(float v) { return __float2bfloat16_rn(v); }
+
+// ---------------------------------------------------------------------------- launchers
+// Every launcher enqueues on `st` and returns the cudaGetLastError() of its launch.
+
+// Patch embedding + token-mask init.  x [B,3,H,W] f32, hole [B,H,W] u8 -> tok f32
+// [B*Ht*Wt, d] (rows in raster token order), v0 u8 [B*Ht*Wt].
+cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt,
+                         const float* we, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st);
+
+// LayerNorm over the last dim (eps 1e-5, biased variance, FP32 statistics).
+template <typename OutT>
+cudaError_t launch_layernorm(const float* x, const float* g, const float* b, OutT* y, int M, int d,
+                             cudaStream_t st);
+
+// FP32 SIMT GEMM C[M,N] = epi(A[M,K] . B[K,N]) with row-major A (lda) and B (ldb).
+cudaError_t launch_gemm_f32(const float* A, int lda, const float* Bm, int ldb, float* C, int ldc,
+                            int M, int N, int K, int epi, const float* bias, const float* resid,
+                            cudaStream_t st);
+
+// BF16 tcgen05 GEMM C[M,N] = epi(A[M,K] . Bt[N,K]^T); A, Bt bf16 K-contiguous.
+// Output: bf16 for EPI_BIAS / EPI_BIAS_GELU, f32 for EPI_BIAS_RESID / EPI_NONE.
+cudaError_t launch_gemm_tc(const bf16* A, const bf16* Bt, void* C, int ldc, int M, int N, int K,
+                           int epi, const float* bias, const float* resid, int* err, cudaStream_t st);
+
+// Mask-aware window attention of all frames; qkv [B*Nt, 3d] (T), v_in/v_out u8 [B*Nt].
+template <typename T>
+cudaError_t launch_attention(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
+                             int Wt, int d, int heads, int offset, cudaStream_t st);
+
+// Decoder stage: out = gelu(conv3x3(upsample2(in)) + bias), NHWC.  wt: [9][Cin][Cout] f32.
+template <typename T>
+cudaError_t launch_upconv(const T* in, int B, int Hi, int Wi, int Cin, const float* wt,
+                          const float* bias, T* out, int Cout, cudaStream_t st);
+
+// Final 3x3 conv to RGB + composite + crop.  in NHWC [B,Hp,Wp,C]; wh [3][C][3][3] f32.
+template <typename T>
+cudaError_t launch_head_composite(const T* in, int B, int Hp, int Wp, int C, const float* wh,
+                                  const float* bh, const float* x, const uint8_t* hole, int H, int W,
+                                  float* out, float* pred, cudaStream_t st);
+
+// Hole-L1 loss: per-block partial sums into `partials` (>= loss_partials(n) floats),
+// then a fixed-order final reduction into *loss.
+int loss_partials(int B, int H, int W);
+cudaError_t launch_l1_hole_loss(const float* out, const float* target, const uint8_t* hole, int B,
+                                int H, int W, float* partials, unsigned* counts, float* loss,
+                                float* grad, cudaStream_t st);
+
+}  // namespace inpaint

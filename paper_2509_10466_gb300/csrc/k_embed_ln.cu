@@ -1,0 +1,231 @@
+// Patch embedding with token-mask init, LayerNorm, and the hole-L1 loss.
+//
+// Patch embedding: the model input is the frame with its masked regions set to 0 plus
+// the known-pixel mask ("Inpainting Manager": the model accepts a frame with masked
+// regions set to 0); a 4x4 stride-4 convolution turns it into tokens.  Because the
+// patches do not overlap this is a GEMM over 64-value patches; with K = 64 it is
+// HBM-bound (13 B/pixel in, 4d B/token out), so it runs on the SIMT pipes.
+#include "common.cuh"
+
+namespace inpaint {
+
+namespace {
+
+constexpr int EMB_TOK = 16;  // tokens per CTA
+
+// we_t: embedding weights transposed to [64][d] (k = c*16 + i*4 + j) for coalesced reads.
+__global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole,
+                                                    int H, int W, int Ht, int Wt,
+                                                    const float* __restrict__ we_t, const float* __restrict__ be,
+                                                    int d, float* __restrict__ tok, uint8_t* __restrict__ v0) {
+  __shared__ float patch[EMB_TOK][64];
+  __shared__ int known_any[EMB_TOK];
+  const int b = blockIdx.y;
+  const int t0 = blockIdx.x * EMB_TOK;
+  const int Nt = Ht * Wt;
+  const size_t HW = (size_t)H * W;
+  if (threadIdx.x < EMB_TOK) known_any[threadIdx.x] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < EMB_TOK * 16; e += blockDim.x) {
+    const int tl = e >> 4, pix = e & 15;
+    const int t = t0 + tl;
+    float r = 0.f, g = 0.f, bl = 0.f, m = 0.f;
+    if (t < Nt) {
+      const int ty = t / Wt, tx = t - (t / Wt) * Wt;
+      const int y = ty * 4 + (pix >> 2), xx = tx * 4 + (pix & 3);
+      if (y < H && xx < W) {
+        const size_t p = (size_t)y * W + xx;
+        if (hole[(size_t)b * HW + p] == 0) {   // known pixel: keep it; hole pixels enter as 0
+          const float* xb = x + (size_t)b * 3 * HW + p;
+          r = xb[0]; g = xb[HW]; bl = xb[2 * HW];
+          m = 1.f;
+        }
+      }
+    }
+    patch[tl][pix] = r;
+    patch[tl][16 + pix] = g;
+    patch[tl][32 + pix] = bl;
+    patch[tl][48 + pix] = m;
+    if (m != 0.f) known_any[tl] = 1;  // every writer stores the same value
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < EMB_TOK * d; e += blockDim.x) {
+    const int tl = e / d, c = e - (e / d) * d;
+    const int t = t0 + tl;
+    if (t >= Nt) continue;
+    float acc = be[c];
+#pragma unroll 16
+    for (int k = 0; k < 64; ++k) acc = fmaf(we_t[k * d + c], patch[tl][k], acc);
+    tok[((size_t)b * Nt + t) * d + c] = acc;
+  }
+  if (threadIdx.x < EMB_TOK && t0 + (int)threadIdx.x < Nt)
+    v0[(size_t)b * Nt + t0 + threadIdx.x] = (uint8_t)known_any[threadIdx.x];
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp per row; NPER = values per lane (d <= 32 * NPER).
+template <typename OutT, int NPER>
+__global__ void __launch_bounds__(256) layernorm_kernel(const float* __restrict__ x, const float* __restrict__ g,
+                                                        const float* __restrict__ bta, OutT* __restrict__ y,
+                                                        int M, int d) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const float* xr = x + (size_t)row * d;
+  const int n = d >> 5;
+  float v[NPER];
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < NPER; ++i) {
+    v[i] = (i < n) ? xr[lane + 32 * i] : 0.f;
+    s += v[i];
+  }
+  const float mean = warp_sum(s) / (float)d;
+  float q = 0.f;
+#pragma unroll
+  for (int i = 0; i < NPER; ++i) {
+    const float t = (i < n) ? v[i] - mean : 0.f;
+    q = fmaf(t, t, q);
+  }
+  const float rstd = rsqrtf(warp_sum(q) / (float)d + 1e-5f);
+  OutT* yr = y + (size_t)row * d;
+#pragma unroll
+  for (int i = 0; i < NPER; ++i) {
+    if (i < n) {
+      const int c = lane + 32 * i;
+      yr[c] = from_f32<OutT>((v[i] - mean) * rstd * g[c] + bta[c]);
+    }
+  }
+}
+
+constexpr int LOSS_THREADS = 256;
+constexpr int LOSS_PIX_PER_CTA = 4096;
+
+// Pass 1: per-CTA sum of |out - target| over hole pixels and count of hole pixels.
+__global__ void __launch_bounds__(LOSS_THREADS) l1_partial_kernel(const float* __restrict__ out,
+                                                                  const float* __restrict__ tgt,
+                                                                  const uint8_t* __restrict__ hole, int HW,
+                                                                  size_t npix, float* partials,
+                                                                  unsigned* counts) {
+  __shared__ float ss[LOSS_THREADS];
+  __shared__ unsigned sc[LOSS_THREADS];
+  float s = 0.f;
+  unsigned c = 0;
+  const size_t base = (size_t)blockIdx.x * LOSS_PIX_PER_CTA;
+  for (int i = threadIdx.x; i < LOSS_PIX_PER_CTA; i += LOSS_THREADS) {
+    const size_t p = base + i;
+    if (p >= npix) break;
+    if (hole[p] != 0) {
+      const size_t b = p / HW, q = p - b * HW;
+      const size_t o = b * 3 * HW + q;
+      s += fabsf(out[o] - tgt[o]) + fabsf(out[o + HW] - tgt[o + HW]) + fabsf(out[o + 2 * HW] - tgt[o + 2 * HW]);
+      ++c;
+    }
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = LOSS_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      ss[threadIdx.x] += ss[threadIdx.x + w];
+      sc[threadIdx.x] += sc[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = ss[0];
+    counts[blockIdx.x] = sc[0];
+  }
+}
+
+// Pass 2: one CTA reduces the partials in a fixed order (FP64) and writes the loss;
+// counts[0] is overwritten with the total hole count for pass 3.
+__global__ void __launch_bounds__(LOSS_THREADS) l1_final_kernel(const float* partials, unsigned* counts, int n,
+                                                                float* loss) {
+  __shared__ double ss[LOSS_THREADS];
+  __shared__ unsigned long long sc[LOSS_THREADS];
+  double s = 0.0;
+  unsigned long long c = 0;
+  for (int i = threadIdx.x; i < n; i += LOSS_THREADS) {
+    s += (double)partials[i];
+    c += counts[i];
+  }
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = LOSS_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      ss[threadIdx.x] += ss[threadIdx.x + w];
+      sc[threadIdx.x] += sc[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    loss[0] = sc[0] ? (float)(ss[0] / (3.0 * (double)sc[0])) : 0.f;
+    counts[0] = (unsigned)sc[0];
+  }
+}
+
+// Pass 3: grad = sign(out - target) / (3 n_hole) on hole pixels, 0 elsewhere.
+__global__ void l1_grad_kernel(const float* __restrict__ out, const float* __restrict__ tgt,
+                               const uint8_t* __restrict__ hole, int HW, size_t npix,
+                               const unsigned* __restrict__ total, float* __restrict__ grad) {
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= npix) return;
+  const unsigned n = total[0];
+  const float scale = n ? 1.0f / (3.0f * (float)n) : 0.f;
+  const size_t b = p / HW, q = p - b * HW;
+  const size_t o = b * 3 * HW + q;
+  const bool h = hole[p] != 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float df = out[o + c * HW] - tgt[o + c * HW];
+    const float sg = df > 0.f ? 1.f : (df < 0.f ? -1.f : 0.f);
+    grad[o + c * HW] = h ? sg * scale : 0.f;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt,
+                         const float* we_t, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st) {
+  dim3 grid(cdiv(Ht * Wt, EMB_TOK), B);
+  embed_kernel<<<grid, 256, 0, st>>>(x, hole, H, W, Ht, Wt, we_t, be, d, tok, v0);
+  return cudaGetLastError();
+}
+
+template <typename OutT>
+cudaError_t launch_layernorm(const float* x, const float* g, const float* b, OutT* y, int M, int d,
+                             cudaStream_t st) {
+  const int blocks = cdiv(M, 8);
+  if (d <= 256)
+    layernorm_kernel<OutT, 8><<<blocks, 256, 0, st>>>(x, g, b, y, M, d);
+  else
+    layernorm_kernel<OutT, 32><<<blocks, 256, 0, st>>>(x, g, b, y, M, d);
+  return cudaGetLastError();
+}
+template cudaError_t launch_layernorm<float>(const float*, const float*, const float*, float*, int, int, cudaStream_t);
+template cudaError_t launch_layernorm<bf16>(const float*, const float*, const float*, bf16*, int, int, cudaStream_t);
+
+int loss_partials(int B, int H, int W) {
+  return (int)(((size_t)B * H * W + LOSS_PIX_PER_CTA - 1) / LOSS_PIX_PER_CTA);
+}
+
+cudaError_t launch_l1_hole_loss(const float* out, const float* target, const uint8_t* hole, int B, int H,
+                                int W, float* partials, unsigned* counts, float* loss, float* grad,
+                                cudaStream_t st) {
+  const size_t npix = (size_t)B * H * W;
+  const int nb = loss_partials(B, H, W);
+  l1_partial_kernel<<<nb, LOSS_THREADS, 0, st>>>(out, target, hole, H * W, npix, partials, counts);
+  l1_final_kernel<<<1, LOSS_THREADS, 0, st>>>(partials, counts, nb, loss);
+  if (grad)
+    l1_grad_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(out, target, hole, H * W, npix, counts, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace inpaint

@@ -1,0 +1,226 @@
+"""GPU parity of the CUDA path against the FP64 oracle (calls go through the C ABI)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_10466_gb300 import binding, synthetic as S
+from paper_2509_10466_gb300.config import BF16, FP32, ModelConfig, WORKLOAD_A, WORKLOAD_B
+
+from helpers import TOL_BF16, TOL_FP32, check_parity, gpu_forward, hole_rel_l2, inputs, lib, oracle_forward
+
+pytestmark = pytest.mark.gpu
+
+
+def small(precision, **kw):
+    base = dict(dim=64, heads=2, window=8, blocks=3, mlp_ratio=2, precision=precision)
+    base.update(kw)
+    return ModelConfig(**base)
+
+
+# ----------------------------------------------------------------------------- tensor-core GEMM unit
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (256, 256, 256), (384, 768, 256), (200, 128, 128),
+                                   (1000, 1024, 256), (4096, 256, 1024), (130, 192, 320)])
+def test_tcgen05_gemm_matches_fp32_matmul(M, N, K):
+    lib()
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).bfloat16()
+    Bt = torch.randn(N, K, generator=g).bfloat16()
+    ref = A.float() @ Bt.float().T
+    C = torch.full((M, N), float("nan"), device="cuda")
+    binding.inpaint_test_gemm_bf16(A.cuda(), Bt.cuda(), C)
+    torch.cuda.synchronize()
+    got = C.cpu()
+    assert torch.isfinite(got).all()
+    rel = (got - ref).norm() / ref.norm()
+    assert rel < 1e-5, float(rel)
+
+
+# ----------------------------------------------------------------------------- FP32 form
+
+def test_fp32_plain_256_matches_oracle():
+    """The plain FP32 workload: 256x256, d128 h4, 2 blocks, MLP ratio 2."""
+    w = WORKLOAD_A
+    weights = S.make_weights(w.model, seed=0, perturb=True)
+    x, hole = inputs(w.batch, w.height, w.width, w.mask_kind, seed=0)
+    check_parity(w.model, weights, x, hole, TOL_FP32)
+
+
+@pytest.mark.parametrize("H,W,B,shift", [(64, 64, 1, 1), (70, 45, 2, 1), (96, 160, 3, 0), (33, 130, 1, 1)])
+def test_fp32_ragged_shapes(H, W, B, shift):
+    cfg = small(FP32, shift=shift)
+    weights = S.make_weights(cfg, seed=H + W, perturb=True)
+    x, hole = inputs(B, H, W, "ellipse_strokes", seed=H * W, area=(0.2, 0.5))
+    check_parity(cfg, weights, x, hole, TOL_FP32)
+
+
+def test_fp32_thin_strokes_leave_windows_empty():
+    """Large holes: some windows have no valid key for several blocks."""
+    cfg = small(FP32, blocks=4)
+    weights = S.make_weights(cfg, seed=3, perturb=True)
+    x, hole = inputs(2, 128, 128, "large_and_thin", seed=5, area=(0.4, 0.9))
+    ref = oracle_forward(cfg, weights, x, hole)
+    assert (ref["masks"][1] == 0).any(), "fixture should contain skipped windows"
+    check_parity(cfg, weights, x, hole, TOL_FP32, ref=ref)
+
+
+# ----------------------------------------------------------------------------- BF16 form
+
+@pytest.mark.parametrize("H,W,B", [(64, 64, 1), (96, 128, 2), (70, 45, 1)])
+def test_bf16_small_shapes(H, W, B):
+    cfg = small(BF16)
+    weights = S.make_weights(cfg, seed=11, perturb=True)
+    x, hole = inputs(B, H, W, "polygons", seed=H + W)
+    check_parity(cfg, weights, x, hole, TOL_BF16)
+
+
+def test_bf16_precision_workload_512_full_size():
+    """Precision workload at full size: 4 frames of 512x512, d256 h8, 8 blocks, MLP ratio 4."""
+    w = WORKLOAD_B
+    weights = S.make_weights(w.model, seed=0)
+    x, hole = inputs(w.batch, w.height, w.width, w.mask_kind, seed=1)
+    gpu = gpu_forward(w.model, weights, x, hole)
+    ref = oracle_forward(w.model, weights, x, hole)
+    errs = check_parity(w.model, weights, x, hole, TOL_BF16, gpu=gpu, ref=ref)
+    print("bf16 512 rel-L2 per frame:", errs)
+
+
+def test_fp32_precision_workload_512_one_frame():
+    w = WORKLOAD_B
+    cfg = w.model.with_precision(FP32)
+    weights = S.make_weights(cfg, seed=0)
+    x, hole = inputs(1, w.height, w.width, w.mask_kind, seed=1)
+    errs = check_parity(cfg, weights, x, hole, TOL_FP32)
+    print("fp32 512 rel-L2:", errs)
+
+
+# ----------------------------------------------------------------------------- edge cases and invariants
+
+@pytest.mark.parametrize("precision", [FP32, BF16])
+def test_all_hole_and_no_hole_frames(precision):
+    cfg = small(precision)
+    weights = S.make_weights(cfg, seed=2, perturb=True)
+    x = S.make_frames(2, 64, 96, seed=2)
+    hole = np.zeros((2, 64, 96), np.uint8)
+    hole[0] = 1                                   # frame 0: everything private, frame 1: nothing
+    gpu = gpu_forward(cfg, weights, x, hole)
+    ref = oracle_forward(cfg, weights, x, hole)
+    np.testing.assert_array_equal(gpu["masks"], ref["masks"])
+    assert (gpu["masks"][:, 0] == 0).all() and (gpu["masks"][:, 1] == 1).all()
+    np.testing.assert_array_equal(gpu["out"][1], x[1])
+    tol = TOL_FP32 if precision == FP32 else TOL_BF16
+    assert hole_rel_l2(gpu["out"][:1], ref["out"][:1], hole[:1])[0] <= tol
+
+
+@pytest.mark.parametrize("precision", [FP32, BF16])
+def test_tiny_frame(precision):
+    cfg = small(precision, blocks=2)
+    weights = S.make_weights(cfg, seed=4, perturb=True)
+    x = S.make_frames(1, 5, 7, seed=4)
+    hole = np.zeros((1, 5, 7), np.uint8)
+    hole[0, 1:4, 2:5] = 1
+    check_parity(cfg, weights, x, hole, TOL_FP32 if precision == FP32 else TOL_BF16)
+
+
+@pytest.mark.parametrize("precision", [FP32, BF16])
+def test_hole_invariance_and_determinism_bitwise(precision):
+    cfg = small(precision)
+    weights = S.make_weights(cfg, seed=5, perturb=True)
+    x, hole = inputs(2, 96, 96, "ellipse_strokes", seed=6)
+    a = gpu_forward(cfg, weights, x, hole)
+    x2 = x.copy()
+    rng = np.random.default_rng(0)
+    noise = rng.uniform(-10, 10, x.shape).astype(np.float32)
+    hm = np.broadcast_to((hole != 0)[:, None], x.shape)
+    x2[hm] = noise[hm]
+    b = gpu_forward(cfg, weights, x2, hole)
+    np.testing.assert_array_equal(a["out"][hm], b["out"][hm])
+    c = gpu_forward(cfg, weights, x, hole)
+    np.testing.assert_array_equal(a["out"], c["out"])
+
+
+def test_batch_ws_and_host_paths_equal_batch():
+    cfg = small(BF16)
+    weights = S.make_weights(cfg, seed=7, perturb=True)
+    x, hole = inputs(2, 64, 128, "polygons", seed=7)
+    lib()
+    inp = binding.Inpainter(cfg, weights)
+    try:
+        xt, ht = torch.from_numpy(x).cuda(), torch.from_numpy(hole).cuda()
+        out1 = inp(xt, ht)
+        nbytes = binding.inpaint_workspace_bytes(inp.ctx, 2, 64, 128)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        out2 = torch.empty_like(xt)
+        binding.inpaint_batch_ws(inp.ctx, ws, xt, ht, out2)
+        out3 = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+        binding.inpaint_batch_host(inp.ctx, torch.from_numpy(x).pin_memory(), torch.from_numpy(hole).pin_memory(),
+                                   out3)
+        torch.cuda.synchronize()
+        assert torch.equal(out1.cpu(), out2.cpu())
+        assert torch.equal(out1.cpu(), out3)
+        small_ws = torch.empty(nbytes // 2, dtype=torch.uint8, device="cuda")
+        with pytest.raises(binding.InpaintError):
+            binding.inpaint_batch_ws(inp.ctx, small_ws, xt, ht, out2)
+    finally:
+        inp.close()
+
+
+def test_invalid_arguments_return_errors():
+    lib()
+    cfg = small(FP32)
+    inp = binding.Inpainter(cfg, S.make_weights(cfg))
+    try:
+        x = torch.zeros(1, 3, 32, 32, device="cuda")
+        h = torch.zeros(1, 32, 32, dtype=torch.uint8, device="cuda")
+        with pytest.raises(binding.InpaintError) as e:
+            binding.inpaint_batch(inp.ctx, x, h[:, :0], torch.empty_like(x))
+        assert e.value.code == binding.E_INVAL
+        with pytest.raises(binding.InpaintError):
+            binding.inpaint_init(cfg, np.zeros(10, np.float32))
+    finally:
+        inp.close()
+
+
+def test_hbm_budget_refuses_large_workspace():
+    lib()
+    cfg = small(FP32)
+    w = S.make_weights(cfg)
+    inp = binding.Inpainter(cfg, w, hbm_budget_bytes=64 << 20)
+    try:
+        x = torch.zeros(8, 3, 512, 512, device="cuda")
+        h = torch.zeros(8, 512, 512, dtype=torch.uint8, device="cuda")
+        with pytest.raises(binding.InpaintError) as e:
+            binding.inpaint_batch(inp.ctx, x, h, torch.empty_like(x))
+        assert e.value.code == binding.E_NOMEM
+    finally:
+        inp.close()
+
+
+# ----------------------------------------------------------------------------- loss
+
+def test_l1_hole_loss_matches_oracle():
+    from oracle import inpaint_oracle as O
+    lib()
+    cfg = small(FP32)
+    inp = binding.Inpainter(cfg, S.make_weights(cfg))
+    try:
+        B, H, W = 3, 70, 90
+        out = S.make_frames(B, H, W, seed=1)
+        tgt = S.make_target(B, H, W, seed=1)
+        hole = S.make_hole(B, H, W, "ellipse_strokes", seed=1)
+        tgt[0, :, :5, :5] = out[0, :, :5, :5]                       # exact ties: sign(0) = 0
+        loss = torch.zeros(1, device="cuda")
+        grad = torch.empty(B, 3, H, W, device="cuda")
+        binding.inpaint_l1_hole_loss(inp.ctx, torch.from_numpy(out).cuda(), torch.from_numpy(tgt).cuda(),
+                                     torch.from_numpy(hole).cuda(), loss, grad)
+        torch.cuda.synchronize()
+        rl, rg = O.l1_hole_loss(torch.from_numpy(out), torch.from_numpy(tgt), torch.from_numpy(hole))
+        assert abs(float(loss) - float(rl)) <= 1e-6 * float(rl)
+        np.testing.assert_allclose(grad.cpu().numpy(), rg.numpy(), rtol=1e-6, atol=0)
+        zero_hole = torch.zeros(B, H, W, dtype=torch.uint8, device="cuda")
+        binding.inpaint_l1_hole_loss(inp.ctx, torch.from_numpy(out).cuda(), torch.from_numpy(tgt).cuda(),
+                                     zero_hole, loss, grad)
+        torch.cuda.synchronize()
+        assert float(loss) == 0.0 and float(grad.abs().max()) == 0.0
+    finally:
+        inp.close()
