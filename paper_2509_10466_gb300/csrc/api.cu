@@ -7,11 +7,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "context.cuh"
 
 namespace inpaint {
-cudaError_t launch_gemm_f32_ex(bool ta, bool tb, const float* A, int lda, const float* Bm, int ldb, float* C, int ldc,
-                               int M, int N, int K, int splits, int epi, const float* bias, const float* resid,
-                               cudaStream_t st);
 int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* grad_out, int B, int H, int W,
                   float* grad_w, cudaStream_t st);
 }  // namespace inpaint
@@ -21,17 +19,6 @@ using namespace inpaint;
 // ------------------------------------------------------------------------- layout
 
 namespace {
-
-// Offsets (in floats) of every tensor of the weight blob, in blob order.
-struct BlockOff {
-  size_t ln1g, ln1b, qkvw, qkvb, projw, projb, ln2g, ln2b, fc1w, fc1b, fc2w, fc2b;
-};
-struct Offsets {
-  size_t embw, embb;
-  std::vector<BlockOff> blk;
-  size_t lnfg, lnfb, d1w, d1b, d2w, d2b, hw, hb;
-  size_t total;
-};
 
 bool check_cfg(const inpaint_config* c) {
   if (!c) return false;
@@ -108,94 +95,6 @@ __global__ void transpose_f32(const float* __restrict__ in, float* __restrict__ 
 }
 
 }  // namespace
-
-// ------------------------------------------------------------------------- context
-
-struct Plan {
-  int B, H, W, Hp, Wp, Ht, Wt, Nt, M;
-  size_t tok, ln, qkv, o, hid, masks, f1, f2, err, end;
-};
-
-struct EventPair {
-  cudaEvent_t a, b;
-  int cls;
-};
-
-struct inpaint_ctx {
-  inpaint_config cfg;
-  int d, heads, L, r, c1, c2, hid;
-  bool use_bf16;
-  Offsets off;
-  size_t nparams;
-  float* w32 = nullptr;        // float32 blob (device)
-  float* embed_wt = nullptr;   // [64][d]
-  float* dec1_wt = nullptr;    // [9][d][c1]
-  float* dec2_wt = nullptr;    // [9][c1][c2]
-  bf16* lin_bf16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
-  size_t lin_block_elems = 0;
-  size_t weight_bytes = 0;
-  int* dev_err = nullptr;
-  uint8_t* arena = nullptr;
-  size_t arena_bytes = 0;
-  // last internal-workspace forward, for inpaint_token_masks
-  bool have_masks = false;
-  Plan last{};
-  // host e2e staging
-  uint8_t* stage = nullptr;
-  size_t stage_bytes = 0;
-  // backward scratch
-  uint8_t* bws = nullptr;
-  size_t bws_bytes = 0;
-  // profiling
-  bool prof = false;
-  std::vector<EventPair> events;
-  size_t ev_used = 0;
-  int64_t launches = 0;
-};
-
-namespace inpaint {
-
-// Bracket one kernel launch with events when profiling is on; counts launches.
-struct LaunchScope {
-  inpaint_ctx* c;
-  cudaStream_t st;
-  int cls;
-  EventPair* ep = nullptr;
-  LaunchScope(inpaint_ctx* c_, cudaStream_t s, int k) : c(c_), st(s), cls(k) {
-    c->launches++;
-    if (!c->prof) return;
-    if (c->ev_used == c->events.size()) {
-      EventPair p;
-      if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return;
-      c->events.push_back(p);
-    }
-    ep = &c->events[c->ev_used++];
-    ep->cls = k;
-    cudaEventRecord(ep->a, st);
-  }
-  ~LaunchScope() {
-    if (ep) cudaEventRecord(ep->b, st);
-  }
-};
-
-int grow(uint8_t** buf, size_t* cap, size_t need, const inpaint_ctx* c, size_t other_bytes) {
-  if (need <= *cap) return INPAINT_OK;
-  if (c->cfg.hbm_budget_bytes && c->weight_bytes + other_bytes + need > c->cfg.hbm_budget_bytes) return INPAINT_E_NOMEM;
-  if (*buf) {
-    cudaFree(*buf);
-    *buf = nullptr;
-    *cap = 0;
-  }
-  if (cudaMalloc(buf, need) != cudaSuccess) {
-    cudaGetLastError();
-    *buf = nullptr;
-    return INPAINT_E_NOMEM;
-  }
-  *cap = need;
-  return INPAINT_OK;
-}
-
-}  // namespace inpaint
 
 namespace {
 

@@ -74,6 +74,18 @@ template <typename T>
 cudaError_t launch_upconv(const T* in, int B, int Hi, int Wi, int Cin, const float* wt,
                           const float* bias, T* out, int Cout, cudaStream_t st);
 
+// Generic FP32 3x3 conv (NHWC), optional x2 upsampling of the input, optional bias
+// (NULL = none), act 0 = identity / 1 = GELU, optional pre-activation output.
+cudaError_t launch_conv3x3_f32(const float* in, int B, int Hi, int Wi, int Cin, bool upsample, const float* wt,
+                               const float* bias, int act, float* out, float* preact, int Cout, cudaStream_t st);
+
+// FP32 SIMT GEMM with optional transposed operands and deterministic split-K: with
+// splits > 1 the raw partial products go to C + s*M*ldc (s = split) for a later
+// fixed-order reduction.
+cudaError_t launch_gemm_f32_ex(bool ta, bool tb, const float* A, int lda, const float* Bm, int ldb, float* C, int ldc,
+                               int M, int N, int K, int splits, int epi, const float* bias, const float* resid,
+                               cudaStream_t st);
+
 // Final 3x3 conv to RGB + composite + crop.  in NHWC [B,Hp,Wp,C]; wh [3][C][3][3] f32.
 template <typename T>
 cudaError_t launch_head_composite(const T* in, int B, int Hp, int Wp, int C, const float* wh,

@@ -1,0 +1,114 @@
+// Library context and shared runtime helpers (internal).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace inpaint {
+
+// Offsets (in floats) of every tensor of the weight blob, in blob order.
+struct BlockOff {
+  size_t ln1g, ln1b, qkvw, qkvb, projw, projb, ln2g, ln2b, fc1w, fc1b, fc2w, fc2b;
+};
+struct Offsets {
+  size_t embw, embb;
+  std::vector<BlockOff> blk;
+  size_t lnfg, lnfb, d1w, d1b, d2w, d2b, hw, hb;
+  size_t total;
+};
+
+
+}  // namespace inpaint
+
+// ------------------------------------------------------------------------- context
+
+using inpaint::Offsets;
+using inpaint::BlockOff;
+
+struct Plan {
+  int B, H, W, Hp, Wp, Ht, Wt, Nt, M;
+  size_t tok, ln, qkv, o, hid, masks, f1, f2, err, end;
+};
+
+struct EventPair {
+  cudaEvent_t a, b;
+  int cls;
+};
+
+struct inpaint_ctx {
+  inpaint_config cfg;
+  int d, heads, L, r, c1, c2, hid;
+  bool use_bf16;
+  Offsets off;
+  size_t nparams;
+  float* w32 = nullptr;        // float32 blob (device)
+  float* embed_wt = nullptr;   // [64][d]
+  float* dec1_wt = nullptr;    // [9][d][c1]
+  float* dec2_wt = nullptr;    // [9][c1][c2]
+  inpaint::bf16* lin_bf16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
+  size_t lin_block_elems = 0;
+  size_t weight_bytes = 0;
+  int* dev_err = nullptr;
+  uint8_t* arena = nullptr;
+  size_t arena_bytes = 0;
+  // last internal-workspace forward, for inpaint_token_masks
+  bool have_masks = false;
+  Plan last{};
+  // host e2e staging
+  uint8_t* stage = nullptr;
+  size_t stage_bytes = 0;
+  // backward scratch
+  uint8_t* bws = nullptr;
+  size_t bws_bytes = 0;
+  // profiling
+  bool prof = false;
+  std::vector<EventPair> events;
+  size_t ev_used = 0;
+  int64_t launches = 0;
+};
+
+namespace inpaint {
+
+// Bracket one kernel launch with events when profiling is on; counts launches.
+struct LaunchScope {
+  inpaint_ctx* c;
+  cudaStream_t st;
+  int cls;
+  EventPair* ep = nullptr;
+  LaunchScope(inpaint_ctx* c_, cudaStream_t s, int k) : c(c_), st(s), cls(k) {
+    c->launches++;
+    if (!c->prof) return;
+    if (c->ev_used == c->events.size()) {
+      EventPair p;
+      if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return;
+      c->events.push_back(p);
+    }
+    ep = &c->events[c->ev_used++];
+    ep->cls = k;
+    cudaEventRecord(ep->a, st);
+  }
+  ~LaunchScope() {
+    if (ep) cudaEventRecord(ep->b, st);
+  }
+};
+
+inline int grow(uint8_t** buf, size_t* cap, size_t need, const inpaint_ctx* c, size_t other_bytes) {
+  if (need <= *cap) return INPAINT_OK;
+  if (c->cfg.hbm_budget_bytes && c->weight_bytes + other_bytes + need > c->cfg.hbm_budget_bytes) return INPAINT_E_NOMEM;
+  if (*buf) {
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+  }
+  if (cudaMalloc(buf, need) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return INPAINT_E_NOMEM;
+  }
+  *cap = need;
+  return INPAINT_OK;
+}
+
+}  // namespace inpaint
+

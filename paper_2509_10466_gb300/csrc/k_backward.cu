@@ -1,10 +1,511 @@
-// Backward pass (weight gradients) of the inpainting forward.
+// Backward pass of the inpainting forward: the gradient of sum(out * grad_out) with
+// respect to every weight, for fine-tuning with the hole-L1 loss (the paper trains with
+// a per-pixel L1 loss weighted towards the masked region, "Training structure").
+//
+// FP32 throughout.  The forward is run once keeping only each block's input; the
+// reverse sweep recomputes one block at a time from its saved input (per-block
+// activation recomputation) and then applies the adjoint of each step:
+//   composite -> head conv -> GELU -> conv (+ x2 upsample adjoint) -> ... -> final LN
+//   block l: fc2 -> GELU -> fc1 -> LN2 (+ residual) -> proj -> masked window attention
+//            -> QKV -> LN1 (+ residual)
+//   patch embedding.
+// The token masks are integers and carry no gradient.  Every reduction (bias, LN scale
+// and shift, split-K weight gradients) sums fixed partitions in a fixed order, so the
+// result is bit-reproducible.
 #include "common.cuh"
+#include "context.cuh"
+
+#include <algorithm>
 
 namespace inpaint {
 
-int backward_impl(inpaint_ctx*, const float*, const uint8_t*, const float*, int, int, int, float*, cudaStream_t) {
-  return INPAINT_E_STATE;
+int gemm_split_count(int K, int splits);
+
+namespace {
+
+constexpr int WS = 8, SLOTS = 64, DH = 32;
+
+__device__ __forceinline__ float gelu_grad(float z) {
+  const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752440f));
+  const float pdf = 0.39894228040143267794f * expf(-0.5f * z * z);
+  return cdf + z * pdf;
+}
+
+__global__ void gelu_fwd_kernel(const float* __restrict__ z, float* __restrict__ h, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    h[i] = gelu_erf(z[i]);
+}
+
+__global__ void gelu_bwd_kernel(const float* __restrict__ z, float* __restrict__ g, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    g[i] *= gelu_grad(z[i]);
+}
+
+// out[i] = sum_s parts[s*n + i], s ascending.
+__global__ void reduce_splits_kernel(const float* __restrict__ parts, int splits, size_t n, float* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += parts[(size_t)k * n + i];
+    out[i] = s;
+  }
+}
+
+// part[c][n] = sum over rows [c*rows, (c+1)*rows) of A[m][n], rows in order.
+__global__ void colsum_partial_kernel(const float* __restrict__ A, int M, int N, int rows, float* __restrict__ part) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (n >= N) return;
+  const int m0 = c * rows, m1 = min(M, m0 + rows);
+  float s = 0.f;
+  for (int m = m0; m < m1; ++m) s += A[(size_t)m * N + n];
+  part[(size_t)c * N + n] = s;
+}
+
+// gp[b][y][x][c] over the padded frame: grad_out on hole pixels of the H x W crop, else 0.
+__global__ void pred_grad_kernel(const float* __restrict__ gout, const uint8_t* __restrict__ hole, int B, int H, int W,
+                                 int Hp, int Wp, float* __restrict__ gp) {
+  const size_t n = (size_t)B * Hp * Wp;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(i % Wp);
+    const int y = (int)((i / Wp) % Hp);
+    const int b = (int)(i / ((size_t)Wp * Hp));
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (y < H && xx < W) {
+      const size_t HW = (size_t)H * W, q = (size_t)y * W + xx;
+      if (hole[(size_t)b * HW + q] != 0) {
+        const float* g = gout + (size_t)b * 3 * HW + q;
+        g0 = g[0]; g1 = g[HW]; g2 = g[2 * HW];
+      }
+    }
+    gp[i * 3 + 0] = g0;
+    gp[i * 3 + 1] = g1;
+    gp[i * 3 + 2] = g2;
+  }
+}
+
+// out[p][c] = (UP ? upsample2(in) : in)[p + offset(tap)][c], zero outside.  in NHWC.
+template <bool UP>
+__global__ void im2col_tap_kernel(const float* __restrict__ in, int B, int Hi, int Wi, int C, int tap,
+                                  float* __restrict__ out) {
+  const int Ho = UP ? 2 * Hi : Hi, Wo = UP ? 2 * Wi : Wi;
+  const int ky = tap / 3 - 1, kx = tap % 3 - 1;
+  const size_t n = (size_t)B * Ho * Wo * C;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const size_t p = i / C;
+    const int ox = (int)(p % Wo), oy = (int)((p / Wo) % Ho), b = (int)(p / ((size_t)Wo * Ho));
+    const int uy = oy + ky, ux = ox + kx;
+    float v = 0.f;
+    if (uy >= 0 && uy < Ho && ux >= 0 && ux < Wo) {
+      const int iy = UP ? uy >> 1 : uy, ix = UP ? ux >> 1 : ux;
+      v = in[(((size_t)b * Hi + iy) * Wi + ix) * C + c];
+    }
+    out[i] = v;
+  }
+}
+
+// gf[b][i][j][c] = sum of the 2x2 children of (i, j) in gu (adjoint of nearest x2 upsampling).
+__global__ void upsample_adjoint_kernel(const float* __restrict__ gu, int B, int Hi, int Wi, int C,
+                                        float* __restrict__ gf) {
+  const size_t n = (size_t)B * Hi * Wi * C;
+  const int Wo = 2 * Wi;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const size_t p = i / C;
+    const int x = (int)(p % Wi), y = (int)((p / Wi) % Hi), b = (int)(p / ((size_t)Wi * Hi));
+    const size_t r0 = ((size_t)b * 2 * Hi + 2 * y) * Wo + 2 * x;
+    const size_t r1 = r0 + Wo;
+    gf[i] = gu[r0 * C + c] + gu[(r0 + 1) * C + c] + gu[r1 * C + c] + gu[(r1 + 1) * C + c];
+  }
+}
+
+// Data-gradient weights of a 3x3 conv: wf[tap][co][ci] = w[co][ci][8 - tap] (input = grad, Cin' = Cout).
+__global__ void flip_conv_w_kernel(const float* __restrict__ w, int Cout, int Cin, float* __restrict__ wf) {
+  const size_t n = (size_t)9 * Cout * Cin;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(i % Cin);
+    const int co = (int)((i / Cin) % Cout);
+    const int tap = (int)(i / ((size_t)Cin * Cout));
+    wf[i] = w[((size_t)co * Cin + ci) * 9 + (8 - tap)];
+  }
+}
+
+// blob[co][ci][tap] = tmp[tap][co][ci]
+__global__ void tap_grad_scatter_kernel(const float* __restrict__ tmp, int Cout, int Cin, float* __restrict__ blob) {
+  const size_t n = (size_t)9 * Cout * Cin;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int tap = (int)(i % 9);
+    const size_t r = i / 9;
+    const int ci = (int)(r % Cin), co = (int)(r / Cin);
+    blob[i] = tmp[((size_t)tap * Cout + co) * Cin + ci];
+  }
+}
+
+// P[b*Nt + t][k], k = ch*16 + i*4 + j: the model input of token t's patch.
+__global__ void patch_matrix_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole, int B, int H,
+                                    int W, int Ht, int Wt, float* __restrict__ P) {
+  const size_t n = (size_t)B * Ht * Wt * 64;
+  const size_t HW = (size_t)H * W;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i & 63);
+    const size_t tok = i >> 6;
+    const int t = (int)(tok % ((size_t)Ht * Wt)), b = (int)(tok / ((size_t)Ht * Wt));
+    const int ch = k >> 4, pi = (k >> 2) & 3, pj = k & 3;
+    const int y = (t / Wt) * 4 + pi, xx = (t % Wt) * 4 + pj;
+    float v = 0.f;
+    if (y < H && xx < W && hole[(size_t)b * HW + (size_t)y * W + xx] == 0)
+      v = (ch < 3) ? x[((size_t)b * 3 + ch) * HW + (size_t)y * W + xx] : 1.f;
+    P[i] = v;
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// LayerNorm adjoint, one warp per row: gx = rstd*(gy*g - mean(gy*g) - xhat*mean(gy*g*xhat))
+// (+ gres when given); gyxhat = gy * xhat for the scale gradient.
+template <int NPER>
+__global__ void __launch_bounds__(256) ln_bwd_kernel(const float* __restrict__ x, const float* __restrict__ gamma,
+                                                     const float* __restrict__ gy, const float* __restrict__ gres,
+                                                     float* __restrict__ gx, float* __restrict__ gyxhat, int M,
+                                                     int d) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const size_t base = (size_t)row * d;
+  const int n = d >> 5;
+  float xv[NPER], gv[NPER];
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < NPER; ++i) {
+    xv[i] = (i < n) ? x[base + lane + 32 * i] : 0.f;
+    gv[i] = (i < n) ? gy[base + lane + 32 * i] : 0.f;
+    s += xv[i];
+  }
+  const float mean = warp_sum(s) / (float)d;
+  float q = 0.f;
+#pragma unroll
+  for (int i = 0; i < NPER; ++i) {
+    const float t = (i < n) ? xv[i] - mean : 0.f;
+    q = fmaf(t, t, q);
+  }
+  const float rstd = rsqrtf(warp_sum(q) / (float)d + 1e-5f);
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < NPER; ++i) {
+    if (i < n) {
+      const float xh = (xv[i] - mean) * rstd;
+      const float gxh = gv[i] * gamma[lane + 32 * i];
+      s1 += gxh;
+      s2 = fmaf(gxh, xh, s2);
+    }
+  }
+  s1 = warp_sum(s1) / (float)d;
+  s2 = warp_sum(s2) / (float)d;
+#pragma unroll
+  for (int i = 0; i < NPER; ++i) {
+    if (i < n) {
+      const int c = lane + 32 * i;
+      const float xh = (xv[i] - mean) * rstd;
+      const float gxh = gv[i] * gamma[c];
+      float g = rstd * (gxh - s1 - xh * s2);
+      if (gres) g += gres[base + c];
+      gx[base + c] = g;
+      gyxhat[base + c] = gv[i] * xh;
+    }
+  }
+}
+
+// Adjoint of the masked window attention for one (window, head, frame); 64 threads.
+struct AttnBwdSmem {
+  float Q[SLOTS][DH + 1], K[SLOTS][DH + 1], V[SLOTS][DH + 1], GO[SLOTS][DH + 1];
+  float P[SLOTS][SLOTS + 1], GS[SLOTS][SLOTS + 1];
+  int ok[SLOTS];
+};
+
+__global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict__ qkv, const uint8_t* __restrict__ v_in,
+                                                         const float* __restrict__ go, float* __restrict__ gqkv, int Ht,
+                                                         int Wt, int d, int offset, int nwx) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  AttnBwdSmem& sm = *reinterpret_cast<AttnBwdSmem*>(smem_raw);
+  const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  const int wy = w / nwx, wx = w - (w / nwx) * nwx;
+  const int s = threadIdx.x;
+  const int ty = wy * WS - offset + (s >> 3), tx = wx * WS - offset + (s & 7);
+  const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
+  const size_t t = real ? (size_t)b * Ht * Wt + (size_t)ty * Wt + tx : 0;
+  const bool ok = real && v_in[t] != 0;
+  sm.ok[s] = ok;
+  const float* row = qkv + t * 3 * d;
+  const float* grow_ = go + t * d + h * DH;
+  for (int i = 0; i < DH; ++i) {
+    sm.Q[s][i] = real ? row[h * DH + i] : 0.f;
+    sm.K[s][i] = ok ? row[d + h * DH + i] : 0.f;
+    sm.V[s][i] = ok ? row[2 * d + h * DH + i] : 0.f;
+    sm.GO[s][i] = real ? grow_[i] : 0.f;
+  }
+  const int any = __syncthreads_or(ok);
+  float* gq = gqkv + t * 3 * d + h * DH;
+  if (!any) {
+    if (real)
+      for (int i = 0; i < DH; ++i) { gq[i] = 0.f; gq[d + i] = 0.f; gq[2 * d + i] = 0.f; }
+    return;
+  }
+  const float scale = 1.0f / sqrtf((float)DH);
+  // query side: probabilities, score gradients, dQ
+  if (real) {
+    float mx = -INFINITY;
+    for (int k = 0; k < SLOTS; ++k) {
+      if (!sm.ok[k]) continue;
+      float sc = 0.f;
+      for (int i = 0; i < DH; ++i) sc = fmaf(sm.Q[s][i], sm.K[k][i], sc);
+      mx = fmaxf(mx, sc * scale);
+    }
+    float l = 0.f;
+    for (int k = 0; k < SLOTS; ++k) {
+      float p = 0.f;
+      if (sm.ok[k]) {
+        float sc = 0.f;
+        for (int i = 0; i < DH; ++i) sc = fmaf(sm.Q[s][i], sm.K[k][i], sc);
+        p = expf(sc * scale - mx);
+      }
+      sm.P[s][k] = p;
+      l += p;
+    }
+    const float inv = 1.f / l;
+    float D = 0.f;
+    for (int k = 0; k < SLOTS; ++k) {
+      const float p = sm.P[s][k] * inv;
+      sm.P[s][k] = p;
+      float gp = 0.f;
+      if (sm.ok[k])
+        for (int i = 0; i < DH; ++i) gp = fmaf(sm.GO[s][i], sm.V[k][i], gp);
+      sm.GS[s][k] = gp;
+      D = fmaf(p, gp, D);
+    }
+    float acc[DH];
+    for (int i = 0; i < DH; ++i) acc[i] = 0.f;
+    for (int k = 0; k < SLOTS; ++k) {
+      const float gs = sm.P[s][k] * (sm.GS[s][k] - D);
+      sm.GS[s][k] = gs;
+      if (sm.ok[k])
+        for (int i = 0; i < DH; ++i) acc[i] = fmaf(gs, sm.K[k][i], acc[i]);
+    }
+    for (int i = 0; i < DH; ++i) gq[i] = acc[i] * scale;
+  } else {
+    for (int k = 0; k < SLOTS; ++k) { sm.P[s][k] = 0.f; sm.GS[s][k] = 0.f; }
+  }
+  __syncthreads();
+  // key side: dK = scale * GS^T Q, dV = P^T dO
+  if (real) {
+    float gk[DH], gv[DH];
+    for (int i = 0; i < DH; ++i) { gk[i] = 0.f; gv[i] = 0.f; }
+    if (ok) {
+      for (int q = 0; q < SLOTS; ++q) {
+        const float gs = sm.GS[q][s], p = sm.P[q][s];
+        for (int i = 0; i < DH; ++i) {
+          gk[i] = fmaf(gs, sm.Q[q][i], gk[i]);
+          gv[i] = fmaf(p, sm.GO[q][i], gv[i]);
+        }
+      }
+    }
+    for (int i = 0; i < DH; ++i) {
+      gq[d + i] = gk[i] * scale;
+      gq[2 * d + i] = gv[i];
+    }
+  }
+}
+
+inline unsigned grid1d(size_t n) {
+  size_t g = (n + 255) / 256;
+  return (unsigned)(g > 65535 ? 65535 : (g ? g : 1));
+}
+
+}  // namespace
+
+int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* gout, int B, int H, int W,
+                  float* gw, cudaStream_t st) {
+  const Offsets& o = c->off;
+  const int Hp = (H + 31) / 32 * 32, Wp = (W + 31) / 32 * 32;
+  const int Ht = Hp / 4, Wt = Wp / 4, Nt = Ht * Wt, M = B * Nt;
+  const int d = c->d, hid = c->hid, L = c->L, c1 = c->c1, c2 = c->c2;
+  const size_t P1 = (size_t)B * 4 * Nt, P2 = (size_t)B * 16 * Nt;   // decoder stage-1 / stage-2 pixels
+  const int SPLIT_MAX = 64;
+  const size_t wmax = std::max({(size_t)d * 3 * d, (size_t)d * hid, (size_t)c1 * d, (size_t)c2 * c1, (size_t)d * 64,
+                                (size_t)3 * c2});
+  const size_t im2 = std::max({P2 * c2, P2 * c1, P1 * d, (size_t)M * 64});
+  const int CH = 128;  // column-sum chunks
+  const size_t nmax = std::max({(size_t)3 * d, (size_t)hid, (size_t)c1, (size_t)c2, (size_t)3});
+
+  // ---- workspace
+  size_t q = 0;
+  auto take = [&](size_t bytes) { size_t at = q; q = align_up(q + bytes, 256); return at; };
+  const size_t oX = take((size_t)(L + 1) * M * d * 4), oMask = take((size_t)(L + 1) * M);
+  const size_t oY1 = take((size_t)M * d * 4), oQKV = take((size_t)M * 3 * d * 4), oO = take((size_t)M * d * 4);
+  const size_t oXM = take((size_t)M * d * 4), oY2 = take((size_t)M * d * 4), oA = take((size_t)M * hid * 4);
+  const size_t oH = take((size_t)M * hid * 4), oGX = take((size_t)M * d * 4), oGXM = take((size_t)M * d * 4);
+  const size_t oGH = take((size_t)M * hid * 4), oGY = take((size_t)M * d * 4), oGQKV = take((size_t)M * 3 * d * 4);
+  const size_t oGO = take((size_t)M * d * 4), oGYX = take((size_t)M * d * 4);
+  const size_t oZ1 = take(P1 * c1 * 4), oF1 = take(P1 * c1 * 4), oZ2 = take(P2 * c2 * 4), oF2 = take(P2 * c2 * 4);
+  const size_t oGP = take(P2 * 3 * 4), oGF2 = take(P2 * c2 * 4), oGU1 = take(P2 * c1 * 4), oGF1 = take(P1 * c1 * 4);
+  const size_t oGU0 = take(P1 * d * 4), oIM = take(im2 * 4), oPART = take((size_t)SPLIT_MAX * wmax * 4);
+  const size_t oCS = take((size_t)CH * nmax * 4), oWF = take((size_t)9 * wmax * 4), oTAP = take((size_t)9 * wmax * 4);
+  int rc = grow(&c->bws, &c->bws_bytes, q, c, c->arena_bytes + c->stage_bytes);
+  if (rc != INPAINT_OK) return rc;
+  uint8_t* ws = c->bws;
+  auto F = [&](size_t off) { return reinterpret_cast<float*>(ws + off); };
+  float* X = F(oX);
+  uint8_t* masks = ws + oMask;
+  float *y1 = F(oY1), *qkv = F(oQKV), *ao = F(oO), *xm = F(oXM), *y2 = F(oY2), *a = F(oA), *hh = F(oH);
+  float *gx = F(oGX), *gxm = F(oGXM), *gh = F(oGH), *gy = F(oGY), *gqkv = F(oGQKV), *go = F(oGO), *gyx = F(oGYX);
+  float *z1 = F(oZ1), *f1 = F(oF1), *z2 = F(oZ2), *f2 = F(oF2), *gp = F(oGP), *gf2 = F(oGF2), *gu1 = F(oGU1);
+  float *gf1 = F(oGF1), *gu0 = F(oGU0), *im = F(oIM), *part = F(oPART), *cs = F(oCS), *wf = F(oWF), *tap = F(oTAP);
+  const float* w = c->w32;
+  auto Xl = [&](int l) { return X + (size_t)l * M * d; };
+
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+  auto K = [&](int cls) { return LaunchScope(c, st, cls); };
+
+  // column sums of A [rows][n] into dst[n]
+  auto colsum = [&](const float* A, int rows, int n, float* dst) {
+    const int rpc = (rows + CH - 1) / CH;
+    const int chunks = (rows + rpc - 1) / rpc;
+    { auto ls = K(K_OTHER); colsum_partial_kernel<<<dim3(cdiv(n, 256), chunks), 256, 0, st>>>(A, rows, n, rpc, cs); }
+    { auto ls = K(K_OTHER); reduce_splits_kernel<<<grid1d(n), 256, 0, st>>>(cs, chunks, (size_t)n, dst); }
+    ok(cudaGetLastError());
+  };
+  // dst[m][n] = sum_r A[r][m] * G[r][n]  (weight gradient X^T G), deterministic split-K
+  auto wgrad = [&](const float* A, int lda, int m, const float* G, int ldg, int n, int rows, float* dst) {
+    int splits = std::min(SPLIT_MAX, std::max(1, rows / 2048));
+    splits = gemm_split_count(rows, splits);
+    { auto ls = K(K_OTHER); ok(launch_gemm_f32_ex(true, false, A, lda, G, ldg, part, n, m, n, rows, splits, EPI_NONE, nullptr, nullptr, st)); }
+    { auto ls = K(K_OTHER); reduce_splits_kernel<<<grid1d((size_t)m * n), 256, 0, st>>>(part, splits, (size_t)m * n, dst); }
+    ok(cudaGetLastError());
+  };
+  // out[M][n] = G[M][k] . Wt^T where Wt is [n][k] row-major (a linear weight [in=n][out=k])
+  auto dgrad = [&](const float* G, int k, const float* Wm, int n, float* out) {
+    auto ls = K(K_OTHER);
+    ok(launch_gemm_f32_ex(false, true, G, k, Wm, k, out, n, M, n, k, 1, EPI_NONE, nullptr, nullptr, st));
+  };
+  // weight + bias gradient of a 3x3 conv whose output gradient is gz [P][cout] (NHWC)
+  // and whose input is `in` (NHWC [B, hi, wi, cin], upsampled first when up).
+  auto conv_wgrad = [&](const float* gz, int cout, const float* in, int hi, int wi, int cin, bool up, size_t P,
+                        size_t wofs, size_t bofs) {
+    colsum(gz, (int)P, cout, gw + bofs);
+    for (int t = 0; t < 9; ++t) {
+      {
+        auto ls = K(K_OTHER);
+        if (up) im2col_tap_kernel<true><<<grid1d(P * cin), 256, 0, st>>>(in, B, hi, wi, cin, t, im);
+        else im2col_tap_kernel<false><<<grid1d(P * cin), 256, 0, st>>>(in, B, hi, wi, cin, t, im);
+      }
+      wgrad(gz, cout, cout, im, cin, cin, (int)P, tap + (size_t)t * cout * cin);
+    }
+    { auto ls = K(K_OTHER); tap_grad_scatter_kernel<<<grid1d((size_t)9 * cout * cin), 256, 0, st>>>(tap, cout, cin, gw + wofs); }
+    ok(cudaGetLastError());
+  };
+  auto ln_bwd = [&](const float* xin, const float* g, const float* gyv, const float* gres, float* gxo, size_t gofs,
+                    size_t bofs) {
+    {
+      auto ls = K(K_OTHER);
+      if (d <= 256) ln_bwd_kernel<8><<<cdiv(M, 8), 256, 0, st>>>(xin, g, gyv, gres, gxo, gyx, M, d);
+      else ln_bwd_kernel<32><<<cdiv(M, 8), 256, 0, st>>>(xin, g, gyv, gres, gxo, gyx, M, d);
+    }
+    ok(cudaGetLastError());
+    colsum(gyx, M, d, gw + gofs);
+    colsum(gyv, M, d, gw + bofs);
+  };
+  // block l forward from X[l]; keeps y1, qkv, o, xm, y2, a, h; writes X[l+1] when `out`
+  auto block_fwd = [&](int l, bool out) {
+    const BlockOff& bo = o.blk[l];
+    const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
+    { auto ls = K(K_LN); ok(launch_layernorm<float>(Xl(l), w + bo.ln1g, w + bo.ln1b, y1, M, d, st)); }
+    { auto ls = K(K_QKV); ok(launch_gemm_f32(y1, d, w + bo.qkvw, 3 * d, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, w + bo.qkvb, nullptr, st)); }
+    { auto ls = K(K_ATTN); ok(launch_attention<float>(qkv, masks + (size_t)l * M, ao, masks + (size_t)(l + 1) * M, B, Ht, Wt, d, c->heads, offset, st)); }
+    { auto ls = K(K_PROJ); ok(launch_gemm_f32(ao, d, w + bo.projw, d, xm, d, M, d, d, EPI_BIAS_RESID, w + bo.projb, Xl(l), st)); }
+    { auto ls = K(K_LN); ok(launch_layernorm<float>(xm, w + bo.ln2g, w + bo.ln2b, y2, M, d, st)); }
+    { auto ls = K(K_FC1); ok(launch_gemm_f32(y2, d, w + bo.fc1w, hid, a, hid, M, hid, d, EPI_BIAS, w + bo.fc1b, nullptr, st)); }
+    { auto ls = K(K_OTHER); gelu_fwd_kernel<<<grid1d((size_t)M * hid), 256, 0, st>>>(a, hh, (size_t)M * hid); }
+    if (out) { auto ls = K(K_FC2); ok(launch_gemm_f32(hh, hid, w + bo.fc2w, d, Xl(l + 1), d, M, d, hid, EPI_BIAS_RESID, w + bo.fc2b, xm, st)); }
+    ok(cudaGetLastError());
+  };
+
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(attn_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(AttnBwdSmem)) !=
+        cudaSuccess)
+      return INPAINT_E_CUDA;
+    attr = true;
+  }
+
+  ok(cudaMemsetAsync(gw, 0, c->nparams * 4, st));
+  // ---- forward, keeping the block inputs
+  { auto ls = K(K_EMBED); ok(launch_embed(x, hole, B, H, W, Ht, Wt, c->embed_wt, w + o.embb, d, X, masks, st)); }
+  for (int l = 0; l < L; ++l) block_fwd(l, true);
+  float* yf = y1;
+  { auto ls = K(K_LN); ok(launch_layernorm<float>(Xl(L), w + o.lnfg, w + o.lnfb, yf, M, d, st)); }
+  { auto ls = K(K_DEC1); ok(launch_conv3x3_f32(yf, B, Ht, Wt, d, true, c->dec1_wt, w + o.d1b, 1, f1, z1, c1, st)); }
+  { auto ls = K(K_DEC2); ok(launch_conv3x3_f32(f1, B, 2 * Ht, 2 * Wt, c1, true, c->dec2_wt, w + o.d2b, 1, f2, z2, c2, st)); }
+
+  // ---- head conv and composite
+  { auto ls = K(K_OTHER); pred_grad_kernel<<<grid1d(P2), 256, 0, st>>>(gout, hole, B, H, W, Hp, Wp, gp); }
+  conv_wgrad(gp, 3, f2, Hp, Wp, c2, false, P2, o.hw, o.hb);
+  { auto ls = K(K_OTHER); flip_conv_w_kernel<<<grid1d((size_t)27 * c2), 256, 0, st>>>(w + o.hw, 3, c2, wf); }
+  { auto ls = K(K_OTHER); ok(launch_conv3x3_f32(gp, B, Hp, Wp, 3, false, wf, nullptr, 0, gf2, nullptr, c2, st)); }
+  // ---- decoder stage 2
+  { auto ls = K(K_OTHER); gelu_bwd_kernel<<<grid1d(P2 * c2), 256, 0, st>>>(z2, gf2, P2 * c2); }
+  conv_wgrad(gf2, c2, f1, 2 * Ht, 2 * Wt, c1, true, P2, o.d2w, o.d2b);
+  { auto ls = K(K_OTHER); flip_conv_w_kernel<<<grid1d((size_t)9 * c2 * c1), 256, 0, st>>>(w + o.d2w, c2, c1, wf); }
+  { auto ls = K(K_OTHER); ok(launch_conv3x3_f32(gf2, B, Hp, Wp, c2, false, wf, nullptr, 0, gu1, nullptr, c1, st)); }
+  { auto ls = K(K_OTHER); upsample_adjoint_kernel<<<grid1d(P1 * c1), 256, 0, st>>>(gu1, B, 2 * Ht, 2 * Wt, c1, gf1); }
+  // ---- decoder stage 1
+  { auto ls = K(K_OTHER); gelu_bwd_kernel<<<grid1d(P1 * c1), 256, 0, st>>>(z1, gf1, P1 * c1); }
+  conv_wgrad(gf1, c1, yf, Ht, Wt, d, true, P1, o.d1w, o.d1b);
+  { auto ls = K(K_OTHER); flip_conv_w_kernel<<<grid1d((size_t)9 * c1 * d), 256, 0, st>>>(w + o.d1w, c1, d, wf); }
+  { auto ls = K(K_OTHER); ok(launch_conv3x3_f32(gf1, B, 2 * Ht, 2 * Wt, c1, false, wf, nullptr, 0, gu0, nullptr, d, st)); }
+  { auto ls = K(K_OTHER); upsample_adjoint_kernel<<<grid1d((size_t)M * d), 256, 0, st>>>(gu0, B, Ht, Wt, d, gy); }
+  // ---- final LayerNorm
+  ln_bwd(Xl(L), w + o.lnfg, gy, nullptr, gx, o.lnfg, o.lnfb);
+
+  // ---- blocks, last to first, each recomputed from its saved input
+  for (int l = L - 1; l >= 0; --l) {
+    const BlockOff& bo = o.blk[l];
+    const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
+    block_fwd(l, false);
+    // MLP: x_{l+1} = xm + gelu(y2 W1 + b1) W2 + b2
+    colsum(gx, M, d, gw + bo.fc2b);
+    wgrad(hh, hid, hid, gx, d, d, M, gw + bo.fc2w);
+    dgrad(gx, d, w + bo.fc2w, hid, gh);
+    { auto ls = K(K_OTHER); gelu_bwd_kernel<<<grid1d((size_t)M * hid), 256, 0, st>>>(a, gh, (size_t)M * hid); }
+    colsum(gh, M, hid, gw + bo.fc1b);
+    wgrad(y2, d, d, gh, hid, hid, M, gw + bo.fc1w);
+    dgrad(gh, hid, w + bo.fc1w, d, gy);
+    ln_bwd(xm, w + bo.ln2g, gy, gx, gxm, bo.ln2g, bo.ln2b);
+    // attention: xm = x_l + attn(LN1(x_l)) Wo + bo
+    colsum(gxm, M, d, gw + bo.projb);
+    wgrad(ao, d, d, gxm, d, d, M, gw + bo.projw);
+    dgrad(gxm, d, w + bo.projw, d, go);
+    {
+      auto ls = K(K_OTHER);
+      const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
+      attn_bwd_kernel<<<dim3(nwy * nwx, c->heads, B), SLOTS, sizeof(AttnBwdSmem), st>>>(
+          qkv, masks + (size_t)l * M, go, gqkv, Ht, Wt, d, offset, nwx);
+      ok(cudaGetLastError());
+    }
+    colsum(gqkv, M, 3 * d, gw + bo.qkvb);
+    wgrad(y1, d, d, gqkv, 3 * d, 3 * d, M, gw + bo.qkvw);
+    dgrad(gqkv, 3 * d, w + bo.qkvw, d, gy);
+    ln_bwd(Xl(l), w + bo.ln1g, gy, gxm, gx, bo.ln1g, bo.ln1b);
+  }
+  // ---- patch embedding
+  colsum(gx, M, d, gw + o.embb);
+  { auto ls = K(K_OTHER); patch_matrix_kernel<<<grid1d((size_t)M * 64), 256, 0, st>>>(x, hole, B, H, W, Ht, Wt, im); }
+  wgrad(gx, d, d, im, 64, 64, M, gw + o.embw);
+  ok(cudaGetLastError());
+  return e == cudaSuccess ? INPAINT_OK : INPAINT_E_CUDA;
 }
 
 }  // namespace inpaint

@@ -19,10 +19,13 @@ constexpr int TPIX = 64;  // 8x8 output pixels per CTA
 constexpr int TCO = 64;   // output channels per CTA
 constexpr int KC = 16;    // input channels per step
 
+// out = act(conv3x3(UP ? upsample2(in) : in) + bias); bias may be NULL; act: 0 none,
+// 1 GELU; if `preact` is given it also receives the value before the activation.
 template <typename T, bool UP>
 __global__ void __launch_bounds__(256) upconv_simt_kernel(const T* __restrict__ in, int Hi, int Wi, int Cin,
                                                           const float* __restrict__ wt, const float* __restrict__ bias,
-                                                          T* __restrict__ out, int Cout) {
+                                                          T* __restrict__ out, int Cout, int act,
+                                                          float* __restrict__ preact) {
   __shared__ __align__(16) float As[KC][TPIX];
   __shared__ __align__(16) float Bs[KC][TCO];
   const int Ho = UP ? 2 * Hi : Hi, Wo = UP ? 2 * Wi : Wi;
@@ -84,11 +87,15 @@ __global__ void __launch_bounds__(256) upconv_simt_kernel(const T* __restrict__ 
     const int p = pg * 4 + i;
     const int oy = oy0 + (p >> 3), ox = ox0 + (p & 7);
     if (oy >= Ho || ox >= Wo) continue;
-    T* dst = out + (((size_t)b * Ho + oy) * Wo + ox) * Cout;
+    const size_t pix = ((size_t)b * Ho + oy) * Wo + ox;
+    T* dst = out + pix * Cout;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int co = co0 + cg * 4 + j;
-      if (co < Cout) dst[co] = from_f32<T>(gelu_erf(acc[i][j] + bias[co]));
+      if (co >= Cout) continue;
+      const float z = acc[i][j] + (bias ? bias[co] : 0.f);
+      if (preact) preact[pix * Cout + co] = z;
+      dst[co] = from_f32<T>(act ? gelu_erf(z) : z);
     }
   }
 }
@@ -145,7 +152,18 @@ cudaError_t launch_upconv(const T* in, int B, int Hi, int Wi, int Cin, const flo
                           int Cout, cudaStream_t st) {
   const int Ho = 2 * Hi, Wo = 2 * Wi;
   dim3 grid(cdiv(Ho, 8) * cdiv(Wo, 8), cdiv(Cout, TCO), B);
-  upconv_simt_kernel<T, true><<<grid, 256, 0, st>>>(in, Hi, Wi, Cin, wt, bias, out, Cout);
+  upconv_simt_kernel<T, true><<<grid, 256, 0, st>>>(in, Hi, Wi, Cin, wt, bias, out, Cout, 1, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv3x3_f32(const float* in, int B, int Hi, int Wi, int Cin, bool upsample, const float* wt,
+                               const float* bias, int act, float* out, float* preact, int Cout, cudaStream_t st) {
+  const int Ho = upsample ? 2 * Hi : Hi, Wo = upsample ? 2 * Wi : Wi;
+  dim3 grid(cdiv(Ho, 8) * cdiv(Wo, 8), cdiv(Cout, TCO), B);
+  if (upsample)
+    upconv_simt_kernel<float, true><<<grid, 256, 0, st>>>(in, Hi, Wi, Cin, wt, bias, out, Cout, act, preact);
+  else
+    upconv_simt_kernel<float, false><<<grid, 256, 0, st>>>(in, Hi, Wi, Cin, wt, bias, out, Cout, act, preact);
   return cudaGetLastError();
 }
 template cudaError_t launch_upconv<float>(const float*, int, int, int, int, const float*, const float*, float*, int,

@@ -153,3 +153,14 @@ cudaError_t launch_gemm_f32(const float* A, int lda, const float* Bm, int ldb, f
 }
 
 }  // namespace inpaint
+
+namespace inpaint {
+// Number of K splits launch_gemm_f32_ex actually uses for a requested count.
+int gemm_split_count(int K, int splits) {
+  if (splits < 1) splits = 1;
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  const int s = (K + kchunk - 1) / kchunk;
+  return s < 1 ? 1 : s;
+}
+}  // namespace inpaint
