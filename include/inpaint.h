@@ -151,6 +151,26 @@ INPAINT_API int inpaint_l1_hole_loss(inpaint_ctx* ctx, const float* out, const f
                          const uint8_t* hole, int B, int H, int W, float* loss_dev,
                          float* grad_out_dev, void* stream);
 
+/* Allocation-free form of inpaint_l1_hole_loss for callers that must not allocate
+ * device memory: processes whose device memory belongs to another allocator, per-frame
+ * real-time loops where cudaMalloc/cudaFree would synchronize the device and stall
+ * other streams, and deployments that forbid allocation after start-up.  The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ * Same arguments, result and fixed-order reduction as inpaint_l1_hole_loss, but no
+ * context and no allocation: its scratch (32 KiB of partial sums) is a fixed array in
+ * the library's device module, present on every device that loads the library until
+ * the process exits.  The first call on a device looks up that array's device address
+ * with the device current (cudaGetSymbolAddress), so make the first call on each
+ * device before any stream capture.  Every call on a device shares the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * ordered by the caller; each call rewrites every scratch value it reads, so leftovers
+ * of an earlier call never leak into a result.  Returns INPAINT_E_INVAL, launching
+ * nothing, when B*H*W exceeds INPAINT_L1_NOALLOC_MAX_PIXELS (4096 x 4096 pixels). */
+#define INPAINT_L1_NOALLOC_MAX_PIXELS (4096 * 4096)
+INPAINT_API int inpaint_l1_hole_loss_noalloc(const float* out, const float* target,
+                                             const uint8_t* hole, int B, int H, int W,
+                                             float* loss_dev, float* grad_out_dev, void* stream);
+
 /* Gradient of sum(out * grad_out) with respect to the weight blob, written to
  * grad_weights (device float32, num_params values, overwritten).  Recomputes the
  * forward, keeping only each block's input, and recomputes each block again during

@@ -56,6 +56,7 @@ _SIGS = {
     "inpaint_batch_host": (_I, [_P, _P, _P, _I, _I, _I, _P, _P]),
     "inpaint_token_masks": (_I, [_P, _P, ctypes.c_size_t]),
     "inpaint_l1_hole_loss": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "inpaint_l1_hole_loss_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "inpaint_backward": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P]),
     "inpaint_sync": (_I, [_P, _P, _I]),
     "inpaint_profile_enable": (_I, [_P, _I]),
@@ -193,6 +194,13 @@ def inpaint_l1_hole_loss(ctx, out, target, hole, loss, grad_out=None, stream=Non
     B, H, W = hole.shape
     _check(load().inpaint_l1_hole_loss(ctx, _ptr(out), _ptr(target), _ptr(hole), B, H, W, _ptr(loss),
                                        _ptr(grad_out), _stream(stream)), "inpaint_l1_hole_loss")
+
+
+def inpaint_l1_hole_loss_noalloc(out, target, hole, loss, grad_out=None, stream=None):
+    """Hole-L1 loss that allocates no device memory (fixed library scratch; see inpaint.h)."""
+    B, H, W = hole.shape
+    _check(load().inpaint_l1_hole_loss_noalloc(_ptr(out), _ptr(target), _ptr(hole), B, H, W, _ptr(loss),
+                                               _ptr(grad_out), _stream(stream)), "inpaint_l1_hole_loss_noalloc")
 
 
 def inpaint_backward(ctx, x, hole, grad_out, grad_weights, stream=None):
