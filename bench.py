@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--size", type=int, default=None, help="override H = W (small ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=20.0,
+                    help="length of the serving run (4 collaborators, 30 fps each); 0 skips it")
     return ap.parse_args()
 
 
@@ -395,6 +397,18 @@ def main():
                "sample": f"1 of the {B} frames ({H}x{W}), full model, FP64, {dt:.1f} s"}
 
     inp.close()
+
+    # ---- serving: 4 collaborators (256^2, 512^2, 720p, 720p) at 30 fps, continuous batching
+    serving = None
+    if args.serving_seconds > 0 and args.batch is None and args.size is None:
+        from paper_2509_10466_gb300.config import SERVING_RESOLUTIONS, WORKLOAD_D_MODEL
+        from paper_2509_10466_gb300.serving import serve
+        rep, _ = serve(WORKLOAD_D_MODEL, S.make_weights(WORKLOAD_D_MODEL, seed=0), SERVING_RESOLUTIONS,
+                       fps=30.0, seconds=args.serving_seconds, seed=rank)
+        serving = {"workload": "4 collaborators x 30 fps Poisson, 256x256 / 512x512 / 720x1280 / 720x1280, "
+                               "drifting-blob holes, d256 h8 L8 r4 BF16, host frames copied in and out",
+                   "seconds": args.serving_seconds, **rep}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -413,6 +427,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
             "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line))
     if dist:

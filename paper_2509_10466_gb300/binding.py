@@ -109,7 +109,12 @@ def _stream(stream):
 
 
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    """Raw pointer of a tensor; the C ABI reads dense row-major memory, so strided views are refused."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to libinpaint must be contiguous (call .contiguous() first)")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 # ----------------------------------------------------------------------------- same-name wrappers

@@ -137,6 +137,10 @@ int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
   transpose_f32<<<64, 256, 0, st>>>(c->w32 + o.embw, c->embed_wt, c->d, 64);
   conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d1w, c->dec1_wt, c->c1, c->d);
   conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d2w, c->dec2_wt, c->c2, c->c1);
+  if (c->use_bf16 && c->dec1_wp && launch_subpixel_weights(c->w32 + o.d1w, c->c1, c->d, c->dec1_wp, st) != cudaSuccess)
+    return INPAINT_E_CUDA;
+  if (c->use_bf16 && c->dec2_wp && launch_subpixel_weights(c->w32 + o.d2w, c->c2, c->c1, c->dec2_wp, st) != cudaSuccess)
+    return INPAINT_E_CUDA;
   if (c->use_bf16) {
     const int d = c->d, h = c->hid;
     for (int l = 0; l < c->L; ++l) {
@@ -163,10 +167,26 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
   float* tok = reinterpret_cast<float*>(ws + p.tok);
   uint8_t* masks = ws + p.masks;
   int* err = c->dev_err;
+  // BF16 form: the embedding also writes the first LayerNorm (block 0's LN1, or the final
+  // LN when there are no blocks) straight into the bf16 GEMM operand
+  bool ln_ready = false;
   {
     LaunchScope ls(c, st, K_EMBED);
-    TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st)));
+    if (c->use_bf16) {
+      const float* g0 = c->w32 + (c->L ? o.blk[0].ln1g : o.lnfg);
+      const float* b0 = c->w32 + (c->L ? o.blk[0].ln1b : o.lnfb);
+      TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st,
+                                g0, b0, reinterpret_cast<bf16*>(ws + p.ln))));
+      ln_ready = true;
+    } else {
+      TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st)));
+    }
   }
+  // BF16 form: the LayerNorm that follows each residual update is fused into the GEMM
+  // epilogue that produces it (proj -> LN2, fc2 -> next LN1 or the final LN) when a
+  // tile spans the whole row; `ln_ready` tracks whether `ln` already holds the input
+  // LayerNorm of the next GEMM.
+  const bool fuse_ln = c->use_bf16 && gemm_tc_ln_supported(d);
   for (int l = 0; l < c->L; ++l) {
     const BlockOff& b = o.blk[l];
     const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
@@ -182,13 +202,39 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       const bf16* wproj = wl + (size_t)3 * d * d;
       const bf16* wfc1 = wl + (size_t)4 * d * d;
       const bf16* wfc2 = wfc1 + (size_t)c->hid * d;
-      { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
+      if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
       { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, err, st))); }
-      { LaunchScope ls(c, st, K_ATTN); TRY(cuda_err(launch_attention<bf16>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st))); }
-      { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_tc(ao, wproj, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, err, st))); }
-      { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
+      { LaunchScope ls(c, st, K_ATTN); TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st))); }
+      if (fuse_ln) {
+        LaunchScope ls(c, st, K_PROJ);
+        TRY(cuda_err(launch_gemm_tc_resid_ln(ao, wproj, tok, M, d, d, c->w32 + b.projb, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, err, st)));
+      } else {
+        { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_tc(ao, wproj, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, err, st))); }
+        { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
+      }
+      if (fuse_ln && mlp_tc_supported(d, c->hid)) {
+        // whole MLP in one kernel: the hidden activations stay on chip
+        const bool last = l + 1 == c->L;
+        const float* ng = c->w32 + (last ? o.lnfg : o.blk[l + 1].ln1g);
+        const float* nb = c->w32 + (last ? o.lnfb : o.blk[l + 1].ln1b);
+        LaunchScope ls(c, st, K_FC1);
+        TRY(cuda_err(launch_mlp_tc(ln, wfc1, wfc2, c->w32 + b.fc1b, c->w32 + b.fc2b, tok, ng, nb, ln, M, d, c->hid, err, st)));
+        ln_ready = true;
+        continue;
+      }
       { LaunchScope ls(c, st, K_FC1); TRY(cuda_err(launch_gemm_tc(ln, wfc1, hid, c->hid, M, c->hid, d, EPI_BIAS_GELU, c->w32 + b.fc1b, nullptr, err, st))); }
-      { LaunchScope ls(c, st, K_FC2); TRY(cuda_err(launch_gemm_tc(hid, wfc2, tok, d, M, d, c->hid, EPI_BIAS_RESID, c->w32 + b.fc2b, tok, err, st))); }
+      if (fuse_ln) {
+        const bool last = l + 1 == c->L;
+        const float* ng = c->w32 + (last ? o.lnfg : o.blk[l + 1].ln1g);
+        const float* nb = c->w32 + (last ? o.lnfb : o.blk[l + 1].ln1b);
+        LaunchScope ls(c, st, K_FC2);
+        TRY(cuda_err(launch_gemm_tc_resid_ln(hid, wfc2, tok, M, d, c->hid, c->w32 + b.fc2b, ng, nb, ln, err, st)));
+        ln_ready = true;
+      } else {
+        LaunchScope ls(c, st, K_FC2);
+        TRY(cuda_err(launch_gemm_tc(hid, wfc2, tok, d, M, d, c->hid, EPI_BIAS_RESID, c->w32 + b.fc2b, tok, err, st)));
+        ln_ready = false;
+      }
     } else {
       float* ln = reinterpret_cast<float*>(ws + p.ln);
       float* qkv = reinterpret_cast<float*>(ws + p.qkv);
@@ -207,9 +253,21 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     bf16* ln = reinterpret_cast<bf16*>(ws + p.ln);
     bf16* f1 = reinterpret_cast<bf16*>(ws + p.f1);
     bf16* f2 = reinterpret_cast<bf16*>(ws + p.f2);
-    { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
-    { LaunchScope ls(c, st, K_DEC1); TRY(cuda_err(launch_upconv<bf16>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st))); }
-    { LaunchScope ls(c, st, K_DEC2); TRY(cuda_err(launch_upconv<bf16>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st))); }
+    if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
+    if (c->dec1_wp && p.Wt >= 16 && p.Ht >= 8) {  // TMA box is 16 x 8 input pixels
+      LaunchScope ls(c, st, K_DEC1);
+      TRY(cuda_err(launch_upconv_tc(ln, p.B, p.Ht, p.Wt, d, c->dec1_wp, c->w32 + o.d1b, f1, c->c1, c->dev_err, st)));
+    } else {
+      LaunchScope ls(c, st, K_DEC1);
+      TRY(cuda_err(launch_upconv<bf16>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st)));
+    }
+    if (c->dec2_wp) {
+      LaunchScope ls(c, st, K_DEC2);
+      TRY(cuda_err(launch_upconv_tc(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wp, c->w32 + o.d2b, f2, c->c2, c->dev_err, st)));
+    } else {
+      LaunchScope ls(c, st, K_DEC2);
+      TRY(cuda_err(launch_upconv<bf16>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st)));
+    }
     { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<bf16>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
   } else {
     float* ln = reinterpret_cast<float*>(ws + p.ln);
@@ -260,6 +318,8 @@ void inpaint_destroy(inpaint_ctx* c) {
   cudaFree(c->dec1_wt);
   cudaFree(c->dec2_wt);
   cudaFree(c->lin_bf16);
+  cudaFree(c->dec1_wp);
+  cudaFree(c->dec2_wp);
   cudaFree(c->dev_err);
   cudaFree(c->arena);
   cudaFree(c->stage);
@@ -295,7 +355,8 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
   const size_t d = c->d, h = c->hid;
   c->lin_block_elems = 4 * d * d + 2 * h * d;
   c->weight_bytes = c->nparams * 4 + 64 * d * 4 + 9 * d * c->c1 * 4 + 9 * (size_t)c->c1 * c->c2 * 4 +
-                    (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 : 0) + 256;
+                    (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 + (size_t)32 * (c->c1 * d + c->c2 * c->c1) : 0) +
+                    256;
   if (cfg->hbm_budget_bytes && c->weight_bytes > cfg->hbm_budget_bytes) {
     delete c;
     return INPAINT_E_NOMEM;
@@ -305,7 +366,11 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
             cudaMalloc(&c->dec1_wt, 9 * d * c->c1 * 4) == cudaSuccess &&
             cudaMalloc(&c->dec2_wt, 9 * (size_t)c->c1 * c->c2 * 4) == cudaSuccess &&
             cudaMalloc(&c->dev_err, 256) == cudaSuccess &&
-            (!c->use_bf16 || cudaMalloc(&c->lin_bf16, (size_t)c->L * c->lin_block_elems * 2) == cudaSuccess);
+            (!c->use_bf16 || cudaMalloc(&c->lin_bf16, (size_t)c->L * c->lin_block_elems * 2) == cudaSuccess) &&
+            (!c->use_bf16 || !upconv_tc_supported(c->d, c->c1) ||
+             cudaMalloc(&c->dec1_wp, (size_t)16 * c->c1 * c->d * 2) == cudaSuccess) &&
+            (!c->use_bf16 || !upconv_tc_supported(c->c1, c->c2) ||
+             cudaMalloc(&c->dec2_wp, (size_t)16 * c->c2 * c->c1 * 2) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
     inpaint_destroy(c);

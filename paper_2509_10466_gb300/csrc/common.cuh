@@ -26,7 +26,8 @@ enum Epi {
   EPI_BIAS = 0,        // C = acc + bias                     (output type T)
   EPI_BIAS_GELU = 1,   // C = gelu(acc + bias)               (output type T)
   EPI_BIAS_RESID = 2,  // C(f32) = resid(f32) + acc + bias   (C may alias resid)
-  EPI_NONE = 3         // C(f32) = acc
+  EPI_NONE = 3,        // C(f32) = acc
+  EPI_RESID_LN = 4     // C(f32) = resid + acc + bias, and LayerNorm(C row) -> bf16 (N == tile width)
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -46,8 +47,10 @@ template <> __device__ __forceinline__ bf16 from_f32<bf16>(float v) { return __f
 
 // Patch embedding + token-mask init.  x [B,3,H,W] f32, hole [B,H,W] u8 -> tok f32
 // [B*Ht*Wt, d] (rows in raster token order), v0 u8 [B*Ht*Wt].
+// With ln_out set, also writes LayerNorm(tok; ln_g, ln_b) as bf16 (block 0's LN1).
 cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt,
-                         const float* we, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st);
+                         const float* we, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st,
+                         const float* ln_g = nullptr, const float* ln_b = nullptr, bf16* ln_out = nullptr);
 
 // LayerNorm over the last dim (eps 1e-5, biased variance, FP32 statistics).
 template <typename OutT>
@@ -64,15 +67,42 @@ cudaError_t launch_gemm_f32(const float* A, int lda, const float* Bm, int ldb, f
 cudaError_t launch_gemm_tc(const bf16* A, const bf16* Bt, void* C, int ldc, int M, int N, int K,
                            int epi, const float* bias, const float* resid, int* err, cudaStream_t st);
 
+// Residual epilogue that also writes LayerNorm(x) (bf16) of each finished row: X is
+// updated in place (X = X + A.Bt^T + bias) and ln_out = LN(X; ln_g, ln_b).  N must be
+// 64, 128 or 256 (one tile spans the row).
+bool gemm_tc_ln_supported(int N);
+cudaError_t launch_gemm_tc_resid_ln(const bf16* A, const bf16* Bt, float* X, int M, int N, int K, const float* bias,
+                                    const float* ln_g, const float* ln_b, bf16* ln_out, int* err, cudaStream_t st);
+
+// Fused MLP on tcgen05: X += gelu(Y W1 + b1) W2 + b2 and ln_out = LN(X) without writing
+// the hidden activations; W1t [hid][d] and W2t [d][hid] bf16 (K-major).  Y may alias
+// ln_out.  Supported for d in {128, 256} and hid a multiple of 128.
+bool mlp_tc_supported(int d, int hid);
+cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const float* b1, const float* b2, float* X,
+                          const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,
+                          cudaStream_t st);
+
 // Mask-aware window attention of all frames; qkv [B*Nt, 3d] (T), v_in/v_out u8 [B*Nt].
 template <typename T>
 cudaError_t launch_attention(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
                              int Wt, int d, int heads, int offset, cudaStream_t st);
 
+// Tensor-core form for BF16 activations (mma.sync bf16, FP32 softmax statistics).
+cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
+                                int Wt, int d, int heads, int offset, cudaStream_t st);
+
 // Decoder stage: out = gelu(conv3x3(upsample2(in)) + bias), NHWC.  wt: [9][Cin][Cout] f32.
 template <typename T>
 cudaError_t launch_upconv(const T* in, int B, int Hi, int Wi, int Cin, const float* wt,
                           const float* bias, T* out, int Cout, cudaStream_t st);
+
+// Decoder stage on tcgen05 (sub-pixel implicit GEMM); wp = merged weights from
+// launch_subpixel_weights ([4][Cout][4*Cin] bf16).  Supported when Cin % 64 == 0 and
+// Cout is 32, 64, 96 or 128.
+bool upconv_tc_supported(int Cin, int Cout);
+cudaError_t launch_subpixel_weights(const float* w, int Cout, int Cin, bf16* wp, cudaStream_t st);
+cudaError_t launch_upconv_tc(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* wp, const float* bias,
+                             bf16* out, int Cout, int* err, cudaStream_t st);
 
 // Generic FP32 3x3 conv (NHWC), optional x2 upsampling of the input, optional bias
 // (NULL = none), act 0 = identity / 1 = GELU, optional pre-activation output.

@@ -48,6 +48,8 @@ struct inpaint_ctx {
   float* dec2_wt = nullptr;    // [9][c1][c2]
   inpaint::bf16* lin_bf16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
   size_t lin_block_elems = 0;
+  inpaint::bf16* dec1_wp = nullptr;  // BF16 form: merged sub-pixel weights [4][c1][4d]
+  inpaint::bf16* dec2_wp = nullptr;  // [4][c2][4c1]
   size_t weight_bytes = 0;
   int* dev_err = nullptr;
   uint8_t* arena = nullptr;

@@ -145,6 +145,173 @@ __global__ void __launch_bounds__(256) head_composite_kernel(const T* __restrict
   }
 }
 
+// Tiled form for bf16 activations: a CTA computes 16 x 32 output pixels of one frame
+// from an 18 x 34 x C halo tile staged in shared memory with 16-byte loads (chunk
+// index XOR-swizzled by pixel so that neighbouring threads hit different banks).
+// Requires C % 8 == 0.
+__global__ void __launch_bounds__(256) head_tile_kernel(const bf16* __restrict__ in, int Hp, int Wp, int C,
+                                                        const float* __restrict__ wh, const float* __restrict__ bh,
+                                                        const float* __restrict__ x, const uint8_t* __restrict__ hole,
+                                                        int H, int W, float* __restrict__ out,
+                                                        float* __restrict__ pred) {
+  extern __shared__ __align__(16) uint8_t hsm[];
+  constexpr int TY = 16, TX = 32, HY = TY + 2, HX = TX + 2;
+  const int nch = C >> 3;
+  const int swz = (nch & (nch - 1)) == 0 ? nch - 1 : 0;
+  bf16* tile = reinterpret_cast<bf16*>(hsm);                                   // [HY*HX][C]
+  float* wsm = reinterpret_cast<float*>(hsm + (size_t)HY * HX * C * 2);        // [9][C][3]
+  const int b = blockIdx.z, y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+  for (int e = threadIdx.x; e < 27 * C; e += blockDim.x) {
+    const int o = e % 3, rest = e / 3, c = rest % C, tap = rest / C;
+    wsm[e] = wh[((size_t)o * C + c) * 9 + tap];
+  }
+  for (int e = threadIdx.x; e < HY * HX * nch; e += blockDim.x) {
+    const int k = e % nch, pix = e / nch;
+    const int hy = pix / HX, hx = pix - (pix / HX) * HX;
+    const int sy = y0 - 1 + hy, sx = x0 - 1 + hx;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (sy >= 0 && sy < Hp && sx >= 0 && sx < Wp)
+      v = *reinterpret_cast<const uint4*>(in + (((size_t)b * Hp + sy) * Wp + sx) * C + 8 * k);
+    *reinterpret_cast<uint4*>(tile + (size_t)pix * C + 8 * (k ^ (pix & swz))) = v;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty0 = threadIdx.x >> 5;
+  const size_t HW = (size_t)H * W;
+#pragma unroll 1
+  for (int rr = 0; rr < 2; ++rr) {
+    const int ty = ty0 + 8 * rr;
+    const int y = y0 + ty, xx = x0 + tx;
+    if (y >= H || xx >= W) continue;
+    float p0 = bh[0], p1 = bh[1], p2 = bh[2];
+    for (int tap = 0; tap < 9; ++tap) {
+      const int pix = (ty + tap / 3) * HX + tx + tap % 3;
+      const bf16* src = tile + (size_t)pix * C;
+      const float* wr = wsm + tap * C * 3;
+      for (int k = 0; k < nch; ++k) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(src + 8 * (k ^ (pix & swz)));
+        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 f = __bfloat1622float2(h2[q]);
+          const float* w0 = wr + 3 * (8 * k + 2 * q);
+          p0 = fmaf(w0[0], f.x, p0); p1 = fmaf(w0[1], f.x, p1); p2 = fmaf(w0[2], f.x, p2);
+          p0 = fmaf(w0[3], f.y, p0); p1 = fmaf(w0[4], f.y, p1); p2 = fmaf(w0[5], f.y, p2);
+        }
+      }
+    }
+    const size_t q = (size_t)y * W + xx;
+    const size_t o = (size_t)b * 3 * HW + q;
+    const bool h = hole[(size_t)b * HW + q] != 0;
+    out[o] = h ? p0 : x[o];
+    out[o + HW] = h ? p1 : x[o + HW];
+    out[o + 2 * HW] = h ? p2 : x[o + 2 * HW];
+    if (pred) {
+      pred[o] = p0;
+      pred[o + HW] = p1;
+      pred[o + 2 * HW] = p2;
+    }
+  }
+}
+
+// Tensor-core form of the head for bf16 activations with C % 16 == 0 (C <= 64):
+// out(16 x 32 pixel tile) = conv3x3 as an implicit GEMM with M = 16 pixels of a row,
+// K = 9 taps x C channels, N = 8 (3 used) on mma.sync m16n8k16.  The 18 x 34 x C halo
+// tile is staged in shared memory with 16-byte chunks XOR-swizzled by pixel; A fragments
+// come from ldmatrix, the weights (bf16) stay in registers.  Each warp owns two output
+// rows (4 m-tiles).  Bias, composite and crop as in the SIMT form.
+__device__ __forceinline__ void ldsm_x4_h(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void mma_16816_h(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ in, int Hp, int Wp,
+                                                       const float* __restrict__ wh, const float* __restrict__ bh,
+                                                       const float* __restrict__ x, const uint8_t* __restrict__ hole,
+                                                       int H, int W, float* __restrict__ out,
+                                                       float* __restrict__ pred) {
+  constexpr int TY = 16, TX = 32, HY = TY + 2, HX = TX + 2, NCH = C / 8, KC = C / 16;
+  extern __shared__ __align__(16) uint8_t hsm[];
+  bf16* tile = reinterpret_cast<bf16*>(hsm);  // [HY*HX][C], chunk k of pixel p at 8*(k ^ (p & (NCH-1)))
+  const int b = blockIdx.z, y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+  for (int e = threadIdx.x; e < HY * HX * NCH; e += blockDim.x) {
+    const int k = e % NCH, pix = e / NCH;
+    const int hy = pix / HX, hx = pix - (pix / HX) * HX;
+    const int sy = y0 - 1 + hy, sx = x0 - 1 + hx;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (sy >= 0 && sy < Hp && sx >= 0 && sx < Wp)
+      v = *reinterpret_cast<const uint4*>(in + (((size_t)b * Hp + sy) * Wp + sx) * C + 8 * k);
+    *reinterpret_cast<uint4*>(tile + (size_t)pix * C + 8 * (k ^ (pix & (NCH - 1)))) = v;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+  // B fragments: k-step (tap, kc) -> rows k = channels kc*16 .. +15 of that tap, col n = output channel
+  uint32_t bw[9][KC][2];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+    for (int kc = 0; kc < KC; ++kc)
+#pragma unroll
+      for (int hlf = 0; hlf < 2; ++hlf) {
+        const int c0 = kc * 16 + hlf * 8 + 2 * tq;
+        float w0 = 0.f, w1 = 0.f;
+        if (g < 3) {
+          w0 = wh[((size_t)g * C + c0) * 9 + tap];
+          w1 = wh[((size_t)g * C + c0 + 1) * 9 + tap];
+        }
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(w0, w1);
+        bw[tap][kc][hlf] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+  const float bias0 = bh[0], bias1 = bh[1], bias2 = bh[2];
+  __syncthreads();
+  const size_t HW = (size_t)H * W;
+#pragma unroll 1
+  for (int mt = 0; mt < 4; ++mt) {
+    const int ty = 2 * warp + (mt >> 1), xs = (mt & 1) * 16;  // output row / first column of this m-tile
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int pix = (ty + tap / 3) * HX + xs + tap % 3 + (lane & 15);
+#pragma unroll
+      for (int kc = 0; kc < KC; ++kc) {
+        const int chunk = 2 * kc + (lane >> 4);
+        uint32_t a[4];
+        ldsm_x4_h(a, tile + (size_t)pix * C + 8 * (chunk ^ (pix & (NCH - 1))));
+        mma_16816_h(acc, a, bw[tap][kc][0], bw[tap][kc][1]);
+      }
+    }
+    if (tq > 1) continue;
+    const int y = y0 + ty;
+    if (y >= H) continue;
+#pragma unroll
+    for (int hrow = 0; hrow < 2; ++hrow) {
+      const int xx = x0 + xs + g + 8 * hrow;
+      if (xx >= W) continue;
+      const size_t q = (size_t)y * W + xx;
+      const size_t o = (size_t)b * 3 * HW + q;
+      const bool h = hole[(size_t)b * HW + q] != 0;
+      if (tq == 0) {
+        const float p0 = acc[2 * hrow] + bias0, p1 = acc[2 * hrow + 1] + bias1;
+        out[o] = h ? p0 : x[o];
+        out[o + HW] = h ? p1 : x[o + HW];
+        if (pred) { pred[o] = p0; pred[o + HW] = p1; }
+      } else {
+        const float p2 = acc[2 * hrow] + bias2;
+        out[o + 2 * HW] = h ? p2 : x[o + 2 * HW];
+        if (pred) pred[o + 2 * HW] = p2;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -175,6 +342,34 @@ template <typename T>
 cudaError_t launch_head_composite(const T* in, int B, int Hp, int Wp, int C, const float* wh, const float* bh,
                                   const float* x, const uint8_t* hole, int H, int W, float* out, float* pred,
                                   cudaStream_t st) {
+  if (sizeof(T) == 2 && (C == 16 || C == 32 || C == 64)) {
+    const size_t smem = (size_t)18 * 34 * C * 2;
+    static size_t attr = 0;
+    if (C == 64 && smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(head_mma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
+    dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
+    const bf16* inb = reinterpret_cast<const bf16*>(in);
+    if (C == 16) head_mma_kernel<16><<<grid, 256, smem, st>>>(inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
+    else if (C == 32) head_mma_kernel<32><<<grid, 256, smem, st>>>(inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
+    else head_mma_kernel<64><<<grid, 256, smem, st>>>(inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
+    return cudaGetLastError();
+  }
+  if (sizeof(T) == 2 && C % 8 == 0) {
+    const size_t smem = (size_t)18 * 34 * C * 2 + (size_t)27 * C * 4;
+    static size_t attr = 0;
+    if (smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(head_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
+    dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
+    head_tile_kernel<<<grid, 256, smem, st>>>(reinterpret_cast<const bf16*>(in), Hp, Wp, C, wh, bh, x, hole, H, W,
+                                             out, pred);
+    return cudaGetLastError();
+  }
   dim3 grid(cdiv(W, 16), cdiv(H, 16), B);
   head_composite_kernel<T><<<grid, 256, 27 * C * sizeof(float), st>>>(in, Hp, Wp, C, wh, bh, x, hole, H, W, out,
                                                                       pred);

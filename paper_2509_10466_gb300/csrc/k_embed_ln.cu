@@ -11,14 +11,21 @@ namespace inpaint {
 
 namespace {
 
-constexpr int EMB_TOK = 16;  // tokens per CTA
+constexpr int EMB_TOK = 32;  // tokens per CTA: warp w owns tokens w, w+8, w+16, w+24
 
-// we_t: embedding weights transposed to [64][d] (k = c*16 + i*4 + j) for coalesced reads.
+__device__ __forceinline__ float warp_sum(float v);
+
+// we_t: embedding weights transposed to [64][d] (k = c*16 + i*4 + j), read as float4 from
+// L1.  Lane l owns channels 8l .. 8l+7 (looping in steps of 256 channels), so a token's
+// row is spread over one warp and its LayerNorm is a warp reduction.  With ln_out set,
+// also writes LayerNorm(tok) (FP32 statistics) as bf16.
 __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole,
                                                     int H, int W, int Ht, int Wt,
                                                     const float* __restrict__ we_t, const float* __restrict__ be,
-                                                    int d, float* __restrict__ tok, uint8_t* __restrict__ v0) {
-  __shared__ float patch[EMB_TOK][64];
+                                                    int d, float* __restrict__ tok, uint8_t* __restrict__ v0,
+                                                    const float* __restrict__ ln_g, const float* __restrict__ ln_b,
+                                                    bf16* __restrict__ ln_out) {
+  __shared__ float P[64][EMB_TOK + 1];
   __shared__ int known_any[EMB_TOK];
   const int b = blockIdx.y;
   const int t0 = blockIdx.x * EMB_TOK;
@@ -34,32 +41,72 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
       const int ty = t / Wt, tx = t - (t / Wt) * Wt;
       const int y = ty * 4 + (pix >> 2), xx = tx * 4 + (pix & 3);
       if (y < H && xx < W) {
-        const size_t p = (size_t)y * W + xx;
-        if (hole[(size_t)b * HW + p] == 0) {   // known pixel: keep it; hole pixels enter as 0
-          const float* xb = x + (size_t)b * 3 * HW + p;
+        const size_t q = (size_t)y * W + xx;
+        if (hole[(size_t)b * HW + q] == 0) {   // known pixel: keep it; hole pixels enter as 0
+          const float* xb = x + (size_t)b * 3 * HW + q;
           r = xb[0]; g = xb[HW]; bl = xb[2 * HW];
           m = 1.f;
         }
       }
     }
-    patch[tl][pix] = r;
-    patch[tl][16 + pix] = g;
-    patch[tl][32 + pix] = bl;
-    patch[tl][48 + pix] = m;
+    P[pix][tl] = r;
+    P[16 + pix][tl] = g;
+    P[32 + pix][tl] = bl;
+    P[48 + pix][tl] = m;
     if (m != 0.f) known_any[tl] = 1;  // every writer stores the same value
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < EMB_TOK * d; e += blockDim.x) {
-    const int tl = e / d, c = e - (e / d) * d;
-    const int t = t0 + tl;
-    if (t >= Nt) continue;
-    float acc = be[c];
-#pragma unroll 16
-    for (int k = 0; k < 64; ++k) acc = fmaf(we_t[k * d + c], patch[tl][k], acc);
-    tok[((size_t)b * Nt + t) * d + c] = acc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c0 = 8 * lane; c0 < d; c0 += 256) {
+    float acc[4][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float bj = be[c0 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i][j] = bj;
+    }
+#pragma unroll 8
+    for (int k = 0; k < 64; ++k) {
+      const float4 wa = __ldg(reinterpret_cast<const float4*>(we_t + (size_t)k * d + c0));
+      const float4 wb = __ldg(reinterpret_cast<const float4*>(we_t + (size_t)k * d + c0 + 4));
+      const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float pv = P[k][warp + 8 * i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(wv[j], pv, acc[i][j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = t0 + warp + 8 * i;
+      if (t >= Nt) continue;
+      float4* dst = reinterpret_cast<float4*>(tok + ((size_t)b * Nt + t) * d + c0);
+      dst[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      dst[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
   }
   if (threadIdx.x < EMB_TOK && t0 + (int)threadIdx.x < Nt)
     v0[(size_t)b * Nt + t0 + threadIdx.x] = (uint8_t)known_any[threadIdx.x];
+  if (!ln_out) return;
+  // LayerNorm of the 4 tokens of this warp (rows just written by this warp)
+  __syncwarp();
+  for (int i = 0; i < 4; ++i) {
+    const int t = t0 + warp + 8 * i;
+    if (t >= Nt) continue;  // uniform across the warp
+    const float* row = tok + ((size_t)b * Nt + t) * d;
+    float s = 0.f;
+    for (int c = lane; c < d; c += 32) s += row[c];
+    const float mean = warp_sum(s) / (float)d;
+    float q = 0.f;
+    for (int c = lane; c < d; c += 32) {
+      const float v = row[c] - mean;
+      q = fmaf(v, v, q);
+    }
+    const float rstd = rsqrtf(warp_sum(q) / (float)d + 1e-5f);
+    bf16* orow = ln_out + ((size_t)b * Nt + t) * d;
+    for (int c = lane; c < d; c += 32) orow[c] = __float2bfloat16_rn((row[c] - mean) * rstd * ln_g[c] + ln_b[c]);
+  }
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -193,9 +240,11 @@ __global__ void l1_grad_kernel(const float* __restrict__ out, const float* __res
 }  // namespace
 
 cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt,
-                         const float* we_t, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st) {
+                         const float* we_t, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st,
+                         const float* ln_g, const float* ln_b, bf16* ln_out) {
+  if (d % 8) return cudaErrorInvalidValue;
   dim3 grid(cdiv(Ht * Wt, EMB_TOK), B);
-  embed_kernel<<<grid, 256, 0, st>>>(x, hole, H, W, Ht, Wt, we_t, be, d, tok, v0);
+  embed_kernel<<<grid, 256, 0, st>>>(x, hole, H, W, Ht, Wt, we_t, be, d, tok, v0, ln_g, ln_b, ln_out);
   return cudaGetLastError();
 }
 

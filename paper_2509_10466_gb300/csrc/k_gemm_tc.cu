@@ -5,14 +5,22 @@
 //   FP32 accumulation in tensor memory.
 //
 // Persistent, warp-specialized CTA (one per SM):
-//   warp 0      TMA producer: A and B tiles (BK = 64 -> one 128-byte swizzle row per
-//               tile row) into a STAGES-deep shared-memory ring;
-//   warp 1      TMEM owner and MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per
-//               stage, accumulating into one of two TMEM buffers;
-//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator, bias / GELU /
-//               residual, vector stores; the other accumulator buffer is filled by
-//               the next tile's MMAs meanwhile.
+//   warp 0        TMA producer: A and B tiles (BK = 64 -> one 128-byte swizzle row per
+//                 tile row) into a STAGES-deep shared-memory ring;
+//   warp 1        TMEM owner and MMA issuer: 4 x tcgen05.mma (M=128, N=BN, K=16) per
+//                 stage, accumulating into one of two TMEM buffers;
+//   warps 2..9    epilogue: two warps per TMEM lane quarter (32 rows each), splitting
+//                 the tile's columns; tcgen05.ld of the finished accumulator, bias /
+//                 GELU / residual / LayerNorm, vector stores.  The other accumulator is
+//                 filled by the next tile's MMAs meanwhile.
 // Output tiles are visited N-fastest so consecutive CTAs reuse the same A rows from L2.
+//
+// EPI_RESID_LN (N == BN, a whole row per tile) also normalizes the new residual row:
+// x = resid + acc + bias is stored (FP32) and y = LayerNorm(x) (eps 1e-5, biased
+// variance, FP32 statistics) is stored as bf16 for the next GEMM.  Each thread reduces
+// its half row chunk by chunk (exact mean and squared deviations per 32 values, merged
+// with Chan's pairwise formula), the two halves of a row are merged through shared
+// memory, and the stored x is re-read to normalize.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -24,7 +32,9 @@ namespace inpaint {
 namespace {
 
 constexpr int BM = 128, BK = 64;
-constexpr int THREADS = 192;
+constexpr int EW = 2;                       // epilogue warps per TMEM lane quarter
+constexpr int EPI_WARPS = 4 * EW;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 
 template <int BN>
 struct TcCfg {
@@ -33,71 +43,80 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
   static constexpr int TMEM_COLS = 2 * BN;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
+  static constexpr int COLS_PER_WARP = BN / EW;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/ +
+                                    EPI_WARPS * 32 * 2 * 4 /*LayerNorm partial statistics*/;
 };
 
-__device__ __forceinline__ void store_row_chunk(int epi, void* C, int ldc, int row, int col, const float* bias,
-                                                const float* resid, const float (&f)[32]) {
-  if (epi == EPI_BIAS || epi == EPI_BIAS_GELU) {
-    bf16* dst = reinterpret_cast<bf16*>(C) + (size_t)row * ldc + col;
-    uint32_t packed[16];
+struct GemmArgs {
+  void* C;
+  int ldc, M, N, K, epi;
+  const float* bias;
+  const float* resid;
+  const float* ln_g;
+  const float* ln_b;
+  bf16* ln_out;
+  int* err;
+};
+
+__device__ __forceinline__ void load32(const float* __restrict__ p, float (&v)[32]) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      float a = f[2 * i] + __ldg(bias + col + 2 * i);
-      float b = f[2 * i + 1] + __ldg(bias + col + 2 * i + 1);
-      if (epi == EPI_BIAS_GELU) { a = gelu_erf(a); b = gelu_erf(b); }
-      __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-      packed[i] = *reinterpret_cast<uint32_t*>(&h);
-    }
-    uint4* d4 = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) d4[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
-  } else {
-    float* dst = reinterpret_cast<float*>(C) + (size_t)row * ldc + col;
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    if (epi == EPI_BIAS_RESID) {
-      const float4* r4 = reinterpret_cast<const float4*>(resid + (size_t)row * ldc + col);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float4 r = r4[i];
-        float4 o;
-        o.x = r.x + (f[4 * i + 0] + __ldg(bias + col + 4 * i + 0));
-        o.y = r.y + (f[4 * i + 1] + __ldg(bias + col + 4 * i + 1));
-        o.z = r.z + (f[4 * i + 2] + __ldg(bias + col + 4 * i + 2));
-        o.w = r.w + (f[4 * i + 3] + __ldg(bias + col + 4 * i + 3));
-        d4[i] = o;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) d4[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
-    }
+  for (int i = 0; i < 8; ++i) {
+    const float4 t = __ldg(p4 + i);
+    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
   }
+}
+
+__device__ __forceinline__ void store32_bf16(bf16* dst, const float (&f)[32]) {
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(f[8 * i + 2 * j], f[8 * i + 2 * j + 1]);
+      w[j] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    d4[i] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+__device__ __forceinline__ void store32_f32(float* dst, const float (&f)[32]) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d4[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+}
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 template <int BN>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                             const __grid_constant__ CUtensorMap tmB, void* C,
-                                                             int ldc, int M, int N, int K, int epi,
-                                                             const float* __restrict__ bias, const float* resid,
-                                                             int* err) {
+                                                             const __grid_constant__ CUtensorMap tmB,
+                                                             const GemmArgs args) {
   using Cfg = TcCfg<BN>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * Cfg::STAGE_BYTES);
   uint64_t* empty = full + S;
-  uint64_t* acc_full = empty + S;   // [2] MMA -> epilogue
+  uint64_t* acc_full = empty + S;      // [2] MMA -> epilogue
   uint64_t* acc_empty = acc_full + 2;  // [2] epilogue -> MMA
   uint64_t* teardown = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* ln_stats = reinterpret_cast<float*>(smem + S * Cfg::STAGE_BYTES + 256);  // [EPI_WARPS][32][2]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_n = N / BN, tiles = ((M + BM - 1) / BM) * tiles_n, nk = K / BK;
+  const int M = args.M, N = args.N;
+  const int tiles_n = N / BN, tiles = ((M + BM - 1) / BM) * tiles_n, nk = args.K / BK;
+  int* err = args.err;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-    for (int a = 0; a < 2; ++a) { tc::mbar_init(&acc_full[a], 1); tc::mbar_init(&acc_empty[a], 4); }
+    for (int a = 0; a < 2; ++a) { tc::mbar_init(&acc_full[a], 1); tc::mbar_init(&acc_empty[a], EPI_WARPS); }
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -116,11 +135,15 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   if (warp == 0) {
     if (lane == 0) {
       uint32_t g = 0;
-      for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
         const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = g % S;
-          if (g >= (uint32_t)S && !tc::mbar_wait(&empty[s], ((g / S) & 1) ^ 1, abort_flag)) goto producer_abort;
+          if (g >= (uint32_t)S && !tc::mbar_wait(&empty[s], ((g / S) & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
+          }
           uint8_t* sa = smem + s * Cfg::STAGE_BYTES;
           tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
           tc::tma_load_2d(sa, &tmA, &full[s], kb * BK, m0);
@@ -130,11 +153,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       // let the last copies land before the CTA may exit
       for (uint32_t h = (g > (uint32_t)S ? g - S : 0); h < g; ++h)
         if (!tc::mbar_wait_timed(&full[h % S], (h / S) & 1)) break;
-      goto producer_done;
-    producer_abort:
-      if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
-      *abort_flag = 1;
-    producer_done:;
+      if (!ok) {
+        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+        *abort_flag = 1;
+      }
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -171,8 +193,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     }
     __syncwarp();
   } else {
-    // epilogue warps 2..5: TMEM sub-partition (warp % 4) holds rows 32*(warp%4) ...
-    const int quarter = warp & 3;
+    // epilogue: TMEM sub-partition (warp % 4) holds rows 32*(warp%4) .. +31; column group cg
+    const int quarter = warp & 3, cg = (warp - 2) >> 2;
+    const int epi = args.epi;
+    const int c_lo = cg * Cfg::COLS_PER_WARP;
     uint32_t i = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
       const uint32_t acc = i & 1, use = i >> 1;
@@ -185,16 +209,95 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       tc::fence_after_sync();
       const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
       const int row = m0 + quarter * 32 + lane;
+      const bool live = row < M;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
+      float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;  // LayerNorm statistics of this part of the row
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = c_lo; c0 < c_lo + Cfg::COLS_PER_WARP; c0 += 32) {
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tbase + c0, r);
         tc::tmem_ld_wait();
+        const int col = n0 + c0;
         float f[32];
+        if (epi == EPI_NONE) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
-        if (row < M) store_row_chunk(epi, C, ldc, row, n0 + c0, bias, resid, f);
+          for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
+          if (live) store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row * args.ldc + col, f);
+          continue;
+        }
+        float bv[32];
+        load32(args.bias + col, bv);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]) + bv[j];
+        if (epi == EPI_BIAS || epi == EPI_BIAS_GELU) {
+          if (epi == EPI_BIAS_GELU) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) f[j] = gelu_erf(f[j]);
+          }
+          if (live) store32_bf16(reinterpret_cast<bf16*>(args.C) + (size_t)row * args.ldc + col, f);
+        } else {  // residual (+ LayerNorm statistics)
+          if (live) {
+            float rv[32];
+            load32(args.resid + (size_t)row * args.ldc + col, rv);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
+            store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row * args.ldc + col, f);
+          }
+          if (epi == EPI_RESID_LN) {
+            float cm = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cm += f[j];
+            cm *= (1.f / 32.f);
+            float cq = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cq = fmaf(f[j] - cm, f[j] - cm, cq);
+            const float nn = run_n + 32.f;
+            const float dl = cm - run_mean;
+            run_mean += dl * (32.f / nn);
+            run_m2 += cq + dl * dl * (run_n * 32.f / nn);
+            run_n = nn;
+          }
+        }
+      }
+      if (epi == EPI_RESID_LN) {
+        // merge the EW column groups of each row (fixed order), then normalize the stored row
+        float* st = ln_stats + ((size_t)(warp - 2) * 32 + lane) * 2;
+        st[0] = run_mean;
+        st[1] = run_m2;
+        named_sync(1 + quarter, 32 * EW);
+        float mean = 0.f, m2 = 0.f, n = 0.f;
+#pragma unroll
+        for (int g2 = 0; g2 < EW; ++g2) {
+          // the warp of column group g2 in this quarter is 2 + 4*g2 + ((quarter - 2) & 3)
+          const float* o = ln_stats + ((size_t)(4 * g2 + ((quarter - 2) & 3)) * 32 + lane) * 2;
+          const float om = o[0], oq = o[1], on = (float)Cfg::COLS_PER_WARP;
+          const float nn = n + on;
+          const float dl = om - mean;
+          mean += dl * (on / nn);
+          m2 += oq + dl * dl * (n * on / nn);
+          n = nn;
+        }
+        named_sync(1 + quarter, 32 * EW);  // the statistics slots are reused by the next tile
+        const float rstd = rsqrtf(m2 / n + 1e-5f);
+        if (live) {
+#pragma unroll 1
+          for (int c0 = c_lo; c0 < c_lo + Cfg::COLS_PER_WARP; c0 += 32) {
+            const int col = n0 + c0;
+            float xv[32], gv[32], bv[32];
+            const float4* xr =
+                reinterpret_cast<const float4*>(reinterpret_cast<const float*>(args.C) + (size_t)row * args.ldc + col);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 t = xr[j];
+              xv[4 * j] = t.x; xv[4 * j + 1] = t.y; xv[4 * j + 2] = t.z; xv[4 * j + 3] = t.w;
+            }
+            load32(args.ln_g + col, gv);
+            load32(args.ln_b + col, bv);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xv[j] = (xv[j] - mean) * rstd * gv[j] + bv[j];
+            store32_bf16(args.ln_out + (size_t)row * N + col, xv);
+          }
+        }
       }
       tc::fence_before_sync();
       __syncwarp();
@@ -248,8 +351,7 @@ int num_sms() {
 }
 
 template <int BN>
-cudaError_t launch_bn(const bf16* A, const bf16* Bt, void* C, int ldc, int M, int N, int K, int epi,
-                      const float* bias, const float* resid, int* err, cudaStream_t st) {
+cudaError_t launch_bn(const bf16* A, const bf16* Bt, const GemmArgs& args, cudaStream_t st) {
   using Cfg = TcCfg<BN>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -259,23 +361,43 @@ cudaError_t launch_bn(const bf16* A, const bf16* Bt, void* C, int ldc, int M, in
     attr_set = true;
   }
   CUtensorMap ma, mb;
-  if (!make_map_2d(&ma, A, (uint64_t)K, (uint64_t)M, BK, BM)) return cudaErrorInvalidValue;
-  if (!make_map_2d(&mb, Bt, (uint64_t)K, (uint64_t)N, BK, BN)) return cudaErrorInvalidValue;
-  const int tiles = ((M + BM - 1) / BM) * (N / BN);
+  if (!make_map_2d(&ma, A, (uint64_t)args.K, (uint64_t)args.M, BK, BM)) return cudaErrorInvalidValue;
+  if (!make_map_2d(&mb, Bt, (uint64_t)args.K, (uint64_t)args.N, BK, BN)) return cudaErrorInvalidValue;
+  const int tiles = ((args.M + BM - 1) / BM) * (args.N / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  gemm_tc_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(ma, mb, C, ldc, M, N, K, epi, bias, resid, err);
+  gemm_tc_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(ma, mb, args);
   return cudaGetLastError();
+}
+
+cudaError_t launch_any(const bf16* A, const bf16* Bt, const GemmArgs& a, cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0 || a.K <= 0 || a.K % BK || a.N % 64 || a.ldc % 8) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt)) & 15) return cudaErrorInvalidValue;
+  if (a.epi != EPI_NONE && !a.bias) return cudaErrorInvalidValue;
+  if (a.epi == EPI_RESID_LN) {  // a whole row per tile
+    if (a.N == 256) return launch_bn<256>(A, Bt, a, st);
+    if (a.N == 128) return launch_bn<128>(A, Bt, a, st);
+    if (a.N == 64) return launch_bn<64>(A, Bt, a, st);
+    return cudaErrorInvalidValue;
+  }
+  if (a.N % 256 == 0) return launch_bn<256>(A, Bt, a, st);
+  if (a.N % 128 == 0) return launch_bn<128>(A, Bt, a, st);
+  return launch_bn<64>(A, Bt, a, st);
 }
 
 }  // namespace
 
+bool gemm_tc_ln_supported(int N) { return N == 64 || N == 128 || N == 256; }
+
 cudaError_t launch_gemm_tc(const bf16* A, const bf16* Bt, void* C, int ldc, int M, int N, int K, int epi,
                            const float* bias, const float* resid, int* err, cudaStream_t st) {
-  if (M <= 0 || N <= 0 || K <= 0 || K % BK || N % 64 || ldc % 8) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt)) & 15) return cudaErrorInvalidValue;
-  if (N % 256 == 0) return launch_bn<256>(A, Bt, C, ldc, M, N, K, epi, bias, resid, err, st);
-  if (N % 128 == 0) return launch_bn<128>(A, Bt, C, ldc, M, N, K, epi, bias, resid, err, st);
-  return launch_bn<64>(A, Bt, C, ldc, M, N, K, epi, bias, resid, err, st);
+  GemmArgs a{C, ldc, M, N, K, epi, bias, resid, nullptr, nullptr, nullptr, err};
+  return launch_any(A, Bt, a, st);
+}
+
+cudaError_t launch_gemm_tc_resid_ln(const bf16* A, const bf16* Bt, float* X, int M, int N, int K, const float* bias,
+                                    const float* ln_g, const float* ln_b, bf16* ln_out, int* err, cudaStream_t st) {
+  GemmArgs a{X, N, M, N, K, EPI_RESID_LN, bias, X, ln_g, ln_b, ln_out, err};
+  return launch_any(A, Bt, a, st);
 }
 
 }  // namespace inpaint

@@ -1,0 +1,466 @@
+// Fused MLP of a transformer block on tcgen05 (BF16 form):
+//   for a tile of 128 token rows and hidden chunks j of 128 columns
+//     H_j  = gelu(Y . W1[:, j] + b1[j])            (MMA1 into TMEM, epilogue to SMEM)
+//     OUT += H_j . W2[j, :]                         (MMA2 from SMEM into TMEM)
+//   x = x + OUT + b2, ln_out = LayerNorm(x) (the next block's LN1, or the final LN).
+// The hidden activations never leave the SM: this removes the write and re-read of the
+// [M, r*d] hidden tensor and keeps the MLP bound by the tensor pipe, not HBM.
+//
+// Y (LN2 output, bf16 [M, D]) is loaded once per tile by TMA and stays in SMEM; W1^T
+// ([hid][D]) k-blocks and W2^T ([D][hid]) k-blocks (as <=128-row halves, one MMA2 per
+// half of OUT's columns) stream through a 5-stage ring of 16 KB in the order the MMA
+// warp consumes them (MMA1 of chunk j+1 is issued before MMA2 of chunk j, so the tensor
+// core works while the epilogue warps turn H_j into bf16).  TMEM: OUT (D cols)
+// + two H buffers (128 cols each).  The bf16 H_j is written in the 128-byte-swizzled
+// K-major layout that the MMA descriptor expects (16-byte chunk c of row r at c ^ (r%8)).
+//
+// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2..17 epilogue (four per TMEM lane
+// quarter, splitting columns): the erf-GELU of every hidden value is the bulk of the
+// instruction work, so the epilogue gets as many warps as the register file allows.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "tc_primitives.cuh"
+
+namespace inpaint {
+
+namespace {
+
+constexpr int BM = 128, BK = 64, HC = 128;   // rows per tile, k-block, hidden chunk
+constexpr int EW = 4, EPI_WARPS = 4 * EW, THREADS = 64 + 32 * EPI_WARPS;
+constexpr int RING = 5;                      // 16 KB weight stages
+
+template <int D>
+struct MlpCfg {
+  static constexpr int A_BYTES = BM * D * 2;                  // Y tile, D/64 atoms of 16 KB
+  static constexpr int HS_BYTES = BM * HC * 2;                // one bf16 H chunk, 2 atoms
+  static constexpr int W1_BYTES = HC * BK * 2;                // one W1 k-block (HC rows)
+  static constexpr int HR = D < 128 ? D : 128;                // W2 rows per load (N of MMA2)
+  static constexpr int NHALF = D / HR;                        // W2 k-block = NHALF loads
+  static constexpr int W2_BYTES = HR * BK * 2;
+  static constexpr int STAGE_BYTES = 16384;
+  static constexpr int SMEM_BYTES = A_BYTES + 2 * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
+                                    512 /*barriers*/ + EPI_WARPS * 32 * 2 * 4 /*LN statistics*/;
+  static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 and 384
+};
+
+struct MlpArgs {
+  float* X;              // residual stream [M, D] f32, updated in place
+  bf16* ln_out;          // [M, D]
+  const float* b1;       // [hid]
+  const float* b2;       // [D]
+  const float* ln_g;
+  const float* ln_b;
+  int M, hid;
+  int* err;
+};
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void load32(const float* __restrict__ p, float (&v)[32]) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 t = __ldg(p4 + i);
+    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constant__ CUtensorMap tmY,
+                                                            const __grid_constant__ CUtensorMap tmW1,
+                                                            const __grid_constant__ CUtensorMap tmW2,
+                                                            const MlpArgs args) {
+  using Cfg = MlpCfg<D>;
+  constexpr int KA = D / BK;   // k-blocks of MMA1 (and atoms of the Y tile)
+  constexpr int KH = HC / BK;  // k-blocks of MMA2 per hidden chunk
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sH = sA + Cfg::A_BYTES;                      // 2 buffers
+  uint8_t* sR = sH + 2 * Cfg::HS_BYTES;                 // ring
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sR + RING * Cfg::STAGE_BYTES);
+  static_assert(Cfg::W1_BYTES <= Cfg::STAGE_BYTES && Cfg::W2_BYTES <= Cfg::STAGE_BYTES, "stage too small");
+  uint64_t* full = bar;                 // [RING]
+  uint64_t* empty = full + RING;        // [RING]
+  uint64_t* a_full = empty + RING;
+  uint64_t* a_empty = a_full + 1;
+  uint64_t* h_full = a_empty + 1;       // [2]
+  uint64_t* h_empty = h_full + 2;       // [2]
+  uint64_t* hs_full = h_empty + 2;      // [2]
+  uint64_t* hs_empty = hs_full + 2;     // [2]
+  uint64_t* o_full = hs_empty + 2;
+  uint64_t* o_empty = o_full + 1;
+  uint64_t* teardown = o_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* ln_stats = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [EPI_WARPS][32][2]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int M = args.M, NJ = args.hid / HC;
+  const int tiles = (M + BM - 1) / BM;
+  int* err = args.err;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RING; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    tc::mbar_init(a_full, 1);
+    tc::mbar_init(a_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&h_full[b], 1);
+      tc::mbar_init(&h_empty[b], EPI_WARPS);
+      tc::mbar_init(&hs_full[b], EPI_WARPS);
+      tc::mbar_init(&hs_empty[b], 1);
+    }
+    tc::mbar_init(o_full, 1);
+    tc::mbar_init(o_empty, EPI_WARPS);
+    tc::mbar_init(teardown, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmY);
+    tc::prefetch_tmap(&tmW1);
+    tc::prefetch_tmap(&tmW2);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;  // ring slot counter
+      bool ok = true;
+      auto push = [&](const CUtensorMap* map, int c0, int c1, uint32_t bytes) {
+        const int s = g % RING;
+        if (g >= (uint32_t)RING && !tc::mbar_wait(&empty[s], ((g / RING) & 1) ^ 1, abort_flag)) return false;
+        tc::mbar_expect_tx(&full[s], bytes);
+        tc::tma_load_2d(sR + s * Cfg::STAGE_BYTES, map, &full[s], c0, c1);
+        ++g;
+        return true;
+      };
+      int t = 0;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+        const int m0 = tile * BM;
+        if (t >= 1 && !tc::mbar_wait(a_empty, (t - 1) & 1, abort_flag)) { ok = false; break; }
+        tc::mbar_expect_tx(a_full, Cfg::A_BYTES);
+        for (int kb = 0; kb < KA; ++kb) tc::tma_load_2d(sA + kb * (BM * BK * 2), &tmY, a_full, kb * BK, m0);
+        for (int j = 0; j <= NJ && ok; ++j) {
+          if (j < NJ)
+            for (int kb = 0; kb < KA && ok; ++kb) ok = push(&tmW1, kb * BK, j * HC, Cfg::W1_BYTES);
+          if (j >= 1)
+            for (int kb = 0; kb < KH && ok; ++kb)
+              for (int hf = 0; hf < Cfg::NHALF && ok; ++hf)
+                ok = push(&tmW2, (j - 1) * HC + kb * BK, hf * Cfg::HR, Cfg::W2_BYTES);
+        }
+      }
+      for (uint32_t h = (g > (uint32_t)RING ? g - RING : 0); h < g; ++h)
+        if (!tc::mbar_wait_timed(&full[h % RING], (h / RING) & 1)) break;
+      if (!ok) {
+        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+        *abort_flag = 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id1 = tc::idesc_bf16_f32(BM, HC);
+      constexpr uint32_t id2 = tc::idesc_bf16_f32(BM, Cfg::HR);
+      uint32_t g = 0, q = 0;  // ring slot counter, hidden-chunk counter (across tiles)
+      bool ok = true;
+      auto pop = [&](int& s) {
+        s = g % RING;
+        if (!tc::mbar_wait(&full[s], (g / RING) & 1, abort_flag)) return false;
+        tc::fence_after_sync();
+        ++g;
+        return true;
+      };
+      auto mma1 = [&](uint32_t qq) {  // H[qq & 1] = Y . W1_chunk^T
+        const uint32_t hb = qq & 1, use = qq >> 1;
+        if (use >= 1 && !tc::mbar_wait(&h_empty[hb], (use & 1) ^ 1, abort_flag)) return false;
+        tc::fence_after_sync();
+        const uint32_t dt = tmem_base + Cfg::H_COL0 + hb * HC;
+        for (int kb = 0; kb < KA; ++kb) {
+          int s;
+          if (!pop(s)) return false;
+          const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sA + kb * (BM * BK * 2)));
+          const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16(dt, ad + 2 * kk, bd + 2 * kk, id1, (kb | kk) != 0);
+          tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(&h_full[hb]);
+        return true;
+      };
+      auto mma2 = [&](uint32_t qq, bool first, bool last, int t) {  // OUT (+)= Hs[qq & 1] . W2_chunk^T
+        const uint32_t hb = qq & 1, use = qq >> 1;
+        if (first && t >= 1 && !tc::mbar_wait(o_empty, (t - 1) & 1, abort_flag)) return false;
+        if (!tc::mbar_wait(&hs_full[hb], use & 1, abort_flag)) return false;
+        tc::fence_after_sync();
+        for (int kb = 0; kb < KH; ++kb) {
+          const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sH + hb * Cfg::HS_BYTES + kb * (BM * BK * 2)));
+          for (int hf = 0; hf < Cfg::NHALF; ++hf) {  // OUT columns hf*HR .. +HR
+            int s;
+            if (!pop(s)) return false;
+            const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              tc::mma_f16(tmem_base + hf * Cfg::HR, ad + 2 * kk, bd + 2 * kk, id2, (!first || kb || kk) ? 1u : 0u);
+            tc::mma_commit(&empty[s]);
+          }
+        }
+        tc::mma_commit(&hs_empty[hb]);
+        if (last) tc::mma_commit(o_full);
+        return true;
+      };
+      int t = 0;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+        if (!tc::mbar_wait(a_full, t & 1, abort_flag)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint32_t q0 = q;
+        for (int j = 0; j <= NJ && ok; ++j) {
+          if (j < NJ) {
+            ok = mma1(q0 + j);
+            if (ok && j == NJ - 1) tc::mma_commit(a_empty);  // Y tile no longer read after the last MMA1
+          }
+          if (ok && j >= 1) ok = mma2(q0 + j - 1, j == 1, j == NJ, t);
+        }
+        q = q0 + NJ;
+      }
+      if (!ok) {
+        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+        *abort_flag = 1;
+      }
+      tc::mma_commit(teardown);
+      tc::mbar_wait_timed(teardown, 0);
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3, cg = (warp - 2) >> 2;
+    const int r = quarter * 32 + lane;  // row within the tile (= TMEM lane)
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+    uint32_t q = 0;
+    bool ok = true;
+    int t = 0;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+      const int row = tile * BM + r;
+      const bool live = row < M;
+      // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 swizzled SMEM operand
+      for (int j = 0; j < NJ; ++j, ++q) {
+        const uint32_t hb = q & 1, use = q >> 1;
+        if (!tc::mbar_wait(&h_full[hb], use & 1, abort_flag)) { ok = false; break; }
+        if (use >= 1 && !tc::mbar_wait(&hs_empty[hb], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
+        __syncwarp();
+        tc::fence_after_sync();
+        uint8_t* hs = sH + hb * Cfg::HS_BYTES;
+#pragma unroll 1
+        for (int c0 = cg * (HC / EW); c0 < (cg + 1) * (HC / EW); c0 += 32) {
+          uint32_t v[32];
+          tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + hb * HC + c0, v);
+          tc::tmem_ld_wait();
+          float bv[32];
+          load32(args.b1 + j * HC + c0, bv);
+          uint32_t pk[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const float a0 = gelu_erf(__uint_as_float(v[2 * k]) + bv[2 * k]);
+            const float a1 = gelu_erf(__uint_as_float(v[2 * k + 1]) + bv[2 * k + 1]);
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+            pk[k] = *reinterpret_cast<uint32_t*>(&h2);
+          }
+          // columns c0 .. c0+31 of row r: atom c0/64, 16-byte chunks (c0%64)/8 .. +3, swizzled by r%8
+          uint8_t* rowp = hs + (c0 >> 6) * (BM * BK * 2) + r * 128;
+          const int ch0 = (c0 & 63) >> 3;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            *reinterpret_cast<uint4*>(rowp + (((ch0 + k) ^ (r & 7)) << 4)) =
+                make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+        }
+        tc::fence_before_sync();
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tc::mbar_arrive(&h_empty[hb]);
+          tc::mbar_arrive(&hs_full[hb]);
+        }
+      }
+      if (!ok) break;
+      // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16
+      if (!tc::mbar_wait(o_full, t & 1, abort_flag)) { ok = false; break; }
+      __syncwarp();
+      tc::fence_after_sync();
+      float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
+      const int c_lo = cg * (D / EW);
+#pragma unroll 1
+      for (int c0 = c_lo; c0 < c_lo + D / EW; c0 += 32) {
+        uint32_t v[32];
+        tc::tmem_ld_32x32b_x32(lane_base + c0, v);
+        tc::tmem_ld_wait();
+        float f[32], bv[32];
+        load32(args.b2 + c0, bv);
+        if (live) {
+          float* xr = args.X + (size_t)row * D + c0;
+          float4* x4 = reinterpret_cast<float4*>(xr);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float4 o = x4[k];
+            f[4 * k] = o.x + (__uint_as_float(v[4 * k]) + bv[4 * k]);
+            f[4 * k + 1] = o.y + (__uint_as_float(v[4 * k + 1]) + bv[4 * k + 1]);
+            f[4 * k + 2] = o.z + (__uint_as_float(v[4 * k + 2]) + bv[4 * k + 2]);
+            f[4 * k + 3] = o.w + (__uint_as_float(v[4 * k + 3]) + bv[4 * k + 3]);
+            x4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) f[k] = 0.f;
+        }
+        float cm = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) cm += f[k];
+        cm *= (1.f / 32.f);
+        float cq = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) cq = fmaf(f[k] - cm, f[k] - cm, cq);
+        const float nn = run_n + 32.f;
+        const float dl = cm - run_mean;
+        run_mean += dl * (32.f / nn);
+        run_m2 += cq + dl * dl * (run_n * 32.f / nn);
+        run_n = nn;
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(o_empty);  // OUT drained: the next tile's MMA2 may start
+      float* st = ln_stats + ((size_t)(warp - 2) * 32 + lane) * 2;
+      st[0] = run_mean;
+      st[1] = run_m2;
+      named_sync(1 + quarter, 32 * EW);
+      float mean = 0.f, m2 = 0.f, n = 0.f;
+#pragma unroll
+      for (int g2 = 0; g2 < EW; ++g2) {
+        const float* o = ln_stats + ((size_t)(4 * g2 + ((quarter - 2) & 3)) * 32 + lane) * 2;
+        const float om = o[0], oq = o[1], on = (float)(D / EW);
+        const float nn = n + on;
+        const float dl = om - mean;
+        mean += dl * (on / nn);
+        m2 += oq + dl * dl * (n * on / nn);
+        n = nn;
+      }
+      named_sync(1 + quarter, 32 * EW);
+      const float rstd = rsqrtf(m2 / n + 1e-5f);
+      if (live) {
+#pragma unroll 1
+        for (int c0 = c_lo; c0 < c_lo + D / EW; c0 += 32) {
+          float xv[32], gv[32], bv[32];
+          const float4* xr = reinterpret_cast<const float4*>(args.X + (size_t)row * D + c0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float4 o = xr[k];
+            xv[4 * k] = o.x; xv[4 * k + 1] = o.y; xv[4 * k + 2] = o.z; xv[4 * k + 3] = o.w;
+          }
+          load32(args.ln_g + c0, gv);
+          load32(args.ln_b + c0, bv);
+          uint4* dst = reinterpret_cast<uint4*>(args.ln_out + (size_t)row * D + c0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int c = 8 * k + 2 * e;
+              __nv_bfloat162 h2 = __floats2bfloat162_rn((xv[c] - mean) * rstd * gv[c] + bv[c],
+                                                        (xv[c + 1] - mean) * rstd * gv[c + 1] + bv[c + 1]);
+              w[e] = *reinterpret_cast<uint32_t*>(&h2);
+            }
+            dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+      }
+    }
+    if (!ok) {
+      if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+      *abort_flag = 1;
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem_base, 512);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_inner, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int D>
+cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
+  using Cfg = MlpCfg<D>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap my, m1, m2;
+  if (!map2d(&my, Y, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
+  if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC)) return cudaErrorInvalidValue;
+  if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, Cfg::HR)) return cudaErrorInvalidValue;
+  const int tiles = (a.M + BM - 1) / BM;
+  const int grid = tiles < num_sms() ? tiles : num_sms();
+  mlp_tc_kernel<D><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(my, m1, m2, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool mlp_tc_supported(int d, int hid) { return (d == 128 || d == 256) && hid % HC == 0 && hid >= HC; }
+
+cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const float* b1, const float* b2, float* X,
+                          const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,
+                          cudaStream_t st) {
+  if (!mlp_tc_supported(d, hid) || M <= 0) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(W1t) | reinterpret_cast<uintptr_t>(W2t)) & 15)
+    return cudaErrorInvalidValue;
+  MlpArgs a{X, ln_out, b1, b2, ln_g, ln_b, M, hid, err};
+  if (d == 256) return launch_d<256>(Y, W1t, W2t, a, st);
+  return launch_d<128>(Y, W1t, W2t, a, st);
+}
+
+}  // namespace inpaint

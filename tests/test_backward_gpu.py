@@ -63,7 +63,7 @@ def test_backward_fd_instance_64():
     out = O.forward(torch.from_numpy(x), torch.from_numpy(hole), torch.from_numpy(weights.astype(np.float64)),
                     w.model)["out"]
     _, gout = O.l1_hole_loss(out, torch.from_numpy(tgt), torch.from_numpy(hole))
-    gout = gout.numpy().astype(np.float32)
+    gout = np.ascontiguousarray(gout.numpy(), dtype=np.float32)
     print(compare(w.model, gpu_grad(w.model, weights, x, hole, gout), oracle_grad(w.model, weights, x, hole, gout)))
 
 
@@ -88,7 +88,8 @@ def test_backward_training_workload_256():
         out = O.forward(torch.from_numpy(x), torch.from_numpy(hole), torch.from_numpy(weights.astype(np.float64)),
                         w.model)["out"]
     _, gout = O.l1_hole_loss(out, torch.from_numpy(tgt), torch.from_numpy(hole))
-    gout = gout.numpy().astype(np.float32)
+    # the oracle's gradient tensor can have permuted strides: the C ABI needs dense NCHW
+    gout = np.ascontiguousarray(gout.numpy(), dtype=np.float32)
     print(compare(w.model, gpu_grad(w.model, weights, x, hole, gout), oracle_grad(w.model, weights, x, hole, gout)))
 
 

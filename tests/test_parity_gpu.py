@@ -74,6 +74,15 @@ def test_bf16_small_shapes(H, W, B):
     check_parity(cfg, weights, x, hole, TOL_BF16)
 
 
+@pytest.mark.parametrize("H,W,B", [(64, 96, 2), (224, 100, 1), (96, 352, 1)])
+def test_bf16_d256_decoder_on_tensor_cores(H, W, B):
+    """d256 puts both decoder stages on tcgen05 (c1 = 64, c2 = 32); ragged tile edges."""
+    cfg = ModelConfig(dim=256, heads=8, window=8, blocks=2, mlp_ratio=4, precision=BF16)
+    weights = S.make_weights(cfg, seed=21, perturb=True)
+    x, hole = inputs(B, H, W, "polygons", seed=H * 7 + W)
+    check_parity(cfg, weights, x, hole, TOL_BF16)
+
+
 def test_bf16_precision_workload_512_full_size():
     """Precision workload at full size: 4 frames of 512x512, d256 h8, 8 blocks, MLP ratio 4."""
     w = WORKLOAD_B
