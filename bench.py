@@ -238,6 +238,7 @@ def main():
 
     from paper_2509_10466_gb300 import binding, build as Bld, synthetic as S
     from paper_2509_10466_gb300.config import FP32
+    from paper_2509_10466_gb300.replicas import frame_seed, job_time_and_throughput
     if rank == 0:
         Bld.build()
     if dist:
@@ -247,8 +248,8 @@ def main():
     w, B, H, W = workload(args)
     cfg = w.model
     weights = S.make_weights(cfg, seed=0)
-    x_np = S.make_frames(B, H, W, seed=1 + 1000 * rank)
-    hole_np = S.make_hole(B, H, W, w.mask_kind, seed=1 + 1000 * rank)
+    x_np = S.make_frames(B, H, W, seed=frame_seed(rank))
+    hole_np = S.make_hole(B, H, W, w.mask_kind, seed=frame_seed(rank))
     dev = torch.device("cuda", local)
     x = torch.from_numpy(x_np).to(dev)
     hole = torch.from_numpy(hole_np).to(dev)
@@ -289,12 +290,8 @@ def main():
     clk = clocks.stop()
     prof = binding.inpaint_profile_read(ctx)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t)
-    value = world * B * args.steps / (total_ms / 1000.0)
+    job_s, value = job_time_and_throughput(sum(step_ms) / 1000.0, B * args.steps, dist, dev)
+    total_ms = 1000.0 * job_s
     ms_per_step = total_ms / args.steps
     srt = sorted(step_ms)
     p50 = srt[len(srt) // 2]
@@ -313,12 +310,7 @@ def main():
         t0 = time.perf_counter()
         binding.inpaint_batch_host(ctx, xh, hh, oh, stream)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t)
-    e2e_value = world * B * args.steps / e2e_total
+    _, e2e_value = job_time_and_throughput(sum(e2e_s), B * args.steps, dist, dev)
     assert np.array_equal(oh.numpy(), out.cpu().numpy()), "host path result differs from the device path"
 
     # ---- plain FP32 form on the same GPU and workload

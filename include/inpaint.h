@@ -213,6 +213,12 @@ INPAINT_API const char* inpaint_strerror(int code);
 INPAINT_API int inpaint_test_gemm_bf16(const void* A, const void* Bt, float* C, int M, int N, int K,
                            void* stream);
 
+/* The two GELU evaluations of the library on device floats x[n]: y_bf16_form[i] as the
+ * BF16 tensor-core epilogues compute it (erf from Abramowitz & Stegun 7.1.26, |error of
+ * erf| <= 1.5e-7) and y_fp32_form[i] with CUDA's erff (the FP32 form). */
+INPAINT_API int inpaint_test_gelu(const float* x, float* y_bf16_form, float* y_fp32_form, int n,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

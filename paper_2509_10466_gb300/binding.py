@@ -64,6 +64,7 @@ _SIGS = {
     "inpaint_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "inpaint_destroy": (None, [_P]),
     "inpaint_test_gemm_bf16": (_I, [_P, _P, _P, _I, _I, _I, _P]),
+    "inpaint_test_gelu": (_I, [_P, _P, _P, _I, _P]),
 }
 
 
@@ -244,6 +245,11 @@ def inpaint_test_gemm_bf16(A, Bt, C, stream=None):
     N = Bt.shape[0]
     _check(load().inpaint_test_gemm_bf16(_ptr(A), _ptr(Bt), _ptr(C), M, N, K, _stream(stream)),
            "inpaint_test_gemm_bf16")
+
+
+def inpaint_test_gelu(x, y_bf16_form, y_fp32_form, stream=None):
+    _check(load().inpaint_test_gelu(_ptr(x), _ptr(y_bf16_form), _ptr(y_fp32_form), x.numel(), _stream(stream)),
+           "inpaint_test_gelu")
 
 
 # ----------------------------------------------------------------------------- convenience object

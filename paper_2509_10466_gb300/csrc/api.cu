@@ -533,6 +533,28 @@ int inpaint_launch_count(inpaint_ctx* c, int64_t* n) {
   return INPAINT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+__global__ void gelu_pair_kernel(const float* __restrict__ x, float* __restrict__ y_bf16_form,
+                                 float* __restrict__ y_fp32_form, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    y_bf16_form[i] = gelu_as(x[i]);
+    y_fp32_form[i] = gelu_erf(x[i]);
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int inpaint_test_gelu(const float* x, float* y_bf16_form, float* y_fp32_form, int n, void* stream) {
+  if (!x || !y_bf16_form || !y_fp32_form || n < 0) return INPAINT_E_INVAL;
+  if (n == 0) return INPAINT_OK;
+  gelu_pair_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, y_bf16_form, y_fp32_form, n);
+  return cuda_err(cudaGetLastError());
+}
+
 int inpaint_test_gemm_bf16(const void* A, const void* Bt, float* C, int M, int N, int K, void* stream) {
   if (!A || !Bt || !C || M <= 0 || N <= 0 || K <= 0 || N % 64 || K % 64) return INPAINT_E_INVAL;
   static int* err = nullptr;

@@ -36,6 +36,36 @@ __host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 __device__ __forceinline__ float gelu_erf(float x) {
   return 0.5f * x * (1.0f + erff(x * 0.70710678118654752440f));
 }
+// GELU for the BF16 form, whose GELU outputs are rounded to bf16 right away: erf from
+// Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26,
+//   erf(z) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-z^2),  t = 1 / (1 + p z),
+// |error| <= 1.5e-7 for z >= 0 (odd extension for z < 0), evaluated with the PTX
+// approximate reciprocal and base-2 exponential.  About 13 instructions instead of the
+// ~30 of a correctly rounded erff; far below the bf16 rounding step of its output.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float gelu_as(float x) {
+  const float z = fabsf(x) * 0.70710678118654752440f;
+  const float t = rcp_approx(fmaf(0.3275911f, z, 1.0f));
+  float p = fmaf(1.061405429f, t, -1.453152027f);
+  p = fmaf(p, t, 1.421413741f);
+  p = fmaf(p, t, -0.284496736f);
+  p = fmaf(p, t, 0.254829592f);
+  p *= t;
+  const float e = ex2_approx(-(z * z) * 1.44269504088896340736f);
+  const float erf_v = copysignf(fmaf(-p, e, 1.0f), x);
+  const float hx = 0.5f * x;
+  return fmaf(hx, erf_v, hx);
+}
+
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(bf16 v) { return __bfloat162float(v); }
 template <typename T> __device__ __forceinline__ T from_f32(float v);
@@ -76,7 +106,7 @@ cudaError_t launch_gemm_tc_resid_ln(const bf16* A, const bf16* Bt, float* X, int
 
 // Fused MLP on tcgen05: X += gelu(Y W1 + b1) W2 + b2 and ln_out = LN(X) without writing
 // the hidden activations; W1t [hid][d] and W2t [d][hid] bf16 (K-major).  Y may alias
-// ln_out.  Supported for d in {128, 256} and hid a multiple of 128.
+// ln_out.  Supported for d in {64, 128, 256} and hid a multiple of 128.
 bool mlp_tc_supported(int d, int hid);
 cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const float* b1, const float* b2, float* X,
                           const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,

@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(THREADS, 1) upconv_tc_kernel(const __grid_cons
           uint32_t packed[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            const float x0 = gelu_erf(__uint_as_float(v[2 * k]) + __ldg(bias + c0 + 2 * k));
-            const float x1 = gelu_erf(__uint_as_float(v[2 * k + 1]) + __ldg(bias + c0 + 2 * k + 1));
+            const float x0 = gelu_as(__uint_as_float(v[2 * k]) + __ldg(bias + c0 + 2 * k));
+            const float x1 = gelu_as(__uint_as_float(v[2 * k + 1]) + __ldg(bias + c0 + 2 * k + 1));
             __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
             packed[k] = *reinterpret_cast<uint32_t*>(&h2);
           }

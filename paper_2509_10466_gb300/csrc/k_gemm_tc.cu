@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (epi == EPI_BIAS || epi == EPI_BIAS_GELU) {
           if (epi == EPI_BIAS_GELU) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) f[j] = gelu_erf(f[j]);
+            for (int j = 0; j < 32; ++j) f[j] = gelu_as(f[j]);
           }
           if (live) store32_bf16(reinterpret_cast<bf16*>(args.C) + (size_t)row * args.ldc + col, f);
         } else {  // residual (+ LayerNorm statistics)

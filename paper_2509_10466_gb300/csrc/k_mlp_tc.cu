@@ -14,9 +14,10 @@
 // + two H buffers (128 cols each).  The bf16 H_j is written in the 128-byte-swizzled
 // K-major layout that the MMA descriptor expects (16-byte chunk c of row r at c ^ (r%8)).
 //
-// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2..17 epilogue (four per TMEM lane
-// quarter, splitting columns): the erf-GELU of every hidden value is the bulk of the
-// instruction work, so the epilogue gets as many warps as the register file allows.
+// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2..9 hidden-chunk epilogue (two per
+// TMEM lane quarter, splitting the chunk's columns), 10..13 final epilogue (one per lane
+// quarter, a whole row per thread: residual, store, LayerNorm).  The final epilogue of a
+// tile overlaps the next tile's hidden chunks.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -28,7 +29,9 @@ namespace inpaint {
 namespace {
 
 constexpr int BM = 128, BK = 64, HC = 128;   // rows per tile, k-block, hidden chunk
-constexpr int EW = 4, EPI_WARPS = 4 * EW, THREADS = 64 + 32 * EPI_WARPS;
+constexpr int EW = 2, EPI_WARPS = 4 * EW;     // GELU warps: two per TMEM lane quarter
+constexpr int OUT_WARPS = 4;                  // final-epilogue warps: one per lane quarter
+constexpr int THREADS = 64 + 32 * (EPI_WARPS + OUT_WARPS);
 constexpr int RING = 5;                      // 16 KB weight stages
 
 template <int D>
@@ -41,7 +44,7 @@ struct MlpCfg {
   static constexpr int W2_BYTES = HR * BK * 2;
   static constexpr int STAGE_BYTES = 16384;
   static constexpr int SMEM_BYTES = A_BYTES + 2 * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
-                                    512 /*barriers*/ + EPI_WARPS * 32 * 2 * 4 /*LN statistics*/;
+                                    512 /*barriers*/;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 and 384
 };
 
@@ -97,7 +100,6 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   uint64_t* teardown = o_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* ln_stats = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [EPI_WARPS][32][2]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, NJ = args.hid / HC;
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       tc::mbar_init(&hs_empty[b], 1);
     }
     tc::mbar_init(o_full, 1);
-    tc::mbar_init(o_empty, EPI_WARPS);
+    tc::mbar_init(o_empty, OUT_WARPS);
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -240,17 +242,14 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       tc::mbar_wait_timed(teardown, 0);
     }
     __syncwarp();
-  } else {
+  } else if (warp < 2 + EPI_WARPS) {
+    // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 swizzled SMEM operand of MMA2
     const int quarter = warp & 3, cg = (warp - 2) >> 2;
     const int r = quarter * 32 + lane;  // row within the tile (= TMEM lane)
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     uint32_t q = 0;
     bool ok = true;
-    int t = 0;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
-      const int row = tile * BM + r;
-      const bool live = row < M;
-      // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 swizzled SMEM operand
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
       for (int j = 0; j < NJ; ++j, ++q) {
         const uint32_t hb = q & 1, use = q >> 1;
         if (!tc::mbar_wait(&h_full[hb], use & 1, abort_flag)) { ok = false; break; }
@@ -268,8 +267,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           uint32_t pk[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            const float a0 = gelu_erf(__uint_as_float(v[2 * k]) + bv[2 * k]);
-            const float a1 = gelu_erf(__uint_as_float(v[2 * k + 1]) + bv[2 * k + 1]);
+            const float a0 = gelu_as(__uint_as_float(v[2 * k]) + bv[2 * k]);
+            const float a1 = gelu_as(__uint_as_float(v[2 * k + 1]) + bv[2 * k + 1]);
             __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
             pk[k] = *reinterpret_cast<uint32_t*>(&h2);
           }
@@ -289,35 +288,43 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           tc::mbar_arrive(&hs_full[hb]);
         }
       }
-      if (!ok) break;
-      // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16
+    }
+    if (!ok) {
+      if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+      *abort_flag = 1;
+    }
+  } else {
+    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; one thread per row
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+    bool ok = true;
+    int t = 0;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+      const int row = tile * BM + r;
+      const bool live = row < M;
       if (!tc::mbar_wait(o_full, t & 1, abort_flag)) { ok = false; break; }
       __syncwarp();
       tc::fence_after_sync();
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
-      const int c_lo = cg * (D / EW);
+      float* xr = args.X + (size_t)(live ? row : 0) * D;
 #pragma unroll 1
-      for (int c0 = c_lo; c0 < c_lo + D / EW; c0 += 32) {
+      for (int c0 = 0; c0 < D; c0 += 32) {
         uint32_t v[32];
         tc::tmem_ld_32x32b_x32(lane_base + c0, v);
         tc::tmem_ld_wait();
+        if (!live) continue;
         float f[32], bv[32];
         load32(args.b2 + c0, bv);
-        if (live) {
-          float* xr = args.X + (size_t)row * D + c0;
-          float4* x4 = reinterpret_cast<float4*>(xr);
+        float4* x4 = reinterpret_cast<float4*>(xr + c0);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float4 o = x4[k];
-            f[4 * k] = o.x + (__uint_as_float(v[4 * k]) + bv[4 * k]);
-            f[4 * k + 1] = o.y + (__uint_as_float(v[4 * k + 1]) + bv[4 * k + 1]);
-            f[4 * k + 2] = o.z + (__uint_as_float(v[4 * k + 2]) + bv[4 * k + 2]);
-            f[4 * k + 3] = o.w + (__uint_as_float(v[4 * k + 3]) + bv[4 * k + 3]);
-            x4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 32; ++k) f[k] = 0.f;
+        for (int k = 0; k < 8; ++k) {
+          const float4 o = x4[k];
+          f[4 * k] = o.x + (__uint_as_float(v[4 * k]) + bv[4 * k]);
+          f[4 * k + 1] = o.y + (__uint_as_float(v[4 * k + 1]) + bv[4 * k + 1]);
+          f[4 * k + 2] = o.z + (__uint_as_float(v[4 * k + 2]) + bv[4 * k + 2]);
+          f[4 * k + 3] = o.w + (__uint_as_float(v[4 * k + 3]) + bv[4 * k + 3]);
+          x4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
         }
         float cm = 0.f;
 #pragma unroll
@@ -335,48 +342,31 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(o_empty);  // OUT drained: the next tile's MMA2 may start
-      float* st = ln_stats + ((size_t)(warp - 2) * 32 + lane) * 2;
-      st[0] = run_mean;
-      st[1] = run_m2;
-      named_sync(1 + quarter, 32 * EW);
-      float mean = 0.f, m2 = 0.f, n = 0.f;
-#pragma unroll
-      for (int g2 = 0; g2 < EW; ++g2) {
-        const float* o = ln_stats + ((size_t)(4 * g2 + ((quarter - 2) & 3)) * 32 + lane) * 2;
-        const float om = o[0], oq = o[1], on = (float)(D / EW);
-        const float nn = n + on;
-        const float dl = om - mean;
-        mean += dl * (on / nn);
-        m2 += oq + dl * dl * (n * on / nn);
-        n = nn;
-      }
-      named_sync(1 + quarter, 32 * EW);
-      const float rstd = rsqrtf(m2 / n + 1e-5f);
-      if (live) {
+      if (!live) continue;
+      const float mean = run_mean, rstd = rsqrtf(run_m2 / (float)D + 1e-5f);
 #pragma unroll 1
-        for (int c0 = c_lo; c0 < c_lo + D / EW; c0 += 32) {
-          float xv[32], gv[32], bv[32];
-          const float4* xr = reinterpret_cast<const float4*>(args.X + (size_t)row * D + c0);
+      for (int c0 = 0; c0 < D; c0 += 32) {
+        float xv[32], gv[32], bv[32];
+        const float4* x4 = reinterpret_cast<const float4*>(xr + c0);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float4 o = xr[k];
-            xv[4 * k] = o.x; xv[4 * k + 1] = o.y; xv[4 * k + 2] = o.z; xv[4 * k + 3] = o.w;
+        for (int k = 0; k < 8; ++k) {
+          const float4 o = x4[k];
+          xv[4 * k] = o.x; xv[4 * k + 1] = o.y; xv[4 * k + 2] = o.z; xv[4 * k + 3] = o.w;
+        }
+        load32(args.ln_g + c0, gv);
+        load32(args.ln_b + c0, bv);
+        uint4* dst = reinterpret_cast<uint4*>(args.ln_out + (size_t)row * D + c0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint32_t w[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c = 8 * k + 2 * e;
+            __nv_bfloat162 h2 = __floats2bfloat162_rn((xv[c] - mean) * rstd * gv[c] + bv[c],
+                                                      (xv[c + 1] - mean) * rstd * gv[c + 1] + bv[c + 1]);
+            w[e] = *reinterpret_cast<uint32_t*>(&h2);
           }
-          load32(args.ln_g + c0, gv);
-          load32(args.ln_b + c0, bv);
-          uint4* dst = reinterpret_cast<uint4*>(args.ln_out + (size_t)row * D + c0);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int c = 8 * k + 2 * e;
-              __nv_bfloat162 h2 = __floats2bfloat162_rn((xv[c] - mean) * rstd * gv[c] + bv[c],
-                                                        (xv[c + 1] - mean) * rstd * gv[c + 1] + bv[c + 1]);
-              w[e] = *reinterpret_cast<uint32_t*>(&h2);
-            }
-            dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
-          }
+          dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
         }
       }
     }
@@ -450,7 +440,7 @@ cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpA
 
 }  // namespace
 
-bool mlp_tc_supported(int d, int hid) { return (d == 128 || d == 256) && hid % HC == 0 && hid >= HC; }
+bool mlp_tc_supported(int d, int hid) { return (d == 64 || d == 128 || d == 256) && hid % HC == 0 && hid >= HC; }
 
 cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const float* b1, const float* b2, float* X,
                           const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,
@@ -460,7 +450,8 @@ cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const
     return cudaErrorInvalidValue;
   MlpArgs a{X, ln_out, b1, b2, ln_g, ln_b, M, hid, err};
   if (d == 256) return launch_d<256>(Y, W1t, W2t, a, st);
-  return launch_d<128>(Y, W1t, W2t, a, st);
+  if (d == 128) return launch_d<128>(Y, W1t, W2t, a, st);
+  return launch_d<64>(Y, W1t, W2t, a, st);
 }
 
 }  // namespace inpaint

@@ -130,7 +130,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 // 32 lanes x 32 consecutive f32 columns: thread i gets lane (base + i), columns c..c+31.
+// The instruction is warp-synchronous (.sync.aligned): reconverge first, since callers
+// branch per lane (rows past M) between loads.
 __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
+  __syncwarp();
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "

@@ -36,6 +36,22 @@ def test_tcgen05_gemm_matches_fp32_matmul(M, N, K):
     assert rel < 1e-5, float(rel)
 
 
+def test_gelu_of_the_bf16_form_matches_erff():
+    """A&S 7.1.26 erf (|error| <= 1.5e-7) inside GELU: within 1e-6 absolute of CUDA's erff GELU,
+    and within 1e-6 of the FP64 closed form, over [-12, 12]."""
+    lib()
+    x = torch.linspace(-12, 12, 200001, dtype=torch.float32)
+    xd = x.cuda()
+    a = torch.empty_like(xd)
+    b = torch.empty_like(xd)
+    binding.inpaint_test_gelu(xd, a, b)
+    torch.cuda.synchronize()
+    ref = 0.5 * x.double() * (1 + torch.erf(x.double() / 2 ** 0.5))
+    assert float((a.cpu().double() - b.cpu().double()).abs().max()) <= 1e-6
+    assert float((a.cpu().double() - ref).abs().max()) <= 1e-6
+    assert float((b.cpu().double() - ref).abs().max()) <= 1e-6
+
+
 # ----------------------------------------------------------------------------- FP32 form
 
 def test_fp32_plain_256_matches_oracle():
