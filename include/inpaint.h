@@ -135,6 +135,21 @@ INPAINT_API int inpaint_batch_ws(inpaint_ctx* ctx, void* workspace, size_t works
 INPAINT_API int inpaint_batch_host(inpaint_ctx* ctx, const float* x_host, const uint8_t* hole_host,
                        int B, int H, int W, float* out_host, void* stream);
 
+/* Full-resolution path with the pre/post processing on the GPU.  The paper runs
+ * segmentation and inpainting at half resolution and scales the outputs by 2
+ * ("Upscaling"), and builds the hole from the masks of the objects the user selected
+ * ("Object Control").  Inputs (device): x [B,3,H,W] float32 full-resolution frames (H,
+ * W even); obj_masks uint8 [B,K,H/2,W/2] per-object masks at model resolution (nonzero
+ * = object pixel); selected uint8 [B,K] (nonzero = the object is private).  Steps:
+ * hole_half = OR of the selected masks (bit-exact); x_half = 2x2 mean of x; inpaint at
+ * H/2 x W/2; out [B,3,H,W] = hole_half[y/2][x/2] ? pred_half[y/2][x/2] : x[y][x]
+ * (nearest x2 upscale; known pixels copied exactly).  hole_half_out (device uint8
+ * [B,H/2,W/2]) receives the hole if not NULL.  Uses the context's workspace.
+ * Errors: E_INVAL for odd H or W, K < 1, NULL pointers. */
+INPAINT_API int inpaint_fullres(inpaint_ctx* ctx, const float* x, const uint8_t* obj_masks,
+                                const uint8_t* selected, int B, int K, int H, int W, float* out,
+                                uint8_t* hole_half_out, void* stream);
+
 /* Token masks v0 ... vL of the last inpaint_frame/inpaint_batch call, copied to host:
  * uint8 [(L+1), B, Ht*Wt] (Ht = H_pad/4, Wt = W_pad/4, row-major tokens).  `n` is
  * the capacity of `host_out` in bytes; E_INVAL if too small, E_STATE if no forward

@@ -331,3 +331,26 @@ def loss_only(x, hole, target, weights, cfg) -> float:
     with torch.no_grad():
         out = forward(x, hole, torch.as_tensor(weights).to(DT), cfg)["out"]
         return float(l1_hole_loss(out, target, hole)[0])
+
+
+# ----------------------------------------------------------------------------- full-resolution pre/post
+
+def fullres(x, obj_masks, selected, weights, cfg) -> dict:
+    """Half-resolution inpainting of full-resolution frames (Section "Upscaling"), with the
+    hole built from the selected objects' masks (Section "Object Control").
+
+    x float [B,3,H,W] (H, W even); obj_masks uint8 [B,K,H/2,W/2]; selected uint8 [B,K].
+    hole_half = OR over selected k of (mask != 0); x_half = mean of each 2x2 block;
+    out = hole_half[y//2, x//2] ? pred_half[y//2, x//2] : x[y, x].
+    """
+    x = torch.as_tensor(x).to(DT)
+    m = torch.as_tensor(obj_masks) != 0
+    sel = torch.as_tensor(selected) != 0
+    B, _, H, W = x.shape
+    hole_half = (m & sel[:, :, None, None]).any(dim=1).to(torch.uint8)
+    x_half = 0.25 * (x[:, :, 0::2, 0::2] + x[:, :, 0::2, 1::2] + x[:, :, 1::2, 0::2] + x[:, :, 1::2, 1::2])
+    r = forward(x_half, hole_half, weights, cfg)
+    up = r["pred"].repeat_interleave(2, dim=2).repeat_interleave(2, dim=3)
+    hole_up = hole_half.repeat_interleave(2, dim=1).repeat_interleave(2, dim=2)
+    out = torch.where((hole_up != 0)[:, None], up, x)
+    return {"out": out, "hole_half": hole_half, "pred_half": r["pred"], "masks": r["masks"]}

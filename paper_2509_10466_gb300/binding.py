@@ -55,6 +55,7 @@ _SIGS = {
     "inpaint_batch_ws": (_I, [_P, _P, ctypes.c_size_t, _P, _P, _I, _I, _I, _P, _P, _P]),
     "inpaint_batch_host": (_I, [_P, _P, _P, _I, _I, _I, _P, _P]),
     "inpaint_token_masks": (_I, [_P, _P, ctypes.c_size_t]),
+    "inpaint_fullres": (_I, [_P, _P, _P, _P, _I, _I, _I, _I, _P, _P, _P]),
     "inpaint_l1_hole_loss": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "inpaint_l1_hole_loss_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "inpaint_backward": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P]),
@@ -188,6 +189,14 @@ def inpaint_batch_host(ctx, x: np.ndarray | object, hole, out, stream=None):
         return ctypes.c_void_p(a.ctypes.data) if isinstance(a, np.ndarray) else ctypes.c_void_p(a.data_ptr())
 
     _check(load().inpaint_batch_host(ctx, hp(x), hp(hole), B, H, W, hp(out), _stream(stream)), "inpaint_batch_host")
+
+
+def inpaint_fullres(ctx, x, obj_masks, selected, out, hole_half=None, stream=None):
+    """Full-resolution frames -> half-resolution inpainting -> x2 upscaled composite (see inpaint.h)."""
+    B, _, H, W = x.shape
+    K = obj_masks.shape[1]
+    _check(load().inpaint_fullres(ctx, _ptr(x), _ptr(obj_masks), _ptr(selected), B, K, H, W, _ptr(out),
+                                  _ptr(hole_half), _stream(stream)), "inpaint_fullres")
 
 
 def inpaint_token_masks(ctx, blocks: int, B: int, Ntok: int) -> np.ndarray:

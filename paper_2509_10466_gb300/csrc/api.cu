@@ -137,6 +137,10 @@ int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
   transpose_f32<<<64, 256, 0, st>>>(c->w32 + o.embw, c->embed_wt, c->d, 64);
   conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d1w, c->dec1_wt, c->c1, c->d);
   conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d2w, c->dec2_wt, c->c2, c->c1);
+  if (c->embed_w16) {
+    // embed.w [d][64] as bf16 = the transpose of the [64][d] copy made above
+    transpose_to_bf16<<<dim3(cdiv(c->d, 32), cdiv(64, 32)), dim3(32, 8), 0, st>>>(c->embed_wt, c->embed_w16, 64, c->d);
+  }
   if (c->use_bf16 && c->dec1_wp && launch_subpixel_weights(c->w32 + o.d1w, c->c1, c->d, c->dec1_wp, st) != cudaSuccess)
     return INPAINT_E_CUDA;
   if (c->use_bf16 && c->dec2_wp && launch_subpixel_weights(c->w32 + o.d2w, c->c2, c->c1, c->dec2_wp, st) != cudaSuccess)
@@ -175,8 +179,12 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     if (c->use_bf16) {
       const float* g0 = c->w32 + (c->L ? o.blk[0].ln1g : o.lnfg);
       const float* b0 = c->w32 + (c->L ? o.blk[0].ln1b : o.lnfb);
-      TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st,
-                                g0, b0, reinterpret_cast<bf16*>(ws + p.ln))));
+      if (c->embed_w16)
+        TRY(cuda_err(launch_embed_tc(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_w16, c->w32 + o.embb, d, tok, masks,
+                                     g0, b0, reinterpret_cast<bf16*>(ws + p.ln), st)));
+      else
+        TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st,
+                                  g0, b0, reinterpret_cast<bf16*>(ws + p.ln))));
       ln_ready = true;
     } else {
       TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st)));
@@ -319,11 +327,13 @@ void inpaint_destroy(inpaint_ctx* c) {
   cudaFree(c->dec2_wt);
   cudaFree(c->lin_bf16);
   cudaFree(c->dec1_wp);
+  cudaFree(c->embed_w16);
   cudaFree(c->dec2_wp);
   cudaFree(c->dev_err);
   cudaFree(c->arena);
   cudaFree(c->stage);
   cudaFree(c->bws);
+  cudaFree(c->pp);
   for (auto& e : c->events) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -355,7 +365,7 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
   const size_t d = c->d, h = c->hid;
   c->lin_block_elems = 4 * d * d + 2 * h * d;
   c->weight_bytes = c->nparams * 4 + 64 * d * 4 + 9 * d * c->c1 * 4 + 9 * (size_t)c->c1 * c->c2 * 4 +
-                    (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 + (size_t)32 * (c->c1 * d + c->c2 * c->c1) : 0) +
+                    (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 + (size_t)32 * (c->c1 * d + c->c2 * c->c1) + 128 * d : 0) +
                     256;
   if (cfg->hbm_budget_bytes && c->weight_bytes > cfg->hbm_budget_bytes) {
     delete c;
@@ -367,6 +377,7 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
             cudaMalloc(&c->dec2_wt, 9 * (size_t)c->c1 * c->c2 * 4) == cudaSuccess &&
             cudaMalloc(&c->dev_err, 256) == cudaSuccess &&
             (!c->use_bf16 || cudaMalloc(&c->lin_bf16, (size_t)c->L * c->lin_block_elems * 2) == cudaSuccess) &&
+            (!c->use_bf16 || !embed_tc_supported(c->d) || cudaMalloc(&c->embed_w16, 64 * d * 2) == cudaSuccess) &&
             (!c->use_bf16 || !upconv_tc_supported(c->d, c->c1) ||
              cudaMalloc(&c->dec1_wp, (size_t)16 * c->c1 * c->d * 2) == cudaSuccess) &&
             (!c->use_bf16 || !upconv_tc_supported(c->c1, c->c2) ||
@@ -461,6 +472,26 @@ int inpaint_token_masks(inpaint_ctx* c, uint8_t* host, size_t n) {
   if (n < need) return INPAINT_E_INVAL;
   if (cudaDeviceSynchronize() != cudaSuccess) return INPAINT_E_CUDA;
   return cuda_err(cudaMemcpy(host, c->arena + c->last.masks, need, cudaMemcpyDeviceToHost));
+}
+
+int inpaint_fullres(inpaint_ctx* c, const float* x, const uint8_t* obj_masks, const uint8_t* selected, int B, int K,
+                    int H, int W, float* out, uint8_t* hole_half_out, void* stream) {
+  if (!c || !x || !obj_masks || !selected || !out || K < 1 || (H & 1) || (W & 1) || bad_shape(B, H, W))
+    return INPAINT_E_INVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int h = H / 2, w = W / 2;
+  const size_t nx = (size_t)B * 3 * h * w, nh = (size_t)B * h * w;
+  const size_t bx = align_up(nx * 4, 256), bh = align_up(nh, 256);
+  TRY(grow(&c->pp, &c->pp_bytes, 3 * bx + bh, c, c->arena_bytes + c->stage_bytes + c->bws_bytes));
+  float* xh = reinterpret_cast<float*>(c->pp);
+  float* pred = reinterpret_cast<float*>(c->pp + bx);
+  float* outh = reinterpret_cast<float*>(c->pp + 2 * bx);
+  uint8_t* hole = hole_half_out ? hole_half_out : c->pp + 3 * bx;
+  { LaunchScope ls(c, st, K_OTHER); TRY(cuda_err(launch_mask_union(obj_masks, selected, B, K, h, w, hole, st))); }
+  { LaunchScope ls(c, st, K_OTHER); TRY(cuda_err(launch_downscale2(x, B, H, W, xh, st))); }
+  TRY(inpaint_batch(c, xh, hole, B, h, w, outh, pred, stream));
+  LaunchScope ls(c, st, K_OTHER);
+  return cuda_err(launch_upscale_composite(pred, hole, x, B, H, W, out, st));
 }
 
 int inpaint_l1_hole_loss(inpaint_ctx* c, const float* out, const float* target, const uint8_t* hole, int B, int H,

@@ -82,6 +82,13 @@ cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int 
                          const float* we, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st,
                          const float* ln_g = nullptr, const float* ln_b = nullptr, bf16* ln_out = nullptr);
 
+// Tensor-core form of the patch embedding (BF16 form): bf16 patches and weights
+// (we16 = embed.w as bf16 [d][64]), FP32 accumulation; writes tok, v0 and LN(tok).
+bool embed_tc_supported(int d);
+cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,
+                            const float* be, int d, float* tok, uint8_t* v0, const float* ln_g, const float* ln_b,
+                            bf16* ln_out, cudaStream_t st);
+
 // LayerNorm over the last dim (eps 1e-5, biased variance, FP32 statistics).
 template <typename OutT>
 cudaError_t launch_layernorm(const float* x, const float* g, const float* b, OutT* y, int M, int d,
@@ -151,6 +158,13 @@ template <typename T>
 cudaError_t launch_head_composite(const T* in, int B, int Hp, int Wp, int C, const float* wh,
                                   const float* bh, const float* x, const uint8_t* hole, int H, int W,
                                   float* out, float* pred, cudaStream_t st);
+
+// Pre/post-processing around the half-resolution pass (see k_prepost.cu).
+cudaError_t launch_mask_union(const uint8_t* masks, const uint8_t* selected, int B, int K, int h, int w, uint8_t* hole,
+                              cudaStream_t st);
+cudaError_t launch_downscale2(const float* x, int B, int H, int W, float* xh, cudaStream_t st);
+cudaError_t launch_upscale_composite(const float* pred_h, const uint8_t* hole_h, const float* x, int B, int H, int W,
+                                     float* out, cudaStream_t st);
 
 // Hole-L1 loss: per-block partial sums into `partials` (>= loss_partials(n) floats),
 // then a fixed-order final reduction into *loss.

@@ -48,6 +48,7 @@ struct inpaint_ctx {
   float* dec2_wt = nullptr;    // [9][c1][c2]
   inpaint::bf16* lin_bf16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
   size_t lin_block_elems = 0;
+  inpaint::bf16* embed_w16 = nullptr;  // BF16 form: embed.w as bf16 [d][64]
   inpaint::bf16* dec1_wp = nullptr;  // BF16 form: merged sub-pixel weights [4][c1][4d]
   inpaint::bf16* dec2_wp = nullptr;  // [4][c2][4c1]
   size_t weight_bytes = 0;
@@ -60,6 +61,9 @@ struct inpaint_ctx {
   // host e2e staging
   uint8_t* stage = nullptr;
   size_t stage_bytes = 0;
+  // half-resolution buffers of inpaint_fullres
+  uint8_t* pp = nullptr;
+  size_t pp_bytes = 0;
   // backward scratch
   uint8_t* bws = nullptr;
   size_t bws_bytes = 0;

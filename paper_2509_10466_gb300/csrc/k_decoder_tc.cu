@@ -37,6 +37,7 @@ struct DecCfg {
   static constexpr int TMEM_COLS = (2 * COUT <= 32) ? 32 : (2 * COUT <= 64 ? 64 : (2 * COUT <= 128 ? 128 : (2 * COUT <= 256 ? 256 : 512)));
   static constexpr int ACC_STRIDE = TMEM_COLS / 2;  // second accumulator starts on a power-of-two column
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
 template <int COUT>

@@ -109,6 +109,143 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
   }
 }
 
+// Tensor-core form (BF16 form): 64 tokens per CTA.  The patch matrix P [64 tok][64]
+// and the embedding weights [d][64] are staged in shared memory as bf16 (rows padded to
+// 144 bytes for conflict-free ldmatrix); warp w computes tokens 16(w%4).. x channels
+// (w/4)*d/2 .. with mma.sync m16n8k16 (K = 64 in 4 steps, FP32 accumulate).  The tile
+// goes through shared memory so the FP32 token rows, the token mask and the fused
+// LayerNorm (FP32 statistics) are written coalesced.
+template <int D>
+struct EmbTc {
+  static constexpr int TOK = 64, KP = 72;          // padded row length (bf16) of P and W
+  static constexpr int P_BYTES = TOK * KP * 2;
+  static constexpr int W_BYTES = D * KP * 2;
+  static constexpr int OUT_STRIDE = D + 4;         // floats per staged output row
+  static constexpr int SMEM = P_BYTES + W_BYTES + TOK * OUT_STRIDE * 4 + 64 * 4;
+};
+
+__device__ __forceinline__ void ldsm_x4_e(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_e(uint32_t (&r)[2], const void* p) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void mma_16816_e(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float warp_sum_e(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole,
+                                                       int H, int W, int Ht, int Wt, const bf16* __restrict__ we16,
+                                                       const float* __restrict__ be, float* __restrict__ tok,
+                                                       uint8_t* __restrict__ v0, const float* __restrict__ ln_g,
+                                                       const float* __restrict__ ln_b, bf16* __restrict__ ln_out) {
+  using C = EmbTc<D>;
+  extern __shared__ __align__(16) uint8_t esm[];
+  bf16* P = reinterpret_cast<bf16*>(esm);                                   // [64][KP]
+  bf16* Ws = reinterpret_cast<bf16*>(esm + C::P_BYTES);                     // [D][KP]
+  float* O = reinterpret_cast<float*>(esm + C::P_BYTES + C::W_BYTES);      // [64][OUT_STRIDE]
+  int* known = reinterpret_cast<int*>(esm + C::P_BYTES + C::W_BYTES + C::TOK * C::OUT_STRIDE * 4);
+  const int b = blockIdx.y, t0 = blockIdx.x * C::TOK, Nt = Ht * Wt;
+  const size_t HW = (size_t)H * W;
+  const int tid = threadIdx.x;
+  if (tid < C::TOK) known[tid] = 0;
+  // weights: [D][64] bf16 rows of 128 B -> padded rows
+  for (int e = tid; e < D * 8; e += 256) {
+    const int n = e >> 3, ch = e & 7;
+    *reinterpret_cast<uint4*>(Ws + n * C::KP + ch * 8) = *reinterpret_cast<const uint4*>(we16 + (size_t)n * 64 + ch * 8);
+  }
+  __syncthreads();
+  for (int e = tid; e < C::TOK * 16; e += 256) {
+    const int tl = e >> 4, pix = e & 15;
+    const int t = t0 + tl;
+    float r = 0.f, g = 0.f, bl = 0.f, m = 0.f;
+    if (t < Nt) {
+      const int ty = t / Wt, tx = t - (t / Wt) * Wt;
+      const int y = ty * 4 + (pix >> 2), xx = tx * 4 + (pix & 3);
+      if (y < H && xx < W) {
+        const size_t q = (size_t)y * W + xx;
+        if (hole[(size_t)b * HW + q] == 0) {
+          const float* xb = x + (size_t)b * 3 * HW + q;
+          r = xb[0]; g = xb[HW]; bl = xb[2 * HW];
+          m = 1.f;
+        }
+      }
+    }
+    bf16* pr = P + tl * C::KP;
+    pr[pix] = __float2bfloat16_rn(r);
+    pr[16 + pix] = __float2bfloat16_rn(g);
+    pr[32 + pix] = __float2bfloat16_rn(bl);
+    pr[48 + pix] = __float2bfloat16_rn(m);
+    if (m != 0.f) known[tl] = 1;  // every writer stores the same value
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int m0 = (warp & 3) * 16;
+  constexpr int NT = D / 16;                      // n-tiles of 8 per warp (half of D)
+  const int n0 = (warp >> 2) * (D / 2);
+  float acc[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    uint32_t a[4];
+    ldsm_x4_e(a, P + (m0 + (lane & 15)) * C::KP + ks * 16 + (lane >> 4) * 8);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      uint32_t bb[2];
+      ldsm_x2_e(bb, Ws + (n0 + 8 * j + (lane & 7)) * C::KP + ks * 16 + ((lane >> 3) & 1) * 8);
+      mma_16816_e(acc[j], a, bb[0], bb[1]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int c = n0 + 8 * j + 2 * tq;
+    const float b0 = be[c], b1 = be[c + 1];
+    O[(m0 + g) * C::OUT_STRIDE + c] = acc[j][0] + b0;
+    O[(m0 + g) * C::OUT_STRIDE + c + 1] = acc[j][1] + b1;
+    O[(m0 + g + 8) * C::OUT_STRIDE + c] = acc[j][2] + b0;
+    O[(m0 + g + 8) * C::OUT_STRIDE + c + 1] = acc[j][3] + b1;
+  }
+  __syncthreads();
+  if (tid < C::TOK && t0 + tid < Nt) v0[(size_t)b * Nt + t0 + tid] = (uint8_t)known[tid];
+  // each warp writes 8 token rows and their LayerNorm
+  for (int i = 0; i < 8; ++i) {
+    const int tl = warp * 8 + i, t = t0 + tl;
+    if (t >= Nt) break;
+    const float* orow = O + tl * C::OUT_STRIDE;
+    float* trow = tok + ((size_t)b * Nt + t) * D;
+    float s = 0.f;
+    for (int c = lane; c < D; c += 32) {
+      const float v = orow[c];
+      trow[c] = v;
+      s += v;
+    }
+    const float mean = warp_sum_e(s) / (float)D;
+    float q = 0.f;
+    for (int c = lane; c < D; c += 32) {
+      const float v = orow[c] - mean;
+      q = fmaf(v, v, q);
+    }
+    const float rstd = rsqrtf(warp_sum_e(q) / (float)D + 1e-5f);
+    bf16* lrow = ln_out + ((size_t)b * Nt + t) * D;
+    for (int c = lane; c < D; c += 32) lrow[c] = __float2bfloat16_rn((orow[c] - mean) * rstd * ln_g[c] + ln_b[c]);
+  }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -246,6 +383,32 @@ cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int 
   dim3 grid(cdiv(Ht * Wt, EMB_TOK), B);
   embed_kernel<<<grid, 256, 0, st>>>(x, hole, H, W, Ht, Wt, we_t, be, d, tok, v0, ln_g, ln_b, ln_out);
   return cudaGetLastError();
+}
+
+bool embed_tc_supported(int d) { return d == 64 || d == 128 || d == 256; }
+
+template <int D>
+cudaError_t launch_embed_tc_d(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,
+                              const float* be, float* tok, uint8_t* v0, const float* ln_g, const float* ln_b,
+                              bf16* ln_out, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(embed_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, EmbTc<D>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid(cdiv(Ht * Wt, EmbTc<D>::TOK), B);
+  embed_tc_kernel<D><<<grid, 256, EmbTc<D>::SMEM, st>>>(x, hole, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,
+                            const float* be, int d, float* tok, uint8_t* v0, const float* ln_g, const float* ln_b,
+                            bf16* ln_out, cudaStream_t st) {
+  if (d == 256) return launch_embed_tc_d<256>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
+  if (d == 128) return launch_embed_tc_d<128>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
+  if (d == 64) return launch_embed_tc_d<64>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
+  return cudaErrorInvalidValue;
 }
 
 template <typename OutT>

@@ -46,6 +46,7 @@ struct TcCfg {
   static constexpr int COLS_PER_WARP = BN / EW;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/ +
                                     EPI_WARPS * 32 * 2 * 4 /*LayerNorm partial statistics*/;
+  static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
 struct GemmArgs {
@@ -214,10 +215,22 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;  // LayerNorm statistics of this part of the row
 #pragma unroll 1
       for (int c0 = c_lo; c0 < c_lo + Cfg::COLS_PER_WARP; c0 += 32) {
+        const int col = n0 + c0;
+        const bool resid = epi == EPI_BIAS_RESID || epi == EPI_RESID_LN;
+        // bias and residual loads first: their latency overlaps the TMEM load
+        float bv[32], rv[32];
+        if (epi != EPI_NONE) load32(args.bias + col, bv);
+        if (resid) {
+          if (live) {
+            load32(args.resid + (size_t)row * args.ldc + col, rv);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) rv[j] = 0.f;
+          }
+        }
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tbase + c0, r);
         tc::tmem_ld_wait();
-        const int col = n0 + c0;
         float f[32];
         if (epi == EPI_NONE) {
 #pragma unroll
@@ -225,8 +238,6 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
           if (live) store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row * args.ldc + col, f);
           continue;
         }
-        float bv[32];
-        load32(args.bias + col, bv);
 #pragma unroll
         for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]) + bv[j];
         if (epi == EPI_BIAS || epi == EPI_BIAS_GELU) {
@@ -236,13 +247,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
           }
           if (live) store32_bf16(reinterpret_cast<bf16*>(args.C) + (size_t)row * args.ldc + col, f);
         } else {  // residual (+ LayerNorm statistics)
-          if (live) {
-            float rv[32];
-            load32(args.resid + (size_t)row * args.ldc + col, rv);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
-            store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row * args.ldc + col, f);
-          }
+          for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
+          if (live) store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row * args.ldc + col, f);
           if (epi == EPI_RESID_LN) {
             float cm = 0.f;
 #pragma unroll

@@ -15,9 +15,11 @@
 // K-major layout that the MMA descriptor expects (16-byte chunk c of row r at c ^ (r%8)).
 //
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2..9 hidden-chunk epilogue (two per
-// TMEM lane quarter, splitting the chunk's columns), 10..13 final epilogue (one per lane
-// quarter, a whole row per thread: residual, store, LayerNorm).  The final epilogue of a
-// tile overlaps the next tile's hidden chunks.
+// TMEM lane quarter, splitting the chunk's columns), then 4*OW final-epilogue warps (OW per
+// lane quarter, D/OW columns of a row each: residual, store, LayerNorm; the parts'
+// statistics are merged through shared memory).  OW = 1 measured fastest.  The final epilogue of a tile overlaps the next tile's
+// hidden chunks; it drains the output accumulator before the next tile's MMA2 can start,
+// so each chunk's residual loads are issued before its TMEM load to overlap the two.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -30,7 +32,7 @@ namespace {
 
 constexpr int BM = 128, BK = 64, HC = 128;   // rows per tile, k-block, hidden chunk
 constexpr int EW = 2, EPI_WARPS = 4 * EW;     // GELU warps: two per TMEM lane quarter
-constexpr int OUT_WARPS = 4;                  // final-epilogue warps: one per lane quarter
+constexpr int OW = 1, OUT_WARPS = 4 * OW;     // final-epilogue warps per lane quarter
 constexpr int THREADS = 64 + 32 * (EPI_WARPS + OUT_WARPS);
 constexpr int RING = 5;                      // 16 KB weight stages
 
@@ -44,8 +46,9 @@ struct MlpCfg {
   static constexpr int W2_BYTES = HR * BK * 2;
   static constexpr int STAGE_BYTES = 16384;
   static constexpr int SMEM_BYTES = A_BYTES + 2 * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
-                                    512 /*barriers*/;
+                                    512 /*barriers*/ + OUT_WARPS * 32 * 2 * 4 /*LayerNorm partials*/;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 and 384
+  static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
 struct MlpArgs {
@@ -100,6 +103,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   uint64_t* teardown = o_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* ln_stats = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [OUT_WARPS][32][2]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, NJ = args.hid / HC;
@@ -294,37 +298,42 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       *abort_flag = 1;
     }
   } else {
-    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; one thread per row
-    const int quarter = warp & 3;
+    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; half a row per thread
+    const int fw = warp - 2 - EPI_WARPS;           // 0 .. OUT_WARPS-1
+    const int quarter = warp & 3, half = fw >> 2;
     const int r = quarter * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+    const int c_lo = half * (D / OW);
     bool ok = true;
     int t = 0;
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
       const int row = tile * BM + r;
       const bool live = row < M;
+      float* xr = args.X + (size_t)(live ? row : 0) * D;
+      if (live) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xr + c_lo), "r"(D / OW * 4) : "memory");
       if (!tc::mbar_wait(o_full, t & 1, abort_flag)) { ok = false; break; }
       __syncwarp();
       tc::fence_after_sync();
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
-      float* xr = args.X + (size_t)(live ? row : 0) * D;
 #pragma unroll 1
-      for (int c0 = 0; c0 < D; c0 += 32) {
+      for (int c0 = c_lo; c0 < c_lo + D / OW; c0 += 32) {
+        float f[32];
+        float4* x4 = reinterpret_cast<float4*>(xr + c0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {  // residual first: its latency overlaps the TMEM load
+          const float4 o = live ? x4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+          f[4 * k] = o.x; f[4 * k + 1] = o.y; f[4 * k + 2] = o.z; f[4 * k + 3] = o.w;
+        }
         uint32_t v[32];
         tc::tmem_ld_32x32b_x32(lane_base + c0, v);
         tc::tmem_ld_wait();
-        if (!live) continue;
-        float f[32], bv[32];
+        float bv[32];
         load32(args.b2 + c0, bv);
-        float4* x4 = reinterpret_cast<float4*>(xr + c0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float4 o = x4[k];
-          f[4 * k] = o.x + (__uint_as_float(v[4 * k]) + bv[4 * k]);
-          f[4 * k + 1] = o.y + (__uint_as_float(v[4 * k + 1]) + bv[4 * k + 1]);
-          f[4 * k + 2] = o.z + (__uint_as_float(v[4 * k + 2]) + bv[4 * k + 2]);
-          f[4 * k + 3] = o.w + (__uint_as_float(v[4 * k + 3]) + bv[4 * k + 3]);
-          x4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+        for (int k = 0; k < 32; ++k) f[k] += __uint_as_float(v[k]) + bv[k];
+        if (live) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) x4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
         }
         float cm = 0.f;
 #pragma unroll
@@ -342,10 +351,28 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(o_empty);  // OUT drained: the next tile's MMA2 may start
+      // merge the two halves of each row in a fixed order
+      float* st = ln_stats + ((size_t)fw * 32 + lane) * 2;
+      st[0] = run_mean;
+      st[1] = run_m2;
+      named_sync(1 + quarter, 32 * OW);
+      float mean = 0.f, m2 = 0.f, n = 0.f;
+#pragma unroll
+      for (int g2 = 0; g2 < OW; ++g2) {
+        // final warp of half g2 in this quarter: fw = 4*g2 + ((quarter - 2) & 3)
+        const float* o = ln_stats + ((size_t)(4 * g2 + ((quarter - 2) & 3)) * 32 + lane) * 2;
+        const float om = o[0], oq = o[1], on = (float)(D / OW);
+        const float nn = n + on;
+        const float dl = om - mean;
+        mean += dl * (on / nn);
+        m2 += oq + dl * dl * (n * on / nn);
+        n = nn;
+      }
+      named_sync(1 + quarter, 32 * OW);  // the partial slots are reused by the next tile
       if (!live) continue;
-      const float mean = run_mean, rstd = rsqrtf(run_m2 / (float)D + 1e-5f);
+      const float rstd = rsqrtf(m2 / n + 1e-5f);
 #pragma unroll 1
-      for (int c0 = 0; c0 < D; c0 += 32) {
+      for (int c0 = c_lo; c0 < c_lo + D / OW; c0 += 32) {
         float xv[32], gv[32], bv[32];
         const float4* x4 = reinterpret_cast<const float4*>(xr + c0);
 #pragma unroll

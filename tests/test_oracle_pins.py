@@ -436,3 +436,34 @@ def test_gradient_central_finite_differences():
         fd = (O.loss_only(x, hole, tgt, wp, cfg) - O.loss_only(x, hole, tgt, wm, cfg)) / (2 * h)
         an = float(grad[i])
         assert abs(fd - an) <= 1e-6 * max(abs(an), abs(fd)) + floor, (i, fd, an, floor)
+
+
+# ----------------------------------------------------------------------------- full-resolution pre/post
+
+def test_fullres_oracle_against_library_and_sets():
+    cfg = small_cfg(blocks=1)
+    flat = S.make_weights(cfg, seed=12, perturb=True)
+    B, K, H, W = 2, 3, 64, 96
+    rng = np.random.default_rng(12)
+    x = torch.from_numpy(S.make_frames(B, H, W, seed=12)).to(DT)
+    masks = torch.from_numpy((rng.random((B, K, H // 2, W // 2)) < 0.15).astype(np.uint8) * 7)
+    sel = torch.tensor([[1, 0, 1], [0, 0, 1]], dtype=torch.uint8)
+    r = O.fullres(x, masks, sel, flat, cfg)
+    # union of the selected masks, by python sets
+    for b in range(B):
+        want = set()
+        for k in range(K):
+            if sel[b, k]:
+                want |= {(int(i), int(j)) for i, j in zip(*np.nonzero(masks[b, k].numpy()))}
+        got = {(int(i), int(j)) for i, j in zip(*np.nonzero(r["hole_half"][b].numpy()))}
+        assert got == want
+    # the half-resolution input is the 2x2 mean, and the pass runs on it
+    xh = F.avg_pool2d(x, 2)
+    ref = O.forward(xh, r["hole_half"], flat, cfg)
+    assert torch.allclose(r["pred_half"], ref["pred"], rtol=1e-12, atol=1e-12)
+    # composite: nearest x2 of pred on the upscaled hole, known pixels copied exactly
+    up = F.interpolate(ref["pred"], scale_factor=2, mode="nearest")
+    hup = F.interpolate(r["hole_half"][:, None].to(DT), scale_factor=2, mode="nearest")[:, 0] != 0
+    hm = hup[:, None].expand_as(x)
+    assert torch.equal(r["out"][~hm], x[~hm])
+    assert torch.equal(r["out"][hm], up[hm])

@@ -249,3 +249,42 @@ def test_l1_hole_loss_matches_oracle():
         assert float(loss) == 0.0 and float(grad.abs().max()) == 0.0
     finally:
         inp.close()
+
+
+# ----------------------------------------------------------------------------- full-resolution pre/post
+
+@pytest.mark.parametrize("precision", [FP32, BF16])
+def test_fullres_pre_post_matches_oracle(precision):
+    from oracle import inpaint_oracle as O
+    lib()
+    cfg = small(precision, blocks=2)
+    weights = S.make_weights(cfg, seed=13, perturb=True)
+    B, K, H, W = 2, 4, 136, 190
+    rng = np.random.default_rng(13)
+    x = S.make_frames(B, H, W, seed=13)
+    masks = np.zeros((B, K, H // 2, W // 2), np.uint8)
+    for b in range(B):
+        for k in range(K):
+            masks[b, k] = S.make_hole(1, H // 2, W // 2, "polygons", seed=100 * b + k, area=(0.02, 0.1))[0] * (k + 1)
+    sel = (rng.random((B, K)) < 0.6).astype(np.uint8)
+    sel[:, 0] = 1
+    inp = binding.Inpainter(cfg, weights)
+    try:
+        xt = torch.from_numpy(x).cuda()
+        out = torch.empty_like(xt)
+        hole_half = torch.empty(B, H // 2, W // 2, dtype=torch.uint8, device="cuda")
+        binding.inpaint_fullres(inp.ctx, xt, torch.from_numpy(masks).cuda(), torch.from_numpy(sel).cuda(), out,
+                                hole_half)
+        torch.cuda.synchronize()
+        out, hole_half = out.cpu().numpy(), hole_half.cpu().numpy()
+    finally:
+        inp.close()
+    with torch.no_grad():
+        ref = O.fullres(torch.from_numpy(x), torch.from_numpy(masks), torch.from_numpy(sel),
+                        torch.from_numpy(weights.astype(np.float64)), cfg)
+    np.testing.assert_array_equal(hole_half, ref["hole_half"].numpy())
+    hup = np.repeat(np.repeat(hole_half, 2, axis=1), 2, axis=2)
+    known = np.broadcast_to((hup == 0)[:, None], x.shape)
+    np.testing.assert_array_equal(out[known], x[known])
+    errs = hole_rel_l2(out, ref["out"].numpy(), hup)
+    assert max(errs) <= (TOL_FP32 if precision == FP32 else TOL_BF16), errs
