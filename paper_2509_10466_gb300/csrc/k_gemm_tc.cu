@@ -44,8 +44,11 @@ struct TcCfg {
   static constexpr int STAGES = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
   static constexpr int TMEM_COLS = 2 * BN;
   static constexpr int COLS_PER_WARP = BN / EW;
+  static constexpr int PARAM_FLOATS = 1024 + 2 * BN;       // bias (N <= 1024) and LayerNorm scale/shift
+  static constexpr int STAGE_ROW = 80;                      // bytes per row of a warp's bf16 store tile
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/ +
-                                    EPI_WARPS * 32 * 2 * 4 /*LayerNorm partial statistics*/;
+                                    EPI_WARPS * 32 * 2 * 4 /*LayerNorm partial statistics*/ +
+                                    PARAM_FLOATS * 4 + EPI_WARPS * 32 * STAGE_ROW /*store tiles*/;
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
@@ -109,6 +112,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* ln_stats = reinterpret_cast<float*>(smem + S * Cfg::STAGE_BYTES + 256);  // [EPI_WARPS][32][2]
+  float* s_bias = ln_stats + EPI_WARPS * 32 * 2;                                     // [1024]
+  float* s_lng = s_bias + 1024;                                                      // [BN]
+  float* s_lnb = s_lng + BN;                                                         // [BN]
+  uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_lnb + BN);                          // [EPI_WARPS][32][STAGE_ROW]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, N = args.N;
@@ -128,6 +135,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     tc::tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
     tc::tmem_relinquish();
   }
+  // per-column epilogue parameters, read once per CTA
+  const bool bias_smem = args.epi != EPI_NONE && N <= 1024;
+  if (bias_smem)
+    for (int c = threadIdx.x; c < N; c += blockDim.x) s_bias[c] = args.bias[c];
+  if (args.epi == EPI_RESID_LN)
+    for (int c = threadIdx.x; c < BN; c += blockDim.x) { s_lng[c] = args.ln_g[c]; s_lnb[c] = args.ln_b[c]; }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -219,7 +232,17 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         const bool resid = epi == EPI_BIAS_RESID || epi == EPI_RESID_LN;
         // bias and residual loads first: their latency overlaps the TMEM load
         float bv[32], rv[32];
-        if (epi != EPI_NONE) load32(args.bias + col, bv);
+        if (epi != EPI_NONE) {
+          if (bias_smem) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              const float4 t = *reinterpret_cast<const float4*>(s_bias + col + j);
+              bv[j] = t.x; bv[j + 1] = t.y; bv[j + 2] = t.z; bv[j + 3] = t.w;
+            }
+          } else {
+            load32(args.bias + col, bv);
+          }
+        }
         if (resid) {
           if (live) {
             load32(args.resid + (size_t)row * args.ldc + col, rv);
@@ -245,7 +268,19 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
             for (int j = 0; j < 32; ++j) f[j] = gelu_as(f[j]);
           }
-          if (live) store32_bf16(reinterpret_cast<bf16*>(args.C) + (size_t)row * args.ldc + col, f);
+          // through the warp's shared tile: each store instruction then covers 8 rows x 64 B
+          uint8_t* tl = s_tile + (size_t)(warp - 2) * 32 * Cfg::STAGE_ROW;
+          __syncwarp();
+          store32_bf16(reinterpret_cast<bf16*>(tl + lane * Cfg::STAGE_ROW), f);
+          __syncwarp();
+          const int row0 = m0 + quarter * 32;
+#pragma unroll
+          for (int sgi = 0; sgi < 4; ++sgi) {
+            const int rr = 8 * sgi + (lane >> 2), ch = lane & 3;
+            const uint4 v = *reinterpret_cast<const uint4*>(tl + rr * Cfg::STAGE_ROW + ch * 16);
+            if (row0 + rr < M)
+              *reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(args.C) + (size_t)(row0 + rr) * args.ldc + col + ch * 8) = v;
+          }
         } else {  // residual (+ LayerNorm statistics)
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
@@ -298,8 +333,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
               const float4 t = xr[j];
               xv[4 * j] = t.x; xv[4 * j + 1] = t.y; xv[4 * j + 2] = t.z; xv[4 * j + 3] = t.w;
             }
-            load32(args.ln_g + col, gv);
-            load32(args.ln_b + col, bv);
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              const float4 tg = *reinterpret_cast<const float4*>(s_lng + c0 + j);
+              const float4 tb = *reinterpret_cast<const float4*>(s_lnb + c0 + j);
+              gv[j] = tg.x; gv[j + 1] = tg.y; gv[j + 2] = tg.z; gv[j + 3] = tg.w;
+              bv[j] = tb.x; bv[j + 1] = tb.y; bv[j + 2] = tb.z; bv[j + 3] = tb.w;
+            }
 #pragma unroll
             for (int j = 0; j < 32; ++j) xv[j] = (xv[j] - mean) * rstd * gv[j] + bv[j];
             store32_bf16(args.ln_out + (size_t)row * N + col, xv);

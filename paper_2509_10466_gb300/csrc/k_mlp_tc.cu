@@ -45,8 +45,10 @@ struct MlpCfg {
   static constexpr int NHALF = D / HR;                        // W2 k-block = NHALF loads
   static constexpr int W2_BYTES = HR * BK * 2;
   static constexpr int STAGE_BYTES = 16384;
+  static constexpr int PARAM_FLOATS = 1024 + 3 * D;          // b1 (hid <= 1024), b2, LayerNorm scale/shift
   static constexpr int SMEM_BYTES = A_BYTES + 2 * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
-                                    512 /*barriers*/ + OUT_WARPS * 32 * 2 * 4 /*LayerNorm partials*/;
+                                    512 /*barriers*/ + OUT_WARPS * 32 * 2 * 4 /*LayerNorm partials*/ +
+                                    PARAM_FLOATS * 4;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 and 384
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
@@ -65,6 +67,13 @@ struct MlpArgs {
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void load32s(const float* p, float (&v)[32]) {  // shared memory
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 t = *reinterpret_cast<const float4*>(p + 4 * i);
+    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+  }
 }
 __device__ __forceinline__ void load32(const float* __restrict__ p, float (&v)[32]) {
   const float4* p4 = reinterpret_cast<const float4*>(p);
@@ -104,6 +113,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* ln_stats = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [OUT_WARPS][32][2]
+  float* s_b1 = ln_stats + OUT_WARPS * 32 * 2;   // [hid]
+  float* s_b2 = s_b1 + 1024;                     // [D]
+  float* s_lng = s_b2 + D;
+  float* s_lnb = s_lng + D;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, NJ = args.hid / HC;
@@ -132,6 +145,12 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, 512);
     tc::tmem_relinquish();
+  }
+  for (int c = threadIdx.x; c < args.hid; c += blockDim.x) s_b1[c] = args.b1[c];
+  for (int c = threadIdx.x; c < D; c += blockDim.x) {
+    s_b2[c] = args.b2[c];
+    s_lng[c] = args.ln_g[c];
+    s_lnb[c] = args.ln_b[c];
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -267,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + hb * HC + c0, v);
           tc::tmem_ld_wait();
           float bv[32];
-          load32(args.b1 + j * HC + c0, bv);
+          load32s(s_b1 + j * HC + c0, bv);
           uint32_t pk[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
@@ -328,7 +347,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         tc::tmem_ld_32x32b_x32(lane_base + c0, v);
         tc::tmem_ld_wait();
         float bv[32];
-        load32(args.b2 + c0, bv);
+        load32s(s_b2 + c0, bv);
 #pragma unroll
         for (int k = 0; k < 32; ++k) f[k] += __uint_as_float(v[k]) + bv[k];
         if (live) {
@@ -380,8 +399,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           const float4 o = x4[k];
           xv[4 * k] = o.x; xv[4 * k + 1] = o.y; xv[4 * k + 2] = o.z; xv[4 * k + 3] = o.w;
         }
-        load32(args.ln_g + c0, gv);
-        load32(args.ln_b + c0, bv);
+        load32s(s_lng + c0, gv);
+        load32s(s_lnb + c0, bv);
         uint4* dst = reinterpret_cast<uint4*>(args.ln_out + (size_t)row * D + c0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -467,7 +486,9 @@ cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpA
 
 }  // namespace
 
-bool mlp_tc_supported(int d, int hid) { return (d == 64 || d == 128 || d == 256) && hid % HC == 0 && hid >= HC; }
+bool mlp_tc_supported(int d, int hid) {
+  return (d == 64 || d == 128 || d == 256) && hid % HC == 0 && hid >= HC && hid <= 1024;
+}
 
 cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const float* b1, const float* b2, float* X,
                           const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,
