@@ -130,6 +130,7 @@ def flops_per_frame(m, H, W):
         "proj_gemm": 2 * N * d * d * L,
         "fc1_gemm": 2 * N * d * r * d * L,
         "fc2_gemm": 2 * N * r * d * d * L,
+        "mlp_fused": 4 * N * d * r * d * L,
         "decoder1": 2 * (4 * N) * 9 * d * c1,
         "decoder2": 2 * (16 * N) * 9 * c1 * c2,
         "head_composite": 2 * (16 * N) * 9 * c2 * 3,
@@ -148,9 +149,11 @@ def bytes_per_frame(m, H, W, act_bytes=2):
         "layernorm": (2 * L + 1) * N * d * (4 + a),
         "qkv_gemm": L * N * (d * a + 3 * d * a),
         "attention": L * N * (3 * d * a + d * a + 2),
-        "proj_gemm": L * N * (d * a + 2 * d * 4),
+        # proj and fc2 (or the fused MLP) also write the next LayerNorm as bf16
+        "proj_gemm": L * N * (d * a + 2 * d * 4 + d * a),
         "fc1_gemm": L * N * (d * a + r * d * a),
-        "fc2_gemm": L * N * (r * d * a + 2 * d * 4),
+        "fc2_gemm": L * N * (r * d * a + 2 * d * 4 + d * a),
+        "mlp_fused": L * N * (d * a + 2 * d * 4 + d * a),
         "decoder1": N * d * a + 4 * N * m.c1 * a,
         "decoder2": 4 * N * m.c1 * a + 16 * N * m.c2 * a,
         "head_composite": 16 * N * m.c2 * a + 25 * H * W,
@@ -359,7 +362,10 @@ def main():
     def roof(name):
         per_step_launches = launches_per_step[name]
         avg_s = kernels[name]["ms_per_launch"] / 1000.0
-        if name.endswith("_gemm") or name == "decoder1":
+        # the binding resource is the one whose floor (work / peak) is longer
+        t_tensor = fl.get(name, 0) / (tc_peak * 1e12)
+        t_hbm = by.get(name, 0) / (hbm_peak * 1e9)
+        if t_tensor > t_hbm:
             work = fl[name] * B / per_step_launches
             ach = work / avg_s / 1e12
             return {"bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": ach / tc_peak,

@@ -225,7 +225,7 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
         const bool last = l + 1 == c->L;
         const float* ng = c->w32 + (last ? o.lnfg : o.blk[l + 1].ln1g);
         const float* nb = c->w32 + (last ? o.lnfb : o.blk[l + 1].ln1b);
-        LaunchScope ls(c, st, K_FC1);
+        LaunchScope ls(c, st, K_MLP);
         TRY(cuda_err(launch_mlp_tc(ln, wfc1, wfc2, c->w32 + b.fc1b, c->w32 + b.fc2b, tok, ng, nb, ln, M, d, c->hid, err, st)));
         ln_ready = true;
         continue;

@@ -15,7 +15,7 @@ typedef __nv_bfloat16 bf16;
 // Kernel-class ids for event timing (match INPAINT_PROFILE_CLASSES in inpaint.h).
 enum KClass {
   K_EMBED = 0, K_LN = 1, K_QKV = 2, K_ATTN = 3, K_PROJ = 4, K_FC1 = 5, K_FC2 = 6,
-  K_DEC1 = 7, K_DEC2 = 8, K_HEAD = 9, K_OTHER = 10
+  K_DEC1 = 7, K_DEC2 = 8, K_HEAD = 9, K_OTHER = 10, K_MLP = 11
 };
 
 // Device-side error codes written into the context's error word.

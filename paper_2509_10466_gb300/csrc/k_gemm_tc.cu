@@ -11,8 +11,10 @@
 //                 stage, accumulating into one of two TMEM buffers;
 //   warps 2..9    epilogue: two warps per TMEM lane quarter (32 rows each), splitting
 //                 the tile's columns; tcgen05.ld of the finished accumulator, bias /
-//                 GELU / residual / LayerNorm, vector stores.  The other accumulator is
-//                 filled by the next tile's MMAs meanwhile.
+//                 GELU / residual / LayerNorm; global rows are read and written through a
+//                 per-warp shared-memory tile so that every access instruction covers
+//                 whole 64-byte row segments.  The other accumulator is filled by the
+//                 next tile's MMAs meanwhile.
 // Output tiles are visited N-fastest so consecutive CTAs reuse the same A rows from L2.
 //
 // EPI_RESID_LN (N == BN, a whole row per tile) also normalizes the new residual row:
@@ -20,12 +22,13 @@
 // variance, FP32 statistics) is stored as bf16 for the next GEMM.  Each thread reduces
 // its half row chunk by chunk (exact mean and squared deviations per 32 values, merged
 // with Chan's pairwise formula), the two halves of a row are merged through shared
-// memory, and the stored x is re-read to normalize.
+// memory, and the stored x is re-read (the warp's own rows) to normalize.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
 #include "tc_primitives.cuh"
+#include "warp_rows.cuh"
 
 namespace inpaint {
 
@@ -45,10 +48,9 @@ struct TcCfg {
   static constexpr int TMEM_COLS = 2 * BN;
   static constexpr int COLS_PER_WARP = BN / EW;
   static constexpr int PARAM_FLOATS = 1024 + 2 * BN;       // bias (N <= 1024) and LayerNorm scale/shift
-  static constexpr int STAGE_ROW = 80;                      // bytes per row of a warp's bf16 store tile
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/ +
                                     EPI_WARPS * 32 * 2 * 4 /*LayerNorm partial statistics*/ +
-                                    PARAM_FLOATS * 4 + EPI_WARPS * 32 * STAGE_ROW /*store tiles*/;
+                                    PARAM_FLOATS * 4 + EPI_WARPS * rows::TILE_BYTES /*row staging tiles*/;
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
@@ -70,26 +72,6 @@ __device__ __forceinline__ void load32(const float* __restrict__ p, float (&v)[3
     const float4 t = __ldg(p4 + i);
     v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
   }
-}
-
-__device__ __forceinline__ void store32_bf16(bf16* dst, const float (&f)[32]) {
-  uint4* d4 = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    uint32_t w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(f[8 * i + 2 * j], f[8 * i + 2 * j + 1]);
-      w[j] = *reinterpret_cast<uint32_t*>(&h);
-    }
-    d4[i] = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-__device__ __forceinline__ void store32_f32(float* dst, const float (&f)[32]) {
-  float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) d4[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
 }
 
 __device__ __forceinline__ void named_sync(int id, int count) {
@@ -115,7 +97,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   float* s_bias = ln_stats + EPI_WARPS * 32 * 2;                                     // [1024]
   float* s_lng = s_bias + 1024;                                                      // [BN]
   float* s_lnb = s_lng + BN;                                                         // [BN]
-  uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_lnb + BN);                          // [EPI_WARPS][32][STAGE_ROW]
+  uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_lnb + BN);                          // [EPI_WARPS][2 KB]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, N = args.N;
@@ -222,8 +204,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       __syncwarp();
       tc::fence_after_sync();
       const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-      const int row = m0 + quarter * 32 + lane;
-      const bool live = row < M;
+      const int row0 = m0 + quarter * 32;    // this warp's 32 rows; the thread owns row0 + lane
+      const int nvalid = M - row0;
+      uint8_t* tl = s_tile + (size_t)(warp - 2) * rows::TILE_BYTES;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;  // LayerNorm statistics of this part of the row
 #pragma unroll 1
@@ -243,14 +226,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             load32(args.bias + col, bv);
           }
         }
-        if (resid) {
-          if (live) {
-            load32(args.resid + (size_t)row * args.ldc + col, rv);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) rv[j] = 0.f;
-          }
-        }
+        if (resid) rows::load32_f32(args.resid + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl, lane, rv);
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tbase + c0, r);
         tc::tmem_ld_wait();
@@ -258,7 +234,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (epi == EPI_NONE) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
-          if (live) store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row * args.ldc + col, f);
+          rows::store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl,
+                            lane, f);
           continue;
         }
 #pragma unroll
@@ -268,23 +245,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
             for (int j = 0; j < 32; ++j) f[j] = gelu_as(f[j]);
           }
-          // through the warp's shared tile: each store instruction then covers 8 rows x 64 B
-          uint8_t* tl = s_tile + (size_t)(warp - 2) * 32 * Cfg::STAGE_ROW;
-          __syncwarp();
-          store32_bf16(reinterpret_cast<bf16*>(tl + lane * Cfg::STAGE_ROW), f);
-          __syncwarp();
-          const int row0 = m0 + quarter * 32;
-#pragma unroll
-          for (int sgi = 0; sgi < 4; ++sgi) {
-            const int rr = 8 * sgi + (lane >> 2), ch = lane & 3;
-            const uint4 v = *reinterpret_cast<const uint4*>(tl + rr * Cfg::STAGE_ROW + ch * 16);
-            if (row0 + rr < M)
-              *reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(args.C) + (size_t)(row0 + rr) * args.ldc + col + ch * 8) = v;
-          }
+          rows::store32_bf16(reinterpret_cast<bf16*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl,
+                             lane, f);
         } else {  // residual (+ LayerNorm statistics)
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
-          if (live) store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row * args.ldc + col, f);
+          rows::store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl,
+                            lane, f);
           if (epi == EPI_RESID_LN) {
             float cm = 0.f;
 #pragma unroll
@@ -321,29 +288,23 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         }
         named_sync(1 + quarter, 32 * EW);  // the statistics slots are reused by the next tile
         const float rstd = rsqrtf(m2 / n + 1e-5f);
-        if (live) {
 #pragma unroll 1
-          for (int c0 = c_lo; c0 < c_lo + Cfg::COLS_PER_WARP; c0 += 32) {
-            const int col = n0 + c0;
-            float xv[32], gv[32], bv[32];
-            const float4* xr =
-                reinterpret_cast<const float4*>(reinterpret_cast<const float*>(args.C) + (size_t)row * args.ldc + col);
+        for (int c0 = c_lo; c0 < c_lo + Cfg::COLS_PER_WARP; c0 += 32) {
+          const int col = n0 + c0;
+          float xv[32], gv[32], bv[32];
+          // the rows this warp stored above (the same 32 x 32 blocks)
+          rows::load32_f32(reinterpret_cast<const float*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid,
+                           tl, lane, xv);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 t = xr[j];
-              xv[4 * j] = t.x; xv[4 * j + 1] = t.y; xv[4 * j + 2] = t.z; xv[4 * j + 3] = t.w;
-            }
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              const float4 tg = *reinterpret_cast<const float4*>(s_lng + c0 + j);
-              const float4 tb = *reinterpret_cast<const float4*>(s_lnb + c0 + j);
-              gv[j] = tg.x; gv[j + 1] = tg.y; gv[j + 2] = tg.z; gv[j + 3] = tg.w;
-              bv[j] = tb.x; bv[j + 1] = tb.y; bv[j + 2] = tb.z; bv[j + 3] = tb.w;
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) xv[j] = (xv[j] - mean) * rstd * gv[j] + bv[j];
-            store32_bf16(args.ln_out + (size_t)row * N + col, xv);
+          for (int j = 0; j < 32; j += 4) {
+            const float4 tg = *reinterpret_cast<const float4*>(s_lng + c0 + j);
+            const float4 tb = *reinterpret_cast<const float4*>(s_lnb + c0 + j);
+            gv[j] = tg.x; gv[j + 1] = tg.y; gv[j + 2] = tg.z; gv[j + 3] = tg.w;
+            bv[j] = tb.x; bv[j + 1] = tb.y; bv[j + 2] = tb.z; bv[j + 3] = tb.w;
           }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) xv[j] = (xv[j] - mean) * rstd * gv[j] + bv[j];
+          rows::store32_bf16(args.ln_out + (size_t)row0 * N + col, N, nvalid, tl, lane, xv);
         }
       }
       tc::fence_before_sync();

@@ -19,12 +19,14 @@
 // lane quarter, D/OW columns of a row each: residual, store, LayerNorm; the parts'
 // statistics are merged through shared memory).  OW = 1 measured fastest.  The final epilogue of a tile overlaps the next tile's
 // hidden chunks; it drains the output accumulator before the next tile's MMA2 can start,
-// so each chunk's residual loads are issued before its TMEM load to overlap the two.
+// so each chunk's residual loads overlap its TMEM load, and rows move between global and
+// shared memory in whole 64-byte segments (warp_rows.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
 #include "tc_primitives.cuh"
+#include "warp_rows.cuh"
 
 namespace inpaint {
 
@@ -48,7 +50,7 @@ struct MlpCfg {
   static constexpr int PARAM_FLOATS = 1024 + 3 * D;          // b1 (hid <= 1024), b2, LayerNorm scale/shift
   static constexpr int SMEM_BYTES = A_BYTES + 2 * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
                                     512 /*barriers*/ + OUT_WARPS * 32 * 2 * 4 /*LayerNorm partials*/ +
-                                    PARAM_FLOATS * 4;
+                                    PARAM_FLOATS * 4 + OUT_WARPS * rows::TILE_BYTES /*row staging tiles*/;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 and 384
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
@@ -75,15 +77,6 @@ __device__ __forceinline__ void load32s(const float* p, float (&v)[32]) {  // sh
     v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
   }
 }
-__device__ __forceinline__ void load32(const float* __restrict__ p, float (&v)[32]) {
-  const float4* p4 = reinterpret_cast<const float4*>(p);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float4 t = __ldg(p4 + i);
-    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
-  }
-}
-
 template <int D>
 __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constant__ CUtensorMap tmY,
                                                             const __grid_constant__ CUtensorMap tmW1,
@@ -117,6 +110,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   float* s_b2 = s_b1 + 1024;                     // [D]
   float* s_lng = s_b2 + D;
   float* s_lnb = s_lng + D;
+  uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_lnb + D);  // [OUT_WARPS][2 KB]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, NJ = args.hid / HC;
@@ -317,43 +311,37 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       *abort_flag = 1;
     }
   } else {
-    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; half a row per thread
+    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; D/OW columns of a row per thread
     const int fw = warp - 2 - EPI_WARPS;           // 0 .. OUT_WARPS-1
     const int quarter = warp & 3, half = fw >> 2;
-    const int r = quarter * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     const int c_lo = half * (D / OW);
+    uint8_t* tl = s_tile + (size_t)fw * rows::TILE_BYTES;
     bool ok = true;
     int t = 0;
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
-      const int row = tile * BM + r;
-      const bool live = row < M;
-      float* xr = args.X + (size_t)(live ? row : 0) * D;
-      if (live) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xr + c_lo), "r"(D / OW * 4) : "memory");
+      const int row0 = tile * BM + quarter * 32;  // this warp's 32 rows; the thread owns row0 + lane
+      const int nvalid = M - row0;
+      float* xb = args.X + (size_t)row0 * D;
+      if (lane < nvalid)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xb + (size_t)lane * D + c_lo), "r"(D / OW * 4)
+                     : "memory");
       if (!tc::mbar_wait(o_full, t & 1, abort_flag)) { ok = false; break; }
       __syncwarp();
       tc::fence_after_sync();
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
 #pragma unroll 1
       for (int c0 = c_lo; c0 < c_lo + D / OW; c0 += 32) {
-        float f[32];
-        float4* x4 = reinterpret_cast<float4*>(xr + c0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {  // residual first: its latency overlaps the TMEM load
-          const float4 o = live ? x4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-          f[4 * k] = o.x; f[4 * k + 1] = o.y; f[4 * k + 2] = o.z; f[4 * k + 3] = o.w;
-        }
         uint32_t v[32];
         tc::tmem_ld_32x32b_x32(lane_base + c0, v);
+        float f[32];
+        rows::load32_f32(xb + c0, D, nvalid, tl, lane, f);  // residual, while the TMEM load is in flight
         tc::tmem_ld_wait();
         float bv[32];
         load32s(s_b2 + c0, bv);
 #pragma unroll
         for (int k = 0; k < 32; ++k) f[k] += __uint_as_float(v[k]) + bv[k];
-        if (live) {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) x4[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
-        }
+        rows::store32_f32(xb + c0, D, nvalid, tl, lane, f);
         float cm = 0.f;
 #pragma unroll
         for (int k = 0; k < 32; ++k) cm += f[k];
@@ -370,50 +358,37 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(o_empty);  // OUT drained: the next tile's MMA2 may start
-      // merge the two halves of each row in a fixed order
-      float* st = ln_stats + ((size_t)fw * 32 + lane) * 2;
-      st[0] = run_mean;
-      st[1] = run_m2;
-      named_sync(1 + quarter, 32 * OW);
-      float mean = 0.f, m2 = 0.f, n = 0.f;
+      float mean = run_mean, m2 = run_m2, n = run_n;
+      if (OW > 1) {
+        // merge the parts of each row in a fixed order
+        float* st = ln_stats + ((size_t)fw * 32 + lane) * 2;
+        st[0] = run_mean;
+        st[1] = run_m2;
+        named_sync(1 + quarter, 32 * OW);
+        mean = 0.f; m2 = 0.f; n = 0.f;
 #pragma unroll
-      for (int g2 = 0; g2 < OW; ++g2) {
-        // final warp of half g2 in this quarter: fw = 4*g2 + ((quarter - 2) & 3)
-        const float* o = ln_stats + ((size_t)(4 * g2 + ((quarter - 2) & 3)) * 32 + lane) * 2;
-        const float om = o[0], oq = o[1], on = (float)(D / OW);
-        const float nn = n + on;
-        const float dl = om - mean;
-        mean += dl * (on / nn);
-        m2 += oq + dl * dl * (n * on / nn);
-        n = nn;
+        for (int g2 = 0; g2 < OW; ++g2) {
+          // final warp of part g2 in this quarter: fw = 4*g2 + ((quarter - 2) & 3)
+          const float* o = ln_stats + ((size_t)(4 * g2 + ((quarter - 2) & 3)) * 32 + lane) * 2;
+          const float om = o[0], oq = o[1], on = (float)(D / OW);
+          const float nn = n + on;
+          const float dl = om - mean;
+          mean += dl * (on / nn);
+          m2 += oq + dl * dl * (n * on / nn);
+          n = nn;
+        }
+        named_sync(1 + quarter, 32 * OW);  // the partial slots are reused by the next tile
       }
-      named_sync(1 + quarter, 32 * OW);  // the partial slots are reused by the next tile
-      if (!live) continue;
       const float rstd = rsqrtf(m2 / n + 1e-5f);
 #pragma unroll 1
       for (int c0 = c_lo; c0 < c_lo + D / OW; c0 += 32) {
         float xv[32], gv[32], bv[32];
-        const float4* x4 = reinterpret_cast<const float4*>(xr + c0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float4 o = x4[k];
-          xv[4 * k] = o.x; xv[4 * k + 1] = o.y; xv[4 * k + 2] = o.z; xv[4 * k + 3] = o.w;
-        }
+        rows::load32_f32(xb + c0, D, nvalid, tl, lane, xv);  // the rows this warp stored above
         load32s(s_lng + c0, gv);
         load32s(s_lnb + c0, bv);
-        uint4* dst = reinterpret_cast<uint4*>(args.ln_out + (size_t)row * D + c0);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          uint32_t w[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c = 8 * k + 2 * e;
-            __nv_bfloat162 h2 = __floats2bfloat162_rn((xv[c] - mean) * rstd * gv[c] + bv[c],
-                                                      (xv[c + 1] - mean) * rstd * gv[c + 1] + bv[c + 1]);
-            w[e] = *reinterpret_cast<uint32_t*>(&h2);
-          }
-          dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
-        }
+        for (int k = 0; k < 32; ++k) xv[k] = (xv[k] - mean) * rstd * gv[k] + bv[k];
+        rows::store32_bf16(args.ln_out + (size_t)row0 * D + c0, D, nvalid, tl, lane, xv);
       }
     }
     if (!ok) {

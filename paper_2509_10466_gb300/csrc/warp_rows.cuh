@@ -1,0 +1,99 @@
+// Warp-cooperative row I/O for the tensor-memory epilogues.
+//
+// A tcgen05.ld of shape 32x32b hands lane i the consecutive columns of accumulator row
+// i, so an epilogue thread owns one row.  Storing (or loading) that row directly makes
+// every warp instruction touch 32 different rows, 16 bytes each: 32 L1 wavefronts and
+// half-used sectors per instruction.  These helpers instead pass each 32-row x 32-column
+// block through a 2 KB per-warp shared-memory tile (rows of 64 bytes, 16-byte chunk j of
+// row r at slot j ^ ((r >> 1) & 3), which keeps both the row-wise and the column-wise
+// phases free of bank conflicts), so that each global instruction covers 8 whole rows
+// x 64 bytes.
+//
+// `base` points at element (0, 0) of the block, `ld` is the row pitch in elements and
+// rows >= `nvalid` are neither read (zeros are returned) nor written.  `tile` is the
+// warp's 2 KB, 128-byte-aligned staging area.  All 32 lanes must call.
+#pragma once
+#include "common.cuh"
+
+namespace inpaint {
+namespace rows {
+
+constexpr int TILE_BYTES = 32 * 64;
+
+__device__ __forceinline__ int slot(int r, int j) { return r * 64 + ((j ^ ((r >> 1) & 3)) << 4); }
+
+// v = row `lane` of a 32 x 32 FP32 block.
+__device__ __forceinline__ void load32_f32(const float* base, size_t ld, int nvalid, uint8_t* tile, int lane,
+                                           float (&v)[32]) {
+  const int rr = lane >> 2, ch = lane & 3;
+  float4 g[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {  // all eight loads in flight before the first use
+    const int h = i >> 2, r = 8 * (i & 3) + rr;
+    g[i] = r < nvalid ? *reinterpret_cast<const float4*>(base + (size_t)r * ld + 16 * h + 4 * ch)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // columns 16h .. 16h+15
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) *reinterpret_cast<float4*>(tile + slot(8 * i + rr, ch)) = g[4 * h + i];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 t = *reinterpret_cast<const float4*>(tile + slot(lane, j));
+      v[16 * h + 4 * j] = t.x; v[16 * h + 4 * j + 1] = t.y; v[16 * h + 4 * j + 2] = t.z; v[16 * h + 4 * j + 3] = t.w;
+    }
+  }
+  __syncwarp();
+}
+
+// Row `lane` of a 32 x 32 FP32 block = v.
+__device__ __forceinline__ void store32_f32(float* base, size_t ld, int nvalid, uint8_t* tile, int lane,
+                                            const float (&v)[32]) {
+  const int rr = lane >> 2, ch = lane & 3;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      *reinterpret_cast<float4*>(tile + slot(lane, j)) =
+          make_float4(v[16 * h + 4 * j], v[16 * h + 4 * j + 1], v[16 * h + 4 * j + 2], v[16 * h + 4 * j + 3]);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = 8 * i + rr;
+      const float4 t = *reinterpret_cast<const float4*>(tile + slot(r, ch));
+      if (r < nvalid) *reinterpret_cast<float4*>(base + (size_t)r * ld + 16 * h + 4 * ch) = t;
+    }
+  }
+  __syncwarp();
+}
+
+// Row `lane` of a 32 x 32 bf16 block = v (rounded to nearest even).
+__device__ __forceinline__ void store32_bf16(bf16* base, size_t ld, int nvalid, uint8_t* tile, int lane,
+                                             const float (&v)[32]) {
+  const int rr = lane >> 2, ch = lane & 3;
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
+      w[e] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(tile + slot(lane, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = 8 * i + rr;
+    const uint4 t = *reinterpret_cast<const uint4*>(tile + slot(r, ch));
+    if (r < nvalid) *reinterpret_cast<uint4*>(base + (size_t)r * ld + 8 * ch) = t;
+  }
+  __syncwarp();
+}
+
+}  // namespace rows
+}  // namespace inpaint
