@@ -220,6 +220,11 @@ INPAINT_API void inpaint_destroy(inpaint_ctx* ctx);
 /* Static description of an error code. */
 INPAINT_API const char* inpaint_strerror(int code);
 
+/* The CUDA runtime error (cudaError_t value and its name) behind the last
+ * INPAINT_E_CUDA that a call on this host thread returned; 0 and "cudaSuccess" if none. */
+INPAINT_API int inpaint_last_cuda_error(void);
+INPAINT_API const char* inpaint_cuda_error_name(int cuda_error);
+
 /* --- unit-test hooks for single kernels (used by the test suite) ---------------- */
 
 /* C[M,N] = A[M,K] . B[K,N] on the BF16 tensor-core GEMM (tcgen05, FP32 accumulate).

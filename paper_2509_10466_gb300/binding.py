@@ -26,7 +26,11 @@ PROFILE_NAMES = ("embed", "layernorm", "qkv_gemm", "attention", "proj_gemm", "fc
 class InpaintError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {strerror(code)} (code {code})")
+        detail = ""
+        if code == E_CUDA:
+            ce = load().inpaint_last_cuda_error()
+            detail = f", {load().inpaint_cuda_error_name(ce).decode()}"
+        super().__init__(f"{what}: {strerror(code)} (code {code}{detail})")
 
 
 class InpaintConfig(ctypes.Structure):
@@ -45,6 +49,8 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 _SIGS = {
     "inpaint_strerror": (ctypes.c_char_p, [_I]),
+    "inpaint_last_cuda_error": (_I, []),
+    "inpaint_cuda_error_name": (ctypes.c_char_p, [_I]),
     "inpaint_num_params": (_I, [ctypes.POINTER(InpaintConfig), ctypes.POINTER(ctypes.c_size_t)]),
     "inpaint_init": (_I, [ctypes.POINTER(InpaintConfig), _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "inpaint_set_weights": (_I, [_P, _P, _I, _P]),

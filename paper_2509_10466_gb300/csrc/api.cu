@@ -124,7 +124,13 @@ Plan make_plan(const inpaint_ctx* c, int B, int H, int W) {
   return p;
 }
 
-int cuda_err(cudaError_t e) { return e == cudaSuccess ? INPAINT_OK : INPAINT_E_CUDA; }
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return INPAINT_OK;
+  g_last_cuda_error = e;
+  return INPAINT_E_CUDA;
+}
 
 #define TRY(call)                          \
   do {                                     \
@@ -298,6 +304,10 @@ bool bad_shape(int B, int H, int W) {
 // ------------------------------------------------------------------------- C ABI
 
 extern "C" {
+
+int inpaint_last_cuda_error(void) { return (int)g_last_cuda_error; }
+
+const char* inpaint_cuda_error_name(int cuda_error) { return cudaGetErrorName((cudaError_t)cuda_error); }
 
 const char* inpaint_strerror(int code) {
   switch (code) {

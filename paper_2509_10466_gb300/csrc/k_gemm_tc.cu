@@ -209,24 +209,18 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       uint8_t* tl = s_tile + (size_t)(warp - 2) * rows::TILE_BYTES;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;  // LayerNorm statistics of this part of the row
+      const bool resid = epi == EPI_BIAS_RESID || epi == EPI_RESID_LN;
+      const int c_hi = c_lo + Cfg::COLS_PER_WARP;
+      float4 gn[8];  // residual loads of the next chunk, issued one chunk ahead
+      if (resid) rows::load32_issue(args.resid + (size_t)row0 * args.ldc + n0 + c_lo, args.ldc, nvalid, lane, gn);
 #pragma unroll 1
-      for (int c0 = c_lo; c0 < c_lo + Cfg::COLS_PER_WARP; c0 += 32) {
+      for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
         const int col = n0 + c0;
-        const bool resid = epi == EPI_BIAS_RESID || epi == EPI_RESID_LN;
-        // bias and residual loads first: their latency overlaps the TMEM load
-        float bv[32], rv[32];
-        if (epi != EPI_NONE) {
-          if (bias_smem) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              const float4 t = *reinterpret_cast<const float4*>(s_bias + col + j);
-              bv[j] = t.x; bv[j + 1] = t.y; bv[j + 2] = t.z; bv[j + 3] = t.w;
-            }
-          } else {
-            load32(args.bias + col, bv);
-          }
+        float rv[32];
+        if (resid) {
+          rows::load32_finish(tl, lane, gn, rv);
+          if (c0 + 32 < c_hi) rows::load32_issue(args.resid + (size_t)row0 * args.ldc + col + 32, args.ldc, nvalid, lane, gn);
         }
-        if (resid) rows::load32_f32(args.resid + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl, lane, rv);
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tbase + c0, r);
         tc::tmem_ld_wait();
@@ -238,8 +232,21 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                             lane, f);
           continue;
         }
+        if (bias_smem) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]) + bv[j];
+          for (int j = 0; j < 32; j += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(s_bias + col + j);
+            f[j] = __uint_as_float(r[j]) + t.x;
+            f[j + 1] = __uint_as_float(r[j + 1]) + t.y;
+            f[j + 2] = __uint_as_float(r[j + 2]) + t.z;
+            f[j + 3] = __uint_as_float(r[j + 3]) + t.w;
+          }
+        } else {
+          float bv[32];
+          load32(args.bias + col, bv);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]) + bv[j];
+        }
         if (epi == EPI_BIAS || epi == EPI_BIAS_GELU) {
           if (epi == EPI_BIAS_GELU) {
 #pragma unroll
@@ -288,22 +295,24 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         }
         named_sync(1 + quarter, 32 * EW);  // the statistics slots are reused by the next tile
         const float rstd = rsqrtf(m2 / n + 1e-5f);
+        const float* xs = reinterpret_cast<const float*>(args.C) + (size_t)row0 * args.ldc + n0;
+        rows::load32_issue(xs + c_lo, args.ldc, nvalid, lane, gn);
 #pragma unroll 1
-        for (int c0 = c_lo; c0 < c_lo + Cfg::COLS_PER_WARP; c0 += 32) {
+        for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
           const int col = n0 + c0;
-          float xv[32], gv[32], bv[32];
+          float xv[32];
           // the rows this warp stored above (the same 32 x 32 blocks)
-          rows::load32_f32(reinterpret_cast<const float*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid,
-                           tl, lane, xv);
+          rows::load32_finish(tl, lane, gn, xv);
+          if (c0 + 32 < c_hi) rows::load32_issue(xs + c0 + 32, args.ldc, nvalid, lane, gn);
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
             const float4 tg = *reinterpret_cast<const float4*>(s_lng + c0 + j);
             const float4 tb = *reinterpret_cast<const float4*>(s_lnb + c0 + j);
-            gv[j] = tg.x; gv[j + 1] = tg.y; gv[j + 2] = tg.z; gv[j + 3] = tg.w;
-            bv[j] = tb.x; bv[j + 1] = tb.y; bv[j + 2] = tb.z; bv[j + 3] = tb.w;
+            xv[j] = (xv[j] - mean) * rstd * tg.x + tb.x;
+            xv[j + 1] = (xv[j + 1] - mean) * rstd * tg.y + tb.y;
+            xv[j + 2] = (xv[j + 2] - mean) * rstd * tg.z + tb.z;
+            xv[j + 3] = (xv[j + 3] - mean) * rstd * tg.w + tb.w;
           }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) xv[j] = (xv[j] - mean) * rstd * gv[j] + bv[j];
           rows::store32_bf16(args.ln_out + (size_t)row0 * N + col, N, nvalid, tl, lane, xv);
         }
       }

@@ -14,7 +14,8 @@
 // + two H buffers (128 cols each).  The bf16 H_j is written in the 128-byte-swizzled
 // K-major layout that the MMA descriptor expects (16-byte chunk c of row r at c ^ (r%8)).
 //
-// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2..9 hidden-chunk epilogue (two per
+// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer (2, 3 idle: warpgroup 0 hands its
+// registers to the final warps), 4..11 hidden-chunk epilogue (two per
 // TMEM lane quarter, splitting the chunk's columns), then 4*OW final-epilogue warps (OW per
 // lane quarter, D/OW columns of a row each: residual, store, LayerNorm; the parts'
 // statistics are merged through shared memory).  OW = 1 measured fastest.  The final epilogue of a tile overlaps the next tile's
@@ -33,9 +34,17 @@ namespace inpaint {
 namespace {
 
 constexpr int BM = 128, BK = 64, HC = 128;   // rows per tile, k-block, hidden chunk
+constexpr int ROLE_WARPS = 4;                 // warpgroup 0: TMA producer, MMA issuer, two idle
 constexpr int EW = 2, EPI_WARPS = 4 * EW;     // GELU warps: two per TMEM lane quarter
 constexpr int OW = 1, OUT_WARPS = 4 * OW;     // final-epilogue warps per lane quarter
-constexpr int THREADS = 64 + 32 * (EPI_WARPS + OUT_WARPS);
+constexpr int THREADS = 32 * (ROLE_WARPS + EPI_WARPS + OUT_WARPS);
+// Registers per thread: launched with 65536 / THREADS; warpgroup 0 gives most of its share
+// to the final-epilogue warpgroup, which keeps two chunks of residual loads in flight.
+constexpr int REG_LAUNCH = 65536 / THREADS, REG_ROLE = 64, REG_FINAL = 184;
+static_assert(OUT_WARPS == 4 && ROLE_WARPS == 4, "register reallocation is per warpgroup");
+static_assert(ROLE_WARPS * REG_ROLE + EPI_WARPS * REG_LAUNCH + OUT_WARPS * REG_FINAL <=
+                  (ROLE_WARPS + EPI_WARPS + OUT_WARPS) * REG_LAUNCH,
+              "register reallocation exceeds the launch allotment");
 constexpr int RING = 5;                      // 16 KB weight stages
 
 template <int D>
@@ -77,7 +86,7 @@ __device__ __forceinline__ void load32s(const float* p, float (&v)[32]) {  // sh
     v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
   }
 }
-template <int D>
+template <int D, int CS>
 __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constant__ CUtensorMap tmY,
                                                             const __grid_constant__ CUtensorMap tmW1,
                                                             const __grid_constant__ CUtensorMap tmW2,
@@ -116,9 +125,17 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   const int M = args.M, NJ = args.hid / HC;
   const int tiles = (M + BM - 1) / BM;
   int* err = args.err;
+  // A cluster of CS CTAs walks groups of CS consecutive tiles in lockstep (every tile
+  // consumes the same weight sequence); CTA `rank` takes tile grp*CS + rank, which may lie
+  // past the last tile: it then computes on zero rows and stores nothing.
+  const int rank = CS > 1 ? (int)tc::cluster_ctarank() : 0;
+  const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+  const int groups = (tiles + CS - 1) / CS;
+  constexpr uint16_t MASK = (uint16_t)((1u << CS) - 1);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < RING; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    // a ring slot is refilled (in every CTA of the cluster) once all CS consumers released it
+    for (int s = 0; s < RING; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], CS); }
     tc::mbar_init(a_full, 1);
     tc::mbar_init(a_empty, 1);
     for (int b = 0; b < 2; ++b) {
@@ -148,38 +165,55 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (CS > 1) tc::cluster_sync();  // every CTA's barriers exist before any multicast reaches them
   tc::fence_after_sync();
   const uint32_t tmem_base = *tmem_slot;
 
+  if (warp < ROLE_WARPS) {
+  tc::setmaxnreg_dec<REG_ROLE>();
   if (warp == 0) {
     if (lane == 0) {
       uint32_t g = 0;  // ring slot counter
       bool ok = true;
-      auto push = [&](const CUtensorMap* map, int c0, int c1, uint32_t bytes) {
+      // each CTA loads 1/CS of every weight stage (rows rank*slice ..) and multicasts it
+      // to the whole cluster; the stage's barrier expects the full stage
+      auto push = [&](const CUtensorMap* map, int c0, int c1, uint32_t bytes, int slice_rows) {
         const int s = g % RING;
         if (g >= (uint32_t)RING && !tc::mbar_wait(&empty[s], ((g / RING) & 1) ^ 1, abort_flag)) return false;
         tc::mbar_expect_tx(&full[s], bytes);
-        tc::tma_load_2d(sR + s * Cfg::STAGE_BYTES, map, &full[s], c0, c1);
+        uint8_t* dst = sR + s * Cfg::STAGE_BYTES + rank * slice_rows * 128;
+        if (CS > 1)
+          tc::tma_load_2d_mc(dst, map, &full[s], c0, c1 + rank * slice_rows, MASK);
+        else
+          tc::tma_load_2d(dst, map, &full[s], c0, c1);
         ++g;
         return true;
       };
       int t = 0;
-      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
-        const int m0 = tile * BM;
+      for (int grp = cid; grp < groups && ok; grp += ncl, ++t) {
+        const int m0 = (grp * CS + rank) * BM;
         if (t >= 1 && !tc::mbar_wait(a_empty, (t - 1) & 1, abort_flag)) { ok = false; break; }
-        tc::mbar_expect_tx(a_full, Cfg::A_BYTES);
-        for (int kb = 0; kb < KA; ++kb) tc::tma_load_2d(sA + kb * (BM * BK * 2), &tmY, a_full, kb * BK, m0);
+        if (m0 < M) {
+          tc::mbar_expect_tx(a_full, Cfg::A_BYTES);
+          for (int kb = 0; kb < KA; ++kb) tc::tma_load_2d(sA + kb * (BM * BK * 2), &tmY, a_full, kb * BK, m0);
+        } else {
+          tc::mbar_arrive(a_full);  // a tile past the end: its results are never stored
+        }
         for (int j = 0; j <= NJ && ok; ++j) {
           if (j < NJ)
-            for (int kb = 0; kb < KA && ok; ++kb) ok = push(&tmW1, kb * BK, j * HC, Cfg::W1_BYTES);
+            for (int kb = 0; kb < KA && ok; ++kb) ok = push(&tmW1, kb * BK, j * HC, Cfg::W1_BYTES, HC / CS);
           if (j >= 1)
             for (int kb = 0; kb < KH && ok; ++kb)
               for (int hf = 0; hf < Cfg::NHALF && ok; ++hf)
-                ok = push(&tmW2, (j - 1) * HC + kb * BK, hf * Cfg::HR, Cfg::W2_BYTES);
+                ok = push(&tmW2, (j - 1) * HC + kb * BK, hf * Cfg::HR, Cfg::W2_BYTES, Cfg::HR / CS);
         }
       }
       for (uint32_t h = (g > (uint32_t)RING ? g - RING : 0); h < g; ++h)
         if (!tc::mbar_wait_timed(&full[h % RING], (h / RING) & 1)) break;
+      // and the other CTAs' releases of the last stages, which arrive on this CTA's barriers
+      if (CS > 1)
+        for (uint32_t h = (g > (uint32_t)RING ? g - RING : 0); h < g; ++h)
+          if (!tc::mbar_wait_timed(&empty[h % RING], (h / RING) & 1)) break;
       if (!ok) {
         if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
         *abort_flag = 1;
@@ -192,6 +226,12 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       constexpr uint32_t id2 = tc::idesc_bf16_f32(BM, Cfg::HR);
       uint32_t g = 0, q = 0;  // ring slot counter, hidden-chunk counter (across tiles)
       bool ok = true;
+      auto release = [&](int s) {  // the stage's MMAs are done: free it in every CTA of the cluster
+        if (CS > 1)
+          tc::mma_commit_mc(&empty[s], MASK);
+        else
+          tc::mma_commit(&empty[s]);
+      };
       auto pop = [&](int& s) {
         s = g % RING;
         if (!tc::mbar_wait(&full[s], (g / RING) & 1, abort_flag)) return false;
@@ -211,7 +251,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16(dt, ad + 2 * kk, bd + 2 * kk, id1, (kb | kk) != 0);
-          tc::mma_commit(&empty[s]);
+          release(s);
         }
         tc::mma_commit(&h_full[hb]);
         return true;
@@ -230,7 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
               tc::mma_f16(tmem_base + hf * Cfg::HR, ad + 2 * kk, bd + 2 * kk, id2, (!first || kb || kk) ? 1u : 0u);
-            tc::mma_commit(&empty[s]);
+            release(s);
           }
         }
         tc::mma_commit(&hs_empty[hb]);
@@ -238,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         return true;
       };
       int t = 0;
-      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+      for (int grp = cid; grp < groups && ok; grp += ncl, ++t) {
         if (!tc::mbar_wait(a_full, t & 1, abort_flag)) { ok = false; break; }
         tc::fence_after_sync();
         const uint32_t q0 = q;
@@ -259,14 +299,15 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       tc::mbar_wait_timed(teardown, 0);
     }
     __syncwarp();
-  } else if (warp < 2 + EPI_WARPS) {
+  }
+  } else if (warp < ROLE_WARPS + EPI_WARPS) {
     // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 swizzled SMEM operand of MMA2
-    const int quarter = warp & 3, cg = (warp - 2) >> 2;
+    const int quarter = warp & 3, cg = (warp - ROLE_WARPS) >> 2;
     const int r = quarter * 32 + lane;  // row within the tile (= TMEM lane)
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     uint32_t q = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    for (int grp = cid; grp < groups && ok; grp += ncl) {
       for (int j = 0; j < NJ; ++j, ++q) {
         const uint32_t hb = q & 1, use = q >> 1;
         if (!tc::mbar_wait(&h_full[hb], use & 1, abort_flag)) { ok = false; break; }
@@ -312,15 +353,16 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     }
   } else {
     // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; D/OW columns of a row per thread
-    const int fw = warp - 2 - EPI_WARPS;           // 0 .. OUT_WARPS-1
+    tc::setmaxnreg_inc<REG_FINAL>();
+    const int fw = warp - ROLE_WARPS - EPI_WARPS;  // 0 .. OUT_WARPS-1
     const int quarter = warp & 3, half = fw >> 2;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     const int c_lo = half * (D / OW);
     uint8_t* tl = s_tile + (size_t)fw * rows::TILE_BYTES;
     bool ok = true;
     int t = 0;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
-      const int row0 = tile * BM + quarter * 32;  // this warp's 32 rows; the thread owns row0 + lane
+    for (int grp = cid; grp < groups && ok; grp += ncl, ++t) {
+      const int row0 = (grp * CS + rank) * BM + quarter * 32;  // this warp's 32 rows; the thread owns row0 + lane
       const int nvalid = M - row0;
       float* xb = args.X + (size_t)row0 * D;
       if (lane < nvalid)
@@ -330,17 +372,25 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       __syncwarp();
       tc::fence_after_sync();
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
+      constexpr int c_hi = D / OW;  // (c_lo = 0 when OW = 1)
+      float4 gn[8];                 // the next chunk's residual, loaded one chunk ahead
+      rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
 #pragma unroll 1
-      for (int c0 = c_lo; c0 < c_lo + D / OW; c0 += 32) {
+      for (int c0 = c_lo; c0 < c_lo + c_hi; c0 += 32) {
         uint32_t v[32];
         tc::tmem_ld_32x32b_x32(lane_base + c0, v);
         float f[32];
-        rows::load32_f32(xb + c0, D, nvalid, tl, lane, f);  // residual, while the TMEM load is in flight
+        rows::load32_finish(tl, lane, gn, f);
+        if (c0 + 32 < c_lo + c_hi) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
         tc::tmem_ld_wait();
-        float bv[32];
-        load32s(s_b2 + c0, bv);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) f[k] += __uint_as_float(v[k]) + bv[k];
+        for (int k = 0; k < 32; k += 4) {
+          const float4 b = *reinterpret_cast<const float4*>(s_b2 + c0 + k);
+          f[k] += __uint_as_float(v[k]) + b.x;
+          f[k + 1] += __uint_as_float(v[k + 1]) + b.y;
+          f[k + 2] += __uint_as_float(v[k + 2]) + b.z;
+          f[k + 3] += __uint_as_float(v[k + 3]) + b.w;
+        }
         rows::store32_f32(xb + c0, D, nvalid, tl, lane, f);
         float cm = 0.f;
 #pragma unroll
@@ -380,14 +430,21 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         named_sync(1 + quarter, 32 * OW);  // the partial slots are reused by the next tile
       }
       const float rstd = rsqrtf(m2 / n + 1e-5f);
+      rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
 #pragma unroll 1
-      for (int c0 = c_lo; c0 < c_lo + D / OW; c0 += 32) {
-        float xv[32], gv[32], bv[32];
-        rows::load32_f32(xb + c0, D, nvalid, tl, lane, xv);  // the rows this warp stored above
-        load32s(s_lng + c0, gv);
-        load32s(s_lnb + c0, bv);
+      for (int c0 = c_lo; c0 < c_lo + c_hi; c0 += 32) {
+        float xv[32];
+        rows::load32_finish(tl, lane, gn, xv);  // the rows this warp stored above
+        if (c0 + 32 < c_lo + c_hi) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) xv[k] = (xv[k] - mean) * rstd * gv[k] + bv[k];
+        for (int k = 0; k < 32; k += 4) {
+          const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
+          const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
+          xv[k] = (xv[k] - mean) * rstd * g4.x + b4.x;
+          xv[k + 1] = (xv[k + 1] - mean) * rstd * g4.y + b4.y;
+          xv[k + 2] = (xv[k + 2] - mean) * rstd * g4.z + b4.z;
+          xv[k + 3] = (xv[k + 3] - mean) * rstd * g4.w + b4.w;
+        }
         rows::store32_bf16(args.ln_out + (size_t)row0 * D + c0, D, nvalid, tl, lane, xv);
       }
     }
@@ -399,6 +456,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
 
   tc::fence_before_sync();
   __syncthreads();
+  if (CS > 1) tc::cluster_sync();  // no CTA leaves while another may still signal it
   if (warp == 1) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem_base, 512);
@@ -440,23 +498,48 @@ int num_sms() {
   return n;
 }
 
-template <int D>
-cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
+template <int D, int CS>
+cudaError_t launch_dc(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
   using Cfg = MlpCfg<D>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
+  auto kern = mlp_tc_kernel<D, CS>;
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.blockDim = dim3(THREADS);
+  lc.dynamicSmemBytes = Cfg::SMEM_BYTES;
+  lc.stream = st;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  static int max_clusters = 0;  // co-resident clusters of CS CTAs at one CTA per SM
+  if (!max_clusters) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr = true;
+    lc.gridDim = dim3(num_sms() / CS * CS);
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &lc);
+    if (e != cudaSuccess) return e;
+    max_clusters = n > 0 ? n : 1;
   }
   CUtensorMap my, m1, m2;
   if (!map2d(&my, Y, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
-  if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC)) return cudaErrorInvalidValue;
-  if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, Cfg::HR)) return cudaErrorInvalidValue;
-  const int tiles = (a.M + BM - 1) / BM;
-  const int grid = tiles < num_sms() ? tiles : num_sms();
-  mlp_tc_kernel<D><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(my, m1, m2, a);
-  return cudaGetLastError();
+  if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC / CS)) return cudaErrorInvalidValue;
+  if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, Cfg::HR / CS)) return cudaErrorInvalidValue;
+  const int groups = ((a.M + BM - 1) / BM + CS - 1) / CS;
+  lc.gridDim = dim3((groups < max_clusters ? groups : max_clusters) * CS);
+  cudaError_t e = cudaLaunchKernelEx(&lc, kern, my, m1, m2, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Weight stages are shared by clusters of two CTAs: half the L2 reads of the weights per
+// tile, which all CTAs otherwise stream from the same lines at the same time.
+constexpr int MLP_CLUSTER = 2;
+
+template <int D>
+cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
+  return launch_dc<D, MLP_CLUSTER>(Y, W1t, W2t, a, st);
 }
 
 }  // namespace

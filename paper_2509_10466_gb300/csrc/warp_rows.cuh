@@ -22,17 +22,21 @@ constexpr int TILE_BYTES = 32 * 64;
 
 __device__ __forceinline__ int slot(int r, int j) { return r * 64 + ((j ^ ((r >> 1) & 3)) << 4); }
 
-// v = row `lane` of a 32 x 32 FP32 block.
-__device__ __forceinline__ void load32_f32(const float* base, size_t ld, int nvalid, uint8_t* tile, int lane,
-                                           float (&v)[32]) {
+// Two halves of load32_f32, so that the next block's loads can be in flight while the
+// current one is processed: issue the coalesced global loads into g ...
+__device__ __forceinline__ void load32_issue(const float* base, size_t ld, int nvalid, int lane, float4 (&g)[8]) {
   const int rr = lane >> 2, ch = lane & 3;
-  float4 g[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {  // all eight loads in flight before the first use
+  for (int i = 0; i < 8; ++i) {
     const int h = i >> 2, r = 8 * (i & 3) + rr;
     g[i] = r < nvalid ? *reinterpret_cast<const float4*>(base + (size_t)r * ld + 16 * h + 4 * ch)
                       : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+}
+
+// ... then transpose them through the tile into row `lane`.
+__device__ __forceinline__ void load32_finish(uint8_t* tile, int lane, const float4 (&g)[8], float (&v)[32]) {
+  const int rr = lane >> 2, ch = lane & 3;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {  // columns 16h .. 16h+15
     __syncwarp();
@@ -46,6 +50,14 @@ __device__ __forceinline__ void load32_f32(const float* base, size_t ld, int nva
     }
   }
   __syncwarp();
+}
+
+// v = row `lane` of a 32 x 32 FP32 block.
+__device__ __forceinline__ void load32_f32(const float* base, size_t ld, int nvalid, uint8_t* tile, int lane,
+                                           float (&v)[32]) {
+  float4 g[8];
+  load32_issue(base, ld, nvalid, lane, g);
+  load32_finish(tile, lane, g, v);
 }
 
 // Row `lane` of a 32 x 32 FP32 block = v.

@@ -99,6 +99,16 @@ def test_bf16_d256_decoder_on_tensor_cores(H, W, B):
     check_parity(cfg, weights, x, hole, TOL_BF16)
 
 
+@pytest.mark.parametrize("dim,ratio,H,W", [(64, 4, 96, 96), (128, 4, 64, 224), (256, 2, 96, 352), (128, 8, 32, 32)])
+def test_bf16_fused_mlp_odd_tile_counts(dim, ratio, H, W):
+    """The fused MLP runs in CTA pairs that share weight stages: odd and partial row-tile
+    counts leave one CTA of the last pair on a tile past the end (5, 7, 17 and 1 tiles)."""
+    cfg = ModelConfig(dim=dim, heads=dim // 32, window=8, blocks=2, mlp_ratio=ratio, precision=BF16)
+    weights = S.make_weights(cfg, seed=dim + ratio, perturb=True)
+    x, hole = inputs(1, H, W, "polygons", seed=H + W + dim)
+    check_parity(cfg, weights, x, hole, TOL_BF16)
+
+
 def test_bf16_precision_workload_512_full_size():
     """Precision workload at full size: 4 frames of 512x512, d256 h8, 8 blocks, MLP ratio 4."""
     w = WORKLOAD_B
