@@ -1,27 +1,33 @@
 // Fused MLP of a transformer block on tcgen05 (BF16 form):
-//   for a tile of 128 token rows and hidden chunks j of 128 columns
+//   for a tile of token rows and hidden chunks j of 128 columns
 //     H_j  = gelu(Y . W1[:, j] + b1[j])            (MMA1 into TMEM, epilogue to SMEM)
 //     OUT += H_j . W2[j, :]                         (MMA2 from SMEM into TMEM)
 //   x = x + OUT + b2, ln_out = LayerNorm(x) (the next block's LN1, or the final LN).
 // The hidden activations never leave the SM: this removes the write and re-read of the
-// [M, r*d] hidden tensor and keeps the MLP bound by the tensor pipe, not HBM.
+// [M, r*d] hidden tensor.
+//
+// CTA pairs (clusters of two SMs) run 2-SM MMAs (cta_group::2) over 256-row tiles: each
+// CTA holds its own 128 rows of Y and of H_j and half of every weight block, the even
+// CTA issues the MMAs for both, and each CTA's TMEM receives the accumulator rows of its
+// own 128 rows.  Per SM this halves the weight bytes that stream from L2 for the same
+// tensor work, which is what bounds a 128-row tile.
 //
 // Y (LN2 output, bf16 [M, D]) is loaded once per tile by TMA and stays in SMEM; W1^T
-// ([hid][D]) k-blocks and W2^T ([D][hid]) k-blocks (as <=128-row halves, one MMA2 per
-// half of OUT's columns) stream through a 5-stage ring of 16 KB in the order the MMA
-// warp consumes them (MMA1 of chunk j+1 is issued before MMA2 of chunk j, so the tensor
-// core works while the epilogue warps turn H_j into bf16).  TMEM: OUT (D cols)
-// + two H buffers (128 cols each).  The bf16 H_j is written in the 128-byte-swizzled
-// K-major layout that the MMA descriptor expects (16-byte chunk c of row r at c ^ (r%8)).
+// ([hid][D]) and W2^T ([D][hid]) k-blocks stream through a ring of 16 KB stages in the
+// order the MMA warp consumes them (MMA1 of chunk j+1 is issued before MMA2 of chunk j,
+// so the tensor core works while the epilogue warps turn H_j into bf16).  TMEM: OUT
+// (D cols) + two H buffers (128 cols each).  The bf16 H_j is written in the
+// 128-byte-swizzled K-major layout that the MMA descriptor expects (16-byte chunk c of
+// row r at c ^ (r%8)).  Barriers that the MMA warp waits on live in the even CTA and
+// count both CTAs' arrivals and TMA bytes; MMA completions are signalled to both CTAs.
 //
-// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer (2, 3 idle: warpgroup 0 hands its
-// registers to the final warps), 4..11 hidden-chunk epilogue (two per
-// TMEM lane quarter, splitting the chunk's columns), then 4*OW final-epilogue warps (OW per
-// lane quarter, D/OW columns of a row each: residual, store, LayerNorm; the parts'
-// statistics are merged through shared memory).  OW = 1 measured fastest.  The final epilogue of a tile overlaps the next tile's
-// hidden chunks; it drains the output accumulator before the next tile's MMA2 can start,
-// so each chunk's residual loads overlap its TMEM load, and rows move between global and
-// shared memory in whole 64-byte segments (warp_rows.cuh).
+// Warps: 0 TMA producer, 1 TMEM owner + MMA issuer (even CTA only; 2, 3 idle:
+// warpgroup 0 hands its registers to the final warps), 4..11 hidden-chunk epilogue (two
+// per TMEM lane quarter, splitting the chunk's columns), 12..15 final epilogue (one per
+// lane quarter, whole rows: residual, store, LayerNorm).  The final epilogue of a tile
+// overlaps the next tile's hidden chunks; it drains the output accumulator before the
+// next tile's MMA2 can start, so residual loads run one chunk ahead, and rows move
+// between global and shared memory in whole 64-byte segments (warp_rows.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -33,34 +39,38 @@ namespace inpaint {
 
 namespace {
 
-constexpr int BM = 128, BK = 64, HC = 128;   // rows per tile, k-block, hidden chunk
+constexpr int BM = 128, BK = 64, HC = 128;   // rows per CTA, k-block, hidden chunk
+constexpr int NB = 2;                         // H buffers (TMEM and SMEM)
+constexpr int LOOK = NB - 1;                  // MMA1 runs this many chunks ahead of MMA2
 constexpr int ROLE_WARPS = 4;                 // warpgroup 0: TMA producer, MMA issuer, two idle
-constexpr int EW = 2, EPI_WARPS = 4 * EW;     // GELU warps: two per TMEM lane quarter
-constexpr int OW = 1, OUT_WARPS = 4 * OW;     // final-epilogue warps per lane quarter
+constexpr int EPI_WARPS = 8;                  // GELU warps: two per TMEM lane quarter
+constexpr int OUT_WARPS = 4;                  // final-epilogue warps: one per lane quarter
 constexpr int THREADS = 32 * (ROLE_WARPS + EPI_WARPS + OUT_WARPS);
+constexpr int RING = 5;                       // 16 KB weight stages
+constexpr uint16_t PAIR = 0x3;                // both CTAs of the cluster
 // Registers per thread: launched with 65536 / THREADS; warpgroup 0 gives most of its share
-// to the final-epilogue warpgroup, which keeps two chunks of residual loads in flight.
+// to the final-epilogue warpgroup.
 constexpr int REG_LAUNCH = 65536 / THREADS, REG_ROLE = 64, REG_FINAL = 184;
-static_assert(OUT_WARPS == 4 && ROLE_WARPS == 4, "register reallocation is per warpgroup");
 static_assert(ROLE_WARPS * REG_ROLE + EPI_WARPS * REG_LAUNCH + OUT_WARPS * REG_FINAL <=
                   (ROLE_WARPS + EPI_WARPS + OUT_WARPS) * REG_LAUNCH,
               "register reallocation exceeds the launch allotment");
-constexpr int RING = 5;                      // 16 KB weight stages
 
 template <int D>
 struct MlpCfg {
-  static constexpr int A_BYTES = BM * D * 2;                  // Y tile, D/64 atoms of 16 KB
-  static constexpr int HS_BYTES = BM * HC * 2;                // one bf16 H chunk, 2 atoms
-  static constexpr int W1_BYTES = HC * BK * 2;                // one W1 k-block (HC rows)
-  static constexpr int HR = D < 128 ? D : 128;                // W2 rows per load (N of MMA2)
-  static constexpr int NHALF = D / HR;                        // W2 k-block = NHALF loads
-  static constexpr int W2_BYTES = HR * BK * 2;
+  static constexpr int A_BYTES = BM * D * 2;                  // this CTA's Y rows, D/64 atoms of 16 KB
+  static constexpr int HS_BYTES = BM * HC * 2;                // one bf16 H chunk, HC/64 atoms of 16 KB
+  static constexpr int KA = D / BK;                           // k-blocks of MMA1
+  static constexpr int KH = HC / BK;                          // k-blocks of MMA2 per chunk
   static constexpr int STAGE_BYTES = 16384;
+  static constexpr int W1_BOX = (HC / 2) * BK * 2;            // this CTA's half of a W1 k-block (HC/2 rows)
+  static constexpr int W1_KB = KA < STAGE_BYTES / W1_BOX ? KA : STAGE_BYTES / W1_BOX;  // k-blocks per stage
+  static constexpr int W1_STAGES = KA / W1_KB;                // W1 stages per chunk
+  static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a W2 k-block (D/2 rows)
   static constexpr int PARAM_FLOATS = 1024 + 3 * D;          // b1 (hid <= 1024), b2, LayerNorm scale/shift
-  static constexpr int SMEM_BYTES = A_BYTES + 2 * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
-                                    512 /*barriers*/ + OUT_WARPS * 32 * 2 * 4 /*LayerNorm partials*/ +
-                                    PARAM_FLOATS * 4 + OUT_WARPS * rows::TILE_BYTES /*row staging tiles*/;
-  static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 and 384
+  static constexpr int SMEM_BYTES = A_BYTES + NB * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
+                                    512 /*barriers*/ + PARAM_FLOATS * 4 + OUT_WARPS * rows::TILE_BYTES;
+  static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 + HC b
+  static_assert(W1_KB * W1_BOX <= STAGE_BYTES && W2_BOX <= STAGE_BYTES, "stage too small");
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
@@ -76,9 +86,6 @@ struct MlpArgs {
 };
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void named_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
 __device__ __forceinline__ void load32s(const float* p, float (&v)[32]) {  // shared memory
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -86,37 +93,34 @@ __device__ __forceinline__ void load32s(const float* p, float (&v)[32]) {  // sh
     v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
   }
 }
-template <int D, int CS>
+
+template <int D>
 __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constant__ CUtensorMap tmY,
                                                             const __grid_constant__ CUtensorMap tmW1,
                                                             const __grid_constant__ CUtensorMap tmW2,
                                                             const MlpArgs args) {
   using Cfg = MlpCfg<D>;
-  constexpr int KA = D / BK;   // k-blocks of MMA1 (and atoms of the Y tile)
-  constexpr int KH = HC / BK;  // k-blocks of MMA2 per hidden chunk
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sH = sA + Cfg::A_BYTES;                      // 2 buffers
-  uint8_t* sR = sH + 2 * Cfg::HS_BYTES;                 // ring
+  uint8_t* sH = sA + Cfg::A_BYTES;                      // NB buffers
+  uint8_t* sR = sH + NB * Cfg::HS_BYTES;                // ring
   uint64_t* bar = reinterpret_cast<uint64_t*>(sR + RING * Cfg::STAGE_BYTES);
-  static_assert(Cfg::W1_BYTES <= Cfg::STAGE_BYTES && Cfg::W2_BYTES <= Cfg::STAGE_BYTES, "stage too small");
-  uint64_t* full = bar;                 // [RING]
-  uint64_t* empty = full + RING;        // [RING]
-  uint64_t* a_full = empty + RING;
-  uint64_t* a_empty = a_full + 1;
-  uint64_t* h_full = a_empty + 1;       // [2]
-  uint64_t* h_empty = h_full + 2;       // [2]
-  uint64_t* hs_full = h_empty + 2;      // [2]
-  uint64_t* hs_empty = hs_full + 2;     // [2]
-  uint64_t* o_full = hs_empty + 2;
-  uint64_t* o_empty = o_full + 1;
+  uint64_t* full = bar;                 // [RING]  even CTA: both CTAs' weight bytes
+  uint64_t* empty = full + RING;        // [RING]  both: stage consumed by the pair's MMAs
+  uint64_t* a_full = empty + RING;      //         even CTA: both CTAs' Y bytes
+  uint64_t* a_empty = a_full + 1;       //         both: Y no longer read
+  uint64_t* h_full = a_empty + 1;       // [NB]    both: H_j in TMEM
+  uint64_t* h_empty = h_full + NB;      // [NB]    even CTA: both CTAs read H_j from TMEM
+  uint64_t* hs_full = h_empty + NB;     // [NB]    even CTA: both CTAs wrote bf16 H_j
+  uint64_t* hs_empty = hs_full + NB;    // [NB]    both: MMA2 read H_j from SMEM
+  uint64_t* o_full = hs_empty + NB;     //         both: OUT complete
+  uint64_t* o_empty = o_full + 1;       //         even CTA: both CTAs drained OUT
   uint64_t* teardown = o_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* ln_stats = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [OUT_WARPS][32][2]
-  float* s_b1 = ln_stats + OUT_WARPS * 32 * 2;   // [hid]
-  float* s_b2 = s_b1 + 1024;                     // [D]
+  float* s_b1 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [hid]
+  float* s_b2 = s_b1 + 1024;                                                      // [D]
   float* s_lng = s_b2 + D;
   float* s_lnb = s_lng + D;
   uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_lnb + D);  // [OUT_WARPS][2 KB]
@@ -125,27 +129,26 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   const int M = args.M, NJ = args.hid / HC;
   const int tiles = (M + BM - 1) / BM;
   int* err = args.err;
-  // A cluster of CS CTAs walks groups of CS consecutive tiles in lockstep (every tile
-  // consumes the same weight sequence); CTA `rank` takes tile grp*CS + rank, which may lie
-  // past the last tile: it then computes on zero rows and stores nothing.
-  const int rank = CS > 1 ? (int)tc::cluster_ctarank() : 0;
-  const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
-  const int groups = (tiles + CS - 1) / CS;
-  constexpr uint16_t MASK = (uint16_t)((1u << CS) - 1);
+  // Pair p covers tiles 2p (even CTA) and 2p+1 (odd CTA); the odd tile may lie past the
+  // last one, the odd CTA then loads no Y rows and stores nothing.
+  const int rank = (int)tc::cluster_ctarank();
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int pairs = (tiles + 1) >> 1;
+  // the even CTA's copy of a barrier (shared::cluster address): the pair's arrivals go there
+  auto lead = [](const void* p) { return tc::mapa_shared(tc::smem_u32(p), 0); };
 
   if (threadIdx.x == 0) {
-    // a ring slot is refilled (in every CTA of the cluster) once all CS consumers released it
-    for (int s = 0; s < RING; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], CS); }
+    for (int s = 0; s < RING; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
     tc::mbar_init(a_full, 1);
     tc::mbar_init(a_empty, 1);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       tc::mbar_init(&h_full[b], 1);
-      tc::mbar_init(&h_empty[b], EPI_WARPS);
-      tc::mbar_init(&hs_full[b], EPI_WARPS);
+      tc::mbar_init(&h_empty[b], 2 * EPI_WARPS);
+      tc::mbar_init(&hs_full[b], 2 * EPI_WARPS);
       tc::mbar_init(&hs_empty[b], 1);
     }
     tc::mbar_init(o_full, 1);
-    tc::mbar_init(o_empty, OUT_WARPS);
+    tc::mbar_init(o_empty, 2 * OUT_WARPS);
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -153,9 +156,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     tc::prefetch_tmap(&tmW1);
     tc::prefetch_tmap(&tmW2);
   }
-  if (warp == 1) {
-    tc::tmem_alloc(tmem_slot, 512);
-    tc::tmem_relinquish();
+  if (warp == 1) {  // one warp of each CTA allocates the pair's TMEM together
+    tc::tmem_alloc_pair(tmem_slot, 512);
+    tc::tmem_relinquish_pair();
   }
   for (int c = threadIdx.x; c < args.hid; c += blockDim.x) s_b1[c] = args.b1[c];
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
@@ -165,158 +168,148 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (CS > 1) tc::cluster_sync();  // every CTA's barriers exist before any multicast reaches them
+  tc::cluster_sync();  // both CTAs' barriers exist before any remote arrival
   tc::fence_after_sync();
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp < ROLE_WARPS) {
-  tc::setmaxnreg_dec<REG_ROLE>();
-  if (warp == 0) {
-    if (lane == 0) {
-      uint32_t g = 0;  // ring slot counter
-      bool ok = true;
-      // each CTA loads 1/CS of every weight stage (rows rank*slice ..) and multicasts it
-      // to the whole cluster; the stage's barrier expects the full stage
-      auto push = [&](const CUtensorMap* map, int c0, int c1, uint32_t bytes, int slice_rows) {
-        const int s = g % RING;
-        if (g >= (uint32_t)RING && !tc::mbar_wait(&empty[s], ((g / RING) & 1) ^ 1, abort_flag)) return false;
-        tc::mbar_expect_tx(&full[s], bytes);
-        uint8_t* dst = sR + s * Cfg::STAGE_BYTES + rank * slice_rows * 128;
-        if (CS > 1)
-          tc::tma_load_2d_mc(dst, map, &full[s], c0, c1 + rank * slice_rows, MASK);
-        else
-          tc::tma_load_2d(dst, map, &full[s], c0, c1);
-        ++g;
-        return true;
-      };
-      int t = 0;
-      for (int grp = cid; grp < groups && ok; grp += ncl, ++t) {
-        const int m0 = (grp * CS + rank) * BM;
-        if (t >= 1 && !tc::mbar_wait(a_empty, (t - 1) & 1, abort_flag)) { ok = false; break; }
-        if (m0 < M) {
-          tc::mbar_expect_tx(a_full, Cfg::A_BYTES);
-          for (int kb = 0; kb < KA; ++kb) tc::tma_load_2d(sA + kb * (BM * BK * 2), &tmY, a_full, kb * BK, m0);
-        } else {
-          tc::mbar_arrive(a_full);  // a tile past the end: its results are never stored
+    tc::setmaxnreg_dec<REG_ROLE>();
+    if (warp == 0) {
+      if (lane == 0) {
+        uint32_t g = 0;  // ring slot counter
+        bool ok = true;
+        // each CTA loads its half of every weight stage into its own ring slot; the even
+        // CTA's barrier expects both halves
+        auto push = [&](const CUtensorMap* map, int nbox, int c0, int c1, int box_bytes) {
+          const int s = g % RING;
+          if (g >= (uint32_t)RING && !tc::mbar_wait(&empty[s], ((g / RING) & 1) ^ 1, abort_flag)) return false;
+          if (rank == 0) tc::mbar_expect_tx(&full[s], 2 * nbox * box_bytes);
+          for (int b = 0; b < nbox; ++b)
+            tc::tma_load_2d_pair(sR + s * Cfg::STAGE_BYTES + b * box_bytes, map, lead(&full[s]), c0 + b * BK, c1);
+          ++g;
+          return true;
+        };
+        int t = 0;
+        for (int p = cid; p < pairs && ok; p += ncl, ++t) {
+          const int m0 = (2 * p + rank) * BM;
+          if (t >= 1 && !tc::mbar_wait(a_empty, (t - 1) & 1, abort_flag)) { ok = false; break; }
+          if (rank == 0) tc::mbar_expect_tx(a_full, ((2 * p + 1) * BM < M ? 2 : 1) * Cfg::A_BYTES);
+          if (m0 < M)
+            for (int kb = 0; kb < Cfg::KA; ++kb)
+              tc::tma_load_2d_pair(sA + kb * (BM * BK * 2), &tmY, lead(a_full), kb * BK, m0);
+          for (int j = 0; j < NJ + LOOK && ok; ++j) {  // the MMA warp's consumption order
+            if (j < NJ)
+              for (int st = 0; st < Cfg::W1_STAGES && ok; ++st)
+                ok = push(&tmW1, Cfg::W1_KB, st * Cfg::W1_KB * BK, j * HC + rank * (HC / 2), Cfg::W1_BOX);
+            if (j >= LOOK)
+              for (int kb = 0; kb < Cfg::KH && ok; ++kb)
+                ok = push(&tmW2, 1, (j - LOOK) * HC + kb * BK, rank * (D / 2), Cfg::W2_BOX);
+          }
         }
-        for (int j = 0; j <= NJ && ok; ++j) {
-          if (j < NJ)
-            for (int kb = 0; kb < KA && ok; ++kb) ok = push(&tmW1, kb * BK, j * HC, Cfg::W1_BYTES, HC / CS);
-          if (j >= 1)
-            for (int kb = 0; kb < KH && ok; ++kb)
-              for (int hf = 0; hf < Cfg::NHALF && ok; ++hf)
-                ok = push(&tmW2, (j - 1) * HC + kb * BK, hf * Cfg::HR, Cfg::W2_BYTES, Cfg::HR / CS);
-        }
-      }
-      for (uint32_t h = (g > (uint32_t)RING ? g - RING : 0); h < g; ++h)
-        if (!tc::mbar_wait_timed(&full[h % RING], (h / RING) & 1)) break;
-      // and the other CTAs' releases of the last stages, which arrive on this CTA's barriers
-      if (CS > 1)
+        // every signal addressed to this CTA has landed before it may exit: the pair's
+        // releases of the last stages and of the last Y tile
         for (uint32_t h = (g > (uint32_t)RING ? g - RING : 0); h < g; ++h)
           if (!tc::mbar_wait_timed(&empty[h % RING], (h / RING) & 1)) break;
-      if (!ok) {
-        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
-        *abort_flag = 1;
-      }
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t id1 = tc::idesc_bf16_f32(BM, HC);
-      constexpr uint32_t id2 = tc::idesc_bf16_f32(BM, Cfg::HR);
-      uint32_t g = 0, q = 0;  // ring slot counter, hidden-chunk counter (across tiles)
-      bool ok = true;
-      auto release = [&](int s) {  // the stage's MMAs are done: free it in every CTA of the cluster
-        if (CS > 1)
-          tc::mma_commit_mc(&empty[s], MASK);
-        else
-          tc::mma_commit(&empty[s]);
-      };
-      auto pop = [&](int& s) {
-        s = g % RING;
-        if (!tc::mbar_wait(&full[s], (g / RING) & 1, abort_flag)) return false;
-        tc::fence_after_sync();
-        ++g;
-        return true;
-      };
-      auto mma1 = [&](uint32_t qq) {  // H[qq & 1] = Y . W1_chunk^T
-        const uint32_t hb = qq & 1, use = qq >> 1;
-        if (use >= 1 && !tc::mbar_wait(&h_empty[hb], (use & 1) ^ 1, abort_flag)) return false;
-        tc::fence_after_sync();
-        const uint32_t dt = tmem_base + Cfg::H_COL0 + hb * HC;
-        for (int kb = 0; kb < KA; ++kb) {
-          int s;
-          if (!pop(s)) return false;
-          const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sA + kb * (BM * BK * 2)));
-          const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16(dt, ad + 2 * kk, bd + 2 * kk, id1, (kb | kk) != 0);
-          release(s);
+        if (t >= 1) tc::mbar_wait_timed(a_empty, (t - 1) & 1);
+        if (!ok) {
+          if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+          *abort_flag = 1;
         }
-        tc::mma_commit(&h_full[hb]);
-        return true;
-      };
-      auto mma2 = [&](uint32_t qq, bool first, bool last, int t) {  // OUT (+)= Hs[qq & 1] . W2_chunk^T
-        const uint32_t hb = qq & 1, use = qq >> 1;
-        if (first && t >= 1 && !tc::mbar_wait(o_empty, (t - 1) & 1, abort_flag)) return false;
-        if (!tc::mbar_wait(&hs_full[hb], use & 1, abort_flag)) return false;
-        tc::fence_after_sync();
-        for (int kb = 0; kb < KH; ++kb) {
-          const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sH + hb * Cfg::HS_BYTES + kb * (BM * BK * 2)));
-          for (int hf = 0; hf < Cfg::NHALF; ++hf) {  // OUT columns hf*HR .. +HR
+      }
+      __syncwarp();
+    } else if (warp == 1 && rank == 0) {
+      if (lane == 0) {
+        constexpr uint32_t id1 = tc::idesc_bf16_f32(2 * BM, HC);
+        constexpr uint32_t id2 = tc::idesc_bf16_f32(2 * BM, D);
+        uint32_t g = 0, q = 0;  // ring slot counter, hidden-chunk counter (across tiles)
+        bool ok = true;
+        auto pop = [&](int& s) {
+          s = g % RING;
+          if (!tc::mbar_wait_cluster(&full[s], (g / RING) & 1, abort_flag)) return false;
+          tc::fence_after_sync();
+          ++g;
+          return true;
+        };
+        auto mma1 = [&](uint32_t qq) {  // H[qq % NB] = Y . W1_chunk^T
+          const uint32_t hb = qq % NB, use = qq / NB;
+          if (use >= 1 && !tc::mbar_wait_cluster(&h_empty[hb], (use & 1) ^ 1, abort_flag)) return false;
+          tc::fence_after_sync();
+          const uint32_t dt = tmem_base + Cfg::H_COL0 + hb * HC;
+          for (int st = 0; st < Cfg::W1_STAGES; ++st) {
             int s;
             if (!pop(s)) return false;
+            for (int b = 0; b < Cfg::W1_KB; ++b) {
+              const int kb = st * Cfg::W1_KB + b;
+              const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sA + kb * (BM * BK * 2)));
+              const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES + b * Cfg::W1_BOX));
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16_pair(dt, ad + 2 * kk, bd + 2 * kk, id1, (kb | kk) != 0);
+            }
+            tc::mma_commit_pair(&empty[s], PAIR);
+          }
+          tc::mma_commit_pair(&h_full[hb], PAIR);
+          return true;
+        };
+        auto mma2 = [&](uint32_t qq, bool first, bool last, int t) {  // OUT (+)= Hs[qq % NB] . W2_chunk^T
+          const uint32_t hb = qq % NB, use = qq / NB;
+          if (first && t >= 1 && !tc::mbar_wait_cluster(o_empty, (t - 1) & 1, abort_flag)) return false;
+          if (!tc::mbar_wait_cluster(&hs_full[hb], use & 1, abort_flag)) return false;
+          tc::fence_after_sync();
+          for (int kb = 0; kb < Cfg::KH; ++kb) {
+            int s;
+            if (!pop(s)) return false;
+            const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sH + hb * Cfg::HS_BYTES + kb * (BM * BK * 2)));
             const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              tc::mma_f16(tmem_base + hf * Cfg::HR, ad + 2 * kk, bd + 2 * kk, id2, (!first || kb || kk) ? 1u : 0u);
-            release(s);
+              tc::mma_f16_pair(tmem_base, ad + 2 * kk, bd + 2 * kk, id2, (!first || kb || kk) ? 1u : 0u);
+            tc::mma_commit_pair(&empty[s], PAIR);
           }
-        }
-        tc::mma_commit(&hs_empty[hb]);
-        if (last) tc::mma_commit(o_full);
-        return true;
-      };
-      int t = 0;
-      for (int grp = cid; grp < groups && ok; grp += ncl, ++t) {
-        if (!tc::mbar_wait(a_full, t & 1, abort_flag)) { ok = false; break; }
-        tc::fence_after_sync();
-        const uint32_t q0 = q;
-        for (int j = 0; j <= NJ && ok; ++j) {
-          if (j < NJ) {
-            ok = mma1(q0 + j);
-            if (ok && j == NJ - 1) tc::mma_commit(a_empty);  // Y tile no longer read after the last MMA1
+          tc::mma_commit_pair(&hs_empty[hb], PAIR);
+          if (last) tc::mma_commit_pair(o_full, PAIR);
+          return true;
+        };
+        int t = 0;
+        for (int p = cid; p < pairs && ok; p += ncl, ++t) {
+          if (!tc::mbar_wait_cluster(a_full, t & 1, abort_flag)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t q0 = q;
+          for (int j = 0; j < NJ + LOOK && ok; ++j) {
+            if (j < NJ) {
+              ok = mma1(q0 + j);
+              if (ok && j == NJ - 1) tc::mma_commit_pair(a_empty, PAIR);  // Y no longer read after the last MMA1
+            }
+            if (ok && j >= LOOK) ok = mma2(q0 + j - LOOK, j == LOOK, j == NJ + LOOK - 1, t);
           }
-          if (ok && j >= 1) ok = mma2(q0 + j - 1, j == 1, j == NJ, t);
+          q = q0 + NJ;
         }
-        q = q0 + NJ;
+        if (!ok) {
+          if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+          *abort_flag = 1;
+        }
+        // every issued MMA has finished (and signalled) before TMEM can be released
+        tc::mma_commit_pair(teardown, 0x1);
+        tc::mbar_wait_timed(teardown, 0);
       }
-      if (!ok) {
-        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
-        *abort_flag = 1;
-      }
-      tc::mma_commit(teardown);
-      tc::mbar_wait_timed(teardown, 0);
+      __syncwarp();
     }
-    __syncwarp();
-  }
   } else if (warp < ROLE_WARPS + EPI_WARPS) {
     // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 swizzled SMEM operand of MMA2
     const int quarter = warp & 3, cg = (warp - ROLE_WARPS) >> 2;
-    const int r = quarter * 32 + lane;  // row within the tile (= TMEM lane)
+    const int r = quarter * 32 + lane;  // row within this CTA's 128 rows (= TMEM lane)
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     uint32_t q = 0;
     bool ok = true;
-    for (int grp = cid; grp < groups && ok; grp += ncl) {
+    for (int p = cid; p < pairs && ok; p += ncl) {
       for (int j = 0; j < NJ; ++j, ++q) {
-        const uint32_t hb = q & 1, use = q >> 1;
+        const uint32_t hb = q % NB, use = q / NB;
         if (!tc::mbar_wait(&h_full[hb], use & 1, abort_flag)) { ok = false; break; }
         if (use >= 1 && !tc::mbar_wait(&hs_empty[hb], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
         __syncwarp();
         tc::fence_after_sync();
         uint8_t* hs = sH + hb * Cfg::HS_BYTES;
 #pragma unroll 1
-        for (int c0 = cg * (HC / EW); c0 < (cg + 1) * (HC / EW); c0 += 32) {
+        for (int c0 = cg * (HC / 2); c0 < (cg + 1) * (HC / 2); c0 += 32) {
           uint32_t v[32];
           tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + hb * HC + c0, v);
           tc::tmem_ld_wait();
@@ -342,46 +335,45 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          tc::mbar_arrive(&h_empty[hb]);
-          tc::mbar_arrive(&hs_full[hb]);
+          tc::mbar_arrive_cluster(lead(&h_empty[hb]));
+          tc::mbar_arrive_cluster(lead(&hs_full[hb]));
         }
       }
     }
+    // the pair's MMA2 releases of the last NB chunks land before this CTA may exit
+    for (uint32_t qq = (q >= NB ? q - NB : 0); qq < q; ++qq) tc::mbar_wait_timed(&hs_empty[qq % NB], (qq / NB) & 1);
     if (!ok) {
       if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
       *abort_flag = 1;
     }
   } else {
-    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; D/OW columns of a row per thread
+    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; one whole row per thread
     tc::setmaxnreg_inc<REG_FINAL>();
     const int fw = warp - ROLE_WARPS - EPI_WARPS;  // 0 .. OUT_WARPS-1
-    const int quarter = warp & 3, half = fw >> 2;
+    const int quarter = warp & 3;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
-    const int c_lo = half * (D / OW);
     uint8_t* tl = s_tile + (size_t)fw * rows::TILE_BYTES;
     bool ok = true;
     int t = 0;
-    for (int grp = cid; grp < groups && ok; grp += ncl, ++t) {
-      const int row0 = (grp * CS + rank) * BM + quarter * 32;  // this warp's 32 rows; the thread owns row0 + lane
+    for (int p = cid; p < pairs && ok; p += ncl, ++t) {
+      const int row0 = (2 * p + rank) * BM + quarter * 32;  // this warp's 32 rows; the thread owns row0 + lane
       const int nvalid = M - row0;
       float* xb = args.X + (size_t)row0 * D;
       if (lane < nvalid)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xb + (size_t)lane * D + c_lo), "r"(D / OW * 4)
-                     : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xb + (size_t)lane * D), "r"(D * 4) : "memory");
       if (!tc::mbar_wait(o_full, t & 1, abort_flag)) { ok = false; break; }
       __syncwarp();
       tc::fence_after_sync();
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
-      constexpr int c_hi = D / OW;  // (c_lo = 0 when OW = 1)
-      float4 gn[8];                 // the next chunk's residual, loaded one chunk ahead
-      rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
+      float4 gn[8];  // the next chunk's residual, loaded one chunk ahead
+      rows::load32_issue(xb, D, nvalid, lane, gn);
 #pragma unroll 1
-      for (int c0 = c_lo; c0 < c_lo + c_hi; c0 += 32) {
+      for (int c0 = 0; c0 < D; c0 += 32) {
         uint32_t v[32];
         tc::tmem_ld_32x32b_x32(lane_base + c0, v);
         float f[32];
         rows::load32_finish(tl, lane, gn, f);
-        if (c0 + 32 < c_lo + c_hi) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
+        if (c0 + 32 < D) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; k += 4) {
@@ -407,43 +399,22 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       }
       tc::fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(o_empty);  // OUT drained: the next tile's MMA2 may start
-      float mean = run_mean, m2 = run_m2, n = run_n;
-      if (OW > 1) {
-        // merge the parts of each row in a fixed order
-        float* st = ln_stats + ((size_t)fw * 32 + lane) * 2;
-        st[0] = run_mean;
-        st[1] = run_m2;
-        named_sync(1 + quarter, 32 * OW);
-        mean = 0.f; m2 = 0.f; n = 0.f;
-#pragma unroll
-        for (int g2 = 0; g2 < OW; ++g2) {
-          // final warp of part g2 in this quarter: fw = 4*g2 + ((quarter - 2) & 3)
-          const float* o = ln_stats + ((size_t)(4 * g2 + ((quarter - 2) & 3)) * 32 + lane) * 2;
-          const float om = o[0], oq = o[1], on = (float)(D / OW);
-          const float nn = n + on;
-          const float dl = om - mean;
-          mean += dl * (on / nn);
-          m2 += oq + dl * dl * (n * on / nn);
-          n = nn;
-        }
-        named_sync(1 + quarter, 32 * OW);  // the partial slots are reused by the next tile
-      }
-      const float rstd = rsqrtf(m2 / n + 1e-5f);
-      rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
+      if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // OUT drained: the next tile's MMA2 may start
+      const float rstd = rsqrtf(run_m2 / run_n + 1e-5f);
+      rows::load32_issue(xb, D, nvalid, lane, gn);
 #pragma unroll 1
-      for (int c0 = c_lo; c0 < c_lo + c_hi; c0 += 32) {
+      for (int c0 = 0; c0 < D; c0 += 32) {
         float xv[32];
         rows::load32_finish(tl, lane, gn, xv);  // the rows this warp stored above
-        if (c0 + 32 < c_lo + c_hi) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
+        if (c0 + 32 < D) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
 #pragma unroll
         for (int k = 0; k < 32; k += 4) {
           const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
           const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
-          xv[k] = (xv[k] - mean) * rstd * g4.x + b4.x;
-          xv[k + 1] = (xv[k + 1] - mean) * rstd * g4.y + b4.y;
-          xv[k + 2] = (xv[k + 2] - mean) * rstd * g4.z + b4.z;
-          xv[k + 3] = (xv[k + 3] - mean) * rstd * g4.w + b4.w;
+          xv[k] = (xv[k] - run_mean) * rstd * g4.x + b4.x;
+          xv[k + 1] = (xv[k + 1] - run_mean) * rstd * g4.y + b4.y;
+          xv[k + 2] = (xv[k + 2] - run_mean) * rstd * g4.z + b4.z;
+          xv[k + 3] = (xv[k + 3] - run_mean) * rstd * g4.w + b4.w;
         }
         rows::store32_bf16(args.ln_out + (size_t)row0 * D + c0, D, nvalid, tl, lane, xv);
       }
@@ -456,10 +427,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
 
   tc::fence_before_sync();
   __syncthreads();
-  if (CS > 1) tc::cluster_sync();  // no CTA leaves while another may still signal it
+  tc::cluster_sync();  // no CTA leaves while its peer may still signal it or read its memory
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem_base, 512);
+    tc::tmem_dealloc_pair(tmem_base, 512);
   }
 }
 
@@ -498,14 +469,14 @@ int num_sms() {
   return n;
 }
 
-template <int D, int CS>
-cudaError_t launch_dc(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
+template <int D>
+cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
   using Cfg = MlpCfg<D>;
-  auto kern = mlp_tc_kernel<D, CS>;
+  auto kern = mlp_tc_kernel<D>;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.x = 2;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   lc.blockDim = dim3(THREADS);
@@ -513,33 +484,24 @@ cudaError_t launch_dc(const bf16* Y, const bf16* W1t, const bf16* W2t, const Mlp
   lc.stream = st;
   lc.attrs = at;
   lc.numAttrs = 1;
-  static int max_clusters = 0;  // co-resident clusters of CS CTAs at one CTA per SM
-  if (!max_clusters) {
+  static int max_pairs = 0;  // co-resident CTA pairs at one CTA per SM
+  if (!max_pairs) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    lc.gridDim = dim3(num_sms() / CS * CS);
+    lc.gridDim = dim3(num_sms() / 2 * 2);
     int n = 0;
     e = cudaOccupancyMaxActiveClusters(&n, kern, &lc);
     if (e != cudaSuccess) return e;
-    max_clusters = n > 0 ? n : 1;
+    max_pairs = n > 0 ? n : 1;
   }
   CUtensorMap my, m1, m2;
   if (!map2d(&my, Y, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
-  if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC / CS)) return cudaErrorInvalidValue;
-  if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, Cfg::HR / CS)) return cudaErrorInvalidValue;
-  const int groups = ((a.M + BM - 1) / BM + CS - 1) / CS;
-  lc.gridDim = dim3((groups < max_clusters ? groups : max_clusters) * CS);
+  if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC / 2)) return cudaErrorInvalidValue;
+  if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;
+  const int pairs = ((a.M + BM - 1) / BM + 1) / 2;
+  lc.gridDim = dim3((pairs < max_pairs ? pairs : max_pairs) * 2);
   cudaError_t e = cudaLaunchKernelEx(&lc, kern, my, m1, m2, a);
   return e != cudaSuccess ? e : cudaGetLastError();
-}
-
-// Weight stages are shared by clusters of two CTAs: half the L2 reads of the weights per
-// tile, which all CTAs otherwise stream from the same lines at the same time.
-constexpr int MLP_CLUSTER = 2;
-
-template <int D>
-cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
-  return launch_dc<D, MLP_CLUSTER>(Y, W1t, W2t, a, st);
 }
 
 }  // namespace
