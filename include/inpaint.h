@@ -76,6 +76,10 @@ typedef struct inpaint_config {
   int32_t shift;      /* 1 = odd blocks use windows offset by half a window  */
   uint64_t seed;      /* recorded only; weights always come from the caller  */
   size_t hbm_budget_bytes; /* cap on the context's device memory, 0 = none   */
+  int32_t mem_slots;  /* temporal memory slots m (0-4).  With m > 0 the odd blocks are
+                         temporal: their queries also attend to the keys / values that up
+                         to m previous frames produced in the same block (memory tensors;
+                         see inpaint_batch_mem).  0 = single-frame spatial model. */
 } inpaint_config;
 
 typedef struct inpaint_ctx inpaint_ctx;
@@ -210,6 +214,26 @@ INPAINT_API int inpaint_sync(inpaint_ctx* ctx, void* stream, int timeout_ms);
 #define INPAINT_PROFILE_CLASSES 12
 INPAINT_API int inpaint_profile_enable(inpaint_ctx* ctx, int on);
 INPAINT_API int inpaint_profile_read(inpaint_ctx* ctx, float* ms, int64_t* launches);
+
+/* Temporal memory (cfg.mem_slots = m > 0).  A frame's memory tensor holds, for every
+ * temporal block (odd l), the k | v rows of its own tokens in that block and their
+ * usable-key mask: what a later frame of the same stream attends to.
+ * inpaint_memory_bytes gives the size of one frame's memory buffer for an H x W stream
+ * (0 when m = 0).  The paper keeps a fixed number of memory tensors of previous outputs
+ * as model inputs and outputs (Sections "Inpainting Manager", "Minimal memory slots"). */
+INPAINT_API int inpaint_memory_bytes(inpaint_ctx* ctx, int H, int W, size_t* bytes);
+
+/* As inpaint_batch, with memory.  mem_in: host array [B * m] of device pointers, frame
+ * b's slots at [b*m .. b*m + m-1], each a previous frame's memory buffer of the same
+ * H x W, or NULL for an empty slot (the array itself may be NULL: no memory).  mem_out:
+ * host array [B] of device buffers (inpaint_memory_bytes each, NULL = not recorded) that
+ * receive each frame's own memory tensor.  Buffers must be 256-byte aligned and are
+ * owned by the caller; an output buffer must not also be an input of the same call.
+ * With every slot empty the result equals inpaint_batch.  Errors: E_INVAL (m = 0 with
+ * memory arguments, misaligned buffers, shapes), E_NOMEM, E_CUDA. */
+INPAINT_API int inpaint_batch_mem(inpaint_ctx* ctx, const float* x, const uint8_t* hole, int B, int H, int W,
+                                  float* out, float* pred, const void* const* mem_in, void* const* mem_out,
+                                  void* stream);
 
 /* Number of kernels this context has launched since creation. */
 INPAINT_API int inpaint_launch_count(inpaint_ctx* ctx, int64_t* count);

@@ -27,6 +27,11 @@ used here are:
   d/4 and d/8 channels, then a 3x3 conv to RGB = pred (no output activation);
 * composite out = pred on hole pixels and x on known pixels (a select, so known pixels
   are copied exactly), cropped back to H x W;
+* temporal memory (mem_slots = m > 0): odd blocks are temporal; a temporal block's
+  queries also attend to the keys/values that each of m previous frames produced in
+  the same block, at the same window positions, where those frames' tokens were usable
+  keys; the window becomes valid if any current or memory key is usable.  A frame's
+  memory tensor is its own k | v and usable-key mask in every temporal block;
 * fine-tuning loss: L1 over hole pixels only, sum / (3 * number of hole pixels), 0 when
   there are no hole pixels (Section "Training structure", "Loss"; the paper also weights
   known pixels, which this path leaves out).
@@ -191,6 +196,56 @@ def window_attention(qkv: torch.Tensor, valid: torch.Tensor, heads: int, widx: t
     return o, nxt
 
 
+def temporal_block(cfg, l: int) -> bool:
+    """Whether block l is a temporal block: with memory slots, odd blocks (the paper's
+    fixed series alternating spatial and temporal blocks, item "Distinct Transformer
+    Blocks"; memory tensors of previous frames, Sections "Inpainting Manager" and
+    "Minimal memory slots")."""
+    return getattr(cfg, "mem_slots", 0) > 0 and l % 2 == 1
+
+
+def window_attention_mem(qkv: torch.Tensor, valid: torch.Tensor, heads: int, widx: torch.Tensor, mem):
+    """window_attention with memory keys: `mem` lists, per memory slot, (kv [N, 2d] =
+    k | v of a past frame at this block, mask [N] = that frame's usable-key mask there),
+    or None for an empty slot.  Query t of window w attends over w's usable current keys
+    and, in every slot, the usable keys at w's positions; o_t = 0 when there is none.
+    next valid[t] = 1 iff t's window had any usable key (current or memory)."""
+    N, d3 = qkv.shape
+    d = d3 // 3
+    dh = d // heads
+    nW, S = widx.shape
+    real = widx >= 0
+    safe = widx.clamp(min=0)
+
+    def heads_of(t):  # [N, d] gathered by window -> [nW, h, S, dh]
+        return t[safe].reshape(nW, S, heads, dh).transpose(1, 2)
+
+    q = heads_of(qkv[:, :d])
+    ks, vs, oks = [heads_of(qkv[:, d:2 * d])], [heads_of(qkv[:, 2 * d:])], [real & (valid[safe] != 0)]
+    for slot in mem:
+        if slot is None:
+            continue
+        kv, mask = slot
+        ks.append(heads_of(kv[:, :d]))
+        vs.append(heads_of(kv[:, d:]))
+        oks.append(real & (mask[safe] != 0))
+    k = torch.cat(ks, dim=2)                                   # [nW, h, S*(1+m), dh]
+    v = torch.cat(vs, dim=2)
+    key_ok = torch.cat(oks, dim=1)                             # [nW, S*(1+m)]
+    any_w = key_ok.any(dim=1)
+    s = q @ k.transpose(-1, -2) / math.sqrt(dh)
+    allowed = key_ok | ~any_w[:, None]
+    s = s.masked_fill(~allowed[:, None, None, :], float("-inf"))
+    e = torch.exp(s - s.max(dim=-1, keepdim=True).values)
+    pr = e / e.sum(dim=-1, keepdim=True)
+    ow = (pr @ v).transpose(1, 2).reshape(nW, S, d) * any_w[:, None, None].to(qkv.dtype)
+    o = qkv.new_zeros(N, d)
+    o = o.index_put((widx[real],), ow[real])
+    nxt = torch.zeros(N, dtype=torch.uint8)
+    nxt[widx[real]] = any_w[:, None].expand(nW, S)[real].to(torch.uint8)
+    return o, nxt
+
+
 def upsample2(f: torch.Tensor) -> torch.Tensor:
     """Nearest-neighbour x2 upsampling of [B, C, H, W]."""
     return f.repeat_interleave(2, dim=2).repeat_interleave(2, dim=3)
@@ -211,11 +266,15 @@ def conv3x3(f: torch.Tensor, w: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
 
 # ----------------------------------------------------------------------------- model
 
-def forward(x, hole, weights, cfg, keep_block_inputs: bool = False) -> dict:
+def forward(x, hole, weights, cfg, keep_block_inputs: bool = False, mem=None) -> dict:
     """The whole pass.  x float [B,3,H,W] in [0,1]; hole uint8 [B,H,W] (nonzero = remove).
 
     Returns out [B,3,H,W], pred [B,3,H,W] (decoder output, cropped), masks
     [(L+1), B, N] uint8 (token masks v0 ... vL) and, on request, the block inputs.
+    With memory slots (cfg.mem_slots > 0), `mem[b]` lists frame b's memory slots (each
+    a previous frame's "memory" entry, or None), and res["memory"][b] is the memory
+    tensor this frame emits: for every temporal block l, (k | v [N, 2d], usable-key
+    mask [N]) of its own tokens at that block.
     """
     x = torch.as_tensor(x).to(DT)
     hole = torch.as_tensor(hole)
@@ -233,6 +292,7 @@ def forward(x, hole, weights, cfg, keep_block_inputs: bool = False) -> dict:
     v = token_mask_init(hp, p)                                                  # [B, N]
     masks = [v]
     block_inputs = []
+    memory = [dict() for _ in range(B)]
     for l in range(cfg.blocks):
         block_inputs.append(tok)
         widx = window_index(Ht, Wt, ws, block_offset(cfg, l))
@@ -240,7 +300,13 @@ def forward(x, hole, weights, cfg, keep_block_inputs: bool = False) -> dict:
         qkv = y @ w[f"{l}.qkv.w"] + w[f"{l}.qkv.b"]
         outs, nxts = [], []
         for bi in range(B):
-            o, nxt = window_attention(qkv[bi], v[bi], cfg.heads, widx)
+            if temporal_block(cfg, l):
+                slots = [None if mem is None or mem[bi] is None or mem[bi][j] is None else mem[bi][j][l]
+                         for j in range(cfg.mem_slots)]
+                o, nxt = window_attention_mem(qkv[bi], v[bi], cfg.heads, widx, slots)
+                memory[bi][l] = (qkv[bi][:, d:].clone(), v[bi].clone())
+            else:
+                o, nxt = window_attention(qkv[bi], v[bi], cfg.heads, widx)
             outs.append(o)
             nxts.append(nxt)
         o = torch.stack(outs)
@@ -258,6 +324,8 @@ def forward(x, hole, weights, cfg, keep_block_inputs: bool = False) -> dict:
     pred = pred_full[:, :, :H, :W]
     out = torch.where((hole != 0)[:, None], pred, x)
     res = {"out": out, "pred": pred, "masks": torch.stack(masks)}
+    if getattr(cfg, "mem_slots", 0) > 0:
+        res["memory"] = memory
     if keep_block_inputs:
         res["block_inputs"] = block_inputs
         res["final_tokens"] = tok

@@ -37,18 +37,21 @@ class InpaintConfig(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("heads", ctypes.c_int32), ("window", ctypes.c_int32),
                 ("blocks", ctypes.c_int32), ("mlp_ratio", ctypes.c_int32), ("patch", ctypes.c_int32),
                 ("dec_c1", ctypes.c_int32), ("dec_c2", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("shift", ctypes.c_int32), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_size_t)]
+                ("shift", ctypes.c_int32), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("mem_slots", ctypes.c_int32)]
 
     @classmethod
     def from_model(cls, cfg: ModelConfig, seed: int = 0, hbm_budget_bytes: int = 0) -> "InpaintConfig":
         return cls(cfg.dim, cfg.heads, cfg.window, cfg.blocks, cfg.mlp_ratio, cfg.patch, cfg.dec_c1, cfg.dec_c2,
-                   cfg.precision, cfg.shift, seed, hbm_budget_bytes)
+                   cfg.precision, cfg.shift, seed, hbm_budget_bytes, cfg.mem_slots)
 
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _SIGS = {
     "inpaint_strerror": (ctypes.c_char_p, [_I]),
+    "inpaint_memory_bytes": (_I, [_P, _I, _I, _P]),
+    "inpaint_batch_mem": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P]),
     "inpaint_last_cuda_error": (_I, []),
     "inpaint_cuda_error_name": (ctypes.c_char_p, [_I]),
     "inpaint_num_params": (_I, [ctypes.POINTER(InpaintConfig), ctypes.POINTER(ctypes.c_size_t)]),
@@ -180,6 +183,27 @@ def inpaint_batch(ctx, x, hole, out, pred=None, stream=None):
            "inpaint_batch")
 
 
+def inpaint_memory_bytes(ctx, H: int, W: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().inpaint_memory_bytes(ctx, H, W, ctypes.byref(n)), "inpaint_memory_bytes")
+    return n.value
+
+
+def inpaint_batch_mem(ctx, x, hole, out, mem_in, mem_out, pred=None, stream=None):
+    """mem_in: list over frames of lists of m device buffers (uint8 CUDA tensors) or None;
+    mem_out: list over frames of a device buffer or None."""
+    B, H, W = hole.shape
+    tab_in = None
+    if mem_in is not None:
+        flat = [None if t is None else _ptr(t).value for slots in mem_in for t in slots]
+        tab_in = (ctypes.c_void_p * len(flat))(*flat)
+    tab_out = None
+    if mem_out is not None:
+        tab_out = (ctypes.c_void_p * B)(*[None if t is None else _ptr(t).value for t in mem_out])
+    _check(load().inpaint_batch_mem(ctx, _ptr(x), _ptr(hole), B, H, W, _ptr(out), _ptr(pred), tab_in, tab_out,
+                                    _stream(stream)), "inpaint_batch_mem")
+
+
 def inpaint_batch_ws(ctx, workspace, x, hole, out, pred=None, stream=None):
     B, H, W = hole.shape
     nbytes = workspace.numel() * workspace.element_size()
@@ -293,6 +317,19 @@ class Inpainter:
         out = torch.empty_like(x)
         pred = torch.empty_like(x) if want_pred else None
         inpaint_batch(self.ctx, x, hole, out, pred, stream)
+        return (out, pred) if want_pred else out
+
+    def memory_buffer(self, H: int, W: int):
+        """A fresh device buffer for one frame's memory tensor (256-byte aligned)."""
+        import torch
+        n = inpaint_memory_bytes(self.ctx, H, W)
+        return torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+
+    def with_memory(self, x, hole, mem_in, mem_out, want_pred: bool = False, stream=None):
+        import torch
+        out = torch.empty_like(x)
+        pred = torch.empty_like(x) if want_pred else None
+        inpaint_batch_mem(self.ctx, x, hole, out, mem_in, mem_out, pred, stream)
         return (out, pred) if want_pred else out
 
     def token_masks(self, B: int, H: int, W: int) -> np.ndarray:

@@ -28,6 +28,7 @@ class ModelConfig:
     dec_c2: int = 0         # decoder stage-2 channels (0 -> d/8)
     precision: int = FP32   # FP32 plain form or BF16 tensor-core form
     shift: int = 1          # 1: odd blocks use windows offset by half a window
+    mem_slots: int = 0      # m: temporal memory slots (odd blocks attend to m past frames)
 
     @property
     def c1(self) -> int:

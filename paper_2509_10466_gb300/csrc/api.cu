@@ -30,6 +30,7 @@ bool check_cfg(const inpaint_config* c) {
   const int c1 = c->dec_c1 ? c->dec_c1 : c->dim / 4;
   const int c2 = c->dec_c2 ? c->dec_c2 : c->dim / 8;
   if (c1 <= 0 || c2 <= 0 || c1 % 4 || c2 % 4 || c1 > 4096 || c2 > 1024) return false;
+  if (c->mem_slots < 0 || c->mem_slots > 4) return false;
   return true;
 }
 
@@ -120,8 +121,18 @@ Plan make_plan(const inpaint_ctx* c, int B, int H, int W) {
   p.f1 = take((size_t)B * (2 * p.Ht) * (2 * p.Wt) * c->c1 * es);
   p.f2 = take((size_t)B * p.Hp * p.Wp * c->c2 * es);
   p.err = take(256);
+  p.memtab = take((size_t)B * (c->cfg.mem_slots > 0 ? c->cfg.mem_slots : 1) * sizeof(void*));
   p.end = q;
   return p;
+}
+
+MemLayout mem_layout(const inpaint_ctx* c, int Nt) {
+  const size_t es = c->use_bf16 ? 2 : 4;
+  MemLayout m;
+  m.kv_bytes = (size_t)Nt * 2 * c->d * es;
+  m.stride = align_up(m.kv_bytes + Nt, 256);
+  m.total = (size_t)(c->L / 2) * m.stride;
+  return m;
 }
 
 thread_local cudaError_t g_last_cuda_error = cudaSuccess;
@@ -171,7 +182,7 @@ int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
 
 // The whole forward pass into workspace `ws` laid out by plan `p`.
 int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, const uint8_t* hole, float* out,
-                float* pred, cudaStream_t st) {
+                float* pred, cudaStream_t st, const MemArgs* mem = nullptr) {
   const Offsets& o = c->off;
   const int d = c->d, M = p.M;
   float* tok = reinterpret_cast<float*>(ws + p.tok);
@@ -206,6 +217,27 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
     uint8_t* v_in = masks + (size_t)l * M;
     uint8_t* v_out = masks + (size_t)(l + 1) * M;
+    // temporal block: the queries also see the memory slots' keys of this block, and each
+    // frame's own k | v and key mask here become part of its memory tensor
+    const bool temporal = c->cfg.mem_slots > 0 && (l & 1);
+    const uint8_t* const* mtab = mem ? mem->tab : nullptr;
+    const size_t moff = mem ? (size_t)(l / 2) * mem->lay.stride : 0, mkv = mem ? mem->lay.kv_bytes : 0;
+    auto record_memory = [&](const void* qkv_any) -> int {
+      if (!mem || !mem->out) return INPAINT_OK;
+      const size_t es = c->use_bf16 ? 2 : 4;
+      const uint8_t* q8 = static_cast<const uint8_t*>(qkv_any);
+      for (int b = 0; b < p.B; ++b) {
+        uint8_t* dst = mem->out[b];
+        if (!dst) continue;
+        const uint8_t* src = q8 + ((size_t)b * p.Nt * 3 * d + d) * es;
+        if (cudaMemcpy2DAsync(dst + moff, 2 * d * es, src, 3 * d * es, 2 * d * es, p.Nt, cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(dst + moff + mkv, v_in + (size_t)b * p.Nt, p.Nt, cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess)
+          return INPAINT_E_CUDA;
+      }
+      return INPAINT_OK;
+    };
     if (c->use_bf16) {
       bf16* ln = reinterpret_cast<bf16*>(ws + p.ln);
       bf16* qkv = reinterpret_cast<bf16*>(ws + p.qkv);
@@ -218,7 +250,14 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       const bf16* wfc2 = wfc1 + (size_t)c->hid * d;
       if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
       { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, err, st))); }
-      { LaunchScope ls(c, st, K_ATTN); TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st))); }
+      if (temporal) {
+        LaunchScope ls(c, st, K_ATTN);
+        TRY(cuda_err(launch_attention_tc_mem(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st)));
+      } else {
+        LaunchScope ls(c, st, K_ATTN);
+        TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st)));
+      }
+      if (temporal) TRY(record_memory(qkv));
       if (fuse_ln) {
         LaunchScope ls(c, st, K_PROJ);
         TRY(cuda_err(launch_gemm_tc_resid_ln(ao, wproj, tok, M, d, d, c->w32 + b.projb, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, err, st)));
@@ -256,7 +295,14 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       float* hid = reinterpret_cast<float*>(ws + p.hid);
       { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<float>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
       { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_f32(ln, d, c->w32 + b.qkvw, 3 * d, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, st))); }
-      { LaunchScope ls(c, st, K_ATTN); TRY(cuda_err(launch_attention<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st))); }
+      if (temporal) {
+        LaunchScope ls(c, st, K_ATTN);
+        TRY(cuda_err(launch_attention_mem<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st)));
+      } else {
+        LaunchScope ls(c, st, K_ATTN);
+        TRY(cuda_err(launch_attention<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st)));
+      }
+      if (temporal) TRY(record_memory(qkv));
       { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_f32(ao, d, c->w32 + b.projw, d, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, st))); }
       { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<float>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
       { LaunchScope ls(c, st, K_FC1); TRY(cuda_err(launch_gemm_f32(ln, d, c->w32 + b.fc1w, c->hid, hid, c->hid, M, c->hid, d, EPI_BIAS_GELU, c->w32 + b.fc1b, nullptr, st))); }
@@ -439,6 +485,48 @@ int inpaint_batch(inpaint_ctx* c, const float* x, const uint8_t* hole, int B, in
   TRY(grow(&c->arena, &c->arena_bytes, p.end, c, c->stage_bytes + c->bws_bytes));
   c->have_masks = false;
   TRY(run_forward(c, c->arena, p, x, hole, out, pred, (cudaStream_t)stream));
+  c->last = p;
+  c->have_masks = true;
+  return INPAINT_OK;
+}
+
+int inpaint_memory_bytes(inpaint_ctx* c, int H, int W, size_t* bytes) {
+  if (!c || !bytes || bad_shape(1, H, W)) return INPAINT_E_INVAL;
+  *bytes = c->cfg.mem_slots > 0 ? mem_layout(c, make_plan(c, 1, H, W).Nt).total : 0;
+  return INPAINT_OK;
+}
+
+int inpaint_batch_mem(inpaint_ctx* c, const float* x, const uint8_t* hole, int B, int H, int W, float* out,
+                      float* pred, const void* const* mem_in, void* const* mem_out, void* stream) {
+  if (!c || !x || !hole || !out || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  const int m = c->cfg.mem_slots;
+  if (m == 0 && (mem_in || mem_out)) return INPAINT_E_INVAL;
+  auto misaligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 255) != 0; };
+  std::vector<const uint8_t*> tab;
+  if (mem_in) {
+    tab.resize((size_t)B * m);
+    for (size_t i = 0; i < tab.size(); ++i) {
+      tab[i] = static_cast<const uint8_t*>(mem_in[i]);
+      if (tab[i] && misaligned(tab[i])) return INPAINT_E_INVAL;
+    }
+  }
+  if (mem_out)
+    for (int b = 0; b < B; ++b)
+      if (mem_out[b] && misaligned(mem_out[b])) return INPAINT_E_INVAL;
+  const Plan p = make_plan(c, B, H, W);
+  TRY(grow(&c->arena, &c->arena_bytes, p.end, c, c->stage_bytes + c->bws_bytes));
+  cudaStream_t st = (cudaStream_t)stream;
+  MemArgs ma;
+  ma.lay = mem_layout(c, p.Nt);
+  ma.out = reinterpret_cast<uint8_t* const*>(mem_out);
+  if (mem_in) {
+    // the pointer table travels with the stream (a pageable source is staged before return)
+    TRY(cuda_err(cudaMemcpyAsync(c->arena + p.memtab, tab.data(), tab.size() * sizeof(void*), cudaMemcpyHostToDevice,
+                                 st)));
+    ma.tab = reinterpret_cast<const uint8_t* const*>(c->arena + p.memtab);
+  }
+  c->have_masks = false;
+  TRY(run_forward(c, c->arena, p, x, hole, out, pred, st, &ma));
   c->last = p;
   c->have_masks = true;
   return INPAINT_OK;

@@ -83,6 +83,100 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_kernel(const T* __restrict__ 
   for (int i = 0; i < DH; ++i) orow[i] = from_f32<T>(acc[i] * inv);
 }
 
+// Temporal form: the window's keys are its usable current tokens and, for each of the m
+// memory slots (a previous frame's k | v and usable-key mask at this block, or none),
+// the usable tokens at the window's positions.  Key blocks of 64 are staged one after
+// the other; each query keeps a running maximum, sum and weighted V (the max is raised
+// once per block and the partial results rescaled).
+template <typename T>
+__global__ void __launch_bounds__(SLOTS) attn_simt_mem_kernel(const T* __restrict__ qkv,
+                                                              const uint8_t* __restrict__ v_in, T* __restrict__ o,
+                                                              uint8_t* __restrict__ v_out, int Ht, int Wt, int d,
+                                                              int offset, int nwx, const uint8_t* const* mem_tab,
+                                                              int m, size_t off_kv, size_t off_mask) {
+  __shared__ float Ks[SLOTS][DH + 1];
+  __shared__ float Vs[SLOTS][DH + 1];
+  __shared__ int okS[SLOTS];
+  const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  const int wy = w / nwx, wx = w - (w / nwx) * nwx;
+  const int s = threadIdx.x;
+  const int ty = wy * WS - offset + (s >> 3), tx = wx * WS - offset + (s & 7);
+  const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
+  const size_t Nt = (size_t)Ht * Wt;
+  const size_t i = real ? (size_t)ty * Wt + tx : 0;  // token within the frame
+  const size_t t = (size_t)b * Nt + i;
+  // key of slot s in key block kb (0 = current frame, 1 + j = memory slot j), or null
+  auto key_row = [&](int kb) -> const T* {
+    if (!real) return nullptr;
+    if (kb == 0) return v_in[t] ? qkv + t * 3 * d + d : nullptr;
+    const uint8_t* base = mem_tab[(size_t)b * m + kb - 1];
+    if (!base || !base[off_mask + i]) return nullptr;
+    return reinterpret_cast<const T*>(base + off_kv) + i * 2 * d;
+  };
+  bool anyk = false;
+  for (int kb = 0; kb <= m; ++kb) anyk = anyk || key_row(kb) != nullptr;
+  const int any = __syncthreads_or(anyk);
+  T* orow = o + t * d + h * DH;
+  if (!any) {
+    if (real) {
+#pragma unroll 8
+      for (int e = 0; e < DH; ++e) orow[e] = from_f32<T>(0.f);
+      if (h == 0) v_out[t] = 0;
+    }
+    return;
+  }
+  if (real && h == 0) v_out[t] = 1;
+  float q[DH];
+  const T* qrow = qkv + t * 3 * d + h * DH;
+#pragma unroll
+  for (int e = 0; e < DH; ++e) q[e] = real ? to_f32(qrow[e]) : 0.f;
+  const float scale = 1.0f / sqrtf((float)DH);
+  float mx = -INFINITY, l = 0.f, acc[DH];
+#pragma unroll
+  for (int e = 0; e < DH; ++e) acc[e] = 0.f;
+  for (int kb = 0; kb <= m; ++kb) {
+    const T* kr = key_row(kb);
+    __syncthreads();  // the previous block's keys are no longer read
+    okS[s] = kr != nullptr;
+#pragma unroll 8
+    for (int e = 0; e < DH; ++e) {
+      Ks[s][e] = kr ? to_f32(kr[h * DH + e]) : 0.f;
+      Vs[s][e] = kr ? to_f32(kr[d + h * DH + e]) : 0.f;
+    }
+    if (!__syncthreads_or(kr != nullptr)) continue;
+    if (!real) continue;
+    float bm = -INFINITY;
+    for (int k = 0; k < SLOTS; ++k) {
+      if (!okS[k]) continue;
+      float sc = 0.f;
+#pragma unroll
+      for (int e = 0; e < DH; ++e) sc = fmaf(q[e], Ks[k][e], sc);
+      bm = fmaxf(bm, sc * scale);
+    }
+    if (bm > mx) {
+      const float a = expf(mx - bm);
+      l *= a;
+#pragma unroll
+      for (int e = 0; e < DH; ++e) acc[e] *= a;
+      mx = bm;
+    }
+    for (int k = 0; k < SLOTS; ++k) {
+      if (!okS[k]) continue;
+      float sc = 0.f;
+#pragma unroll
+      for (int e = 0; e < DH; ++e) sc = fmaf(q[e], Ks[k][e], sc);
+      const float p = expf(sc * scale - mx);
+      l += p;
+#pragma unroll
+      for (int e = 0; e < DH; ++e) acc[e] = fmaf(p, Vs[k][e], acc[e]);
+    }
+  }
+  if (!real) return;
+  const float inv = 1.f / l;
+#pragma unroll
+  for (int e = 0; e < DH; ++e) orow[e] = from_f32<T>(acc[e] * inv);
+}
+
 }  // namespace
 
 template <typename T>
@@ -98,6 +192,22 @@ template cudaError_t launch_attention<float>(const float*, const uint8_t*, float
                                              int, cudaStream_t);
 template cudaError_t launch_attention<bf16>(const bf16*, const uint8_t*, bf16*, uint8_t*, int, int, int, int, int,
                                             int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
+                                 int heads, int offset, const uint8_t* const* mem_tab, int m, size_t off_kv,
+                                 size_t off_mask, cudaStream_t st) {
+  const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
+  dim3 grid(nwy * nwx, heads, B);
+  attn_simt_mem_kernel<T><<<grid, SLOTS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, mem_tab,
+                                                  mem_tab ? m : 0, off_kv, off_mask);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_attention_mem<float>(const float*, const uint8_t*, float*, uint8_t*, int, int, int, int,
+                                                 int, int, const uint8_t* const*, int, size_t, size_t, cudaStream_t);
+template cudaError_t launch_attention_mem<bf16>(const bf16*, const uint8_t*, bf16*, uint8_t*, int, int, int, int, int,
+                                                int, const uint8_t* const*, int, size_t, size_t, cudaStream_t);
 
 }  // namespace inpaint
 
@@ -300,6 +410,184 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
   }
 }
 
+// Temporal form on tensor cores: key blocks of 64 (the current window, then each memory
+// slot's tokens at the window's positions) are staged one after the other into the same
+// K / V buffers; per block S = Q K^T, the running row maximum is raised, the running sum
+// and O rescaled by 2^(old max - new max), and O += P V.  Blocks without a usable key
+// are skipped.
+__global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __restrict__ qkv,
+                                                                 const uint8_t* __restrict__ v_in,
+                                                                 bf16* __restrict__ o, uint8_t* __restrict__ v_out,
+                                                                 int Ht, int Wt, int d, int offset, int nwx,
+                                                                 const uint8_t* const* mem_tab, int m,
+                                                                 size_t off_kv, size_t off_mask) {
+  __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
+  __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
+  __shared__ __align__(16) bf16 Vs[HPC][SLOTS][ROWB];
+  __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
+  __shared__ int sidx[SLOTS];       // token index within the frame, -1 for a void slot
+  __shared__ unsigned okw[2];
+  const int w = blockIdx.x, b = blockIdx.z;
+  const int wy = w / nwx, wx = w - (w / nwx) * nwx;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Nt = Ht * Wt;
+  const int h0 = HPC * blockIdx.y;
+
+  if (tid < SLOTS) {
+    const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
+    const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
+    sidx[tid] = real ? ty * Wt + tx : -1;
+    stok[tid] = real ? b * Nt + ty * Wt + tx : -1;
+    bool any = real && v_in[b * Nt + ty * Wt + tx] != 0;
+    for (int j = 0; j < m && !any; ++j) {
+      const uint8_t* base = mem_tab[(size_t)b * m + j];
+      any = real && base && base[off_mask + ty * Wt + tx] != 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, any);
+    if (lane == 0) okw[warp] = bal;
+  }
+  __syncthreads();
+  if ((okw[0] | okw[1]) == 0u) {  // no usable key anywhere: the window outputs 0 and stays invalid
+    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
+      const int s = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
+      const int t = stok[s];
+      if (t >= 0) {
+        *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) = make_uint4(0, 0, 0, 0);
+        if (h0 == 0 && hh == 0 && ch == 0) v_out[t] = 0;
+      }
+    }
+    return;
+  }
+  if (h0 == 0 && tid < SLOTS && stok[tid] >= 0) v_out[stok[tid]] = 1;
+  for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {  // Q of both heads (real slots)
+    const int s = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
+    const int t = stok[s];
+    cp_async16(&Qs[hh][s][ch * 8], qkv + (size_t)(t >= 0 ? t : 0) * 3 * d + (h0 + hh) * DH + ch * 8, t >= 0);
+  }
+
+  const int hh = warp >> 2, wq = warp & 3;
+  const int g = lane >> 2, tq = lane & 3;
+  const int r0 = wq * 16;
+  const float sl2 = 1.4426950408889634f / sqrtf((float)DH);  // scale * log2(e)
+  float mx0 = -INFINITY, mx1 = -INFINITY, l0 = 0.f, l1 = 0.f;
+  float oc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
+  uint32_t qa[2][4];
+  for (int kb = 0; kb <= m; ++kb) {
+    const uint8_t* base = kb == 0 ? nullptr : mem_tab[(size_t)b * m + kb - 1];
+    if (kb > 0 && !base) continue;  // an empty memory slot (uniform across the CTA)
+    __syncthreads();                // the previous block's K / V are no longer read
+    if (tid < SLOTS) {
+      const int i = sidx[tid];
+      const bool ok = i >= 0 && (kb == 0 ? v_in[b * Nt + i] != 0 : base[off_mask + i] != 0);
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      if (lane == 0) okw[warp] = bal;
+    }
+    __syncthreads();
+    const unsigned long long keymask = (unsigned long long)okw[0] | ((unsigned long long)okw[1] << 32);
+    if (keymask == 0ull) continue;
+    for (int e = tid; e < SLOTS * 4 * HPC * 2; e += TC_THREADS) {  // K and V of both heads
+      const int part = e >> 9, r = e & 511;
+      const int s = r >> 3, hh2 = (r >> 2) & 1, ch = r & 3;
+      const bool valid = ((keymask >> s) & 1ull) != 0;
+      const int i = sidx[s] >= 0 ? sidx[s] : 0;
+      const bf16* src = kb == 0 ? qkv + (size_t)(b * Nt + i) * 3 * d + (1 + part) * d
+                                : reinterpret_cast<const bf16*>(base + off_kv) + (size_t)i * 2 * d + part * d;
+      cp_async16((part == 0 ? &Ks[hh2][s][0] : &Vs[hh2][s][0]) + ch * 8, src + (h0 + hh2) * DH + ch * 8, valid);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    {
+      const int row = r0 + (lane & 15), col = (lane >> 4) * 8;
+      ldsm_x4(qa[0], &Qs[hh][row][col]);
+      ldsm_x4(qa[1], &Qs[hh][row][col + 16]);
+    }
+    float sc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      sc[j][0] = sc[j][1] = sc[j][2] = sc[j][3] = 0.f;
+      uint32_t kbf[4];
+      ldsm_x4(kbf, &Ks[hh][8 * j + (lane & 7)][(lane >> 3) * 8]);
+      mma_bf16_16816(sc[j], qa[0], kbf[0], kbf[1]);
+      mma_bf16_16816(sc[j], qa[1], kbf[2], kbf[3]);
+    }
+    float bm0 = -INFINITY, bm1 = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int key = 8 * j + 2 * tq + c;
+        const bool okk = (keymask >> key) & 1ull;
+        sc[j][c] = okk ? sc[j][c] * sl2 : -INFINITY;
+        sc[j][2 + c] = okk ? sc[j][2 + c] * sl2 : -INFINITY;
+        bm0 = fmaxf(bm0, sc[j][c]);
+        bm1 = fmaxf(bm1, sc[j][2 + c]);
+      }
+    }
+    bm0 = fmaxf(bm0, __shfl_xor_sync(0xffffffffu, bm0, 1));
+    bm0 = fmaxf(bm0, __shfl_xor_sync(0xffffffffu, bm0, 2));
+    bm1 = fmaxf(bm1, __shfl_xor_sync(0xffffffffu, bm1, 1));
+    bm1 = fmaxf(bm1, __shfl_xor_sync(0xffffffffu, bm1, 2));
+    const float n0 = fmaxf(mx0, bm0), n1 = fmaxf(mx1, bm1);
+    const float a0 = exp2f(mx0 - n0), a1 = exp2f(mx1 - n1);  // 0 on the first usable block
+    mx0 = n0;
+    mx1 = n1;
+    l0 *= a0;
+    l1 *= a1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      oc[j][0] *= a0; oc[j][1] *= a0;
+      oc[j][2] *= a1; oc[j][3] *= a1;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        sc[j][c] = exp2f(sc[j][c] - mx0);
+        sc[j][2 + c] = exp2f(sc[j][2 + c] - mx1);
+        l0 += sc[j][c];
+        l1 += sc[j][2 + c];
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      uint32_t pa[4];
+      pa[0] = pack_bf16(sc[2 * kk][0], sc[2 * kk][1]);
+      pa[1] = pack_bf16(sc[2 * kk][2], sc[2 * kk][3]);
+      pa[2] = pack_bf16(sc[2 * kk + 1][0], sc[2 * kk + 1][1]);
+      pa[3] = pack_bf16(sc[2 * kk + 1][2], sc[2 * kk + 1][3]);
+#pragma unroll
+      for (int nn = 0; nn < 2; ++nn) {
+        uint32_t vb[4];
+        ldsm_x4_t(vb, &Vs[hh][16 * kk + (lane & 7) + ((lane >> 3) & 1) * 8][16 * nn + (lane >> 4) * 8]);
+        mma_bf16_16816(oc[2 * nn], pa, vb[0], vb[1]);
+        mma_bf16_16816(oc[2 * nn + 1], pa, vb[2], vb[3]);
+      }
+    }
+  }
+  l0 += __shfl_xor_sync(0xffffffffu, l0, 1);
+  l0 += __shfl_xor_sync(0xffffffffu, l0, 2);
+  l1 += __shfl_xor_sync(0xffffffffu, l1, 1);
+  l1 += __shfl_xor_sync(0xffffffffu, l1, 2);
+  const float inv0 = 1.f / l0, inv1 = 1.f / l1;
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g][8 * j + 2 * tq]) = pack_bf16(oc[j][0] * inv0, oc[j][1] * inv0);
+    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g + 8][8 * j + 2 * tq]) = pack_bf16(oc[j][2] * inv1, oc[j][3] * inv1);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = lane; e < 16 * 4; e += 32) {
+    const int s = r0 + (e >> 2), ch = e & 3;
+    const int t = stok[s];
+    if (t >= 0)
+      *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) =
+          *reinterpret_cast<const uint4*>(&Qs[hh][s][ch * 8]);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht, int Wt,
@@ -308,6 +596,17 @@ cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, u
   if (heads % HPC) return cudaErrorInvalidValue;
   dim3 grid(nwy * nwx, heads / HPC, B);
   attn_tc_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
+                                    int Wt, int d, int heads, int offset, const uint8_t* const* mem_tab, int m,
+                                    size_t off_kv, size_t off_mask, cudaStream_t st) {
+  const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
+  if (heads % HPC) return cudaErrorInvalidValue;
+  dim3 grid(nwy * nwx, heads / HPC, B);
+  attn_tc_mem_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, mem_tab,
+                                                  mem_tab ? m : 0, off_kv, off_mask);
   return cudaGetLastError();
 }
 
