@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--size", type=int, default=None, help="override H = W (small ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-memory-sweep", action="store_true",
+                    help="skip the temporal-memory leg (one 640x360 stream, m = 0, 2, 3, 4 slots)")
     ap.add_argument("--serving-seconds", type=float, default=20.0,
                     help="length of the serving run (4 collaborators, 30 fps each); 0 skips it")
     return ap.parse_args()
@@ -396,6 +398,40 @@ def main():
 
     inp.close()
 
+    # ---- temporal memory: one 640x360 stream (the paper's inference size), frame by frame,
+    # with m = 0, 2, 3, 4 memory slots; per-frame device time with CUDA events
+    memory_sweep = None
+    if not args.no_memory_sweep and args.batch is None and args.size is None:
+        from dataclasses import replace as _replace
+        Hm, Wm = 360, 640
+        xm = torch.from_numpy(S.make_frames(1, Hm, Wm, seed=7)).to(dev)
+        hm = torch.from_numpy(S.make_hole(1, Hm, Wm, "polygons", seed=7)).to(dev)
+        memory_sweep = {"workload": "one 640x360 stream (padded to 640x384), d256 h8 L8 r4 BF16, batch 1, "
+                                    "frame by frame; odd blocks temporal when m > 0",
+                        "paper_context_ms": {"2": 14.7, "3": 18.6, "4": 23.0,
+                                             "note": "RTX 3070 TensorRT FP16 modified DSTT, frame time per the "
+                                                     "paper's memory-slot table; another model and GPU"}}
+        for m in (0, 2, 3, 4):
+            cfg_m = _replace(cfg, mem_slots=m)
+            inp_m = binding.Inpainter(cfg_m, weights)
+            bufs = [inp_m.memory_buffer(Hm, Wm) for _ in range(m + 1)] if m else []
+            ev = []
+            for k in range(23):
+                slots = [[bufs[(k - 1 - j) % (m + 1)] if k - 1 - j >= 0 else None for j in range(m)]] if m else None
+                outs = [bufs[k % (m + 1)]] if m else None
+                a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                if m:
+                    inp_m.with_memory(xm, hm, slots, outs)
+                else:
+                    inp_m(xm, hm)
+                b2.record()
+                ev.append((a, b2))
+            torch.cuda.synchronize()
+            times = sorted(x.elapsed_time(y) for x, y in ev[3:])
+            memory_sweep[f"m={m}"] = {"ms_per_frame_p50": times[len(times) // 2], "ms_per_frame_min": times[0]}
+            inp_m.close()
+
     # ---- serving: 4 collaborators (256^2, 512^2, 720p, 720p) at 30 fps, continuous batching
     serving = None
     if args.serving_seconds > 0 and args.batch is None and args.size is None:
@@ -426,6 +462,7 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
             "serving": serving,
+            "memory_sweep": memory_sweep,
         }
         print(json.dumps(line))
     if dist:

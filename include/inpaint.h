@@ -223,17 +223,20 @@ INPAINT_API int inpaint_profile_read(inpaint_ctx* ctx, float* ms, int64_t* launc
  * as model inputs and outputs (Sections "Inpainting Manager", "Minimal memory slots"). */
 INPAINT_API int inpaint_memory_bytes(inpaint_ctx* ctx, int H, int W, size_t* bytes);
 
-/* As inpaint_batch, with memory.  mem_in: host array [B * m] of device pointers, frame
+/* As inpaint_batch (workspace NULL: the context's own; else as inpaint_batch_ws, with
+ * ws_bytes >= inpaint_workspace_bytes), with memory.  mem_in: host array [B * m] of device pointers, frame
  * b's slots at [b*m .. b*m + m-1], each a previous frame's memory buffer of the same
  * H x W, or NULL for an empty slot (the array itself may be NULL: no memory).  mem_out:
  * host array [B] of device buffers (inpaint_memory_bytes each, NULL = not recorded) that
  * receive each frame's own memory tensor.  Buffers must be 256-byte aligned and are
  * owned by the caller; an output buffer must not also be an input of the same call.
- * With every slot empty the result equals inpaint_batch.  Errors: E_INVAL (m = 0 with
- * memory arguments, misaligned buffers, shapes), E_NOMEM, E_CUDA. */
-INPAINT_API int inpaint_batch_mem(inpaint_ctx* ctx, const float* x, const uint8_t* hole, int B, int H, int W,
-                                  float* out, float* pred, const void* const* mem_in, void* const* mem_out,
-                                  void* stream);
+ * B * m may be at most 512 (the slot table travels in the kernel parameters, so the call
+ * makes no host-to-device copy).  With every slot empty the result equals inpaint_batch.
+ * Errors: E_INVAL (m = 0 with memory arguments, B * m > 512, misaligned buffers,
+ * shapes), E_NOMEM, E_CUDA. */
+INPAINT_API int inpaint_batch_mem(inpaint_ctx* ctx, void* workspace, size_t ws_bytes, const float* x,
+                                  const uint8_t* hole, int B, int H, int W, float* out, float* pred,
+                                  const void* const* mem_in, void* const* mem_out, void* stream);
 
 /* Number of kernels this context has launched since creation. */
 INPAINT_API int inpaint_launch_count(inpaint_ctx* ctx, int64_t* count);

@@ -51,7 +51,7 @@ _I = ctypes.c_int
 _SIGS = {
     "inpaint_strerror": (ctypes.c_char_p, [_I]),
     "inpaint_memory_bytes": (_I, [_P, _I, _I, _P]),
-    "inpaint_batch_mem": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P]),
+    "inpaint_batch_mem": (_I, [_P, _P, ctypes.c_size_t, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P]),
     "inpaint_last_cuda_error": (_I, []),
     "inpaint_cuda_error_name": (ctypes.c_char_p, [_I]),
     "inpaint_num_params": (_I, [ctypes.POINTER(InpaintConfig), ctypes.POINTER(ctypes.c_size_t)]),
@@ -189,10 +189,12 @@ def inpaint_memory_bytes(ctx, H: int, W: int) -> int:
     return n.value
 
 
-def inpaint_batch_mem(ctx, x, hole, out, mem_in, mem_out, pred=None, stream=None):
+def inpaint_batch_mem(ctx, x, hole, out, mem_in, mem_out, pred=None, stream=None, workspace=None):
     """mem_in: list over frames of lists of m device buffers (uint8 CUDA tensors) or None;
-    mem_out: list over frames of a device buffer or None."""
+    mem_out: list over frames of a device buffer or None; workspace: None (the context's)
+    or a uint8 CUDA tensor of at least inpaint_workspace_bytes."""
     B, H, W = hole.shape
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     tab_in = None
     if mem_in is not None:
         flat = [None if t is None else _ptr(t).value for slots in mem_in for t in slots]
@@ -200,8 +202,8 @@ def inpaint_batch_mem(ctx, x, hole, out, mem_in, mem_out, pred=None, stream=None
     tab_out = None
     if mem_out is not None:
         tab_out = (ctypes.c_void_p * B)(*[None if t is None else _ptr(t).value for t in mem_out])
-    _check(load().inpaint_batch_mem(ctx, _ptr(x), _ptr(hole), B, H, W, _ptr(out), _ptr(pred), tab_in, tab_out,
-                                    _stream(stream)), "inpaint_batch_mem")
+    _check(load().inpaint_batch_mem(ctx, _ptr(workspace), nbytes, _ptr(x), _ptr(hole), B, H, W, _ptr(out), _ptr(pred),
+                                    tab_in, tab_out, _stream(stream)), "inpaint_batch_mem")
 
 
 def inpaint_batch_ws(ctx, workspace, x, hole, out, pred=None, stream=None):

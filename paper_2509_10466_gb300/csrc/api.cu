@@ -121,7 +121,6 @@ Plan make_plan(const inpaint_ctx* c, int B, int H, int W) {
   p.f1 = take((size_t)B * (2 * p.Ht) * (2 * p.Wt) * c->c1 * es);
   p.f2 = take((size_t)B * p.Hp * p.Wp * c->c2 * es);
   p.err = take(256);
-  p.memtab = take((size_t)B * (c->cfg.mem_slots > 0 ? c->cfg.mem_slots : 1) * sizeof(void*));
   p.end = q;
   return p;
 }
@@ -220,7 +219,7 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     // temporal block: the queries also see the memory slots' keys of this block, and each
     // frame's own k | v and key mask here become part of its memory tensor
     const bool temporal = c->cfg.mem_slots > 0 && (l & 1);
-    const uint8_t* const* mtab = mem ? mem->tab : nullptr;
+    const MemTab* mtab = mem ? mem->tab : nullptr;
     const size_t moff = mem ? (size_t)(l / 2) * mem->lay.stride : 0, mkv = mem ? mem->lay.kv_bytes : 0;
     auto record_memory = [&](const void* qkv_any) -> int {
       if (!mem || !mem->out) return INPAINT_OK;
@@ -496,37 +495,40 @@ int inpaint_memory_bytes(inpaint_ctx* c, int H, int W, size_t* bytes) {
   return INPAINT_OK;
 }
 
-int inpaint_batch_mem(inpaint_ctx* c, const float* x, const uint8_t* hole, int B, int H, int W, float* out,
-                      float* pred, const void* const* mem_in, void* const* mem_out, void* stream) {
+int inpaint_batch_mem(inpaint_ctx* c, void* workspace, size_t ws_bytes, const float* x, const uint8_t* hole, int B,
+                      int H, int W, float* out, float* pred, const void* const* mem_in, void* const* mem_out,
+                      void* stream) {
   if (!c || !x || !hole || !out || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return INPAINT_E_INVAL;
   const int m = c->cfg.mem_slots;
   if (m == 0 && (mem_in || mem_out)) return INPAINT_E_INVAL;
   auto misaligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 255) != 0; };
-  std::vector<const uint8_t*> tab;
-  if (mem_in) {
-    tab.resize((size_t)B * m);
-    for (size_t i = 0; i < tab.size(); ++i) {
-      tab[i] = static_cast<const uint8_t*>(mem_in[i]);
-      if (tab[i] && misaligned(tab[i])) return INPAINT_E_INVAL;
+  if (mem_in && (size_t)B * m > (size_t)MEM_TAB_MAX) return INPAINT_E_INVAL;
+  MemTab tab{};
+  if (mem_in)
+    for (int i = 0; i < B * m; ++i) {
+      tab.p[i] = static_cast<const uint8_t*>(mem_in[i]);
+      if (tab.p[i] && misaligned(tab.p[i])) return INPAINT_E_INVAL;
     }
-  }
   if (mem_out)
     for (int b = 0; b < B; ++b)
       if (mem_out[b] && misaligned(mem_out[b])) return INPAINT_E_INVAL;
   const Plan p = make_plan(c, B, H, W);
-  TRY(grow(&c->arena, &c->arena_bytes, p.end, c, c->stage_bytes + c->bws_bytes));
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  if (ws) {
+    if (ws_bytes < p.end) return INPAINT_E_INVAL;
+  } else {
+    TRY(grow(&c->arena, &c->arena_bytes, p.end, c, c->stage_bytes + c->bws_bytes));
+    ws = c->arena;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   MemArgs ma;
   ma.lay = mem_layout(c, p.Nt);
   ma.out = reinterpret_cast<uint8_t* const*>(mem_out);
-  if (mem_in) {
-    // the pointer table travels with the stream (a pageable source is staged before return)
-    TRY(cuda_err(cudaMemcpyAsync(c->arena + p.memtab, tab.data(), tab.size() * sizeof(void*), cudaMemcpyHostToDevice,
-                                 st)));
-    ma.tab = reinterpret_cast<const uint8_t* const*>(c->arena + p.memtab);
-  }
+  if (mem_in) ma.tab = &tab;  // passed by value in each attention launch
+  if (ws != c->arena) return run_forward(c, ws, p, x, hole, out, pred, st, &ma);
   c->have_masks = false;
-  TRY(run_forward(c, c->arena, p, x, hole, out, pred, st, &ma));
+  TRY(run_forward(c, ws, p, x, hole, out, pred, st, &ma));
   c->last = p;
   c->have_masks = true;
   return INPAINT_OK;

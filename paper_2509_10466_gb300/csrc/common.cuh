@@ -128,16 +128,21 @@ cudaError_t launch_attention(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v
 cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
                                 int Wt, int d, int heads, int offset, cudaStream_t st);
 
-// Temporal blocks: as above, plus the keys of m memory slots.  mem_tab [B][m] holds device
-// pointers to previous frames' memory buffers (null = empty slot); a buffer holds, at
-// off_kv, k | v rows [Nt][2d] (T) and, at off_mask, the usable-key mask [Nt] of this block.
+// Temporal blocks: as above, plus the keys of m memory slots.  tab->p[b*m + j] is a device
+// pointer to a previous frame's memory buffer (null = empty slot; tab null = no memory);
+// a buffer holds, at off_kv, k | v rows [Nt][2d] (T) and, at off_mask, the usable-key
+// mask [Nt] of this block.  The table travels by value in the kernel parameters.
+constexpr int MEM_TAB_MAX = 512;
+struct MemTab {
+  const uint8_t* p[MEM_TAB_MAX];
+};
 template <typename T>
 cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
-                                 int heads, int offset, const uint8_t* const* mem_tab, int m, size_t off_kv,
-                                 size_t off_mask, cudaStream_t st);
+                                 int heads, int offset, const MemTab* tab, int m, size_t off_kv, size_t off_mask,
+                                 cudaStream_t st);
 cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
-                                    int Wt, int d, int heads, int offset, const uint8_t* const* mem_tab, int m,
-                                    size_t off_kv, size_t off_mask, cudaStream_t st);
+                                    int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
+                                    size_t off_mask, cudaStream_t st);
 
 // Decoder stage: out = gelu(conv3x3(upsample2(in)) + bias), NHWC.  wt: [9][Cin][Cout] f32.
 template <typename T>

@@ -28,7 +28,7 @@ using inpaint::BlockOff;
 
 struct Plan {
   int B, H, W, Hp, Wp, Ht, Wt, Nt, M;
-  size_t tok, ln, qkv, o, hid, masks, f1, f2, err, memtab, end;
+  size_t tok, ln, qkv, o, hid, masks, f1, f2, err, end;
 };
 
 // One frame's memory tensor (temporal blocks l = 1, 3, ...; block l at (l / 2) * stride):
@@ -37,11 +37,11 @@ struct MemLayout {
   size_t kv_bytes = 0, stride = 0, total = 0;
 };
 
-// Memory slots of one batched call: tab = device table [B][m] of previous frames'
-// buffers (null entries = empty slots, the table itself null = no memory), out = host
-// array [B] of this call's output buffers (null = do not record).
+// Memory slots of one batched call: tab = table [B][m] of previous frames' buffers (null
+// entries = empty slots, the table itself null = no memory), out = host array [B] of this
+// call's output buffers (null = do not record).
 struct MemArgs {
-  const uint8_t* const* tab = nullptr;
+  const inpaint::MemTab* tab = nullptr;
   uint8_t* const* out = nullptr;
   MemLayout lay;
 };

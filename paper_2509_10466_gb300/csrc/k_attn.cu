@@ -92,8 +92,9 @@ template <typename T>
 __global__ void __launch_bounds__(SLOTS) attn_simt_mem_kernel(const T* __restrict__ qkv,
                                                               const uint8_t* __restrict__ v_in, T* __restrict__ o,
                                                               uint8_t* __restrict__ v_out, int Ht, int Wt, int d,
-                                                              int offset, int nwx, const uint8_t* const* mem_tab,
-                                                              int m, size_t off_kv, size_t off_mask) {
+                                                              int offset, int nwx,
+                                                              const __grid_constant__ MemTab mem_tab, int m,
+                                                              size_t off_kv, size_t off_mask) {
   __shared__ float Ks[SLOTS][DH + 1];
   __shared__ float Vs[SLOTS][DH + 1];
   __shared__ int okS[SLOTS];
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_mem_kernel(const T* __restric
   auto key_row = [&](int kb) -> const T* {
     if (!real) return nullptr;
     if (kb == 0) return v_in[t] ? qkv + t * 3 * d + d : nullptr;
-    const uint8_t* base = mem_tab[(size_t)b * m + kb - 1];
+    const uint8_t* base = mem_tab.p[b * m + kb - 1];
     if (!base || !base[off_mask + i]) return nullptr;
     return reinterpret_cast<const T*>(base + off_kv) + i * 2 * d;
   };
@@ -195,19 +196,21 @@ template cudaError_t launch_attention<bf16>(const bf16*, const uint8_t*, bf16*, 
 
 template <typename T>
 cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
-                                 int heads, int offset, const uint8_t* const* mem_tab, int m, size_t off_kv,
-                                 size_t off_mask, cudaStream_t st) {
+                                 int heads, int offset, const MemTab* tab, int m, size_t off_kv, size_t off_mask,
+                                 cudaStream_t st) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
+  if (tab && (size_t)B * m > (size_t)MEM_TAB_MAX) return cudaErrorInvalidValue;
+  static const MemTab none{};
   dim3 grid(nwy * nwx, heads, B);
-  attn_simt_mem_kernel<T><<<grid, SLOTS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, mem_tab,
-                                                  mem_tab ? m : 0, off_kv, off_mask);
+  attn_simt_mem_kernel<T><<<grid, SLOTS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, tab ? *tab : none,
+                                                  tab ? m : 0, off_kv, off_mask);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_attention_mem<float>(const float*, const uint8_t*, float*, uint8_t*, int, int, int, int,
-                                                 int, int, const uint8_t* const*, int, size_t, size_t, cudaStream_t);
+                                                 int, int, const MemTab*, int, size_t, size_t, cudaStream_t);
 template cudaError_t launch_attention_mem<bf16>(const bf16*, const uint8_t*, bf16*, uint8_t*, int, int, int, int, int,
-                                                int, const uint8_t* const*, int, size_t, size_t, cudaStream_t);
+                                                int, const MemTab*, int, size_t, size_t, cudaStream_t);
 
 }  // namespace inpaint
 
@@ -419,7 +422,7 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
                                                                  const uint8_t* __restrict__ v_in,
                                                                  bf16* __restrict__ o, uint8_t* __restrict__ v_out,
                                                                  int Ht, int Wt, int d, int offset, int nwx,
-                                                                 const uint8_t* const* mem_tab, int m,
+                                                                 const __grid_constant__ MemTab mem_tab, int m,
                                                                  size_t off_kv, size_t off_mask) {
   __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
   __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
     stok[tid] = real ? b * Nt + ty * Wt + tx : -1;
     bool any = real && v_in[b * Nt + ty * Wt + tx] != 0;
     for (int j = 0; j < m && !any; ++j) {
-      const uint8_t* base = mem_tab[(size_t)b * m + j];
+      const uint8_t* base = mem_tab.p[b * m + j];
       any = real && base && base[off_mask + ty * Wt + tx] != 0;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, any);
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
   for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
   uint32_t qa[2][4];
   for (int kb = 0; kb <= m; ++kb) {
-    const uint8_t* base = kb == 0 ? nullptr : mem_tab[(size_t)b * m + kb - 1];
+    const uint8_t* base = kb == 0 ? nullptr : mem_tab.p[b * m + kb - 1];
     if (kb > 0 && !base) continue;  // an empty memory slot (uniform across the CTA)
     __syncthreads();                // the previous block's K / V are no longer read
     if (tid < SLOTS) {
@@ -600,13 +603,15 @@ cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, u
 }
 
 cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
-                                    int Wt, int d, int heads, int offset, const uint8_t* const* mem_tab, int m,
-                                    size_t off_kv, size_t off_mask, cudaStream_t st) {
+                                    int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
+                                    size_t off_mask, cudaStream_t st) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   if (heads % HPC) return cudaErrorInvalidValue;
+  if (tab && (size_t)B * m > (size_t)MEM_TAB_MAX) return cudaErrorInvalidValue;
+  static const MemTab none{};
   dim3 grid(nwy * nwx, heads / HPC, B);
-  attn_tc_mem_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, mem_tab,
-                                                  mem_tab ? m : 0, off_kv, off_mask);
+  attn_tc_mem_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, tab ? *tab : none,
+                                                  tab ? m : 0, off_kv, off_mask);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,11 @@ Requests that arrive while others are on the GPU join the next batches as slots 
 memory free up, and batches on different streams overlap on the device.  The kernels
 are batch-invariant, so a frame's result is the same alone and in the mix.
 
+With temporal memory (m slots), a collaborator's frame reads the memory tensors of its
+m previous frames: a batch then takes at most one frame per collaborator (in arrival
+order), and the executor keeps each collaborator's ring of m + 1 memory buffers on the
+device and orders a frame after its predecessor's batch with a CUDA event.
+
 The scheduler is written against an executor interface (`launch`, `poll`, `bytes_for`)
 so that its admission and failure logic is tested on the CPU with a fake device;
 `GpuExecutor` runs the real library on CUDA streams.
@@ -68,7 +73,8 @@ class Scheduler:
     """
 
     def __init__(self, executor, slots: int = 4, max_batch: int = 4, hbm_budget: int = 8 << 30,
-                 timeout_s: float = 5.0, clock: Callable[[], float] = time.perf_counter, keep_outputs: bool = False):
+                 timeout_s: float = 5.0, clock: Callable[[], float] = time.perf_counter, keep_outputs: bool = False,
+                 one_per_collab: bool = False):
         if slots < 1 or max_batch < 1:
             raise ValueError("slots and max_batch must be >= 1")
         self.ex = executor
@@ -78,6 +84,7 @@ class Scheduler:
         self.timeout = timeout_s
         self.clock = clock
         self.keep_outputs = keep_outputs
+        self.one_per_collab = one_per_collab
         self.queues: Dict[tuple, collections.deque] = collections.OrderedDict()
         self.running: List[Batch] = []
         self.in_use = 0
@@ -145,9 +152,18 @@ class Scheduler:
             if key is None:
                 return
             q = self.queues[key]
-            n = 0
-            while n < len(q) and n < self.max_batch and q[n].arrival <= now:
-                n += 1
+            # candidates in arrival order; with one_per_collab a collaborator's later frames
+            # wait for a later batch (they read the memory its earlier frame writes)
+            pick, seen = [], set()
+            for i, r in enumerate(q):
+                if len(pick) == self.max_batch or r.arrival > now:
+                    break
+                if self.one_per_collab:
+                    if r.collab in seen:
+                        continue
+                    seen.add(r.collab)
+                pick.append(i)
+            n = len(pick)
             H, W = key
             need = self.ex.bytes_for(n, H, W)
             while n > 1 and self.in_use + need > self.budget:
@@ -158,7 +174,9 @@ class Scheduler:
                     raise SchedulerError(f"a single {H}x{W} frame needs {need} B, above the budget {self.budget} B")
                 self.admission_waits += 1
                 return
-            reqs = [q.popleft() for _ in range(n)]
+            chosen = set(pick[:n])
+            reqs = [q[i] for i in pick[:n]]
+            self.queues[key] = q = collections.deque(r for i, r in enumerate(q) if i not in chosen)
             slot = self.slots_free.pop(0)
             b = Batch(reqs, H, W, need, slot)
             for r in reqs:
@@ -249,6 +267,10 @@ class GpuExecutor:
         self.binding = binding
         self.inp = inpainter
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.m = inpainter.cfg.mem_slots
+        self.rings: Dict[int, list] = {}       # collaborator -> m + 1 memory buffers
+        self.count: Dict[int, int] = {}        # collaborator -> frames launched
+        self.last_ev: Dict[int, object] = {}   # collaborator -> event of its latest batch
 
     def bytes_for(self, B, H, W):
         ws = self.binding.inpaint_workspace_bytes(self.inp.ctx, B, H, W)
@@ -267,11 +289,29 @@ class GpuExecutor:
             for i, r in enumerate(b.reqs):
                 x[i].copy_(r.x, non_blocking=True)
                 hole[i].copy_(r.hole, non_blocking=True)
-            self.binding.inpaint_batch_ws(self.inp.ctx, ws, x, hole, out, None, st)
+            if self.m == 0:
+                self.binding.inpaint_batch_ws(self.inp.ctx, ws, x, hole, out, None, st)
+            else:
+                mem_in, mem_out = [], []
+                for r in b.reqs:
+                    c = r.collab
+                    if c not in self.rings:
+                        self.rings[c] = [self.inp.memory_buffer(H, W) for _ in range(self.m + 1)]
+                        self.count[c] = 0
+                    ring, k = self.rings[c], self.count[c]
+                    mem_in.append([ring[(k - 1 - j) % (self.m + 1)] if k - 1 - j >= 0 else None for j in range(self.m)])
+                    mem_out.append(ring[k % (self.m + 1)])
+                    self.count[c] = k + 1
+                    if c in self.last_ev:
+                        st.wait_event(self.last_ev[c])
+                self.binding.inpaint_batch_mem(self.inp.ctx, x, hole, out, mem_in, mem_out, None, st, workspace=ws)
             host = torch.empty((B, 3, H, W), dtype=torch.float32, pin_memory=True)
             host.copy_(out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
+            if self.m:
+                for r in b.reqs:
+                    self.last_ev[r.collab] = ev
         return (ev, host, (ws, x, hole, out))
 
     def poll(self, handle):
@@ -308,9 +348,10 @@ def serve(cfg, weights, resolutions=((256, 256), (512, 512), (720, 1280), (720, 
         ex = GpuExecutor(inp, slots)
         pool = make_collaborator_frames(resolutions, seed=seed)
         # warm up each resolution once (kernel attributes, allocator)
-        for (H, W) in sorted(set(resolutions)):
+        for i, (H, W) in enumerate(sorted(set(resolutions))):
             xs, hs = pool[resolutions.index((H, W))]
-            b = Batch([Request(-1, 0, H, W, 0.0, xs[0], hs[0])], H, W, 0, 0)
+            # a collaborator id of its own: warm-up frames do not enter a stream's memory
+            b = Batch([Request(-1, -1 - i, H, W, 0.0, xs[0], hs[0])], H, W, 0, 0)
             h = ex.launch(b)
             h[0].synchronize()
         reqs = poisson_requests(resolutions, fps, seconds, seed)
@@ -318,7 +359,8 @@ def serve(cfg, weights, resolutions=((256, 256), (512, 512), (720, 1280), (720, 
             xs, hs = pool[r.collab]
             k = r.rid % len(xs)
             r.x, r.hole = xs[k], hs[k]
-        sch = Scheduler(ex, slots=slots, max_batch=max_batch, hbm_budget=hbm_budget, keep_outputs=keep_outputs)
+        sch = Scheduler(ex, slots=slots, max_batch=max_batch, hbm_budget=hbm_budget, keep_outputs=keep_outputs,
+                        one_per_collab=cfg.mem_slots > 0)
         wall0 = time.perf_counter()
         sch.run(reqs)
         torch.cuda.synchronize()

@@ -123,3 +123,28 @@ def test_poisson_workload_shape():
     assert 2200 < len(reqs) < 2600
     assert all(a.arrival <= b.arrival for a, b in zip(reqs, reqs[1:]))
     assert {(r.H, r.W) for r in reqs} == {(256, 256), (512, 512), (720, 1280)}
+
+
+def test_with_memory_a_batch_takes_one_frame_per_collaborator_in_order():
+    """With temporal memory a frame reads what its collaborator's previous frame writes:
+    no batch holds two frames of one collaborator, and each collaborator's frames are
+    launched in arrival order, while other collaborators still share batches."""
+    clock = Clock()
+    dev = FakeDevice(clock, per_frame=0.005)
+    sch = Scheduler(dev, slots=2, max_batch=4, hbm_budget=1 << 40, clock=clock, one_per_collab=True)
+    reqs = []
+    for k in range(6):                 # collaborators 0 and 1 queue 3 frames each at t = 0
+        reqs.append(Request(k, k % 2, 64, 64, 0.0))
+    reqs.append(Request(6, 2, 64, 64, 0.0))
+    drive(sch, clock, reqs)
+    assert all(r.status == "done" for r in sch.finished) and len(sch.finished) == 7
+    collab = {r.rid: r.collab for r in reqs}
+    seen = {}
+    for batch in dev.launched:
+        cs = [collab[i] for i in batch]
+        assert len(cs) == len(set(cs)), batch
+        for i in batch:
+            c = collab[i]
+            assert seen.get(c, -1) < i
+            seen[c] = i
+    assert max(len(b) for b in dev.launched) >= 2

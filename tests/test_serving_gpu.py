@@ -32,3 +32,30 @@ def test_each_result_is_the_same_alone_and_in_the_mix(precision):
             assert torch.equal(alone[0].cpu(), r.out), (r.rid, r.H, r.W)
     finally:
         inp.close()
+
+
+def test_with_memory_each_stream_matches_its_frames_run_alone_in_order():
+    """Temporal memory in the serving loop: every collaborator's frames, replayed alone in
+    order with the same memory rotation, give the same bytes as in the mix."""
+    lib()
+    cfg = ModelConfig(dim=64, heads=2, window=8, blocks=4, mlp_ratio=2, precision=BF16, mem_slots=2)
+    weights = S.make_weights(cfg, seed=9, perturb=True)
+    res = ((64, 64), (96, 160), (96, 160))
+    rep, finished = serve(cfg, weights, resolutions=res, fps=60, seconds=0.6, slots=3, max_batch=3,
+                          keep_outputs=True)
+    assert rep["status"].get("done", 0) == rep["requests"]
+    inp = binding.Inpainter(cfg, weights)
+    try:
+        for c in range(len(res)):
+            mine = sorted((r for r in finished if r.collab == c), key=lambda r: r.rid)
+            H, W = res[c]
+            bufs = []
+            for k, r in enumerate(mine):
+                slots = [bufs[k - 1 - j] if k - 1 - j >= 0 else None for j in range(2)]
+                buf = inp.memory_buffer(H, W)
+                alone = inp.with_memory(r.x[None].cuda(), r.hole[None].cuda(), [slots], [buf])
+                torch.cuda.synchronize()
+                bufs.append(buf)
+                assert torch.equal(alone[0].cpu(), r.out), (c, k, r.rid)
+    finally:
+        inp.close()
