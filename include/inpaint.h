@@ -208,10 +208,10 @@ INPAINT_API int inpaint_sync(inpaint_ctx* ctx, void* stream, int timeout_ms);
  * each kernel launch of the context is bracketed by an event pair.  Classes:
  * 0 embed, 1 layernorm, 2 qkv gemm, 3 attention, 4 proj gemm, 5 fc1 gemm, 6 fc2 gemm,
  * 7 decoder stage 1, 8 decoder stage 2, 9 head + composite, 10 other, 11 fused MLP
- * (fc1 + GELU + fc2 + residual + LayerNorm in one kernel).
+ * (fc1 + GELU + fc2 + residual + LayerNorm in one kernel), 12 point cloud, 13 splat.
  * inpaint_profile_read synchronizes and returns total milliseconds and launch
  * counts per class (arrays of INPAINT_PROFILE_CLASSES), then clears them. */
-#define INPAINT_PROFILE_CLASSES 12
+#define INPAINT_PROFILE_CLASSES 14
 INPAINT_API int inpaint_profile_enable(inpaint_ctx* ctx, int on);
 INPAINT_API int inpaint_profile_read(inpaint_ctx* ctx, float* ms, int64_t* launches);
 
@@ -237,6 +237,33 @@ INPAINT_API int inpaint_memory_bytes(inpaint_ctx* ctx, int H, int W, size_t* byt
 INPAINT_API int inpaint_batch_mem(inpaint_ctx* ctx, void* workspace, size_t ws_bytes, const float* x,
                                   const uint8_t* hole, int B, int H, int W, float* out, float* pred,
                                   const void* const* mem_in, void* const* mem_out, void* stream);
+
+/* Coloured point cloud of an inpainted frame (the paper transplants the inpainted RGB
+ * onto the depth measurements, Section "Point Cloud Visualisation", and maps camera
+ * points into the viewer's world with p' = R p + t, Section "Perspective Alignment").
+ * depth: device float [H][W] (a pixel is a point when its depth is finite and > 0);
+ * rgb: device float [3][H][W]; cam: host float[4] = fx, fy, cx, cy of the pinhole
+ * camera (pixel centres at +0.5); rt: host float[12] = R (row-major) then t, camera to
+ * world.  points: device float [H*W][6] = world x, y, z (NaN for non-points), r, g, b.
+ * Back-projection x = d (u + 0.5 - cx) / fx, y = d (v + 0.5 - cy) / fy, z = d; every
+ * operation rounded separately (no fused multiply-add), so results are reproducible bit
+ * for bit.  Errors: E_INVAL, E_CUDA. */
+INPAINT_API int inpaint_point_cloud(inpaint_ctx* ctx, const float* depth, const float* rgb, int H, int W,
+                                    const float* cam, const float* rt, float* points, void* stream);
+
+/* Headless z-buffered splat of a point cloud (device [n_points][6] as above) into an
+ * Ho x Wo image at a remote viewpoint: q = R p + t with rt = world to viewer (host
+ * float[12]); points with q_z > 1e-3 cover pixel (floor(fy q_y / q_z + cy),
+ * floor(fx q_x / q_z + cx)) of the view camera (host float[4]) when inside the image;
+ * per pixel the nearest point wins, equal depths the lower point index.  Outputs
+ * (device): img float [3][Ho][Wo] (0 where empty), depth_out float [Ho][Wo] (q_z, +inf
+ * where empty) and index_out int32 [Ho][Wo] (winning point, -1 where empty); the last
+ * two may be NULL.  Uses a scratch buffer of the context (one splat in flight per
+ * context).  The paper renders with OpenGL; this path has no graphics API.  Errors:
+ * E_INVAL, E_NOMEM, E_CUDA. */
+INPAINT_API int inpaint_point_splat(inpaint_ctx* ctx, const float* points, int64_t n_points, const float* view,
+                                    const float* rt, int Ho, int Wo, float* img, float* depth_out, int32_t* index_out,
+                                    void* stream);
 
 /* Number of kernels this context has launched since creation. */
 INPAINT_API int inpaint_launch_count(inpaint_ctx* ctx, int64_t* count);

@@ -18,9 +18,9 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libinpaint
 _lib = None
 
 INPAINT_OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE, E_DEVICE = range(7)
-PROFILE_CLASSES = 12
+PROFILE_CLASSES = 14
 PROFILE_NAMES = ("embed", "layernorm", "qkv_gemm", "attention", "proj_gemm", "fc1_gemm", "fc2_gemm",
-                 "decoder1", "decoder2", "head_composite", "other", "mlp_fused")
+                 "decoder1", "decoder2", "head_composite", "other", "mlp_fused", "point_cloud", "splat")
 
 
 class InpaintError(RuntimeError):
@@ -51,6 +51,8 @@ _I = ctypes.c_int
 _SIGS = {
     "inpaint_strerror": (ctypes.c_char_p, [_I]),
     "inpaint_memory_bytes": (_I, [_P, _I, _I, _P]),
+    "inpaint_point_cloud": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "inpaint_point_splat": (_I, [_P, _P, ctypes.c_int64, _P, _P, _I, _I, _P, _P, _P, _P]),
     "inpaint_batch_mem": (_I, [_P, _P, ctypes.c_size_t, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P]),
     "inpaint_last_cuda_error": (_I, []),
     "inpaint_cuda_error_name": (ctypes.c_char_p, [_I]),
@@ -204,6 +206,29 @@ def inpaint_batch_mem(ctx, x, hole, out, mem_in, mem_out, pred=None, stream=None
         tab_out = (ctypes.c_void_p * B)(*[None if t is None else _ptr(t).value for t in mem_out])
     _check(load().inpaint_batch_mem(ctx, _ptr(workspace), nbytes, _ptr(x), _ptr(hole), B, H, W, _ptr(out), _ptr(pred),
                                     tab_in, tab_out, _stream(stream)), "inpaint_batch_mem")
+
+
+def _host_f32(vals, n):
+    a = (ctypes.c_float * n)(*[float(v) for v in np.asarray(vals, dtype=np.float64).reshape(-1)])
+    return a
+
+
+def inpaint_point_cloud(ctx, depth, rgb, cam, R, t, points, stream=None):
+    """depth [H, W], rgb [3, H, W] and points [H*W, 6] are float32 CUDA tensors; cam =
+    (fx, fy, cx, cy); R [3, 3] and t [3] map camera points to the world."""
+    H, W = depth.shape
+    rt = np.concatenate([np.asarray(R, np.float64).reshape(9), np.asarray(t, np.float64).reshape(3)])
+    _check(load().inpaint_point_cloud(ctx, _ptr(depth), _ptr(rgb), H, W, _host_f32(cam, 4), _host_f32(rt, 12),
+                                      _ptr(points), _stream(stream)), "inpaint_point_cloud")
+
+
+def inpaint_point_splat(ctx, points, view, R, t, img, depth_out=None, index_out=None, stream=None):
+    """points [N, 6]; img [3, Ho, Wo]; depth_out [Ho, Wo] float32; index_out [Ho, Wo] int32."""
+    _, Ho, Wo = img.shape
+    rt = np.concatenate([np.asarray(R, np.float64).reshape(9), np.asarray(t, np.float64).reshape(3)])
+    _check(load().inpaint_point_splat(ctx, _ptr(points), points.shape[0], _host_f32(view, 4), _host_f32(rt, 12), Ho,
+                                      Wo, _ptr(img), _ptr(depth_out), _ptr(index_out), _stream(stream)),
+           "inpaint_point_splat")
 
 
 def inpaint_batch_ws(ctx, workspace, x, hole, out, pred=None, stream=None):

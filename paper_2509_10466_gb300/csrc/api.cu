@@ -389,6 +389,7 @@ void inpaint_destroy(inpaint_ctx* c) {
   cudaFree(c->stage);
   cudaFree(c->bws);
   cudaFree(c->pp);
+  cudaFree(c->zbuf);
   for (auto& e : c->events) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -532,6 +533,27 @@ int inpaint_batch_mem(inpaint_ctx* c, void* workspace, size_t ws_bytes, const fl
   c->last = p;
   c->have_masks = true;
   return INPAINT_OK;
+}
+
+int inpaint_point_cloud(inpaint_ctx* c, const float* depth, const float* rgb, int H, int W, const float* cam,
+                        const float* rt, float* points, void* stream) {
+  if (!c || !depth || !rgb || !cam || !rt || !points || H < 1 || W < 1 || (size_t)H * W > ((size_t)1 << 30))
+    return INPAINT_E_INVAL;
+  if (!(cam[0] != 0.f && cam[1] != 0.f)) return INPAINT_E_INVAL;
+  LaunchScope ls(c, (cudaStream_t)stream, K_CLOUD);
+  return cuda_err(launch_point_cloud(depth, rgb, H, W, cam, rt, points, (cudaStream_t)stream));
+}
+
+int inpaint_point_splat(inpaint_ctx* c, const float* points, int64_t n_points, const float* view, const float* rt,
+                        int Ho, int Wo, float* img, float* depth_out, int32_t* index_out, void* stream) {
+  if (!c || (!points && n_points > 0) || n_points < 0 || n_points > ((int64_t)1 << 32) - 1 || !view || !rt || !img ||
+      Ho < 1 || Wo < 1 || (size_t)Ho * Wo > ((size_t)1 << 30))
+    return INPAINT_E_INVAL;
+  const size_t need = (size_t)Ho * Wo * sizeof(unsigned long long);
+  TRY(grow(&c->zbuf, &c->zbuf_bytes, need, c, c->arena_bytes + c->stage_bytes + c->bws_bytes + c->pp_bytes));
+  LaunchScope ls(c, (cudaStream_t)stream, K_SPLAT);
+  return cuda_err(launch_splat(points, n_points, view, rt, Ho, Wo, reinterpret_cast<unsigned long long*>(c->zbuf), img,
+                               depth_out, index_out, (cudaStream_t)stream));
 }
 
 int inpaint_frame(inpaint_ctx* c, const float* x, const uint8_t* hole, int H, int W, float* out, void* stream) {

@@ -15,7 +15,7 @@ typedef __nv_bfloat16 bf16;
 // Kernel-class ids for event timing (match INPAINT_PROFILE_CLASSES in inpaint.h).
 enum KClass {
   K_EMBED = 0, K_LN = 1, K_QKV = 2, K_ATTN = 3, K_PROJ = 4, K_FC1 = 5, K_FC2 = 6,
-  K_DEC1 = 7, K_DEC2 = 8, K_HEAD = 9, K_OTHER = 10, K_MLP = 11
+  K_DEC1 = 7, K_DEC2 = 8, K_HEAD = 9, K_OTHER = 10, K_MLP = 11, K_CLOUD = 12, K_SPLAT = 13
 };
 
 // Device-side error codes written into the context's error word.
@@ -143,6 +143,14 @@ cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_
 cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
                                     int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
                                     size_t off_mask, cudaStream_t st);
+
+// Coloured point cloud (world x, y, z, r, g, b per pixel; NaN coordinates where the depth
+// is not usable) and z-buffered splat into an Ho x Wo image.  cam / view: fx, fy, cx, cy;
+// rt: R row-major (9) then t (3), host arrays.  keys: Ho*Wo scratch.
+cudaError_t launch_point_cloud(const float* depth, const float* rgb, int H, int W, const float* cam, const float* rt,
+                               float* pts, cudaStream_t st);
+cudaError_t launch_splat(const float* pts, int64_t N, const float* view, const float* rt, int Ho, int Wo,
+                         unsigned long long* keys, float* img, float* dep, int32_t* ind, cudaStream_t st);
 
 // Decoder stage: out = gelu(conv3x3(upsample2(in)) + bias), NHWC.  wt: [9][Cin][Cout] f32.
 template <typename T>

@@ -82,6 +82,9 @@ struct inpaint_ctx {
   // backward scratch
   uint8_t* bws = nullptr;
   size_t bws_bytes = 0;
+  // z-buffer keys of inpaint_point_splat
+  uint8_t* zbuf = nullptr;
+  size_t zbuf_bytes = 0;
   // profiling
   bool prof = false;
   std::vector<EventPair> events;
