@@ -80,6 +80,10 @@ typedef struct inpaint_config {
                          temporal: their queries also attend to the keys / values that up
                          to m previous frames produced in the same block (memory tensors;
                          see inpaint_batch_mem).  0 = single-frame spatial model. */
+  int32_t pos_bias;   /* 1 = learned relative-position bias in every window softmax: a
+                         per-head table [15][15] (blob: after each block's fc2.b) added
+                         to the score of query (qy, qx) and key (ky, kx) of a window at
+                         [ky - qy + 7][kx - qx + 7].  0 = none. */
 } inpaint_config;
 
 typedef struct inpaint_ctx inpaint_ctx;
@@ -88,7 +92,8 @@ typedef struct inpaint_ctx inpaint_ctx;
  * row-major): embed.w [d,4,4,4] (out, in = R,G,B,mask, ky, kx), embed.b [d]; per block:
  * ln1.g, ln1.b [d], qkv.w [d,3d] (in, out; out = q | k | v, head h at columns
  * 32h.. of each third), qkv.b [3d], proj.w [d,d], proj.b [d], ln2.g, ln2.b [d],
- * fc1.w [d, r*d], fc1.b [r*d], fc2.w [r*d, d], fc2.b [d]; then lnf.g, lnf.b [d],
+ * fc1.w [d, r*d], fc1.b [r*d], fc2.w [r*d, d], fc2.b [d] (then relpos [heads,15,15]
+ * when pos_bias = 1); then lnf.g, lnf.b [d],
  * dec1.w [c1,d,3,3], dec1.b [c1], dec2.w [c2,c1,3,3], dec2.b [c2], head.w [3,c2,3,3],
  * head.b [3].  Errors: E_INVAL for a NULL or unsupported config. */
 INPAINT_API int inpaint_num_params(const inpaint_config* cfg, size_t* n_params);

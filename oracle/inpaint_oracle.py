@@ -23,6 +23,8 @@ used here are:
   no such key outputs 0; after the attention of block l every real token of a window
   with any usable key becomes valid: v[l+1][t] = OR of v[l] over t's window;
 * softmax scale 1/sqrt(d_h); LayerNorm eps 1e-5 with biased variance; exact erf GELU;
+* optional relative-position bias (pos_bias = 1): a learned per-head table added to the
+  scores of query slot i and key slot j by their row and column offset in the window;
 * final LayerNorm, then two stages of (nearest x2 upsample, 3x3 conv pad 1, GELU) with
   d/4 and d/8 channels, then a 3x3 conv to RGB = pred (no output activation);
 * composite out = pred on hole pixels and x on known pixels (a select, so known pixels
@@ -76,6 +78,8 @@ def unpack(flat: torch.Tensor, cfg) -> dict:
         take(f"{l}.ln2.g", d); take(f"{l}.ln2.b", d)
         take(f"{l}.fc1.w", d, r * d); take(f"{l}.fc1.b", r * d)
         take(f"{l}.fc2.w", r * d, d); take(f"{l}.fc2.b", d)
+        if getattr(cfg, "pos_bias", 0):
+            take(f"{l}.relpos", cfg.heads, 2 * cfg.window - 1, 2 * cfg.window - 1)
     take("lnf.g", d); take("lnf.b", d)
     take("dec1.w", c1, d, 3, 3); take("dec1.b", c1)
     take("dec2.w", c2, c1, 3, 3); take("dec2.b", c2)
@@ -90,6 +94,8 @@ def num_params(cfg) -> int:
     c1 = cfg.dec_c1 or d // 4
     c2 = cfg.dec_c2 or d // 8
     blk = 2 * d + 3 * d * d + 3 * d + d * d + d + 2 * d + 2 * r * d * d + r * d + d
+    if getattr(cfg, "pos_bias", 0):
+        blk += cfg.heads * (2 * cfg.window - 1) ** 2
     return (d * 4 * p * p + d + cfg.blocks * blk + 2 * d
             + c1 * d * 9 + c1 + c2 * c1 * 9 + c2 + 3 * c2 * 9 + 3)
 
@@ -163,13 +169,24 @@ def gelu(x: torch.Tensor) -> torch.Tensor:
     return 0.5 * x * (1.0 + torch.erf(x / math.sqrt(2.0)))
 
 
-def window_attention(qkv: torch.Tensor, valid: torch.Tensor, heads: int, widx: torch.Tensor):
+def relpos_bias(relpos: torch.Tensor, ws: int) -> torch.Tensor:
+    """[heads, 2ws-1, 2ws-1] table -> [heads, S, S] score bias of query slot i and key slot
+    j of a window (slot = row * ws + column): relpos[h, rj - ri + ws-1, cj - ci + ws-1]."""
+    r = torch.arange(ws * ws) // ws
+    c = torch.arange(ws * ws) % ws
+    dy = r[None, :] - r[:, None] + ws - 1
+    dx = c[None, :] - c[:, None] + ws - 1
+    return relpos[:, dy, dx]
+
+
+def window_attention(qkv: torch.Tensor, valid: torch.Tensor, heads: int, widx: torch.Tensor, relpos=None):
     """Mask-aware windowed multi-head attention of one frame.
 
     qkv [N, 3d] (q | k | v, head h at columns h*d_h ... within each third), valid [N]
     (1 = usable key).  For query t in window w: o_t = sum over keys s of w with
-    valid[s] of softmax_s(q_t . k_s / sqrt(d_h)) v_s, per head; o_t = 0 when w has
-    no valid key.  Returns (o [N, d], next valid [N] = OR of valid over t's window).
+    valid[s] of softmax_s(q_t . k_s / sqrt(d_h) [+ relative-position bias]) v_s, per
+    head; o_t = 0 when w has no valid key.  Returns (o [N, d], next valid [N] = OR of
+    valid over t's window).
     """
     N, d3 = qkv.shape
     d = d3 // 3
@@ -183,6 +200,8 @@ def window_attention(qkv: torch.Tensor, valid: torch.Tensor, heads: int, widx: t
     k = qkv[:, d:2 * d][safe].reshape(nW, S, heads, dh).transpose(1, 2)
     v = qkv[:, 2 * d:][safe].reshape(nW, S, heads, dh).transpose(1, 2)
     s = q @ k.transpose(-1, -2) / math.sqrt(dh)                            # [nW, h, S, S]
+    if relpos is not None:
+        s = s + relpos_bias(relpos, int(round(S ** 0.5)))[None]
     # windows without a usable key get a harmless stand-in key set; their output is zeroed
     allowed = key_ok | ~any_w[:, None]
     s = s.masked_fill(~allowed[:, None, None, :], float("-inf"))
@@ -204,7 +223,7 @@ def temporal_block(cfg, l: int) -> bool:
     return getattr(cfg, "mem_slots", 0) > 0 and l % 2 == 1
 
 
-def window_attention_mem(qkv: torch.Tensor, valid: torch.Tensor, heads: int, widx: torch.Tensor, mem):
+def window_attention_mem(qkv: torch.Tensor, valid: torch.Tensor, heads: int, widx: torch.Tensor, mem, relpos=None):
     """window_attention with memory keys: `mem` lists, per memory slot, (kv [N, 2d] =
     k | v of a past frame at this block, mask [N] = that frame's usable-key mask there),
     or None for an empty slot.  Query t of window w attends over w's usable current keys
@@ -234,6 +253,8 @@ def window_attention_mem(qkv: torch.Tensor, valid: torch.Tensor, heads: int, wid
     key_ok = torch.cat(oks, dim=1)                             # [nW, S*(1+m)]
     any_w = key_ok.any(dim=1)
     s = q @ k.transpose(-1, -2) / math.sqrt(dh)
+    if relpos is not None:  # memory keys sit at the same window positions as current ones
+        s = s + relpos_bias(relpos, int(round(S ** 0.5))).repeat(1, 1, len(ks))[None]
     allowed = key_ok | ~any_w[:, None]
     s = s.masked_fill(~allowed[:, None, None, :], float("-inf"))
     e = torch.exp(s - s.max(dim=-1, keepdim=True).values)
@@ -298,15 +319,16 @@ def forward(x, hole, weights, cfg, keep_block_inputs: bool = False, mem=None) ->
         widx = window_index(Ht, Wt, ws, block_offset(cfg, l))
         y = layer_norm(tok, w[f"{l}.ln1.g"], w[f"{l}.ln1.b"])
         qkv = y @ w[f"{l}.qkv.w"] + w[f"{l}.qkv.b"]
+        rp = w[f"{l}.relpos"] if getattr(cfg, "pos_bias", 0) else None
         outs, nxts = [], []
         for bi in range(B):
             if temporal_block(cfg, l):
                 slots = [None if mem is None or mem[bi] is None or mem[bi][j] is None else mem[bi][j][l]
                          for j in range(cfg.mem_slots)]
-                o, nxt = window_attention_mem(qkv[bi], v[bi], cfg.heads, widx, slots)
+                o, nxt = window_attention_mem(qkv[bi], v[bi], cfg.heads, widx, slots, rp)
                 memory[bi][l] = (qkv[bi][:, d:].clone(), v[bi].clone())
             else:
-                o, nxt = window_attention(qkv[bi], v[bi], cfg.heads, widx)
+                o, nxt = window_attention(qkv[bi], v[bi], cfg.heads, widx, rp)
             outs.append(o)
             nxts.append(nxt)
         o = torch.stack(outs)

@@ -38,12 +38,12 @@ class InpaintConfig(ctypes.Structure):
                 ("blocks", ctypes.c_int32), ("mlp_ratio", ctypes.c_int32), ("patch", ctypes.c_int32),
                 ("dec_c1", ctypes.c_int32), ("dec_c2", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("shift", ctypes.c_int32), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_size_t),
-                ("mem_slots", ctypes.c_int32)]
+                ("mem_slots", ctypes.c_int32), ("pos_bias", ctypes.c_int32)]
 
     @classmethod
     def from_model(cls, cfg: ModelConfig, seed: int = 0, hbm_budget_bytes: int = 0) -> "InpaintConfig":
         return cls(cfg.dim, cfg.heads, cfg.window, cfg.blocks, cfg.mlp_ratio, cfg.patch, cfg.dec_c1, cfg.dec_c2,
-                   cfg.precision, cfg.shift, seed, hbm_budget_bytes, cfg.mem_slots)
+                   cfg.precision, cfg.shift, seed, hbm_budget_bytes, cfg.mem_slots, cfg.pos_bias)
 
 
 _P = ctypes.c_void_p

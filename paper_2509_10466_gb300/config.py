@@ -29,6 +29,7 @@ class ModelConfig:
     precision: int = FP32   # FP32 plain form or BF16 tensor-core form
     shift: int = 1          # 1: odd blocks use windows offset by half a window
     mem_slots: int = 0      # m: temporal memory slots (odd blocks attend to m past frames)
+    pos_bias: int = 0       # 1: learned relative-position bias (per head, 15 x 15) in the window softmax
 
     @property
     def c1(self) -> int:

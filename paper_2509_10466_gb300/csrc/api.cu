@@ -31,6 +31,7 @@ bool check_cfg(const inpaint_config* c) {
   const int c2 = c->dec_c2 ? c->dec_c2 : c->dim / 8;
   if (c1 <= 0 || c2 <= 0 || c1 % 4 || c2 % 4 || c1 > 4096 || c2 > 1024) return false;
   if (c->mem_slots < 0 || c->mem_slots > 4) return false;
+  if (c->pos_bias != 0 && c->pos_bias != 1) return false;
   return true;
 }
 
@@ -50,6 +51,7 @@ Offsets make_offsets(const inpaint_config& c) {
     b.ln2g = take(d); b.ln2b = take(d);
     b.fc1w = take(d * r * d); b.fc1b = take(r * d);
     b.fc2w = take(r * d * d); b.fc2b = take(d);
+    if (c.pos_bias) b.relpos = take((size_t)c.heads * 225);
     o.blk.push_back(b);
   }
   o.lnfg = take(d); o.lnfb = take(d);
@@ -219,6 +221,7 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     // temporal block: the queries also see the memory slots' keys of this block, and each
     // frame's own k | v and key mask here become part of its memory tensor
     const bool temporal = c->cfg.mem_slots > 0 && (l & 1);
+    const float* rp = c->cfg.pos_bias ? c->w32 + b.relpos : nullptr;
     const MemTab* mtab = mem ? mem->tab : nullptr;
     const size_t moff = mem ? (size_t)(l / 2) * mem->lay.stride : 0, mkv = mem ? mem->lay.kv_bytes : 0;
     auto record_memory = [&](const void* qkv_any) -> int {
@@ -251,10 +254,10 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, err, st))); }
       if (temporal) {
         LaunchScope ls(c, st, K_ATTN);
-        TRY(cuda_err(launch_attention_tc_mem(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st)));
+        TRY(cuda_err(launch_attention_tc_mem(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st, rp)));
       } else {
         LaunchScope ls(c, st, K_ATTN);
-        TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st)));
+        TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp)));
       }
       if (temporal) TRY(record_memory(qkv));
       if (fuse_ln) {
@@ -296,10 +299,10 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_f32(ln, d, c->w32 + b.qkvw, 3 * d, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, st))); }
       if (temporal) {
         LaunchScope ls(c, st, K_ATTN);
-        TRY(cuda_err(launch_attention_mem<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st)));
+        TRY(cuda_err(launch_attention_mem<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st, rp)));
       } else {
         LaunchScope ls(c, st, K_ATTN);
-        TRY(cuda_err(launch_attention<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st)));
+        TRY(cuda_err(launch_attention<float>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp)));
       }
       if (temporal) TRY(record_memory(qkv));
       { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_f32(ao, d, c->w32 + b.projw, d, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, st))); }

@@ -120,13 +120,16 @@ cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const
                           cudaStream_t st);
 
 // Mask-aware window attention of all frames; qkv [B*Nt, 3d] (T), v_in/v_out u8 [B*Nt].
+// relpos (optional, device f32 [heads][15][15]): relative-position bias added to the
+// score of query slot (qy, qx) and key slot (ky, kx) at [(ky - qy + 7) * 15 + kx - qx + 7].
 template <typename T>
 cudaError_t launch_attention(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
-                             int Wt, int d, int heads, int offset, cudaStream_t st);
+                             int Wt, int d, int heads, int offset, cudaStream_t st, const float* relpos = nullptr);
 
 // Tensor-core form for BF16 activations (mma.sync bf16, FP32 softmax statistics).
 cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
-                                int Wt, int d, int heads, int offset, cudaStream_t st);
+                                int Wt, int d, int heads, int offset, cudaStream_t st,
+                                const float* relpos = nullptr);
 
 // Temporal blocks: as above, plus the keys of m memory slots.  tab->p[b*m + j] is a device
 // pointer to a previous frame's memory buffer (null = empty slot; tab null = no memory);
@@ -139,10 +142,10 @@ struct MemTab {
 template <typename T>
 cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
                                  int heads, int offset, const MemTab* tab, int m, size_t off_kv, size_t off_mask,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const float* relpos = nullptr);
 cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
                                     int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
-                                    size_t off_mask, cudaStream_t st);
+                                    size_t off_mask, cudaStream_t st, const float* relpos = nullptr);
 
 // Coloured point cloud (world x, y, z, r, g, b per pixel; NaN coordinates where the depth
 // is not usable) and z-buffered splat into an Ho x Wo image.  cam / view: fx, fy, cx, cy;

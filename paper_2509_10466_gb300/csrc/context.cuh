@@ -10,6 +10,7 @@ namespace inpaint {
 // Offsets (in floats) of every tensor of the weight blob, in blob order.
 struct BlockOff {
   size_t ln1g, ln1b, qkvw, qkvb, projw, projb, ln2g, ln2b, fc1w, fc1b, fc2w, fc2b;
+  size_t relpos = 0;  // [heads][15][15] when the config has a relative-position bias
 };
 struct Offsets {
   size_t embw, embb;

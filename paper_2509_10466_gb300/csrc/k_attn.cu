@@ -21,14 +21,20 @@ constexpr int WS = 8;      // window side
 constexpr int SLOTS = 64;  // WS * WS
 constexpr int DH = 32;     // head dim
 
+// Relative-position bias of query slot s and key slot k: table[(ky - sy + 7) * 15 + (kx - sx + 7)].
+__device__ __forceinline__ int relpos_index(int s, int k) { return ((k >> 3) - (s >> 3) + 7) * 15 + ((k & 7) - (s & 7) + 7); }
+
 template <typename T>
 __global__ void __launch_bounds__(SLOTS) attn_simt_kernel(const T* __restrict__ qkv, const uint8_t* __restrict__ v_in,
                                                           T* __restrict__ o, uint8_t* __restrict__ v_out, int Ht,
-                                                          int Wt, int d, int offset, int nwx) {
+                                                          int Wt, int d, int offset, int nwx,
+                                                          const float* __restrict__ relpos) {
   __shared__ float Ks[SLOTS][DH + 1];
   __shared__ float Vs[SLOTS][DH + 1];
   __shared__ int okS[SLOTS];
+  __shared__ float rp[225];
   const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  for (int e = threadIdx.x; e < 225; e += SLOTS) rp[e] = relpos ? relpos[h * 225 + e] : 0.f;
   const int wy = w / nwx, wx = w - (w / nwx) * nwx;
   const int s = threadIdx.x;
   const int ty = wy * WS - offset + (s >> 3), tx = wx * WS - offset + (s & 7);
@@ -63,7 +69,7 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_kernel(const T* __restrict__ 
     float sc = 0.f;
 #pragma unroll
     for (int i = 0; i < DH; ++i) sc = fmaf(q[i], Ks[k][i], sc);
-    mx = fmaxf(mx, sc * scale);
+    mx = fmaxf(mx, sc * scale + rp[relpos_index(s, k)]);
   }
   float l = 0.f, acc[DH];
 #pragma unroll
@@ -73,7 +79,7 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_kernel(const T* __restrict__ 
     float sc = 0.f;
 #pragma unroll
     for (int i = 0; i < DH; ++i) sc = fmaf(q[i], Ks[k][i], sc);
-    const float p = expf(sc * scale - mx);
+    const float p = expf(sc * scale + rp[relpos_index(s, k)] - mx);
     l += p;
 #pragma unroll
     for (int i = 0; i < DH; ++i) acc[i] = fmaf(p, Vs[k][i], acc[i]);
@@ -94,11 +100,14 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_mem_kernel(const T* __restric
                                                               uint8_t* __restrict__ v_out, int Ht, int Wt, int d,
                                                               int offset, int nwx,
                                                               const __grid_constant__ MemTab mem_tab, int m,
-                                                              size_t off_kv, size_t off_mask) {
+                                                              size_t off_kv, size_t off_mask,
+                                                              const float* __restrict__ relpos) {
   __shared__ float Ks[SLOTS][DH + 1];
   __shared__ float Vs[SLOTS][DH + 1];
   __shared__ int okS[SLOTS];
+  __shared__ float rp[225];
   const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  for (int e = threadIdx.x; e < 225; e += SLOTS) rp[e] = relpos ? relpos[h * 225 + e] : 0.f;
   const int wy = w / nwx, wx = w - (w / nwx) * nwx;
   const int s = threadIdx.x;
   const int ty = wy * WS - offset + (s >> 3), tx = wx * WS - offset + (s & 7);
@@ -152,7 +161,7 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_mem_kernel(const T* __restric
       float sc = 0.f;
 #pragma unroll
       for (int e = 0; e < DH; ++e) sc = fmaf(q[e], Ks[k][e], sc);
-      bm = fmaxf(bm, sc * scale);
+      bm = fmaxf(bm, sc * scale + rp[relpos_index(s, k)]);
     }
     if (bm > mx) {
       const float a = expf(mx - bm);
@@ -166,7 +175,7 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_mem_kernel(const T* __restric
       float sc = 0.f;
 #pragma unroll
       for (int e = 0; e < DH; ++e) sc = fmaf(q[e], Ks[k][e], sc);
-      const float p = expf(sc * scale - mx);
+      const float p = expf(sc * scale + rp[relpos_index(s, k)] - mx);
       l += p;
 #pragma unroll
       for (int e = 0; e < DH; ++e) acc[e] = fmaf(p, Vs[k][e], acc[e]);
@@ -182,35 +191,36 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_mem_kernel(const T* __restric
 
 template <typename T>
 cudaError_t launch_attention(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
-                             int heads, int offset, cudaStream_t st) {
+                             int heads, int offset, cudaStream_t st, const float* relpos) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   dim3 grid(nwy * nwx, heads, B);
-  attn_simt_kernel<T><<<grid, SLOTS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx);
+  attn_simt_kernel<T><<<grid, SLOTS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, relpos);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_attention<float>(const float*, const uint8_t*, float*, uint8_t*, int, int, int, int, int,
-                                             int, cudaStream_t);
+                                             int, cudaStream_t, const float*);
 template cudaError_t launch_attention<bf16>(const bf16*, const uint8_t*, bf16*, uint8_t*, int, int, int, int, int,
-                                            int, cudaStream_t);
+                                            int, cudaStream_t, const float*);
 
 template <typename T>
 cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
                                  int heads, int offset, const MemTab* tab, int m, size_t off_kv, size_t off_mask,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const float* relpos) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   if (tab && (size_t)B * m > (size_t)MEM_TAB_MAX) return cudaErrorInvalidValue;
   static const MemTab none{};
   dim3 grid(nwy * nwx, heads, B);
   attn_simt_mem_kernel<T><<<grid, SLOTS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, tab ? *tab : none,
-                                                  tab ? m : 0, off_kv, off_mask);
+                                                  tab ? m : 0, off_kv, off_mask, relpos);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_attention_mem<float>(const float*, const uint8_t*, float*, uint8_t*, int, int, int, int,
-                                                 int, int, const MemTab*, int, size_t, size_t, cudaStream_t);
+                                                 int, int, const MemTab*, int, size_t, size_t, cudaStream_t,
+                                                 const float*);
 template cudaError_t launch_attention_mem<bf16>(const bf16*, const uint8_t*, bf16*, uint8_t*, int, int, int, int, int,
-                                                int, const MemTab*, int, size_t, size_t, cudaStream_t);
+                                                int, const MemTab*, int, size_t, size_t, cudaStream_t, const float*);
 
 }  // namespace inpaint
 
@@ -232,6 +242,7 @@ namespace inpaint {
 namespace {
 
 constexpr int HPC = 2;            // heads per CTA
+constexpr float LOG2E = 1.4426950408889634f;
 constexpr int TC_THREADS = 128 * HPC;
 constexpr int ROWB = 40;  // bf16 per staged row: 32 + 8 pad (80 B rows, conflict-free ldmatrix)
 
@@ -269,9 +280,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restrict__ qkv,
                                                              const uint8_t* __restrict__ v_in, bf16* __restrict__ o,
                                                              uint8_t* __restrict__ v_out, int Ht, int Wt, int d,
-                                                             int offset, int nwx) {
+                                                             int offset, int nwx, const float* __restrict__ relpos) {
   // blockIdx.y = head pair: warps 0-3 serve head 2y, warps 4-7 head 2y+1
   __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
+  __shared__ float rps[HPC][225];  // relative-position bias of the two heads (0 without one)
   __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
   __shared__ __align__(16) bf16 Vs[HPC][SLOTS][ROWB];
   __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
@@ -281,6 +293,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Nt = Ht * Wt;
 
+  for (int e = tid; e < HPC * 225; e += TC_THREADS)
+    rps[e / 225][e % 225] = relpos ? relpos[(HPC * blockIdx.y + e / 225) * 225 + e % 225] : 0.f;
   if (tid < SLOTS) {
     const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
     const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
@@ -350,8 +364,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
     for (int c = 0; c < 2; ++c) {
       const int key = 8 * j + 2 * tq + c;
       const bool okk = (keymask >> key) & 1ull;
-      sc[j][c] = okk ? sc[j][c] * sl2 : -INFINITY;
-      sc[j][2 + c] = okk ? sc[j][2 + c] * sl2 : -INFINITY;
+      sc[j][c] = okk ? fmaf(sc[j][c], sl2, rps[hh][relpos_index(r0 + g, key)] * LOG2E) : -INFINITY;
+      sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E) : -INFINITY;
       mx0 = fmaxf(mx0, sc[j][c]);
       mx1 = fmaxf(mx1, sc[j][2 + c]);
     }
@@ -423,8 +437,10 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
                                                                  bf16* __restrict__ o, uint8_t* __restrict__ v_out,
                                                                  int Ht, int Wt, int d, int offset, int nwx,
                                                                  const __grid_constant__ MemTab mem_tab, int m,
-                                                                 size_t off_kv, size_t off_mask) {
+                                                                 size_t off_kv, size_t off_mask,
+                                                                 const float* __restrict__ relpos) {
   __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
+  __shared__ float rps[HPC][225];
   __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
   __shared__ __align__(16) bf16 Vs[HPC][SLOTS][ROWB];
   __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
@@ -435,6 +451,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Nt = Ht * Wt;
   const int h0 = HPC * blockIdx.y;
+  for (int e = tid; e < HPC * 225; e += TC_THREADS)
+    rps[e / 225][e % 225] = relpos ? relpos[(h0 + e / 225) * 225 + e % 225] : 0.f;
 
   if (tid < SLOTS) {
     const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
@@ -522,8 +540,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
       for (int c = 0; c < 2; ++c) {
         const int key = 8 * j + 2 * tq + c;
         const bool okk = (keymask >> key) & 1ull;
-        sc[j][c] = okk ? sc[j][c] * sl2 : -INFINITY;
-        sc[j][2 + c] = okk ? sc[j][2 + c] * sl2 : -INFINITY;
+        sc[j][c] = okk ? fmaf(sc[j][c], sl2, rps[hh][relpos_index(r0 + g, key)] * LOG2E) : -INFINITY;
+        sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E) : -INFINITY;
         bm0 = fmaxf(bm0, sc[j][c]);
         bm1 = fmaxf(bm1, sc[j][2 + c]);
       }
@@ -594,24 +612,24 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
 }  // namespace
 
 cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht, int Wt,
-                                int d, int heads, int offset, cudaStream_t st) {
+                                int d, int heads, int offset, cudaStream_t st, const float* relpos) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   if (heads % HPC) return cudaErrorInvalidValue;
   dim3 grid(nwy * nwx, heads / HPC, B);
-  attn_tc_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx);
+  attn_tc_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, relpos);
   return cudaGetLastError();
 }
 
 cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
                                     int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
-                                    size_t off_mask, cudaStream_t st) {
+                                    size_t off_mask, cudaStream_t st, const float* relpos) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   if (heads % HPC) return cudaErrorInvalidValue;
   if (tab && (size_t)B * m > (size_t)MEM_TAB_MAX) return cudaErrorInvalidValue;
   static const MemTab none{};
   dim3 grid(nwy * nwx, heads / HPC, B);
   attn_tc_mem_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, tab ? *tab : none,
-                                                  tab ? m : 0, off_kv, off_mask);
+                                                  tab ? m : 0, off_kv, off_mask, relpos);
   return cudaGetLastError();
 }
 

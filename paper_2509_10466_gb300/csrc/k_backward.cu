@@ -223,15 +223,22 @@ __global__ void __launch_bounds__(256) ln_bwd_kernel(const float* __restrict__ x
 struct AttnBwdSmem {
   float Q[SLOTS][DH + 1], K[SLOTS][DH + 1], V[SLOTS][DH + 1], GO[SLOTS][DH + 1];
   float P[SLOTS][SLOTS + 1], GS[SLOTS][SLOTS + 1];
+  float rp[225];
   int ok[SLOTS];
 };
 
+__device__ __forceinline__ int relpos_idx(int s, int k) { return ((k >> 3) - (s >> 3) + 7) * 15 + ((k & 7) - (s & 7) + 7); }
+
 __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict__ qkv, const uint8_t* __restrict__ v_in,
                                                          const float* __restrict__ go, float* __restrict__ gqkv, int Ht,
-                                                         int Wt, int d, int offset, int nwx) {
+                                                         int Wt, int d, int offset, int nwx,
+                                                         const float* __restrict__ relpos, float* __restrict__ gbias) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   AttnBwdSmem& sm = *reinterpret_cast<AttnBwdSmem*>(smem_raw);
   const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  // this CTA's partial gradient of the relative-position table: [frame][window][head][225]
+  float* gb = gbias ? gbias + (((size_t)b * gridDim.x + w) * gridDim.y + h) * 225 : nullptr;
+  for (int e = threadIdx.x; e < 225; e += SLOTS) sm.rp[e] = relpos ? relpos[h * 225 + e] : 0.f;
   const int wy = w / nwx, wx = w - (w / nwx) * nwx;
   const int s = threadIdx.x;
   const int ty = wy * WS - offset + (s >> 3), tx = wx * WS - offset + (s & 7);
@@ -252,6 +259,8 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
   if (!any) {
     if (real)
       for (int i = 0; i < DH; ++i) { gq[i] = 0.f; gq[d + i] = 0.f; gq[2 * d + i] = 0.f; }
+    if (gb)
+      for (int e = s; e < 225; e += SLOTS) gb[e] = 0.f;
     return;
   }
   const float scale = 1.0f / sqrtf((float)DH);
@@ -262,7 +271,7 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
       if (!sm.ok[k]) continue;
       float sc = 0.f;
       for (int i = 0; i < DH; ++i) sc = fmaf(sm.Q[s][i], sm.K[k][i], sc);
-      mx = fmaxf(mx, sc * scale);
+      mx = fmaxf(mx, sc * scale + sm.rp[relpos_idx(s, k)]);
     }
     float l = 0.f;
     for (int k = 0; k < SLOTS; ++k) {
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
       if (sm.ok[k]) {
         float sc = 0.f;
         for (int i = 0; i < DH; ++i) sc = fmaf(sm.Q[s][i], sm.K[k][i], sc);
-        p = expf(sc * scale - mx);
+        p = expf(sc * scale + sm.rp[relpos_idx(s, k)] - mx);
       }
       sm.P[s][k] = p;
       l += p;
@@ -299,6 +308,18 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
     for (int k = 0; k < SLOTS; ++k) { sm.P[s][k] = 0.f; sm.GS[s][k] = 0.f; }
   }
   __syncthreads();
+  // relative-position table: d score / d table entry = 1, so its gradient is the sum of the
+  // score gradients over the (query, key) slot pairs at that offset (fixed order)
+  if (gb)
+    for (int e = s; e < 225; e += SLOTS) {
+      const int dy = e / 15 - 7, dx = e % 15 - 7;
+      float acc = 0.f;
+      for (int q = 0; q < SLOTS; ++q) {
+        const int ky = (q >> 3) + dy, kx = (q & 7) + dx;
+        if (ky >= 0 && ky < 8 && kx >= 0 && kx < 8) acc += sm.GS[q][ky * 8 + kx];
+      }
+      gb[e] = acc;
+    }
   // key side: dK = scale * GS^T Q, dV = P^T dO
   if (real) {
     float gk[DH], gv[DH];
@@ -317,6 +338,16 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
       gq[2 * d + i] = gv[i];
     }
   }
+}
+
+// out[h][r] = sum over the n windows (fixed order) of part[(i * heads + h) * 225 + r]
+__global__ void relpos_grad_reduce_kernel(const float* __restrict__ part, int n, int heads, float* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= heads * 225) return;
+  const int h = e / 225, r = e - h * 225;
+  float acc = 0.f;
+  for (int i = 0; i < n; ++i) acc += part[((size_t)i * heads + h) * 225 + r];
+  out[e] = acc;
 }
 
 inline unsigned grid1d(size_t n) {
@@ -353,6 +384,8 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   const size_t oGP = take(P2 * 3 * 4), oGF2 = take(P2 * c2 * 4), oGU1 = take(P2 * c1 * 4), oGF1 = take(P1 * c1 * 4);
   const size_t oGU0 = take(P1 * d * 4), oIM = take(im2 * 4), oPART = take((size_t)SPLIT_MAX * wmax * 4);
   const size_t oCS = take((size_t)CH * nmax * 4), oWF = take((size_t)9 * wmax * 4), oTAP = take((size_t)9 * wmax * 4);
+  const int nw_max = ((Ht + 4 + WS - 1) / WS) * ((Wt + 4 + WS - 1) / WS);  // windows of the offset grid (the larger)
+  const size_t oRP = take(c->cfg.pos_bias ? (size_t)B * nw_max * c->heads * 225 * 4 : 256);
   int rc = grow(&c->bws, &c->bws_bytes, q, c, c->arena_bytes + c->stage_bytes);
   if (rc != INPAINT_OK) return rc;
   uint8_t* ws = c->bws;
@@ -363,6 +396,7 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   float *gx = F(oGX), *gxm = F(oGXM), *gh = F(oGH), *gy = F(oGY), *gqkv = F(oGQKV), *go = F(oGO), *gyx = F(oGYX);
   float *z1 = F(oZ1), *f1 = F(oF1), *z2 = F(oZ2), *f2 = F(oF2), *gp = F(oGP), *gf2 = F(oGF2), *gu1 = F(oGU1);
   float *gf1 = F(oGF1), *gu0 = F(oGU0), *im = F(oIM), *part = F(oPART), *cs = F(oCS), *wf = F(oWF), *tap = F(oTAP);
+  float* rpart = F(oRP);
   const float* w = c->w32;
   auto Xl = [&](int l) { return X + (size_t)l * M * d; };
 
@@ -424,7 +458,8 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
     const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
     { auto ls = K(K_LN); ok(launch_layernorm<float>(Xl(l), w + bo.ln1g, w + bo.ln1b, y1, M, d, st)); }
     { auto ls = K(K_QKV); ok(launch_gemm_f32(y1, d, w + bo.qkvw, 3 * d, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, w + bo.qkvb, nullptr, st)); }
-    { auto ls = K(K_ATTN); ok(launch_attention<float>(qkv, masks + (size_t)l * M, ao, masks + (size_t)(l + 1) * M, B, Ht, Wt, d, c->heads, offset, st)); }
+    const float* rp = c->cfg.pos_bias ? w + bo.relpos : nullptr;
+    { auto ls = K(K_ATTN); ok(launch_attention<float>(qkv, masks + (size_t)l * M, ao, masks + (size_t)(l + 1) * M, B, Ht, Wt, d, c->heads, offset, st, rp)); }
     { auto ls = K(K_PROJ); ok(launch_gemm_f32(ao, d, w + bo.projw, d, xm, d, M, d, d, EPI_BIAS_RESID, w + bo.projb, Xl(l), st)); }
     { auto ls = K(K_LN); ok(launch_layernorm<float>(xm, w + bo.ln2g, w + bo.ln2b, y2, M, d, st)); }
     { auto ls = K(K_FC1); ok(launch_gemm_f32(y2, d, w + bo.fc1w, hid, a, hid, M, hid, d, EPI_BIAS, w + bo.fc1b, nullptr, st)); }
@@ -491,9 +526,16 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
     {
       auto ls = K(K_OTHER);
       const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
+      const bool rpb = c->cfg.pos_bias != 0;
       attn_bwd_kernel<<<dim3(nwy * nwx, c->heads, B), SLOTS, sizeof(AttnBwdSmem), st>>>(
-          qkv, masks + (size_t)l * M, go, gqkv, Ht, Wt, d, offset, nwx);
+          qkv, masks + (size_t)l * M, go, gqkv, Ht, Wt, d, offset, nwx, rpb ? w + bo.relpos : nullptr,
+          rpb ? rpart : nullptr);
       ok(cudaGetLastError());
+      if (rpb) {
+        relpos_grad_reduce_kernel<<<cdiv(c->heads * 225, 256), 256, 0, st>>>(rpart, B * nwy * nwx, c->heads,
+                                                                               gw + bo.relpos);
+        ok(cudaGetLastError());
+      }
     }
     colsum(gqkv, M, 3 * d, gw + bo.qkvb);
     wgrad(y1, d, d, gqkv, 3 * d, 3 * d, M, gw + bo.qkvw);

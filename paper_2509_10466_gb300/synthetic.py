@@ -27,7 +27,9 @@ def param_shapes(cfg):
     """Ordered (name, shape) list of the flat weight blob for a config ``cfg``.
 
     Matrices of linear layers are stored as (in, out): a token row ``y`` maps to
-    ``y @ W + b``.  Conv kernels are (out, in, ky, kx).  The embedding's 4 input
+    ``y @ W + b``.  Conv kernels are (out, in, ky, kx).  With ``pos_bias`` each block
+    ends with its relative-position bias (heads, 15, 15), indexed by
+    (key row - query row + 7, key column - query column + 7) inside a window.  The embedding's 4 input
     channels are R, G, B of the hole-zeroed frame and then the known-pixel mask.
     """
     d, r, p = cfg.dim, cfg.mlp_ratio, cfg.patch
@@ -43,6 +45,8 @@ def param_shapes(cfg):
             (f"blk{l}.fc1.w", (d, r * d)), (f"blk{l}.fc1.b", (r * d,)),
             (f"blk{l}.fc2.w", (r * d, d)), (f"blk{l}.fc2.b", (d,)),
         ]
+        if getattr(cfg, "pos_bias", 0):
+            out += [(f"blk{l}.relpos", (cfg.heads, 2 * cfg.window - 1, 2 * cfg.window - 1))]
     out += [
         ("lnf.g", (d,)), ("lnf.b", (d,)),
         ("dec1.w", (c1, d, 3, 3)), ("dec1.b", (c1,)),
@@ -66,6 +70,8 @@ def make_weights(cfg, seed: int = 0, std: float = 0.02, perturb: bool = False) -
         is_ln = ".ln" in name or name.startswith("ln")
         if leaf == "w":
             a = rng.standard_normal(n) * std
+        elif leaf == "relpos":  # relative-position bias of the window softmax
+            a = rng.standard_normal(n) * (0.5 if perturb else std)
         elif is_ln and leaf == "g":
             a = np.ones(n) + (rng.standard_normal(n) * 0.1 if perturb else 0.0)
         else:  # biases and LayerNorm shifts
