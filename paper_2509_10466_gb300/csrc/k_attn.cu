@@ -277,13 +277,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+template <bool RP>  // RP: the model has a relative-position bias
 __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restrict__ qkv,
                                                              const uint8_t* __restrict__ v_in, bf16* __restrict__ o,
                                                              uint8_t* __restrict__ v_out, int Ht, int Wt, int d,
                                                              int offset, int nwx, const float* __restrict__ relpos) {
   // blockIdx.y = head pair: warps 0-3 serve head 2y, warps 4-7 head 2y+1
   __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
-  __shared__ float rps[HPC][225];  // relative-position bias of the two heads (0 without one)
+  __shared__ float rps[RP ? HPC : 1][RP ? 225 : 1];  // relative-position bias of the two heads
   __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
   __shared__ __align__(16) bf16 Vs[HPC][SLOTS][ROWB];
   __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
@@ -293,8 +294,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Nt = Ht * Wt;
 
-  for (int e = tid; e < HPC * 225; e += TC_THREADS)
-    rps[e / 225][e % 225] = relpos ? relpos[(HPC * blockIdx.y + e / 225) * 225 + e % 225] : 0.f;
+  if (RP)
+    for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(HPC * blockIdx.y + e / 225) * 225 + e % 225];
   if (tid < SLOTS) {
     const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
     const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
@@ -364,8 +365,10 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
     for (int c = 0; c < 2; ++c) {
       const int key = 8 * j + 2 * tq + c;
       const bool okk = (keymask >> key) & 1ull;
-      sc[j][c] = okk ? fmaf(sc[j][c], sl2, rps[hh][relpos_index(r0 + g, key)] * LOG2E) : -INFINITY;
-      sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E) : -INFINITY;
+      const float bb0 = RP ? rps[hh][relpos_index(r0 + g, key)] * LOG2E : 0.f;
+      const float bb1 = RP ? rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
+      sc[j][c] = okk ? (RP ? fmaf(sc[j][c], sl2, bb0) : sc[j][c] * sl2) : -INFINITY;
+      sc[j][2 + c] = okk ? (RP ? fmaf(sc[j][2 + c], sl2, bb1) : sc[j][2 + c] * sl2) : -INFINITY;
       mx0 = fmaxf(mx0, sc[j][c]);
       mx1 = fmaxf(mx1, sc[j][2 + c]);
     }
@@ -432,6 +435,7 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
 // K / V buffers; per block S = Q K^T, the running row maximum is raised, the running sum
 // and O rescaled by 2^(old max - new max), and O += P V.  Blocks without a usable key
 // are skipped.
+template <bool RP>
 __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __restrict__ qkv,
                                                                  const uint8_t* __restrict__ v_in,
                                                                  bf16* __restrict__ o, uint8_t* __restrict__ v_out,
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
                                                                  size_t off_kv, size_t off_mask,
                                                                  const float* __restrict__ relpos) {
   __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
-  __shared__ float rps[HPC][225];
+  __shared__ float rps[RP ? HPC : 1][RP ? 225 : 1];
   __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
   __shared__ __align__(16) bf16 Vs[HPC][SLOTS][ROWB];
   __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
@@ -451,8 +455,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Nt = Ht * Wt;
   const int h0 = HPC * blockIdx.y;
-  for (int e = tid; e < HPC * 225; e += TC_THREADS)
-    rps[e / 225][e % 225] = relpos ? relpos[(h0 + e / 225) * 225 + e % 225] : 0.f;
+  if (RP)
+    for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(h0 + e / 225) * 225 + e % 225];
 
   if (tid < SLOTS) {
     const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
@@ -540,8 +544,10 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
       for (int c = 0; c < 2; ++c) {
         const int key = 8 * j + 2 * tq + c;
         const bool okk = (keymask >> key) & 1ull;
-        sc[j][c] = okk ? fmaf(sc[j][c], sl2, rps[hh][relpos_index(r0 + g, key)] * LOG2E) : -INFINITY;
-        sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E) : -INFINITY;
+        const float bb0 = RP ? rps[hh][relpos_index(r0 + g, key)] * LOG2E : 0.f;
+        const float bb1 = RP ? rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
+        sc[j][c] = okk ? (RP ? fmaf(sc[j][c], sl2, bb0) : sc[j][c] * sl2) : -INFINITY;
+        sc[j][2 + c] = okk ? (RP ? fmaf(sc[j][2 + c], sl2, bb1) : sc[j][2 + c] * sl2) : -INFINITY;
         bm0 = fmaxf(bm0, sc[j][c]);
         bm1 = fmaxf(bm1, sc[j][2 + c]);
       }
@@ -616,7 +622,10 @@ cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, u
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   if (heads % HPC) return cudaErrorInvalidValue;
   dim3 grid(nwy * nwx, heads / HPC, B);
-  attn_tc_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, relpos);
+  if (relpos)
+    attn_tc_kernel<true><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, relpos);
+  else
+    attn_tc_kernel<false><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, nullptr);
   return cudaGetLastError();
 }
 
@@ -628,8 +637,12 @@ cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* 
   if (tab && (size_t)B * m > (size_t)MEM_TAB_MAX) return cudaErrorInvalidValue;
   static const MemTab none{};
   dim3 grid(nwy * nwx, heads / HPC, B);
-  attn_tc_mem_kernel<<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, tab ? *tab : none,
-                                                  tab ? m : 0, off_kv, off_mask, relpos);
+  if (relpos)
+    attn_tc_mem_kernel<true><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
+                                                          tab ? *tab : none, tab ? m : 0, off_kv, off_mask, relpos);
+  else
+    attn_tc_mem_kernel<false><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
+                                                           tab ? *tab : none, tab ? m : 0, off_kv, off_mask, nullptr);
   return cudaGetLastError();
 }
 

@@ -243,15 +243,19 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
   extern __shared__ __align__(16) uint8_t hsm[];
   bf16* tile = reinterpret_cast<bf16*>(hsm);  // [HY*HX][C], chunk k of pixel p at 8*(k ^ (p & (NCH-1)))
   const int b = blockIdx.z, y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+  // halo tile by cp.async, all copies in flight at once (zero fill outside the image)
   for (int e = threadIdx.x; e < HY * HX * NCH; e += blockDim.x) {
     const int k = e % NCH, pix = e / NCH;
     const int hy = pix / HX, hx = pix - (pix / HX) * HX;
     const int sy = y0 - 1 + hy, sx = x0 - 1 + hx;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (sy >= 0 && sy < Hp && sx >= 0 && sx < Wp)
-      v = *reinterpret_cast<const uint4*>(in + (((size_t)b * Hp + sy) * Wp + sx) * C + 8 * k);
-    *reinterpret_cast<uint4*>(tile + (size_t)pix * C + 8 * (k ^ (pix & (NCH - 1)))) = v;
+    const bool inside = sy >= 0 && sy < Hp && sx >= 0 && sx < Wp;
+    const bf16* src = in + (((size_t)b * Hp + (inside ? sy : 0)) * Wp + (inside ? sx : 0)) * C + 8 * k;
+    const uint32_t dst = static_cast<uint32_t>(
+        __cvta_generic_to_shared(tile + (size_t)pix * C + 8 * (k ^ (pix & (NCH - 1)))));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(inside ? 16 : 0)
+                 : "memory");
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
   // B fragments: k-step (tap, kc) -> rows k = channels kc*16 .. +15 of that tap, col n = output channel
   uint32_t bw[9][KC][2];

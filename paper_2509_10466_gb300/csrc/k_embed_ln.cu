@@ -169,28 +169,51 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
     *reinterpret_cast<uint4*>(Ws + n * C::KP + ch * 8) = *reinterpret_cast<const uint4*>(we16 + (size_t)n * 64 + ch * 8);
   }
   __syncthreads();
-  for (int e = tid; e < C::TOK * 16; e += 256) {
-    const int tl = e >> 4, pix = e & 15;
+  static_assert(C::TOK * 4 == 256, "one thread per (token, pixel row)");
+  {
+    // thread -> pixel row pr of token tl; a warp covers 32 neighbouring tokens of one
+    // pixel row, so its loads are contiguous 16-byte runs; all loads are independent
+    const int tl = tid & (C::TOK - 1), pr = tid / C::TOK;
     const int t = t0 + tl;
-    float r = 0.f, g = 0.f, bl = 0.f, m = 0.f;
+    float rv[4] = {0.f, 0.f, 0.f, 0.f}, gv[4] = {0.f, 0.f, 0.f, 0.f}, bv[4] = {0.f, 0.f, 0.f, 0.f};
+    bool kn[4] = {false, false, false, false};
     if (t < Nt) {
       const int ty = t / Wt, tx = t - (t / Wt) * Wt;
-      const int y = ty * 4 + (pix >> 2), xx = tx * 4 + (pix & 3);
-      if (y < H && xx < W) {
-        const size_t q = (size_t)y * W + xx;
-        if (hole[(size_t)b * HW + q] == 0) {
-          const float* xb = x + (size_t)b * 3 * HW + q;
-          r = xb[0]; g = xb[HW]; bl = xb[2 * HW];
-          m = 1.f;
+      const int y = ty * 4 + pr, xx0 = tx * 4;
+      if (y < H) {
+        const size_t q = (size_t)y * W + xx0;
+        const float* xb = x + (size_t)b * 3 * HW + q;
+        const uint8_t* hb = hole + (size_t)b * HW + q;
+        if ((W & 3) == 0 && xx0 + 3 < W) {  // 16-byte aligned: vector loads
+          const float4 r4 = *reinterpret_cast<const float4*>(xb);
+          const float4 g4 = *reinterpret_cast<const float4*>(xb + HW);
+          const float4 b4 = *reinterpret_cast<const float4*>(xb + 2 * HW);
+          const uchar4 h4 = *reinterpret_cast<const uchar4*>(hb);
+          rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
+          gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
+          bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+          kn[0] = h4.x == 0; kn[1] = h4.y == 0; kn[2] = h4.z == 0; kn[3] = h4.w == 0;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (xx0 + j < W) {
+              rv[j] = xb[j]; gv[j] = xb[HW + j]; bv[j] = xb[2 * HW + j];
+              kn[j] = hb[j] == 0;
+            }
         }
       }
     }
-    bf16* pr = P + tl * C::KP;
-    pr[pix] = __float2bfloat16_rn(r);
-    pr[16 + pix] = __float2bfloat16_rn(g);
-    pr[32 + pix] = __float2bfloat16_rn(bl);
-    pr[48 + pix] = __float2bfloat16_rn(m);
-    if (m != 0.f) known[tl] = 1;  // every writer stores the same value
+    bf16* prow = P + tl * C::KP + 4 * pr;
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // hole pixels enter as 0 (the mask channel carries them)
+      prow[j] = __float2bfloat16_rn(kn[j] ? rv[j] : 0.f);
+      prow[16 + j] = __float2bfloat16_rn(kn[j] ? gv[j] : 0.f);
+      prow[32 + j] = __float2bfloat16_rn(kn[j] ? bv[j] : 0.f);
+      prow[48 + j] = __float2bfloat16_rn(kn[j] ? 1.f : 0.f);
+      any = any || kn[j];
+    }
+    if (any) known[tl] = 1;  // every writer stores the same value
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
@@ -229,20 +252,25 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
     const float* orow = O + tl * C::OUT_STRIDE;
     float* trow = tok + ((size_t)b * Nt + t) * D;
     float s = 0.f;
-    for (int c = lane; c < D; c += 32) {
-      const float v = orow[c];
-      trow[c] = v;
-      s += v;
+    for (int c = 2 * lane; c < D; c += 64) {  // two channels per lane: 256-byte warp stores
+      const float2 v = *reinterpret_cast<const float2*>(orow + c);
+      *reinterpret_cast<float2*>(trow + c) = v;
+      s += v.x + v.y;
     }
     const float mean = warp_sum_e(s) / (float)D;
     float q = 0.f;
-    for (int c = lane; c < D; c += 32) {
-      const float v = orow[c] - mean;
-      q = fmaf(v, v, q);
+    for (int c = 2 * lane; c < D; c += 64) {
+      const float2 v = *reinterpret_cast<const float2*>(orow + c);
+      q = fmaf(v.x - mean, v.x - mean, q);
+      q = fmaf(v.y - mean, v.y - mean, q);
     }
     const float rstd = rsqrtf(warp_sum_e(q) / (float)D + 1e-5f);
     bf16* lrow = ln_out + ((size_t)b * Nt + t) * D;
-    for (int c = lane; c < D; c += 32) lrow[c] = __float2bfloat16_rn((orow[c] - mean) * rstd * ln_g[c] + ln_b[c]);
+    for (int c = 2 * lane; c < D; c += 64) {
+      const float2 v = *reinterpret_cast<const float2*>(orow + c);
+      *reinterpret_cast<__nv_bfloat162*>(lrow + c) = __floats2bfloat162_rn((v.x - mean) * rstd * ln_g[c] + ln_b[c],
+                                                                          (v.y - mean) * rstd * ln_g[c + 1] + ln_b[c + 1]);
+    }
   }
 }
 
