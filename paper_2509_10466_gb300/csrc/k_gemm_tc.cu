@@ -44,13 +44,14 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int STAGES = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
+  static constexpr int STAGES = (BN == 256) ? 3 : (BN == 128 ? 5 : 6);
   static constexpr int TMEM_COLS = 2 * BN;
   static constexpr int COLS_PER_WARP = BN / EW;
   static constexpr int PARAM_FLOATS = 1024 + 2 * BN;       // bias (N <= 1024) and LayerNorm scale/shift
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/ +
                                     EPI_WARPS * 32 * 2 * 4 /*LayerNorm partial statistics*/ +
-                                    PARAM_FLOATS * 4 + EPI_WARPS * rows::TILE_BYTES /*row staging tiles*/;
+                                    PARAM_FLOATS * 4 + 1024 /*tile alignment*/ +
+                                    EPI_WARPS * 3 * rows::TILE_BYTES /*two store tiles + a load tile per warp*/;
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
@@ -81,6 +82,8 @@ __device__ __forceinline__ void named_sync(int id, int count) {
 template <int BN>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmB,
+                                                             const __grid_constant__ CUtensorMap tmC,
+                                                             const __grid_constant__ CUtensorMap tmLN,
                                                              const GemmArgs args) {
   using Cfg = TcCfg<BN>;
   constexpr int S = Cfg::STAGES;
@@ -97,7 +100,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   float* s_bias = ln_stats + EPI_WARPS * 32 * 2;                                     // [1024]
   float* s_lng = s_bias + 1024;                                                      // [BN]
   float* s_lnb = s_lng + BN;                                                         // [BN]
-  uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_lnb + BN);                          // [EPI_WARPS][2 KB]
+  uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_lnb + BN) + 1023) &
+                                               ~uintptr_t(1023));                  // [EPI_WARPS][3][2 KB]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, N = args.N;
@@ -192,10 +196,21 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     // epilogue: TMEM sub-partition (warp % 4) holds rows 32*(warp%4) .. +31; column group cg
     const int quarter = warp & 3, cg = (warp - 2) >> 2;
     const int epi = args.epi;
-    const int c_lo = cg * Cfg::COLS_PER_WARP;
+    const int c_lo = cg * Cfg::COLS_PER_WARP, c_hi = c_lo + Cfg::COLS_PER_WARP;
+    const bool resid = epi == EPI_BIAS_RESID || epi == EPI_RESID_LN;
+    rows::AsyncRows st{s_tile + (size_t)(warp - 2) * 3 * rows::TILE_BYTES, 0};
+    uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;  // residual loads
     uint32_t i = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
       const uint32_t acc = i & 1, use = i >> 1;
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      const int row0 = m0 + quarter * 32;    // this warp's 32 rows; the thread owns row0 + lane
+      const int nvalid = M - row0;
+      if (resid && lane < nvalid)  // the residual rows into L2 while the tile's MMAs run
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(args.resid + (size_t)(row0 + lane) * args.ldc +
+                                                                        n0 + c_lo),
+                     "r"(Cfg::COLS_PER_WARP * 4)
+                     : "memory");
       if (!tc::mbar_wait(&acc_full[acc], use & 1, abort_flag)) {
         if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
         *abort_flag = 1;
@@ -203,14 +218,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       }
       __syncwarp();
       tc::fence_after_sync();
-      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-      const int row0 = m0 + quarter * 32;    // this warp's 32 rows; the thread owns row0 + lane
-      const int nvalid = M - row0;
-      uint8_t* tl = s_tile + (size_t)(warp - 2) * rows::TILE_BYTES;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN;
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;  // LayerNorm statistics of this part of the row
-      const bool resid = epi == EPI_BIAS_RESID || epi == EPI_RESID_LN;
-      const int c_hi = c_lo + Cfg::COLS_PER_WARP;
       float4 gn[8];  // residual loads of the next chunk, issued one chunk ahead
       if (resid) rows::load32_issue(args.resid + (size_t)row0 * args.ldc + n0 + c_lo, args.ldc, nvalid, lane, gn);
 #pragma unroll 1
@@ -228,8 +237,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (epi == EPI_NONE) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
-          rows::store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl,
-                            lane, f);
+          rows::store32_f32_async(&tmC, st, col, row0, lane, f);
           continue;
         }
         if (bias_smem) {
@@ -252,14 +260,16 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
             for (int j = 0; j < 32; ++j) f[j] = gelu_as(f[j]);
           }
-          rows::store32_bf16(reinterpret_cast<bf16*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl,
-                             lane, f);
-        } else {  // residual (+ LayerNorm statistics)
+          rows::store32_bf16_async(&tmC, st, col, row0, lane, f);
+        } else {  // residual (+ LayerNorm statistics; x stays in TMEM for the normalisation)
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
-          rows::store32_f32(reinterpret_cast<float*>(args.C) + (size_t)row0 * args.ldc + col, args.ldc, nvalid, tl,
-                            lane, f);
+          rows::store32_f32_async(&tmC, st, col, row0, lane, f);
           if (epi == EPI_RESID_LN) {
+            uint32_t xr[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xr[j] = __float_as_uint(f[j]);
+            tc::tmem_st_32x32b_x32(tbase + c0, xr);
             float cm = 0.f;
 #pragma unroll
             for (int j = 0; j < 32; ++j) cm += f[j];
@@ -276,10 +286,11 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         }
       }
       if (epi == EPI_RESID_LN) {
-        // merge the EW column groups of each row (fixed order), then normalize the stored row
-        float* st = ln_stats + ((size_t)(warp - 2) * 32 + lane) * 2;
-        st[0] = run_mean;
-        st[1] = run_m2;
+        tc::tmem_st_wait();
+        // merge the EW column groups of each row (fixed order), then normalize the row held in TMEM
+        float* sts = ln_stats + ((size_t)(warp - 2) * 32 + lane) * 2;
+        sts[0] = run_mean;
+        sts[1] = run_m2;
         named_sync(1 + quarter, 32 * EW);
         float mean = 0.f, m2 = 0.f, n = 0.f;
 #pragma unroll
@@ -295,31 +306,29 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         }
         named_sync(1 + quarter, 32 * EW);  // the statistics slots are reused by the next tile
         const float rstd = rsqrtf(m2 / n + 1e-5f);
-        const float* xs = reinterpret_cast<const float*>(args.C) + (size_t)row0 * args.ldc + n0;
-        rows::load32_issue(xs + c_lo, args.ldc, nvalid, lane, gn);
 #pragma unroll 1
         for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
-          const int col = n0 + c0;
+          uint32_t xr[32];
+          tc::tmem_ld_32x32b_x32(tbase + c0, xr);
+          tc::tmem_ld_wait();
           float xv[32];
-          // the rows this warp stored above (the same 32 x 32 blocks)
-          rows::load32_finish(tl, lane, gn, xv);
-          if (c0 + 32 < c_hi) rows::load32_issue(xs + c0 + 32, args.ldc, nvalid, lane, gn);
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
             const float4 tg = *reinterpret_cast<const float4*>(s_lng + c0 + j);
             const float4 tb = *reinterpret_cast<const float4*>(s_lnb + c0 + j);
-            xv[j] = (xv[j] - mean) * rstd * tg.x + tb.x;
-            xv[j + 1] = (xv[j + 1] - mean) * rstd * tg.y + tb.y;
-            xv[j + 2] = (xv[j + 2] - mean) * rstd * tg.z + tb.z;
-            xv[j + 3] = (xv[j + 3] - mean) * rstd * tg.w + tb.w;
+            xv[j] = (__uint_as_float(xr[j]) - mean) * rstd * tg.x + tb.x;
+            xv[j + 1] = (__uint_as_float(xr[j + 1]) - mean) * rstd * tg.y + tb.y;
+            xv[j + 2] = (__uint_as_float(xr[j + 2]) - mean) * rstd * tg.z + tb.z;
+            xv[j + 3] = (__uint_as_float(xr[j + 3]) - mean) * rstd * tg.w + tb.w;
           }
-          rows::store32_bf16(args.ln_out + (size_t)row0 * N + col, N, nvalid, tl, lane, xv);
+          rows::store32_bf16_async(&tmLN, st, n0 + c0, row0, lane, xv);
         }
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
     }
+    rows::async_drain(lane);
   }
 
   tc::fence_before_sync();
@@ -367,6 +376,21 @@ int num_sms() {
   return n;
 }
 
+// Store map of a [rows][inner] matrix (row pitch ld elements of es bytes): 32-row boxes of
+// 64 bytes in the 64-byte swizzle that the epilogue's staging tiles use.
+bool make_store_map(CUtensorMap* m, const void* base, bool f32, uint64_t inner, uint64_t rows, uint64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const uint32_t es = f32 ? 4 : 2;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {ld * es};
+  cuuint32_t box[2] = {64 / es, 32};
+  cuuint32_t ess[2] = {1, 1};
+  return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+            strides, box, ess, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN>
 cudaError_t launch_bn(const bf16* A, const bf16* Bt, const GemmArgs& args, cudaStream_t st) {
   using Cfg = TcCfg<BN>;
@@ -382,7 +406,18 @@ cudaError_t launch_bn(const bf16* A, const bf16* Bt, const GemmArgs& args, cudaS
   if (!make_map_2d(&mb, Bt, (uint64_t)args.K, (uint64_t)args.N, BK, BN)) return cudaErrorInvalidValue;
   const int tiles = ((args.M + BM - 1) / BM) * (args.N / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  gemm_tc_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(ma, mb, args);
+  // outputs: C (f32 for the residual epilogues and EPI_NONE, else bf16) and the LayerNorm output
+  CUtensorMap mc, ml;
+  const bool c32 = args.epi == EPI_NONE || args.epi == EPI_BIAS_RESID || args.epi == EPI_RESID_LN;
+  if ((reinterpret_cast<uintptr_t>(args.C) & 15) || (args.ldc * (c32 ? 4 : 2)) % 16) return cudaErrorInvalidValue;
+  if (!make_store_map(&mc, args.C, c32, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.ldc))
+    return cudaErrorInvalidValue;
+  ml = mc;
+  if (args.epi == EPI_RESID_LN &&
+      ((reinterpret_cast<uintptr_t>(args.ln_out) & 15) ||
+       !make_store_map(&ml, args.ln_out, false, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.N)))
+    return cudaErrorInvalidValue;
+  gemm_tc_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(ma, mb, mc, ml, args);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 // warp's 2 KB, 128-byte-aligned staging area.  All 32 lanes must call.
 #pragma once
 #include "common.cuh"
+#include "tc_primitives.cuh"
 
 namespace inpaint {
 namespace rows {
@@ -104,6 +105,70 @@ __device__ __forceinline__ void store32_bf16(bf16* base, size_t ld, int nvalid, 
     const uint4 t = *reinterpret_cast<const uint4*>(tile + slot(r, ch));
     if (r < nvalid) *reinterpret_cast<uint4*>(base + (size_t)r * ld + 8 * ch) = t;
   }
+  __syncwarp();
+}
+
+// Asynchronous form for the tensor-memory epilogues: the warp stages a 32-row x 64-byte
+// box in one of its two tiles (the same swizzle, which is the TMA 64-byte swizzle when
+// the tile is 512-byte aligned) and lane 0 hands it to a TMA store; the warp does not
+// wait for global memory.  A tile is reused only once the store issued from it two boxes
+// earlier has read it.  Rows past the tensor map's extent are not written.
+struct AsyncRows {
+  uint8_t* tiles;  // 2 x TILE_BYTES, 512-byte aligned
+  int k;
+};
+
+__device__ __forceinline__ uint8_t* async_acquire(AsyncRows& a, int lane) {
+  uint8_t* t = a.tiles + (a.k & 1) * TILE_BYTES;
+  ++a.k;
+  if (lane == 0) tc::bulk_wait_read<1>();
+  __syncwarp();
+  return t;
+}
+
+__device__ __forceinline__ void async_issue(const CUtensorMap* map, const uint8_t* t, int c0, int r0, int lane) {
+  tc::fence_proxy_async_smem();
+  __syncwarp();
+  if (lane == 0) {
+    tc::tma_store_2d(map, t, c0, r0);
+    tc::bulk_commit();
+  }
+}
+
+// Row `lane` of a 32 x 32 bf16 box at (column c0, row r0) = v.
+__device__ __forceinline__ void store32_bf16_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int lane,
+                                                   const float (&v)[32]) {
+  uint8_t* t = async_acquire(a, lane);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
+      w[e] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(t + slot(lane, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  async_issue(map, t, c0, r0, lane);
+}
+
+// Row `lane` of a 32 x 32 FP32 block at (column c0, row r0) = v, as two 16-column boxes.
+__device__ __forceinline__ void store32_f32_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int lane,
+                                                  const float (&v)[32]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint8_t* t = async_acquire(a, lane);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      *reinterpret_cast<float4*>(t + slot(lane, j)) =
+          make_float4(v[16 * h + 4 * j], v[16 * h + 4 * j + 1], v[16 * h + 4 * j + 2], v[16 * h + 4 * j + 3]);
+    async_issue(map, t, c0 + 16 * h, r0, lane);
+  }
+}
+
+// All of this warp's stores complete (before the CTA exits).
+__device__ __forceinline__ void async_drain(int lane) {
+  if (lane == 0) tc::bulk_wait<0>();
   __syncwarp();
 }
 
