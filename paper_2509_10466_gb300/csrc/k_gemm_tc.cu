@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (epi == EPI_NONE) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
-          rows::store32_f32_async(&tmC, st, col, row0, lane, f);
+          rows::store32_f32_async(&tmC, st, col, row0, nvalid, lane, f);
           continue;
         }
         if (bias_smem) {
@@ -260,11 +260,11 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
             for (int j = 0; j < 32; ++j) f[j] = gelu_as(f[j]);
           }
-          rows::store32_bf16_async(&tmC, st, col, row0, lane, f);
+          rows::store32_bf16_async(&tmC, st, col, row0, nvalid, lane, f);
         } else {  // residual (+ LayerNorm statistics; x stays in TMEM for the normalisation)
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
-          rows::store32_f32_async(&tmC, st, col, row0, lane, f);
+          rows::store32_f32_async(&tmC, st, col, row0, nvalid, lane, f);
           if (epi == EPI_RESID_LN) {
             uint32_t xr[32];
 #pragma unroll
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             xv[j + 2] = (__uint_as_float(xr[j + 2]) - mean) * rstd * tg.z + tb.z;
             xv[j + 3] = (__uint_as_float(xr[j + 3]) - mean) * rstd * tg.w + tb.w;
           }
-          rows::store32_bf16_async(&tmLN, st, n0 + c0, row0, lane, xv);
+          rows::store32_bf16_async(&tmLN, st, n0 + c0, row0, nvalid, lane, xv);
         }
       }
       tc::fence_before_sync();

@@ -26,8 +26,9 @@
 // per TMEM lane quarter, splitting the chunk's columns), 12..15 final epilogue (one per
 // lane quarter, whole rows: residual, store, LayerNorm).  The final epilogue of a tile
 // overlaps the next tile's hidden chunks; it drains the output accumulator before the
-// next tile's MMA2 can start, so residual loads run one chunk ahead, and rows move
-// between global and shared memory in whole 64-byte segments (warp_rows.cuh).
+// next tile's MMA2 can start, so residual loads run one chunk ahead (rows moved in whole
+// 64-byte segments, warp_rows.cuh), the new x goes out by TMA stores and back into OUT,
+// and the LayerNorm pass reads it from TMEM and stores by TMA as well.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -46,7 +47,7 @@ constexpr int ROLE_WARPS = 4;                 // warpgroup 0: TMA producer, MMA 
 constexpr int EPI_WARPS = 8;                  // GELU warps: two per TMEM lane quarter
 constexpr int OUT_WARPS = 4;                  // final-epilogue warps: one per lane quarter
 constexpr int THREADS = 32 * (ROLE_WARPS + EPI_WARPS + OUT_WARPS);
-constexpr int RING = 5;                       // 16 KB weight stages
+constexpr int RING = 4;                       // 16 KB weight stages
 constexpr uint16_t PAIR = 0x3;                // both CTAs of the cluster
 // Registers per thread: launched with 65536 / THREADS; warpgroup 0 gives most of its share
 // to the final-epilogue warpgroup.
@@ -68,7 +69,8 @@ struct MlpCfg {
   static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a W2 k-block (D/2 rows)
   static constexpr int PARAM_FLOATS = 1024 + 3 * D;          // b1 (hid <= 1024), b2, LayerNorm scale/shift
   static constexpr int SMEM_BYTES = A_BYTES + NB * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
-                                    512 /*barriers*/ + PARAM_FLOATS * 4 + OUT_WARPS * rows::TILE_BYTES;
+                                    512 /*barriers*/ + PARAM_FLOATS * 4 + 1024 /*tile alignment*/ +
+                                    OUT_WARPS * 3 * rows::TILE_BYTES /*two store tiles + a load tile per warp*/;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 + HC b
   static_assert(W1_KB * W1_BOX <= STAGE_BYTES && W2_BOX <= STAGE_BYTES, "stage too small");
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
@@ -98,6 +100,8 @@ template <int D>
 __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constant__ CUtensorMap tmY,
                                                             const __grid_constant__ CUtensorMap tmW1,
                                                             const __grid_constant__ CUtensorMap tmW2,
+                                                            const __grid_constant__ CUtensorMap tmX,
+                                                            const __grid_constant__ CUtensorMap tmLN,
                                                             const MlpArgs args) {
   using Cfg = MlpCfg<D>;
   extern __shared__ uint8_t smem_raw[];
@@ -123,7 +127,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   float* s_b2 = s_b1 + 1024;                                                      // [D]
   float* s_lng = s_b2 + D;
   float* s_lnb = s_lng + D;
-  uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_lnb + D);  // [OUT_WARPS][2 KB]
+  uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_lnb + D) + 1023) &
+                                               ~uintptr_t(1023));  // [OUT_WARPS][3][2 KB]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, NJ = args.hid / HC;
@@ -352,7 +357,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     const int fw = warp - ROLE_WARPS - EPI_WARPS;  // 0 .. OUT_WARPS-1
     const int quarter = warp & 3;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
-    uint8_t* tl = s_tile + (size_t)fw * rows::TILE_BYTES;
+    rows::AsyncRows st{s_tile + (size_t)fw * 3 * rows::TILE_BYTES, 0};
+    uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;  // residual loads
     bool ok = true;
     int t = 0;
     for (int p = cid; p < pairs && ok; p += ncl, ++t) {
@@ -364,6 +370,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       if (!tc::mbar_wait(o_full, t & 1, abort_flag)) { ok = false; break; }
       __syncwarp();
       tc::fence_after_sync();
+      // pass 1: x = x + OUT + b2 (stored asynchronously and written back into OUT), statistics
       float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
       float4 gn[8];  // the next chunk's residual, loaded one chunk ahead
       rows::load32_issue(xb, D, nvalid, lane, gn);
@@ -383,7 +390,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           f[k + 2] += __uint_as_float(v[k + 2]) + b.z;
           f[k + 3] += __uint_as_float(v[k + 3]) + b.w;
         }
-        rows::store32_f32(xb + c0, D, nvalid, tl, lane, f);
+        rows::store32_f32_async(&tmX, st, c0, row0, nvalid, lane, f);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = __float_as_uint(f[k]);
+        tc::tmem_st_32x32b_x32(lane_base + c0, v);
         float cm = 0.f;
 #pragma unroll
         for (int k = 0; k < 32; ++k) cm += f[k];
@@ -397,28 +407,31 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         run_m2 += cq + dl * dl * (run_n * 32.f / nn);
         run_n = nn;
       }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // OUT drained: the next tile's MMA2 may start
+      tc::tmem_st_wait();
+      // pass 2: LayerNorm of the row held in OUT, stored asynchronously; then OUT is free
       const float rstd = rsqrtf(run_m2 / run_n + 1e-5f);
-      rows::load32_issue(xb, D, nvalid, lane, gn);
 #pragma unroll 1
       for (int c0 = 0; c0 < D; c0 += 32) {
+        uint32_t xr[32];
+        tc::tmem_ld_32x32b_x32(lane_base + c0, xr);
+        tc::tmem_ld_wait();
         float xv[32];
-        rows::load32_finish(tl, lane, gn, xv);  // the rows this warp stored above
-        if (c0 + 32 < D) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
 #pragma unroll
         for (int k = 0; k < 32; k += 4) {
           const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
           const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
-          xv[k] = (xv[k] - run_mean) * rstd * g4.x + b4.x;
-          xv[k + 1] = (xv[k + 1] - run_mean) * rstd * g4.y + b4.y;
-          xv[k + 2] = (xv[k + 2] - run_mean) * rstd * g4.z + b4.z;
-          xv[k + 3] = (xv[k + 3] - run_mean) * rstd * g4.w + b4.w;
+          xv[k] = (__uint_as_float(xr[k]) - run_mean) * rstd * g4.x + b4.x;
+          xv[k + 1] = (__uint_as_float(xr[k + 1]) - run_mean) * rstd * g4.y + b4.y;
+          xv[k + 2] = (__uint_as_float(xr[k + 2]) - run_mean) * rstd * g4.z + b4.z;
+          xv[k + 3] = (__uint_as_float(xr[k + 3]) - run_mean) * rstd * g4.w + b4.w;
         }
-        rows::store32_bf16(args.ln_out + (size_t)row0 * D + c0, D, nvalid, tl, lane, xv);
+        rows::store32_bf16_async(&tmLN, st, c0, row0, nvalid, lane, xv);
       }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // OUT drained: the next tile's MMA2 may start
     }
+    rows::async_drain(lane);
     if (!ok) {
       if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
       *abort_flag = 1;
@@ -458,6 +471,21 @@ bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Store map of a dense [rows][inner] matrix: 32-row boxes of 64 bytes, 64-byte swizzle
+// (the layout of the drain warps' staging tiles).
+bool store_map(CUtensorMap* m, const void* base, bool f32, uint64_t inner, uint64_t rows) {
+  auto fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const uint32_t es = f32 ? 4 : 2;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * es};
+  cuuint32_t box[2] = {64 / es, 32};
+  cuuint32_t ess[2] = {1, 1};
+  return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+            strides, box, ess, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -494,13 +522,15 @@ cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpA
     if (e != cudaSuccess) return e;
     max_pairs = n > 0 ? n : 1;
   }
-  CUtensorMap my, m1, m2;
+  CUtensorMap my, m1, m2, mx, mln;
   if (!map2d(&my, Y, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
+  if (!store_map(&mx, a.X, true, D, (uint64_t)a.M) || !store_map(&mln, a.ln_out, false, D, (uint64_t)a.M))
+    return cudaErrorInvalidValue;
   if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC / 2)) return cudaErrorInvalidValue;
   if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;
   const int pairs = ((a.M + BM - 1) / BM + 1) / 2;
   lc.gridDim = dim3((pairs < max_pairs ? pairs : max_pairs) * 2);
-  cudaError_t e = cudaLaunchKernelEx(&lc, kern, my, m1, m2, a);
+  cudaError_t e = cudaLaunchKernelEx(&lc, kern, my, m1, m2, mx, mln, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

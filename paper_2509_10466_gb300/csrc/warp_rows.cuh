@@ -112,7 +112,8 @@ __device__ __forceinline__ void store32_bf16(bf16* base, size_t ld, int nvalid, 
 // box in one of its two tiles (the same swizzle, which is the TMA 64-byte swizzle when
 // the tile is 512-byte aligned) and lane 0 hands it to a TMA store; the warp does not
 // wait for global memory.  A tile is reused only once the store issued from it two boxes
-// earlier has read it.  Rows past the tensor map's extent are not written.
+// earlier has read it.  Rows past the tensor map's extent are not written, and a box with
+// no row inside it (nvalid <= 0) is not issued at all.
 struct AsyncRows {
   uint8_t* tiles;  // 2 x TILE_BYTES, 512-byte aligned
   int k;
@@ -126,18 +127,19 @@ __device__ __forceinline__ uint8_t* async_acquire(AsyncRows& a, int lane) {
   return t;
 }
 
-__device__ __forceinline__ void async_issue(const CUtensorMap* map, const uint8_t* t, int c0, int r0, int lane) {
+__device__ __forceinline__ void async_issue(const CUtensorMap* map, const uint8_t* t, int c0, int r0, int nvalid,
+                                            int lane) {
   tc::fence_proxy_async_smem();
   __syncwarp();
-  if (lane == 0) {
+  if (lane == 0 && nvalid > 0) {
     tc::tma_store_2d(map, t, c0, r0);
     tc::bulk_commit();
   }
 }
 
 // Row `lane` of a 32 x 32 bf16 box at (column c0, row r0) = v.
-__device__ __forceinline__ void store32_bf16_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int lane,
-                                                   const float (&v)[32]) {
+__device__ __forceinline__ void store32_bf16_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int nvalid,
+                                                   int lane, const float (&v)[32]) {
   uint8_t* t = async_acquire(a, lane);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -149,12 +151,12 @@ __device__ __forceinline__ void store32_bf16_async(const CUtensorMap* map, Async
     }
     *reinterpret_cast<uint4*>(t + slot(lane, j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  async_issue(map, t, c0, r0, lane);
+  async_issue(map, t, c0, r0, nvalid, lane);
 }
 
 // Row `lane` of a 32 x 32 FP32 block at (column c0, row r0) = v, as two 16-column boxes.
-__device__ __forceinline__ void store32_f32_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int lane,
-                                                  const float (&v)[32]) {
+__device__ __forceinline__ void store32_f32_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int nvalid,
+                                                  int lane, const float (&v)[32]) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint8_t* t = async_acquire(a, lane);
@@ -162,7 +164,7 @@ __device__ __forceinline__ void store32_f32_async(const CUtensorMap* map, AsyncR
     for (int j = 0; j < 4; ++j)
       *reinterpret_cast<float4*>(t + slot(lane, j)) =
           make_float4(v[16 * h + 4 * j], v[16 * h + 4 * j + 1], v[16 * h + 4 * j + 2], v[16 * h + 4 * j + 3]);
-    async_issue(map, t, c0 + 16 * h, r0, lane);
+    async_issue(map, t, c0 + 16 * h, r0, nvalid, lane);
   }
 }
 
