@@ -109,6 +109,16 @@ def test_bf16_fused_mlp_odd_tile_counts(dim, ratio, H, W):
     check_parity(cfg, weights, x, hole, TOL_BF16)
 
 
+@pytest.mark.parametrize("dim,H,W", [(384, 64, 96), (512, 96, 64)])
+def test_bf16_wide_decoder_channels(dim, H, W):
+    """Wider models put 96 and 128 channels on the tensor-core decoder (d/4), the head of
+    d512 reads 64 channels."""
+    cfg = ModelConfig(dim=dim, heads=dim // 32, window=8, blocks=1, mlp_ratio=1, precision=BF16)
+    weights = S.make_weights(cfg, seed=dim, perturb=True)
+    x, hole = inputs(1, H, W, "polygons", seed=dim + 1)
+    check_parity(cfg, weights, x, hole, TOL_BF16)
+
+
 def test_bf16_precision_workload_512_full_size():
     """Precision workload at full size: 4 frames of 512x512, d256 h8, 8 blocks, MLP ratio 4."""
     w = WORKLOAD_B
