@@ -12,7 +12,8 @@ CUDA events (L2 flushed by a 256 MiB write between steps); `e2e` is the same met
 through the host-buffer entry point (pinned host -> device copies and the device ->
 host read of the output inside the timed region).  Beside it: the plain FP32 form on
 the same GPU, p50/p99 step latency, attention TFLOP/s, the roofline of the dominant
-kernel from per-launch CUDA events, and the FP64 oracle timed on the host cores.
+kernel from per-launch CUDA events (a second run of the K steps, as the events between
+launches add time), and the FP64 oracle timed on the host cores.
 With N > 1 every rank runs an independent replica (frames are independent).
 """
 from __future__ import annotations
@@ -272,29 +273,36 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, per-step events, per-launch events (roofline), L2 flush between steps
+    # ---- timed region: K steps, per-step events, L2 flush between steps
+    def timed_steps():
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     n0 = binding.inpaint_launch_count(ctx)
-    binding.inpaint_profile_read(ctx)  # clear
-    binding.inpaint_profile_enable(ctx, True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        evs[k][0].record(stream)
-        step()
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = timed_steps()
+    launches = binding.inpaint_launch_count(ctx) - n0
     if dist:
         dist.barrier()
+    # ---- the same K steps again with an event pair around every kernel launch (per-class
+    # times for the roofline); the events between launches cost time, so these steps do
+    # not enter `value`
+    binding.inpaint_profile_read(ctx)  # clear
+    binding.inpaint_profile_enable(ctx, True)
+    prof_step_ms = timed_steps()
     binding.inpaint_profile_enable(ctx, False)
-    launches = binding.inpaint_launch_count(ctx) - n0
     clk = clocks.stop()
     prof = binding.inpaint_profile_read(ctx)
-    step_ms = [a.elapsed_time(b) for a, b in evs]
     job_s, value = job_time_and_throughput(sum(step_ms) / 1000.0, B * args.steps, dist, dev)
     total_ms = 1000.0 * job_s
     ms_per_step = total_ms / args.steps
@@ -492,6 +500,7 @@ def main():
                        "seq_len": (-(-H // 32) * 8) * (-(-W // 32) * 8), "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "latency_ms": {"p50": p50, "p99": p99, "per": f"batch of {B} frames"},
+            "ms_per_step_with_launch_events": sum(prof_step_ms) / len(prof_step_ms),
             "fp32_plain": fp32,
             "attn_tflops": attn_tflops,
             "roofline": roofline,

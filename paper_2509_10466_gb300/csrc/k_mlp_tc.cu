@@ -1,7 +1,7 @@
 // Fused MLP of a transformer block on tcgen05 (BF16 form):
 //   for a tile of token rows and hidden chunks j of 128 columns
-//     H_j  = gelu(Y . W1[:, j] + b1[j])            (MMA1 into TMEM, epilogue to SMEM)
-//     OUT += H_j . W2[j, :]                         (MMA2 from SMEM into TMEM)
+//     H_j  = gelu(Y . W1[:, j] + b1[j])            (MMA1 into TMEM, epilogue back into TMEM)
+//     OUT += H_j . W2[j, :]                         (MMA2, A operand from TMEM, into TMEM)
 //   x = x + OUT + b2, ln_out = LayerNorm(x) (the next block's LN1, or the final LN).
 // The hidden activations never leave the SM: this removes the write and re-read of the
 // [M, r*d] hidden tensor.
@@ -10,27 +10,34 @@
 // CTA holds its own 128 rows of Y and of H_j and half of every weight block, the even
 // CTA issues the MMAs for both, and each CTA's TMEM receives the accumulator rows of its
 // own 128 rows.  Per SM this halves the weight bytes that stream from L2 for the same
-// tensor work, which is what bounds a 128-row tile.
+// tensor work.
 //
 // Y (LN2 output, bf16 [M, D]) is loaded once per tile by TMA and stays in SMEM; W1^T
 // ([hid][D]) and W2^T ([D][hid]) k-blocks stream through a ring of 16 KB stages in the
 // order the MMA warp consumes them (MMA1 of chunk j+1 is issued before MMA2 of chunk j,
-// so the tensor core works while the epilogue warps turn H_j into bf16).  TMEM: OUT
-// (D cols) + two H buffers (128 cols each).  The bf16 H_j is written in the
-// 128-byte-swizzled K-major layout that the MMA descriptor expects (16-byte chunk c of
-// row r at c ^ (r%8)).  Barriers that the MMA warp waits on live in the even CTA and
-// count both CTAs' arrivals and TMA bytes; MMA completions are signalled to both CTAs.
+// so the tensor core works while the epilogue warps turn H_j into bf16); the ring takes
+// what shared memory is left (one chunk's weights at D = 256).  TMEM: OUT (D cols) + two
+// H buffers (128 cols each).  The
+// epilogue writes the bf16 H_j over the FP32 columns it has just read (two hidden
+// columns per 32-bit TMEM column, the tcgen05 A-operand layout), so no SMEM holds
+// hidden values.  Barriers that the MMA warp waits on live in the even CTA and count both
+// CTAs' arrivals and TMA bytes; MMA completions are signalled to both CTAs.
 //
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer (even CTA only; 2, 3 idle:
 // warpgroup 0 hands its registers to the final warps), 4..11 hidden-chunk epilogue (two
 // per TMEM lane quarter, splitting the chunk's columns), 12..15 final epilogue (one per
-// lane quarter, whole rows: residual, store, LayerNorm).  The final epilogue of a tile
-// overlaps the next tile's hidden chunks; it drains the output accumulator before the
-// next tile's MMA2 can start, so residual loads run one chunk ahead (rows moved in whole
-// 64-byte segments, warp_rows.cuh), the new x goes out by TMA stores and back into OUT,
-// and the LayerNorm pass reads it from TMEM and stores by TMA as well.
+// lane quarter).  The output accumulator must be drained (residual, store, LayerNorm)
+// before the next tile's MMA2 can start, and the tensor core idles meanwhile, so three
+// warps per lane quarter share each drain by columns: the final warp takes the first half
+// of the columns, and each GELU warp a quarter once it has finished the next tile's first
+// hidden chunk.  The three exchange per-row partial statistics (Welford) through shared
+// memory and merge them in one fixed order.  Residual loads run one 32-column block ahead
+// and rows move in whole 64-byte segments (warp_rows.cuh); the new x also goes back into
+// OUT, from where the LayerNorm pass reads it.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <type_traits>
 
 #include "common.cuh"
 #include "tc_primitives.cuh"
@@ -41,25 +48,31 @@ namespace inpaint {
 namespace {
 
 constexpr int BM = 128, BK = 64, HC = 128;   // rows per CTA, k-block, hidden chunk
-constexpr int NB = 2;                         // H buffers (TMEM and SMEM)
+constexpr int NB = 2;                         // H buffers in TMEM (FP32, then bf16 in place)
 constexpr int LOOK = NB - 1;                  // MMA1 runs this many chunks ahead of MMA2
 constexpr int ROLE_WARPS = 4;                 // warpgroup 0: TMA producer, MMA issuer, two idle
 constexpr int EPI_WARPS = 8;                  // GELU warps: two per TMEM lane quarter
 constexpr int OUT_WARPS = 4;                  // final-epilogue warps: one per lane quarter
 constexpr int THREADS = 32 * (ROLE_WARPS + EPI_WARPS + OUT_WARPS);
-constexpr int RING = 4;                       // 16 KB weight stages
 constexpr uint16_t PAIR = 0x3;                // both CTAs of the cluster
 // Registers per thread: launched with 65536 / THREADS; warpgroup 0 gives most of its share
 // to the final-epilogue warpgroup.
-constexpr int REG_LAUNCH = 65536 / THREADS, REG_ROLE = 64, REG_FINAL = 184;
-static_assert(ROLE_WARPS * REG_ROLE + EPI_WARPS * REG_LAUNCH + OUT_WARPS * REG_FINAL <=
+constexpr int REG_LAUNCH = 65536 / THREADS / 8 * 8;
+constexpr int REG_ROLE = 72, REG_FINAL = 184, REG_EPI = REG_LAUNCH;
+static_assert(ROLE_WARPS * REG_ROLE + EPI_WARPS * REG_EPI + OUT_WARPS * REG_FINAL <=
                   (ROLE_WARPS + EPI_WARPS + OUT_WARPS) * REG_LAUNCH,
               "register reallocation exceeds the launch allotment");
+constexpr int EPI_COLS = HC / (EPI_WARPS / 4);  // hidden columns of a chunk per GELU warp
+static_assert(EPI_COLS % 32 == 0 && EPI_COLS <= 64, "GELU warp column split");
+static_assert(EPI_WARPS == 8, "the output drain is shared by the final warp and two GELU warps per lane quarter");
+constexpr int DRAIN_WARPS = EPI_WARPS + OUT_WARPS;
+// Each drain warp stores by TMA from two staging tiles and loads residual rows through a
+// third.
+constexpr int DRAIN_TILES = 3 * DRAIN_WARPS;
 
 template <int D>
 struct MlpCfg {
   static constexpr int A_BYTES = BM * D * 2;                  // this CTA's Y rows, D/64 atoms of 16 KB
-  static constexpr int HS_BYTES = BM * HC * 2;                // one bf16 H chunk, HC/64 atoms of 16 KB
   static constexpr int KA = D / BK;                           // k-blocks of MMA1
   static constexpr int KH = HC / BK;                          // k-blocks of MMA2 per chunk
   static constexpr int STAGE_BYTES = 16384;
@@ -68,9 +81,19 @@ struct MlpCfg {
   static constexpr int W1_STAGES = KA / W1_KB;                // W1 stages per chunk
   static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a W2 k-block (D/2 rows)
   static constexpr int PARAM_FLOATS = 1024 + 3 * D;          // b1 (hid <= 1024), b2, LayerNorm scale/shift
-  static constexpr int SMEM_BYTES = A_BYTES + NB * HS_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
+  // 16 KB weight stages: as many as fit (up to two chunks' worth; four, one chunk, at D = 256)
+  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 3 * D) * 4 +
+                                     1024 /*tile alignment*/ + DRAIN_TILES * rows::TILE_BYTES + 3 * BM * 2 * 4;
+  static constexpr int RING_FIT = (232448 - FIXED_BYTES) / STAGE_BYTES;
+  static constexpr int RING = RING_FIT < 8 ? RING_FIT : 8;
+  static_assert(RING >= 4, "weight ring too shallow");
+  static constexpr int SMEM_BYTES = A_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
                                     512 /*barriers*/ + PARAM_FLOATS * 4 + 1024 /*tile alignment*/ +
-                                    OUT_WARPS * 3 * rows::TILE_BYTES /*two store tiles + a load tile per warp*/;
+                                    DRAIN_TILES * rows::TILE_BYTES /*staging tiles of the drain warps*/ +
+                                    3 * BM * 2 * 4 /*partial row statistics of the three drain slices*/;
+  // Drain column slices, in 32-column blocks: the final warp takes the first FS blocks,
+  // each GELU warp GS blocks (none when D = 64).
+  static constexpr int NCH = D / 32, GS = NCH / 4, FS = NCH - 2 * GS;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 + HC b
   static_assert(W1_KB * W1_BOX <= STAGE_BYTES && W2_BOX <= STAGE_BYTES, "stage too small");
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
@@ -87,14 +110,6 @@ struct MlpArgs {
   int* err;
 };
 
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void load32s(const float* p, float (&v)[32]) {  // shared memory
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float4 t = *reinterpret_cast<const float4*>(p + 4 * i);
-    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
-  }
-}
 
 template <int D>
 __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constant__ CUtensorMap tmY,
@@ -104,31 +119,31 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
                                                             const __grid_constant__ CUtensorMap tmLN,
                                                             const MlpArgs args) {
   using Cfg = MlpCfg<D>;
+  constexpr int RING = Cfg::RING;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sH = sA + Cfg::A_BYTES;                      // NB buffers
-  uint8_t* sR = sH + NB * Cfg::HS_BYTES;                // ring
+  uint8_t* sR = sA + Cfg::A_BYTES;                      // ring
   uint64_t* bar = reinterpret_cast<uint64_t*>(sR + RING * Cfg::STAGE_BYTES);
   uint64_t* full = bar;                 // [RING]  even CTA: both CTAs' weight bytes
   uint64_t* empty = full + RING;        // [RING]  both: stage consumed by the pair's MMAs
   uint64_t* a_full = empty + RING;      //         even CTA: both CTAs' Y bytes
   uint64_t* a_empty = a_full + 1;       //         both: Y no longer read
   uint64_t* h_full = a_empty + 1;       // [NB]    both: H_j in TMEM
-  uint64_t* h_empty = h_full + NB;      // [NB]    even CTA: both CTAs read H_j from TMEM
-  uint64_t* hs_full = h_empty + NB;     // [NB]    even CTA: both CTAs wrote bf16 H_j
-  uint64_t* hs_empty = hs_full + NB;    // [NB]    both: MMA2 read H_j from SMEM
-  uint64_t* o_full = hs_empty + NB;     //         both: OUT complete
+  uint64_t* h_done = h_full + NB;       // [NB]    even CTA: both CTAs turned H_j into bf16 (in TMEM)
+  uint64_t* o_full = h_done + NB;       //         both: OUT complete
   uint64_t* o_empty = o_full + 1;       //         even CTA: both CTAs drained OUT
   uint64_t* teardown = o_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
+  uint64_t* stat_bar = teardown + 1;    // [4]     per lane quarter: the three drain slices' statistics
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(stat_bar + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_b1 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [hid]
   float* s_b2 = s_b1 + 1024;                                                      // [D]
   float* s_lng = s_b2 + D;
   float* s_lnb = s_lng + D;
   uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_lnb + D) + 1023) &
-                                               ~uintptr_t(1023));  // [OUT_WARPS][3][2 KB]
+                                               ~uintptr_t(1023));  // [DRAIN_WARPS][2 KB]
+  float* s_stat = reinterpret_cast<float*>(s_tile + DRAIN_TILES * rows::TILE_BYTES);  // [3][BM][mean, M2]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, NJ = args.hid / HC;
@@ -148,12 +163,11 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     tc::mbar_init(a_empty, 1);
     for (int b = 0; b < NB; ++b) {
       tc::mbar_init(&h_full[b], 1);
-      tc::mbar_init(&h_empty[b], 2 * EPI_WARPS);
-      tc::mbar_init(&hs_full[b], 2 * EPI_WARPS);
-      tc::mbar_init(&hs_empty[b], 1);
+      tc::mbar_init(&h_done[b], 2 * EPI_WARPS);
     }
     tc::mbar_init(o_full, 1);
-    tc::mbar_init(o_empty, 2 * OUT_WARPS);
+    tc::mbar_init(o_empty, 2 * DRAIN_WARPS);
+    for (int k = 0; k < 4; ++k) tc::mbar_init(&stat_bar[k], 3 * 32);
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -176,6 +190,110 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   tc::cluster_sync();  // both CTAs' barriers exist before any remote arrival
   tc::fence_after_sync();
   const uint32_t tmem_base = *tmem_slot;
+
+  // The output drain of pair p's tile (the t-th of this CTA) for this warp's 32 rows
+  // (lane quarter warp & 3) and the nch 32-column blocks from column c_lo: x = x + OUT +
+  // b2, stored and written back into OUT, partial row statistics (Welford) exchanged with
+  // the quarter's two other drain warps (slice `role`), then the LayerNorm of the slice.
+  // Rows move in whole 64-byte segments through the warp's staging tiles: the stores go
+  // out by TMA from the two tiles of `st`, and `tl` serves the residual loads.  With
+  // `ahead`, each residual block is loaded while the previous one is processed (the GELU
+  // warps' slices go without: their registers are fewer).
+  auto drain = [&](auto ahead, int t, int p, int role, int c_lo, int nch, uint8_t* tl, rows::AsyncRows& st) -> bool {
+    const int quarter = warp & 3;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+    const int row0 = (2 * p + rank) * BM + quarter * 32;  // the thread owns row row0 + lane
+    const int nvalid = M - row0;
+    float* xb = args.X + (size_t)row0 * D;
+    if (!tc::mbar_wait(o_full, t & 1, abort_flag)) return false;
+    __syncwarp();
+    tc::fence_after_sync();
+    // pass 1: x = x + OUT + b2 (stored and written back into OUT), statistics
+    float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
+    if (nch > 0) {
+      float4 gn[8];  // the next block's residual, loaded one block ahead
+      if constexpr (decltype(ahead)::value) rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
+#pragma unroll 1
+      for (int c0 = c_lo; c0 < c_lo + 32 * nch; c0 += 32) {
+        uint32_t v[32];
+        tc::tmem_ld_32x32b_x32(lane_base + c0, v);
+        float f[32];
+        if constexpr (decltype(ahead)::value) {
+          rows::load32_finish(tl, lane, gn, f);
+          if (c0 + 32 < c_lo + 32 * nch) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
+        } else {
+          rows::load32_f32(xb + c0, D, nvalid, tl, lane, f);
+        }
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) {
+          const float4 b = *reinterpret_cast<const float4*>(s_b2 + c0 + k);
+          f[k] += __uint_as_float(v[k]) + b.x;
+          f[k + 1] += __uint_as_float(v[k + 1]) + b.y;
+          f[k + 2] += __uint_as_float(v[k + 2]) + b.z;
+          f[k + 3] += __uint_as_float(v[k + 3]) + b.w;
+        }
+        rows::store32_f32_async(&tmX, st, c0, row0, nvalid, lane, f);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = __float_as_uint(f[k]);
+        tc::tmem_st_32x32b_x32(lane_base + c0, v);
+        float cm = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) cm += f[k];
+        cm *= (1.f / 32.f);
+        float cq = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) cq = fmaf(f[k] - cm, f[k] - cm, cq);
+        const float nn = run_n + 32.f;
+        const float dl = cm - run_mean;
+        run_mean += dl * (32.f / nn);
+        run_m2 += cq + dl * dl * (run_n * 32.f / nn);
+        run_n = nn;
+      }
+      tc::tmem_st_wait();
+    }
+    // the three slices' statistics of each row, merged by all three warps in one order
+    float* sr = s_stat + (size_t)(quarter * 32 + lane) * 2;
+    sr[role * BM * 2] = run_mean;
+    sr[role * BM * 2 + 1] = run_m2;
+    tc::mbar_arrive(&stat_bar[quarter]);
+    if (!tc::mbar_wait(&stat_bar[quarter], t & 1, abort_flag)) return false;
+    float n = 0.f, mean = 0.f, m2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int nk = 32 * (k == 0 ? Cfg::FS : Cfg::GS);
+      if (nk == 0) continue;
+      const float mk = sr[k * BM * 2], qk = sr[k * BM * 2 + 1];
+      const float nn = __fadd_rn(n, (float)nk);
+      const float dl = __fsub_rn(mk, mean);
+      mean = __fadd_rn(mean, __fmul_rn(dl, __fdiv_rn((float)nk, nn)));
+      m2 = __fadd_rn(__fadd_rn(m2, qk), __fmul_rn(__fmul_rn(dl, dl), __fdiv_rn(__fmul_rn(n, (float)nk), nn)));
+      n = nn;
+    }
+    const float rstd = rsqrtf(__fadd_rn(__fdiv_rn(m2, n), 1e-5f));
+    // pass 2: LayerNorm of the slice, from the x held in OUT; then this slice of OUT is free
+#pragma unroll 1
+    for (int c0 = c_lo; c0 < c_lo + 32 * nch; c0 += 32) {
+      uint32_t xr[32];
+      tc::tmem_ld_32x32b_x32(lane_base + c0, xr);
+      tc::tmem_ld_wait();
+      float xv[32];
+#pragma unroll
+      for (int k = 0; k < 32; k += 4) {
+        const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
+        const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
+        xv[k] = (__uint_as_float(xr[k]) - mean) * rstd * g4.x + b4.x;
+        xv[k + 1] = (__uint_as_float(xr[k + 1]) - mean) * rstd * g4.y + b4.y;
+        xv[k + 2] = (__uint_as_float(xr[k + 2]) - mean) * rstd * g4.z + b4.z;
+        xv[k + 3] = (__uint_as_float(xr[k + 3]) - mean) * rstd * g4.w + b4.w;
+      }
+      rows::store32_bf16_async(&tmLN, st, c0, row0, nvalid, lane, xv);
+    }
+    tc::fence_before_sync();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // the next tile's MMA2 may start once all slices are out
+    return true;
+  };
 
   if (warp < ROLE_WARPS) {
     tc::setmaxnreg_dec<REG_ROLE>();
@@ -237,7 +355,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         };
         auto mma1 = [&](uint32_t qq) {  // H[qq % NB] = Y . W1_chunk^T
           const uint32_t hb = qq % NB, use = qq / NB;
-          if (use >= 1 && !tc::mbar_wait_cluster(&h_empty[hb], (use & 1) ^ 1, abort_flag)) return false;
+          // H buffer free: the previous use's GELU read it (h_done cannot run two phases
+          // ahead: its next phase needs this very MMA1), and that use's MMA2, issued
+          // before this MMA1, read the bf16 values before this MMA1 overwrites them
+          if (use >= 1 && !tc::mbar_wait_cluster(&h_done[hb], (use & 1) ^ 1, abort_flag)) return false;
           tc::fence_after_sync();
           const uint32_t dt = tmem_base + Cfg::H_COL0 + hb * HC;
           for (int st = 0; st < Cfg::W1_STAGES; ++st) {
@@ -255,22 +376,24 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           tc::mma_commit_pair(&h_full[hb], PAIR);
           return true;
         };
-        auto mma2 = [&](uint32_t qq, bool first, bool last, int t) {  // OUT (+)= Hs[qq % NB] . W2_chunk^T
+        auto mma2 = [&](uint32_t qq, bool first, bool last, int t) {  // OUT (+)= bf16 H[qq % NB] . W2_chunk^T
           const uint32_t hb = qq % NB, use = qq / NB;
           if (first && t >= 1 && !tc::mbar_wait_cluster(o_empty, (t - 1) & 1, abort_flag)) return false;
-          if (!tc::mbar_wait_cluster(&hs_full[hb], use & 1, abort_flag)) return false;
+          if (!tc::mbar_wait_cluster(&h_done[hb], use & 1, abort_flag)) return false;
           tc::fence_after_sync();
           for (int kb = 0; kb < Cfg::KH; ++kb) {
             int s;
             if (!pop(s)) return false;
-            const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sH + hb * Cfg::HS_BYTES + kb * (BM * BK * 2)));
             const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-              tc::mma_f16_pair(tmem_base, ad + 2 * kk, bd + 2 * kk, id2, (!first || kb || kk) ? 1u : 0u);
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              // hidden column k lives in GELU warp k / EPI_COLS's columns, two per TMEM column
+              const int k = kb * BK + kk * 16;
+              const uint32_t at = tmem_base + Cfg::H_COL0 + hb * HC + (k / EPI_COLS) * EPI_COLS + (k % EPI_COLS) / 2;
+              tc::mma_f16_pair_ta(tmem_base, at, bd + 2 * kk, id2, (!first || kb || kk) ? 1u : 0u);
+            }
             tc::mma_commit_pair(&empty[s], PAIR);
           }
-          tc::mma_commit_pair(&hs_empty[hb], PAIR);
           if (last) tc::mma_commit_pair(o_full, PAIR);
           return true;
         };
@@ -299,137 +422,78 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
       __syncwarp();
     }
   } else if (warp < ROLE_WARPS + EPI_WARPS) {
-    // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 swizzled SMEM operand of MMA2
+    // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 in TMEM (the A operand of MMA2);
+    // after a tile's first chunk, this warp's slice of the previous tile's output drain
     const int quarter = warp & 3, cg = (warp - ROLE_WARPS) >> 2;
-    const int r = quarter * 32 + lane;  // row within this CTA's 128 rows (= TMEM lane)
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+    rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 3 * rows::TILE_BYTES, 0};
+    uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;
+    const int d_lo = 32 * (Cfg::FS + cg * Cfg::GS);
+    constexpr int NL = EPI_COLS / 32;   // 32-column TMEM loads per chunk, issued before one wait
     uint32_t q = 0;
     bool ok = true;
-    for (int p = cid; p < pairs && ok; p += ncl) {
-      for (int j = 0; j < NJ; ++j, ++q) {
+    int t = 0;
+    for (int p = cid; p < pairs && ok; p += ncl, ++t) {
+      for (int j = 0; j < NJ && ok; ++j, ++q) {
         const uint32_t hb = q % NB, use = q / NB;
         if (!tc::mbar_wait(&h_full[hb], use & 1, abort_flag)) { ok = false; break; }
-        if (use >= 1 && !tc::mbar_wait(&hs_empty[hb], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
         __syncwarp();
         tc::fence_after_sync();
-        uint8_t* hs = sH + hb * Cfg::HS_BYTES;
-#pragma unroll 1
-        for (int c0 = cg * (HC / 2); c0 < (cg + 1) * (HC / 2); c0 += 32) {
-          uint32_t v[32];
-          tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + hb * HC + c0, v);
-          tc::tmem_ld_wait();
-          float bv[32];
-          load32s(s_b1 + j * HC + c0, bv);
+        const int cb = cg * EPI_COLS;
+        uint32_t v[NL][32];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + hb * HC + cb + 32 * l, v[l]);
+        tc::tmem_ld_wait();
+        // bf16 GELU values back into the first EPI_COLS / 2 columns this warp just read
+        // (pairs of hidden columns per 32-bit TMEM column): MMA2's A operand
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+          const float* bp = s_b1 + j * HC + cb + 32 * l;
           uint32_t pk[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const float a0 = gelu_as(__uint_as_float(v[2 * k]) + bv[2 * k]);
-            const float a1 = gelu_as(__uint_as_float(v[2 * k + 1]) + bv[2 * k + 1]);
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
-            pk[k] = *reinterpret_cast<uint32_t*>(&h2);
+          for (int k = 0; k < 16; k += 2) {
+            const float4 b4 = *reinterpret_cast<const float4*>(bp + 2 * k);
+            const uint32_t* x = &v[l][2 * k];
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(gelu_as(__uint_as_float(x[0]) + b4.x),
+                                                      gelu_as(__uint_as_float(x[1]) + b4.y));
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(gelu_as(__uint_as_float(x[2]) + b4.z),
+                                                      gelu_as(__uint_as_float(x[3]) + b4.w));
+            pk[k] = *reinterpret_cast<uint32_t*>(&h0);
+            pk[k + 1] = *reinterpret_cast<uint32_t*>(&h1);
           }
-          // columns c0 .. c0+31 of row r: atom c0/64, 16-byte chunks (c0%64)/8 .. +3, swizzled by r%8
-          uint8_t* rowp = hs + (c0 >> 6) * (BM * BK * 2) + r * 128;
-          const int ch0 = (c0 & 63) >> 3;
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            *reinterpret_cast<uint4*>(rowp + (((ch0 + k) ^ (r & 7)) << 4)) =
-                make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+          tc::tmem_st_32x32b_x16(lane_base + Cfg::H_COL0 + hb * HC + cb + 16 * l, pk);
         }
+        tc::tmem_st_wait();
         tc::fence_before_sync();
-        fence_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          tc::mbar_arrive_cluster(lead(&h_empty[hb]));
-          tc::mbar_arrive_cluster(lead(&hs_full[hb]));
-        }
+        if (lane == 0) tc::mbar_arrive_cluster(lead(&h_done[hb]));
+        // the previous tile's output is complete once this tile's first H chunk is (its
+        // MMAs were issued before this chunk's MMA1)
+        if (j == 0 && t >= 1) ok = drain(std::false_type{}, t - 1, p - ncl, 1 + cg, d_lo, Cfg::GS, tl, st);
       }
     }
-    // the pair's MMA2 releases of the last NB chunks land before this CTA may exit
-    for (uint32_t qq = (q >= NB ? q - NB : 0); qq < q; ++qq) tc::mbar_wait_timed(&hs_empty[qq % NB], (qq / NB) & 1);
+    if (ok && t >= 1) ok = drain(std::false_type{}, t - 1, cid + (t - 1) * ncl, 1 + cg, d_lo, Cfg::GS, tl, st);
+    rows::async_drain(lane);
     if (!ok) {
       if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
       *abort_flag = 1;
     }
   } else {
-    // ---- final: x = x + OUT + b2, LayerNorm(x) -> bf16; one whole row per thread
+    // ---- final: the first slice of every tile's output drain (x = x + OUT + b2, LN)
     tc::setmaxnreg_inc<REG_FINAL>();
-    const int fw = warp - ROLE_WARPS - EPI_WARPS;  // 0 .. OUT_WARPS-1
     const int quarter = warp & 3;
-    const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
-    rows::AsyncRows st{s_tile + (size_t)fw * 3 * rows::TILE_BYTES, 0};
-    uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;  // residual loads
+    rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 3 * rows::TILE_BYTES, 0};
+    uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;
     bool ok = true;
     int t = 0;
     for (int p = cid; p < pairs && ok; p += ncl, ++t) {
-      const int row0 = (2 * p + rank) * BM + quarter * 32;  // this warp's 32 rows; the thread owns row0 + lane
-      const int nvalid = M - row0;
-      float* xb = args.X + (size_t)row0 * D;
-      if (lane < nvalid)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(xb + (size_t)lane * D), "r"(D * 4) : "memory");
-      if (!tc::mbar_wait(o_full, t & 1, abort_flag)) { ok = false; break; }
-      __syncwarp();
-      tc::fence_after_sync();
-      // pass 1: x = x + OUT + b2 (stored asynchronously and written back into OUT), statistics
-      float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
-      float4 gn[8];  // the next chunk's residual, loaded one chunk ahead
-      rows::load32_issue(xb, D, nvalid, lane, gn);
-#pragma unroll 1
-      for (int c0 = 0; c0 < D; c0 += 32) {
-        uint32_t v[32];
-        tc::tmem_ld_32x32b_x32(lane_base + c0, v);
-        float f[32];
-        rows::load32_finish(tl, lane, gn, f);
-        if (c0 + 32 < D) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int k = 0; k < 32; k += 4) {
-          const float4 b = *reinterpret_cast<const float4*>(s_b2 + c0 + k);
-          f[k] += __uint_as_float(v[k]) + b.x;
-          f[k + 1] += __uint_as_float(v[k + 1]) + b.y;
-          f[k + 2] += __uint_as_float(v[k + 2]) + b.z;
-          f[k + 3] += __uint_as_float(v[k + 3]) + b.w;
-        }
-        rows::store32_f32_async(&tmX, st, c0, row0, nvalid, lane, f);
-#pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = __float_as_uint(f[k]);
-        tc::tmem_st_32x32b_x32(lane_base + c0, v);
-        float cm = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) cm += f[k];
-        cm *= (1.f / 32.f);
-        float cq = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) cq = fmaf(f[k] - cm, f[k] - cm, cq);
-        const float nn = run_n + 32.f;
-        const float dl = cm - run_mean;
-        run_mean += dl * (32.f / nn);
-        run_m2 += cq + dl * dl * (run_n * 32.f / nn);
-        run_n = nn;
-      }
-      tc::tmem_st_wait();
-      // pass 2: LayerNorm of the row held in OUT, stored asynchronously; then OUT is free
-      const float rstd = rsqrtf(run_m2 / run_n + 1e-5f);
-#pragma unroll 1
-      for (int c0 = 0; c0 < D; c0 += 32) {
-        uint32_t xr[32];
-        tc::tmem_ld_32x32b_x32(lane_base + c0, xr);
-        tc::tmem_ld_wait();
-        float xv[32];
-#pragma unroll
-        for (int k = 0; k < 32; k += 4) {
-          const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
-          const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
-          xv[k] = (__uint_as_float(xr[k]) - run_mean) * rstd * g4.x + b4.x;
-          xv[k + 1] = (__uint_as_float(xr[k + 1]) - run_mean) * rstd * g4.y + b4.y;
-          xv[k + 2] = (__uint_as_float(xr[k + 2]) - run_mean) * rstd * g4.z + b4.z;
-          xv[k + 3] = (__uint_as_float(xr[k + 3]) - run_mean) * rstd * g4.w + b4.w;
-        }
-        rows::store32_bf16_async(&tmLN, st, c0, row0, nvalid, lane, xv);
-      }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // OUT drained: the next tile's MMA2 may start
+      // the tile's residual rows head for L2 while its MMAs run
+      const int row0 = (2 * p + rank) * BM + quarter * 32;
+      if (lane < M - row0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(args.X + (size_t)(row0 + lane) * D),
+                     "r"(D * 4)
+                     : "memory");
+      ok = drain(std::true_type{}, t, p, 0, 0, Cfg::FS, tl, st);
     }
     rows::async_drain(lane);
     if (!ok) {
@@ -544,7 +608,8 @@ cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const
                           const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,
                           cudaStream_t st) {
   if (!mlp_tc_supported(d, hid) || M <= 0) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(W1t) | reinterpret_cast<uintptr_t>(W2t)) & 15)
+  if ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(W1t) | reinterpret_cast<uintptr_t>(W2t) |
+       reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(ln_out)) & 15)
     return cudaErrorInvalidValue;
   MlpArgs a{X, ln_out, b1, b2, ln_g, ln_b, M, hid, err};
   if (d == 256) return launch_d<256>(Y, W1t, W2t, a, st);
