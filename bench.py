@@ -133,7 +133,7 @@ def flops_per_frame(m, H, W):
         "proj_gemm": 2 * N * d * d * L,
         "fc1_gemm": 2 * N * d * r * d * L,
         "fc2_gemm": 2 * N * r * d * d * L,
-        "mlp_fused": 4 * N * d * r * d * L,
+        "proj_mlp_fused": 2 * N * d * d * L + 4 * N * d * r * d * L,
         "decoder1": 2 * (4 * N) * 9 * d * c1,
         "decoder2": 2 * (16 * N) * 9 * c1 * c2,
         "head_composite": 2 * (16 * N) * 9 * c2 * 3,
@@ -156,7 +156,9 @@ def bytes_per_frame(m, H, W, act_bytes=2):
         "proj_gemm": L * N * (d * a + 2 * d * 4 + d * a),
         "fc1_gemm": L * N * (d * a + r * d * a),
         "fc2_gemm": L * N * (r * d * a + 2 * d * 4 + d * a),
-        "mlp_fused": L * N * (d * a + 2 * d * 4 + d * a),
+        # the fused projection + MLP reads the attention output and the residual row and
+        # writes the new residual row and its LayerNorm
+        "proj_mlp_fused": L * N * (d * a + 2 * d * 4 + d * a),
         "decoder1": N * d * a + 4 * N * m.c1 * a,
         "decoder2": 4 * N * m.c1 * a + 16 * N * m.c2 * a,
         "head_composite": 16 * N * m.c2 * a + 25 * H * W,

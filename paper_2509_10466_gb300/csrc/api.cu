@@ -260,22 +260,24 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
         TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp)));
       }
       if (temporal) TRY(record_memory(qkv));
+      if (fuse_ln && mlp_tc_supported(d, c->hid)) {
+        // projection, residual, LN2 and the whole MLP in one kernel: only the attention
+        // output and the residual row come in, only the new residual row and its LN leave
+        const bool last = l + 1 == c->L;
+        const float* ng = c->w32 + (last ? o.lnfg : o.blk[l + 1].ln1g);
+        const float* nb = c->w32 + (last ? o.lnfb : o.blk[l + 1].ln1b);
+        LaunchScope ls(c, st, K_MLP);
+        TRY(cuda_err(launch_proj_mlp_tc(ao, wproj, c->w32 + b.projb, c->w32 + b.ln2g, c->w32 + b.ln2b, wfc1, wfc2,
+                                        c->w32 + b.fc1b, c->w32 + b.fc2b, tok, ng, nb, ln, M, d, c->hid, err, st)));
+        ln_ready = true;
+        continue;
+      }
       if (fuse_ln) {
         LaunchScope ls(c, st, K_PROJ);
         TRY(cuda_err(launch_gemm_tc_resid_ln(ao, wproj, tok, M, d, d, c->w32 + b.projb, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, err, st)));
       } else {
         { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_tc(ao, wproj, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, err, st))); }
         { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
-      }
-      if (fuse_ln && mlp_tc_supported(d, c->hid)) {
-        // whole MLP in one kernel: the hidden activations stay on chip
-        const bool last = l + 1 == c->L;
-        const float* ng = c->w32 + (last ? o.lnfg : o.blk[l + 1].ln1g);
-        const float* nb = c->w32 + (last ? o.lnfb : o.blk[l + 1].ln1b);
-        LaunchScope ls(c, st, K_MLP);
-        TRY(cuda_err(launch_mlp_tc(ln, wfc1, wfc2, c->w32 + b.fc1b, c->w32 + b.fc2b, tok, ng, nb, ln, M, d, c->hid, err, st)));
-        ln_ready = true;
-        continue;
       }
       { LaunchScope ls(c, st, K_FC1); TRY(cuda_err(launch_gemm_tc(ln, wfc1, hid, c->hid, M, c->hid, d, EPI_BIAS_GELU, c->w32 + b.fc1b, nullptr, err, st))); }
       if (fuse_ln) {

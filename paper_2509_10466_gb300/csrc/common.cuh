@@ -111,13 +111,15 @@ bool gemm_tc_ln_supported(int N);
 cudaError_t launch_gemm_tc_resid_ln(const bf16* A, const bf16* Bt, float* X, int M, int N, int K, const float* bias,
                                     const float* ln_g, const float* ln_b, bf16* ln_out, int* err, cudaStream_t st);
 
-// Fused MLP on tcgen05: X += gelu(Y W1 + b1) W2 + b2 and ln_out = LN(X) without writing
-// the hidden activations; W1t [hid][d] and W2t [d][hid] bf16 (K-major).  Y may alias
-// ln_out.  Supported for d in {64, 128, 256} and hid a multiple of 128.
+// Fused attention projection + MLP on tcgen05: x1 = X + A Wp + bp, Y = LN2(x1),
+// X = x1 + gelu(Y W1 + b1) W2 + b2 and ln_out = LN(X), without writing x1, Y or the hidden
+// activations; Wpt [d][d], W1t [hid][d] and W2t [d][hid] bf16 (K-major), A [M][d] bf16.
+// Supported for d in {64, 128, 256} and hid a multiple of 128 up to 1024.
 bool mlp_tc_supported(int d, int hid);
-cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const float* b1, const float* b2, float* X,
-                          const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,
-                          cudaStream_t st);
+cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const float* ln2_g,
+                               const float* ln2_b, const bf16* W1t, const bf16* W2t, const float* b1,
+                               const float* b2, float* X, const float* ln_g, const float* ln_b, bf16* ln_out, int M,
+                               int d, int hid, int* err, cudaStream_t st);
 
 // Mask-aware window attention of all frames; qkv [B*Nt, 3d] (T), v_in/v_out u8 [B*Nt].
 // relpos (optional, device f32 [heads][15][15]): relative-position bias added to the

@@ -1,39 +1,43 @@
-// Fused MLP of a transformer block on tcgen05 (BF16 form):
-//   for a tile of token rows and hidden chunks j of 128 columns
-//     H_j  = gelu(Y . W1[:, j] + b1[j])            (MMA1 into TMEM, epilogue back into TMEM)
-//     OUT += H_j . W2[j, :]                         (MMA2, A operand from TMEM, into TMEM)
-//   x = x + OUT + b2, ln_out = LayerNorm(x) (the next block's LN1, or the final LN).
-// The hidden activations never leave the SM: this removes the write and re-read of the
-// [M, r*d] hidden tensor.
+// Fused attention projection + MLP of a transformer block on tcgen05 (BF16 form), for
+// a tile of token rows:
+//   x1   = x + A . Wp + bp                      (MMA_P into TMEM; A = attention output)
+//   Y    = LayerNorm2(x1)                        (bf16, written into the SMEM A buffer)
+//   for hidden chunks j of 128 columns:
+//     H_j  = gelu(Y . W1[:, j] + b1[j])         (MMA1 into TMEM, epilogue back into TMEM)
+//     OUT += H_j . W2[j, :]                      (MMA2, A operand from TMEM; OUT holds x1)
+//   x = OUT + b2, ln_out = LayerNorm(x) (the next block's LN1, or the final LN).
+// Neither x1, its LayerNorm nor the hidden activations leave the SM: the intermediate
+// residual row goes from the projection's accumulator into the output accumulator (as
+// its starting value), so the only HBM traffic is the attention output and the residual
+// row in, the new residual row and its LayerNorm out.
 //
 // CTA pairs (clusters of two SMs) run 2-SM MMAs (cta_group::2) over 256-row tiles: each
-// CTA holds its own 128 rows of Y and of H_j and half of every weight block, the even
+// CTA holds its own 128 rows of A / Y and of H_j and half of every weight block, the even
 // CTA issues the MMAs for both, and each CTA's TMEM receives the accumulator rows of its
 // own 128 rows.  Per SM this halves the weight bytes that stream from L2 for the same
 // tensor work.
 //
-// Y (LN2 output, bf16 [M, D]) is loaded once per tile by TMA and stays in SMEM; W1^T
-// ([hid][D]) and W2^T ([D][hid]) k-blocks stream through a ring of 16 KB stages in the
-// order the MMA warp consumes them (MMA1 of chunk j+1 is issued before MMA2 of chunk j,
-// so the tensor core works while the epilogue warps turn H_j into bf16); the ring takes
-// what shared memory is left (one chunk's weights at D = 256).  TMEM: OUT (D cols) + two
-// H buffers (128 cols each).  The
-// epilogue writes the bf16 H_j over the FP32 columns it has just read (two hidden
-// columns per 32-bit TMEM column, the tcgen05 A-operand layout), so no SMEM holds
-// hidden values.  Barriers that the MMA warp waits on live in the even CTA and count both
-// CTAs' arrivals and TMA bytes; MMA completions are signalled to both CTAs.
+// A is loaded once per tile by TMA into SMEM; after MMA_P the drain warps overwrite it
+// with Y in the 128-byte-swizzled K-major layout of a TMA load, the A operand of every
+// MMA1.  Wp^T, W1^T ([hid][D]) and W2^T ([D][hid]) k-blocks stream through a ring of
+// 16 KB stages in the order the MMA warp consumes them (MMA1 of chunk j+1 is issued
+// before MMA2 of chunk j, so the tensor core works while the epilogue warps turn H_j
+// into bf16); the ring takes what shared memory is left.  TMEM: OUT (D cols) + two H
+// buffers (128 cols each).  The epilogue writes the bf16 H_j over the FP32 columns it
+// has just read (two hidden columns per 32-bit TMEM column, the tcgen05 A-operand
+// layout).  Barriers that the MMA warp waits on live in the even CTA and count both CTAs'
+// arrivals and TMA bytes; MMA completions are signalled to both CTAs.
 //
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer (even CTA only; 2, 3 idle:
 // warpgroup 0 hands its registers to the final warps), 4..11 hidden-chunk epilogue (two
 // per TMEM lane quarter, splitting the chunk's columns), 12..15 final epilogue (one per
-// lane quarter).  The output accumulator must be drained (residual, store, LayerNorm)
-// before the next tile's MMA2 can start, and the tensor core idles meanwhile, so three
-// warps per lane quarter share each drain by columns: the final warp takes the first half
-// of the columns, and each GELU warp a quarter once it has finished the next tile's first
-// hidden chunk.  The three exchange per-row partial statistics (Welford) through shared
-// memory and merge them in one fixed order.  Residual loads run one 32-column block ahead
-// and rows move in whole 64-byte segments (warp_rows.cuh); the new x also goes back into
-// OUT, from where the LayerNorm pass reads it.
+// lane quarter).  The tensor core idles while the accumulator is drained, twice per tile
+// (after MMA_P: residual, LayerNorm2 into SMEM; after the last MMA2: store, LayerNorm),
+// so three warps per lane quarter share both drains by columns: the final warp takes the
+// first half of the columns, each GELU warp a quarter.  The three exchange per-row
+// partial statistics (Welford) through shared memory and merge them in one fixed order.
+// Residual rows are prefetched to L2 a tile ahead, then loaded one 32-column block ahead;
+// rows move in whole 64-byte segments (warp_rows.cuh) and leave by TMA stores.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -66,23 +70,23 @@ constexpr int EPI_COLS = HC / (EPI_WARPS / 4);  // hidden columns of a chunk per
 static_assert(EPI_COLS % 32 == 0 && EPI_COLS <= 64, "GELU warp column split");
 static_assert(EPI_WARPS == 8, "the output drain is shared by the final warp and two GELU warps per lane quarter");
 constexpr int DRAIN_WARPS = EPI_WARPS + OUT_WARPS;
-// Each drain warp stores by TMA from two staging tiles and loads residual rows through a
-// third.
+// Each drain warp has three staging tiles: TMA stores rotate through all three, residual
+// loads go through one of them.
 constexpr int DRAIN_TILES = 3 * DRAIN_WARPS;
 
 template <int D>
 struct MlpCfg {
-  static constexpr int A_BYTES = BM * D * 2;                  // this CTA's Y rows, D/64 atoms of 16 KB
-  static constexpr int KA = D / BK;                           // k-blocks of MMA1
+  static constexpr int A_BYTES = BM * D * 2;                  // this CTA's A (then Y) rows, D/64 atoms of 16 KB
+  static constexpr int KA = D / BK;                           // k-blocks of MMA_P and MMA1
   static constexpr int KH = HC / BK;                          // k-blocks of MMA2 per chunk
   static constexpr int STAGE_BYTES = 16384;
   static constexpr int W1_BOX = (HC / 2) * BK * 2;            // this CTA's half of a W1 k-block (HC/2 rows)
   static constexpr int W1_KB = KA < STAGE_BYTES / W1_BOX ? KA : STAGE_BYTES / W1_BOX;  // k-blocks per stage
   static constexpr int W1_STAGES = KA / W1_KB;                // W1 stages per chunk
-  static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a W2 k-block (D/2 rows)
-  static constexpr int PARAM_FLOATS = 1024 + 3 * D;          // b1 (hid <= 1024), b2, LayerNorm scale/shift
+  static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a Wp or W2 k-block (D/2 rows)
+  static constexpr int PARAM_FLOATS = 1024 + 6 * D;          // b1 (hid <= 1024), b2, bp, two LayerNorms
   // 16 KB weight stages: as many as fit (up to two chunks' worth; four, one chunk, at D = 256)
-  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 3 * D) * 4 +
+  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 6 * D) * 4 +
                                      1024 /*tile alignment*/ + DRAIN_TILES * rows::TILE_BYTES + 3 * BM * 2 * 4;
   static constexpr int RING_FIT = (232448 - FIXED_BYTES) / STAGE_BYTES;
   static constexpr int RING = RING_FIT < 8 ? RING_FIT : 8;
@@ -102,9 +106,12 @@ struct MlpCfg {
 struct MlpArgs {
   float* X;              // residual stream [M, D] f32, updated in place
   bf16* ln_out;          // [M, D]
+  const float* bp;       // [D] projection bias
+  const float* ln2_g;    // [D] LayerNorm2
+  const float* ln2_b;
   const float* b1;       // [hid]
   const float* b2;       // [D]
-  const float* ln_g;
+  const float* ln_g;     // [D] LayerNorm of ln_out
   const float* ln_b;
   int M, hid;
   int* err;
@@ -112,8 +119,9 @@ struct MlpArgs {
 
 
 template <int D>
-__global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constant__ CUtensorMap tmY,
-                                                            const __grid_constant__ CUtensorMap tmW1,
+__global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                 const __grid_constant__ CUtensorMap tmWp,
+                                                                 const __grid_constant__ CUtensorMap tmW1,
                                                             const __grid_constant__ CUtensorMap tmW2,
                                                             const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmLN,
@@ -127,9 +135,11 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   uint64_t* bar = reinterpret_cast<uint64_t*>(sR + RING * Cfg::STAGE_BYTES);
   uint64_t* full = bar;                 // [RING]  even CTA: both CTAs' weight bytes
   uint64_t* empty = full + RING;        // [RING]  both: stage consumed by the pair's MMAs
-  uint64_t* a_full = empty + RING;      //         even CTA: both CTAs' Y bytes
+  uint64_t* a_full = empty + RING;      //         even CTA: both CTAs' A bytes
   uint64_t* a_empty = a_full + 1;       //         both: Y no longer read
-  uint64_t* h_full = a_empty + 1;       // [NB]    both: H_j in TMEM
+  uint64_t* p_full = a_empty + 1;       //         both: projection accumulator in OUT
+  uint64_t* a_ready = p_full + 1;       //         even CTA: both CTAs wrote Y (SMEM) and x1 (OUT)
+  uint64_t* h_full = a_ready + 1;       // [NB]    both: H_j in TMEM
   uint64_t* h_done = h_full + NB;       // [NB]    even CTA: both CTAs turned H_j into bf16 (in TMEM)
   uint64_t* o_full = h_done + NB;       //         both: OUT complete
   uint64_t* o_empty = o_full + 1;       //         even CTA: both CTAs drained OUT
@@ -141,7 +151,10 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   float* s_b2 = s_b1 + 1024;                                                      // [D]
   float* s_lng = s_b2 + D;
   float* s_lnb = s_lng + D;
-  uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_lnb + D) + 1023) &
+  float* s_bp = s_lnb + D;
+  float* s_l2g = s_bp + D;
+  float* s_l2b = s_l2g + D;
+  uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_l2b + D) + 1023) &
                                                ~uintptr_t(1023));  // [DRAIN_WARPS][2 KB]
   float* s_stat = reinterpret_cast<float*>(s_tile + DRAIN_TILES * rows::TILE_BYTES);  // [3][BM][mean, M2]
 
@@ -161,6 +174,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     for (int s = 0; s < RING; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
     tc::mbar_init(a_full, 1);
     tc::mbar_init(a_empty, 1);
+    tc::mbar_init(p_full, 1);
+    tc::mbar_init(a_ready, 2 * DRAIN_WARPS);
     for (int b = 0; b < NB; ++b) {
       tc::mbar_init(&h_full[b], 1);
       tc::mbar_init(&h_done[b], 2 * EPI_WARPS);
@@ -171,7 +186,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
-    tc::prefetch_tmap(&tmY);
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmWp);
     tc::prefetch_tmap(&tmW1);
     tc::prefetch_tmap(&tmW2);
   }
@@ -184,6 +200,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     s_b2[c] = args.b2[c];
     s_lng[c] = args.ln_g[c];
     s_lnb[c] = args.ln_b[c];
+    s_bp[c] = args.bp[c];
+    s_l2g[c] = args.ln2_g[c];
+    s_l2b[c] = args.ln2_b[c];
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -191,24 +210,68 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
   tc::fence_after_sync();
   const uint32_t tmem_base = *tmem_slot;
 
-  // The output drain of pair p's tile (the t-th of this CTA) for this warp's 32 rows
-  // (lane quarter warp & 3) and the nch 32-column blocks from column c_lo: x = x + OUT +
-  // b2, stored and written back into OUT, partial row statistics (Welford) exchanged with
-  // the quarter's two other drain warps (slice `role`), then the LayerNorm of the slice.
-  // Rows move in whole 64-byte segments through the warp's staging tiles: the stores go
-  // out by TMA from the two tiles of `st`, and `tl` serves the residual loads.  With
-  // `ahead`, each residual block is loaded while the previous one is processed (the GELU
-  // warps' slices go without: their registers are fewer).
-  auto drain = [&](auto ahead, int t, int p, int role, int c_lo, int nch, uint8_t* tl, rows::AsyncRows& st) -> bool {
-    const int quarter = warp & 3;
+  // Both drains of pair p's tile (the t-th of this CTA) run in three warps per lane
+  // quarter (warp & 3, 32 rows, the thread owning row row0 + lane), each over its slice of
+  // nch 32-column blocks from column c_lo (slice `role`: 0 final warp, 1 and 2 the GELU
+  // warps).  Rows move in whole 64-byte segments through the warp's three staging tiles:
+  // stores go out by TMA from all three (`st`), and `tl`, one of them, serves the
+  // residual loads once the stores have read it.
+
+  // The slices' Welford partials of each row, merged by all three warps in one fixed
+  // order (phase: the barrier's phase parity); mean and 1 / std of the whole row.
+  auto row_stats = [&](int quarter, int role, uint32_t phase, float run_mean, float run_m2, float& mean,
+                       float& rstd) -> bool {
+    float* sr = s_stat + (size_t)(quarter * 32 + lane) * 2;
+    sr[role * BM * 2] = run_mean;
+    sr[role * BM * 2 + 1] = run_m2;
+    tc::mbar_arrive(&stat_bar[quarter]);
+    if (!tc::mbar_wait(&stat_bar[quarter], phase, abort_flag)) return false;
+    float n = 0.f, m2 = 0.f;
+    mean = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int nk = 32 * (k == 0 ? Cfg::FS : Cfg::GS);
+      if (nk == 0) continue;
+      const float mk = sr[k * BM * 2], qk = sr[k * BM * 2 + 1];
+      const float nn = __fadd_rn(n, (float)nk);
+      const float dl = __fsub_rn(mk, mean);
+      mean = __fadd_rn(mean, __fmul_rn(dl, __fdiv_rn((float)nk, nn)));
+      m2 = __fadd_rn(__fadd_rn(m2, qk), __fmul_rn(__fmul_rn(dl, dl), __fdiv_rn(__fmul_rn(n, (float)nk), nn)));
+      n = nn;
+    }
+    rstd = rsqrtf(__fadd_rn(__fdiv_rn(m2, n), 1e-5f));
+    return true;
+  };
+  // Exact mean and squared deviations of 32 values, merged into the running partial
+  // (Chan's pairwise formula).
+  auto block_stats = [](const float (&f)[32], float& run_n, float& run_mean, float& run_m2) {
+    float cm = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) cm += f[k];
+    cm *= (1.f / 32.f);
+    float cq = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) cq = fmaf(f[k] - cm, f[k] - cm, cq);
+    const float nn = run_n + 32.f;
+    const float dl = cm - run_mean;
+    run_mean += dl * (32.f / nn);
+    run_m2 += cq + dl * dl * (run_n * 32.f / nn);
+    run_n = nn;
+  };
+
+  // After MMA_P: x1 = x + OUT + bp back into OUT (the starting value of MMA2's
+  // accumulation), Y = LayerNorm2(x1) as bf16 into the SMEM A buffer.  With `ahead`, each
+  // residual block is loaded while the previous one is processed (the GELU warps' slices
+  // go without: their registers are fewer).
+  auto mid = [&](auto ahead, int t, int p, int role, int c_lo, int nch, uint8_t* tl) -> bool {
+    const int quarter = warp & 3, r = quarter * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
-    const int row0 = (2 * p + rank) * BM + quarter * 32;  // the thread owns row row0 + lane
+    const int row0 = (2 * p + rank) * BM + quarter * 32;
     const int nvalid = M - row0;
-    float* xb = args.X + (size_t)row0 * D;
-    if (!tc::mbar_wait(o_full, t & 1, abort_flag)) return false;
+    const float* xb = args.X + (size_t)row0 * D;
+    if (!tc::mbar_wait(p_full, t & 1, abort_flag)) return false;
     __syncwarp();
     tc::fence_after_sync();
-    // pass 1: x = x + OUT + b2 (stored and written back into OUT), statistics
     float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
     if (nch > 0) {
       float4 gn[8];  // the next block's residual, loaded one block ahead
@@ -227,71 +290,103 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; k += 4) {
-          const float4 b = *reinterpret_cast<const float4*>(s_b2 + c0 + k);
+          const float4 b = *reinterpret_cast<const float4*>(s_bp + c0 + k);
           f[k] += __uint_as_float(v[k]) + b.x;
           f[k + 1] += __uint_as_float(v[k + 1]) + b.y;
           f[k + 2] += __uint_as_float(v[k + 2]) + b.z;
           f[k + 3] += __uint_as_float(v[k + 3]) + b.w;
         }
-        rows::store32_f32_async(&tmX, st, c0, row0, nvalid, lane, f);
 #pragma unroll
         for (int k = 0; k < 32; ++k) v[k] = __float_as_uint(f[k]);
         tc::tmem_st_32x32b_x32(lane_base + c0, v);
-        float cm = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) cm += f[k];
-        cm *= (1.f / 32.f);
-        float cq = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) cq = fmaf(f[k] - cm, f[k] - cm, cq);
-        const float nn = run_n + 32.f;
-        const float dl = cm - run_mean;
-        run_mean += dl * (32.f / nn);
-        run_m2 += cq + dl * dl * (run_n * 32.f / nn);
-        run_n = nn;
+        block_stats(f, run_n, run_mean, run_m2);
       }
       tc::tmem_st_wait();
     }
-    // the three slices' statistics of each row, merged by all three warps in one order
-    float* sr = s_stat + (size_t)(quarter * 32 + lane) * 2;
-    sr[role * BM * 2] = run_mean;
-    sr[role * BM * 2 + 1] = run_m2;
-    tc::mbar_arrive(&stat_bar[quarter]);
-    if (!tc::mbar_wait(&stat_bar[quarter], t & 1, abort_flag)) return false;
-    float n = 0.f, mean = 0.f, m2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int nk = 32 * (k == 0 ? Cfg::FS : Cfg::GS);
-      if (nk == 0) continue;
-      const float mk = sr[k * BM * 2], qk = sr[k * BM * 2 + 1];
-      const float nn = __fadd_rn(n, (float)nk);
-      const float dl = __fsub_rn(mk, mean);
-      mean = __fadd_rn(mean, __fmul_rn(dl, __fdiv_rn((float)nk, nn)));
-      m2 = __fadd_rn(__fadd_rn(m2, qk), __fmul_rn(__fmul_rn(dl, dl), __fdiv_rn(__fmul_rn(n, (float)nk), nn)));
-      n = nn;
-    }
-    const float rstd = rsqrtf(__fadd_rn(__fdiv_rn(m2, n), 1e-5f));
-    // pass 2: LayerNorm of the slice, from the x held in OUT; then this slice of OUT is free
+    float mean, rstd;
+    if (!row_stats(quarter, role, 0, run_mean, run_m2, mean, rstd)) return false;
 #pragma unroll 1
     for (int c0 = c_lo; c0 < c_lo + 32 * nch; c0 += 32) {
       uint32_t xr[32];
       tc::tmem_ld_32x32b_x32(lane_base + c0, xr);
       tc::tmem_ld_wait();
+      uint32_t pk[16];
+#pragma unroll
+      for (int k = 0; k < 32; k += 4) {
+        const float4 g4 = *reinterpret_cast<const float4*>(s_l2g + c0 + k);
+        const float4 b4 = *reinterpret_cast<const float4*>(s_l2b + c0 + k);
+        __nv_bfloat162 y0 = __floats2bfloat162_rn((__uint_as_float(xr[k]) - mean) * rstd * g4.x + b4.x,
+                                                  (__uint_as_float(xr[k + 1]) - mean) * rstd * g4.y + b4.y);
+        __nv_bfloat162 y1 = __floats2bfloat162_rn((__uint_as_float(xr[k + 2]) - mean) * rstd * g4.z + b4.z,
+                                                  (__uint_as_float(xr[k + 3]) - mean) * rstd * g4.w + b4.w);
+        pk[k / 2] = *reinterpret_cast<uint32_t*>(&y0);
+        pk[k / 2 + 1] = *reinterpret_cast<uint32_t*>(&y1);
+      }
+      // columns c0 .. c0+31 of row r: atom c0/64, 16-byte chunks (c0%64)/8 .. +3, swizzled by r%8
+      uint8_t* rowp = sA + (c0 >> 6) * (BM * BK * 2) + r * 128;
+      const int ch0 = (c0 & 63) >> 3;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        *reinterpret_cast<uint4*>(rowp + (((ch0 + k) ^ (r & 7)) << 4)) =
+            make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+    }
+    tc::fence_proxy_async_smem();  // Y is read by the tensor core (async proxy)
+    tc::fence_before_sync();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive_cluster(lead(a_ready));
+    return true;
+  };
+
+  // After the last MMA2: x = OUT + b2 stored, ln_out = LayerNorm(x) stored; then OUT is free.
+  auto fin = [&](int t, int p, int role, int c_lo, int nch, rows::AsyncRows& st) -> bool {
+    const int quarter = warp & 3;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+    const int row0 = (2 * p + rank) * BM + quarter * 32;
+    const int nvalid = M - row0;
+    if (!tc::mbar_wait(o_full, t & 1, abort_flag)) return false;
+    __syncwarp();
+    tc::fence_after_sync();
+    float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
+#pragma unroll 1
+    for (int c0 = c_lo; c0 < c_lo + 32 * nch; c0 += 32) {
+      uint32_t v[32];
+      tc::tmem_ld_32x32b_x32(lane_base + c0, v);
+      tc::tmem_ld_wait();
+      float f[32];
+#pragma unroll
+      for (int k = 0; k < 32; k += 4) {
+        const float4 b = *reinterpret_cast<const float4*>(s_b2 + c0 + k);
+        f[k] = __uint_as_float(v[k]) + b.x;
+        f[k + 1] = __uint_as_float(v[k + 1]) + b.y;
+        f[k + 2] = __uint_as_float(v[k + 2]) + b.z;
+        f[k + 3] = __uint_as_float(v[k + 3]) + b.w;
+      }
+      rows::store32_f32_async(&tmX, st, c0, row0, nvalid, lane, f);
+      block_stats(f, run_n, run_mean, run_m2);
+    }
+    float mean, rstd;
+    if (!row_stats(quarter, role, 1, run_mean, run_m2, mean, rstd)) return false;
+#pragma unroll 1
+    for (int c0 = c_lo; c0 < c_lo + 32 * nch; c0 += 32) {
+      uint32_t v[32];
+      tc::tmem_ld_32x32b_x32(lane_base + c0, v);
+      tc::tmem_ld_wait();
       float xv[32];
 #pragma unroll
       for (int k = 0; k < 32; k += 4) {
+        const float4 b = *reinterpret_cast<const float4*>(s_b2 + c0 + k);
         const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
         const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
-        xv[k] = (__uint_as_float(xr[k]) - mean) * rstd * g4.x + b4.x;
-        xv[k + 1] = (__uint_as_float(xr[k + 1]) - mean) * rstd * g4.y + b4.y;
-        xv[k + 2] = (__uint_as_float(xr[k + 2]) - mean) * rstd * g4.z + b4.z;
-        xv[k + 3] = (__uint_as_float(xr[k + 3]) - mean) * rstd * g4.w + b4.w;
+        xv[k] = ((__uint_as_float(v[k]) + b.x) - mean) * rstd * g4.x + b4.x;
+        xv[k + 1] = ((__uint_as_float(v[k + 1]) + b.y) - mean) * rstd * g4.y + b4.y;
+        xv[k + 2] = ((__uint_as_float(v[k + 2]) + b.z) - mean) * rstd * g4.z + b4.z;
+        xv[k + 3] = ((__uint_as_float(v[k + 3]) + b.w) - mean) * rstd * g4.w + b4.w;
       }
       rows::store32_bf16_async(&tmLN, st, c0, row0, nvalid, lane, xv);
     }
     tc::fence_before_sync();
     __syncwarp();
-    if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // the next tile's MMA2 may start once all slices are out
+    if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // the next tile's MMA_P may start once all slices are out
     return true;
   };
 
@@ -319,7 +414,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           if (rank == 0) tc::mbar_expect_tx(a_full, ((2 * p + 1) * BM < M ? 2 : 1) * Cfg::A_BYTES);
           if (m0 < M)
             for (int kb = 0; kb < Cfg::KA; ++kb)
-              tc::tma_load_2d_pair(sA + kb * (BM * BK * 2), &tmY, lead(a_full), kb * BK, m0);
+              tc::tma_load_2d_pair(sA + kb * (BM * BK * 2), &tmA, lead(a_full), kb * BK, m0);
+          for (int kb = 0; kb < Cfg::KA && ok; ++kb)  // the projection's k-blocks first
+            ok = push(&tmWp, 1, kb * BK, rank * (D / 2), Cfg::W2_BOX);
           for (int j = 0; j < NJ + LOOK && ok; ++j) {  // the MMA warp's consumption order
             if (j < NJ)
               for (int st = 0; st < Cfg::W1_STAGES && ok; ++st)
@@ -330,7 +427,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           }
         }
         // every signal addressed to this CTA has landed before it may exit: the pair's
-        // releases of the last stages and of the last Y tile
+        // releases of the last stages and of the last A / Y tile
         for (uint32_t h = (g > (uint32_t)RING ? g - RING : 0); h < g; ++h)
           if (!tc::mbar_wait_timed(&empty[h % RING], (h / RING) & 1)) break;
         if (t >= 1) tc::mbar_wait_timed(a_empty, (t - 1) & 1);
@@ -376,9 +473,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
           tc::mma_commit_pair(&h_full[hb], PAIR);
           return true;
         };
-        auto mma2 = [&](uint32_t qq, bool first, bool last, int t) {  // OUT (+)= bf16 H[qq % NB] . W2_chunk^T
+        auto mma2 = [&](uint32_t qq, bool last) {  // OUT += bf16 H[qq % NB] . W2_chunk^T
           const uint32_t hb = qq % NB, use = qq / NB;
-          if (first && t >= 1 && !tc::mbar_wait_cluster(o_empty, (t - 1) & 1, abort_flag)) return false;
           if (!tc::mbar_wait_cluster(&h_done[hb], use & 1, abort_flag)) return false;
           tc::fence_after_sync();
           for (int kb = 0; kb < Cfg::KH; ++kb) {
@@ -390,24 +486,43 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
               // hidden column k lives in GELU warp k / EPI_COLS's columns, two per TMEM column
               const int k = kb * BK + kk * 16;
               const uint32_t at = tmem_base + Cfg::H_COL0 + hb * HC + (k / EPI_COLS) * EPI_COLS + (k % EPI_COLS) / 2;
-              tc::mma_f16_pair_ta(tmem_base, at, bd + 2 * kk, id2, (!first || kb || kk) ? 1u : 0u);
+              tc::mma_f16_pair_ta(tmem_base, at, bd + 2 * kk, id2, 1u);
             }
             tc::mma_commit_pair(&empty[s], PAIR);
           }
           if (last) tc::mma_commit_pair(o_full, PAIR);
           return true;
         };
+        // OUT = A . Wp^T (the drains of the previous tile are done with OUT)
+        auto mma_p = [&](int t) {
+          if (!tc::mbar_wait_cluster(a_full, t & 1, abort_flag)) return false;
+          if (t >= 1 && !tc::mbar_wait_cluster(o_empty, (t - 1) & 1, abort_flag)) return false;
+          tc::fence_after_sync();
+          for (int kb = 0; kb < Cfg::KA; ++kb) {
+            int s;
+            if (!pop(s)) return false;
+            const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sA + kb * (BM * BK * 2)));
+            const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16_pair(tmem_base, ad + 2 * kk, bd + 2 * kk, id2, (kb | kk) != 0);
+            tc::mma_commit_pair(&empty[s], PAIR);
+          }
+          tc::mma_commit_pair(p_full, PAIR);
+          // Y in SMEM and x1 in OUT, from both CTAs
+          if (!tc::mbar_wait_cluster(a_ready, t & 1, abort_flag)) return false;
+          tc::fence_after_sync();
+          return true;
+        };
         int t = 0;
         for (int p = cid; p < pairs && ok; p += ncl, ++t) {
-          if (!tc::mbar_wait_cluster(a_full, t & 1, abort_flag)) { ok = false; break; }
-          tc::fence_after_sync();
+          ok = mma_p(t);
           const uint32_t q0 = q;
           for (int j = 0; j < NJ + LOOK && ok; ++j) {
             if (j < NJ) {
               ok = mma1(q0 + j);
               if (ok && j == NJ - 1) tc::mma_commit_pair(a_empty, PAIR);  // Y no longer read after the last MMA1
             }
-            if (ok && j >= LOOK) ok = mma2(q0 + j - LOOK, j == LOOK, j == NJ + LOOK - 1, t);
+            if (ok && j >= LOOK) ok = mma2(q0 + j - LOOK, j == NJ + LOOK - 1);
           }
           q = q0 + NJ;
         }
@@ -423,7 +538,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     }
   } else if (warp < ROLE_WARPS + EPI_WARPS) {
     // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 in TMEM (the A operand of MMA2);
-    // after a tile's first chunk, this warp's slice of the previous tile's output drain
+    // before and after them, this warp's slices of the tile's two drains
     const int quarter = warp & 3, cg = (warp - ROLE_WARPS) >> 2;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 3 * rows::TILE_BYTES, 0};
@@ -434,6 +549,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
     bool ok = true;
     int t = 0;
     for (int p = cid; p < pairs && ok; p += ncl, ++t) {
+      ok = mid(std::false_type{}, t, p, 1 + cg, d_lo, Cfg::GS, tl);
       for (int j = 0; j < NJ && ok; ++j, ++q) {
         const uint32_t hb = q % NB, use = q / NB;
         if (!tc::mbar_wait(&h_full[hb], use & 1, abort_flag)) { ok = false; break; }
@@ -467,33 +583,35 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_tc_kernel(const __grid_constan
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive_cluster(lead(&h_done[hb]));
-        // the previous tile's output is complete once this tile's first H chunk is (its
-        // MMAs were issued before this chunk's MMA1)
-        if (j == 0 && t >= 1) ok = drain(std::false_type{}, t - 1, p - ncl, 1 + cg, d_lo, Cfg::GS, tl, st);
       }
+      if (ok) ok = fin(t, p, 1 + cg, d_lo, Cfg::GS, st);
     }
-    if (ok && t >= 1) ok = drain(std::false_type{}, t - 1, cid + (t - 1) * ncl, 1 + cg, d_lo, Cfg::GS, tl, st);
     rows::async_drain(lane);
     if (!ok) {
       if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
       *abort_flag = 1;
     }
   } else {
-    // ---- final: the first slice of every tile's output drain (x = x + OUT + b2, LN)
+    // ---- final: the first slice of both drains of every tile
     tc::setmaxnreg_inc<REG_FINAL>();
     const int quarter = warp & 3;
     rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 3 * rows::TILE_BYTES, 0};
     uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;
     bool ok = true;
     int t = 0;
-    for (int p = cid; p < pairs && ok; p += ncl, ++t) {
-      // the tile's residual rows head for L2 while its MMAs run
+    // a tile's residual rows head for L2 while the previous tile's MMAs run
+    auto prefetch = [&](int p) {
       const int row0 = (2 * p + rank) * BM + quarter * 32;
-      if (lane < M - row0)
+      if (p < pairs && lane < M - row0)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(args.X + (size_t)(row0 + lane) * D),
                      "r"(D * 4)
                      : "memory");
-      ok = drain(std::true_type{}, t, p, 0, 0, Cfg::FS, tl, st);
+    };
+    prefetch(cid);
+    for (int p = cid; p < pairs && ok; p += ncl, ++t) {
+      ok = mid(std::true_type{}, t, p, 0, 0, Cfg::FS, tl);
+      prefetch(p + ncl);
+      if (ok) ok = fin(t, p, 0, 0, Cfg::FS, st);
     }
     rows::async_drain(lane);
     if (!ok) {
@@ -562,9 +680,10 @@ int num_sms() {
 }
 
 template <int D>
-cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpArgs& a, cudaStream_t st) {
+cudaError_t launch_d(const bf16* A, const bf16* Wpt, const bf16* W1t, const bf16* W2t, const MlpArgs& a,
+                     cudaStream_t st) {
   using Cfg = MlpCfg<D>;
-  auto kern = mlp_tc_kernel<D>;
+  auto kern = proj_mlp_tc_kernel<D>;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -586,15 +705,16 @@ cudaError_t launch_d(const bf16* Y, const bf16* W1t, const bf16* W2t, const MlpA
     if (e != cudaSuccess) return e;
     max_pairs = n > 0 ? n : 1;
   }
-  CUtensorMap my, m1, m2, mx, mln;
-  if (!map2d(&my, Y, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
+  CUtensorMap ma, mp, m1, m2, mx, mln;
+  if (!map2d(&ma, A, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
+  if (!map2d(&mp, Wpt, D, D, BK, D / 2)) return cudaErrorInvalidValue;
   if (!store_map(&mx, a.X, true, D, (uint64_t)a.M) || !store_map(&mln, a.ln_out, false, D, (uint64_t)a.M))
     return cudaErrorInvalidValue;
   if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC / 2)) return cudaErrorInvalidValue;
   if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;
   const int pairs = ((a.M + BM - 1) / BM + 1) / 2;
   lc.gridDim = dim3((pairs < max_pairs ? pairs : max_pairs) * 2);
-  cudaError_t e = cudaLaunchKernelEx(&lc, kern, my, m1, m2, mx, mln, a);
+  cudaError_t e = cudaLaunchKernelEx(&lc, kern, ma, mp, m1, m2, mx, mln, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -604,17 +724,18 @@ bool mlp_tc_supported(int d, int hid) {
   return (d == 64 || d == 128 || d == 256) && hid % HC == 0 && hid >= HC && hid <= 1024;
 }
 
-cudaError_t launch_mlp_tc(const bf16* Y, const bf16* W1t, const bf16* W2t, const float* b1, const float* b2, float* X,
-                          const float* ln_g, const float* ln_b, bf16* ln_out, int M, int d, int hid, int* err,
-                          cudaStream_t st) {
+cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const float* ln2_g,
+                               const float* ln2_b, const bf16* W1t, const bf16* W2t, const float* b1,
+                               const float* b2, float* X, const float* ln_g, const float* ln_b, bf16* ln_out, int M,
+                               int d, int hid, int* err, cudaStream_t st) {
   if (!mlp_tc_supported(d, hid) || M <= 0) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(W1t) | reinterpret_cast<uintptr_t>(W2t) |
-       reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(ln_out)) & 15)
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Wpt) | reinterpret_cast<uintptr_t>(W1t) |
+       reinterpret_cast<uintptr_t>(W2t) | reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(ln_out)) & 15)
     return cudaErrorInvalidValue;
-  MlpArgs a{X, ln_out, b1, b2, ln_g, ln_b, M, hid, err};
-  if (d == 256) return launch_d<256>(Y, W1t, W2t, a, st);
-  if (d == 128) return launch_d<128>(Y, W1t, W2t, a, st);
-  return launch_d<64>(Y, W1t, W2t, a, st);
+  MlpArgs a{X, ln_out, bp, ln2_g, ln2_b, b1, b2, ln_g, ln_b, M, hid, err};
+  if (d == 256) return launch_d<256>(A, Wpt, W1t, W2t, a, st);
+  if (d == 128) return launch_d<128>(A, Wpt, W1t, W2t, a, st);
+  return launch_d<64>(A, Wpt, W1t, W2t, a, st);
 }
 
 }  // namespace inpaint
