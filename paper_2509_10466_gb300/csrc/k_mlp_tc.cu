@@ -70,8 +70,8 @@ constexpr int EPI_COLS = HC / (EPI_WARPS / 4);  // hidden columns of a chunk per
 static_assert(EPI_COLS % 32 == 0 && EPI_COLS <= 64, "GELU warp column split");
 static_assert(EPI_WARPS == 8, "the output drain is shared by the final warp and two GELU warps per lane quarter");
 constexpr int DRAIN_WARPS = EPI_WARPS + OUT_WARPS;
-// Each drain warp has three staging tiles: TMA stores rotate through all three, residual
-// loads go through one of them.
+// Each drain warp stores by TMA from two staging tiles and loads residual rows through a
+// third.
 constexpr int DRAIN_TILES = 3 * DRAIN_WARPS;
 
 template <int D>
@@ -213,9 +213,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   // Both drains of pair p's tile (the t-th of this CTA) run in three warps per lane
   // quarter (warp & 3, 32 rows, the thread owning row row0 + lane), each over its slice of
   // nch 32-column blocks from column c_lo (slice `role`: 0 final warp, 1 and 2 the GELU
-  // warps).  Rows move in whole 64-byte segments through the warp's three staging tiles:
-  // stores go out by TMA from all three (`st`), and `tl`, one of them, serves the
-  // residual loads once the stores have read it.
+  // warps).  Rows move in whole 64-byte segments through the warp's staging tiles: stores
+  // go out by TMA from the two tiles of `st`, and `tl` serves the residual loads.
 
   // The slices' Welford partials of each row, merged by all three warps in one fixed
   // order (phase: the barrier's phase parity); mean and 1 / std of the whole row.
