@@ -296,6 +296,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
 
   if (RP)
     for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(HPC * blockIdx.y + e / 225) * 225 + e % 225];
+  pdl_trigger();
+  pdl_wait();
   if (tid < SLOTS) {
     const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
     const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
@@ -457,6 +459,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
   const int h0 = HPC * blockIdx.y;
   if (RP)
     for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(h0 + e / 225) * 225 + e % 225];
+  pdl_trigger();
+  pdl_wait();
 
   if (tid < SLOTS) {
     const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
@@ -623,10 +627,10 @@ cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, u
   if (heads % HPC) return cudaErrorInvalidValue;
   dim3 grid(nwy * nwx, heads / HPC, B);
   if (relpos)
-    attn_tc_kernel<true><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, relpos);
-  else
-    attn_tc_kernel<false><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx, nullptr);
-  return cudaGetLastError();
+    return launch_pdl(attn_tc_kernel<true>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
+                      relpos);
+  return launch_pdl(attn_tc_kernel<false>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
+                    (const float*)nullptr);
 }
 
 cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
@@ -638,12 +642,10 @@ cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* 
   static const MemTab none{};
   dim3 grid(nwy * nwx, heads / HPC, B);
   if (relpos)
-    attn_tc_mem_kernel<true><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
-                                                          tab ? *tab : none, tab ? m : 0, off_kv, off_mask, relpos);
-  else
-    attn_tc_mem_kernel<false><<<grid, TC_THREADS, 0, st>>>(qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
-                                                           tab ? *tab : none, tab ? m : 0, off_kv, off_mask, nullptr);
-  return cudaGetLastError();
+    return launch_pdl(attn_tc_mem_kernel<true>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset,
+                      nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, relpos);
+  return launch_pdl(attn_tc_mem_kernel<false>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset,
+                    nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, (const float*)nullptr);
 }
 
 }  // namespace inpaint

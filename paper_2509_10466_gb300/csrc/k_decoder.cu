@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
   extern __shared__ __align__(16) uint8_t hsm[];
   bf16* tile = reinterpret_cast<bf16*>(hsm);  // [HY*HX][C], chunk k of pixel p at 8*(k ^ (p & (NCH-1)))
   const int b = blockIdx.z, y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+  pdl_trigger();
+  pdl_wait();
   // halo tile by cp.async, all copies in flight at once (zero fill outside the image)
   for (int e = threadIdx.x; e < HY * HX * NCH; e += blockDim.x) {
     const int k = e % NCH, pix = e / NCH;
@@ -356,10 +358,9 @@ cudaError_t launch_head_composite(const T* in, int B, int Hp, int Wp, int C, con
     }
     dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
     const bf16* inb = reinterpret_cast<const bf16*>(in);
-    if (C == 16) head_mma_kernel<16><<<grid, 256, smem, st>>>(inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
-    else if (C == 32) head_mma_kernel<32><<<grid, 256, smem, st>>>(inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
-    else head_mma_kernel<64><<<grid, 256, smem, st>>>(inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
-    return cudaGetLastError();
+    if (C == 16) return launch_pdl(head_mma_kernel<16>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
+    if (C == 32) return launch_pdl(head_mma_kernel<32>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
+    return launch_pdl(head_mma_kernel<64>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
   }
   if (sizeof(T) == 2 && C % 8 == 0) {
     const size_t smem = (size_t)18 * 34 * C * 2 + (size_t)27 * C * 4;

@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(THREADS, 1) upconv_tc_kernel(const __grid_cons
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_trigger();
+  pdl_wait();
 
   // tile -> (parity p fastest, then column tile, row tile, frame)
   auto decode = [&](int tile, int& p, int& j0, int& i0, int& img) {
@@ -288,7 +290,9 @@ cudaError_t launch_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const bf
   }
   const int tiles = B * ((Hi + TH - 1) / TH) * ((Wi + TW - 1) / TW) * 4;
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  upconv_tc_kernel<COUT><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(mi, mw, out, B, Hi, Wi, Cin, bias, err);
+  cudaError_t le = launch_pdl(upconv_tc_kernel<COUT>, grid, dim3(THREADS), Cfg::SMEM_BYTES, st, mi, mw, out, B, Hi,
+                              Wi, Cin, bias, err);
+  if (le != cudaSuccess) return le;
   return cudaGetLastError();
 }
 

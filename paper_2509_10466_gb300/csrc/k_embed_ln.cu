@@ -168,6 +168,8 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
     const int n = e >> 3, ch = e & 7;
     *reinterpret_cast<uint4*>(Ws + n * C::KP + ch * 8) = *reinterpret_cast<const uint4*>(we16 + (size_t)n * 64 + ch * 8);
   }
+  pdl_trigger();
+  pdl_wait();
   __syncthreads();
   static_assert(C::TOK * 4 == 256, "one thread per (token, pixel row)");
   {
@@ -426,8 +428,8 @@ cudaError_t launch_embed_tc_d(const float* x, const uint8_t* hole, int B, int H,
     attr = true;
   }
   dim3 grid(cdiv(Ht * Wt, EmbTc<D>::TOK), B);
-  embed_tc_kernel<D><<<grid, 256, EmbTc<D>::SMEM, st>>>(x, hole, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out);
-  return cudaGetLastError();
+  return launch_pdl(embed_tc_kernel<D>, grid, dim3(256), EmbTc<D>::SMEM, st, x, hole, H, W, Ht, Wt, we16, be, tok, v0,
+                    ln_g, ln_b, ln_out);
 }
 
 cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,

@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_trigger();
+  pdl_wait();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -417,7 +419,8 @@ cudaError_t launch_bn(const bf16* A, const bf16* Bt, const GemmArgs& args, cudaS
       ((reinterpret_cast<uintptr_t>(args.ln_out) & 15) ||
        !make_store_map(&ml, args.ln_out, false, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.N)))
     return cudaErrorInvalidValue;
-  gemm_tc_kernel<BN><<<grid, THREADS, Cfg::SMEM_BYTES, st>>>(ma, mb, mc, ml, args);
+  cudaError_t le = launch_pdl(gemm_tc_kernel<BN>, grid, dim3(THREADS), Cfg::SMEM_BYTES, st, ma, mb, mc, ml, args);
+  if (le != cudaSuccess) return le;
   return cudaGetLastError();
 }
 

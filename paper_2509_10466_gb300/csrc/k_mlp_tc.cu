@@ -209,6 +209,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   tc::cluster_sync();  // both CTAs' barriers exist before any remote arrival
   tc::fence_after_sync();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_trigger();
+  pdl_wait();
 
   // Both drains of pair p's tile (the t-th of this CTA) run in three warps per lane
   // quarter (warp & 3, 32 rows, the thread owning row row0 + lane), each over its slice of
@@ -684,16 +686,18 @@ cudaError_t launch_d(const bf16* A, const bf16* Wpt, const bf16* W1t, const bf16
   using Cfg = MlpCfg<D>;
   auto kern = proj_mlp_tc_kernel<D>;
   cudaLaunchConfig_t lc = {};
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = 2;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   lc.blockDim = dim3(THREADS);
   lc.dynamicSmemBytes = Cfg::SMEM_BYTES;
   lc.stream = st;
   lc.attrs = at;
-  lc.numAttrs = 1;
+  lc.numAttrs = 1;  // occupancy query without the stream attribute
   static int max_pairs = 0;  // co-resident CTA pairs at one CTA per SM
   if (!max_pairs) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
@@ -713,6 +717,7 @@ cudaError_t launch_d(const bf16* A, const bf16* Wpt, const bf16* W1t, const bf16
   if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;
   const int pairs = ((a.M + BM - 1) / BM + 1) / 2;
   lc.gridDim = dim3((pairs < max_pairs ? pairs : max_pairs) * 2);
+  lc.numAttrs = 2;
   cudaError_t e = cudaLaunchKernelEx(&lc, kern, ma, mp, m1, m2, mx, mln, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
