@@ -63,18 +63,31 @@ Offsets make_offsets(const inpaint_config& c) {
 }
 
 // out[n*K + k] = bf16(in[k*N + n])  (linear weight [in=K, out=N] -> K-major B operand)
-__global__ void transpose_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, int K, int N) {
+// in [K][N] -> out [N][K] bf16, row k of `in` scaled by kscale[k] if given
+__global__ void transpose_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, int K, int N,
+                                  const float* __restrict__ kscale) {
   __shared__ float t[32][33];
   const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int k = k0 + i, n = n0 + threadIdx.x;
-    t[i][threadIdx.x] = (k < K && n < N) ? in[(size_t)k * N + n] : 0.f;
+    t[i][threadIdx.x] = (k < K && n < N) ? in[(size_t)k * N + n] * (kscale ? kscale[k] : 1.f) : 0.f;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int n = n0 + i, k = k0 + threadIdx.x;
     if (n < N && k < K) out[(size_t)n * K + k] = __float2bfloat16_rn(t[threadIdx.x][i]);
   }
+}
+
+// A LayerNorm's shift beta [K] folded into the bias of the linear layer W [K][N] that
+// follows it: out[n] = b[n] + sum_k beta[k] W[k][n] (its scale goes into W itself).
+__global__ void fold_bias_kernel(const float* __restrict__ W, const float* __restrict__ beta,
+                                 const float* __restrict__ b, float* __restrict__ out, int K, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double acc = b[n];
+  for (int k = 0; k < K; ++k) acc += (double)beta[k] * W[(size_t)k * N + n];
+  out[n] = (float)acc;
 }
 
 // conv weight [Cout][Cin][9] -> [9][Cin][Cout]
@@ -157,7 +170,8 @@ int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
   conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d2w, c->dec2_wt, c->c2, c->c1);
   if (c->embed_w16) {
     // embed.w [d][64] as bf16 = the transpose of the [64][d] copy made above
-    transpose_to_bf16<<<dim3(cdiv(c->d, 32), cdiv(64, 32)), dim3(32, 8), 0, st>>>(c->embed_wt, c->embed_w16, 64, c->d);
+    transpose_to_bf16<<<dim3(cdiv(c->d, 32), cdiv(64, 32)), dim3(32, 8), 0, st>>>(c->embed_wt, c->embed_w16, 64, c->d,
+                                                                                   nullptr);
   }
   if (c->use_bf16 && c->dec1_wp && launch_subpixel_weights(c->w32 + o.d1w, c->c1, c->d, c->dec1_wp, st) != cudaSuccess)
     return INPAINT_E_CUDA;
@@ -167,14 +181,24 @@ int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
     const int d = c->d, h = c->hid;
     for (int l = 0; l < c->L; ++l) {
       bf16* base = c->lin_bf16 + (size_t)l * c->lin_block_elems;
-      struct { size_t src; int K, N; size_t dst; } mats[4] = {
-          {o.blk[l].qkvw, d, 3 * d, 0},
-          {o.blk[l].projw, d, d, (size_t)3 * d * d},
-          {o.blk[l].fc1w, d, h, (size_t)4 * d * d},
-          {o.blk[l].fc2w, h, d, (size_t)4 * d * d + (size_t)h * d}};
+      const BlockOff& b = o.blk[l];
+      const float* g1 = c->fold_ln ? c->w32 + b.ln1g : nullptr;
+      const float* g2 = c->fold_ln ? c->w32 + b.ln2g : nullptr;
+      struct { size_t src; int K, N; size_t dst; const float* kscale; } mats[4] = {
+          {b.qkvw, d, 3 * d, 0, g1},
+          {b.projw, d, d, (size_t)3 * d * d, nullptr},
+          {b.fc1w, d, h, (size_t)4 * d * d, g2},
+          {b.fc2w, h, d, (size_t)4 * d * d + (size_t)h * d, nullptr}};
       for (auto& m : mats) {
         dim3 grid(cdiv(m.N, 32), cdiv(m.K, 32));
-        transpose_to_bf16<<<grid, dim3(32, 8), 0, st>>>(c->w32 + m.src, base + m.dst, m.K, m.N);
+        transpose_to_bf16<<<grid, dim3(32, 8), 0, st>>>(c->w32 + m.src, base + m.dst, m.K, m.N, m.kscale);
+      }
+      if (c->fold_ln) {
+        float* fb = c->fold_b + (size_t)l * (3 * d + h);
+        fold_bias_kernel<<<cdiv(3 * d, 128), 128, 0, st>>>(c->w32 + b.qkvw, c->w32 + b.ln1b, c->w32 + b.qkvb, fb, d,
+                                                           3 * d);
+        fold_bias_kernel<<<cdiv(h, 128), 128, 0, st>>>(c->w32 + b.fc1w, c->w32 + b.ln2b, c->w32 + b.fc1b, fb + 3 * d,
+                                                       d, h);
       }
     }
   }
@@ -195,8 +219,9 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
   {
     LaunchScope ls(c, st, K_EMBED);
     if (c->use_bf16) {
-      const float* g0 = c->w32 + (c->L ? o.blk[0].ln1g : o.lnfg);
-      const float* b0 = c->w32 + (c->L ? o.blk[0].ln1b : o.lnfb);
+      // with folding, block 0's LN1 affine lives in its QKV weights: normalized rows only
+      const float* g0 = c->fold_ln ? nullptr : c->w32 + (c->L ? o.blk[0].ln1g : o.lnfg);
+      const float* b0 = c->fold_ln ? nullptr : c->w32 + (c->L ? o.blk[0].ln1b : o.lnfb);
       if (c->embed_w16)
         TRY(cuda_err(launch_embed_tc(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_w16, c->w32 + o.embb, d, tok, masks,
                                      g0, b0, reinterpret_cast<bf16*>(ws + p.ln), st)));
@@ -251,7 +276,8 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       const bf16* wfc1 = wl + (size_t)4 * d * d;
       const bf16* wfc2 = wfc1 + (size_t)c->hid * d;
       if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
-      { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, c->w32 + b.qkvb, nullptr, err, st))); }
+      const float* fold = c->fold_ln ? c->fold_b + (size_t)l * (3 * d + c->hid) : nullptr;
+      { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, fold ? fold : c->w32 + b.qkvb, nullptr, err, st))); }
       if (temporal) {
         LaunchScope ls(c, st, K_ATTN);
         TRY(cuda_err(launch_attention_tc_mem(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st, rp)));
@@ -260,15 +286,16 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
         TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp)));
       }
       if (temporal) TRY(record_memory(qkv));
-      if (fuse_ln && mlp_tc_supported(d, c->hid)) {
+      if (c->fold_ln) {
         // projection, residual, LN2 and the whole MLP in one kernel: only the attention
         // output and the residual row come in, only the new residual row and its LN leave
+        // (normalized only: the next block's LN1 affine is folded too; the final LN keeps it)
         const bool last = l + 1 == c->L;
-        const float* ng = c->w32 + (last ? o.lnfg : o.blk[l + 1].ln1g);
-        const float* nb = c->w32 + (last ? o.lnfb : o.blk[l + 1].ln1b);
+        const float* ng = last ? c->w32 + o.lnfg : nullptr;
+        const float* nb = last ? c->w32 + o.lnfb : nullptr;
         LaunchScope ls(c, st, K_MLP);
-        TRY(cuda_err(launch_proj_mlp_tc(ao, wproj, c->w32 + b.projb, c->w32 + b.ln2g, c->w32 + b.ln2b, wfc1, wfc2,
-                                        c->w32 + b.fc1b, c->w32 + b.fc2b, tok, ng, nb, ln, M, d, c->hid, err, st)));
+        TRY(cuda_err(launch_proj_mlp_tc(ao, wproj, c->w32 + b.projb, wfc1, wfc2, fold + 3 * d, c->w32 + b.fc2b, tok,
+                                        ng, nb, ln, M, d, c->hid, err, st)));
         ln_ready = true;
         continue;
       }
@@ -386,6 +413,7 @@ void inpaint_destroy(inpaint_ctx* c) {
   cudaFree(c->dec1_wt);
   cudaFree(c->dec2_wt);
   cudaFree(c->lin_bf16);
+  cudaFree(c->fold_b);
   cudaFree(c->dec1_wp);
   cudaFree(c->embed_w16);
   cudaFree(c->dec2_wp);
@@ -425,8 +453,11 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
   }
   const size_t d = c->d, h = c->hid;
   c->lin_block_elems = 4 * d * d + 2 * h * d;
+  c->fold_ln = c->use_bf16 && c->L > 0 && gemm_tc_ln_supported(c->d) && mlp_tc_supported(c->d, c->hid) &&
+               embed_tc_supported(c->d);
   c->weight_bytes = c->nparams * 4 + 64 * d * 4 + 9 * d * c->c1 * 4 + 9 * (size_t)c->c1 * c->c2 * 4 +
                     (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 + (size_t)32 * (c->c1 * d + c->c2 * c->c1) + 128 * d : 0) +
+                    (c->fold_ln ? (size_t)c->L * (3 * d + h) * 4 : 0) +
                     256;
   if (cfg->hbm_budget_bytes && c->weight_bytes > cfg->hbm_budget_bytes) {
     delete c;
@@ -438,6 +469,7 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
             cudaMalloc(&c->dec2_wt, 9 * (size_t)c->c1 * c->c2 * 4) == cudaSuccess &&
             cudaMalloc(&c->dev_err, 256) == cudaSuccess &&
             (!c->use_bf16 || cudaMalloc(&c->lin_bf16, (size_t)c->L * c->lin_block_elems * 2) == cudaSuccess) &&
+            (!c->fold_ln || cudaMalloc(&c->fold_b, (size_t)c->L * (3 * d + h) * 4) == cudaSuccess) &&
             (!c->use_bf16 || !embed_tc_supported(c->d) || cudaMalloc(&c->embed_w16, 64 * d * 2) == cudaSuccess) &&
             (!c->use_bf16 || !upconv_tc_supported(c->d, c->c1) ||
              cudaMalloc(&c->dec1_wp, (size_t)16 * c->c1 * c->d * 2) == cudaSuccess) &&

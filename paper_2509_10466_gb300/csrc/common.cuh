@@ -108,7 +108,8 @@ cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int 
                          const float* ln_g = nullptr, const float* ln_b = nullptr, bf16* ln_out = nullptr);
 
 // Tensor-core form of the patch embedding (BF16 form): bf16 patches and weights
-// (we16 = embed.w as bf16 [d][64]), FP32 accumulation; writes tok, v0 and LN(tok).
+// (we16 = embed.w as bf16 [d][64]), FP32 accumulation; writes tok, v0 and LN(tok)
+// (without the affine part when ln_g is null: it is then folded into the next GEMM).
 bool embed_tc_supported(int d);
 cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,
                             const float* be, int d, float* tok, uint8_t* v0, const float* ln_g, const float* ln_b,
@@ -136,15 +137,16 @@ bool gemm_tc_ln_supported(int N);
 cudaError_t launch_gemm_tc_resid_ln(const bf16* A, const bf16* Bt, float* X, int M, int N, int K, const float* bias,
                                     const float* ln_g, const float* ln_b, bf16* ln_out, int* err, cudaStream_t st);
 
-// Fused attention projection + MLP on tcgen05: x1 = X + A Wp + bp, Y = LN2(x1),
-// X = x1 + gelu(Y W1 + b1) W2 + b2 and ln_out = LN(X), without writing x1, Y or the hidden
-// activations; Wpt [d][d], W1t [hid][d] and W2t [d][hid] bf16 (K-major), A [M][d] bf16.
-// Supported for d in {64, 128, 256} and hid a multiple of 128 up to 1024.
+// Fused attention projection + MLP on tcgen05: x1 = X + A Wp + bp, Y = normalized x1
+// (LN2 without its affine part, which is folded into W1t / b1), X = x1 + gelu(Y W1 + b1)
+// W2 + b2 and ln_out = normalized X (times ln_g plus ln_b when they are given), without
+// writing x1, Y or the hidden activations; Wpt [d][d], W1t [hid][d] and W2t [d][hid] bf16
+// (K-major), A [M][d] bf16.  Supported for d in {64, 128, 256} and hid a multiple of 128
+// up to 1024.
 bool mlp_tc_supported(int d, int hid);
-cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const float* ln2_g,
-                               const float* ln2_b, const bf16* W1t, const bf16* W2t, const float* b1,
-                               const float* b2, float* X, const float* ln_g, const float* ln_b, bf16* ln_out, int M,
-                               int d, int hid, int* err, cudaStream_t st);
+cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const bf16* W1t, const bf16* W2t,
+                               const float* b1, const float* b2, float* X, const float* ln_g, const float* ln_b,
+                               bf16* ln_out, int M, int d, int hid, int* err, cudaStream_t st);
 
 // Mask-aware window attention of all frames; qkv [B*Nt, 3d] (T), v_in/v_out u8 [B*Nt].
 // relpos (optional, device f32 [heads][15][15]): relative-position bias added to the

@@ -63,6 +63,11 @@ struct inpaint_ctx {
   float* dec1_wt = nullptr;    // [9][d][c1]
   float* dec2_wt = nullptr;    // [9][c1][c2]
   inpaint::bf16* lin_bf16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
+  // BF16 form with the fused projection + MLP: the affine part of LN1 and LN2 is folded
+  // into the QKV and fc1 weights (lin_bf16) and biases (fold_b, per block qkv [3d] then
+  // fc1 [rd]); the LayerNorm producers then write the normalized rows only
+  bool fold_ln = false;
+  float* fold_b = nullptr;
   size_t lin_block_elems = 0;
   inpaint::bf16* embed_w16 = nullptr;  // BF16 form: embed.w as bf16 [d][64]
   inpaint::bf16* dec1_wp = nullptr;  // BF16 form: merged sub-pixel weights [4][c1][4d]

@@ -270,8 +270,12 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
     bf16* lrow = ln_out + ((size_t)b * Nt + t) * D;
     for (int c = 2 * lane; c < D; c += 64) {
       const float2 v = *reinterpret_cast<const float2*>(orow + c);
-      *reinterpret_cast<__nv_bfloat162*>(lrow + c) = __floats2bfloat162_rn((v.x - mean) * rstd * ln_g[c] + ln_b[c],
-                                                                          (v.y - mean) * rstd * ln_g[c + 1] + ln_b[c + 1]);
+      float y0 = (v.x - mean) * rstd, y1 = (v.y - mean) * rstd;
+      if (ln_g) {  // else the affine part is folded into the next GEMM
+        y0 = y0 * ln_g[c] + ln_b[c];
+        y1 = y1 * ln_g[c + 1] + ln_b[c + 1];
+      }
+      *reinterpret_cast<__nv_bfloat162*>(lrow + c) = __floats2bfloat162_rn(y0, y1);
     }
   }
 }

@@ -1,11 +1,13 @@
 // Fused attention projection + MLP of a transformer block on tcgen05 (BF16 form), for
 // a tile of token rows:
 //   x1   = x + A . Wp + bp                      (MMA_P into TMEM; A = attention output)
-//   Y    = LayerNorm2(x1)                        (bf16, written into the SMEM A buffer)
+//   Y    = normalized x1                         (bf16, written into the SMEM A buffer;
+//                                                 LayerNorm2's affine part is folded into W1)
 //   for hidden chunks j of 128 columns:
 //     H_j  = gelu(Y . W1[:, j] + b1[j])         (MMA1 into TMEM, epilogue back into TMEM)
 //     OUT += H_j . W2[j, :]                      (MMA2, A operand from TMEM; OUT holds x1)
-//   x = OUT + b2, ln_out = LayerNorm(x) (the next block's LN1, or the final LN).
+//   x = OUT + b2, ln_out = normalized x: the next block's LN1 without its affine part
+//   (folded into that block's QKV weights), or the final LN with it.
 // Neither x1, its LayerNorm nor the hidden activations leave the SM: the intermediate
 // residual row goes from the projection's accumulator into the output accumulator (as
 // its starting value), so the only HBM traffic is the attention output and the residual
@@ -84,9 +86,9 @@ struct MlpCfg {
   static constexpr int W1_KB = KA < STAGE_BYTES / W1_BOX ? KA : STAGE_BYTES / W1_BOX;  // k-blocks per stage
   static constexpr int W1_STAGES = KA / W1_KB;                // W1 stages per chunk
   static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a Wp or W2 k-block (D/2 rows)
-  static constexpr int PARAM_FLOATS = 1024 + 6 * D;          // b1 (hid <= 1024), b2, bp, two LayerNorms
+  static constexpr int PARAM_FLOATS = 1024 + 4 * D;          // b1 (hid <= 1024), b2, bp, final LayerNorm
   // 16 KB weight stages: as many as fit (up to two chunks' worth; four, one chunk, at D = 256)
-  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 6 * D) * 4 +
+  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 4 * D) * 4 +
                                      1024 /*tile alignment*/ + DRAIN_TILES * rows::TILE_BYTES + 3 * BM * 2 * 4;
   static constexpr int RING_FIT = (232448 - FIXED_BYTES) / STAGE_BYTES;
   static constexpr int RING = RING_FIT < 8 ? RING_FIT : 8;
@@ -107,11 +109,9 @@ struct MlpArgs {
   float* X;              // residual stream [M, D] f32, updated in place
   bf16* ln_out;          // [M, D]
   const float* bp;       // [D] projection bias
-  const float* ln2_g;    // [D] LayerNorm2
-  const float* ln2_b;
   const float* b1;       // [hid]
   const float* b2;       // [D]
-  const float* ln_g;     // [D] LayerNorm of ln_out
+  const float* ln_g;     // [D] affine part of the LayerNorm of ln_out, or null
   const float* ln_b;
   int M, hid;
   int* err;
@@ -152,9 +152,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   float* s_lng = s_b2 + D;
   float* s_lnb = s_lng + D;
   float* s_bp = s_lnb + D;
-  float* s_l2g = s_bp + D;
-  float* s_l2b = s_l2g + D;
-  uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_l2b + D) + 1023) &
+  uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_bp + D) + 1023) &
                                                ~uintptr_t(1023));  // [DRAIN_WARPS][2 KB]
   float* s_stat = reinterpret_cast<float*>(s_tile + DRAIN_TILES * rows::TILE_BYTES);  // [3][BM][mean, M2]
 
@@ -198,11 +196,9 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   for (int c = threadIdx.x; c < args.hid; c += blockDim.x) s_b1[c] = args.b1[c];
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
     s_b2[c] = args.b2[c];
-    s_lng[c] = args.ln_g[c];
-    s_lnb[c] = args.ln_b[c];
+    s_lng[c] = args.ln_g ? args.ln_g[c] : 1.f;
+    s_lnb[c] = args.ln_b ? args.ln_b[c] : 0.f;
     s_bp[c] = args.bp[c];
-    s_l2g[c] = args.ln2_g[c];
-    s_l2b[c] = args.ln2_b[c];
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -261,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   };
 
   // After MMA_P: x1 = x + OUT + bp back into OUT (the starting value of MMA2's
-  // accumulation), Y = LayerNorm2(x1) as bf16 into the SMEM A buffer.  With `ahead`, each
+  // accumulation), Y = (x1 - mean) / std as bf16 into the SMEM A buffer.  With `ahead`, each
   // residual block is loaded while the previous one is processed (the GELU warps' slices
   // go without: their registers are fewer).
   auto mid = [&](auto ahead, int t, int p, int role, int c_lo, int nch, uint8_t* tl) -> bool {
@@ -313,15 +309,10 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
       tc::tmem_ld_wait();
       uint32_t pk[16];
 #pragma unroll
-      for (int k = 0; k < 32; k += 4) {
-        const float4 g4 = *reinterpret_cast<const float4*>(s_l2g + c0 + k);
-        const float4 b4 = *reinterpret_cast<const float4*>(s_l2b + c0 + k);
-        __nv_bfloat162 y0 = __floats2bfloat162_rn((__uint_as_float(xr[k]) - mean) * rstd * g4.x + b4.x,
-                                                  (__uint_as_float(xr[k + 1]) - mean) * rstd * g4.y + b4.y);
-        __nv_bfloat162 y1 = __floats2bfloat162_rn((__uint_as_float(xr[k + 2]) - mean) * rstd * g4.z + b4.z,
-                                                  (__uint_as_float(xr[k + 3]) - mean) * rstd * g4.w + b4.w);
-        pk[k / 2] = *reinterpret_cast<uint32_t*>(&y0);
-        pk[k / 2 + 1] = *reinterpret_cast<uint32_t*>(&y1);
+      for (int k = 0; k < 32; k += 2) {
+        __nv_bfloat162 y = __floats2bfloat162_rn((__uint_as_float(xr[k]) - mean) * rstd,
+                                                 (__uint_as_float(xr[k + 1]) - mean) * rstd);
+        pk[k / 2] = *reinterpret_cast<uint32_t*>(&y);
       }
       // columns c0 .. c0+31 of row r: atom c0/64, 16-byte chunks (c0%64)/8 .. +3, swizzled by r%8
       uint8_t* rowp = sA + (c0 >> 6) * (BM * BK * 2) + r * 128;
@@ -338,7 +329,9 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     return true;
   };
 
-  // After the last MMA2: x = OUT + b2 stored, ln_out = LayerNorm(x) stored; then OUT is free.
+  // After the last MMA2: x = OUT + b2 stored and written back into OUT, ln_out =
+  // (x - mean) / std (times ln_g plus ln_b for the final LayerNorm) stored; then OUT is free.
+  const bool affine = args.ln_g != nullptr;
   auto fin = [&](int t, int p, int role, int c_lo, int nch, rows::AsyncRows& st) -> bool {
     const int quarter = warp & 3;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
@@ -363,8 +356,12 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         f[k + 3] = __uint_as_float(v[k + 3]) + b.w;
       }
       rows::store32_f32_async(&tmX, st, c0, row0, nvalid, lane, f);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = __float_as_uint(f[k]);
+      tc::tmem_st_32x32b_x32(lane_base + c0, v);
       block_stats(f, run_n, run_mean, run_m2);
     }
+    tc::tmem_st_wait();
     float mean, rstd;
     if (!row_stats(quarter, role, 1, run_mean, run_m2, mean, rstd)) return false;
 #pragma unroll 1
@@ -374,14 +371,17 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
       tc::tmem_ld_wait();
       float xv[32];
 #pragma unroll
-      for (int k = 0; k < 32; k += 4) {
-        const float4 b = *reinterpret_cast<const float4*>(s_b2 + c0 + k);
-        const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
-        const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
-        xv[k] = ((__uint_as_float(v[k]) + b.x) - mean) * rstd * g4.x + b4.x;
-        xv[k + 1] = ((__uint_as_float(v[k + 1]) + b.y) - mean) * rstd * g4.y + b4.y;
-        xv[k + 2] = ((__uint_as_float(v[k + 2]) + b.z) - mean) * rstd * g4.z + b4.z;
-        xv[k + 3] = ((__uint_as_float(v[k + 3]) + b.w) - mean) * rstd * g4.w + b4.w;
+      for (int k = 0; k < 32; ++k) xv[k] = (__uint_as_float(v[k]) - mean) * rstd;
+      if (affine) {
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) {
+          const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
+          const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
+          xv[k] = xv[k] * g4.x + b4.x;
+          xv[k + 1] = xv[k + 1] * g4.y + b4.y;
+          xv[k + 2] = xv[k + 2] * g4.z + b4.z;
+          xv[k + 3] = xv[k + 3] * g4.w + b4.w;
+        }
       }
       rows::store32_bf16_async(&tmLN, st, c0, row0, nvalid, lane, xv);
     }
@@ -728,15 +728,15 @@ bool mlp_tc_supported(int d, int hid) {
   return (d == 64 || d == 128 || d == 256) && hid % HC == 0 && hid >= HC && hid <= 1024;
 }
 
-cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const float* ln2_g,
-                               const float* ln2_b, const bf16* W1t, const bf16* W2t, const float* b1,
-                               const float* b2, float* X, const float* ln_g, const float* ln_b, bf16* ln_out, int M,
-                               int d, int hid, int* err, cudaStream_t st) {
+cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const bf16* W1t, const bf16* W2t,
+                               const float* b1, const float* b2, float* X, const float* ln_g, const float* ln_b,
+                               bf16* ln_out, int M, int d, int hid, int* err, cudaStream_t st) {
   if (!mlp_tc_supported(d, hid) || M <= 0) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Wpt) | reinterpret_cast<uintptr_t>(W1t) |
        reinterpret_cast<uintptr_t>(W2t) | reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(ln_out)) & 15)
     return cudaErrorInvalidValue;
-  MlpArgs a{X, ln_out, bp, ln2_g, ln2_b, b1, b2, ln_g, ln_b, M, hid, err};
+  if ((ln_g == nullptr) != (ln_b == nullptr)) return cudaErrorInvalidValue;
+  MlpArgs a{X, ln_out, bp, b1, b2, ln_g, ln_b, M, hid, err};
   if (d == 256) return launch_d<256>(A, Wpt, W1t, W2t, a, st);
   if (d == 128) return launch_d<128>(A, Wpt, W1t, W2t, a, st);
   return launch_d<64>(A, Wpt, W1t, W2t, a, st);
