@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
         const size_t q = (size_t)y * W + xx0;
         const float* xb = x + (size_t)b * 3 * HW + q;
         const uint8_t* hb = hole + (size_t)b * HW + q;
-        if ((W & 3) == 0 && xx0 + 3 < W) {  // 16-byte aligned: vector loads
+        if ((W & 3) == 0 && xx0 + 3 < W && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(hole)) & 15) == 0) {
+          // 16-byte aligned: vector loads
           const float4 r4 = *reinterpret_cast<const float4*>(xb);
           const float4 g4 = *reinterpret_cast<const float4*>(xb + HW);
           const float4 b4 = *reinterpret_cast<const float4*>(xb + 2 * HW);

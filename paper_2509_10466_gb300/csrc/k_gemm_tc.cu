@@ -66,13 +66,10 @@ struct GemmArgs {
   int* err;
 };
 
+// scalar loads: parameter vectors sit at any offset of the weight blob
 __device__ __forceinline__ void load32(const float* __restrict__ p, float (&v)[32]) {
-  const float4* p4 = reinterpret_cast<const float4*>(p);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float4 t = __ldg(p4 + i);
-    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
-  }
+  for (int i = 0; i < 32; ++i) v[i] = __ldg(p + i);
 }
 
 __device__ __forceinline__ void named_sync(int id, int count) {

@@ -72,9 +72,9 @@ constexpr int EPI_COLS = HC / (EPI_WARPS / 4);  // hidden columns of a chunk per
 static_assert(EPI_COLS % 32 == 0 && EPI_COLS <= 64, "GELU warp column split");
 static_assert(EPI_WARPS == 8, "the output drain is shared by the final warp and two GELU warps per lane quarter");
 constexpr int DRAIN_WARPS = EPI_WARPS + OUT_WARPS;
-// Each drain warp stores by TMA from two staging tiles and loads residual rows through a
-// third.
-constexpr int DRAIN_TILES = 3 * DRAIN_WARPS;
+// Each drain warp stores by TMA from two staging tiles; residual rows are loaded through
+// the first of them once the previous stores have read it.
+constexpr int DRAIN_TILES = 2 * DRAIN_WARPS;
 
 template <int D>
 struct MlpCfg {
@@ -86,9 +86,9 @@ struct MlpCfg {
   static constexpr int W1_KB = KA < STAGE_BYTES / W1_BOX ? KA : STAGE_BYTES / W1_BOX;  // k-blocks per stage
   static constexpr int W1_STAGES = KA / W1_KB;                // W1 stages per chunk
   static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a Wp or W2 k-block (D/2 rows)
-  static constexpr int PARAM_FLOATS = 1024 + 4 * D;          // b1 (hid <= 1024), b2, bp, final LayerNorm
+  static constexpr int PARAM_FLOATS = 1024 + 2 * D;          // b1 (hid <= 1024), b2, bp
   // 16 KB weight stages: as many as fit (up to two chunks' worth; four, one chunk, at D = 256)
-  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 4 * D) * 4 +
+  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 2 * D) * 4 +
                                      1024 /*tile alignment*/ + DRAIN_TILES * rows::TILE_BYTES + 3 * BM * 2 * 4;
   static constexpr int RING_FIT = (232448 - FIXED_BYTES) / STAGE_BYTES;
   static constexpr int RING = RING_FIT < 8 ? RING_FIT : 8;
@@ -149,9 +149,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_b1 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [hid]
   float* s_b2 = s_b1 + 1024;                                                      // [D]
-  float* s_lng = s_b2 + D;
-  float* s_lnb = s_lng + D;
-  float* s_bp = s_lnb + D;
+  float* s_bp = s_b2 + D;
   uint8_t* s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_bp + D) + 1023) &
                                                ~uintptr_t(1023));  // [DRAIN_WARPS][2 KB]
   float* s_stat = reinterpret_cast<float*>(s_tile + DRAIN_TILES * rows::TILE_BYTES);  // [3][BM][mean, M2]
@@ -196,8 +194,6 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   for (int c = threadIdx.x; c < args.hid; c += blockDim.x) s_b1[c] = args.b1[c];
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
     s_b2[c] = args.b2[c];
-    s_lng[c] = args.ln_g ? args.ln_g[c] : 1.f;
-    s_lnb[c] = args.ln_b ? args.ln_b[c] : 0.f;
     s_bp[c] = args.bp[c];
   }
   tc::fence_before_sync();
@@ -211,8 +207,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   // Both drains of pair p's tile (the t-th of this CTA) run in three warps per lane
   // quarter (warp & 3, 32 rows, the thread owning row row0 + lane), each over its slice of
   // nch 32-column blocks from column c_lo (slice `role`: 0 final warp, 1 and 2 the GELU
-  // warps).  Rows move in whole 64-byte segments through the warp's staging tiles: stores
-  // go out by TMA from the two tiles of `st`, and `tl` serves the residual loads.
+  // warps).  Rows move in whole 64-byte segments through the warp's two staging tiles:
+  // stores go out by TMA from both (`st`), and `tl`, the first, serves the residual loads.
 
   // The slices' Welford partials of each row, merged by all three warps in one fixed
   // order (phase: the barrier's phase parity); mean and 1 / std of the whole row.
@@ -266,6 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     const int row0 = (2 * p + rank) * BM + quarter * 32;
     const int nvalid = M - row0;
     const float* xb = args.X + (size_t)row0 * D;
+    if (lane == 0) tc::bulk_wait_read<0>();  // the previous tile's stores are done with `tl`
     if (!tc::mbar_wait(p_full, t & 1, abort_flag)) return false;
     __syncwarp();
     tc::fence_after_sync();
@@ -372,16 +369,9 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
       float xv[32];
 #pragma unroll
       for (int k = 0; k < 32; ++k) xv[k] = (__uint_as_float(v[k]) - mean) * rstd;
-      if (affine) {
+      if (affine) {  // scalar loads: the parameters' offset in the weight blob has no alignment
 #pragma unroll
-        for (int k = 0; k < 32; k += 4) {
-          const float4 g4 = *reinterpret_cast<const float4*>(s_lng + c0 + k);
-          const float4 b4 = *reinterpret_cast<const float4*>(s_lnb + c0 + k);
-          xv[k] = xv[k] * g4.x + b4.x;
-          xv[k + 1] = xv[k + 1] * g4.y + b4.y;
-          xv[k + 2] = xv[k + 2] * g4.z + b4.z;
-          xv[k + 3] = xv[k + 3] * g4.w + b4.w;
-        }
+        for (int k = 0; k < 32; ++k) xv[k] = xv[k] * __ldg(args.ln_g + c0 + k) + __ldg(args.ln_b + c0 + k);
       }
       rows::store32_bf16_async(&tmLN, st, c0, row0, nvalid, lane, xv);
     }
@@ -542,8 +532,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     // before and after them, this warp's slices of the tile's two drains
     const int quarter = warp & 3, cg = (warp - ROLE_WARPS) >> 2;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
-    rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 3 * rows::TILE_BYTES, 0};
-    uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;
+    rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 2 * rows::TILE_BYTES, 0};
+    uint8_t* tl = st.tiles;
     const int d_lo = 32 * (Cfg::FS + cg * Cfg::GS);
     constexpr int NL = EPI_COLS / 32;   // 32-column TMEM loads per chunk, issued before one wait
     uint32_t q = 0;
@@ -596,8 +586,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     // ---- final: the first slice of both drains of every tile
     tc::setmaxnreg_inc<REG_FINAL>();
     const int quarter = warp & 3;
-    rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 3 * rows::TILE_BYTES, 0};
-    uint8_t* tl = st.tiles + 2 * rows::TILE_BYTES;
+    rows::AsyncRows st{s_tile + (size_t)(warp - ROLE_WARPS) * 2 * rows::TILE_BYTES, 0};
+    uint8_t* tl = st.tiles;
     bool ok = true;
     int t = 0;
     // a tile's residual rows head for L2 while the previous tile's MMAs run
