@@ -231,7 +231,7 @@ template cudaError_t launch_attention_mem<bf16>(const bf16*, const uint8_t*, bf1
 // slots 16(w % 4) .. +15.  The slot -> token map and the usable-key bitmask of the window
 // are computed once per CTA.
 // Q, K, V of the window (64 x 32 bf16 each) are staged in shared memory with cp.async
-// (void slots and unusable keys zero-filled), then per warp:
+// (void slots zero-filled) while the key mask is read, then per warp:
 //   S = Q K^T      16 x 64, 2 k-steps x 8 n-tiles of mma.m16n8k16 (fragments by ldmatrix)
 //   masked softmax over the 64 keys in registers (quad shuffles for row max / sum)
 //   O = P V        16 x 32, P re-packed to bf16 straight from the S accumulators,
@@ -298,18 +298,35 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
     for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(HPC * blockIdx.y + e / 225) * 225 + e % 225];
   pdl_trigger();
   pdl_wait();
+  const int h0 = HPC * blockIdx.y;
+  // slot s of the window -> token row (-1 for a void slot), by arithmetic alone
+  auto slot_token = [&](int sl) {
+    const int ty = wy * WS - offset + (sl >> 3), tx = wx * WS - offset + (sl & 7);
+    return (ty >= 0 && ty < Ht && tx >= 0 && tx < Wt) ? b * Nt + ty * Wt + tx : -1;
+  };
+  // stage Q, K and V of both heads for every real slot (16-byte chunks, zero-filled for void
+  // slots) while the key mask is read: unusable keys are real rows whose scores the softmax
+  // sets to -inf, so their contents never matter
+#pragma unroll
+  for (int part = 0; part < 3; ++part) {
+    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
+      const int sl = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
+      const int t = slot_token(sl);
+      const bf16* src = qkv + (size_t)(t >= 0 ? t : 0) * 3 * d + part * d + (h0 + hh) * DH + ch * 8;
+      bf16* dst = (part == 0 ? &Qs[hh][sl][0] : part == 1 ? &Ks[hh][sl][0] : &Vs[hh][sl][0]) + ch * 8;
+      cp_async16(dst, src, t >= 0);
+    }
+  }
   if (tid < SLOTS) {
-    const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
-    const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
-    const int t = real ? b * Nt + ty * Wt + tx : -1;
+    const int t = slot_token(tid);
     stok[tid] = t;
-    const bool ok = real && v_in[t] != 0;
+    const bool ok = t >= 0 && v_in[t] != 0;
     const unsigned bal = __ballot_sync(0xffffffffu, ok);
     if (lane == 0) okw[warp] = bal;
   }
+  cp_async_wait_all();
   __syncthreads();
   const unsigned long long keymask = (unsigned long long)okw[0] | ((unsigned long long)okw[1] << 32);
-  const int h0 = HPC * blockIdx.y;
 
   if (keymask == 0ull) {  // no usable key: the window outputs 0 and stays invalid
     for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
@@ -323,21 +340,6 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
     return;
   }
   if (h0 == 0 && tid < SLOTS && stok[tid] >= 0) v_out[stok[tid]] = 1;
-
-  // stage Q (real slots), K and V (usable keys) of both heads, 16-byte chunks, zero-filled otherwise
-#pragma unroll
-  for (int part = 0; part < 3; ++part) {
-    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
-      const int s = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
-      const int t = stok[s];
-      const bool valid = part == 0 ? t >= 0 : ((keymask >> s) & 1ull) != 0;
-      const bf16* src = qkv + (size_t)(t >= 0 ? t : 0) * 3 * d + part * d + (h0 + hh) * DH + ch * 8;
-      bf16* dst = (part == 0 ? &Qs[hh][s][0] : part == 1 ? &Ks[hh][s][0] : &Vs[hh][s][0]) + ch * 8;
-      cp_async16(dst, src, valid);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
 
   const int hh = warp >> 2, wq = warp & 3;
   const int g = lane >> 2, tq = lane & 3;
