@@ -283,7 +283,7 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
         TRY(cuda_err(launch_attention_tc_mem(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st, rp)));
       } else {
         LaunchScope ls(c, st, K_ATTN);
-        TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp)));
+        TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp, err)));
       }
       if (temporal) TRY(record_memory(qkv));
       if (c->fold_ln) {

@@ -155,10 +155,11 @@ template <typename T>
 cudaError_t launch_attention(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
                              int Wt, int d, int heads, int offset, cudaStream_t st, const float* relpos = nullptr);
 
-// Tensor-core form for BF16 activations (mma.sync bf16, FP32 softmax statistics).
+// Tensor-core form for BF16 activations (mma.sync bf16, FP32 softmax statistics); err
+// (optional) receives DEV_MBAR_TIMEOUT if a window's TMA staging does not complete.
 cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
                                 int Wt, int d, int heads, int offset, cudaStream_t st,
-                                const float* relpos = nullptr);
+                                const float* relpos = nullptr, int* err = nullptr);
 
 // Temporal blocks: as above, plus the keys of m memory slots.  tab->p[b*m + j] is a device
 // pointer to a previous frame's memory buffer (null = empty slot; tab null = no memory);

@@ -11,7 +11,11 @@
 // SIMT form: one CTA per (window, head, frame), one thread per window slot.  K and V
 // of the window's usable keys are staged in shared memory; each query thread runs a
 // two-pass softmax (max, then exp-sum and weighted V) in FP32.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
+#include "tc_primitives.cuh"
 
 namespace inpaint {
 
@@ -434,6 +438,207 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
   }
 }
 
+// The same with Q, K and V staged by TMA: a 4D tensor map views qkv as [B][Ht][Wt][3d],
+// so one box {32 channels, 8 x 8 tokens} is the window's 64 rows of one part (Q, K or
+// V) of one head; void slots of shifted border windows lie outside the map and arrive as
+// zeros.  Six boxes per CTA replace 24 address computations and cp.async per thread.  The
+// boxes land in 64-byte rows with the 64-byte TMA swizzle (16-byte chunk c of slot row r
+// at c ^ ((r >> 1) & 3)), which the ldmatrix addresses below follow (conflict-free).
+__device__ __forceinline__ uint32_t swz64(int row, int chunk) {
+  return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
+}
+
+template <bool RP>
+__global__ void __launch_bounds__(TC_THREADS) attn_tma_kernel(const __grid_constant__ CUtensorMap tmQKV,
+                                                              const uint8_t* __restrict__ v_in,
+                                                              bf16* __restrict__ o, uint8_t* __restrict__ v_out,
+                                                              int Ht, int Wt, int d, int offset, int nwx,
+                                                              const float* __restrict__ relpos, int* err) {
+  extern __shared__ uint8_t asm_raw[];
+  // [part Q, K, V][head of the pair] tiles of 64 slot rows x 64 bytes, 512-byte aligned
+  uint8_t* tiles = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(asm_raw) + 511) & ~uintptr_t(511));
+  __shared__ float rps[RP ? HPC : 1][RP ? 225 : 1];
+  __shared__ int stok[SLOTS];
+  __shared__ unsigned okw[2];
+  __shared__ __align__(8) uint64_t bar;
+  const int w = blockIdx.x, b = blockIdx.z;
+  const int wy = w / nwx, wx = w - (w / nwx) * nwx;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Nt = Ht * Wt;
+  const int h0 = HPC * blockIdx.y;
+  constexpr int TILE = SLOTS * DH * 2;
+  auto tile = [&](int part, int hh) { return tiles + (part * HPC + hh) * TILE; };
+
+  if (RP)
+    for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(h0 + e / 225) * 225 + e % 225];
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmQKV);
+  }
+  __syncthreads();
+  pdl_trigger();
+  pdl_wait();
+  if (tid == 0) {
+    tc::mbar_expect_tx(&bar, 3 * HPC * TILE);
+    for (int part = 0; part < 3; ++part)
+      for (int hh = 0; hh < HPC; ++hh)
+        tc::tma_load_4d(tile(part, hh), &tmQKV, &bar, part * d + (h0 + hh) * DH, wx * WS - offset, wy * WS - offset,
+                        b);
+  }
+  // the window's key mask while the boxes land
+  if (tid < SLOTS) {
+    const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
+    const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
+    const int t = real ? b * Nt + ty * Wt + tx : -1;
+    stok[tid] = t;
+    const bool ok = real && v_in[t] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) okw[warp] = bal;
+  }
+  const bool landed = tc::mbar_wait_timed(&bar, 0);
+  __syncthreads();
+  if (!landed) {
+    if (tid == 0 && err) atomicExch(err, DEV_MBAR_TIMEOUT);
+    return;
+  }
+  const unsigned long long keymask = (unsigned long long)okw[0] | ((unsigned long long)okw[1] << 32);
+
+  if (keymask == 0ull) {  // no usable key: the window outputs 0 and stays invalid
+    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
+      const int sl = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
+      const int t = stok[sl];
+      if (t >= 0) {
+        *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) = make_uint4(0, 0, 0, 0);
+        if (h0 == 0 && hh == 0 && ch == 0) v_out[t] = 0;
+      }
+    }
+    return;
+  }
+  if (h0 == 0 && tid < SLOTS && stok[tid] >= 0) v_out[stok[tid]] = 1;
+
+  const int hh = warp >> 2, wq = warp & 3;
+  const int g = lane >> 2, tq = lane & 3;
+  const int r0 = wq * 16;
+  uint8_t* Qt = tile(0, hh);
+  const uint8_t* Kt = tile(1, hh);
+  const uint8_t* Vt = tile(2, hh);
+  // ---- S = Q K^T
+  uint32_t qa[2][4];
+  {
+    const int row = r0 + (lane & 15);
+    ldsm_x4(qa[0], Qt + swz64(row, lane >> 4));
+    ldsm_x4(qa[1], Qt + swz64(row, 2 + (lane >> 4)));
+  }
+  float sc[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    sc[j][0] = sc[j][1] = sc[j][2] = sc[j][3] = 0.f;
+    uint32_t kb[4];  // (k 0-7, 8-15) of k-step 0 and (16-23, 24-31) of k-step 1, keys 8j .. 8j+7
+    ldsm_x4(kb, Kt + swz64(8 * j + (lane & 7), lane >> 3));
+    mma_bf16_16816(sc[j], qa[0], kb[0], kb[1]);
+    mma_bf16_16816(sc[j], qa[1], kb[2], kb[3]);
+  }
+  // ---- masked softmax (rows g and g+8 of this warp's 16), FP32
+  const float sl2 = 1.4426950408889634f / sqrtf((float)DH);  // scale * log2(e)
+  float mx0 = -INFINITY, mx1 = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int key = 8 * j + 2 * tq + c;
+      const bool okk = (keymask >> key) & 1ull;
+      const float bb0 = RP ? rps[hh][relpos_index(r0 + g, key)] * LOG2E : 0.f;
+      const float bb1 = RP ? rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
+      sc[j][c] = okk ? (RP ? fmaf(sc[j][c], sl2, bb0) : sc[j][c] * sl2) : -INFINITY;
+      sc[j][2 + c] = okk ? (RP ? fmaf(sc[j][2 + c], sl2, bb1) : sc[j][2 + c] * sl2) : -INFINITY;
+      mx0 = fmaxf(mx0, sc[j][c]);
+      mx1 = fmaxf(mx1, sc[j][2 + c]);
+    }
+  }
+  mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 1));
+  mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 2));
+  mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 1));
+  mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 2));
+  float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      sc[j][c] = exp2f(sc[j][c] - mx0);
+      sc[j][2 + c] = exp2f(sc[j][2 + c] - mx1);
+      l0 += sc[j][c];
+      l1 += sc[j][2 + c];
+    }
+  }
+  l0 += __shfl_xor_sync(0xffffffffu, l0, 1);
+  l0 += __shfl_xor_sync(0xffffffffu, l0, 2);
+  l1 += __shfl_xor_sync(0xffffffffu, l1, 1);
+  l1 += __shfl_xor_sync(0xffffffffu, l1, 2);
+  // ---- O = P V
+  float oc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {  // keys 16kk .. 16kk+15
+    uint32_t pa[4];
+    pa[0] = pack_bf16(sc[2 * kk][0], sc[2 * kk][1]);
+    pa[1] = pack_bf16(sc[2 * kk][2], sc[2 * kk][3]);
+    pa[2] = pack_bf16(sc[2 * kk + 1][0], sc[2 * kk + 1][1]);
+    pa[3] = pack_bf16(sc[2 * kk + 1][2], sc[2 * kk + 1][3]);
+#pragma unroll
+    for (int nn = 0; nn < 2; ++nn) {  // head dims 16nn .. 16nn+15
+      uint32_t vb[4];
+      ldsm_x4_t(vb, Vt + swz64(16 * kk + (lane & 7) + ((lane >> 3) & 1) * 8, 2 * nn + (lane >> 4)));
+      mma_bf16_16816(oc[2 * nn], pa, vb[0], vb[1]);
+      mma_bf16_16816(oc[2 * nn + 1], pa, vb[2], vb[3]);
+    }
+  }
+  const float inv0 = 1.f / l0, inv1 = 1.f / l1;
+  __syncwarp();
+  // stage this warp's 16 output rows in its own Q rows, then store 16-byte chunks
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g, j) + 4 * tq) = pack_bf16(oc[j][0] * inv0, oc[j][1] * inv0);
+    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g + 8, j) + 4 * tq) = pack_bf16(oc[j][2] * inv1, oc[j][3] * inv1);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = lane; e < 16 * 4; e += 32) {
+    const int sl = r0 + (e >> 2), ch = e & 3;
+    const int t = stok[sl];
+    if (t >= 0)
+      *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) =
+          *reinterpret_cast<const uint4*>(Qt + swz64(sl, ch));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// qkv [B][Ht][Wt][3d] bf16 as a 4D map with {32 channels, 8, 8, 1} boxes, 64-byte swizzle
+bool qkv_map(CUtensorMap* m, const bf16* qkv, int B, int Ht, int Wt, int d) {
+  auto fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(qkv) & 15)) return false;
+  const uint64_t row = (uint64_t)3 * d * 2;
+  cuuint64_t dims[4] = {(cuuint64_t)3 * d, (cuuint64_t)Wt, (cuuint64_t)Ht, (cuuint64_t)B};
+  cuuint64_t strides[3] = {row, row * Wt, row * Wt * Ht};
+  cuuint32_t box[4] = {DH, WS, WS, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(qkv), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Temporal form on tensor cores: key blocks of 64 (the current window, then each memory
 // slot's tokens at the window's positions) are staged one after the other into the same
 // K / V buffers; per block S = Q K^T, the running row maximum is raised, the running sum
@@ -624,10 +829,19 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
 }  // namespace
 
 cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht, int Wt,
-                                int d, int heads, int offset, cudaStream_t st, const float* relpos) {
+                                int d, int heads, int offset, cudaStream_t st, const float* relpos, int* err) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   if (heads % HPC) return cudaErrorInvalidValue;
   dim3 grid(nwy * nwx, heads / HPC, B);
+  CUtensorMap m;
+  if (qkv_map(&m, qkv, B, Ht, Wt, d)) {
+    constexpr int smem = 3 * HPC * SLOTS * DH * 2 + 512;
+    if (relpos)
+      return launch_pdl(attn_tma_kernel<true>, grid, dim3(TC_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
+                        nwx, relpos, err);
+    return launch_pdl(attn_tma_kernel<false>, grid, dim3(TC_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
+                      nwx, (const float*)nullptr, err);
+  }
   if (relpos)
     return launch_pdl(attn_tc_kernel<true>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
                       relpos);
