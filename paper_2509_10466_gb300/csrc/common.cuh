@@ -61,12 +61,17 @@ __host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 __device__ __forceinline__ float gelu_erf(float x) {
   return 0.5f * x * (1.0f + erff(x * 0.70710678118654752440f));
 }
-// GELU for the BF16 form, whose GELU outputs are rounded to bf16 right away: erf from
-// Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26,
-//   erf(z) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-z^2),  t = 1 / (1 + p z),
-// |error| <= 1.5e-7 for z >= 0 (odd extension for z < 0), evaluated with the PTX
-// approximate reciprocal and base-2 exponential.  About 13 instructions instead of the
-// ~30 of a correctly rounded erff; far below the bf16 rounding step of its output.
+// GELU for the BF16 form, whose GELU outputs are rounded to bf16 right away:
+//   gelu(x) ~ x * sigmoid(x * P(x^2)),  P of degree 4,
+// the logistic form of the normal CDF with an odd polynomial argument whose
+// coefficients were fitted (iteratively reweighted least squares, minimax-like) to
+// 0.5 x (1 + erf(x / sqrt 2)) on [-12, 12]: |error| <= 5e-6 absolute there (GPU test
+// against the FP64 closed form), x P(x^2) is increasing and the form saturates to x and
+// to 0 beyond.  The coefficients below already carry the factor -log2(e) of exp2; the
+// sigmoid uses the PTX approximate base-2 exponential and reciprocal (an overflowing
+// exponential gives 0 for large negative x).  8 FP32 operations and 2 MUFU per value.
+// The error is below the bf16 rounding step of the output (2^-9 relative) for
+// |gelu(x)| >= 3e-3, and absolutely smaller elsewhere.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -78,17 +83,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return r;
 }
 __device__ __forceinline__ float gelu_as(float x) {
-  const float z = fabsf(x) * 0.70710678118654752440f;
-  const float t = rcp_approx(fmaf(0.3275911f, z, 1.0f));
-  float p = fmaf(1.061405429f, t, -1.453152027f);
-  p = fmaf(p, t, 1.421413741f);
-  p = fmaf(p, t, -0.284496736f);
-  p = fmaf(p, t, 0.254829592f);
-  p *= t;
-  const float e = ex2_approx(-(z * z) * 1.44269504088896340736f);
-  const float erf_v = copysignf(fmaf(-p, e, 1.0f), x);
-  const float hx = 0.5f * x;
-  return fmaf(hx, erf_v, hx);
+  const float x2 = x * x;
+  float p = fmaf(-2.6439463454153156e-06f, x2, 7.70496335462667e-05f);
+  p = fmaf(p, x2, 4.2379501974210143e-04f);
+  p = fmaf(p, x2, -1.0534834861755371e-01f);
+  p = fmaf(p, x2, -2.3019843101501465f);
+  return x * rcp_approx(1.0f + ex2_approx(x * p));
 }
 
 __device__ __forceinline__ float to_f32(float v) { return v; }

@@ -37,8 +37,9 @@ def test_tcgen05_gemm_matches_fp32_matmul(M, N, K):
 
 
 def test_gelu_of_the_bf16_form_matches_erff():
-    """A&S 7.1.26 erf (|error| <= 1.5e-7) inside GELU: within 1e-6 absolute of CUDA's erff GELU,
-    and within 1e-6 of the FP64 closed form, over [-12, 12]."""
+    """The BF16 form's GELU, x * sigmoid(x P(x^2)): within 6e-6 absolute of CUDA's erff GELU
+    and of the FP64 closed form over [-12, 12] (the fit's FP32 error is 4.9e-6); the FP32
+    form's erff GELU within 1e-6 of the closed form."""
     lib()
     x = torch.linspace(-12, 12, 200001, dtype=torch.float32)
     xd = x.cuda()
@@ -47,9 +48,17 @@ def test_gelu_of_the_bf16_form_matches_erff():
     binding.inpaint_test_gelu(xd, a, b)
     torch.cuda.synchronize()
     ref = 0.5 * x.double() * (1 + torch.erf(x.double() / 2 ** 0.5))
-    assert float((a.cpu().double() - b.cpu().double()).abs().max()) <= 1e-6
-    assert float((a.cpu().double() - ref).abs().max()) <= 1e-6
+    assert float((a.cpu().double() - b.cpu().double()).abs().max()) <= 6e-6
+    assert float((a.cpu().double() - ref).abs().max()) <= 6e-6
     assert float((b.cpu().double() - ref).abs().max()) <= 1e-6
+    # saturation: x for large x, 0 (no NaN) for large negative x
+    big = torch.tensor([-1e4, -100.0, -30.0, 30.0, 100.0, 1e4]).cuda()
+    ya = torch.empty_like(big)
+    yb = torch.empty_like(big)
+    binding.inpaint_test_gelu(big, ya, yb)
+    torch.cuda.synchronize()
+    assert torch.isfinite(ya).all()
+    assert torch.equal(ya.cpu()[3:], big.cpu()[3:]) and float(ya.cpu()[:3].abs().max()) == 0.0
 
 
 # ----------------------------------------------------------------------------- FP32 form
