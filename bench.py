@@ -165,6 +165,9 @@ def bytes_per_frame(m, H, W, act_bytes=2):
     }
 
 
+TRAFFIC_HEADERS = ("common.cuh", "tc_primitives.cuh", "warp_rows.cuh")
+
+
 def read_traffic():
     """Per-launch DRAM bytes of each kernel class from the committed ncu summary, if current."""
     import hashlib
@@ -180,7 +183,10 @@ def read_traffic():
         src = os.path.join(ROOT, "paper_2509_10466_gb300", "csrc", kv["source"])
         if not os.path.exists(src):
             continue
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        hs = hashlib.sha256(open(src, "rb").read())
+        for hdr in TRAFFIC_HEADERS:  # the device code every kernel source includes
+            hs.update(open(os.path.join(ROOT, "paper_2509_10466_gb300", "csrc", hdr), "rb").read())
+        h = hs.hexdigest()[:16]
         if h == kv.get("sha"):
             out[kv["class"]] = float(kv["bytes_per_launch"])
     return out

@@ -294,9 +294,9 @@ INPAINT_API int inpaint_test_gemm_bf16(const void* A, const void* Bt, float* C, 
                            void* stream);
 
 /* The two GELU evaluations of the library on device floats x[n]: y_bf16_form[i] as the
- * BF16 tensor-core epilogues compute it (x * sigmoid(x P(x^2)) with a fitted degree-4 P,
- * |error| <= 5e-6 absolute on [-12, 12], saturating beyond) and y_fp32_form[i] with
- * CUDA's erff (the FP32 form). */
+ * BF16 tensor-core epilogues compute it (0.5 x (1 + tanh(x P(x^2))) with a fitted degree-4
+ * P and the approximate hardware tanh: |error| <= 6e-6 + 2.5e-4 |x| absolute on [-12, 12],
+ * saturating beyond) and y_fp32_form[i] with CUDA's erff (the FP32 form). */
 INPAINT_API int inpaint_test_gelu(const float* x, float* y_bf16_form, float* y_fp32_form, int n,
                                   void* stream);
 

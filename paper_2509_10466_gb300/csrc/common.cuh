@@ -62,33 +62,28 @@ __device__ __forceinline__ float gelu_erf(float x) {
   return 0.5f * x * (1.0f + erff(x * 0.70710678118654752440f));
 }
 // GELU for the BF16 form, whose GELU outputs are rounded to bf16 right away:
-//   gelu(x) ~ x * sigmoid(x * P(x^2)),  P of degree 4,
-// the logistic form of the normal CDF with an odd polynomial argument whose
-// coefficients were fitted (iteratively reweighted least squares, minimax-like) to
-// 0.5 x (1 + erf(x / sqrt 2)) on [-12, 12]: |error| <= 5e-6 absolute there (GPU test
-// against the FP64 closed form), x P(x^2) is increasing and the form saturates to x and
-// to 0 beyond.  The coefficients below already carry the factor -log2(e) of exp2; the
-// sigmoid uses the PTX approximate base-2 exponential and reciprocal (an overflowing
-// exponential gives 0 for large negative x).  8 FP32 operations and 2 MUFU per value.
-// The error is below the bf16 rounding step of the output (2^-9 relative) for
-// |gelu(x)| >= 3e-3, and absolutely smaller elsewhere.
-__device__ __forceinline__ float rcp_approx(float x) {
+//   gelu(x) ~ x * sigmoid(2u) = 0.5 x (1 + tanh(u)),  u = x P(x^2),  P of degree 4,
+// the logistic form of the normal CDF with an odd polynomial argument whose coefficients
+// were fitted (iteratively reweighted least squares, minimax-like) to
+// 0.5 x (1 + erf(x / sqrt 2)) on [-12, 12]: |error| <= 5e-6 absolute there with an exact
+// tanh; u is increasing in x and the form saturates to x and to 0 beyond.  The tanh is the
+// PTX approximate hyperbolic tangent (one MUFU operation, relative error about 2^-11),
+// which adds at most about 2.5e-4 |x| absolute: 2.5e-4 relative to the output for x > 0,
+// an eighth of the bf16 rounding step 2^-9 of the output; for x < 0 (output near 0) the
+// added error is absolute.  8 FP32 operations and 1 MUFU per value.
+__device__ __forceinline__ float tanh_approx(float x) {
   float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float ex2_approx(float x) {
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ float gelu_as(float x) {
   const float x2 = x * x;
-  float p = fmaf(-2.6439463454153156e-06f, x2, 7.70496335462667e-05f);
-  p = fmaf(p, x2, 4.2379501974210143e-04f);
-  p = fmaf(p, x2, -1.0534834861755371e-01f);
-  p = fmaf(p, x2, -2.3019843101501465f);
-  return x * rcp_approx(1.0f + ex2_approx(x * p));
+  float p = fmaf(9.163219942820433e-07f, x2, -2.670336834853515e-05f);
+  p = fmaf(p, x2, -1.468761620344594e-04f);
+  p = fmaf(p, x2, 3.6510955542325974e-02f);
+  p = fmaf(p, x2, 7.97806978225708e-01f);
+  const float hx = 0.5f * x;
+  return fmaf(hx, tanh_approx(x * p), hx);
 }
 
 __device__ __forceinline__ float to_f32(float v) { return v; }

@@ -113,7 +113,8 @@ __device__ __forceinline__ void store32_bf16(bf16* base, size_t ld, int nvalid, 
 // the tile is 512-byte aligned) and lane 0 hands it to a TMA store; the warp does not
 // wait for global memory.  A tile is reused only once the store issued from it two boxes
 // earlier has read it.  Rows past the tensor map's extent are not written, and a box with
-// no row inside it (nvalid <= 0) is not issued at all.
+// no row inside it (nvalid <= 0) is not issued at all; it still commits a (then empty)
+// bulk group, so that the group count behind each tile stays the box count.
 struct AsyncRows {
   uint8_t* tiles;  // 2 x TILE_BYTES, 512-byte aligned
   int k;
@@ -131,9 +132,9 @@ __device__ __forceinline__ void async_issue(const CUtensorMap* map, const uint8_
                                             int lane) {
   tc::fence_proxy_async_smem();
   __syncwarp();
-  if (lane == 0 && nvalid > 0) {
-    tc::tma_store_2d(map, t, c0, r0);
-    tc::bulk_commit();
+  if (lane == 0) {
+    if (nvalid > 0) tc::tma_store_2d(map, t, c0, r0);
+    tc::bulk_commit();  // an empty group when nothing is stored: the tile rotation counts every box
   }
 }
 

@@ -37,8 +37,10 @@ def test_tcgen05_gemm_matches_fp32_matmul(M, N, K):
 
 
 def test_gelu_of_the_bf16_form_matches_erff():
-    """The BF16 form's GELU, x * sigmoid(x P(x^2)): within 6e-6 absolute of CUDA's erff GELU
-    and of the FP64 closed form over [-12, 12] (the fit's FP32 error is 4.9e-6); the FP32
+    """The BF16 form's GELU, 0.5 x (1 + tanh(x P(x^2))) with the approximate hardware tanh:
+    within 6e-6 + 2.5e-4 |x| of CUDA's erff GELU and of the FP64 closed form over [-12, 12]
+    (the fit's error is 4.9e-6; the tanh's relative error of about 2^-11 scales with 0.5 |x|),
+    which for x > 0 is 2.5e-4 relative, an eighth of the bf16 step of the output; the FP32
     form's erff GELU within 1e-6 of the closed form."""
     lib()
     x = torch.linspace(-12, 12, 200001, dtype=torch.float32)
@@ -48,8 +50,11 @@ def test_gelu_of_the_bf16_form_matches_erff():
     binding.inpaint_test_gelu(xd, a, b)
     torch.cuda.synchronize()
     ref = 0.5 * x.double() * (1 + torch.erf(x.double() / 2 ** 0.5))
-    assert float((a.cpu().double() - b.cpu().double()).abs().max()) <= 6e-6
-    assert float((a.cpu().double() - ref).abs().max()) <= 6e-6
+    bound = 6e-6 + 2.5e-4 * x.double().abs()
+    assert bool(((a.cpu().double() - b.cpu().double()).abs() <= bound + 1e-6).all())
+    assert bool(((a.cpu().double() - ref).abs() <= bound).all())
+    pos = x > 0.5
+    assert float(((a.cpu().double() - ref).abs() / ref.abs())[pos].max()) <= 2.6e-4
     assert float((b.cpu().double() - ref).abs().max()) <= 1e-6
     # saturation: x for large x, 0 (no NaN) for large negative x
     big = torch.tensor([-1e4, -100.0, -30.0, 30.0, 100.0, 1e4]).cuda()
