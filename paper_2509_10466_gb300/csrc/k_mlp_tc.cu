@@ -35,15 +35,14 @@
 // per TMEM lane quarter, splitting the chunk's columns), 12..15 final epilogue (one per
 // lane quarter).  The tensor core idles while the accumulator is drained, twice per tile
 // (after MMA_P: residual, LayerNorm2 into SMEM; after the last MMA2: store, LayerNorm),
-// so three warps per lane quarter share both drains by columns: the final warp takes the
-// first half of the columns, each GELU warp a quarter.  The three exchange per-row
+// so three warps per lane quarter share both drains by columns (at D = 256: 64 columns
+// for the final warp, 96 for each GELU warp; at D = 128: half and two quarters).  The three exchange per-row
 // partial statistics (Welford) through shared memory and merge them in one fixed order.
 // Residual rows are prefetched to L2 a tile ahead, then loaded one 32-column block ahead;
 // rows move in whole 64-byte segments (warp_rows.cuh) and leave by TMA stores.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include <type_traits>
 
 #include "common.cuh"
 #include "tc_primitives.cuh"
@@ -98,8 +97,8 @@ struct MlpCfg {
                                     DRAIN_TILES * rows::TILE_BYTES /*staging tiles of the drain warps*/ +
                                     3 * BM * 2 * 4 /*partial row statistics of the three drain slices*/;
   // Drain column slices, in 32-column blocks: the final warp takes the first FS blocks,
-  // each GELU warp GS blocks (none when D = 64).
-  static constexpr int NCH = D / 32, GS = NCH / 4, FS = NCH - 2 * GS;
+  // each GELU warp GS blocks (none when D = 64), as even as 32-column blocks allow.
+  static constexpr int NCH = D / 32, GS = NCH == 8 ? 3 : NCH / 4, FS = NCH - 2 * GS;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 + HC b
   static_assert(W1_KB * W1_BOX <= STAGE_BYTES && W2_BOX <= STAGE_BYTES, "stage too small");
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
@@ -253,34 +252,29 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   };
 
   // After MMA_P: x1 = x + OUT + bp back into OUT (the starting value of MMA2's
-  // accumulation), Y = (x1 - mean) / std as bf16 into the SMEM A buffer.  With `ahead`, each
-  // residual block is loaded while the previous one is processed (the GELU warps' slices
-  // go without: their registers are fewer).
-  auto mid = [&](auto ahead, int t, int p, int role, int c_lo, int nch, uint8_t* tl) -> bool {
+  // accumulation), Y = (x1 - mean) / std as bf16 into the SMEM A buffer.  Each residual
+  // block is loaded while the previous one is processed, the first while MMA_P runs.
+  auto mid = [&](int t, int p, int role, int c_lo, int nch, uint8_t* tl) -> bool {
     const int quarter = warp & 3, r = quarter * 32 + lane;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     const int row0 = (2 * p + rank) * BM + quarter * 32;
     const int nvalid = M - row0;
     const float* xb = args.X + (size_t)row0 * D;
+    float4 gn[8];  // the next block's residual, loaded one block ahead (the first while MMA_P runs)
+    if (nch > 0) rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
     if (lane == 0) tc::bulk_wait_read<0>();  // the previous tile's stores are done with `tl`
     if (!tc::mbar_wait(p_full, t & 1, abort_flag)) return false;
     __syncwarp();
     tc::fence_after_sync();
     float run_n = 0.f, run_mean = 0.f, run_m2 = 0.f;
     if (nch > 0) {
-      float4 gn[8];  // the next block's residual, loaded one block ahead
-      if constexpr (decltype(ahead)::value) rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
 #pragma unroll 1
       for (int c0 = c_lo; c0 < c_lo + 32 * nch; c0 += 32) {
         uint32_t v[32];
         tc::tmem_ld_32x32b_x32(lane_base + c0, v);
         float f[32];
-        if constexpr (decltype(ahead)::value) {
-          rows::load32_finish(tl, lane, gn, f);
-          if (c0 + 32 < c_lo + 32 * nch) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
-        } else {
-          rows::load32_f32(xb + c0, D, nvalid, tl, lane, f);
-        }
+        rows::load32_finish(tl, lane, gn, f);
+        if (c0 + 32 < c_lo + 32 * nch) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; k += 4) {
@@ -540,7 +534,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     bool ok = true;
     int t = 0;
     for (int p = cid; p < pairs && ok; p += ncl, ++t) {
-      ok = mid(std::false_type{}, t, p, 1 + cg, d_lo, Cfg::GS, tl);
+      ok = mid(t, p, 1 + cg, d_lo, Cfg::GS, tl);
       for (int j = 0; j < NJ && ok; ++j, ++q) {
         const uint32_t hb = q % NB, use = q / NB;
         if (!tc::mbar_wait(&h_full[hb], use & 1, abort_flag)) { ok = false; break; }
@@ -600,7 +594,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     };
     prefetch(cid);
     for (int p = cid; p < pairs && ok; p += ncl, ++t) {
-      ok = mid(std::true_type{}, t, p, 0, 0, Cfg::FS, tl);
+      ok = mid(t, p, 0, 0, Cfg::FS, tl);
       prefetch(p + ncl);
       if (ok) ok = fin(t, p, 0, 0, Cfg::FS, st);
     }
