@@ -71,6 +71,13 @@ __device__ __forceinline__ float gelu_erf(float x) {
 // which adds at most about 2.5e-4 |x| absolute: 2.5e-4 relative to the output for x > 0,
 // an eighth of the bf16 rounding step 2^-9 of the output; for x < 0 (output near 0) the
 // added error is absolute.  8 FP32 operations and 1 MUFU per value.
+// 2^x by the PTX approximate base-2 exponential (one MUFU operation; subnormal results
+// flush to 0, 2^-inf = 0).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ float tanh_approx(float x) {
   float r;
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));

@@ -390,8 +390,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
   for (int j = 0; j < 8; ++j) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      sc[j][c] = exp2f(sc[j][c] - mx0);
-      sc[j][2 + c] = exp2f(sc[j][2 + c] - mx1);
+      sc[j][c] = ex2_approx(sc[j][c] - mx0);
+      sc[j][2 + c] = ex2_approx(sc[j][2 + c] - mx1);
       l0 += sc[j][c];
       l1 += sc[j][2 + c];
     }
@@ -539,19 +539,27 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tma_kernel(const __grid_const
     mma_bf16_16816(sc[j], qa[0], kb[0], kb[1]);
     mma_bf16_16816(sc[j], qa[1], kb[2], kb[3]);
   }
-  // ---- masked softmax (rows g and g+8 of this warp's 16), FP32
+  // ---- masked softmax (rows g and g+8 of this warp's 16), FP32, base 2.  Without the
+  // relative-position bias the maxima are taken on the raw scores (the scale is positive)
+  // and the scale enters with the maximum in one FMA in the exponent.
   const float sl2 = 1.4426950408889634f / sqrtf((float)DH);  // scale * log2(e)
+  const unsigned long long km = keymask >> (2 * tq);  // bit 8j + c: key 8j + 2tq + c
   float mx0 = -INFINITY, mx1 = -INFINITY;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const int key = 8 * j + 2 * tq + c;
-      const bool okk = (keymask >> key) & 1ull;
-      const float bb0 = RP ? rps[hh][relpos_index(r0 + g, key)] * LOG2E : 0.f;
-      const float bb1 = RP ? rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
-      sc[j][c] = okk ? (RP ? fmaf(sc[j][c], sl2, bb0) : sc[j][c] * sl2) : -INFINITY;
-      sc[j][2 + c] = okk ? (RP ? fmaf(sc[j][2 + c], sl2, bb1) : sc[j][2 + c] * sl2) : -INFINITY;
+      const bool okk = (km >> (8 * j + c)) & 1ull;
+      if constexpr (RP) {
+        const int key = 8 * j + 2 * tq + c;
+        const float bb0 = rps[hh][relpos_index(r0 + g, key)] * LOG2E;
+        const float bb1 = rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E;
+        sc[j][c] = okk ? fmaf(sc[j][c], sl2, bb0) : -INFINITY;
+        sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, bb1) : -INFINITY;
+      } else {
+        sc[j][c] = okk ? sc[j][c] : -INFINITY;
+        sc[j][2 + c] = okk ? sc[j][2 + c] : -INFINITY;
+      }
       mx0 = fmaxf(mx0, sc[j][c]);
       mx1 = fmaxf(mx1, sc[j][2 + c]);
     }
@@ -560,13 +568,16 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tma_kernel(const __grid_const
   mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 2));
   mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 1));
   mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 2));
+  // every row has a usable key (keymask != 0), so the maxima are finite
+  const float sx = RP ? 1.f : sl2;
+  const float o0 = -mx0 * sx, o1 = -mx1 * sx;
   float l0 = 0.f, l1 = 0.f;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      sc[j][c] = exp2f(sc[j][c] - mx0);
-      sc[j][2 + c] = exp2f(sc[j][2 + c] - mx1);
+      sc[j][c] = ex2_approx(fmaf(sc[j][c], sx, o0));
+      sc[j][2 + c] = ex2_approx(fmaf(sc[j][2 + c], sx, o1));
       l0 += sc[j][c];
       l1 += sc[j][2 + c];
     }
@@ -768,7 +779,7 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
     bm1 = fmaxf(bm1, __shfl_xor_sync(0xffffffffu, bm1, 1));
     bm1 = fmaxf(bm1, __shfl_xor_sync(0xffffffffu, bm1, 2));
     const float n0 = fmaxf(mx0, bm0), n1 = fmaxf(mx1, bm1);
-    const float a0 = exp2f(mx0 - n0), a1 = exp2f(mx1 - n1);  // 0 on the first usable block
+    const float a0 = ex2_approx(mx0 - n0), a1 = ex2_approx(mx1 - n1);  // 0 on the first usable block
     mx0 = n0;
     mx1 = n1;
     l0 *= a0;
@@ -782,8 +793,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
     for (int j = 0; j < 8; ++j) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        sc[j][c] = exp2f(sc[j][c] - mx0);
-        sc[j][2 + c] = exp2f(sc[j][2 + c] - mx1);
+        sc[j][c] = ex2_approx(sc[j][c] - mx0);
+        sc[j][2 + c] = ex2_approx(sc[j][2 + c] - mx1);
         l0 += sc[j][c];
         l1 += sc[j][2 + c];
       }
