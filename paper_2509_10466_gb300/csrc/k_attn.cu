@@ -441,23 +441,30 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
 // The same with Q, K and V staged by TMA: a 4D tensor map views qkv as [B][Ht][Wt][3d],
 // so one box {32 channels, 8 x 8 tokens} is the window's 64 rows of one part (Q, K or
 // V) of one head; void slots of shifted border windows lie outside the map and arrive as
-// zeros.  Six boxes per CTA replace 24 address computations and cp.async per thread.  The
+// zeros.  Three boxes per CTA (one head) replace the per-thread address computations and
+// cp.async.  The
 // boxes land in 64-byte rows with the 64-byte TMA swizzle (16-byte chunk c of slot row r
 // at c ^ ((r >> 1) & 3)), which the ldmatrix addresses below follow (conflict-free).
 __device__ __forceinline__ uint32_t swz64(int row, int chunk) {
   return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
 }
 
+// One head per CTA: 128 threads and 12 KB of boxes, so that many CTAs per SM keep TMA
+// loads in flight (two or more heads per CTA measured slower).
+constexpr int HPT = 1;
+constexpr int TMA_THREADS = 128 * HPT;
+static_assert(3 * HPT * SLOTS * DH * 2 + 512 <= 48 * 1024, "boxes exceed the default dynamic shared memory");
+
 template <bool RP>
-__global__ void __launch_bounds__(TC_THREADS) attn_tma_kernel(const __grid_constant__ CUtensorMap tmQKV,
+__global__ void __launch_bounds__(TMA_THREADS) attn_tma_kernel(const __grid_constant__ CUtensorMap tmQKV,
                                                               const uint8_t* __restrict__ v_in,
                                                               bf16* __restrict__ o, uint8_t* __restrict__ v_out,
                                                               int Ht, int Wt, int d, int offset, int nwx,
                                                               const float* __restrict__ relpos, int* err) {
   extern __shared__ uint8_t asm_raw[];
-  // [part Q, K, V][head of the pair] tiles of 64 slot rows x 64 bytes, 512-byte aligned
+  // [part Q, K, V][head of the CTA] tiles of 64 slot rows x 64 bytes, 512-byte aligned
   uint8_t* tiles = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(asm_raw) + 511) & ~uintptr_t(511));
-  __shared__ float rps[RP ? HPC : 1][RP ? 225 : 1];
+  __shared__ float rps[RP ? HPT : 1][RP ? 225 : 1];
   __shared__ int stok[SLOTS];
   __shared__ unsigned okw[2];
   __shared__ __align__(8) uint64_t bar;
@@ -465,12 +472,12 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tma_kernel(const __grid_const
   const int wy = w / nwx, wx = w - (w / nwx) * nwx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Nt = Ht * Wt;
-  const int h0 = HPC * blockIdx.y;
+  const int h0 = HPT * blockIdx.y;
   constexpr int TILE = SLOTS * DH * 2;
-  auto tile = [&](int part, int hh) { return tiles + (part * HPC + hh) * TILE; };
+  auto tile = [&](int part, int hh) { return tiles + (part * HPT + hh) * TILE; };
 
   if (RP)
-    for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(h0 + e / 225) * 225 + e % 225];
+    for (int e = tid; e < HPT * 225; e += TMA_THREADS) rps[e / 225][e % 225] = relpos[(h0 + e / 225) * 225 + e % 225];
   if (tid == 0) {
     tc::mbar_init(&bar, 1);
     tc::fence_mbar_init();
@@ -480,9 +487,9 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tma_kernel(const __grid_const
   pdl_trigger();
   pdl_wait();
   if (tid == 0) {
-    tc::mbar_expect_tx(&bar, 3 * HPC * TILE);
+    tc::mbar_expect_tx(&bar, 3 * HPT * TILE);
     for (int part = 0; part < 3; ++part)
-      for (int hh = 0; hh < HPC; ++hh)
+      for (int hh = 0; hh < HPT; ++hh)
         tc::tma_load_4d(tile(part, hh), &tmQKV, &bar, part * d + (h0 + hh) * DH, wx * WS - offset, wy * WS - offset,
                         b);
   }
@@ -505,8 +512,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tma_kernel(const __grid_const
   const unsigned long long keymask = (unsigned long long)okw[0] | ((unsigned long long)okw[1] << 32);
 
   if (keymask == 0ull) {  // no usable key: the window outputs 0 and stays invalid
-    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
-      const int sl = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
+    for (int e = tid; e < SLOTS * 4 * HPT; e += TMA_THREADS) {
+      const int sl = e / (4 * HPT), hh = (e >> 2) % HPT, ch = e & 3;
       const int t = stok[sl];
       if (t >= 0) {
         *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) = make_uint4(0, 0, 0, 0);
@@ -845,12 +852,13 @@ cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, u
   if (heads % HPC) return cudaErrorInvalidValue;
   dim3 grid(nwy * nwx, heads / HPC, B);
   CUtensorMap m;
-  if (qkv_map(&m, qkv, B, Ht, Wt, d)) {
-    constexpr int smem = 3 * HPC * SLOTS * DH * 2 + 512;
+  if (heads % HPT == 0 && qkv_map(&m, qkv, B, Ht, Wt, d)) {
+    constexpr int smem = 3 * HPT * SLOTS * DH * 2 + 512;
+    const dim3 tgrid(nwy * nwx, heads / HPT, B);
     if (relpos)
-      return launch_pdl(attn_tma_kernel<true>, grid, dim3(TC_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
+      return launch_pdl(attn_tma_kernel<true>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
                         nwx, relpos, err);
-    return launch_pdl(attn_tma_kernel<false>, grid, dim3(TC_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
+    return launch_pdl(attn_tma_kernel<false>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
                       nwx, (const float*)nullptr, err);
   }
   if (relpos)

@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(256) head_tile_kernel(const bf16* __restrict__
 // out(16 x 32 pixel tile) = conv3x3 as an implicit GEMM with M = 16 pixels of a row,
 // K = 9 taps x C channels, N = 8 (3 used) on mma.sync m16n8k16.  The 18 x 34 x C halo
 // tile is staged in shared memory with 16-byte chunks XOR-swizzled by pixel; A fragments
-// come from ldmatrix, the weights (bf16) stay in registers.  Each warp owns two output
-// rows (4 m-tiles).  Bias, composite and crop as in the SIMT form.
+// come from ldmatrix.  The CTA turns the weights into the bf16 B fragments once, in shared
+// memory, from which every warp reads its lane's.  Each warp owns two output rows (4
+// m-tiles); the three predicted channels then go through shared memory (over the halo
+// tile) so that bias, composite and crop run over whole rows with 16-byte accesses.
 __device__ __forceinline__ void ldsm_x4_h(uint32_t (&r)[4], const void* p) {
   const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
@@ -238,10 +240,15 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
                                                        const float* __restrict__ wh, const float* __restrict__ bh,
                                                        const float* __restrict__ x, const uint8_t* __restrict__ hole,
                                                        int H, int W, float* __restrict__ out,
-                                                       float* __restrict__ pred) {
+                                                       float* __restrict__ pred, int vec) {
   constexpr int TY = 16, TX = 32, HY = TY + 2, HX = TX + 2, NCH = C / 8, KC = C / 16;
+  constexpr int NFRAG = 9 * KC * 2;  // B fragments per lane: (tap, kc, half)
   extern __shared__ __align__(16) uint8_t hsm[];
   bf16* tile = reinterpret_cast<bf16*>(hsm);  // [HY*HX][C], chunk k of pixel p at 8*(k ^ (p & (NCH-1)))
+  __shared__ uint32_t sfrag[NFRAG][32];  // bf16 pairs, per lane
+  // predictions of the tile with the bias added, over the halo tile once the MMAs are done
+  float(*spred)[TY][TX] = reinterpret_cast<float(*)[TY][TX]>(hsm);
+  static_assert(3 * TY * TX * 4 <= HY * HX * C * 2, "prediction tile exceeds the halo tile");
   const int b = blockIdx.z, y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
   pdl_trigger();
   pdl_wait();
@@ -257,32 +264,33 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(inside ? 16 : 0)
                  : "memory");
   }
+  // B fragment (tap, kc, half) of lane (g, tq): rows k = channels kc*16 + half*8 + 2tq, +1 of
+  // that tap, column n = output channel g (zero for g >= 3)
+  for (int e = threadIdx.x; e < NFRAG * 32; e += blockDim.x) {
+    const int f = e >> 5, ln = e & 31, fg = ln >> 2, ftq = ln & 3;
+    const int tap = f / (KC * 2), kc = (f / 2) % KC, hlf = f & 1;
+    const int c0 = kc * 16 + hlf * 8 + 2 * ftq;
+    const float w0 = fg < 3 ? __ldg(wh + (fg * C + c0) * 9 + tap) : 0.f;
+    const float w1 = fg < 3 ? __ldg(wh + (fg * C + c0 + 1) * 9 + tap) : 0.f;
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(w0, w1);
+    sfrag[f][ln] = *reinterpret_cast<uint32_t*>(&h2);
+  }
   asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-  // B fragments: k-step (tap, kc) -> rows k = channels kc*16 .. +15 of that tap, col n = output channel
   uint32_t bw[9][KC][2];
 #pragma unroll
   for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
     for (int kc = 0; kc < KC; ++kc)
 #pragma unroll
-      for (int hlf = 0; hlf < 2; ++hlf) {
-        const int c0 = kc * 16 + hlf * 8 + 2 * tq;
-        float w0 = 0.f, w1 = 0.f;
-        if (g < 3) {
-          w0 = wh[((size_t)g * C + c0) * 9 + tap];
-          w1 = wh[((size_t)g * C + c0 + 1) * 9 + tap];
-        }
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(w0, w1);
-        bw[tap][kc][hlf] = *reinterpret_cast<uint32_t*>(&h2);
-      }
+      for (int hlf = 0; hlf < 2; ++hlf) bw[tap][kc][hlf] = sfrag[(tap * KC + kc) * 2 + hlf][lane];
   const float bias0 = bh[0], bias1 = bh[1], bias2 = bh[2];
-  __syncthreads();
-  const size_t HW = (size_t)H * W;
-#pragma unroll 1
+  float acc[4][4];
+#pragma unroll
   for (int mt = 0; mt < 4; ++mt) {
     const int ty = 2 * warp + (mt >> 1), xs = (mt & 1) * 16;  // output row / first column of this m-tile
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int pix = (ty + tap / 3) * HX + xs + tap % 3 + (lane & 15);
@@ -291,28 +299,47 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
         const int chunk = 2 * kc + (lane >> 4);
         uint32_t a[4];
         ldsm_x4_h(a, tile + (size_t)pix * C + 8 * (chunk ^ (pix & (NCH - 1))));
-        mma_16816_h(acc, a, bw[tap][kc][0], bw[tap][kc][1]);
+        mma_16816_h(acc[mt], a, bw[tap][kc][0], bw[tap][kc][1]);
       }
     }
-    if (tq > 1) continue;
-    const int y = y0 + ty;
-    if (y >= H) continue;
+  }
+  __syncthreads();  // every warp is done with the halo tile
 #pragma unroll
-    for (int hrow = 0; hrow < 2; ++hrow) {
-      const int xx = x0 + xs + g + 8 * hrow;
-      if (xx >= W) continue;
-      const size_t q = (size_t)y * W + xx;
-      const size_t o = (size_t)b * 3 * HW + q;
-      const bool h = hole[(size_t)b * HW + q] != 0;
-      if (tq == 0) {
-        const float p0 = acc[2 * hrow] + bias0, p1 = acc[2 * hrow + 1] + bias1;
-        out[o] = h ? p0 : x[o];
-        out[o + HW] = h ? p1 : x[o + HW];
-        if (pred) { pred[o] = p0; pred[o + HW] = p1; }
-      } else {
-        const float p2 = acc[2 * hrow] + bias2;
-        out[o + 2 * HW] = h ? p2 : x[o + 2 * HW];
-        if (pred) pred[o + 2 * HW] = p2;
+  for (int mt = 0; mt < 4; ++mt) {
+    const int ty = 2 * warp + (mt >> 1), xs = (mt & 1) * 16;
+    // accumulator rows g, g + 8 = pixels xs + g, xs + g + 8; columns 2tq, 2tq + 1 = channels
+    if (tq == 0) {
+      spred[0][ty][xs + g] = acc[mt][0] + bias0;
+      spred[1][ty][xs + g] = acc[mt][1] + bias1;
+      spred[0][ty][xs + g + 8] = acc[mt][2] + bias0;
+      spred[1][ty][xs + g + 8] = acc[mt][3] + bias1;
+    } else if (tq == 1) {
+      spred[2][ty][xs + g] = acc[mt][0] + bias2;
+      spred[2][ty][xs + g + 8] = acc[mt][2] + bias2;
+    }
+  }
+  __syncthreads();
+  // composite and crop: out = hole ? pred : x, rows of the tile, four pixels per thread step
+  const size_t HW = (size_t)H * W;
+  for (int e = threadIdx.x; e < 3 * TY * (TX / 4); e += blockDim.x) {
+    const int ch = e / (TY * (TX / 4)), r = (e / (TX / 4)) % TY, x4 = 4 * (e % (TX / 4));
+    const int y = y0 + r, xx = x0 + x4;
+    if (y >= H || xx >= W) continue;
+    const size_t q = (size_t)y * W + xx;
+    const size_t o = (size_t)b * 3 * HW + (size_t)ch * HW + q;
+    const float* pv = &spred[ch][r][x4];
+    if (vec && xx + 4 <= W) {  // 16-byte aligned: W % 4 == 0 and aligned bases
+      const uchar4 hm = *reinterpret_cast<const uchar4*>(hole + (size_t)b * HW + q);
+      const float4 xv = *reinterpret_cast<const float4*>(x + o);
+      const float4 p4 = *reinterpret_cast<const float4*>(pv);
+      *reinterpret_cast<float4*>(out + o) =
+          make_float4(hm.x ? p4.x : xv.x, hm.y ? p4.y : xv.y, hm.z ? p4.z : xv.z, hm.w ? p4.w : xv.w);
+      if (pred) *reinterpret_cast<float4*>(pred + o) = p4;
+    } else {
+      for (int k = 0; k < 4 && xx + k < W; ++k) {
+        const bool h = hole[(size_t)b * HW + q + k] != 0;
+        out[o + k] = h ? pv[k] : x[o + k];
+        if (pred) pred[o + k] = pv[k];
       }
     }
   }
@@ -358,9 +385,13 @@ cudaError_t launch_head_composite(const T* in, int B, int Hp, int Wp, int C, con
     }
     dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
     const bf16* inb = reinterpret_cast<const bf16*>(in);
-    if (C == 16) return launch_pdl(head_mma_kernel<16>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
-    if (C == 32) return launch_pdl(head_mma_kernel<32>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
-    return launch_pdl(head_mma_kernel<64>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred);
+    // whole-row 16-byte accesses of x, out, pred (and 4-byte of the hole mask) when aligned
+    const int vec = W % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(out) |
+                                    reinterpret_cast<uintptr_t>(pred) | reinterpret_cast<uintptr_t>(hole)) &
+                                   15) == 0;
+    if (C == 16) return launch_pdl(head_mma_kernel<16>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred, vec);
+    if (C == 32) return launch_pdl(head_mma_kernel<32>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred, vec);
+    return launch_pdl(head_mma_kernel<64>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred, vec);
   }
   if (sizeof(T) == 2 && C % 8 == 0) {
     const size_t smem = (size_t)18 * 34 * C * 2 + (size_t)27 * C * 4;
