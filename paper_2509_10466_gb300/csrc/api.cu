@@ -177,6 +177,10 @@ int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
     return INPAINT_E_CUDA;
   if (c->use_bf16 && c->dec2_wp && launch_subpixel_weights(c->w32 + o.d2w, c->c2, c->c1, c->dec2_wp, st) != cudaSuccess)
     return INPAINT_E_CUDA;
+  if (c->use_bf16 && c->dec1_ws && launch_stacked_weights(c->w32 + o.d1w, c->c1, c->d, c->dec1_ws, st) != cudaSuccess)
+    return INPAINT_E_CUDA;
+  if (c->use_bf16 && c->dec2_ws && launch_stacked_weights(c->w32 + o.d2w, c->c2, c->c1, c->dec2_ws, st) != cudaSuccess)
+    return INPAINT_E_CUDA;
   if (c->use_bf16) {
     const int d = c->d, h = c->hid;
     for (int l = 0; l < c->L; ++l) {
@@ -345,14 +349,20 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     bf16* f1 = reinterpret_cast<bf16*>(ws + p.f1);
     bf16* f2 = reinterpret_cast<bf16*>(ws + p.f2);
     if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
-    if (c->dec1_wp && p.Wt >= 16 && p.Ht >= 8) {  // TMA box is 16 x 8 input pixels
+    if (c->dec1_ws && upconv_t_supported(d, c->c1, p.Ht, p.Wt)) {
+      LaunchScope ls(c, st, K_DEC1);
+      TRY(cuda_err(launch_upconv_t(ln, p.B, p.Ht, p.Wt, d, c->dec1_ws, c->w32 + o.d1b, f1, c->c1, c->dev_err, st)));
+    } else if (c->dec1_wp && p.Wt >= 16 && p.Ht >= 8) {  // TMA box is 16 x 8 input pixels
       LaunchScope ls(c, st, K_DEC1);
       TRY(cuda_err(launch_upconv_tc(ln, p.B, p.Ht, p.Wt, d, c->dec1_wp, c->w32 + o.d1b, f1, c->c1, c->dev_err, st)));
     } else {
       LaunchScope ls(c, st, K_DEC1);
       TRY(cuda_err(launch_upconv<bf16>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st)));
     }
-    if (c->dec2_wp) {
+    if (c->dec2_ws && upconv_t_supported(c->c1, c->c2, 2 * p.Ht, 2 * p.Wt)) {
+      LaunchScope ls(c, st, K_DEC2);
+      TRY(cuda_err(launch_upconv_t(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_ws, c->w32 + o.d2b, f2, c->c2, c->dev_err, st)));
+    } else if (c->dec2_wp) {
       LaunchScope ls(c, st, K_DEC2);
       TRY(cuda_err(launch_upconv_tc(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wp, c->w32 + o.d2b, f2, c->c2, c->dev_err, st)));
     } else {
@@ -417,6 +427,8 @@ void inpaint_destroy(inpaint_ctx* c) {
   cudaFree(c->dec1_wp);
   cudaFree(c->embed_w16);
   cudaFree(c->dec2_wp);
+  cudaFree(c->dec1_ws);
+  cudaFree(c->dec2_ws);
   cudaFree(c->dev_err);
   cudaFree(c->arena);
   cudaFree(c->stage);
@@ -458,6 +470,7 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
   c->weight_bytes = c->nparams * 4 + 64 * d * 4 + 9 * d * c->c1 * 4 + 9 * (size_t)c->c1 * c->c2 * 4 +
                     (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 + (size_t)32 * (c->c1 * d + c->c2 * c->c1) + 128 * d : 0) +
                     (c->fold_ln ? (size_t)c->L * (3 * d + h) * 4 : 0) +
+                    (c->use_bf16 ? 2 * (upconv_t_weight_elems(d, c->c1) + upconv_t_weight_elems(c->c1, c->c2)) : 0) +
                     256;
   if (cfg->hbm_budget_bytes && c->weight_bytes > cfg->hbm_budget_bytes) {
     delete c;
@@ -474,7 +487,11 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
             (!c->use_bf16 || !upconv_tc_supported(c->d, c->c1) ||
              cudaMalloc(&c->dec1_wp, (size_t)16 * c->c1 * c->d * 2) == cudaSuccess) &&
             (!c->use_bf16 || !upconv_tc_supported(c->c1, c->c2) ||
-             cudaMalloc(&c->dec2_wp, (size_t)16 * c->c2 * c->c1 * 2) == cudaSuccess);
+             cudaMalloc(&c->dec2_wp, (size_t)16 * c->c2 * c->c1 * 2) == cudaSuccess) &&
+            (!c->use_bf16 || !upconv_t_weight_elems(c->d, c->c1) ||
+             cudaMalloc(&c->dec1_ws, upconv_t_weight_elems(c->d, c->c1) * 2) == cudaSuccess) &&
+            (!c->use_bf16 || !upconv_t_weight_elems(c->c1, c->c2) ||
+             cudaMalloc(&c->dec2_ws, upconv_t_weight_elems(c->c1, c->c2) * 2) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
     inpaint_destroy(c);

@@ -199,6 +199,15 @@ bool upconv_tc_supported(int Cin, int Cout);
 cudaError_t launch_subpixel_weights(const float* w, int Cout, int Cin, bf16* wp, cudaStream_t st);
 cudaError_t launch_upconv_tc(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* wp, const float* bias,
                              bf16* out, int Cout, int* err, cudaStream_t st);
+// The same stage with the parities stacked on the MMA's M side (128 x 256 x 16 MMAs): ws =
+// launch_stacked_weights's [groups][shifts][128][Cin] bf16, upconv_t_weight_elems(Cin,
+// Cout) elements (0 = unsupported).  Supported when Cin % 64 == 0, Cout is 32 or 64 and
+// the input is at least 16 x 16 pixels.
+bool upconv_t_supported(int Cin, int Cout, int Hi, int Wi);
+size_t upconv_t_weight_elems(int Cin, int Cout);
+cudaError_t launch_stacked_weights(const float* w, int Cout, int Cin, bf16* ws, cudaStream_t st);
+cudaError_t launch_upconv_t(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* ws, const float* bias,
+                            bf16* out, int Cout, int* err, cudaStream_t st);
 
 // Generic FP32 3x3 conv (NHWC), optional x2 upsampling of the input, optional bias
 // (NULL = none), act 0 = identity / 1 = GELU, optional pre-activation output.

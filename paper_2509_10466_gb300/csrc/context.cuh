@@ -72,6 +72,8 @@ struct inpaint_ctx {
   inpaint::bf16* embed_w16 = nullptr;  // BF16 form: embed.w as bf16 [d][64]
   inpaint::bf16* dec1_wp = nullptr;  // BF16 form: merged sub-pixel weights [4][c1][4d]
   inpaint::bf16* dec2_wp = nullptr;  // [4][c2][4c1]
+  inpaint::bf16* dec1_ws = nullptr;  // BF16 form: parity-stacked sub-pixel weights (transposed stage)
+  inpaint::bf16* dec2_ws = nullptr;
   size_t weight_bytes = 0;
   int* dev_err = nullptr;
   uint8_t* arena = nullptr;

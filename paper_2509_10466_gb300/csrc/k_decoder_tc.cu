@@ -231,6 +231,249 @@ __global__ void subpixel_weights_kernel(const float* __restrict__ w, int Cout, i
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Transposed form for Cout = 32 or 64, with the parities stacked on the MMA's M side.
+// A tcgen05.mma takes as long for N = 32 or 64 as for N = 256, so the form above (M =
+// pixels, N = Cout) runs its tensor core at Cout / 256 of its rate.  Here a tile is a
+// 16 x 16 block of input pixels (N = 256, pixel q = 16 py + px) and the accumulator row
+// g * Cout + co holds output channel co of parity g of a group of NG = 128 / Cout parities
+// (all four at Cout = 32; the two of output-row parity a at Cout = 64):
+//   D[g Cout + co][q] = sum over input shifts (sy, sx) and channels ci of
+//                       Ws[s][g Cout + co][ci] . in[i0 + py + sy][j0 + px + sx][ci]
+// over the shifts any parity of the group uses (9 at Cout = 32, 6 at Cout = 64), with Ws
+// the parity's merged 2 x 2-tap weight for that shift, or 0 where the parity does not
+// read that shift (stacked_weights_kernel).  Every MMA is 128 x 256 x 16.  The epilogue
+// thread of accumulator row (g, co) turns 32 pixels at a time into bf16 GELU outputs,
+// transposes them through a 2 KB shared tile (32 pixels x 32 channels) and stores 16-byte
+// channel chunks of each output pixel (2 (i0 + py) + a, 2 (j0 + px) + b).
+constexpr int TQ = 16;            // tile = TQ x TQ input pixels
+constexpr int T_STAGES = 4;
+constexpr int T_THREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2-5 and 6-9: one epilogue group per accumulator
+
+template <int COUT>
+struct DecTCfg {
+  static constexpr int NG = 128 / COUT;                 // parities per group (stacked on M)
+  static constexpr int GROUPS = 4 / NG;
+  static constexpr int NSH = NG == 4 ? 9 : 6;           // input shifts per group
+  static constexpr int A_BYTES = 128 * BK * 2;          // stacked weights of one (shift, chunk)
+  static constexpr int B_BYTES = TQ * TQ * BK * 2;      // the shifted pixel block
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM_BYTES = T_STAGES * STAGE_BYTES + 1024 + 256 + 8 * 2048;
+  static_assert(COUT == 32 || COUT == 64, "stacked parities need Cout = 32 or 64");
+  static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
+};
+
+// Input offset of 3x3 row tap ky for output-row parity a after nearest x2 upsampling:
+// floor((a + ky - 1) / 2), in {-1, 0, 1}.
+__host__ __device__ __forceinline__ int tap_offset(int a, int k) { return (a + k + 1) / 2 - 1; }
+
+// Shift s of group grp as (sy, sx) and whether parity (a, b) reads it.
+__device__ __forceinline__ void group_shift(int ng, int grp, int s, int& sy, int& sx) {
+  if (ng == 4) { sy = s / 3 - 1; sx = s % 3 - 1; }
+  else { sy = s / 3 + grp - 1; sx = s % 3 - 1; }
+}
+
+// ws[(grp * NSH + s) * 128 + g * Cout + co][ci] (bf16): the sum of the 3x3 taps (ky, kx)
+// of w[co][ci][ky][kx] whose inputs land on shift s for parity g of group grp, 0 where the
+// parity does not read that shift.
+__global__ void stacked_weights_kernel(const float* __restrict__ w, int Cout, int Cin, bf16* __restrict__ ws) {
+  const int ng = 128 / Cout, nsh = ng == 4 ? 9 : 6, groups = 4 / ng;
+  const size_t n = (size_t)groups * nsh * 128 * Cin;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(e % Cin);
+    const int row = (int)((e / Cin) % 128);
+    const int gs = (int)(e / ((size_t)Cin * 128));
+    const int s = gs % nsh, grp = gs / nsh;
+    const int g = row / Cout, co = row % Cout;
+    const int a = ng == 4 ? g >> 1 : grp, b = ng == 4 ? g & 1 : g;
+    int sy, sx;
+    group_shift(ng, grp, s, sy, sx);
+    float acc = 0.f;
+    for (int ky = 0; ky < 3; ++ky)
+      for (int kx = 0; kx < 3; ++kx)
+        if (tap_offset(a, ky) == sy && tap_offset(b, kx) == sx) acc += w[((size_t)co * Cin + ci) * 9 + ky * 3 + kx];
+    ws[e] = __float2bfloat16_rn(acc);
+  }
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_constant__ CUtensorMap tmIn,
+                                                                const __grid_constant__ CUtensorMap tmW, bf16* out,
+                                                                int B, int Hi, int Wi, int Cin,
+                                                                const float* __restrict__ bias, int* err) {
+  using Cfg = DecTCfg<COUT>;
+  constexpr int NG = Cfg::NG, GROUPS = Cfg::GROUPS, NSH = Cfg::NSH;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + T_STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + T_STAGES;
+  uint64_t* acc_full = empty + T_STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* teardown = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint8_t* stage_tiles = smem + T_STAGES * Cfg::STAGE_BYTES + 256;  // [8 epilogue warps][32 pixels][64 B]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx_n = (Wi + TQ - 1) / TQ, by_n = (Hi + TQ - 1) / TQ;
+  const int tiles = B * by_n * bx_n * GROUPS;
+  const int kc = Cin / BK, nk = NSH * kc;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < T_STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    for (int a = 0; a < 2; ++a) { tc::mbar_init(&acc_full[a], 1); tc::mbar_init(&acc_empty[a], 4); }
+    tc::mbar_init(teardown, 1);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmIn);
+    tc::prefetch_tmap(&tmW);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, 512);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem_base = *tmem_slot;
+  pdl_trigger();
+  pdl_wait();
+
+  // tile -> (group fastest, then column block, row block, frame)
+  auto decode = [&](int tile, int& grp, int& j0, int& i0, int& img) {
+    grp = tile % GROUPS;
+    int r = tile / GROUPS;
+    j0 = (r % bx_n) * TQ;
+    r /= bx_n;
+    i0 = (r % by_n) * TQ;
+    img = r / by_n;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        int grp, j0, i0, img;
+        decode(tile, grp, j0, i0, img);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % T_STAGES;
+          if (g >= (uint32_t)T_STAGES && !tc::mbar_wait(&empty[s], ((g / T_STAGES) & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int sh = kb / kc, c0 = (kb - sh * kc) * BK;
+          int sy, sx;
+          group_shift(NG, grp, sh, sy, sx);
+          uint8_t* sa = smem + s * Cfg::STAGE_BYTES;
+          tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
+          tc::tma_load_2d(sa, &tmW, &full[s], c0, (grp * NSH + sh) * 128);
+          tc::tma_load_4d(sa + Cfg::A_BYTES, &tmIn, &full[s], c0, j0 + sx, i0 + sy, img);
+        }
+      }
+      for (uint32_t h = (g > (uint32_t)T_STAGES ? g - T_STAGES : 0); h < g; ++h)
+        if (!tc::mbar_wait_timed(&full[h % T_STAGES], (h / T_STAGES) & 1)) break;
+      if (!ok) {
+        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+        *abort_flag = 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, TQ * TQ);
+      uint32_t g = 0, i = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++i) {
+        const uint32_t acc = i & 1, use = i >> 1;
+        if (use >= 1 && !tc::mbar_wait(&acc_empty[acc], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint32_t dtm = tmem_base + acc * (TQ * TQ);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % T_STAGES;
+          if (!tc::mbar_wait(&full[s], (g / T_STAGES) & 1, abort_flag)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(smem + s * Cfg::STAGE_BYTES);
+          const uint64_t ad = tc::desc_kmajor_sw128(sa);
+          const uint64_t bd = tc::desc_kmajor_sw128(sa + Cfg::A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16(dtm, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
+          tc::mma_commit(&empty[s]);
+        }
+        if (ok) tc::mma_commit(&acc_full[acc]);
+      }
+      if (!ok) {
+        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+        *abort_flag = 1;
+      }
+      tc::mma_commit(teardown);
+      tc::mbar_wait_timed(teardown, 0);
+    }
+    __syncwarp();
+  } else {
+    const int quarter = warp & 3, grp_e = (warp - 2) >> 2;
+    const int Ho = 2 * Hi, Wo = 2 * Wi;
+    const int row = quarter * 32 + lane;             // accumulator row: parity g, channel co
+    const int co = row % COUT;
+    const int cbase = (quarter * 32) % COUT;         // first channel of this warp's rows
+    uint8_t* tl = stage_tiles + (size_t)(warp - 2) * 2048;
+    uint32_t i = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
+      const uint32_t acc = i & 1, use = i >> 1;
+      if ((int)acc != grp_e) continue;  // the other group drains this accumulator
+      if (!tc::mbar_wait(&acc_full[acc], use & 1, abort_flag)) {
+        if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      __syncwarp();
+      tc::fence_after_sync();
+      int grp, j0, i0, img;
+      decode(tile, grp, j0, i0, img);
+      // every row of a warp belongs to the same parity (a, b) = (wa, wb)
+      const int wa = NG == 4 ? quarter >> 1 : grp, wb = NG == 4 ? quarter & 1 : quarter >> 1;
+      const float bv = __ldg(bias + co);
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * (TQ * TQ);
+#pragma unroll 1
+      for (int c = 0; c < TQ * TQ; c += 32) {
+        uint32_t v[32];
+        tc::tmem_ld_32x32b_x32(tbase + c, v);
+        tc::tmem_ld_wait();
+        if (c + 32 >= TQ * TQ) {  // the accumulator is free once its last columns are read
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
+        }
+        // pixel c + k of channel co -> tile[k][lane] (bf16)
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          *reinterpret_cast<bf16*>(tl + k * 64 + lane * 2) = __float2bfloat16_rn(gelu_as(__uint_as_float(v[k]) + bv));
+        __syncwarp();
+        // 16-byte chunk ch of pixel k: channels cbase + 8 ch .. +7 of output pixel (2 (i0 + py) + wa, 2 (j0 + px) + wb)
+#pragma unroll
+        for (int r4 = 0; r4 < 4; ++r4) {
+          const int k = r4 * 8 + (lane >> 2), ch = lane & 3;
+          const int q = c + k, py = q / TQ, px = q % TQ;
+          const int pi = i0 + py, pj = j0 + px;
+          if (pi < Hi && pj < Wi) {
+            const uint4 val = *reinterpret_cast<const uint4*>(tl + k * 64 + ch * 16);
+            bf16* dst = out + (((size_t)img * Ho + 2 * pi + wa) * Wo + 2 * pj + wb) * COUT + cbase + ch * 8;
+            *reinterpret_cast<uint4*>(dst) = val;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem_base, 512);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -296,6 +539,48 @@ cudaError_t launch_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const bf
   return cudaGetLastError();
 }
 
+template <int COUT>
+cudaError_t launch_t_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* ws, const float* bias, bf16* out,
+                          int* err, cudaStream_t st) {
+  using Cfg = DecTCfg<COUT>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(upconv_t_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorInvalidValue;
+  CUtensorMap mi, mw;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)Wi, (cuuint64_t)Hi, (cuuint64_t)B};
+    cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)Wi * Cin * 2, (cuuint64_t)Hi * Wi * Cin * 2};
+    cuuint32_t box[4] = {BK, TQ, TQ, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (fn(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims, strides, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)Cfg::GROUPS * Cfg::NSH * 128};
+    cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
+    cuuint32_t box[2] = {BK, 128};
+    cuuint32_t es[2] = {1, 1};
+    if (fn(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ws), dims, strides, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  const int tiles = B * ((Hi + TQ - 1) / TQ) * ((Wi + TQ - 1) / TQ) * Cfg::GROUPS;
+  const int grid = tiles < num_sms() ? tiles : num_sms();
+  cudaError_t le = launch_pdl(upconv_t_kernel<COUT>, grid, dim3(T_THREADS), Cfg::SMEM_BYTES, st, mi, mw, out, B, Hi,
+                              Wi, Cin, bias, err);
+  if (le != cudaSuccess) return le;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool upconv_tc_supported(int Cin, int Cout) {
@@ -317,6 +602,35 @@ cudaError_t launch_upconv_tc(const bf16* in, int B, int Hi, int Wi, int Cin, con
     case 96: return launch_cout<96>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
     default: return launch_cout<128>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
   }
+}
+
+}  // namespace inpaint
+
+namespace inpaint {
+
+bool upconv_t_supported(int Cin, int Cout, int Hi, int Wi) {
+  return Cin % 64 == 0 && (Cout == 32 || Cout == 64) && Hi >= TQ && Wi >= TQ;
+}
+
+size_t upconv_t_weight_elems(int Cin, int Cout) {
+  if (Cin % 64 || (Cout != 32 && Cout != 64)) return 0;
+  const int ng = 128 / Cout;
+  return (size_t)(4 / ng) * (ng == 4 ? 9 : 6) * 128 * Cin;
+}
+
+cudaError_t launch_stacked_weights(const float* w, int Cout, int Cin, bf16* ws, cudaStream_t st) {
+  if (!upconv_t_weight_elems(Cin, Cout)) return cudaErrorInvalidValue;
+  stacked_weights_kernel<<<256, 256, 0, st>>>(w, Cout, Cin, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upconv_t(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* ws, const float* bias,
+                            bf16* out, int Cout, int* err, cudaStream_t st) {
+  if (!upconv_t_supported(Cin, Cout, Hi, Wi)) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(ws) | reinterpret_cast<uintptr_t>(out)) & 15)
+    return cudaErrorInvalidValue;
+  if (Cout == 32) return launch_t_cout<32>(in, B, Hi, Wi, Cin, ws, bias, out, err, st);
+  return launch_t_cout<64>(in, B, Hi, Wi, Cin, ws, bias, out, err, st);
 }
 
 }  // namespace inpaint
