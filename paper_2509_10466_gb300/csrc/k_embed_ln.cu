@@ -114,14 +114,17 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
 // 144 bytes for conflict-free ldmatrix); warp w computes tokens 16(w%4).. x channels
 // (w/4)*d/2 .. with mma.sync m16n8k16 (K = 64 in 4 steps, FP32 accumulate).  The tile
 // goes through shared memory so the FP32 token rows, the token mask and the fused
-// LayerNorm (FP32 statistics) are written coalesced.
+// LayerNorm are written coalesced.  The LayerNorm statistics (FP32, two passes: mean,
+// then squared deviations) come from the accumulator registers: quad shuffles, then the
+// two column halves of a row through shared memory, so that the store loop has no
+// reductions left.
 template <int D>
 struct EmbTc {
   static constexpr int TOK = 64, KP = 72;          // padded row length (bf16) of P and W
   static constexpr int P_BYTES = TOK * KP * 2;
   static constexpr int W_BYTES = D * KP * 2;
   static constexpr int OUT_STRIDE = D + 4;         // floats per staged output row
-  static constexpr int SMEM = P_BYTES + W_BYTES + TOK * OUT_STRIDE * 4 + 64 * 4;
+  static constexpr int SMEM = P_BYTES + W_BYTES + TOK * OUT_STRIDE * 4 + TOK * 4 /*known*/ + 4 * TOK * 4 /*row statistics*/;
 };
 
 __device__ __forceinline__ void ldsm_x4_e(uint32_t (&r)[4], const void* p) {
@@ -141,11 +144,6 @@ __device__ __forceinline__ void mma_16816_e(float (&c)[4], const uint32_t (&a)[4
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-__device__ __forceinline__ float warp_sum_e(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 template <int D>
 __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole,
@@ -159,6 +157,8 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
   bf16* Ws = reinterpret_cast<bf16*>(esm + C::P_BYTES);                     // [D][KP]
   float* O = reinterpret_cast<float*>(esm + C::P_BYTES + C::W_BYTES);      // [64][OUT_STRIDE]
   int* known = reinterpret_cast<int*>(esm + C::P_BYTES + C::W_BYTES + C::TOK * C::OUT_STRIDE * 4);
+  float* red = reinterpret_cast<float*>(known + C::TOK);  // [TOK][2 column halves] row sums
+  float* red2 = red + 2 * C::TOK;                          // [TOK][2] squared deviations
   const int b = blockIdx.y, t0 = blockIdx.x * C::TOK, Nt = Ht * Wt;
   const size_t HW = (size_t)H * W;
   const int tid = threadIdx.x;
@@ -237,40 +237,67 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
       mma_16816_e(acc[j], a, bb[0], bb[1]);
     }
   }
+  // bias; this thread's parts of rows m0 + g and m0 + g + 8 (columns n0 + 8j + 2tq, +1)
+  const int half = warp >> 2;
+  float sa = 0.f, sb = 0.f;
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
     const int c = n0 + 8 * j + 2 * tq;
     const float b0 = be[c], b1 = be[c + 1];
-    O[(m0 + g) * C::OUT_STRIDE + c] = acc[j][0] + b0;
-    O[(m0 + g) * C::OUT_STRIDE + c + 1] = acc[j][1] + b1;
-    O[(m0 + g + 8) * C::OUT_STRIDE + c] = acc[j][2] + b0;
-    O[(m0 + g + 8) * C::OUT_STRIDE + c + 1] = acc[j][3] + b1;
+    acc[j][0] += b0;
+    acc[j][1] += b1;
+    acc[j][2] += b0;
+    acc[j][3] += b1;
+    sa += acc[j][0] + acc[j][1];
+    sb += acc[j][2] + acc[j][3];
+  }
+  sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+  sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+  sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+  sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+  if (tq == 0) {
+    red[(m0 + g) * 2 + half] = sa;
+    red[(m0 + g + 8) * 2 + half] = sb;
+  }
+  __syncthreads();
+  const float ma = (red[(m0 + g) * 2] + red[(m0 + g) * 2 + 1]) * (1.f / D);
+  const float mb = (red[(m0 + g + 8) * 2] + red[(m0 + g + 8) * 2 + 1]) * (1.f / D);
+  float qa = 0.f, qb = 0.f;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int c = n0 + 8 * j + 2 * tq;
+    qa = fmaf(acc[j][0] - ma, acc[j][0] - ma, qa);
+    qa = fmaf(acc[j][1] - ma, acc[j][1] - ma, qa);
+    qb = fmaf(acc[j][2] - mb, acc[j][2] - mb, qb);
+    qb = fmaf(acc[j][3] - mb, acc[j][3] - mb, qb);
+    O[(m0 + g) * C::OUT_STRIDE + c] = acc[j][0];
+    O[(m0 + g) * C::OUT_STRIDE + c + 1] = acc[j][1];
+    O[(m0 + g + 8) * C::OUT_STRIDE + c] = acc[j][2];
+    O[(m0 + g + 8) * C::OUT_STRIDE + c + 1] = acc[j][3];
+  }
+  qa += __shfl_xor_sync(0xffffffffu, qa, 1);
+  qa += __shfl_xor_sync(0xffffffffu, qa, 2);
+  qb += __shfl_xor_sync(0xffffffffu, qb, 1);
+  qb += __shfl_xor_sync(0xffffffffu, qb, 2);
+  if (tq == 0) {
+    red2[(m0 + g) * 2 + half] = qa;
+    red2[(m0 + g + 8) * 2 + half] = qb;
   }
   __syncthreads();
   if (tid < C::TOK && t0 + tid < Nt) v0[(size_t)b * Nt + t0 + tid] = (uint8_t)known[tid];
   // each warp writes 8 token rows and their LayerNorm
+#pragma unroll 2
   for (int i = 0; i < 8; ++i) {
     const int tl = warp * 8 + i, t = t0 + tl;
     if (t >= Nt) break;
     const float* orow = O + tl * C::OUT_STRIDE;
     float* trow = tok + ((size_t)b * Nt + t) * D;
-    float s = 0.f;
+    const float mean = (red[tl * 2] + red[tl * 2 + 1]) * (1.f / D);
+    const float rstd = rsqrtf((red2[tl * 2] + red2[tl * 2 + 1]) * (1.f / D) + 1e-5f);
+    bf16* lrow = ln_out + ((size_t)b * Nt + t) * D;
     for (int c = 2 * lane; c < D; c += 64) {  // two channels per lane: 256-byte warp stores
       const float2 v = *reinterpret_cast<const float2*>(orow + c);
       *reinterpret_cast<float2*>(trow + c) = v;
-      s += v.x + v.y;
-    }
-    const float mean = warp_sum_e(s) / (float)D;
-    float q = 0.f;
-    for (int c = 2 * lane; c < D; c += 64) {
-      const float2 v = *reinterpret_cast<const float2*>(orow + c);
-      q = fmaf(v.x - mean, v.x - mean, q);
-      q = fmaf(v.y - mean, v.y - mean, q);
-    }
-    const float rstd = rsqrtf(warp_sum_e(q) / (float)D + 1e-5f);
-    bf16* lrow = ln_out + ((size_t)b * Nt + t) * D;
-    for (int c = 2 * lane; c < D; c += 64) {
-      const float2 v = *reinterpret_cast<const float2*>(orow + c);
       float y0 = (v.x - mean) * rstd, y1 = (v.y - mean) * rstd;
       if (ln_g) {  // else the affine part is folded into the next GEMM
         y0 = y0 * ln_g[c] + ln_b[c];
