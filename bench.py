@@ -134,8 +134,9 @@ def flops_per_frame(m, H, W):
         "fc1_gemm": 2 * N * d * r * d * L,
         "fc2_gemm": 2 * N * r * d * d * L,
         "proj_mlp_fused": 2 * N * d * d * L + 4 * N * d * r * d * L,
-        "decoder1": 2 * (4 * N) * 9 * d * c1,
-        "decoder2": 2 * (16 * N) * 9 * c1 * c2,
+        # nearest x2 upsampling then a 3x3 conv: per output parity a 2x2 conv on the input
+        "decoder1": 2 * (4 * N) * 4 * d * c1,
+        "decoder2": 2 * (16 * N) * 4 * c1 * c2,
         "head_composite": 2 * (16 * N) * 9 * c2 * 3,
         "embed": 2 * N * 64 * d,
     }
