@@ -25,7 +25,8 @@
 // 16 KB stages in the order the MMA warp consumes them (MMA1 of chunk j+1 is issued
 // before MMA2 of chunk j, so the tensor core works while the epilogue warps turn H_j
 // into bf16); the ring takes what shared memory is left.  TMEM: OUT (D cols) + two H
-// buffers (128 cols each).  The epilogue writes the bf16 H_j over the FP32 columns it
+// buffers (128 cols each); MMA_P accumulates into the H buffers' columns, so the next
+// tile's projection runs while the final drain still reads OUT.  The epilogue writes the bf16 H_j over the FP32 columns it
 // has just read (two hidden columns per 32-bit TMEM column, the tcgen05 A-operand
 // layout).  Barriers that the MMA warp waits on live in the even CTA and count both CTAs'
 // arrivals and TMA bytes; MMA completions are signalled to both CTAs.
@@ -100,6 +101,7 @@ struct MlpCfg {
   // each GELU warp GS blocks (none when D = 64), as even as 32-column blocks allow.
   static constexpr int NCH = D / 32, GS = NCH == 8 ? 3 : NCH / 4, FS = NCH - 2 * GS;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 + HC b
+  static_assert(H_COL0 + D <= 512 && NB * HC >= D, "MMA_P's accumulator lives in the H buffers' columns");
   static_assert(W1_KB * W1_BOX <= STAGE_BYTES && W2_BOX <= STAGE_BYTES, "stage too small");
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
@@ -141,8 +143,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   uint64_t* h_full = a_ready + 1;       // [NB]    both: H_j in TMEM
   uint64_t* h_done = h_full + NB;       // [NB]    even CTA: both CTAs turned H_j into bf16 (in TMEM)
   uint64_t* o_full = h_done + NB;       //         both: OUT complete
-  uint64_t* o_empty = o_full + 1;       //         even CTA: both CTAs drained OUT
-  uint64_t* teardown = o_empty + 1;
+  uint64_t* teardown = o_full + 1;
   uint64_t* stat_bar = teardown + 1;    // [4]     per lane quarter: the three drain slices' statistics
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(stat_bar + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -176,7 +177,6 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
       tc::mbar_init(&h_done[b], 2 * EPI_WARPS);
     }
     tc::mbar_init(o_full, 1);
-    tc::mbar_init(o_empty, 2 * DRAIN_WARPS);
     for (int k = 0; k < 4; ++k) tc::mbar_init(&stat_bar[k], 3 * 32);
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
@@ -251,8 +251,10 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     run_n = nn;
   };
 
-  // After MMA_P: x1 = x + OUT + bp back into OUT (the starting value of MMA2's
-  // accumulation), Y = (x1 - mean) / std as bf16 into the SMEM A buffer.  Each residual
+  // After MMA_P: x1 = x + P + bp into OUT (P: MMA_P's accumulator in the H columns; x1 is
+  // the starting value of MMA2's accumulation), Y = (x1 - mean) / std as bf16 into the
+  // SMEM A buffer.  A warp's OUT columns are its own final-drain slice of the previous
+  // tile, which it has finished.  Each residual
   // block is loaded while the previous one is processed, the first while MMA_P runs.
   auto mid = [&](int t, int p, int role, int c_lo, int nch, uint8_t* tl) -> bool {
     const int quarter = warp & 3, r = quarter * 32 + lane;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
 #pragma unroll 1
       for (int c0 = c_lo; c0 < c_lo + 32 * nch; c0 += 32) {
         uint32_t v[32];
-        tc::tmem_ld_32x32b_x32(lane_base + c0, v);
+        tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + c0, v);
         float f[32];
         rows::load32_finish(tl, lane, gn, f);
         if (c0 + 32 < c_lo + 32 * nch) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
@@ -371,7 +373,6 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     }
     tc::fence_before_sync();
     __syncwarp();
-    if (lane == 0) tc::mbar_arrive_cluster(lead(o_empty));  // the next tile's MMA_P may start once all slices are out
     return true;
   };
 
@@ -478,10 +479,10 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
           if (last) tc::mma_commit_pair(o_full, PAIR);
           return true;
         };
-        // OUT = A . Wp^T (the drains of the previous tile are done with OUT)
+        // P = A . Wp^T into the H columns: the previous tile's MMA2s, issued before, have
+        // read them (tcgen05 MMAs run in issue order); its final drain may still read OUT
         auto mma_p = [&](int t) {
           if (!tc::mbar_wait_cluster(a_full, t & 1, abort_flag)) return false;
-          if (t >= 1 && !tc::mbar_wait_cluster(o_empty, (t - 1) & 1, abort_flag)) return false;
           tc::fence_after_sync();
           for (int kb = 0; kb < Cfg::KA; ++kb) {
             int s;
@@ -489,7 +490,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
             const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sA + kb * (BM * BK * 2)));
             const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sR + s * Cfg::STAGE_BYTES));
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16_pair(tmem_base, ad + 2 * kk, bd + 2 * kk, id2, (kb | kk) != 0);
+            for (int kk = 0; kk < BK / 16; ++kk)
+              tc::mma_f16_pair(tmem_base + Cfg::H_COL0, ad + 2 * kk, bd + 2 * kk, id2, (kb | kk) != 0);
             tc::mma_commit_pair(&empty[s], PAIR);
           }
           tc::mma_commit_pair(p_full, PAIR);
