@@ -104,9 +104,11 @@ def test_bf16_small_shapes(H, W, B):
     check_parity(cfg, weights, x, hole, TOL_BF16)
 
 
-@pytest.mark.parametrize("H,W,B", [(64, 96, 2), (224, 100, 1), (96, 352, 1)])
+@pytest.mark.parametrize("H,W,B", [(64, 96, 2), (224, 100, 1), (96, 352, 1), (32, 64, 1)])
 def test_bf16_d256_decoder_on_tensor_cores(H, W, B):
-    """d256 puts both decoder stages on tcgen05 (c1 = 64, c2 = 32); ragged tile edges."""
+    """d256 puts both decoder stages on tcgen05 (c1 = 64, c2 = 32), with the parities
+    stacked on M for inputs of at least 16 x 16 pixels; ragged tile edges.  At 32 x 64
+    (8 x 16 tokens) the first stage takes the M = pixels form, the second the stacked one."""
     cfg = ModelConfig(dim=256, heads=8, window=8, blocks=2, mlp_ratio=4, precision=BF16)
     weights = S.make_weights(cfg, seed=21, perturb=True)
     x, hole = inputs(B, H, W, "polygons", seed=H * 7 + W)
