@@ -445,6 +445,11 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restr
 // cp.async.  The
 // boxes land in 64-byte rows with the 64-byte TMA swizzle (16-byte chunk c of slot row r
 // at c ^ ((r >> 1) & 3)), which the ldmatrix addresses below follow (conflict-free).
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
 __device__ __forceinline__ uint32_t swz64(int row, int chunk) {
   return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
 }
@@ -552,25 +557,30 @@ __global__ void __launch_bounds__(TMA_THREADS) attn_tma_kernel(const __grid_cons
   const float sl2 = 1.4426950408889634f / sqrtf((float)DH);  // scale * log2(e)
   const unsigned long long km = keymask >> (2 * tq);  // bit 8j + c: key 8j + 2tq + c
   float mx0 = -INFINITY, mx1 = -INFINITY;
+  auto mask_and_max = [&](auto masked) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 8; ++j) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const bool okk = (km >> (8 * j + c)) & 1ull;
-      if constexpr (RP) {
-        const int key = 8 * j + 2 * tq + c;
-        const float bb0 = rps[hh][relpos_index(r0 + g, key)] * LOG2E;
-        const float bb1 = rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E;
-        sc[j][c] = okk ? fmaf(sc[j][c], sl2, bb0) : -INFINITY;
-        sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, bb1) : -INFINITY;
-      } else {
-        sc[j][c] = okk ? sc[j][c] : -INFINITY;
-        sc[j][2 + c] = okk ? sc[j][2 + c] : -INFINITY;
+      for (int c = 0; c < 2; ++c) {
+        const bool okk = (km >> (8 * j + c)) & 1ull;
+        if constexpr (RP) {
+          const int key = 8 * j + 2 * tq + c;
+          const float bb0 = rps[hh][relpos_index(r0 + g, key)] * LOG2E;
+          const float bb1 = rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E;
+          sc[j][c] = okk ? fmaf(sc[j][c], sl2, bb0) : -INFINITY;
+          sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, bb1) : -INFINITY;
+        } else if constexpr (decltype(masked)::value) {
+          sc[j][c] = okk ? sc[j][c] : -INFINITY;
+          sc[j][2 + c] = okk ? sc[j][2 + c] : -INFINITY;
+        }
+        mx0 = fmaxf(mx0, sc[j][c]);
+        mx1 = fmaxf(mx1, sc[j][2 + c]);
       }
-      mx0 = fmaxf(mx0, sc[j][c]);
-      mx1 = fmaxf(mx1, sc[j][2 + c]);
     }
-  }
+  };
+  // a window whose 64 keys are all usable (most of a frame) skips the selects
+  if (RP || keymask != ~0ull) mask_and_max(BoolTag<true>{});
+  else mask_and_max(BoolTag<false>{});
   mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 1));
   mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 2));
   mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 1));
