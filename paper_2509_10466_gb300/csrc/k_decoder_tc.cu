@@ -14,7 +14,10 @@
 // Same persistent warp-specialized structure as the token GEMM: warp 0 TMA, warp 1
 // MMA (M=128, N=Cout), two TMEM accumulators; the epilogue (bias, GELU, bf16, NHWC
 // scatter to the parity's pixels) has two groups of 4 warps, group g draining the
-// tiles that land in accumulator g, so two tiles are drained at once.
+// tiles that land in accumulator g, so two tiles are drained at once.  This M = pixels
+// form (upconv_tc_kernel) serves inputs under 16 x 16 pixels and Cout of 96 or 128; at
+// Cout = 32 and 64 the transposed form below (upconv_t_kernel) stacks the parities on M
+// so that every MMA is 128 x 256 x 16.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
