@@ -461,7 +461,7 @@ constexpr int TMA_THREADS = 128 * HPT;
 static_assert(3 * HPT * SLOTS * DH * 2 + 512 <= 48 * 1024, "boxes exceed the default dynamic shared memory");
 
 template <bool RP>
-__global__ void __launch_bounds__(TMA_THREADS) attn_tma_kernel(const __grid_constant__ CUtensorMap tmQKV,
+__global__ void __launch_bounds__(TMA_THREADS, 8) attn_tma_kernel(const __grid_constant__ CUtensorMap tmQKV,
                                                               const uint8_t* __restrict__ v_in,
                                                               bf16* __restrict__ o, uint8_t* __restrict__ v_out,
                                                               int Ht, int Wt, int d, int offset, int nwx,
@@ -588,23 +588,18 @@ __global__ void __launch_bounds__(TMA_THREADS) attn_tma_kernel(const __grid_cons
   // every row has a usable key (keymask != 0), so the maxima are finite
   const float sx = RP ? 1.f : sl2;
   const float o0 = -mx0 * sx, o1 = -mx1 * sx;
-  float l0 = 0.f, l1 = 0.f;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       sc[j][c] = ex2_approx(fmaf(sc[j][c], sx, o0));
       sc[j][2 + c] = ex2_approx(fmaf(sc[j][2 + c], sx, o1));
-      l0 += sc[j][c];
-      l1 += sc[j][2 + c];
     }
   }
-  l0 += __shfl_xor_sync(0xffffffffu, l0, 1);
-  l0 += __shfl_xor_sync(0xffffffffu, l0, 2);
-  l1 += __shfl_xor_sync(0xffffffffu, l1, 1);
-  l1 += __shfl_xor_sync(0xffffffffu, l1, 2);
-  // ---- O = P V
-  float oc[4][4];
+  // ---- O = P V, and the row sums of the bf16 P as one more MMA against ones (FP32
+  // accumulation; every column of `ls` holds its row's sum, so no shuffles)
+  float oc[4][4], ls[4] = {0.f, 0.f, 0.f, 0.f};
+  const uint32_t ones = pack_bf16(1.f, 1.f);
 #pragma unroll
   for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
 #pragma unroll
@@ -621,8 +616,9 @@ __global__ void __launch_bounds__(TMA_THREADS) attn_tma_kernel(const __grid_cons
       mma_bf16_16816(oc[2 * nn], pa, vb[0], vb[1]);
       mma_bf16_16816(oc[2 * nn + 1], pa, vb[2], vb[3]);
     }
+    mma_bf16_16816(ls, pa, ones, ones);
   }
-  const float inv0 = 1.f / l0, inv1 = 1.f / l1;
+  const float inv0 = 1.f / ls[0], inv1 = 1.f / ls[2];
   __syncwarp();
   // stage this warp's 16 output rows in its own Q rows, then store 16-byte chunks
 #pragma unroll
