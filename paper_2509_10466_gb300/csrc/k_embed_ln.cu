@@ -109,22 +109,23 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
   }
 }
 
-// Tensor-core form (BF16 form): 64 tokens per CTA.  The patch matrix P [64 tok][64]
-// and the embedding weights [d][64] are staged in shared memory as bf16 (rows padded to
-// 144 bytes for conflict-free ldmatrix); warp w computes tokens 16(w%4).. x channels
-// (w/4)*d/2 .. with mma.sync m16n8k16 (K = 64 in 4 steps, FP32 accumulate).  The tile
-// goes through shared memory so the FP32 token rows, the token mask and the fused
-// LayerNorm are written coalesced.  The LayerNorm statistics (FP32, two passes: mean,
-// then squared deviations) come from the accumulator registers: quad shuffles, then the
-// two column halves of a row through shared memory, so that the store loop has no
-// reductions left.
+// Tensor-core form (BF16 form): 32 tokens per CTA (76 KB of shared memory at d = 256, so
+// three CTAs per SM).  The patch matrix P [32 tok][64] and the embedding weights [d][64]
+// are staged in shared memory as bf16 (rows padded to 144 bytes for conflict-free
+// ldmatrix); warp w computes tokens 16(w%2).. x channels (w/2)*d/4 .. with mma.sync
+// m16n8k16 (K = 64 in 4 steps, FP32 accumulate).  The tile goes through shared memory so
+// the FP32 token rows, the token mask and the fused LayerNorm are written coalesced.  The
+// LayerNorm statistics (FP32, two passes: mean, then squared deviations) come from the
+// accumulator registers: quad shuffles, then the four column parts of a row through
+// shared memory in a fixed order, so that the store loop has no reductions left.
 template <int D>
 struct EmbTc {
-  static constexpr int TOK = 64, KP = 72;          // padded row length (bf16) of P and W
+  static constexpr int TOK = 32, KP = 72;          // tokens per CTA; padded row length (bf16) of P and W
+  static constexpr int MT = TOK / 16, NQ = 8 / MT;  // warps: MT token tiles x NQ column parts
   static constexpr int P_BYTES = TOK * KP * 2;
   static constexpr int W_BYTES = D * KP * 2;
   static constexpr int OUT_STRIDE = D + 4;         // floats per staged output row
-  static constexpr int SMEM = P_BYTES + W_BYTES + TOK * OUT_STRIDE * 4 + TOK * 4 /*known*/ + 4 * TOK * 4 /*row statistics*/;
+  static constexpr int SMEM = P_BYTES + W_BYTES + TOK * OUT_STRIDE * 4 + TOK * 4 /*known*/ + 2 * NQ * TOK * 4 /*row statistics*/;
 };
 
 __device__ __forceinline__ void ldsm_x4_e(uint32_t (&r)[4], const void* p) {
@@ -153,12 +154,12 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
                                                        const float* __restrict__ ln_b, bf16* __restrict__ ln_out) {
   using C = EmbTc<D>;
   extern __shared__ __align__(16) uint8_t esm[];
-  bf16* P = reinterpret_cast<bf16*>(esm);                                   // [64][KP]
+  bf16* P = reinterpret_cast<bf16*>(esm);                                   // [TOK][KP]
   bf16* Ws = reinterpret_cast<bf16*>(esm + C::P_BYTES);                     // [D][KP]
-  float* O = reinterpret_cast<float*>(esm + C::P_BYTES + C::W_BYTES);      // [64][OUT_STRIDE]
+  float* O = reinterpret_cast<float*>(esm + C::P_BYTES + C::W_BYTES);      // [TOK][OUT_STRIDE]
   int* known = reinterpret_cast<int*>(esm + C::P_BYTES + C::W_BYTES + C::TOK * C::OUT_STRIDE * 4);
-  float* red = reinterpret_cast<float*>(known + C::TOK);  // [TOK][2 column halves] row sums
-  float* red2 = red + 2 * C::TOK;                          // [TOK][2] squared deviations
+  float* red = reinterpret_cast<float*>(known + C::TOK);  // [TOK][NQ column parts] row sums
+  float* red2 = red + C::NQ * C::TOK;                      // [TOK][NQ] squared deviations
   const int b = blockIdx.y, t0 = blockIdx.x * C::TOK, Nt = Ht * Wt;
   const size_t HW = (size_t)H * W;
   const int tid = threadIdx.x;
@@ -171,8 +172,8 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
   pdl_trigger();
   pdl_wait();
   __syncthreads();
-  static_assert(C::TOK * 4 == 256, "one thread per (token, pixel row)");
-  {
+  static_assert(C::TOK * 4 <= 256, "one thread per (token, pixel row)");
+  if (tid < C::TOK * 4) {
     // thread -> pixel row pr of token tl; a warp covers 32 neighbouring tokens of one
     // pixel row, so its loads are contiguous 16-byte runs; all loads are independent
     const int tl = tid & (C::TOK - 1), pr = tid / C::TOK;
@@ -220,9 +221,9 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
-  const int m0 = (warp & 3) * 16;
-  constexpr int NT = D / 16;                      // n-tiles of 8 per warp (half of D)
-  const int n0 = (warp >> 2) * (D / 2);
+  const int m0 = (warp % C::MT) * 16;
+  constexpr int NT = D / 8 / C::NQ;               // n-tiles of 8 per warp (D / NQ columns)
+  const int n0 = (warp / C::MT) * (D / C::NQ);
   float acc[NT][4];
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
     }
   }
   // bias; this thread's parts of rows m0 + g and m0 + g + 8 (columns n0 + 8j + 2tq, +1)
-  const int half = warp >> 2;
+  const int half = warp / C::MT;  // this warp's column part
   float sa = 0.f, sb = 0.f;
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
@@ -256,12 +257,18 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
   sb += __shfl_xor_sync(0xffffffffu, sb, 1);
   sb += __shfl_xor_sync(0xffffffffu, sb, 2);
   if (tq == 0) {
-    red[(m0 + g) * 2 + half] = sa;
-    red[(m0 + g + 8) * 2 + half] = sb;
+    red[(m0 + g) * C::NQ + half] = sa;
+    red[(m0 + g + 8) * C::NQ + half] = sb;
   }
   __syncthreads();
-  const float ma = (red[(m0 + g) * 2] + red[(m0 + g) * 2 + 1]) * (1.f / D);
-  const float mb = (red[(m0 + g + 8) * 2] + red[(m0 + g + 8) * 2 + 1]) * (1.f / D);
+  auto part_sum = [&](const float* r, int row) {  // the column parts of a row, in a fixed order
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < C::NQ; ++k) v += r[row * C::NQ + k];
+    return v;
+  };
+  const float ma = part_sum(red, m0 + g) * (1.f / D);
+  const float mb = part_sum(red, m0 + g + 8) * (1.f / D);
   float qa = 0.f, qb = 0.f;
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
@@ -280,20 +287,20 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
   qb += __shfl_xor_sync(0xffffffffu, qb, 1);
   qb += __shfl_xor_sync(0xffffffffu, qb, 2);
   if (tq == 0) {
-    red2[(m0 + g) * 2 + half] = qa;
-    red2[(m0 + g + 8) * 2 + half] = qb;
+    red2[(m0 + g) * C::NQ + half] = qa;
+    red2[(m0 + g + 8) * C::NQ + half] = qb;
   }
   __syncthreads();
   if (tid < C::TOK && t0 + tid < Nt) v0[(size_t)b * Nt + t0 + tid] = (uint8_t)known[tid];
-  // each warp writes 8 token rows and their LayerNorm
+  // each warp writes TOK / 8 token rows and their LayerNorm
 #pragma unroll 2
-  for (int i = 0; i < 8; ++i) {
-    const int tl = warp * 8 + i, t = t0 + tl;
+  for (int i = 0; i < C::TOK / 8; ++i) {
+    const int tl = warp * (C::TOK / 8) + i, t = t0 + tl;
     if (t >= Nt) break;
     const float* orow = O + tl * C::OUT_STRIDE;
     float* trow = tok + ((size_t)b * Nt + t) * D;
-    const float mean = (red[tl * 2] + red[tl * 2 + 1]) * (1.f / D);
-    const float rstd = rsqrtf((red2[tl * 2] + red2[tl * 2 + 1]) * (1.f / D) + 1e-5f);
+    const float mean = part_sum(red, tl) * (1.f / D);
+    const float rstd = rsqrtf(part_sum(red2, tl) * (1.f / D) + 1e-5f);
     bf16* lrow = ln_out + ((size_t)b * Nt + t) * D;
     for (int c = 2 * lane; c < D; c += 64) {  // two channels per lane: 256-byte warp stores
       const float2 v = *reinterpret_cast<const float2*>(orow + c);
