@@ -74,7 +74,8 @@ typedef struct inpaint_config {
   int32_t precision;  /* INPAINT_FP32 (SIMT FP32) or INPAINT_BF16 (tensor cores,
                          FP32 accumulation, softmax statistics and LayerNorms) */
   int32_t shift;      /* 1 = odd blocks use windows offset by half a window  */
-  uint64_t seed;      /* recorded only; weights always come from the caller  */
+  uint64_t seed;      /* seed of the default weights (inpaint_init with NULL
+                         weights, inpaint_default_weights); unused otherwise   */
   size_t hbm_budget_bytes; /* cap on the context's device memory, 0 = none   */
   int32_t mem_slots;  /* temporal memory slots m (0-4).  With m > 0 the odd blocks are
                          temporal: their queries also attend to the keys / values that up
@@ -98,11 +99,26 @@ typedef struct inpaint_ctx inpaint_ctx;
  * head.b [3].  Errors: E_INVAL for a NULL or unsupported config. */
 INPAINT_API int inpaint_num_params(const inpaint_config* cfg, size_t* n_params);
 
+/* The default weight blob of `cfg` for `seed`, written to host_out (host float32, n >=
+ * inpaint_num_params values).  The paper trains its own inpainter and publishes no
+ * weights; the workloads run on random-init weights N(0, 0.02).  Host code only: it
+ * needs no GPU.  Value i of the blob depends on (seed, i) alone (counter-based):
+ *   mix(z): z += 0x9E3779B97F4A7C15; z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9;
+ *           z = (z ^ z >> 27) * 0x94D049BB133111EB; return z ^ z >> 31   (SplitMix64)
+ *   r = mix(mix(seed) + i)                                  (64-bit wrap-around)
+ *   u1 = ((r >> 32) + 0.5) / 2^32,  u2 = ((r & 0xFFFFFFFF) + 0.5) / 2^32
+ *   z = sqrt(-2 ln u1) cos(2 pi u2)   (Box-Muller, double precision)
+ * Matrices, conv kernels and relative-position tables get (float)(0.02 z); LayerNorm
+ * scales 1; biases and LayerNorm shifts 0.  Errors: E_INVAL (config, NULL, n too small). */
+INPAINT_API int inpaint_default_weights(const inpaint_config* cfg, uint64_t seed, float* host_out, size_t n);
+
 /* Create a context on the current CUDA device and upload `weights` (host float32,
- * `n_weights` values in blob order; must equal inpaint_num_params).  The context
- * owns its copy of the weights and a device workspace that grows on demand up to
- * hbm_budget_bytes.  Blocks until the upload is done.  Errors: E_INVAL (config,
- * NULL weights, count mismatch), E_NOMEM, E_CUDA.  *out is NULL on error. */
+ * `n_weights` values in blob order; must equal inpaint_num_params).  With weights =
+ * NULL the context takes the default blob of cfg->seed (inpaint_default_weights;
+ * n_weights 0 or num_params); inpaint_get_weights exports it.  The context owns its
+ * copy of the weights and a device workspace that grows on demand up to
+ * hbm_budget_bytes.  Blocks until the upload is done.  Errors: E_INVAL (config, count
+ * mismatch), E_NOMEM, E_CUDA.  *out is NULL on error. */
 INPAINT_API int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weights,
                  inpaint_ctx** out);
 
@@ -183,13 +199,18 @@ INPAINT_API int inpaint_l1_hole_loss(inpaint_ctx* ctx, const float* out, const f
  * Same arguments, result and fixed-order reduction as inpaint_l1_hole_loss, but no
  * context and no allocation: its scratch (32 KiB of partial sums) is a fixed array in
  * the library's device module, present on every device that loads the library until
- * the process exits.  The first call on a device looks up that array's device address
- * with the device current (cudaGetSymbolAddress), so make the first call on each
- * device before any stream capture.  Every call on a device shares the one array:
+ * the process exits.  Each call looks up that array's device address with the device
+ * current (cudaGetSymbolAddress), so make the first call on each device before any
+ * stream capture.  Under CUDA's lazy module loading that first call on a device also
+ * loads the library's device module, which reserves the 32 KiB there (a driver-side
+ * allocation that may synchronize the device): callers that must not allocate at all
+ * once running make one warm-up call per device at start-up.  Every call on a device
+ * shares the one array:
  * calls that overlap on the GPU (other streams, other host threads) race and must be
  * ordered by the caller; each call rewrites every scratch value it reads, so leftovers
  * of an earlier call never leak into a result.  Returns INPAINT_E_INVAL, launching
- * nothing, when B*H*W exceeds INPAINT_L1_NOALLOC_MAX_PIXELS (4096 x 4096 pixels). */
+ * nothing, when B*H*W exceeds INPAINT_L1_NOALLOC_MAX_PIXELS (4096 x 4096 pixels), and
+ * INPAINT_E_CUDA (with inpaint_last_cuda_error set) when a CUDA call fails. */
 #define INPAINT_L1_NOALLOC_MAX_PIXELS (4096 * 4096)
 INPAINT_API int inpaint_l1_hole_loss_noalloc(const float* out, const float* target,
                                              const uint8_t* hole, int B, int H, int W,
@@ -289,9 +310,18 @@ INPAINT_API const char* inpaint_cuda_error_name(int cuda_error);
 
 /* C[M,N] = A[M,K] . B[K,N] on the BF16 tensor-core GEMM (tcgen05, FP32 accumulate).
  * A: bf16 row-major [M,K]; Bt: bf16 row-major [N,K] (B transposed, K contiguous);
- * C: float32 row-major [M,N].  M % 128 == 0, N % 64 == 0, K % 64 == 0. */
+ * C: float32 row-major [M,N].  M >= 1 (rows of the last 128-row tile past M are read as
+ * zeros and not stored), N % 64 == 0, K % 64 == 0. */
 INPAINT_API int inpaint_test_gemm_bf16(const void* A, const void* Bt, float* C, int M, int N, int K,
                            void* stream);
+
+/* Failure detection on the device, exercised without a fault: one thread waits on an
+ * mbarrier that nothing arrives at, with the same bounded wait the tensor-core kernels
+ * use but a limit of limit_us microseconds (1 to 1000000) instead of their 2 s.  When the
+ * limit passes it writes the device error code of an expired wait into the context's
+ * error word, as those kernels do, and returns; inpaint_sync then reports E_DEVICE and
+ * clears the word.  Errors: E_INVAL, E_CUDA. */
+INPAINT_API int inpaint_test_wait_expiry(inpaint_ctx* ctx, int limit_us, void* stream);
 
 /* The two GELU evaluations of the library on device floats x[n]: y_bf16_form[i] as the
  * BF16 tensor-core epilogues compute it (0.5 x (1 + tanh(x P(x^2))) with a fitted degree-4

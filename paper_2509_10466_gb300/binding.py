@@ -77,6 +77,8 @@ _SIGS = {
     "inpaint_destroy": (None, [_P]),
     "inpaint_test_gemm_bf16": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "inpaint_test_gelu": (_I, [_P, _P, _P, _I, _P]),
+    "inpaint_test_wait_expiry": (_I, [_P, _I, _P]),
+    "inpaint_default_weights": (_I, [ctypes.POINTER(InpaintConfig), ctypes.c_uint64, _P, ctypes.c_size_t]),
 }
 
 
@@ -139,13 +141,27 @@ def inpaint_num_params(cfg: ModelConfig) -> int:
     return n.value
 
 
-def inpaint_init(cfg: ModelConfig, weights: np.ndarray, seed: int = 0, hbm_budget_bytes: int = 0):
-    w = np.ascontiguousarray(weights, dtype=np.float32)
+def inpaint_init(cfg: ModelConfig, weights, seed: int = 0, hbm_budget_bytes: int = 0):
+    """weights: a float32 blob, or None for the library's default blob of `seed`."""
     c = InpaintConfig.from_model(cfg, seed, hbm_budget_bytes)
     ctx = ctypes.c_void_p()
+    if weights is None:
+        _check(load().inpaint_init(ctypes.byref(c), None, 0, ctypes.byref(ctx)), "inpaint_init")
+        return ctx
+    w = np.ascontiguousarray(weights, dtype=np.float32)
     _check(load().inpaint_init(ctypes.byref(c), w.ctypes.data_as(ctypes.c_void_p), w.size, ctypes.byref(ctx)),
            "inpaint_init")
     return ctx
+
+
+def inpaint_default_weights(cfg: ModelConfig, seed: int = 0) -> np.ndarray:
+    """The library's default weight blob of `seed` (host code; no GPU needed)."""
+    n = inpaint_num_params(cfg)
+    out = np.empty(n, np.float32)
+    c = InpaintConfig.from_model(cfg, seed)
+    _check(load().inpaint_default_weights(ctypes.byref(c), seed, out.ctypes.data_as(ctypes.c_void_p), n),
+           "inpaint_default_weights")
+    return out
 
 
 def inpaint_destroy(ctx):
@@ -313,6 +329,10 @@ def inpaint_test_gemm_bf16(A, Bt, C, stream=None):
            "inpaint_test_gemm_bf16")
 
 
+def inpaint_test_wait_expiry(ctx, limit_us: int, stream=None):
+    _check(load().inpaint_test_wait_expiry(ctx, limit_us, _stream(stream)), "inpaint_test_wait_expiry")
+
+
 def inpaint_test_gelu(x, y_bf16_form, y_fp32_form, stream=None):
     _check(load().inpaint_test_gelu(_ptr(x), _ptr(y_bf16_form), _ptr(y_fp32_form), x.numel(), _stream(stream)),
            "inpaint_test_gelu")
@@ -323,10 +343,11 @@ def inpaint_test_gelu(x, y_bf16_form, y_fp32_form, stream=None):
 class Inpainter:
     """Owns one library context; methods take torch CUDA tensors."""
 
-    def __init__(self, cfg: ModelConfig, weights: np.ndarray, hbm_budget_bytes: int = 0):
+    def __init__(self, cfg: ModelConfig, weights, hbm_budget_bytes: int = 0, seed: int = 0):
+        """weights: a float32 blob, or None for the library's default blob of `seed`."""
         self.cfg = cfg
         self.n_params = inpaint_num_params(cfg)
-        self.ctx = inpaint_init(cfg, weights, hbm_budget_bytes=hbm_budget_bytes)
+        self.ctx = inpaint_init(cfg, weights, seed=seed, hbm_budget_bytes=hbm_budget_bytes)
 
     def close(self):
         if self.ctx is not None:

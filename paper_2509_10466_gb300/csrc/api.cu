@@ -1,6 +1,7 @@
 // C ABI and runtime of the inpainting library: context, weight layouts, workspace
 // planning, the forward sequence and event-based per-kernel timing.
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -8,6 +9,7 @@
 
 #include "common.cuh"
 #include "context.cuh"
+#include "tc_primitives.cuh"
 
 namespace inpaint {
 int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* grad_out, int B, int H, int W,
@@ -62,6 +64,57 @@ Offsets make_offsets(const inpaint_config& c) {
   return o;
 }
 
+// Default weights from a seed (inpaint_init with NULL weights, inpaint_default_weights).
+// Counter-based, so value i of the blob depends on (seed, i) only:
+//   r  = mix(mix(seed) + i)   mix = the SplitMix64 output function (Steele, Lea and
+//                             Flood 2014): z += 0x9E3779B97F4A7C15;
+//                             z = (z ^ z>>30) * 0xBF58476D1CE4E5B9;
+//                             z = (z ^ z>>27) * 0x94D049BB133111EB; z ^ z>>31
+//   u1 = (r>>32 + 0.5) / 2^32,  u2 = (r & 0xFFFFFFFF + 0.5) / 2^32
+//   z  = sqrt(-2 ln u1) cos(2 pi u2)                        (Box and Muller 1958, FP64)
+// Matrices, conv kernels and relative-position tables: float(0.02 z); LayerNorm scales 1;
+// biases and LayerNorm shifts 0.
+uint64_t splitmix_out(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void default_weights(const inpaint_config& c, const Offsets& o, uint64_t seed, float* w) {
+  const uint64_t key = splitmix_out(seed);
+  auto normal = [&](size_t at, size_t n) {
+    for (size_t i = at; i < at + n; ++i) {
+      const uint64_t r = splitmix_out(key + (uint64_t)i);
+      const double u1 = ((double)(r >> 32) + 0.5) * (1.0 / 4294967296.0);
+      const double u2 = ((double)(r & 0xFFFFFFFFull) + 0.5) * (1.0 / 4294967296.0);
+      const double z = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+      w[i] = (float)(0.02 * z);
+    }
+  };
+  auto fill = [&](size_t at, size_t n, float v) {
+    for (size_t i = at; i < at + n; ++i) w[i] = v;
+  };
+  const size_t d = c.dim, r = c.mlp_ratio;
+  const size_t c1 = c.dec_c1 ? c.dec_c1 : d / 4, c2 = c.dec_c2 ? c.dec_c2 : d / 8;
+  normal(o.embw, d * 64);
+  fill(o.embb, d, 0.f);
+  for (int l = 0; l < c.blocks; ++l) {
+    const BlockOff& b = o.blk[l];
+    fill(b.ln1g, d, 1.f); fill(b.ln1b, d, 0.f);
+    normal(b.qkvw, d * 3 * d); fill(b.qkvb, 3 * d, 0.f);
+    normal(b.projw, d * d); fill(b.projb, d, 0.f);
+    fill(b.ln2g, d, 1.f); fill(b.ln2b, d, 0.f);
+    normal(b.fc1w, d * r * d); fill(b.fc1b, r * d, 0.f);
+    normal(b.fc2w, r * d * d); fill(b.fc2b, d, 0.f);
+    if (c.pos_bias) normal(b.relpos, (size_t)c.heads * 225);
+  }
+  fill(o.lnfg, d, 1.f); fill(o.lnfb, d, 0.f);
+  normal(o.d1w, c1 * d * 9); fill(o.d1b, c1, 0.f);
+  normal(o.d2w, c2 * c1 * 9); fill(o.d2b, c2, 0.f);
+  normal(o.hw, 3 * c2 * 9); fill(o.hb, 3, 0.f);
+}
+
 // out[n*K + k] = bf16(in[k*N + n])  (linear weight [in=K, out=N] -> K-major B operand)
 // in [K][N] -> out [N][K] bf16, row k of `in` scaled by kscale[k] if given
 __global__ void transpose_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, int K, int N,
@@ -112,6 +165,18 @@ __global__ void transpose_f32(const float* __restrict__ in, float* __restrict__ 
 
 }  // namespace
 
+namespace inpaint {
+
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+int record_cuda_error(cudaError_t e) {
+  if (e == cudaSuccess) return INPAINT_OK;
+  g_last_cuda_error = e;
+  return INPAINT_E_CUDA;
+}
+
+}  // namespace inpaint
+
 namespace {
 
 Plan make_plan(const inpaint_ctx* c, int B, int H, int W) {
@@ -149,13 +214,7 @@ MemLayout mem_layout(const inpaint_ctx* c, int Nt) {
   return m;
 }
 
-thread_local cudaError_t g_last_cuda_error = cudaSuccess;
-
-int cuda_err(cudaError_t e) {
-  if (e == cudaSuccess) return INPAINT_OK;
-  g_last_cuda_error = e;
-  return INPAINT_E_CUDA;
-}
+int cuda_err(cudaError_t e) { return record_cuda_error(e); }
 
 #define TRY(call)                          \
   do {                                     \
@@ -415,6 +474,14 @@ int inpaint_num_params(const inpaint_config* cfg, size_t* n) {
   return INPAINT_OK;
 }
 
+int inpaint_default_weights(const inpaint_config* cfg, uint64_t seed, float* host_out, size_t n) {
+  if (!check_cfg(cfg) || !host_out) return INPAINT_E_INVAL;
+  const Offsets o = make_offsets(*cfg);
+  if (n < o.total) return INPAINT_E_INVAL;
+  default_weights(*cfg, o, seed, host_out);
+  return INPAINT_OK;
+}
+
 void inpaint_destroy(inpaint_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
@@ -445,7 +512,7 @@ void inpaint_destroy(inpaint_ctx* c) {
 int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weights, inpaint_ctx** out) {
   if (!out) return INPAINT_E_INVAL;
   *out = nullptr;
-  if (!check_cfg(cfg) || !weights) return INPAINT_E_INVAL;
+  if (!check_cfg(cfg)) return INPAINT_E_INVAL;
   inpaint_ctx* c = new (std::nothrow) inpaint_ctx();
   if (!c) return INPAINT_E_NOMEM;
   c->cfg = *cfg;
@@ -459,7 +526,21 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
   c->use_bf16 = cfg->precision == INPAINT_BF16;
   c->off = make_offsets(*cfg);
   c->nparams = c->off.total;
-  if (n_weights != c->nparams) {
+  std::vector<float> generated;
+  if (!weights) {  // the documented default blob of cfg->seed
+    if (n_weights != 0 && n_weights != c->nparams) {
+      delete c;
+      return INPAINT_E_INVAL;
+    }
+    try {
+      generated.resize(c->nparams);
+    } catch (...) {
+      delete c;
+      return INPAINT_E_NOMEM;
+    }
+    default_weights(*cfg, c->off, cfg->seed, generated.data());
+    weights = generated.data();
+  } else if (n_weights != c->nparams) {
     delete c;
     return INPAINT_E_INVAL;
   }
@@ -743,6 +824,18 @@ int inpaint_launch_count(inpaint_ctx* c, int64_t* n) {
 }  // extern "C"
 
 namespace {
+// One thread waits on an mbarrier that expects one arrival which never comes (bounded by
+// limit_ns), then reports the expired wait as the tensor-core kernels do.
+__global__ void wait_expiry_kernel(int* err, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  tc::mbar_init(&bar, 1);
+  tc::fence_mbar_init();
+  if (!tc::mbar_wait(&bar, 0, &abort_flag, limit_ns)) atomicExch(err, DEV_MBAR_TIMEOUT);
+}
+
 __global__ void gelu_pair_kernel(const float* __restrict__ x, float* __restrict__ y_bf16_form,
                                  float* __restrict__ y_fp32_form, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -754,6 +847,13 @@ __global__ void gelu_pair_kernel(const float* __restrict__ x, float* __restrict_
 }  // namespace
 
 extern "C" {
+
+int inpaint_test_wait_expiry(inpaint_ctx* c, int limit_us, void* stream) {
+  if (!c || limit_us < 1 || limit_us > 1000000) return INPAINT_E_INVAL;
+  LaunchScope ls(c, (cudaStream_t)stream, K_OTHER);
+  wait_expiry_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(c->dev_err, (uint64_t)limit_us * 1000ull);
+  return cuda_err(cudaGetLastError());
+}
 
 int inpaint_test_gelu(const float* x, float* y_bf16_form, float* y_fp32_form, int n, void* stream) {
   if (!x || !y_bf16_form || !y_fp32_form || n < 0) return INPAINT_E_INVAL;

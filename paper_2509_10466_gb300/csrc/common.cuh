@@ -30,6 +30,10 @@ enum Epi {
   EPI_RESID_LN = 4     // C(f32) = resid + acc + bias, and LayerNorm(C row) -> bf16 (N == tile width)
 };
 
+// INPAINT_OK for cudaSuccess; otherwise records `e` as the calling host thread's last CUDA
+// error (inpaint_last_cuda_error) and returns INPAINT_E_CUDA.
+int record_cuda_error(cudaError_t e);
+
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Programmatic dependent launch.  The forward's kernels are launched with programmatic

@@ -231,11 +231,10 @@ template cudaError_t launch_attention_mem<bf16>(const bf16*, const uint8_t*, bf1
 // ---------------------------------------------------------------------------------
 // Tensor-core form (BF16 operands, FP32 scores / softmax statistics / accumulation).
 //
-// One CTA per (window, head pair, frame), 8 warps; warp w serves head w / 4 and owns query
-// slots 16(w % 4) .. +15.  The slot -> token map and the usable-key bitmask of the window
-// are computed once per CTA.
-// Q, K, V of the window (64 x 32 bf16 each) are staged in shared memory with cp.async
-// (void slots zero-filled) while the key mask is read, then per warp:
+// One CTA per (window, head, frame), 4 warps; warp w owns query slots 16w .. +15.  The
+// slot -> token map and the usable-key bitmask of the window are computed once per CTA.
+// Q, K, V of the window (64 x 32 bf16 each) are staged in shared memory by TMA while the
+// key mask is read, then per warp:
 //   S = Q K^T      16 x 64, 2 k-steps x 8 n-tiles of mma.m16n8k16 (fragments by ldmatrix)
 //   masked softmax over the 64 keys in registers (quad shuffles for row max / sum)
 //   O = P V        16 x 32, P re-packed to bf16 straight from the S accumulators,
@@ -281,169 +280,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-template <bool RP>  // RP: the model has a relative-position bias
-__global__ void __launch_bounds__(TC_THREADS) attn_tc_kernel(const bf16* __restrict__ qkv,
-                                                             const uint8_t* __restrict__ v_in, bf16* __restrict__ o,
-                                                             uint8_t* __restrict__ v_out, int Ht, int Wt, int d,
-                                                             int offset, int nwx, const float* __restrict__ relpos) {
-  // blockIdx.y = head pair: warps 0-3 serve head 2y, warps 4-7 head 2y+1
-  __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
-  __shared__ float rps[RP ? HPC : 1][RP ? 225 : 1];  // relative-position bias of the two heads
-  __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
-  __shared__ __align__(16) bf16 Vs[HPC][SLOTS][ROWB];
-  __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
-  __shared__ unsigned okw[2];
-  const int w = blockIdx.x, b = blockIdx.z;
-  const int wy = w / nwx, wx = w - (w / nwx) * nwx;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int Nt = Ht * Wt;
-
-  if (RP)
-    for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(HPC * blockIdx.y + e / 225) * 225 + e % 225];
-  pdl_trigger();
-  pdl_wait();
-  const int h0 = HPC * blockIdx.y;
-  // slot s of the window -> token row (-1 for a void slot), by arithmetic alone
-  auto slot_token = [&](int sl) {
-    const int ty = wy * WS - offset + (sl >> 3), tx = wx * WS - offset + (sl & 7);
-    return (ty >= 0 && ty < Ht && tx >= 0 && tx < Wt) ? b * Nt + ty * Wt + tx : -1;
-  };
-  // stage Q, K and V of both heads for every real slot (16-byte chunks, zero-filled for void
-  // slots) while the key mask is read: unusable keys are real rows whose scores the softmax
-  // sets to -inf, so their contents never matter
-#pragma unroll
-  for (int part = 0; part < 3; ++part) {
-    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
-      const int sl = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
-      const int t = slot_token(sl);
-      const bf16* src = qkv + (size_t)(t >= 0 ? t : 0) * 3 * d + part * d + (h0 + hh) * DH + ch * 8;
-      bf16* dst = (part == 0 ? &Qs[hh][sl][0] : part == 1 ? &Ks[hh][sl][0] : &Vs[hh][sl][0]) + ch * 8;
-      cp_async16(dst, src, t >= 0);
-    }
-  }
-  if (tid < SLOTS) {
-    const int t = slot_token(tid);
-    stok[tid] = t;
-    const bool ok = t >= 0 && v_in[t] != 0;
-    const unsigned bal = __ballot_sync(0xffffffffu, ok);
-    if (lane == 0) okw[warp] = bal;
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  const unsigned long long keymask = (unsigned long long)okw[0] | ((unsigned long long)okw[1] << 32);
-
-  if (keymask == 0ull) {  // no usable key: the window outputs 0 and stays invalid
-    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
-      const int s = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
-      const int t = stok[s];
-      if (t >= 0) {
-        *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) = make_uint4(0, 0, 0, 0);
-        if (h0 == 0 && hh == 0 && ch == 0) v_out[t] = 0;
-      }
-    }
-    return;
-  }
-  if (h0 == 0 && tid < SLOTS && stok[tid] >= 0) v_out[stok[tid]] = 1;
-
-  const int hh = warp >> 2, wq = warp & 3;
-  const int g = lane >> 2, tq = lane & 3;
-  const int r0 = wq * 16;
-  // ---- S = Q K^T
-  uint32_t qa[2][4];
-  {
-    const int row = r0 + (lane & 15), col = (lane >> 4) * 8;
-    ldsm_x4(qa[0], &Qs[hh][row][col]);
-    ldsm_x4(qa[1], &Qs[hh][row][col + 16]);
-  }
-  float sc[8][4];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    sc[j][0] = sc[j][1] = sc[j][2] = sc[j][3] = 0.f;
-    uint32_t kb[4];  // (k 0-7, 8-15) of k-step 0 and (16-23, 24-31) of k-step 1, keys 8j .. 8j+7
-    ldsm_x4(kb, &Ks[hh][8 * j + (lane & 7)][(lane >> 3) * 8]);
-    mma_bf16_16816(sc[j], qa[0], kb[0], kb[1]);
-    mma_bf16_16816(sc[j], qa[1], kb[2], kb[3]);
-  }
-  // ---- masked softmax (rows g and g+8 of this warp's 16), FP32
-  const float sl2 = 1.4426950408889634f / sqrtf((float)DH);  // scale * log2(e)
-  float mx0 = -INFINITY, mx1 = -INFINITY;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int key = 8 * j + 2 * tq + c;
-      const bool okk = (keymask >> key) & 1ull;
-      const float bb0 = RP ? rps[hh][relpos_index(r0 + g, key)] * LOG2E : 0.f;
-      const float bb1 = RP ? rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
-      sc[j][c] = okk ? (RP ? fmaf(sc[j][c], sl2, bb0) : sc[j][c] * sl2) : -INFINITY;
-      sc[j][2 + c] = okk ? (RP ? fmaf(sc[j][2 + c], sl2, bb1) : sc[j][2 + c] * sl2) : -INFINITY;
-      mx0 = fmaxf(mx0, sc[j][c]);
-      mx1 = fmaxf(mx1, sc[j][2 + c]);
-    }
-  }
-  mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 1));
-  mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, 2));
-  mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 1));
-  mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, 2));
-  float l0 = 0.f, l1 = 0.f;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      sc[j][c] = ex2_approx(sc[j][c] - mx0);
-      sc[j][2 + c] = ex2_approx(sc[j][2 + c] - mx1);
-      l0 += sc[j][c];
-      l1 += sc[j][2 + c];
-    }
-  }
-  l0 += __shfl_xor_sync(0xffffffffu, l0, 1);
-  l0 += __shfl_xor_sync(0xffffffffu, l0, 2);
-  l1 += __shfl_xor_sync(0xffffffffu, l1, 1);
-  l1 += __shfl_xor_sync(0xffffffffu, l1, 2);
-  // ---- O = P V
-  float oc[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {  // keys 16kk .. 16kk+15
-    uint32_t pa[4];
-    pa[0] = pack_bf16(sc[2 * kk][0], sc[2 * kk][1]);
-    pa[1] = pack_bf16(sc[2 * kk][2], sc[2 * kk][3]);
-    pa[2] = pack_bf16(sc[2 * kk + 1][0], sc[2 * kk + 1][1]);
-    pa[3] = pack_bf16(sc[2 * kk + 1][2], sc[2 * kk + 1][3]);
-#pragma unroll
-    for (int nn = 0; nn < 2; ++nn) {  // head dims 16nn .. 16nn+15
-      uint32_t vb[4];
-      ldsm_x4_t(vb, &Vs[hh][16 * kk + (lane & 7) + ((lane >> 3) & 1) * 8][16 * nn + (lane >> 4) * 8]);
-      mma_bf16_16816(oc[2 * nn], pa, vb[0], vb[1]);
-      mma_bf16_16816(oc[2 * nn + 1], pa, vb[2], vb[3]);
-    }
-  }
-  const float inv0 = 1.f / l0, inv1 = 1.f / l1;
-  __syncwarp();
-  // stage this warp's 16 output rows in its own Q rows, then store 16-byte chunks
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g][8 * j + 2 * tq]) = pack_bf16(oc[j][0] * inv0, oc[j][1] * inv0);
-    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g + 8][8 * j + 2 * tq]) = pack_bf16(oc[j][2] * inv1, oc[j][3] * inv1);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int e = lane; e < 16 * 4; e += 32) {
-    const int s = r0 + (e >> 2), ch = e & 3;
-    const int t = stok[s];
-    if (t >= 0)
-      *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) =
-          *reinterpret_cast<const uint4*>(&Qs[hh][s][ch * 8]);
-  }
-}
-
-// The same with Q, K and V staged by TMA: a 4D tensor map views qkv as [B][Ht][Wt][3d],
-// so one box {32 channels, 8 x 8 tokens} is the window's 64 rows of one part (Q, K or
-// V) of one head; void slots of shifted border windows lie outside the map and arrive as
-// zeros.  Three boxes per CTA (one head) replace the per-thread address computations and
-// cp.async.  The
-// boxes land in 64-byte rows with the 64-byte TMA swizzle (16-byte chunk c of slot row r
+// Q, K and V are staged by TMA: a 4D tensor map views qkv as [B][Ht][Wt][3d], so one box
+// {32 channels, 8 x 8 tokens} is the window's 64 rows of one part (Q, K or V) of one
+// head; void slots of shifted border windows lie outside the map and arrive as zeros.
+// The boxes land in 64-byte rows with the 64-byte TMA swizzle (16-byte chunk c of slot row r
 // at c ^ ((r >> 1) & 3)), which the ldmatrix addresses below follow (conflict-free).
 template <bool B>
 struct BoolTag {
@@ -855,23 +695,17 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
 cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht, int Wt,
                                 int d, int heads, int offset, cudaStream_t st, const float* relpos, int* err) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
-  if (heads % HPC) return cudaErrorInvalidValue;
-  dim3 grid(nwy * nwx, heads / HPC, B);
+  // one kernel only: a tensor map that cannot be built (no driver entry point, a
+  // misaligned qkv) is an error, not a reason to run another kernel
   CUtensorMap m;
-  if (heads % HPT == 0 && qkv_map(&m, qkv, B, Ht, Wt, d)) {
-    constexpr int smem = 3 * HPT * SLOTS * DH * 2 + 512;
-    const dim3 tgrid(nwy * nwx, heads / HPT, B);
-    if (relpos)
-      return launch_pdl(attn_tma_kernel<true>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
-                        nwx, relpos, err);
-    return launch_pdl(attn_tma_kernel<false>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
-                      nwx, (const float*)nullptr, err);
-  }
+  if (heads % HPT || !qkv_map(&m, qkv, B, Ht, Wt, d)) return cudaErrorInvalidValue;
+  constexpr int smem = 3 * HPT * SLOTS * DH * 2 + 512;
+  const dim3 tgrid(nwy * nwx, heads / HPT, B);
   if (relpos)
-    return launch_pdl(attn_tc_kernel<true>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
-                      relpos);
-  return launch_pdl(attn_tc_kernel<false>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset, nwx,
-                    (const float*)nullptr);
+    return launch_pdl(attn_tma_kernel<true>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
+                      nwx, relpos, err);
+  return launch_pdl(attn_tma_kernel<false>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
+                    nwx, (const float*)nullptr, err);
 }
 
 cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,

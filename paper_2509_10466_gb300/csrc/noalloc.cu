@@ -26,19 +26,28 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_addr[MAX_DEVICES] = {};
 
-// Device address of g_l1_scratch on the current device (looked up once per device).
-int scratch_address(void** out) {
+// Device address of g_l1_scratch in the current device's context.  It is looked up on
+// every call (a runtime lookup, no allocation), so a context that was destroyed and
+// created again (cudaDeviceReset) never leaves a stale address behind.  While `st` is
+// capturing, the lookup is skipped and the address found by the last call on this device
+// is used.
+int scratch_address(cudaStream_t st, void** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return INPAINT_E_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return record_cuda_error(e);
   if (dev < 0 || dev >= MAX_DEVICES) return INPAINT_E_INVAL;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return record_cuda_error(e);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_l1_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return INPAINT_E_CUDA;
-    }
+    e = cudaGetSymbolAddress(&p, g_l1_scratch);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    if (!p) return INPAINT_E_CUDA;
     g_addr[dev] = p;
+  } else if (!g_addr[dev]) {
+    return INPAINT_E_STATE;  // no call on this device before the capture began
   }
   *out = g_addr[dev];
   return INPAINT_OK;
@@ -55,13 +64,11 @@ extern "C" int inpaint_l1_hole_loss_noalloc(const float* out, const float* targe
   if (!out || !target || !hole || !loss || B < 1 || H < 1 || W < 1) return INPAINT_E_INVAL;
   if ((unsigned long long)B * H * W > (unsigned long long)INPAINT_L1_NOALLOC_MAX_PIXELS) return INPAINT_E_INVAL;
   void* base = nullptr;
-  const int rc = scratch_address(&base);
+  const int rc = scratch_address((cudaStream_t)stream, &base);
   if (rc != INPAINT_OK) return rc;
   float* partials = static_cast<float*>(base);
   unsigned* counts = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(base) + MAX_PARTIALS * sizeof(float));
   // the partial pass writes every slot it later reads, so stale contents never leak in
-  return launch_l1_hole_loss(out, target, hole, B, H, W, partials, counts, loss, grad, (cudaStream_t)stream) ==
-                 cudaSuccess
-             ? INPAINT_OK
-             : INPAINT_E_CUDA;
+  return record_cuda_error(
+      launch_l1_hole_loss(out, target, hole, B, H, W, partials, counts, loss, grad, (cudaStream_t)stream));
 }

@@ -80,6 +80,52 @@ def make_weights(cfg, seed: int = 0, std: float = 0.02, perturb: bool = False) -
     return np.concatenate(parts)
 
 
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+_MIX2 = np.uint64(0x94D049BB133111EB)
+
+
+def _splitmix_out(z):
+    """The SplitMix64 output function (Steele, Lea and Flood 2014) on uint64 values (wrapping)."""
+    z = z + _GOLDEN
+    z = (z ^ (z >> np.uint64(30))) * _MIX1
+    z = (z ^ (z >> np.uint64(27))) * _MIX2
+    return z ^ (z >> np.uint64(31))
+
+
+def counter_normals(seed: int, start: int, n: int) -> np.ndarray:
+    """Standard normals of blob positions start .. start+n-1 from the counter-based stream of
+    ``seed``: r = mix(mix(seed) + i), two 32-bit halves -> uniforms in (0, 1) -> Box-Muller
+    (FP64).  The library's inpaint_default_weights draws the same stream."""
+    with np.errstate(over="ignore"):
+        key = _splitmix_out(np.array([seed], dtype=np.uint64))[0]
+        r = _splitmix_out(key + np.arange(start, start + n, dtype=np.uint64))
+    u1 = ((r >> np.uint64(32)).astype(np.float64) + 0.5) * (1.0 / 4294967296.0)
+    u2 = ((r & np.uint64(0xFFFFFFFF)).astype(np.float64) + 0.5) * (1.0 / 4294967296.0)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(6.283185307179586 * u2)
+
+
+def default_weights(cfg, seed: int = 0, std: float = 0.02) -> np.ndarray:
+    """The default blob of the C library (inpaint_init with NULL weights) in numpy: value i of
+    the blob is drawn from (seed, i) alone; matrices, conv kernels and relative-position
+    tables float32(std * z), LayerNorm scales 1, biases and shifts 0."""
+    parts = []
+    at = 0
+    for name, shape in param_shapes(cfg):
+        n = int(np.prod(shape))
+        leaf = name.rsplit(".", 1)[1]
+        is_ln = ".ln" in name or name.startswith("ln")
+        if leaf in ("w", "relpos"):
+            a = (std * counter_normals(seed, at, n)).astype(np.float32)
+        elif is_ln and leaf == "g":
+            a = np.ones(n, np.float32)
+        else:
+            a = np.zeros(n, np.float32)
+        parts.append(a)
+        at += n
+    return np.concatenate(parts)
+
+
 # ----------------------------------------------------------------------------- frames
 
 def make_frames(batch: int, height: int, width: int, seed: int = 0) -> np.ndarray:

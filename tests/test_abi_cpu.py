@@ -58,3 +58,45 @@ def test_strerror_covers_codes(lib):
     for code in range(7):
         assert binding.strerror(code) and "unknown" not in binding.strerror(code)
     assert "unknown" in binding.strerror(99)
+
+
+@pytest.mark.parametrize("name,seed", [("plain_fp32_256", 0), ("fd_64", 7), ("precision_512", 123456789)])
+def test_default_weights_match_the_documented_generator(lib, name, seed):
+    # the C library's host generator against the numpy restatement of the documented
+    # counter-based stream (SplitMix64 output function, Box-Muller in FP64); libm and
+    # numpy may differ in the last bit of log / cos, so one float32 ulp is allowed
+    import numpy as np
+    cfg = WORKLOADS[name].model
+    c_blob = binding.inpaint_default_weights(cfg, seed)
+    py_blob = S.default_weights(cfg, seed)
+    assert c_blob.shape == py_blob.shape
+    ulp = np.spacing(np.abs(py_blob).astype(np.float32))
+    assert np.all(np.abs(c_blob - py_blob) <= ulp)
+
+
+def test_default_weights_layout_and_distribution(lib):
+    import numpy as np
+    from scipy import stats
+    cfg = ModelConfig(dim=64, heads=2, window=8, blocks=2, mlp_ratio=2, pos_bias=1)
+    w = binding.inpaint_default_weights(cfg, 3)
+    at = 0
+    for nm, shape in S.param_shapes(cfg):
+        n = int(np.prod(shape))
+        a = w[at:at + n]
+        leaf = nm.rsplit(".", 1)[1]
+        if leaf in ("w", "relpos"):
+            assert a.std() > 0
+        elif (".ln" in nm or nm.startswith("ln")) and leaf == "g":
+            assert np.all(a == 1.0)
+        else:
+            assert np.all(a == 0.0)
+        at += n
+    assert at == w.size
+    # the matrices together are N(0, 0.02): Kolmogorov-Smirnov against the normal law
+    mats = np.concatenate([w[o:o + int(np.prod(s))] for o, (nm, s) in
+                           zip(np.cumsum([0] + [int(np.prod(s)) for _, s in S.param_shapes(cfg)])[:-1],
+                               S.param_shapes(cfg)) if nm.endswith(".w")])
+    assert stats.kstest(mats / 0.02, "norm").pvalue > 1e-3
+    # different seeds give different blobs, the same seed the same one
+    assert not np.array_equal(w, binding.inpaint_default_weights(cfg, 4))
+    assert np.array_equal(w, binding.inpaint_default_weights(cfg, 3))

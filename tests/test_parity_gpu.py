@@ -324,3 +324,26 @@ def test_fullres_pre_post_matches_oracle(precision):
     np.testing.assert_array_equal(out[known], x[known])
     errs = hole_rel_l2(out, ref["out"].numpy(), hup)
     assert max(errs) <= (TOL_FP32 if precision == FP32 else TOL_BF16), errs
+
+
+# ----------------------------------------------------------------------------- default weights
+
+@pytest.mark.parametrize("precision", [FP32, BF16])
+def test_context_from_null_weights_runs_the_documented_default_blob(precision):
+    """inpaint_init with NULL weights draws the documented counter-based blob of the
+    config's seed; the exported blob equals the numpy restatement (within one float32
+    ulp) and the forward pass of that context matches the oracle run on the exported blob."""
+    lib()
+    cfg = small(precision, blocks=2, pos_bias=1)
+    inp = binding.Inpainter(cfg, None, seed=77)
+    try:
+        blob = binding.inpaint_get_weights(inp.ctx, inp.n_params)
+        py = S.default_weights(cfg, 77)
+        assert np.all(np.abs(blob - py) <= np.spacing(np.abs(py).astype(np.float32)))
+        x, hole = inputs(2, 64, 96, "polygons", seed=77)
+        out = inp(torch.from_numpy(x).cuda(), torch.from_numpy(hole).cuda())
+        torch.cuda.synchronize()
+        gpu = {"out": out.cpu().numpy(), "masks": inp.token_masks(2, 64, 96)}
+    finally:
+        inp.close()
+    check_parity(cfg, blob, x, hole, TOL_FP32 if precision == FP32 else TOL_BF16, gpu=gpu)

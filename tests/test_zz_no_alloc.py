@@ -49,6 +49,58 @@ def test_noalloc_loss_matches_context_loss_twice_in_a_row():
         inp.close()
 
 
+def _dense_case(B, H, W, seed):
+    # seeded uniform frames and a random 20 % hole, drawn on the device (a full-scratch
+    # case has 16.7 M pixels)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    out = torch.rand(B, 3, H, W, device="cuda", generator=g)
+    tgt = torch.rand(B, 3, H, W, device="cuda", generator=g)
+    hole = (torch.rand(B, H, W, device="cuda", generator=g) < 0.2).to(torch.uint8)
+    return out, tgt, hole
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 4096, 4096), (4, 2048, 2048)])
+def test_noalloc_loss_with_its_scratch_exactly_full(B, H, W):
+    # B * H * W == INPAINT_L1_NOALLOC_MAX_PIXELS: every partial-sum slot is in use
+    assert B * H * W == MAX_PIXELS
+    lib()
+    cfg = ModelConfig(dim=64, heads=2, window=8, blocks=1, mlp_ratio=2)
+    inp = binding.Inpainter(cfg, S.make_weights(cfg))
+    try:
+        out, tgt, hole = _dense_case(B, H, W, seed=B)
+        ref_loss = torch.zeros(1, device="cuda")
+        ref_grad = torch.empty_like(out)
+        binding.inpaint_l1_hole_loss(inp.ctx, out, tgt, hole, ref_loss, ref_grad)
+        loss = torch.full((1,), float("nan"), device="cuda")
+        grad = torch.full_like(out, float("nan"))
+        binding.inpaint_l1_hole_loss_noalloc(out, tgt, hole, loss, grad)
+        torch.cuda.synchronize()
+        assert abs(float(loss) - float(ref_loss)) <= 1e-6 * abs(float(ref_loss))
+        assert torch.equal(grad, ref_grad)
+    finally:
+        inp.close()
+
+
+def test_noalloc_loss_without_gradient_on_a_side_stream():
+    lib()
+    cfg = ModelConfig(dim=64, heads=2, window=8, blocks=1, mlp_ratio=2)
+    inp = binding.Inpainter(cfg, S.make_weights(cfg))
+    try:
+        out, tgt, hole = _case(3, 200, 330, seed=5)
+        ref_loss = torch.zeros(1, device="cuda")
+        binding.inpaint_l1_hole_loss(inp.ctx, out, tgt, hole, ref_loss, None)
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            loss = torch.full((1,), float("nan"), device="cuda")
+            binding.inpaint_l1_hole_loss_noalloc(out, tgt, hole, loss, None, side)
+        side.synchronize()
+        assert abs(float(loss) - float(ref_loss)) <= 1e-6 * abs(float(ref_loss))
+    finally:
+        inp.close()
+
+
 def test_noalloc_loss_rejects_inputs_beyond_its_scratch():
     lib()
     dummy = torch.zeros(1, device="cuda")
