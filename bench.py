@@ -487,6 +487,26 @@ def main():
                 "bf16_speedup": (B / (ms_per_step / 1000.0)) / (B / (ms32 / 1000.0))}
         inp32.close()
 
+    # ---- the FP16 operand form (the paper's engine precision) on the same GPU and workload
+    fp16 = None
+    if not args.no_fp32:
+        from paper_2509_10466_gb300.config import FP16
+        inp16 = binding.Inpainter(cfg.with_precision(FP16), weights)
+        out16 = torch.empty_like(x)
+        for _ in range(3):
+            binding.inpaint_batch(inp16.ctx, x, hole, out16, None, stream)
+        ev16 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev16[k][0].record(stream)
+            binding.inpaint_batch(inp16.ctx, x, hole, out16, None, stream)
+            ev16[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms16 = sum(a.elapsed_time(b) for a, b in ev16) / args.steps
+        fp16 = {"value": B / (ms16 / 1000.0), "unit": UNIT, "ms_per_step": ms16,
+                "note": "same kernels with FP16 instead of BF16 tensor-core operands"}
+        inp16.close()
+
     # ---- roofline of the dominant kernel class (per-launch CUDA events in the timed region)
     from json import load as _jl
     peaks = {}
@@ -638,6 +658,7 @@ def main():
             "latency_ms": {"p50": p50, "p99": p99, "per": f"batch of {B} frames"},
             "ms_per_step_with_launch_events": sum(prof_step_ms) / len(prof_step_ms),
             "fp32_plain": fp32,
+            "fp16": fp16,
             "attn_tflops": attn_tflops,
             "roofline": roofline,
             "kernels": per_kernel,

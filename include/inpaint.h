@@ -32,7 +32,7 @@
  *     context's internal workspace (inpaint_frame/batch/batch_host/backward) must not
  *     overlap on different streams; inpaint_batch_ws takes a caller workspace and may
  *     run concurrently on different streams with different workspaces.
- *   - Requirements: window = 8, patch = 4, dim / heads = 32; dim % 64 == 0 for BF16.
+ *   - Requirements: window = 8, patch = 4, dim / heads = 32; dim % 64 == 0 for BF16 / FP16.
  */
 #ifndef INPAINT_H
 #define INPAINT_H
@@ -60,7 +60,10 @@ enum {
   INPAINT_E_DEVICE = 6    /* a kernel reported an error (e.g. a bounded wait ran out) */
 };
 
-enum { INPAINT_FP32 = 0, INPAINT_BF16 = 1 };
+/* Precision forms: FP32 on the SIMT pipes; BF16 or FP16 operands on the tensor cores
+ * with FP32 accumulation, softmax statistics, LayerNorms and residual stream.  The
+ * paper's engine runs in FP16 ("Inpainting Model", "Hardware"). */
+enum { INPAINT_FP32 = 0, INPAINT_BF16 = 1, INPAINT_FP16 = 2 };
 
 typedef struct inpaint_config {
   int32_t dim;        /* token channels d                                   */
@@ -71,8 +74,9 @@ typedef struct inpaint_config {
   int32_t patch;      /* patch-embedding stride (must be 4)                 */
   int32_t dec_c1;     /* decoder stage-1 channels, 0 = dim / 4              */
   int32_t dec_c2;     /* decoder stage-2 channels, 0 = dim / 8              */
-  int32_t precision;  /* INPAINT_FP32 (SIMT FP32) or INPAINT_BF16 (tensor cores,
-                         FP32 accumulation, softmax statistics and LayerNorms) */
+  int32_t precision;  /* INPAINT_FP32 (SIMT FP32), INPAINT_BF16 or INPAINT_FP16 (16-bit
+                         tensor-core operands, FP32 accumulation, softmax statistics
+                         and LayerNorms) */
   int32_t shift;      /* 1 = odd blocks use windows offset by half a window  */
   uint64_t seed;      /* seed of the default weights (inpaint_init with NULL
                          weights, inpaint_default_weights); unused otherwise   */

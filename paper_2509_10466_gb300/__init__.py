@@ -4,6 +4,6 @@ The compute path is the C-ABI library ``libinpaint.so`` (hand-written sm_103a CU
 ``binding`` marshals arguments into it.  Importing this package does not load the
 library; ``binding.load()`` does and raises if it is missing.
 """
-from .config import ModelConfig, Workload, FP32, BF16, WORKLOADS  # noqa: F401
+from .config import ModelConfig, Workload, FP32, BF16, FP16, WORKLOADS  # noqa: F401
 
-__all__ = ["ModelConfig", "Workload", "FP32", "BF16", "WORKLOADS"]
+__all__ = ["ModelConfig", "Workload", "FP32", "BF16", "FP16", "WORKLOADS"]

@@ -14,6 +14,7 @@ from dataclasses import dataclass, replace
 
 FP32 = 0
 BF16 = 1
+FP16 = 2
 
 
 @dataclass(frozen=True)
@@ -26,7 +27,7 @@ class ModelConfig:
     patch: int = 4          # 4x4 stride-4 patch embedding
     dec_c1: int = 0         # decoder stage-1 channels (0 -> d/4)
     dec_c2: int = 0         # decoder stage-2 channels (0 -> d/8)
-    precision: int = FP32   # FP32 plain form or BF16 tensor-core form
+    precision: int = FP32   # FP32 plain form, or the BF16 / FP16 tensor-core forms
     shift: int = 1          # 1: odd blocks use windows offset by half a window
     mem_slots: int = 0      # m: temporal memory slots (odd blocks attend to m past frames)
     pos_bias: int = 0       # 1: learned relative-position bias (per head, 15 x 15) in the window softmax

@@ -26,9 +26,10 @@ bool check_cfg(const inpaint_config* c) {
   if (!c) return false;
   if (c->window != 8 || c->patch != 4) return false;
   if (c->dim <= 0 || c->dim % 32 || c->heads <= 0 || c->dim != c->heads * 32) return false;
-  if (c->precision == INPAINT_BF16 && c->dim % 64) return false;  // tensor-core tiles are 64 wide
+  if ((c->precision == INPAINT_BF16 || c->precision == INPAINT_FP16) && c->dim % 64)
+    return false;  // tensor-core tiles are 64 wide
   if (c->blocks < 0 || c->blocks > 64 || c->mlp_ratio <= 0 || c->mlp_ratio > 16) return false;
-  if (c->precision != INPAINT_FP32 && c->precision != INPAINT_BF16) return false;
+  if (c->precision != INPAINT_FP32 && c->precision != INPAINT_BF16 && c->precision != INPAINT_FP16) return false;
   const int c1 = c->dec_c1 ? c->dec_c1 : c->dim / 4;
   const int c2 = c->dec_c2 ? c->dec_c2 : c->dim / 8;
   if (c1 <= 0 || c2 <= 0 || c1 % 4 || c2 % 4 || c1 > 4096 || c2 > 1024) return false;
@@ -115,10 +116,11 @@ void default_weights(const inpaint_config& c, const Offsets& o, uint64_t seed, f
   normal(o.hw, 3 * c2 * 9); fill(o.hb, 3, 0.f);
 }
 
-// out[n*K + k] = bf16(in[k*N + n])  (linear weight [in=K, out=N] -> K-major B operand)
-// in [K][N] -> out [N][K] bf16, row k of `in` scaled by kscale[k] if given
-__global__ void transpose_to_bf16(const float* __restrict__ in, bf16* __restrict__ out, int K, int N,
-                                  const float* __restrict__ kscale) {
+// out[n*K + k] = T(in[k*N + n])  (linear weight [in=K, out=N] -> K-major B operand)
+// in [K][N] -> out [N][K] in the 16-bit type T, row k of `in` scaled by kscale[k] if given
+template <typename T>
+__global__ void transpose_to_h16(const float* __restrict__ in, T* __restrict__ out, int K, int N,
+                                 const float* __restrict__ kscale) {
   __shared__ float t[32][33];
   const int k0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
@@ -128,7 +130,7 @@ __global__ void transpose_to_bf16(const float* __restrict__ in, bf16* __restrict
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int n = n0 + i, k = k0 + threadIdx.x;
-    if (n < N && k < K) out[(size_t)n * K + k] = __float2bfloat16_rn(t[threadIdx.x][i]);
+    if (n < N && k < K) out[(size_t)n * K + k] = from_f32<T>(t[threadIdx.x][i]);
   }
 }
 
@@ -188,7 +190,7 @@ Plan make_plan(const inpaint_ctx* c, int B, int H, int W) {
   p.Wt = p.Wp / 4;
   p.Nt = p.Ht * p.Wt;
   p.M = B * p.Nt;
-  const size_t es = c->use_bf16 ? 2 : 4;
+  const size_t es = c->use_tc ? 2 : 4;
   const size_t M = p.M, d = c->d;
   size_t q = 0;
   auto take = [&](size_t bytes) { size_t at = q; q = align_up(q + bytes, 256); return at; };
@@ -206,7 +208,7 @@ Plan make_plan(const inpaint_ctx* c, int B, int H, int W) {
 }
 
 MemLayout mem_layout(const inpaint_ctx* c, int Nt) {
-  const size_t es = c->use_bf16 ? 2 : 4;
+  const size_t es = c->use_tc ? 2 : 4;
   MemLayout m;
   m.kv_bytes = (size_t)Nt * 2 * c->d * es;
   m.stride = align_up(m.kv_bytes + Nt, 256);
@@ -222,85 +224,98 @@ int cuda_err(cudaError_t e) { return record_cuda_error(e); }
     if (rc_ != INPAINT_OK) return rc_;     \
   } while (0)
 
+// Derived weight copies of a 16-bit form (operand type T).
+template <typename T>
+int prepare_layouts_h16(inpaint_ctx* c, cudaStream_t st) {
+  const Offsets& o = c->off;
+  if (c->embed_w16) {
+    // embed.w [d][64] in T = the transpose of the [64][d] FP32 copy
+    transpose_to_h16<T><<<dim3(cdiv(c->d, 32), cdiv(64, 32)), dim3(32, 8), 0, st>>>(
+        c->embed_wt, reinterpret_cast<T*>(c->embed_w16), 64, c->d, nullptr);
+  }
+  if (c->dec1_wp &&
+      launch_subpixel_weights<T>(c->w32 + o.d1w, c->c1, c->d, reinterpret_cast<T*>(c->dec1_wp), st) != cudaSuccess)
+    return INPAINT_E_CUDA;
+  if (c->dec2_wp &&
+      launch_subpixel_weights<T>(c->w32 + o.d2w, c->c2, c->c1, reinterpret_cast<T*>(c->dec2_wp), st) != cudaSuccess)
+    return INPAINT_E_CUDA;
+  if (c->dec1_ws &&
+      launch_stacked_weights<T>(c->w32 + o.d1w, c->c1, c->d, reinterpret_cast<T*>(c->dec1_ws), st) != cudaSuccess)
+    return INPAINT_E_CUDA;
+  if (c->dec2_ws &&
+      launch_stacked_weights<T>(c->w32 + o.d2w, c->c2, c->c1, reinterpret_cast<T*>(c->dec2_ws), st) != cudaSuccess)
+    return INPAINT_E_CUDA;
+  const int d = c->d, h = c->hid;
+  for (int l = 0; l < c->L; ++l) {
+    T* base = reinterpret_cast<T*>(c->lin16) + (size_t)l * c->lin_block_elems;
+    const BlockOff& b = o.blk[l];
+    const float* g1 = c->fold_ln ? c->w32 + b.ln1g : nullptr;
+    const float* g2 = c->fold_ln ? c->w32 + b.ln2g : nullptr;
+    struct { size_t src; int K, N; size_t dst; const float* kscale; } mats[4] = {
+        {b.qkvw, d, 3 * d, 0, g1},
+        {b.projw, d, d, (size_t)3 * d * d, nullptr},
+        {b.fc1w, d, h, (size_t)4 * d * d, g2},
+        {b.fc2w, h, d, (size_t)4 * d * d + (size_t)h * d, nullptr}};
+    for (auto& m : mats) {
+      dim3 grid(cdiv(m.N, 32), cdiv(m.K, 32));
+      transpose_to_h16<T><<<grid, dim3(32, 8), 0, st>>>(c->w32 + m.src, base + m.dst, m.K, m.N, m.kscale);
+    }
+    if (c->fold_ln) {
+      float* fb = c->fold_b + (size_t)l * (3 * d + h);
+      fold_bias_kernel<<<cdiv(3 * d, 128), 128, 0, st>>>(c->w32 + b.qkvw, c->w32 + b.ln1b, c->w32 + b.qkvb, fb, d,
+                                                         3 * d);
+      fold_bias_kernel<<<cdiv(h, 128), 128, 0, st>>>(c->w32 + b.fc1w, c->w32 + b.ln2b, c->w32 + b.fc1b, fb + 3 * d, d,
+                                                     h);
+    }
+  }
+  return INPAINT_OK;
+}
+
 int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
   const Offsets& o = c->off;
   transpose_f32<<<64, 256, 0, st>>>(c->w32 + o.embw, c->embed_wt, c->d, 64);
   conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d1w, c->dec1_wt, c->c1, c->d);
   conv_w_to_tap_major<<<256, 256, 0, st>>>(c->w32 + o.d2w, c->dec2_wt, c->c2, c->c1);
-  if (c->embed_w16) {
-    // embed.w [d][64] as bf16 = the transpose of the [64][d] copy made above
-    transpose_to_bf16<<<dim3(cdiv(c->d, 32), cdiv(64, 32)), dim3(32, 8), 0, st>>>(c->embed_wt, c->embed_w16, 64, c->d,
-                                                                                   nullptr);
-  }
-  if (c->use_bf16 && c->dec1_wp && launch_subpixel_weights(c->w32 + o.d1w, c->c1, c->d, c->dec1_wp, st) != cudaSuccess)
-    return INPAINT_E_CUDA;
-  if (c->use_bf16 && c->dec2_wp && launch_subpixel_weights(c->w32 + o.d2w, c->c2, c->c1, c->dec2_wp, st) != cudaSuccess)
-    return INPAINT_E_CUDA;
-  if (c->use_bf16 && c->dec1_ws && launch_stacked_weights(c->w32 + o.d1w, c->c1, c->d, c->dec1_ws, st) != cudaSuccess)
-    return INPAINT_E_CUDA;
-  if (c->use_bf16 && c->dec2_ws && launch_stacked_weights(c->w32 + o.d2w, c->c2, c->c1, c->dec2_ws, st) != cudaSuccess)
-    return INPAINT_E_CUDA;
-  if (c->use_bf16) {
-    const int d = c->d, h = c->hid;
-    for (int l = 0; l < c->L; ++l) {
-      bf16* base = c->lin_bf16 + (size_t)l * c->lin_block_elems;
-      const BlockOff& b = o.blk[l];
-      const float* g1 = c->fold_ln ? c->w32 + b.ln1g : nullptr;
-      const float* g2 = c->fold_ln ? c->w32 + b.ln2g : nullptr;
-      struct { size_t src; int K, N; size_t dst; const float* kscale; } mats[4] = {
-          {b.qkvw, d, 3 * d, 0, g1},
-          {b.projw, d, d, (size_t)3 * d * d, nullptr},
-          {b.fc1w, d, h, (size_t)4 * d * d, g2},
-          {b.fc2w, h, d, (size_t)4 * d * d + (size_t)h * d, nullptr}};
-      for (auto& m : mats) {
-        dim3 grid(cdiv(m.N, 32), cdiv(m.K, 32));
-        transpose_to_bf16<<<grid, dim3(32, 8), 0, st>>>(c->w32 + m.src, base + m.dst, m.K, m.N, m.kscale);
-      }
-      if (c->fold_ln) {
-        float* fb = c->fold_b + (size_t)l * (3 * d + h);
-        fold_bias_kernel<<<cdiv(3 * d, 128), 128, 0, st>>>(c->w32 + b.qkvw, c->w32 + b.ln1b, c->w32 + b.qkvb, fb, d,
-                                                           3 * d);
-        fold_bias_kernel<<<cdiv(h, 128), 128, 0, st>>>(c->w32 + b.fc1w, c->w32 + b.ln2b, c->w32 + b.fc1b, fb + 3 * d,
-                                                       d, h);
-      }
-    }
-  }
+  if (c->use_tc) TRY(c->fp16 ? prepare_layouts_h16<f16>(c, st) : prepare_layouts_h16<bf16>(c, st));
   return cuda_err(cudaGetLastError());
 }
 
-// The whole forward pass into workspace `ws` laid out by plan `p`.
-int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, const uint8_t* hole, float* out,
-                float* pred, cudaStream_t st, const MemArgs* mem = nullptr) {
+// The whole forward pass into workspace `ws` laid out by plan `p`, with activations of
+// type A: float for the FP32 SIMT form, bf16 or f16 for the 16-bit tensor-core forms.
+template <typename A>
+int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, const uint8_t* hole, float* out,
+                  float* pred, cudaStream_t st, const MemArgs* mem) {
+  constexpr bool TC = sizeof(A) == 2;
   const Offsets& o = c->off;
   const int d = c->d, M = p.M;
   float* tok = reinterpret_cast<float*>(ws + p.tok);
   uint8_t* masks = ws + p.masks;
   int* err = c->dev_err;
-  // BF16 form: the embedding also writes the first LayerNorm (block 0's LN1, or the final
-  // LN when there are no blocks) straight into the bf16 GEMM operand
+  // 16-bit forms: the embedding also writes the first LayerNorm (block 0's LN1, or the
+  // final LN when there are no blocks) straight into the 16-bit GEMM operand
   bool ln_ready = false;
   {
     LaunchScope ls(c, st, K_EMBED);
-    if (c->use_bf16) {
+    if constexpr (TC) {
       // with folding, block 0's LN1 affine lives in its QKV weights: normalized rows only
       const float* g0 = c->fold_ln ? nullptr : c->w32 + (c->L ? o.blk[0].ln1g : o.lnfg);
       const float* b0 = c->fold_ln ? nullptr : c->w32 + (c->L ? o.blk[0].ln1b : o.lnfb);
       if (c->embed_w16)
-        TRY(cuda_err(launch_embed_tc(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_w16, c->w32 + o.embb, d, tok, masks,
-                                     g0, b0, reinterpret_cast<bf16*>(ws + p.ln), st)));
+        TRY(cuda_err(launch_embed_tc<A>(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, reinterpret_cast<const A*>(c->embed_w16),
+                                        c->w32 + o.embb, d, tok, masks, g0, b0, reinterpret_cast<A*>(ws + p.ln), st)));
       else
-        TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st,
-                                  g0, b0, reinterpret_cast<bf16*>(ws + p.ln))));
+        TRY(cuda_err(launch_embed<A>(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks,
+                                     st, g0, b0, reinterpret_cast<A*>(ws + p.ln))));
       ln_ready = true;
     } else {
       TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st)));
     }
   }
-  // BF16 form: the LayerNorm that follows each residual update is fused into the GEMM
+  // 16-bit forms: the LayerNorm that follows each residual update is fused into the GEMM
   // epilogue that produces it (proj -> LN2, fc2 -> next LN1 or the final LN) when a
   // tile spans the whole row; `ln_ready` tracks whether `ln` already holds the input
   // LayerNorm of the next GEMM.
-  const bool fuse_ln = c->use_bf16 && gemm_tc_ln_supported(d);
+  const bool fuse_ln = TC && gemm_tc_ln_supported(d);
   for (int l = 0; l < c->L; ++l) {
     const BlockOff& b = o.blk[l];
     const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
@@ -314,7 +329,7 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     const size_t moff = mem ? (size_t)(l / 2) * mem->lay.stride : 0, mkv = mem ? mem->lay.kv_bytes : 0;
     auto record_memory = [&](const void* qkv_any) -> int {
       if (!mem || !mem->out) return INPAINT_OK;
-      const size_t es = c->use_bf16 ? 2 : 4;
+      const size_t es = sizeof(A);
       const uint8_t* q8 = static_cast<const uint8_t*>(qkv_any);
       for (int b = 0; b < p.B; ++b) {
         uint8_t* dst = mem->out[b];
@@ -328,22 +343,22 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       }
       return INPAINT_OK;
     };
-    if (c->use_bf16) {
-      bf16* ln = reinterpret_cast<bf16*>(ws + p.ln);
-      bf16* qkv = reinterpret_cast<bf16*>(ws + p.qkv);
-      bf16* ao = reinterpret_cast<bf16*>(ws + p.o);
-      bf16* hid = reinterpret_cast<bf16*>(ws + p.hid);
-      const bf16* wl = c->lin_bf16 + (size_t)l * c->lin_block_elems;
-      const bf16* wqkv = wl;
-      const bf16* wproj = wl + (size_t)3 * d * d;
-      const bf16* wfc1 = wl + (size_t)4 * d * d;
-      const bf16* wfc2 = wfc1 + (size_t)c->hid * d;
-      if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
+    if constexpr (TC) {
+      A* ln = reinterpret_cast<A*>(ws + p.ln);
+      A* qkv = reinterpret_cast<A*>(ws + p.qkv);
+      A* ao = reinterpret_cast<A*>(ws + p.o);
+      A* hid = reinterpret_cast<A*>(ws + p.hid);
+      const A* wl = reinterpret_cast<const A*>(c->lin16) + (size_t)l * c->lin_block_elems;
+      const A* wqkv = wl;
+      const A* wproj = wl + (size_t)3 * d * d;
+      const A* wfc1 = wl + (size_t)4 * d * d;
+      const A* wfc2 = wfc1 + (size_t)c->hid * d;
+      if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<A>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
       const float* fold = c->fold_ln ? c->fold_b + (size_t)l * (3 * d + c->hid) : nullptr;
       { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, fold ? fold : c->w32 + b.qkvb, nullptr, err, st))); }
       if (temporal) {
         LaunchScope ls(c, st, K_ATTN);
-        TRY(cuda_err(launch_attention_tc_mem(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st, rp)));
+        TRY(cuda_err(launch_attention_tc_mem<A>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st, rp, err)));
       } else {
         LaunchScope ls(c, st, K_ATTN);
         TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp, err)));
@@ -367,7 +382,7 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
         TRY(cuda_err(launch_gemm_tc_resid_ln(ao, wproj, tok, M, d, d, c->w32 + b.projb, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, err, st)));
       } else {
         { LaunchScope ls(c, st, K_PROJ); TRY(cuda_err(launch_gemm_tc(ao, wproj, tok, d, M, d, d, EPI_BIAS_RESID, c->w32 + b.projb, tok, err, st))); }
-        { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
+        { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<A>(tok, c->w32 + b.ln2g, c->w32 + b.ln2b, ln, M, d, st))); }
       }
       { LaunchScope ls(c, st, K_FC1); TRY(cuda_err(launch_gemm_tc(ln, wfc1, hid, c->hid, M, c->hid, d, EPI_BIAS_GELU, c->w32 + b.fc1b, nullptr, err, st))); }
       if (fuse_ln) {
@@ -403,32 +418,36 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
       { LaunchScope ls(c, st, K_FC2); TRY(cuda_err(launch_gemm_f32(hid, c->hid, c->w32 + b.fc2w, d, tok, d, M, d, c->hid, EPI_BIAS_RESID, c->w32 + b.fc2b, tok, st))); }
     }
   }
-  if (c->use_bf16) {
-    bf16* ln = reinterpret_cast<bf16*>(ws + p.ln);
-    bf16* f1 = reinterpret_cast<bf16*>(ws + p.f1);
-    bf16* f2 = reinterpret_cast<bf16*>(ws + p.f2);
-    if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<bf16>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
+  if constexpr (TC) {
+    A* ln = reinterpret_cast<A*>(ws + p.ln);
+    A* f1 = reinterpret_cast<A*>(ws + p.f1);
+    A* f2 = reinterpret_cast<A*>(ws + p.f2);
+    const A* dec1_ws = reinterpret_cast<const A*>(c->dec1_ws);
+    const A* dec2_ws = reinterpret_cast<const A*>(c->dec2_ws);
+    const A* dec1_wp = reinterpret_cast<const A*>(c->dec1_wp);
+    const A* dec2_wp = reinterpret_cast<const A*>(c->dec2_wp);
+    if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<A>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
     if (c->dec1_ws && upconv_t_supported(d, c->c1, p.Ht, p.Wt)) {
       LaunchScope ls(c, st, K_DEC1);
-      TRY(cuda_err(launch_upconv_t(ln, p.B, p.Ht, p.Wt, d, c->dec1_ws, c->w32 + o.d1b, f1, c->c1, c->dev_err, st)));
+      TRY(cuda_err(launch_upconv_t<A>(ln, p.B, p.Ht, p.Wt, d, dec1_ws, c->w32 + o.d1b, f1, c->c1, c->dev_err, st)));
     } else if (c->dec1_wp && p.Wt >= 16 && p.Ht >= 8) {  // TMA box is 16 x 8 input pixels
       LaunchScope ls(c, st, K_DEC1);
-      TRY(cuda_err(launch_upconv_tc(ln, p.B, p.Ht, p.Wt, d, c->dec1_wp, c->w32 + o.d1b, f1, c->c1, c->dev_err, st)));
+      TRY(cuda_err(launch_upconv_tc<A>(ln, p.B, p.Ht, p.Wt, d, dec1_wp, c->w32 + o.d1b, f1, c->c1, c->dev_err, st)));
     } else {
       LaunchScope ls(c, st, K_DEC1);
-      TRY(cuda_err(launch_upconv<bf16>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st)));
+      TRY(cuda_err(launch_upconv<A>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st)));
     }
     if (c->dec2_ws && upconv_t_supported(c->c1, c->c2, 2 * p.Ht, 2 * p.Wt)) {
       LaunchScope ls(c, st, K_DEC2);
-      TRY(cuda_err(launch_upconv_t(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_ws, c->w32 + o.d2b, f2, c->c2, c->dev_err, st)));
+      TRY(cuda_err(launch_upconv_t<A>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, dec2_ws, c->w32 + o.d2b, f2, c->c2, c->dev_err, st)));
     } else if (c->dec2_wp) {
       LaunchScope ls(c, st, K_DEC2);
-      TRY(cuda_err(launch_upconv_tc(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wp, c->w32 + o.d2b, f2, c->c2, c->dev_err, st)));
+      TRY(cuda_err(launch_upconv_tc<A>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, dec2_wp, c->w32 + o.d2b, f2, c->c2, c->dev_err, st)));
     } else {
       LaunchScope ls(c, st, K_DEC2);
-      TRY(cuda_err(launch_upconv<bf16>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st)));
+      TRY(cuda_err(launch_upconv<A>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st)));
     }
-    { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<bf16>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
+    { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<A>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
   } else {
     float* ln = reinterpret_cast<float*>(ws + p.ln);
     float* f1 = reinterpret_cast<float*>(ws + p.f1);
@@ -439,6 +458,13 @@ int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, cons
     { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<float>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
   }
   return INPAINT_OK;
+}
+
+int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, const uint8_t* hole, float* out,
+                float* pred, cudaStream_t st, const MemArgs* mem = nullptr) {
+  if (!c->use_tc) return run_forward_t<float>(c, ws, p, x, hole, out, pred, st, mem);
+  if (c->fp16) return run_forward_t<f16>(c, ws, p, x, hole, out, pred, st, mem);
+  return run_forward_t<bf16>(c, ws, p, x, hole, out, pred, st, mem);
 }
 
 bool bad_shape(int B, int H, int W) {
@@ -489,7 +515,7 @@ void inpaint_destroy(inpaint_ctx* c) {
   cudaFree(c->embed_wt);
   cudaFree(c->dec1_wt);
   cudaFree(c->dec2_wt);
-  cudaFree(c->lin_bf16);
+  cudaFree(c->lin16);
   cudaFree(c->fold_b);
   cudaFree(c->dec1_wp);
   cudaFree(c->embed_w16);
@@ -523,7 +549,8 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
   c->hid = cfg->dim * cfg->mlp_ratio;
   c->c1 = cfg->dec_c1 ? cfg->dec_c1 : cfg->dim / 4;
   c->c2 = cfg->dec_c2 ? cfg->dec_c2 : cfg->dim / 8;
-  c->use_bf16 = cfg->precision == INPAINT_BF16;
+  c->use_tc = cfg->precision == INPAINT_BF16 || cfg->precision == INPAINT_FP16;
+  c->fp16 = cfg->precision == INPAINT_FP16;
   c->off = make_offsets(*cfg);
   c->nparams = c->off.total;
   std::vector<float> generated;
@@ -546,12 +573,12 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
   }
   const size_t d = c->d, h = c->hid;
   c->lin_block_elems = 4 * d * d + 2 * h * d;
-  c->fold_ln = c->use_bf16 && c->L > 0 && gemm_tc_ln_supported(c->d) && mlp_tc_supported(c->d, c->hid) &&
+  c->fold_ln = c->use_tc && c->L > 0 && gemm_tc_ln_supported(c->d) && mlp_tc_supported(c->d, c->hid) &&
                embed_tc_supported(c->d);
   c->weight_bytes = c->nparams * 4 + 64 * d * 4 + 9 * d * c->c1 * 4 + 9 * (size_t)c->c1 * c->c2 * 4 +
-                    (c->use_bf16 ? (size_t)c->L * c->lin_block_elems * 2 + (size_t)32 * (c->c1 * d + c->c2 * c->c1) + 128 * d : 0) +
+                    (c->use_tc ? (size_t)c->L * c->lin_block_elems * 2 + (size_t)32 * (c->c1 * d + c->c2 * c->c1) + 128 * d : 0) +
                     (c->fold_ln ? (size_t)c->L * (3 * d + h) * 4 : 0) +
-                    (c->use_bf16 ? 2 * (upconv_t_weight_elems(d, c->c1) + upconv_t_weight_elems(c->c1, c->c2)) : 0) +
+                    (c->use_tc ? 2 * (upconv_t_weight_elems(d, c->c1) + upconv_t_weight_elems(c->c1, c->c2)) : 0) +
                     256;
   if (cfg->hbm_budget_bytes && c->weight_bytes > cfg->hbm_budget_bytes) {
     delete c;
@@ -562,16 +589,16 @@ int inpaint_init(const inpaint_config* cfg, const float* weights, size_t n_weigh
             cudaMalloc(&c->dec1_wt, 9 * d * c->c1 * 4) == cudaSuccess &&
             cudaMalloc(&c->dec2_wt, 9 * (size_t)c->c1 * c->c2 * 4) == cudaSuccess &&
             cudaMalloc(&c->dev_err, 256) == cudaSuccess &&
-            (!c->use_bf16 || cudaMalloc(&c->lin_bf16, (size_t)c->L * c->lin_block_elems * 2) == cudaSuccess) &&
+            (!c->use_tc || cudaMalloc(&c->lin16, (size_t)c->L * c->lin_block_elems * 2) == cudaSuccess) &&
             (!c->fold_ln || cudaMalloc(&c->fold_b, (size_t)c->L * (3 * d + h) * 4) == cudaSuccess) &&
-            (!c->use_bf16 || !embed_tc_supported(c->d) || cudaMalloc(&c->embed_w16, 64 * d * 2) == cudaSuccess) &&
-            (!c->use_bf16 || !upconv_tc_supported(c->d, c->c1) ||
+            (!c->use_tc || !embed_tc_supported(c->d) || cudaMalloc(&c->embed_w16, 64 * d * 2) == cudaSuccess) &&
+            (!c->use_tc || !upconv_tc_supported(c->d, c->c1) ||
              cudaMalloc(&c->dec1_wp, (size_t)16 * c->c1 * c->d * 2) == cudaSuccess) &&
-            (!c->use_bf16 || !upconv_tc_supported(c->c1, c->c2) ||
+            (!c->use_tc || !upconv_tc_supported(c->c1, c->c2) ||
              cudaMalloc(&c->dec2_wp, (size_t)16 * c->c2 * c->c1 * 2) == cudaSuccess) &&
-            (!c->use_bf16 || !upconv_t_weight_elems(c->d, c->c1) ||
+            (!c->use_tc || !upconv_t_weight_elems(c->d, c->c1) ||
              cudaMalloc(&c->dec1_ws, upconv_t_weight_elems(c->d, c->c1) * 2) == cudaSuccess) &&
-            (!c->use_bf16 || !upconv_t_weight_elems(c->c1, c->c2) ||
+            (!c->use_tc || !upconv_t_weight_elems(c->c1, c->c2) ||
              cudaMalloc(&c->dec2_ws, upconv_t_weight_elems(c->c1, c->c2) * 2) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -11,6 +12,7 @@
 namespace inpaint {
 
 typedef __nv_bfloat16 bf16;
+typedef __half f16;
 
 // Kernel-class ids for event timing (match INPAINT_PROFILE_CLASSES in inpaint.h).
 enum KClass {
@@ -99,27 +101,79 @@ __device__ __forceinline__ float gelu_as(float x) {
 
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(bf16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(f16 v) { return __half2float(v); }
 template <typename T> __device__ __forceinline__ T from_f32(float v);
 template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
 template <> __device__ __forceinline__ bf16 from_f32<bf16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ f16 from_f32<f16>(float v) { return __float2half_rn(v); }
+
+// The two 16-bit operand types of the tensor-core forms, BF16 (8-bit exponent, 8-bit
+// significand) and FP16 (5-bit exponent, 11-bit significand): a pair of FP32 values packed
+// into one 32-bit word (low half first, round to nearest even) and back, and the operand
+// format code of the kind::f16 tcgen05 instruction descriptor (0 = F16, 1 = BF16).
+template <typename T> struct H16;
+template <> struct H16<bf16> {
+  static constexpr uint32_t kMmaFmt = 1;
+  static __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ float2 unpack2(uint32_t v) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v));
+  }
+};
+template <> struct H16<f16> {
+  static constexpr uint32_t kMmaFmt = 0;
+  static __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ float2 unpack2(uint32_t v) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&v));
+  }
+};
+
+// D(16x8, f32) += A(16x16) . B(16x8) on the warp-level tensor-core instruction, with A and
+// B in 16-bit type T (register fragments of mma.m16n8k16, row.col).
+template <typename T>
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1);
+template <>
+__device__ __forceinline__ void mma16816<bf16>(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+template <>
+__device__ __forceinline__ void mma16816<f16>(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 
 // ---------------------------------------------------------------------------- launchers
 // Every launcher enqueues on `st` and returns the cudaGetLastError() of its launch.
 
 // Patch embedding + token-mask init.  x [B,3,H,W] f32, hole [B,H,W] u8 -> tok f32
 // [B*Ht*Wt, d] (rows in raster token order), v0 u8 [B*Ht*Wt].
-// With ln_out set, also writes LayerNorm(tok; ln_g, ln_b) as bf16 (block 0's LN1).
+// With ln_out set, also writes LayerNorm(tok; ln_g, ln_b) in T (block 0's LN1).  T is the
+// 16-bit type of the tensor-core forms (bf16 or f16); the FP32 form passes no ln_out.
+template <typename T = bf16>
 cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt,
                          const float* we, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st,
-                         const float* ln_g = nullptr, const float* ln_b = nullptr, bf16* ln_out = nullptr);
+                         const float* ln_g = nullptr, const float* ln_b = nullptr, T* ln_out = nullptr);
 
-// Tensor-core form of the patch embedding (BF16 form): bf16 patches and weights
-// (we16 = embed.w as bf16 [d][64]), FP32 accumulation; writes tok, v0 and LN(tok)
+// Tensor-core form of the patch embedding (16-bit forms): patches and weights in T
+// (we16 = embed.w as T [d][64]), FP32 accumulation; writes tok, v0 and LN(tok)
 // (without the affine part when ln_g is null: it is then folded into the next GEMM).
 bool embed_tc_supported(int d);
-cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,
+template <typename T>
+cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const T* we16,
                             const float* be, int d, float* tok, uint8_t* v0, const float* ln_g, const float* ln_b,
-                            bf16* ln_out, cudaStream_t st);
+                            T* ln_out, cudaStream_t st);
 
 // LayerNorm over the last dim (eps 1e-5, biased variance, FP32 statistics).
 template <typename OutT>
@@ -131,28 +185,31 @@ cudaError_t launch_gemm_f32(const float* A, int lda, const float* Bm, int ldb, f
                             int M, int N, int K, int epi, const float* bias, const float* resid,
                             cudaStream_t st);
 
-// BF16 tcgen05 GEMM C[M,N] = epi(A[M,K] . Bt[N,K]^T); A, Bt bf16 K-contiguous.
-// Output: bf16 for EPI_BIAS / EPI_BIAS_GELU, f32 for EPI_BIAS_RESID / EPI_NONE.
-cudaError_t launch_gemm_tc(const bf16* A, const bf16* Bt, void* C, int ldc, int M, int N, int K,
+// 16-bit tcgen05 GEMM C[M,N] = epi(A[M,K] . Bt[N,K]^T); A, Bt in T (bf16 or f16),
+// K-contiguous.  Output: T for EPI_BIAS / EPI_BIAS_GELU, f32 for EPI_BIAS_RESID / EPI_NONE.
+template <typename T>
+cudaError_t launch_gemm_tc(const T* A, const T* Bt, void* C, int ldc, int M, int N, int K,
                            int epi, const float* bias, const float* resid, int* err, cudaStream_t st);
 
-// Residual epilogue that also writes LayerNorm(x) (bf16) of each finished row: X is
+// Residual epilogue that also writes LayerNorm(x) (in T) of each finished row: X is
 // updated in place (X = X + A.Bt^T + bias) and ln_out = LN(X; ln_g, ln_b).  N must be
 // 64, 128 or 256 (one tile spans the row).
 bool gemm_tc_ln_supported(int N);
-cudaError_t launch_gemm_tc_resid_ln(const bf16* A, const bf16* Bt, float* X, int M, int N, int K, const float* bias,
-                                    const float* ln_g, const float* ln_b, bf16* ln_out, int* err, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gemm_tc_resid_ln(const T* A, const T* Bt, float* X, int M, int N, int K, const float* bias,
+                                    const float* ln_g, const float* ln_b, T* ln_out, int* err, cudaStream_t st);
 
 // Fused attention projection + MLP on tcgen05: x1 = X + A Wp + bp, Y = normalized x1
 // (LN2 without its affine part, which is folded into W1t / b1), X = x1 + gelu(Y W1 + b1)
 // W2 + b2 and ln_out = normalized X (times ln_g plus ln_b when they are given), without
-// writing x1, Y or the hidden activations; Wpt [d][d], W1t [hid][d] and W2t [d][hid] bf16
-// (K-major), A [M][d] bf16.  Supported for d in {64, 128, 256} and hid a multiple of 128
-// up to 1024.
+// writing x1, Y or the hidden activations; Wpt [d][d], W1t [hid][d] and W2t [d][hid] in T
+// (K-major), A [M][d] in T (bf16 or f16).  Supported for d in {64, 128, 256} and hid a
+// multiple of 128 up to 1024.
 bool mlp_tc_supported(int d, int hid);
-cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const bf16* W1t, const bf16* W2t,
+template <typename T>
+cudaError_t launch_proj_mlp_tc(const T* A, const T* Wpt, const float* bp, const T* W1t, const T* W2t,
                                const float* b1, const float* b2, float* X, const float* ln_g, const float* ln_b,
-                               bf16* ln_out, int M, int d, int hid, int* err, cudaStream_t st);
+                               T* ln_out, int M, int d, int hid, int* err, cudaStream_t st);
 
 // Mask-aware window attention of all frames; qkv [B*Nt, 3d] (T), v_in/v_out u8 [B*Nt].
 // relpos (optional, device f32 [heads][15][15]): relative-position bias added to the
@@ -161,9 +218,11 @@ template <typename T>
 cudaError_t launch_attention(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
                              int Wt, int d, int heads, int offset, cudaStream_t st, const float* relpos = nullptr);
 
-// Tensor-core form for BF16 activations (mma.sync bf16, FP32 softmax statistics); err
-// (optional) receives DEV_MBAR_TIMEOUT if a window's TMA staging does not complete.
-cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
+// Tensor-core form for 16-bit activations T (bf16 or f16; mma.sync, FP32 softmax
+// statistics); err (optional) receives DEV_MBAR_TIMEOUT if a window's TMA staging does not
+// complete.
+template <typename T>
+cudaError_t launch_attention_tc(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
                                 int Wt, int d, int heads, int offset, cudaStream_t st,
                                 const float* relpos = nullptr, int* err = nullptr);
 
@@ -179,9 +238,11 @@ template <typename T>
 cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
                                  int heads, int offset, const MemTab* tab, int m, size_t off_kv, size_t off_mask,
                                  cudaStream_t st, const float* relpos = nullptr);
-cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
+template <typename T>
+cudaError_t launch_attention_tc_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
                                     int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
-                                    size_t off_mask, cudaStream_t st, const float* relpos = nullptr);
+                                    size_t off_mask, cudaStream_t st, const float* relpos = nullptr,
+                                    int* err = nullptr);
 
 // Coloured point cloud (world x, y, z, r, g, b per pixel; NaN coordinates where the depth
 // is not usable) and z-buffered splat into an Ho x Wo image.  cam / view: fx, fy, cx, cy;
@@ -197,21 +258,25 @@ cudaError_t launch_upconv(const T* in, int B, int Hi, int Wi, int Cin, const flo
                           const float* bias, T* out, int Cout, cudaStream_t st);
 
 // Decoder stage on tcgen05 (sub-pixel implicit GEMM); wp = merged weights from
-// launch_subpixel_weights ([4][Cout][4*Cin] bf16).  Supported when Cin % 64 == 0 and
-// Cout is 32, 64, 96 or 128.
+// launch_subpixel_weights ([4][Cout][4*Cin] in T, bf16 or f16).  Supported when Cin % 64
+// == 0 and Cout is 32, 64, 96 or 128.
 bool upconv_tc_supported(int Cin, int Cout);
-cudaError_t launch_subpixel_weights(const float* w, int Cout, int Cin, bf16* wp, cudaStream_t st);
-cudaError_t launch_upconv_tc(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* wp, const float* bias,
-                             bf16* out, int Cout, int* err, cudaStream_t st);
+template <typename T>
+cudaError_t launch_subpixel_weights(const float* w, int Cout, int Cin, T* wp, cudaStream_t st);
+template <typename T>
+cudaError_t launch_upconv_tc(const T* in, int B, int Hi, int Wi, int Cin, const T* wp, const float* bias,
+                             T* out, int Cout, int* err, cudaStream_t st);
 // The same stage with the parities stacked on the MMA's M side (128 x 256 x 16 MMAs): ws =
-// launch_stacked_weights's [groups][shifts][128][Cin] bf16, upconv_t_weight_elems(Cin,
+// launch_stacked_weights's [groups][shifts][128][Cin] in T, upconv_t_weight_elems(Cin,
 // Cout) elements (0 = unsupported).  Supported when Cin % 64 == 0, Cout is 32 or 64 and
 // the input is at least 16 x 16 pixels.
 bool upconv_t_supported(int Cin, int Cout, int Hi, int Wi);
 size_t upconv_t_weight_elems(int Cin, int Cout);
-cudaError_t launch_stacked_weights(const float* w, int Cout, int Cin, bf16* ws, cudaStream_t st);
-cudaError_t launch_upconv_t(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* ws, const float* bias,
-                            bf16* out, int Cout, int* err, cudaStream_t st);
+template <typename T>
+cudaError_t launch_stacked_weights(const float* w, int Cout, int Cin, T* ws, cudaStream_t st);
+template <typename T>
+cudaError_t launch_upconv_t(const T* in, int B, int Hi, int Wi, int Cin, const T* ws, const float* bias,
+                            T* out, int Cout, int* err, cudaStream_t st);
 
 // Generic FP32 3x3 conv (NHWC), optional x2 upsampling of the input, optional bias
 // (NULL = none), act 0 = identity / 1 = GELU, optional pre-activation output.

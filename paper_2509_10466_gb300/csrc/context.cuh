@@ -55,25 +55,27 @@ struct EventPair {
 struct inpaint_ctx {
   inpaint_config cfg;
   int d, heads, L, r, c1, c2, hid;
-  bool use_bf16;
+  bool use_tc;  // a 16-bit tensor-core form (BF16 or FP16); else the FP32 SIMT form
+  bool fp16;    // the 16-bit operand type is FP16 (else BF16)
   Offsets off;
   size_t nparams;
   float* w32 = nullptr;        // float32 blob (device)
   float* embed_wt = nullptr;   // [64][d]
   float* dec1_wt = nullptr;    // [9][d][c1]
   float* dec2_wt = nullptr;    // [9][c1][c2]
-  inpaint::bf16* lin_bf16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
+  // Derived weight copies of the 16-bit forms, in the operand type (bf16 or f16 bits):
+  uint16_t* lin16 = nullptr;    // per block: qkv^T [3d][d], proj^T [d][d], fc1^T [rd][d], fc2^T [d][rd]
   // BF16 form with the fused projection + MLP: the affine part of LN1 and LN2 is folded
-  // into the QKV and fc1 weights (lin_bf16) and biases (fold_b, per block qkv [3d] then
+  // into the QKV and fc1 weights (lin16) and biases (fold_b, per block qkv [3d] then
   // fc1 [rd]); the LayerNorm producers then write the normalized rows only
   bool fold_ln = false;
   float* fold_b = nullptr;
   size_t lin_block_elems = 0;
-  inpaint::bf16* embed_w16 = nullptr;  // BF16 form: embed.w as bf16 [d][64]
-  inpaint::bf16* dec1_wp = nullptr;  // BF16 form: merged sub-pixel weights [4][c1][4d]
-  inpaint::bf16* dec2_wp = nullptr;  // [4][c2][4c1]
-  inpaint::bf16* dec1_ws = nullptr;  // BF16 form: parity-stacked sub-pixel weights (transposed stage)
-  inpaint::bf16* dec2_ws = nullptr;
+  uint16_t* embed_w16 = nullptr;  // embed.w [d][64]
+  uint16_t* dec1_wp = nullptr;    // merged sub-pixel weights [4][c1][4d]
+  uint16_t* dec2_wp = nullptr;    // [4][c2][4c1]
+  uint16_t* dec1_ws = nullptr;    // parity-stacked sub-pixel weights (transposed stage)
+  uint16_t* dec2_ws = nullptr;
   size_t weight_bytes = 0;
   int* dev_err = nullptr;
   uint8_t* arena = nullptr;

@@ -206,6 +206,8 @@ template cudaError_t launch_attention<float>(const float*, const uint8_t*, float
                                              int, cudaStream_t, const float*);
 template cudaError_t launch_attention<bf16>(const bf16*, const uint8_t*, bf16*, uint8_t*, int, int, int, int, int,
                                             int, cudaStream_t, const float*);
+template cudaError_t launch_attention<f16>(const f16*, const uint8_t*, f16*, uint8_t*, int, int, int, int, int, int,
+                                           cudaStream_t, const float*);
 
 template <typename T>
 cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
@@ -225,19 +227,22 @@ template cudaError_t launch_attention_mem<float>(const float*, const uint8_t*, f
                                                  const float*);
 template cudaError_t launch_attention_mem<bf16>(const bf16*, const uint8_t*, bf16*, uint8_t*, int, int, int, int, int,
                                                 int, const MemTab*, int, size_t, size_t, cudaStream_t, const float*);
+template cudaError_t launch_attention_mem<f16>(const f16*, const uint8_t*, f16*, uint8_t*, int, int, int, int, int,
+                                               int, const MemTab*, int, size_t, size_t, cudaStream_t, const float*);
 
 }  // namespace inpaint
 
 // ---------------------------------------------------------------------------------
-// Tensor-core form (BF16 operands, FP32 scores / softmax statistics / accumulation).
+// Tensor-core form (16-bit operands T = bf16 or f16, FP32 scores / softmax statistics /
+// accumulation).
 //
 // One CTA per (window, head, frame), 4 warps; warp w owns query slots 16w .. +15.  The
 // slot -> token map and the usable-key bitmask of the window are computed once per CTA.
-// Q, K, V of the window (64 x 32 bf16 each) are staged in shared memory by TMA while the
+// Q, K, V of the window (64 x 32 values each) are staged in shared memory by TMA while the
 // key mask is read, then per warp:
 //   S = Q K^T      16 x 64, 2 k-steps x 8 n-tiles of mma.m16n8k16 (fragments by ldmatrix)
 //   masked softmax over the 64 keys in registers (quad shuffles for row max / sum)
-//   O = P V        16 x 32, P re-packed to bf16 straight from the S accumulators,
+//   O = P V        16 x 32, P re-packed to T straight from the S accumulators,
 //                  V fragments by ldmatrix.trans; O scaled by 1/rowsum in FP32.
 // The window is small (64x64x32), so the kernel is bound by reading Q, K, V and
 // writing O; many small CTAs per SM keep enough loads in flight.
@@ -247,7 +252,7 @@ namespace {
 constexpr int HPC = 2;            // heads per CTA
 constexpr float LOG2E = 1.4426950408889634f;
 constexpr int TC_THREADS = 128 * HPC;
-constexpr int ROWB = 40;  // bf16 per staged row: 32 + 8 pad (80 B rows, conflict-free ldmatrix)
+constexpr int ROWB = 40;  // 16-bit values per staged row: 32 + 8 pad (80 B rows, conflict-free ldmatrix)
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
@@ -267,17 +272,6 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(a));
-}
-__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&h);
 }
 
 // Q, K and V are staged by TMA: a 4D tensor map views qkv as [B][Ht][Wt][3d], so one box
@@ -300,10 +294,10 @@ constexpr int HPT = 1;
 constexpr int TMA_THREADS = 128 * HPT;
 static_assert(3 * HPT * SLOTS * DH * 2 + 512 <= 48 * 1024, "boxes exceed the default dynamic shared memory");
 
-template <bool RP>
+template <bool RP, typename T>
 __global__ void __launch_bounds__(TMA_THREADS, 8) attn_tma_kernel(const __grid_constant__ CUtensorMap tmQKV,
                                                               const uint8_t* __restrict__ v_in,
-                                                              bf16* __restrict__ o, uint8_t* __restrict__ v_out,
+                                                              T* __restrict__ o, uint8_t* __restrict__ v_out,
                                                               int Ht, int Wt, int d, int offset, int nwx,
                                                               const float* __restrict__ relpos, int* err) {
   extern __shared__ uint8_t asm_raw[];
@@ -388,8 +382,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 8) attn_tma_kernel(const __grid_c
     sc[j][0] = sc[j][1] = sc[j][2] = sc[j][3] = 0.f;
     uint32_t kb[4];  // (k 0-7, 8-15) of k-step 0 and (16-23, 24-31) of k-step 1, keys 8j .. 8j+7
     ldsm_x4(kb, Kt + swz64(8 * j + (lane & 7), lane >> 3));
-    mma_bf16_16816(sc[j], qa[0], kb[0], kb[1]);
-    mma_bf16_16816(sc[j], qa[1], kb[2], kb[3]);
+    mma16816<T>(sc[j], qa[0], kb[0], kb[1]);
+    mma16816<T>(sc[j], qa[1], kb[2], kb[3]);
   }
   // ---- masked softmax (rows g and g+8 of this warp's 16), FP32, base 2.  Without the
   // relative-position bias the maxima are taken on the raw scores (the scale is positive)
@@ -436,35 +430,35 @@ __global__ void __launch_bounds__(TMA_THREADS, 8) attn_tma_kernel(const __grid_c
       sc[j][2 + c] = ex2_approx(fmaf(sc[j][2 + c], sx, o1));
     }
   }
-  // ---- O = P V, and the row sums of the bf16 P as one more MMA against ones (FP32
+  // ---- O = P V, and the row sums of the 16-bit P as one more MMA against ones (FP32
   // accumulation; every column of `ls` holds its row's sum, so no shuffles)
   float oc[4][4], ls[4] = {0.f, 0.f, 0.f, 0.f};
-  const uint32_t ones = pack_bf16(1.f, 1.f);
+  const uint32_t ones = H16<T>::pack2(1.f, 1.f);
 #pragma unroll
   for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {  // keys 16kk .. 16kk+15
     uint32_t pa[4];
-    pa[0] = pack_bf16(sc[2 * kk][0], sc[2 * kk][1]);
-    pa[1] = pack_bf16(sc[2 * kk][2], sc[2 * kk][3]);
-    pa[2] = pack_bf16(sc[2 * kk + 1][0], sc[2 * kk + 1][1]);
-    pa[3] = pack_bf16(sc[2 * kk + 1][2], sc[2 * kk + 1][3]);
+    pa[0] = H16<T>::pack2(sc[2 * kk][0], sc[2 * kk][1]);
+    pa[1] = H16<T>::pack2(sc[2 * kk][2], sc[2 * kk][3]);
+    pa[2] = H16<T>::pack2(sc[2 * kk + 1][0], sc[2 * kk + 1][1]);
+    pa[3] = H16<T>::pack2(sc[2 * kk + 1][2], sc[2 * kk + 1][3]);
 #pragma unroll
     for (int nn = 0; nn < 2; ++nn) {  // head dims 16nn .. 16nn+15
       uint32_t vb[4];
       ldsm_x4_t(vb, Vt + swz64(16 * kk + (lane & 7) + ((lane >> 3) & 1) * 8, 2 * nn + (lane >> 4)));
-      mma_bf16_16816(oc[2 * nn], pa, vb[0], vb[1]);
-      mma_bf16_16816(oc[2 * nn + 1], pa, vb[2], vb[3]);
+      mma16816<T>(oc[2 * nn], pa, vb[0], vb[1]);
+      mma16816<T>(oc[2 * nn + 1], pa, vb[2], vb[3]);
     }
-    mma_bf16_16816(ls, pa, ones, ones);
+    mma16816<T>(ls, pa, ones, ones);
   }
   const float inv0 = 1.f / ls[0], inv1 = 1.f / ls[2];
   __syncwarp();
   // stage this warp's 16 output rows in its own Q rows, then store 16-byte chunks
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g, j) + 4 * tq) = pack_bf16(oc[j][0] * inv0, oc[j][1] * inv0);
-    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g + 8, j) + 4 * tq) = pack_bf16(oc[j][2] * inv1, oc[j][3] * inv1);
+    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g, j) + 4 * tq) = H16<T>::pack2(oc[j][0] * inv0, oc[j][1] * inv0);
+    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g + 8, j) + 4 * tq) = H16<T>::pack2(oc[j][2] * inv1, oc[j][3] * inv1);
   }
   __syncwarp();
 #pragma unroll
@@ -489,8 +483,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// qkv [B][Ht][Wt][3d] bf16 as a 4D map with {32 channels, 8, 8, 1} boxes, 64-byte swizzle
-bool qkv_map(CUtensorMap* m, const bf16* qkv, int B, int Ht, int Wt, int d) {
+// qkv [B][Ht][Wt][3d] (16-bit T) as a 4D map with {32 channels, 8, 8, 1} boxes, 64-byte swizzle
+template <typename T>
+bool qkv_map(CUtensorMap* m, const T* qkv, int B, int Ht, int Wt, int d) {
   auto fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(qkv) & 15)) return false;
   const uint64_t row = (uint64_t)3 * d * 2;
@@ -498,7 +493,7 @@ bool qkv_map(CUtensorMap* m, const bf16* qkv, int B, int Ht, int Wt, int d) {
   cuuint64_t strides[3] = {row, row * Wt, row * Wt * Ht};
   cuuint32_t box[4] = {DH, WS, WS, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(qkv), dims, strides, box, es,
+  return fn(m, tc::tma_dtype<T>(), 4, const_cast<T*>(qkv), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -508,18 +503,18 @@ bool qkv_map(CUtensorMap* m, const bf16* qkv, int B, int Ht, int Wt, int d) {
 // K / V buffers; per block S = Q K^T, the running row maximum is raised, the running sum
 // and O rescaled by 2^(old max - new max), and O += P V.  Blocks without a usable key
 // are skipped.
-template <bool RP>
-__global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __restrict__ qkv,
+template <bool RP, typename T>
+__global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const T* __restrict__ qkv,
                                                                  const uint8_t* __restrict__ v_in,
-                                                                 bf16* __restrict__ o, uint8_t* __restrict__ v_out,
+                                                                 T* __restrict__ o, uint8_t* __restrict__ v_out,
                                                                  int Ht, int Wt, int d, int offset, int nwx,
                                                                  const __grid_constant__ MemTab mem_tab, int m,
                                                                  size_t off_kv, size_t off_mask,
                                                                  const float* __restrict__ relpos) {
-  __shared__ __align__(16) bf16 Qs[HPC][SLOTS][ROWB];
+  __shared__ __align__(16) T Qs[HPC][SLOTS][ROWB];
   __shared__ float rps[RP ? HPC : 1][RP ? 225 : 1];
-  __shared__ __align__(16) bf16 Ks[HPC][SLOTS][ROWB];
-  __shared__ __align__(16) bf16 Vs[HPC][SLOTS][ROWB];
+  __shared__ __align__(16) T Ks[HPC][SLOTS][ROWB];
+  __shared__ __align__(16) T Vs[HPC][SLOTS][ROWB];
   __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
   __shared__ int sidx[SLOTS];       // token index within the frame, -1 for a void slot
   __shared__ unsigned okw[2];
@@ -592,8 +587,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
       const int s = r >> 3, hh2 = (r >> 2) & 1, ch = r & 3;
       const bool valid = ((keymask >> s) & 1ull) != 0;
       const int i = sidx[s] >= 0 ? sidx[s] : 0;
-      const bf16* src = kb == 0 ? qkv + (size_t)(b * Nt + i) * 3 * d + (1 + part) * d
-                                : reinterpret_cast<const bf16*>(base + off_kv) + (size_t)i * 2 * d + part * d;
+      const T* src = kb == 0 ? qkv + (size_t)(b * Nt + i) * 3 * d + (1 + part) * d
+                             : reinterpret_cast<const T*>(base + off_kv) + (size_t)i * 2 * d + part * d;
       cp_async16((part == 0 ? &Ks[hh2][s][0] : &Vs[hh2][s][0]) + ch * 8, src + (h0 + hh2) * DH + ch * 8, valid);
     }
     cp_async_wait_all();
@@ -609,8 +604,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
       sc[j][0] = sc[j][1] = sc[j][2] = sc[j][3] = 0.f;
       uint32_t kbf[4];
       ldsm_x4(kbf, &Ks[hh][8 * j + (lane & 7)][(lane >> 3) * 8]);
-      mma_bf16_16816(sc[j], qa[0], kbf[0], kbf[1]);
-      mma_bf16_16816(sc[j], qa[1], kbf[2], kbf[3]);
+      mma16816<T>(sc[j], qa[0], kbf[0], kbf[1]);
+      mma16816<T>(sc[j], qa[1], kbf[2], kbf[3]);
     }
     float bm0 = -INFINITY, bm1 = -INFINITY;
 #pragma unroll
@@ -655,16 +650,16 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
       uint32_t pa[4];
-      pa[0] = pack_bf16(sc[2 * kk][0], sc[2 * kk][1]);
-      pa[1] = pack_bf16(sc[2 * kk][2], sc[2 * kk][3]);
-      pa[2] = pack_bf16(sc[2 * kk + 1][0], sc[2 * kk + 1][1]);
-      pa[3] = pack_bf16(sc[2 * kk + 1][2], sc[2 * kk + 1][3]);
+      pa[0] = H16<T>::pack2(sc[2 * kk][0], sc[2 * kk][1]);
+      pa[1] = H16<T>::pack2(sc[2 * kk][2], sc[2 * kk][3]);
+      pa[2] = H16<T>::pack2(sc[2 * kk + 1][0], sc[2 * kk + 1][1]);
+      pa[3] = H16<T>::pack2(sc[2 * kk + 1][2], sc[2 * kk + 1][3]);
 #pragma unroll
       for (int nn = 0; nn < 2; ++nn) {
         uint32_t vb[4];
         ldsm_x4_t(vb, &Vs[hh][16 * kk + (lane & 7) + ((lane >> 3) & 1) * 8][16 * nn + (lane >> 4) * 8]);
-        mma_bf16_16816(oc[2 * nn], pa, vb[0], vb[1]);
-        mma_bf16_16816(oc[2 * nn + 1], pa, vb[2], vb[3]);
+        mma16816<T>(oc[2 * nn], pa, vb[0], vb[1]);
+        mma16816<T>(oc[2 * nn + 1], pa, vb[2], vb[3]);
       }
     }
   }
@@ -676,8 +671,8 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g][8 * j + 2 * tq]) = pack_bf16(oc[j][0] * inv0, oc[j][1] * inv0);
-    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g + 8][8 * j + 2 * tq]) = pack_bf16(oc[j][2] * inv1, oc[j][3] * inv1);
+    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g][8 * j + 2 * tq]) = H16<T>::pack2(oc[j][0] * inv0, oc[j][1] * inv0);
+    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g + 8][8 * j + 2 * tq]) = H16<T>::pack2(oc[j][2] * inv1, oc[j][3] * inv1);
   }
   __syncwarp();
 #pragma unroll
@@ -692,35 +687,47 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const bf16* __r
 
 }  // namespace
 
-cudaError_t launch_attention_tc(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht, int Wt,
+template <typename T>
+cudaError_t launch_attention_tc(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt,
                                 int d, int heads, int offset, cudaStream_t st, const float* relpos, int* err) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   // one kernel only: a tensor map that cannot be built (no driver entry point, a
   // misaligned qkv) is an error, not a reason to run another kernel
   CUtensorMap m;
-  if (heads % HPT || !qkv_map(&m, qkv, B, Ht, Wt, d)) return cudaErrorInvalidValue;
+  if (heads % HPT || !qkv_map<T>(&m, qkv, B, Ht, Wt, d)) return cudaErrorInvalidValue;
   constexpr int smem = 3 * HPT * SLOTS * DH * 2 + 512;
   const dim3 tgrid(nwy * nwx, heads / HPT, B);
   if (relpos)
-    return launch_pdl(attn_tma_kernel<true>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
-                      nwx, relpos, err);
-  return launch_pdl(attn_tma_kernel<false>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d, offset,
-                    nwx, (const float*)nullptr, err);
+    return launch_pdl(attn_tma_kernel<true, T>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d,
+                      offset, nwx, relpos, err);
+  return launch_pdl(attn_tma_kernel<false, T>, tgrid, dim3(TMA_THREADS), smem, st, m, v_in, o, v_out, Ht, Wt, d,
+                    offset, nwx, (const float*)nullptr, err);
 }
 
-cudaError_t launch_attention_tc_mem(const bf16* qkv, const uint8_t* v_in, bf16* o, uint8_t* v_out, int B, int Ht,
-                                    int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
-                                    size_t off_mask, cudaStream_t st, const float* relpos) {
+template <typename T>
+cudaError_t launch_attention_tc_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt,
+                                    int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
+                                    size_t off_mask, cudaStream_t st, const float* relpos, int* err) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
   if (heads % HPC) return cudaErrorInvalidValue;
   if (tab && (size_t)B * m > (size_t)MEM_TAB_MAX) return cudaErrorInvalidValue;
   static const MemTab none{};
   dim3 grid(nwy * nwx, heads / HPC, B);
   if (relpos)
-    return launch_pdl(attn_tc_mem_kernel<true>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset,
-                      nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, relpos);
-  return launch_pdl(attn_tc_mem_kernel<false>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d, offset,
-                    nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, (const float*)nullptr);
+    return launch_pdl(attn_tc_mem_kernel<true, T>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d,
+                      offset, nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, relpos);
+  return launch_pdl(attn_tc_mem_kernel<false, T>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d,
+                    offset, nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, (const float*)nullptr);
 }
+
+#define INSTANTIATE(T)                                                                                              \
+  template cudaError_t launch_attention_tc<T>(const T*, const uint8_t*, T*, uint8_t*, int, int, int, int, int, int,  \
+                                              cudaStream_t, const float*, int*);                                    \
+  template cudaError_t launch_attention_tc_mem<T>(const T*, const uint8_t*, T*, uint8_t*, int, int, int, int, int,   \
+                                                  int, const MemTab*, int, size_t, size_t, cudaStream_t,            \
+                                                  const float*, int*);
+INSTANTIATE(bf16)
+INSTANTIATE(f16)
+#undef INSTANTIATE
 
 }  // namespace inpaint

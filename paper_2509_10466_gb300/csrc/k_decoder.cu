@@ -145,11 +145,12 @@ __global__ void __launch_bounds__(256) head_composite_kernel(const T* __restrict
   }
 }
 
-// Tiled form for bf16 activations: a CTA computes 16 x 32 output pixels of one frame
+// Tiled form for 16-bit activations (T = bf16 or f16): a CTA computes 16 x 32 output pixels of one frame
 // from an 18 x 34 x C halo tile staged in shared memory with 16-byte loads (chunk
 // index XOR-swizzled by pixel so that neighbouring threads hit different banks).
 // Requires C % 8 == 0.
-__global__ void __launch_bounds__(256) head_tile_kernel(const bf16* __restrict__ in, int Hp, int Wp, int C,
+template <typename T>
+__global__ void __launch_bounds__(256) head_tile_kernel(const T* __restrict__ in, int Hp, int Wp, int C,
                                                         const float* __restrict__ wh, const float* __restrict__ bh,
                                                         const float* __restrict__ x, const uint8_t* __restrict__ hole,
                                                         int H, int W, float* __restrict__ out,
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) head_tile_kernel(const bf16* __restrict__
   constexpr int TY = 16, TX = 32, HY = TY + 2, HX = TX + 2;
   const int nch = C >> 3;
   const int swz = (nch & (nch - 1)) == 0 ? nch - 1 : 0;
-  bf16* tile = reinterpret_cast<bf16*>(hsm);                                   // [HY*HX][C]
+  T* tile = reinterpret_cast<T*>(hsm);                                         // [HY*HX][C]
   float* wsm = reinterpret_cast<float*>(hsm + (size_t)HY * HX * C * 2);        // [9][C][3]
   const int b = blockIdx.z, y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
   for (int e = threadIdx.x; e < 27 * C; e += blockDim.x) {
@@ -185,14 +186,14 @@ __global__ void __launch_bounds__(256) head_tile_kernel(const bf16* __restrict__
     float p0 = bh[0], p1 = bh[1], p2 = bh[2];
     for (int tap = 0; tap < 9; ++tap) {
       const int pix = (ty + tap / 3) * HX + tx + tap % 3;
-      const bf16* src = tile + (size_t)pix * C;
+      const T* src = tile + (size_t)pix * C;
       const float* wr = wsm + tap * C * 3;
       for (int k = 0; k < nch; ++k) {
         const uint4 raw = *reinterpret_cast<const uint4*>(src + 8 * (k ^ (pix & swz)));
-        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
+        const uint32_t h2[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float2 f = __bfloat1622float2(h2[q]);
+          const float2 f = H16<T>::unpack2(h2[q]);
           const float* w0 = wr + 3 * (8 * k + 2 * q);
           p0 = fmaf(w0[0], f.x, p0); p1 = fmaf(w0[1], f.x, p1); p2 = fmaf(w0[2], f.x, p2);
           p0 = fmaf(w0[3], f.y, p0); p1 = fmaf(w0[4], f.y, p1); p2 = fmaf(w0[5], f.y, p2);
@@ -213,11 +214,11 @@ __global__ void __launch_bounds__(256) head_tile_kernel(const bf16* __restrict__
   }
 }
 
-// Tensor-core form of the head for bf16 activations with C % 16 == 0 (C <= 64):
+// Tensor-core form of the head for 16-bit activations with C % 16 == 0 (C <= 64):
 // out(16 x 32 pixel tile) = conv3x3 as an implicit GEMM with M = 16 pixels of a row,
 // K = 9 taps x C channels, N = 8 (3 used) on mma.sync m16n8k16.  The 18 x 34 x C halo
 // tile is staged in shared memory with 16-byte chunks XOR-swizzled by pixel; A fragments
-// come from ldmatrix.  The CTA turns the weights into the bf16 B fragments once, in shared
+// come from ldmatrix.  The CTA turns the weights into the 16-bit B fragments once, in shared
 // memory, from which every warp reads its lane's.  Each warp owns two output rows (4
 // m-tiles); the three predicted channels then go through shared memory (over the halo
 // tile) so that bias, composite and crop run over whole rows with 16-byte accesses.
@@ -227,16 +228,8 @@ __device__ __forceinline__ void ldsm_x4_h(uint32_t (&r)[4], const void* p) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(a));
 }
-__device__ __forceinline__ void mma_16816_h(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int C>
-__global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ in, int Hp, int Wp,
+template <int C, typename T>
+__global__ void __launch_bounds__(256) head_mma_kernel(const T* __restrict__ in, int Hp, int Wp,
                                                        const float* __restrict__ wh, const float* __restrict__ bh,
                                                        const float* __restrict__ x, const uint8_t* __restrict__ hole,
                                                        int H, int W, float* __restrict__ out,
@@ -244,8 +237,8 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
   constexpr int TY = 16, TX = 32, HY = TY + 2, HX = TX + 2, NCH = C / 8, KC = C / 16;
   constexpr int NFRAG = 9 * KC * 2;  // B fragments per lane: (tap, kc, half)
   extern __shared__ __align__(16) uint8_t hsm[];
-  bf16* tile = reinterpret_cast<bf16*>(hsm);  // [HY*HX][C], chunk k of pixel p at 8*(k ^ (p & (NCH-1)))
-  __shared__ uint32_t sfrag[NFRAG][32];  // bf16 pairs, per lane
+  T* tile = reinterpret_cast<T*>(hsm);  // [HY*HX][C], chunk k of pixel p at 8*(k ^ (p & (NCH-1)))
+  __shared__ uint32_t sfrag[NFRAG][32];  // 16-bit pairs, per lane
   // predictions of the tile with the bias added, over the halo tile once the MMAs are done
   float(*spred)[TY][TX] = reinterpret_cast<float(*)[TY][TX]>(hsm);
   static_assert(3 * TY * TX * 4 <= HY * HX * C * 2, "prediction tile exceeds the halo tile");
@@ -258,7 +251,7 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
     const int hy = pix / HX, hx = pix - (pix / HX) * HX;
     const int sy = y0 - 1 + hy, sx = x0 - 1 + hx;
     const bool inside = sy >= 0 && sy < Hp && sx >= 0 && sx < Wp;
-    const bf16* src = in + (((size_t)b * Hp + (inside ? sy : 0)) * Wp + (inside ? sx : 0)) * C + 8 * k;
+    const T* src = in + (((size_t)b * Hp + (inside ? sy : 0)) * Wp + (inside ? sx : 0)) * C + 8 * k;
     const uint32_t dst = static_cast<uint32_t>(
         __cvta_generic_to_shared(tile + (size_t)pix * C + 8 * (k ^ (pix & (NCH - 1)))));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(inside ? 16 : 0)
@@ -272,8 +265,7 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
     const int c0 = kc * 16 + hlf * 8 + 2 * ftq;
     const float w0 = fg < 3 ? __ldg(wh + (fg * C + c0) * 9 + tap) : 0.f;
     const float w1 = fg < 3 ? __ldg(wh + (fg * C + c0 + 1) * 9 + tap) : 0.f;
-    __nv_bfloat162 h2 = __floats2bfloat162_rn(w0, w1);
-    sfrag[f][ln] = *reinterpret_cast<uint32_t*>(&h2);
+    sfrag[f][ln] = H16<T>::pack2(w0, w1);
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
@@ -299,7 +291,7 @@ __global__ void __launch_bounds__(256) head_mma_kernel(const bf16* __restrict__ 
         const int chunk = 2 * kc + (lane >> 4);
         uint32_t a[4];
         ldsm_x4_h(a, tile + (size_t)pix * C + 8 * (chunk ^ (pix & (NCH - 1))));
-        mma_16816_h(acc[mt], a, bw[tap][kc][0], bw[tap][kc][1]);
+        mma16816<T>(acc[mt], a, bw[tap][kc][0], bw[tap][kc][1]);
       }
     }
   }
@@ -370,41 +362,50 @@ template cudaError_t launch_upconv<float>(const float*, int, int, int, int, cons
                                           cudaStream_t);
 template cudaError_t launch_upconv<bf16>(const bf16*, int, int, int, int, const float*, const float*, bf16*, int,
                                          cudaStream_t);
+template cudaError_t launch_upconv<f16>(const f16*, int, int, int, int, const float*, const float*, f16*, int,
+                                        cudaStream_t);
 
 template <typename T>
 cudaError_t launch_head_composite(const T* in, int B, int Hp, int Wp, int C, const float* wh, const float* bh,
                                   const float* x, const uint8_t* hole, int H, int W, float* out, float* pred,
                                   cudaStream_t st) {
-  if (sizeof(T) == 2 && (C == 16 || C == 32 || C == 64)) {
-    const size_t smem = (size_t)18 * 34 * C * 2;
-    static size_t attr = 0;
-    if (C == 64 && smem > attr) {
-      cudaError_t e = cudaFuncSetAttribute(head_mma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr = smem;
+  if constexpr (sizeof(T) == 2) {
+    if (C == 16 || C == 32 || C == 64) {
+      const size_t smem = (size_t)18 * 34 * C * 2;
+      static size_t attr = 0;
+      if (C == 64 && smem > attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(head_mma_kernel<64, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+      }
+      dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
+      // whole-row 16-byte accesses of x, out, pred (and 4-byte of the hole mask) when aligned
+      const int vec = W % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(out) |
+                                      reinterpret_cast<uintptr_t>(pred) | reinterpret_cast<uintptr_t>(hole)) &
+                                     15) == 0;
+      if (C == 16)
+        return launch_pdl(head_mma_kernel<16, T>, grid, dim3(256), smem, st, in, Hp, Wp, wh, bh, x, hole, H, W, out,
+                          pred, vec);
+      if (C == 32)
+        return launch_pdl(head_mma_kernel<32, T>, grid, dim3(256), smem, st, in, Hp, Wp, wh, bh, x, hole, H, W, out,
+                          pred, vec);
+      return launch_pdl(head_mma_kernel<64, T>, grid, dim3(256), smem, st, in, Hp, Wp, wh, bh, x, hole, H, W, out,
+                        pred, vec);
     }
-    dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
-    const bf16* inb = reinterpret_cast<const bf16*>(in);
-    // whole-row 16-byte accesses of x, out, pred (and 4-byte of the hole mask) when aligned
-    const int vec = W % 4 == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(out) |
-                                    reinterpret_cast<uintptr_t>(pred) | reinterpret_cast<uintptr_t>(hole)) &
-                                   15) == 0;
-    if (C == 16) return launch_pdl(head_mma_kernel<16>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred, vec);
-    if (C == 32) return launch_pdl(head_mma_kernel<32>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred, vec);
-    return launch_pdl(head_mma_kernel<64>, grid, dim3(256), smem, st, inb, Hp, Wp, wh, bh, x, hole, H, W, out, pred, vec);
-  }
-  if (sizeof(T) == 2 && C % 8 == 0) {
-    const size_t smem = (size_t)18 * 34 * C * 2 + (size_t)27 * C * 4;
-    static size_t attr = 0;
-    if (smem > attr) {
-      cudaError_t e = cudaFuncSetAttribute(head_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr = smem;
+    if (C % 8 == 0) {
+      const size_t smem = (size_t)18 * 34 * C * 2 + (size_t)27 * C * 4;
+      static size_t attr = 0;
+      if (smem > attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(head_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+      }
+      dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
+      head_tile_kernel<T><<<grid, 256, smem, st>>>(in, Hp, Wp, C, wh, bh, x, hole, H, W, out, pred);
+      return cudaGetLastError();
     }
-    dim3 grid(cdiv(W, 32), cdiv(H, 16), B);
-    head_tile_kernel<<<grid, 256, smem, st>>>(reinterpret_cast<const bf16*>(in), Hp, Wp, C, wh, bh, x, hole, H, W,
-                                             out, pred);
-    return cudaGetLastError();
   }
   dim3 grid(cdiv(W, 16), cdiv(H, 16), B);
   head_composite_kernel<T><<<grid, 256, 27 * C * sizeof(float), st>>>(in, Hp, Wp, C, wh, bh, x, hole, H, W, out,
@@ -417,5 +418,8 @@ template cudaError_t launch_head_composite<float>(const float*, int, int, int, i
 template cudaError_t launch_head_composite<bf16>(const bf16*, int, int, int, int, const float*, const float*,
                                                  const float*, const uint8_t*, int, int, float*, float*,
                                                  cudaStream_t);
+template cudaError_t launch_head_composite<f16>(const f16*, int, int, int, int, const float*, const float*,
+                                                const float*, const uint8_t*, int, int, float*, float*,
+                                                cudaStream_t);
 
 }  // namespace inpaint

@@ -1,6 +1,6 @@
 // Decoder stages on tcgen05 tensor cores (BF16 form):
-//   out = gelu(conv3x3(upsample2(in)) + bias),  in NHWC [B, Hi, Wi, Cin] bf16,
-//   out NHWC [B, 2Hi, 2Wi, Cout] bf16.
+//   out = gelu(conv3x3(upsample2(in)) + bias),  in NHWC [B, Hi, Wi, Cin] in T,
+//   out NHWC [B, 2Hi, 2Wi, Cout] in T (T = bf16 or f16: the 16-bit forms).
 //
 // Nearest x2 upsampling followed by a 3x3 conv is, for each output parity (a, b) of
 // pixel (2i+a, 2j+b), a 2x2 conv on the low-resolution input with merged weights:
@@ -9,10 +9,10 @@
 // M = B*Hi*Wi pixels, N = Cout, K = 4*Cin (2.25x fewer products than 9*Cin).  The A
 // tile of one (tap, 64-channel chunk) is a 4D TMA box {64 ch, 16 cols, 8 rows, 1 frame}
 // of the NHWC input shifted by the tap offset; TMA's out-of-bounds fill supplies the
-// conv's zero padding.  The merged weights are a K-major [4][Cout][4*Cin] bf16 matrix.
+// conv's zero padding.  The merged weights are a K-major [4][Cout][4*Cin] matrix in T.
 //
 // Same persistent warp-specialized structure as the token GEMM: warp 0 TMA, warp 1
-// MMA (M=128, N=Cout), two TMEM accumulators; the epilogue (bias, GELU, bf16, NHWC
+// MMA (M=128, N=Cout), two TMEM accumulators; the epilogue (bias, GELU, 16-bit, NHWC
 // scatter to the parity's pixels) has two groups of 4 warps, group g draining the
 // tiles that land in accumulator g, so two tiles are drained at once.  This M = pixels
 // form (upconv_tc_kernel) serves inputs under 16 x 16 pixels and Cout of 96 or 128; at
@@ -43,9 +43,9 @@ struct DecCfg {
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
 
-template <int COUT>
+template <int COUT, typename T>
 __global__ void __launch_bounds__(THREADS, 1) upconv_tc_kernel(const __grid_constant__ CUtensorMap tmIn,
-                                                               const __grid_constant__ CUtensorMap tmW, bf16* out,
+                                                               const __grid_constant__ CUtensorMap tmW, T* out,
                                                                int B, int Hi, int Wi, int Cin,
                                                                const float* __restrict__ bias, int* err) {
   using Cfg = DecCfg<COUT>;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(THREADS, 1) upconv_tc_kernel(const __grid_cons
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, COUT);
+      constexpr uint32_t idesc = tc::idesc_f32acc(H16<T>::kMmaFmt, BM, COUT);
       uint32_t g = 0, i = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++i) {
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(THREADS, 1) upconv_tc_kernel(const __grid_cons
       const int pi = i0 + r / TW, pj = j0 + r % TW;
       const bool valid = pi < Hi && pj < Wi;
       const int oy = 2 * pi + (p >> 1), ox = 2 * pj + (p & 1);
-      bf16* dst = out + (((size_t)img * Ho + oy) * Wo + ox) * COUT;
+      T* dst = out + (((size_t)img * Ho + oy) * Wo + ox) * COUT;
       const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * Cfg::ACC_STRIDE;
 #pragma unroll 1
       for (int c0 = 0; c0 < COUT; c0 += 32) {
@@ -189,8 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1) upconv_tc_kernel(const __grid_cons
           for (int k = 0; k < 16; ++k) {
             const float x0 = gelu_as(__uint_as_float(v[2 * k]) + __ldg(bias + c0 + 2 * k));
             const float x1 = gelu_as(__uint_as_float(v[2 * k + 1]) + __ldg(bias + c0 + 2 * k + 1));
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-            packed[k] = *reinterpret_cast<uint32_t*>(&h2);
+            packed[k] = H16<T>::pack2(x0, x1);
           }
           uint4* d4 = reinterpret_cast<uint4*>(dst + c0);
 #pragma unroll
@@ -212,9 +211,10 @@ __global__ void __launch_bounds__(THREADS, 1) upconv_tc_kernel(const __grid_cons
   }
 }
 
-// Merged sub-pixel weights: wp[p][co][tap*Cin + ci] (bf16), p = a*2 + b, tap = dy*2 + dx,
+// Merged sub-pixel weights: wp[p][co][tap*Cin + ci] (in T), p = a*2 + b, tap = dy*2 + dx,
 // summing the 3x3 taps that land on the same low-resolution input pixel.
-__global__ void subpixel_weights_kernel(const float* __restrict__ w, int Cout, int Cin, bf16* __restrict__ wp) {
+template <typename T>
+__global__ void subpixel_weights_kernel(const float* __restrict__ w, int Cout, int Cin, T* __restrict__ wp) {
   const size_t n = (size_t)4 * Cout * 4 * Cin;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int ci = (int)(e % Cin);
@@ -230,7 +230,7 @@ __global__ void subpixel_weights_kernel(const float* __restrict__ w, int Cout, i
     float s = 0.f;
     for (int ky = ky0; ky <= ky1; ++ky)
       for (int kx = kx0; kx <= kx1; ++kx) s += w[((size_t)co * Cin + ci) * 9 + ky * 3 + kx];
-    wp[e] = __float2bfloat16_rn(s);
+    wp[e] = from_f32<T>(s);
   }
 }
 
@@ -246,7 +246,7 @@ __global__ void subpixel_weights_kernel(const float* __restrict__ w, int Cout, i
 // over the shifts any parity of the group uses (9 at Cout = 32, 6 at Cout = 64), with Ws
 // the parity's merged 2 x 2-tap weight for that shift, or 0 where the parity does not
 // read that shift (stacked_weights_kernel).  Every MMA is 128 x 256 x 16.  The epilogue
-// thread of accumulator row (g, co) turns 32 pixels at a time into bf16 GELU outputs,
+// thread of accumulator row (g, co) turns 32 pixels at a time into 16-bit GELU outputs,
 // transposes them through a 2 KB shared tile (32 pixels x 32 channels) and stores 16-byte
 // channel chunks of each output pixel (2 (i0 + py) + a, 2 (j0 + px) + b).
 constexpr int TQ = 16;            // tile = TQ x TQ input pixels
@@ -276,10 +276,11 @@ __device__ __forceinline__ void group_shift(int ng, int grp, int s, int& sy, int
   else { sy = s / 3 + grp - 1; sx = s % 3 - 1; }
 }
 
-// ws[(grp * NSH + s) * 128 + g * Cout + co][ci] (bf16): the sum of the 3x3 taps (ky, kx)
+// ws[(grp * NSH + s) * 128 + g * Cout + co][ci] (in T): the sum of the 3x3 taps (ky, kx)
 // of w[co][ci][ky][kx] whose inputs land on shift s for parity g of group grp, 0 where the
 // parity does not read that shift.
-__global__ void stacked_weights_kernel(const float* __restrict__ w, int Cout, int Cin, bf16* __restrict__ ws) {
+template <typename T>
+__global__ void stacked_weights_kernel(const float* __restrict__ w, int Cout, int Cin, T* __restrict__ ws) {
   const int ng = 128 / Cout, nsh = ng == 4 ? 9 : 6, groups = 4 / ng;
   const size_t n = (size_t)groups * nsh * 128 * Cin;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -295,13 +296,13 @@ __global__ void stacked_weights_kernel(const float* __restrict__ w, int Cout, in
     for (int ky = 0; ky < 3; ++ky)
       for (int kx = 0; kx < 3; ++kx)
         if (tap_offset(a, ky) == sy && tap_offset(b, kx) == sx) acc += w[((size_t)co * Cin + ci) * 9 + ky * 3 + kx];
-    ws[e] = __float2bfloat16_rn(acc);
+    ws[e] = from_f32<T>(acc);
   }
 }
 
-template <int COUT>
+template <int COUT, typename T>
 __global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_constant__ CUtensorMap tmIn,
-                                                                const __grid_constant__ CUtensorMap tmW, bf16* out,
+                                                                const __grid_constant__ CUtensorMap tmW, T* out,
                                                                 int B, int Hi, int Wi, int Cin,
                                                                 const float* __restrict__ bias, int* err) {
   using Cfg = DecTCfg<COUT>;
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_con
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, TQ * TQ);
+      constexpr uint32_t idesc = tc::idesc_f32acc(H16<T>::kMmaFmt, 128, TQ * TQ);
       uint32_t g = 0, i = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++i) {
@@ -447,10 +448,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_con
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
         }
-        // pixel c + k of channel co -> tile[k][lane] (bf16)
+        // pixel c + k of channel co -> tile[k][lane] (16-bit)
 #pragma unroll
         for (int k = 0; k < 32; ++k)
-          *reinterpret_cast<bf16*>(tl + k * 64 + lane * 2) = __float2bfloat16_rn(gelu_as(__uint_as_float(v[k]) + bv));
+          *reinterpret_cast<T*>(tl + k * 64 + lane * 2) = from_f32<T>(gelu_as(__uint_as_float(v[k]) + bv));
         __syncwarp();
         // 16-byte chunk ch of pixel k: channels cbase + 8 ch .. +7 of output pixel (2 (i0 + py) + wa, 2 (j0 + px) + wb)
 #pragma unroll
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_con
           const int pi = i0 + py, pj = j0 + px;
           if (pi < Hi && pj < Wi) {
             const uint4 val = *reinterpret_cast<const uint4*>(tl + k * 64 + ch * 16);
-            bf16* dst = out + (((size_t)img * Ho + 2 * pi + wa) * Wo + 2 * pj + wb) * COUT + cbase + ch * 8;
+            T* dst = out + (((size_t)img * Ho + 2 * pi + wa) * Wo + 2 * pj + wb) * COUT + cbase + ch * 8;
             *reinterpret_cast<uint4*>(dst) = val;
           }
         }
@@ -500,13 +501,13 @@ int num_sms() {
   return n;
 }
 
-template <int COUT>
-cudaError_t launch_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* wp, const float* bias, bf16* out,
-                        int* err, cudaStream_t st) {
+template <int COUT, typename T>
+cudaError_t launch_cout(const T* in, int B, int Hi, int Wi, int Cin, const T* wp, const float* bias, T* out, int* err,
+                        cudaStream_t st) {
   using Cfg = DecCfg<COUT>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(upconv_tc_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(upconv_tc_kernel<COUT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -519,7 +520,7 @@ cudaError_t launch_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const bf
     cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)Wi * Cin * 2, (cuuint64_t)Hi * Wi * Cin * 2};
     cuuint32_t box[4] = {BK, TW, TH, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
-    if (fn(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims, strides, box, es,
+    if (fn(&mi, tc::tma_dtype<T>(), 4, const_cast<T*>(in), dims, strides, box, es,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
@@ -529,26 +530,26 @@ cudaError_t launch_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const bf
     cuuint64_t strides[1] = {(cuuint64_t)4 * Cin * 2};
     cuuint32_t box[2] = {BK, COUT};
     cuuint32_t es[2] = {1, 1};
-    if (fn(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(wp), dims, strides, box, es,
+    if (fn(&mw, tc::tma_dtype<T>(), 2, const_cast<T*>(wp), dims, strides, box, es,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   const int tiles = B * ((Hi + TH - 1) / TH) * ((Wi + TW - 1) / TW) * 4;
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  cudaError_t le = launch_pdl(upconv_tc_kernel<COUT>, grid, dim3(THREADS), Cfg::SMEM_BYTES, st, mi, mw, out, B, Hi,
+  cudaError_t le = launch_pdl(upconv_tc_kernel<COUT, T>, grid, dim3(THREADS), Cfg::SMEM_BYTES, st, mi, mw, out, B, Hi,
                               Wi, Cin, bias, err);
   if (le != cudaSuccess) return le;
   return cudaGetLastError();
 }
 
-template <int COUT>
-cudaError_t launch_t_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* ws, const float* bias, bf16* out,
+template <int COUT, typename T>
+cudaError_t launch_t_cout(const T* in, int B, int Hi, int Wi, int Cin, const T* ws, const float* bias, T* out,
                           int* err, cudaStream_t st) {
   using Cfg = DecTCfg<COUT>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(upconv_t_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(upconv_t_kernel<COUT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -561,7 +562,7 @@ cudaError_t launch_t_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const 
     cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)Wi * Cin * 2, (cuuint64_t)Hi * Wi * Cin * 2};
     cuuint32_t box[4] = {BK, TQ, TQ, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
-    if (fn(&mi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims, strides, box, es,
+    if (fn(&mi, tc::tma_dtype<T>(), 4, const_cast<T*>(in), dims, strides, box, es,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
@@ -571,14 +572,14 @@ cudaError_t launch_t_cout(const bf16* in, int B, int Hi, int Wi, int Cin, const 
     cuuint64_t strides[1] = {(cuuint64_t)Cin * 2};
     cuuint32_t box[2] = {BK, 128};
     cuuint32_t es[2] = {1, 1};
-    if (fn(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ws), dims, strides, box, es,
+    if (fn(&mw, tc::tma_dtype<T>(), 2, const_cast<T*>(ws), dims, strides, box, es,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
   const int tiles = B * ((Hi + TQ - 1) / TQ) * ((Wi + TQ - 1) / TQ) * Cfg::GROUPS;
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  cudaError_t le = launch_pdl(upconv_t_kernel<COUT>, grid, dim3(T_THREADS), Cfg::SMEM_BYTES, st, mi, mw, out, B, Hi,
+  cudaError_t le = launch_pdl(upconv_t_kernel<COUT, T>, grid, dim3(T_THREADS), Cfg::SMEM_BYTES, st, mi, mw, out, B, Hi,
                               Wi, Cin, bias, err);
   if (le != cudaSuccess) return le;
   return cudaGetLastError();
@@ -590,20 +591,22 @@ bool upconv_tc_supported(int Cin, int Cout) {
   return Cin % 64 == 0 && (Cout == 32 || Cout == 64 || Cout == 96 || Cout == 128);
 }
 
-cudaError_t launch_subpixel_weights(const float* w, int Cout, int Cin, bf16* wp, cudaStream_t st) {
-  subpixel_weights_kernel<<<256, 256, 0, st>>>(w, Cout, Cin, wp);
+template <typename T>
+cudaError_t launch_subpixel_weights(const float* w, int Cout, int Cin, T* wp, cudaStream_t st) {
+  subpixel_weights_kernel<T><<<256, 256, 0, st>>>(w, Cout, Cin, wp);
   return cudaGetLastError();
 }
 
-cudaError_t launch_upconv_tc(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* wp, const float* bias,
-                             bf16* out, int Cout, int* err, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_upconv_tc(const T* in, int B, int Hi, int Wi, int Cin, const T* wp, const float* bias, T* out,
+                             int Cout, int* err, cudaStream_t st) {
   if (!upconv_tc_supported(Cin, Cout)) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(wp)) & 15) return cudaErrorInvalidValue;
   switch (Cout) {
-    case 32: return launch_cout<32>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
-    case 64: return launch_cout<64>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
-    case 96: return launch_cout<96>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
-    default: return launch_cout<128>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
+    case 32: return launch_cout<32, T>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
+    case 64: return launch_cout<64, T>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
+    case 96: return launch_cout<96, T>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
+    default: return launch_cout<128, T>(in, B, Hi, Wi, Cin, wp, bias, out, err, st);
   }
 }
 
@@ -621,19 +624,32 @@ size_t upconv_t_weight_elems(int Cin, int Cout) {
   return (size_t)(4 / ng) * (ng == 4 ? 9 : 6) * 128 * Cin;
 }
 
-cudaError_t launch_stacked_weights(const float* w, int Cout, int Cin, bf16* ws, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_stacked_weights(const float* w, int Cout, int Cin, T* ws, cudaStream_t st) {
   if (!upconv_t_weight_elems(Cin, Cout)) return cudaErrorInvalidValue;
-  stacked_weights_kernel<<<256, 256, 0, st>>>(w, Cout, Cin, ws);
+  stacked_weights_kernel<T><<<256, 256, 0, st>>>(w, Cout, Cin, ws);
   return cudaGetLastError();
 }
 
-cudaError_t launch_upconv_t(const bf16* in, int B, int Hi, int Wi, int Cin, const bf16* ws, const float* bias,
-                            bf16* out, int Cout, int* err, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_upconv_t(const T* in, int B, int Hi, int Wi, int Cin, const T* ws, const float* bias, T* out,
+                            int Cout, int* err, cudaStream_t st) {
   if (!upconv_t_supported(Cin, Cout, Hi, Wi)) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(ws) | reinterpret_cast<uintptr_t>(out)) & 15)
     return cudaErrorInvalidValue;
-  if (Cout == 32) return launch_t_cout<32>(in, B, Hi, Wi, Cin, ws, bias, out, err, st);
-  return launch_t_cout<64>(in, B, Hi, Wi, Cin, ws, bias, out, err, st);
+  if (Cout == 32) return launch_t_cout<32, T>(in, B, Hi, Wi, Cin, ws, bias, out, err, st);
+  return launch_t_cout<64, T>(in, B, Hi, Wi, Cin, ws, bias, out, err, st);
 }
+
+#define INSTANTIATE(T)                                                                                              \
+  template cudaError_t launch_subpixel_weights<T>(const float*, int, int, T*, cudaStream_t);                        \
+  template cudaError_t launch_upconv_tc<T>(const T*, int, int, int, int, const T*, const float*, T*, int, int*,     \
+                                           cudaStream_t);                                                           \
+  template cudaError_t launch_stacked_weights<T>(const float*, int, int, T*, cudaStream_t);                         \
+  template cudaError_t launch_upconv_t<T>(const T*, int, int, int, int, const T*, const float*, T*, int, int*,      \
+                                          cudaStream_t);
+INSTANTIATE(bf16)
+INSTANTIATE(f16)
+#undef INSTANTIATE
 
 }  // namespace inpaint

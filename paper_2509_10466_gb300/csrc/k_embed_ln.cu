@@ -18,13 +18,14 @@ __device__ __forceinline__ float warp_sum(float v);
 // we_t: embedding weights transposed to [64][d] (k = c*16 + i*4 + j), read as float4 from
 // L1.  Lane l owns channels 8l .. 8l+7 (looping in steps of 256 channels), so a token's
 // row is spread over one warp and its LayerNorm is a warp reduction.  With ln_out set,
-// also writes LayerNorm(tok) (FP32 statistics) as bf16.
+// also writes LayerNorm(tok) (FP32 statistics) in the 16-bit type T.
+template <typename T>
 __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole,
                                                     int H, int W, int Ht, int Wt,
                                                     const float* __restrict__ we_t, const float* __restrict__ be,
                                                     int d, float* __restrict__ tok, uint8_t* __restrict__ v0,
                                                     const float* __restrict__ ln_g, const float* __restrict__ ln_b,
-                                                    bf16* __restrict__ ln_out) {
+                                                    T* __restrict__ ln_out) {
   __shared__ float P[64][EMB_TOK + 1];
   __shared__ int known_any[EMB_TOK];
   const int b = blockIdx.y;
@@ -104,14 +105,14 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
       q = fmaf(v, v, q);
     }
     const float rstd = rsqrtf(warp_sum(q) / (float)d + 1e-5f);
-    bf16* orow = ln_out + ((size_t)b * Nt + t) * d;
-    for (int c = lane; c < d; c += 32) orow[c] = __float2bfloat16_rn((row[c] - mean) * rstd * ln_g[c] + ln_b[c]);
+    T* orow = ln_out + ((size_t)b * Nt + t) * d;
+    for (int c = lane; c < d; c += 32) orow[c] = from_f32<T>((row[c] - mean) * rstd * ln_g[c] + ln_b[c]);
   }
 }
 
-// Tensor-core form (BF16 form): 32 tokens per CTA (76 KB of shared memory at d = 256, so
+// Tensor-core form (16-bit forms): 32 tokens per CTA (76 KB of shared memory at d = 256, so
 // three CTAs per SM).  The patch matrix P [32 tok][64] and the embedding weights [d][64]
-// are staged in shared memory as bf16 (rows padded to 144 bytes for conflict-free
+// are staged in shared memory in T (rows padded to 144 bytes for conflict-free
 // ldmatrix); warp w computes tokens 16(w%2).. x channels (w/2)*d/4 .. with mma.sync
 // m16n8k16 (K = 64 in 4 steps, FP32 accumulate).  The tile goes through shared memory so
 // the FP32 token rows, the token mask and the fused LayerNorm are written coalesced.  The
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
 // shared memory in a fixed order, so that the store loop has no reductions left.
 template <int D>
 struct EmbTc {
-  static constexpr int TOK = 32, KP = 72;          // tokens per CTA; padded row length (bf16) of P and W
+  static constexpr int TOK = 32, KP = 72;          // tokens per CTA; padded row length (16-bit) of P and W
   static constexpr int MT = TOK / 16, NQ = 8 / MT;  // warps: MT token tiles x NQ column parts
   static constexpr int P_BYTES = TOK * KP * 2;
   static constexpr int W_BYTES = D * KP * 2;
@@ -138,24 +139,16 @@ __device__ __forceinline__ void ldsm_x2_e(uint32_t (&r)[2], const void* p) {
   const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
 }
-__device__ __forceinline__ void mma_16816_e(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole,
-                                                       int H, int W, int Ht, int Wt, const bf16* __restrict__ we16,
+                                                       int H, int W, int Ht, int Wt, const T* __restrict__ we16,
                                                        const float* __restrict__ be, float* __restrict__ tok,
                                                        uint8_t* __restrict__ v0, const float* __restrict__ ln_g,
-                                                       const float* __restrict__ ln_b, bf16* __restrict__ ln_out) {
+                                                       const float* __restrict__ ln_b, T* __restrict__ ln_out) {
   using C = EmbTc<D>;
   extern __shared__ __align__(16) uint8_t esm[];
-  bf16* P = reinterpret_cast<bf16*>(esm);                                   // [TOK][KP]
-  bf16* Ws = reinterpret_cast<bf16*>(esm + C::P_BYTES);                     // [D][KP]
+  T* P = reinterpret_cast<T*>(esm);                                         // [TOK][KP]
+  T* Ws = reinterpret_cast<T*>(esm + C::P_BYTES);                           // [D][KP]
   float* O = reinterpret_cast<float*>(esm + C::P_BYTES + C::W_BYTES);      // [TOK][OUT_STRIDE]
   int* known = reinterpret_cast<int*>(esm + C::P_BYTES + C::W_BYTES + C::TOK * C::OUT_STRIDE * 4);
   float* red = reinterpret_cast<float*>(known + C::TOK);  // [TOK][NQ column parts] row sums
@@ -164,7 +157,7 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
   const size_t HW = (size_t)H * W;
   const int tid = threadIdx.x;
   if (tid < C::TOK) known[tid] = 0;
-  // weights: [D][64] bf16 rows of 128 B -> padded rows
+  // weights: [D][64] 16-bit rows of 128 B -> padded rows
   for (int e = tid; e < D * 8; e += 256) {
     const int n = e >> 3, ch = e & 7;
     *reinterpret_cast<uint4*>(Ws + n * C::KP + ch * 8) = *reinterpret_cast<const uint4*>(we16 + (size_t)n * 64 + ch * 8);
@@ -207,14 +200,14 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
         }
       }
     }
-    bf16* prow = P + tl * C::KP + 4 * pr;
+    T* prow = P + tl * C::KP + 4 * pr;
     bool any = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {  // hole pixels enter as 0 (the mask channel carries them)
-      prow[j] = __float2bfloat16_rn(kn[j] ? rv[j] : 0.f);
-      prow[16 + j] = __float2bfloat16_rn(kn[j] ? gv[j] : 0.f);
-      prow[32 + j] = __float2bfloat16_rn(kn[j] ? bv[j] : 0.f);
-      prow[48 + j] = __float2bfloat16_rn(kn[j] ? 1.f : 0.f);
+      prow[j] = from_f32<T>(kn[j] ? rv[j] : 0.f);
+      prow[16 + j] = from_f32<T>(kn[j] ? gv[j] : 0.f);
+      prow[32 + j] = from_f32<T>(kn[j] ? bv[j] : 0.f);
+      prow[48 + j] = from_f32<T>(kn[j] ? 1.f : 0.f);
       any = any || kn[j];
     }
     if (any) known[tl] = 1;  // every writer stores the same value
@@ -235,7 +228,7 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
     for (int j = 0; j < NT; ++j) {
       uint32_t bb[2];
       ldsm_x2_e(bb, Ws + (n0 + 8 * j + (lane & 7)) * C::KP + ks * 16 + ((lane >> 3) & 1) * 8);
-      mma_16816_e(acc[j], a, bb[0], bb[1]);
+      mma16816<T>(acc[j], a, bb[0], bb[1]);
     }
   }
   // bias; this thread's parts of rows m0 + g and m0 + g + 8 (columns n0 + 8j + 2tq, +1)
@@ -301,7 +294,7 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
     float* trow = tok + ((size_t)b * Nt + t) * D;
     const float mean = part_sum(red, tl) * (1.f / D);
     const float rstd = rsqrtf(part_sum(red2, tl) * (1.f / D) + 1e-5f);
-    bf16* lrow = ln_out + ((size_t)b * Nt + t) * D;
+    T* lrow = ln_out + ((size_t)b * Nt + t) * D;
     for (int c = 2 * lane; c < D; c += 64) {  // two channels per lane: 256-byte warp stores
       const float2 v = *reinterpret_cast<const float2*>(orow + c);
       *reinterpret_cast<float2*>(trow + c) = v;
@@ -310,7 +303,7 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
         y0 = y0 * ln_g[c] + ln_b[c];
         y1 = y1 * ln_g[c + 1] + ln_b[c + 1];
       }
-      *reinterpret_cast<__nv_bfloat162*>(lrow + c) = __floats2bfloat162_rn(y0, y1);
+      *reinterpret_cast<uint32_t*>(lrow + c) = H16<T>::pack2(y0, y1);
     }
   }
 }
@@ -445,40 +438,55 @@ __global__ void l1_grad_kernel(const float* __restrict__ out, const float* __res
 
 }  // namespace
 
+template <typename T>
 cudaError_t launch_embed(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt,
                          const float* we_t, const float* be, int d, float* tok, uint8_t* v0, cudaStream_t st,
-                         const float* ln_g, const float* ln_b, bf16* ln_out) {
+                         const float* ln_g, const float* ln_b, T* ln_out) {
   if (d % 8) return cudaErrorInvalidValue;
   dim3 grid(cdiv(Ht * Wt, EMB_TOK), B);
-  embed_kernel<<<grid, 256, 0, st>>>(x, hole, H, W, Ht, Wt, we_t, be, d, tok, v0, ln_g, ln_b, ln_out);
+  embed_kernel<T><<<grid, 256, 0, st>>>(x, hole, H, W, Ht, Wt, we_t, be, d, tok, v0, ln_g, ln_b, ln_out);
   return cudaGetLastError();
 }
+template cudaError_t launch_embed<bf16>(const float*, const uint8_t*, int, int, int, int, int, const float*,
+                                        const float*, int, float*, uint8_t*, cudaStream_t, const float*,
+                                        const float*, bf16*);
+template cudaError_t launch_embed<f16>(const float*, const uint8_t*, int, int, int, int, int, const float*,
+                                       const float*, int, float*, uint8_t*, cudaStream_t, const float*, const float*,
+                                       f16*);
 
 bool embed_tc_supported(int d) { return d == 64 || d == 128 || d == 256; }
 
-template <int D>
-cudaError_t launch_embed_tc_d(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,
+template <int D, typename T>
+cudaError_t launch_embed_tc_d(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const T* we16,
                               const float* be, float* tok, uint8_t* v0, const float* ln_g, const float* ln_b,
-                              bf16* ln_out, cudaStream_t st) {
+                              T* ln_out, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(embed_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, EmbTc<D>::SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(embed_tc_kernel<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, EmbTc<D>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid(cdiv(Ht * Wt, EmbTc<D>::TOK), B);
-  return launch_pdl(embed_tc_kernel<D>, grid, dim3(256), EmbTc<D>::SMEM, st, x, hole, H, W, Ht, Wt, we16, be, tok, v0,
+  return launch_pdl(embed_tc_kernel<D, T>, grid, dim3(256), EmbTc<D>::SMEM, st, x, hole, H, W, Ht, Wt, we16, be, tok, v0,
                     ln_g, ln_b, ln_out);
 }
 
-cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const bf16* we16,
+template <typename T>
+cudaError_t launch_embed_tc(const float* x, const uint8_t* hole, int B, int H, int W, int Ht, int Wt, const T* we16,
                             const float* be, int d, float* tok, uint8_t* v0, const float* ln_g, const float* ln_b,
-                            bf16* ln_out, cudaStream_t st) {
-  if (d == 256) return launch_embed_tc_d<256>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
-  if (d == 128) return launch_embed_tc_d<128>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
-  if (d == 64) return launch_embed_tc_d<64>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
+                            T* ln_out, cudaStream_t st) {
+  if (d == 256) return launch_embed_tc_d<256, T>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
+  if (d == 128) return launch_embed_tc_d<128, T>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
+  if (d == 64) return launch_embed_tc_d<64, T>(x, hole, B, H, W, Ht, Wt, we16, be, tok, v0, ln_g, ln_b, ln_out, st);
   return cudaErrorInvalidValue;
 }
+template cudaError_t launch_embed_tc<bf16>(const float*, const uint8_t*, int, int, int, int, int, const bf16*,
+                                           const float*, int, float*, uint8_t*, const float*, const float*, bf16*,
+                                           cudaStream_t);
+template cudaError_t launch_embed_tc<f16>(const float*, const uint8_t*, int, int, int, int, int, const f16*,
+                                          const float*, int, float*, uint8_t*, const float*, const float*, f16*,
+                                          cudaStream_t);
 
 template <typename OutT>
 cudaError_t launch_layernorm(const float* x, const float* g, const float* b, OutT* y, int M, int d,
@@ -492,6 +500,7 @@ cudaError_t launch_layernorm(const float* x, const float* g, const float* b, Out
 }
 template cudaError_t launch_layernorm<float>(const float*, const float*, const float*, float*, int, int, cudaStream_t);
 template cudaError_t launch_layernorm<bf16>(const float*, const float*, const float*, bf16*, int, int, cudaStream_t);
+template cudaError_t launch_layernorm<f16>(const float*, const float*, const float*, f16*, int, int, cudaStream_t);
 
 int loss_partials(int B, int H, int W) {
   return (int)(((size_t)B * H * W + LOSS_PIX_PER_CTA - 1) / LOSS_PIX_PER_CTA);

@@ -1,8 +1,8 @@
-// BF16 tensor-core GEMM on tcgen05 for the token GEMMs of the transformer blocks
+// 16-bit tensor-core GEMM on tcgen05 for the token GEMMs of the transformer blocks
 // (QKV, attention projection + residual, MLP fc1 + GELU, fc2 + residual).
 //
-//   C[M, N] = epilogue(A[M, K] . Bt[N, K]^T),  A and Bt bf16 with K contiguous,
-//   FP32 accumulation in tensor memory.
+//   C[M, N] = epilogue(A[M, K] . Bt[N, K]^T),  A and Bt in T (bf16 or f16) with K
+//   contiguous, FP32 accumulation in tensor memory.
 //
 // Persistent, warp-specialized CTA (one per SM):
 //   warp 0        TMA producer: A and B tiles (BK = 64 -> one 128-byte swizzle row per
@@ -19,7 +19,7 @@
 //
 // EPI_RESID_LN (N == BN, a whole row per tile) also normalizes the new residual row:
 // x = resid + acc + bias is stored (FP32) and y = LayerNorm(x) (eps 1e-5, biased
-// variance, FP32 statistics) is stored as bf16 for the next GEMM.  Each thread reduces
+// variance, FP32 statistics) is stored in T for the next GEMM.  Each thread reduces
 // its half row chunk by chunk (exact mean and squared deviations per 32 values, merged
 // with Chan's pairwise formula), the two halves of a row are merged through shared
 // memory, and the stored x is re-read (the warp's own rows) to normalize.
@@ -62,7 +62,7 @@ struct GemmArgs {
   const float* resid;
   const float* ln_g;
   const float* ln_b;
-  bf16* ln_out;
+  void* ln_out;
   int* err;
 };
 
@@ -76,7 +76,7 @@ __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <int BN>
+template <int BN, typename T>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                              const __grid_constant__ CUtensorMap tmB,
                                                              const __grid_constant__ CUtensorMap tmC,
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      constexpr uint32_t idesc = tc::idesc_f32acc(H16<T>::kMmaFmt, BM, BN);
       uint32_t g = 0, i = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++i) {
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
             for (int j = 0; j < 32; ++j) f[j] = gelu_as(f[j]);
           }
-          rows::store32_bf16_async(&tmC, st, col, row0, nvalid, lane, f);
+          rows::store32_h16_async<T>(&tmC, st, col, row0, nvalid, lane, f);
         } else {  // residual (+ LayerNorm statistics; x stays in TMEM for the normalisation)
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             xv[j + 2] = (__uint_as_float(xr[j + 2]) - mean) * rstd * tg.z + tb.z;
             xv[j + 3] = (__uint_as_float(xr[j + 3]) - mean) * rstd * tg.w + tb.w;
           }
-          rows::store32_bf16_async(&tmLN, st, n0 + c0, row0, nvalid, lane, xv);
+          rows::store32_h16_async<T>(&tmLN, st, n0 + c0, row0, nvalid, lane, xv);
         }
       }
       tc::fence_before_sync();
@@ -350,16 +350,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// rows x inner bf16 matrix, inner contiguous; box = box_inner x box_rows, 128-byte swizzle.
-bool make_map_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_inner,
-                 uint32_t box_rows) {
+// rows x inner matrix of 16-bit elements (tensor-map type dt), inner contiguous; box =
+// box_inner x box_rows, 128-byte swizzle.
+bool make_map_2d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t rows,
+                 uint32_t box_inner, uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {inner * 2};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -375,9 +376,11 @@ int num_sms() {
   return n;
 }
 
-// Store map of a [rows][inner] matrix (row pitch ld elements of es bytes): 32-row boxes of
-// 64 bytes in the 64-byte swizzle that the epilogue's staging tiles use.
-bool make_store_map(CUtensorMap* m, const void* base, bool f32, uint64_t inner, uint64_t rows, uint64_t ld) {
+// Store map of a [rows][inner] matrix (row pitch ld elements of es bytes; f32, else the
+// 16-bit type dt16): 32-row boxes of 64 bytes in the 64-byte swizzle that the epilogue's
+// staging tiles use.
+bool make_store_map(CUtensorMap* m, const void* base, bool f32, CUtensorMapDataType dt16, uint64_t inner,
+                    uint64_t rows, uint64_t ld) {
   auto fn = encode_fn();
   if (!fn) return false;
   const uint32_t es = f32 ? 4 : 2;
@@ -385,71 +388,84 @@ bool make_store_map(CUtensorMap* m, const void* base, bool f32, uint64_t inner, 
   cuuint64_t strides[1] = {ld * es};
   cuuint32_t box[2] = {64 / es, 32};
   cuuint32_t ess[2] = {1, 1};
-  return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+  return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : dt16, 2, const_cast<void*>(base), dims,
             strides, box, ess, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
-cudaError_t launch_bn(const bf16* A, const bf16* Bt, const GemmArgs& args, cudaStream_t st) {
+template <int BN, typename T>
+cudaError_t launch_bn(const T* A, const T* Bt, const GemmArgs& args, cudaStream_t st) {
   using Cfg = TcCfg<BN>;
+  constexpr CUtensorMapDataType dt = tc::tma_dtype<T>();
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   CUtensorMap ma, mb;
-  if (!make_map_2d(&ma, A, (uint64_t)args.K, (uint64_t)args.M, BK, BM)) return cudaErrorInvalidValue;
-  if (!make_map_2d(&mb, Bt, (uint64_t)args.K, (uint64_t)args.N, BK, BN)) return cudaErrorInvalidValue;
+  if (!make_map_2d(&ma, dt, A, (uint64_t)args.K, (uint64_t)args.M, BK, BM)) return cudaErrorInvalidValue;
+  if (!make_map_2d(&mb, dt, Bt, (uint64_t)args.K, (uint64_t)args.N, BK, BN)) return cudaErrorInvalidValue;
   const int tiles = ((args.M + BM - 1) / BM) * (args.N / BN);
   const int grid = tiles < num_sms() ? tiles : num_sms();
-  // outputs: C (f32 for the residual epilogues and EPI_NONE, else bf16) and the LayerNorm output
+  // outputs: C (f32 for the residual epilogues and EPI_NONE, else T) and the LayerNorm output
   CUtensorMap mc, ml;
   const bool c32 = args.epi == EPI_NONE || args.epi == EPI_BIAS_RESID || args.epi == EPI_RESID_LN;
   if ((reinterpret_cast<uintptr_t>(args.C) & 15) || (args.ldc * (c32 ? 4 : 2)) % 16) return cudaErrorInvalidValue;
-  if (!make_store_map(&mc, args.C, c32, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.ldc))
+  if (!make_store_map(&mc, args.C, c32, dt, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.ldc))
     return cudaErrorInvalidValue;
   ml = mc;
   if (args.epi == EPI_RESID_LN &&
       ((reinterpret_cast<uintptr_t>(args.ln_out) & 15) ||
-       !make_store_map(&ml, args.ln_out, false, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.N)))
+       !make_store_map(&ml, args.ln_out, false, dt, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.N)))
     return cudaErrorInvalidValue;
-  cudaError_t le = launch_pdl(gemm_tc_kernel<BN>, grid, dim3(THREADS), Cfg::SMEM_BYTES, st, ma, mb, mc, ml, args);
+  cudaError_t le = launch_pdl(gemm_tc_kernel<BN, T>, grid, dim3(THREADS), Cfg::SMEM_BYTES, st, ma, mb, mc, ml, args);
   if (le != cudaSuccess) return le;
   return cudaGetLastError();
 }
 
-cudaError_t launch_any(const bf16* A, const bf16* Bt, const GemmArgs& a, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_any(const T* A, const T* Bt, const GemmArgs& a, cudaStream_t st) {
   if (a.M <= 0 || a.N <= 0 || a.K <= 0 || a.K % BK || a.N % 64 || a.ldc % 8) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt)) & 15) return cudaErrorInvalidValue;
   if (a.epi != EPI_NONE && !a.bias) return cudaErrorInvalidValue;
   if (a.epi == EPI_RESID_LN) {  // a whole row per tile
-    if (a.N == 256) return launch_bn<256>(A, Bt, a, st);
-    if (a.N == 128) return launch_bn<128>(A, Bt, a, st);
-    if (a.N == 64) return launch_bn<64>(A, Bt, a, st);
+    if (a.N == 256) return launch_bn<256, T>(A, Bt, a, st);
+    if (a.N == 128) return launch_bn<128, T>(A, Bt, a, st);
+    if (a.N == 64) return launch_bn<64, T>(A, Bt, a, st);
     return cudaErrorInvalidValue;
   }
-  if (a.N % 256 == 0) return launch_bn<256>(A, Bt, a, st);
-  if (a.N % 128 == 0) return launch_bn<128>(A, Bt, a, st);
-  return launch_bn<64>(A, Bt, a, st);
+  if (a.N % 256 == 0) return launch_bn<256, T>(A, Bt, a, st);
+  if (a.N % 128 == 0) return launch_bn<128, T>(A, Bt, a, st);
+  return launch_bn<64, T>(A, Bt, a, st);
 }
 
 }  // namespace
 
 bool gemm_tc_ln_supported(int N) { return N == 64 || N == 128 || N == 256; }
 
-cudaError_t launch_gemm_tc(const bf16* A, const bf16* Bt, void* C, int ldc, int M, int N, int K, int epi,
+template <typename T>
+cudaError_t launch_gemm_tc(const T* A, const T* Bt, void* C, int ldc, int M, int N, int K, int epi,
                            const float* bias, const float* resid, int* err, cudaStream_t st) {
   GemmArgs a{C, ldc, M, N, K, epi, bias, resid, nullptr, nullptr, nullptr, err};
-  return launch_any(A, Bt, a, st);
+  return launch_any<T>(A, Bt, a, st);
 }
 
-cudaError_t launch_gemm_tc_resid_ln(const bf16* A, const bf16* Bt, float* X, int M, int N, int K, const float* bias,
-                                    const float* ln_g, const float* ln_b, bf16* ln_out, int* err, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_gemm_tc_resid_ln(const T* A, const T* Bt, float* X, int M, int N, int K, const float* bias,
+                                    const float* ln_g, const float* ln_b, T* ln_out, int* err, cudaStream_t st) {
   GemmArgs a{X, N, M, N, K, EPI_RESID_LN, bias, X, ln_g, ln_b, ln_out, err};
-  return launch_any(A, Bt, a, st);
+  return launch_any<T>(A, Bt, a, st);
 }
+
+#define INSTANTIATE(T)                                                                                           \
+  template cudaError_t launch_gemm_tc<T>(const T*, const T*, void*, int, int, int, int, int, const float*,        \
+                                         const float*, int*, cudaStream_t);                                       \
+  template cudaError_t launch_gemm_tc_resid_ln<T>(const T*, const T*, float*, int, int, int, const float*,       \
+                                                  const float*, const float*, T*, int*, cudaStream_t);
+INSTANTIATE(bf16)
+INSTANTIATE(f16)
+#undef INSTANTIATE
 
 }  // namespace inpaint

@@ -1,7 +1,7 @@
-// Fused attention projection + MLP of a transformer block on tcgen05 (BF16 form), for
-// a tile of token rows:
+// Fused attention projection + MLP of a transformer block on tcgen05 (the 16-bit forms:
+// operands in T = bf16 or f16, FP32 accumulation), for a tile of token rows:
 //   x1   = x + A . Wp + bp                      (MMA_P into TMEM; A = attention output)
-//   Y    = normalized x1                         (bf16, written into the SMEM A buffer;
+//   Y    = normalized x1                         (T, written into the SMEM A buffer;
 //                                                 LayerNorm2's affine part is folded into W1)
 //   for hidden chunks j of 128 columns:
 //     H_j  = gelu(Y . W1[:, j] + b1[j])         (MMA1 into TMEM, epilogue back into TMEM)
@@ -24,9 +24,9 @@
 // MMA1.  Wp^T, W1^T ([hid][D]) and W2^T ([D][hid]) k-blocks stream through a ring of
 // 16 KB stages in the order the MMA warp consumes them (MMA1 of chunk j+1 is issued
 // before MMA2 of chunk j, so the tensor core works while the epilogue warps turn H_j
-// into bf16); the ring takes what shared memory is left.  TMEM: OUT (D cols) + two H
+// into 16-bit values); the ring takes what shared memory is left.  TMEM: OUT (D cols) + two H
 // buffers (128 cols each); MMA_P accumulates into the H buffers' columns, so the next
-// tile's projection runs while the final drain still reads OUT.  The epilogue writes the bf16 H_j over the FP32 columns it
+// tile's projection runs while the final drain still reads OUT.  The epilogue writes the 16-bit H_j over the FP32 columns it
 // has just read (two hidden columns per 32-bit TMEM column, the tcgen05 A-operand
 // layout).  Barriers that the MMA warp waits on live in the even CTA and count both CTAs'
 // arrivals and TMA bytes; MMA completions are signalled to both CTAs.
@@ -54,7 +54,7 @@ namespace inpaint {
 namespace {
 
 constexpr int BM = 128, BK = 64, HC = 128;   // rows per CTA, k-block, hidden chunk
-constexpr int NB = 2;                         // H buffers in TMEM (FP32, then bf16 in place)
+constexpr int NB = 2;                         // H buffers in TMEM (FP32, then 16-bit in place)
 constexpr int LOOK = NB - 1;                  // MMA1 runs this many chunks ahead of MMA2
 constexpr int ROLE_WARPS = 4;                 // warpgroup 0: TMA producer, MMA issuer, two idle
 constexpr int EPI_WARPS = 8;                  // GELU warps: two per TMEM lane quarter
@@ -108,7 +108,7 @@ struct MlpCfg {
 
 struct MlpArgs {
   float* X;              // residual stream [M, D] f32, updated in place
-  bf16* ln_out;          // [M, D]
+  void* ln_out;          // [M, D] of the operand type
   const float* bp;       // [D] projection bias
   const float* b1;       // [hid]
   const float* b2;       // [D]
@@ -119,7 +119,7 @@ struct MlpArgs {
 };
 
 
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                  const __grid_constant__ CUtensorMap tmWp,
                                                                  const __grid_constant__ CUtensorMap tmW1,
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   uint64_t* p_full = a_empty + 1;       //         both: projection accumulator in OUT
   uint64_t* a_ready = p_full + 1;       //         even CTA: both CTAs wrote Y (SMEM) and x1 (OUT)
   uint64_t* h_full = a_ready + 1;       // [NB]    both: H_j in TMEM
-  uint64_t* h_done = h_full + NB;       // [NB]    even CTA: both CTAs turned H_j into bf16 (in TMEM)
+  uint64_t* h_done = h_full + NB;       // [NB]    even CTA: both CTAs turned H_j into 16-bit values (in TMEM)
   uint64_t* o_full = h_done + NB;       //         both: OUT complete
   uint64_t* teardown = o_full + 1;
   uint64_t* stat_bar = teardown + 1;    // [4]     per lane quarter: the three drain slices' statistics
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   };
 
   // After MMA_P: x1 = x + P + bp into OUT (P: MMA_P's accumulator in the H columns; x1 is
-  // the starting value of MMA2's accumulation), Y = (x1 - mean) / std as bf16 into the
+  // the starting value of MMA2's accumulation), Y = (x1 - mean) / std in T into the
   // SMEM A buffer.  A warp's OUT columns are its own final-drain slice of the previous
   // tile, which it has finished.  Each residual
   // block is loaded while the previous one is processed, the first while MMA_P runs.
@@ -302,11 +302,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
       tc::tmem_ld_wait();
       uint32_t pk[16];
 #pragma unroll
-      for (int k = 0; k < 32; k += 2) {
-        __nv_bfloat162 y = __floats2bfloat162_rn((__uint_as_float(xr[k]) - mean) * rstd,
-                                                 (__uint_as_float(xr[k + 1]) - mean) * rstd);
-        pk[k / 2] = *reinterpret_cast<uint32_t*>(&y);
-      }
+      for (int k = 0; k < 32; k += 2)
+        pk[k / 2] = H16<T>::pack2((__uint_as_float(xr[k]) - mean) * rstd, (__uint_as_float(xr[k + 1]) - mean) * rstd);
       // columns c0 .. c0+31 of row r: atom c0/64, 16-byte chunks (c0%64)/8 .. +3, swizzled by r%8
       uint8_t* rowp = sA + (c0 >> 6) * (BM * BK * 2) + r * 128;
       const int ch0 = (c0 & 63) >> 3;
@@ -369,7 +366,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
 #pragma unroll
         for (int k = 0; k < 32; ++k) xv[k] = xv[k] * __ldg(args.ln_g + c0 + k) + __ldg(args.ln_b + c0 + k);
       }
-      rows::store32_bf16_async(&tmLN, st, c0, row0, nvalid, lane, xv);
+      rows::store32_h16_async<T>(&tmLN, st, c0, row0, nvalid, lane, xv);
     }
     tc::fence_before_sync();
     __syncwarp();
@@ -425,8 +422,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
       __syncwarp();
     } else if (warp == 1 && rank == 0) {
       if (lane == 0) {
-        constexpr uint32_t id1 = tc::idesc_bf16_f32(2 * BM, HC);
-        constexpr uint32_t id2 = tc::idesc_bf16_f32(2 * BM, D);
+        constexpr uint32_t id1 = tc::idesc_f32acc(H16<T>::kMmaFmt, 2 * BM, HC);
+        constexpr uint32_t id2 = tc::idesc_f32acc(H16<T>::kMmaFmt, 2 * BM, D);
         uint32_t g = 0, q = 0;  // ring slot counter, hidden-chunk counter (across tiles)
         bool ok = true;
         auto pop = [&](int& s) {
@@ -440,7 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
           const uint32_t hb = qq % NB, use = qq / NB;
           // H buffer free: the previous use's GELU read it (h_done cannot run two phases
           // ahead: its next phase needs this very MMA1), and that use's MMA2, issued
-          // before this MMA1, read the bf16 values before this MMA1 overwrites them
+          // before this MMA1, read the 16-bit values before this MMA1 overwrites them
           if (use >= 1 && !tc::mbar_wait_cluster(&h_done[hb], (use & 1) ^ 1, abort_flag)) return false;
           tc::fence_after_sync();
           const uint32_t dt = tmem_base + Cfg::H_COL0 + hb * HC;
@@ -459,7 +456,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
           tc::mma_commit_pair(&h_full[hb], PAIR);
           return true;
         };
-        auto mma2 = [&](uint32_t qq, bool last) {  // OUT += bf16 H[qq % NB] . W2_chunk^T
+        auto mma2 = [&](uint32_t qq, bool last) {  // OUT += 16-bit H[qq % NB] . W2_chunk^T
           const uint32_t hb = qq % NB, use = qq / NB;
           if (!tc::mbar_wait_cluster(&h_done[hb], use & 1, abort_flag)) return false;
           tc::fence_after_sync();
@@ -524,7 +521,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
       __syncwarp();
     }
   } else if (warp < ROLE_WARPS + EPI_WARPS) {
-    // ---- hidden chunks: TMEM H -> bias + GELU -> bf16 in TMEM (the A operand of MMA2);
+    // ---- hidden chunks: TMEM H -> bias + GELU -> T in TMEM (the A operand of MMA2);
     // before and after them, this warp's slices of the tile's two drains
     const int quarter = warp & 3, cg = (warp - ROLE_WARPS) >> 2;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
@@ -547,7 +544,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
 #pragma unroll
         for (int l = 0; l < NL; ++l) tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + hb * HC + cb + 32 * l, v[l]);
         tc::tmem_ld_wait();
-        // bf16 GELU values back into the first EPI_COLS / 2 columns this warp just read
+        // 16-bit GELU values back into the first EPI_COLS / 2 columns this warp just read
         // (pairs of hidden columns per 32-bit TMEM column): MMA2's A operand
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
@@ -557,12 +554,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
           for (int k = 0; k < 16; k += 2) {
             const float4 b4 = *reinterpret_cast<const float4*>(bp + 2 * k);
             const uint32_t* x = &v[l][2 * k];
-            __nv_bfloat162 h0 = __floats2bfloat162_rn(gelu_as(__uint_as_float(x[0]) + b4.x),
-                                                      gelu_as(__uint_as_float(x[1]) + b4.y));
-            __nv_bfloat162 h1 = __floats2bfloat162_rn(gelu_as(__uint_as_float(x[2]) + b4.z),
-                                                      gelu_as(__uint_as_float(x[3]) + b4.w));
-            pk[k] = *reinterpret_cast<uint32_t*>(&h0);
-            pk[k + 1] = *reinterpret_cast<uint32_t*>(&h1);
+            pk[k] = H16<T>::pack2(gelu_as(__uint_as_float(x[0]) + b4.x), gelu_as(__uint_as_float(x[1]) + b4.y));
+            pk[k + 1] = H16<T>::pack2(gelu_as(__uint_as_float(x[2]) + b4.z), gelu_as(__uint_as_float(x[3]) + b4.w));
           }
           tc::tmem_st_32x32b_x16(lane_base + Cfg::H_COL0 + hb * HC + cb + 16 * l, pk);
         }
@@ -628,21 +621,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool map2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint32_t box_inner, uint32_t box_rows) {
+bool map2d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t rows, uint32_t box_inner,
+           uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {inner * 2};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Store map of a dense [rows][inner] matrix: 32-row boxes of 64 bytes, 64-byte swizzle
 // (the layout of the drain warps' staging tiles).
-bool store_map(CUtensorMap* m, const void* base, bool f32, uint64_t inner, uint64_t rows) {
+bool store_map(CUtensorMap* m, const void* base, bool f32, CUtensorMapDataType dt16, uint64_t inner, uint64_t rows) {
   auto fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
   const uint32_t es = f32 ? 4 : 2;
@@ -650,7 +644,7 @@ bool store_map(CUtensorMap* m, const void* base, bool f32, uint64_t inner, uint6
   cuuint64_t strides[1] = {inner * es};
   cuuint32_t box[2] = {64 / es, 32};
   cuuint32_t ess[2] = {1, 1};
-  return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+  return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : dt16, 2, const_cast<void*>(base), dims,
             strides, box, ess, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -666,11 +660,11 @@ int num_sms() {
   return n;
 }
 
-template <int D>
-cudaError_t launch_d(const bf16* A, const bf16* Wpt, const bf16* W1t, const bf16* W2t, const MlpArgs& a,
-                     cudaStream_t st) {
+template <int D, typename T>
+cudaError_t launch_d(const T* A, const T* Wpt, const T* W1t, const T* W2t, const MlpArgs& a, cudaStream_t st) {
   using Cfg = MlpCfg<D>;
-  auto kern = proj_mlp_tc_kernel<D>;
+  constexpr CUtensorMapDataType dt = tc::tma_dtype<T>();
+  auto kern = proj_mlp_tc_kernel<D, T>;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -695,12 +689,12 @@ cudaError_t launch_d(const bf16* A, const bf16* Wpt, const bf16* W1t, const bf16
     max_pairs = n > 0 ? n : 1;
   }
   CUtensorMap ma, mp, m1, m2, mx, mln;
-  if (!map2d(&ma, A, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
-  if (!map2d(&mp, Wpt, D, D, BK, D / 2)) return cudaErrorInvalidValue;
-  if (!store_map(&mx, a.X, true, D, (uint64_t)a.M) || !store_map(&mln, a.ln_out, false, D, (uint64_t)a.M))
+  if (!map2d(&ma, dt, A, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
+  if (!map2d(&mp, dt, Wpt, D, D, BK, D / 2)) return cudaErrorInvalidValue;
+  if (!store_map(&mx, a.X, true, dt, D, (uint64_t)a.M) || !store_map(&mln, a.ln_out, false, dt, D, (uint64_t)a.M))
     return cudaErrorInvalidValue;
-  if (!map2d(&m1, W1t, D, (uint64_t)a.hid, BK, HC / 2)) return cudaErrorInvalidValue;
-  if (!map2d(&m2, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;
+  if (!map2d(&m1, dt, W1t, D, (uint64_t)a.hid, BK, HC / 2)) return cudaErrorInvalidValue;
+  if (!map2d(&m2, dt, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;
   const int pairs = ((a.M + BM - 1) / BM + 1) / 2;
   lc.gridDim = dim3((pairs < max_pairs ? pairs : max_pairs) * 2);
   lc.numAttrs = 2;
@@ -714,18 +708,26 @@ bool mlp_tc_supported(int d, int hid) {
   return (d == 64 || d == 128 || d == 256) && hid % HC == 0 && hid >= HC && hid <= 1024;
 }
 
-cudaError_t launch_proj_mlp_tc(const bf16* A, const bf16* Wpt, const float* bp, const bf16* W1t, const bf16* W2t,
+template <typename T>
+cudaError_t launch_proj_mlp_tc(const T* A, const T* Wpt, const float* bp, const T* W1t, const T* W2t,
                                const float* b1, const float* b2, float* X, const float* ln_g, const float* ln_b,
-                               bf16* ln_out, int M, int d, int hid, int* err, cudaStream_t st) {
+                               T* ln_out, int M, int d, int hid, int* err, cudaStream_t st) {
   if (!mlp_tc_supported(d, hid) || M <= 0) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Wpt) | reinterpret_cast<uintptr_t>(W1t) |
        reinterpret_cast<uintptr_t>(W2t) | reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(ln_out)) & 15)
     return cudaErrorInvalidValue;
   if ((ln_g == nullptr) != (ln_b == nullptr)) return cudaErrorInvalidValue;
   MlpArgs a{X, ln_out, bp, b1, b2, ln_g, ln_b, M, hid, err};
-  if (d == 256) return launch_d<256>(A, Wpt, W1t, W2t, a, st);
-  if (d == 128) return launch_d<128>(A, Wpt, W1t, W2t, a, st);
-  return launch_d<64>(A, Wpt, W1t, W2t, a, st);
+  if (d == 256) return launch_d<256, T>(A, Wpt, W1t, W2t, a, st);
+  if (d == 128) return launch_d<128, T>(A, Wpt, W1t, W2t, a, st);
+  return launch_d<64, T>(A, Wpt, W1t, W2t, a, st);
 }
+
+template cudaError_t launch_proj_mlp_tc<bf16>(const bf16*, const bf16*, const float*, const bf16*, const bf16*,
+                                              const float*, const float*, float*, const float*, const float*, bf16*,
+                                              int, int, int, int*, cudaStream_t);
+template cudaError_t launch_proj_mlp_tc<f16>(const f16*, const f16*, const float*, const f16*, const f16*,
+                                             const float*, const float*, float*, const float*, const float*, f16*, int,
+                                             int, int, int*, cudaStream_t);
 
 }  // namespace inpaint

@@ -7,6 +7,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include "common.cuh"
+
 namespace inpaint {
 namespace tc {
 
@@ -322,13 +324,23 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+// Instruction descriptor, kind::f16: D f32, A and B of format `fmt` (0 = f16, 1 = bf16;
+// both operands always share it), both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t fmt, int M, int N) {
   return (1u << 4)                             // D format: f32
-         | (1u << 7)                           // A format: bf16
-         | (1u << 10)                          // B format: bf16
+         | (fmt << 7)                          // A format
+         | (fmt << 10)                         // B format
          | ((uint32_t)(N >> 3) << 17)          // N / 8
          | ((uint32_t)(M >> 4) << 24);         // M / 16
+}
+
+// Tensor-map element type of a 16-bit operand type (the copies move bits; the type only
+// names the element size and the out-of-bounds fill, zero for both).
+template <typename T>
+constexpr CUtensorMapDataType tma_dtype() {
+  if constexpr (sizeof(T) == 4) return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  else if constexpr (H16<T>::kMmaFmt == 1) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  else return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
 }
 
 }  // namespace tc

@@ -83,19 +83,17 @@ __device__ __forceinline__ void store32_f32(float* base, size_t ld, int nvalid, 
   __syncwarp();
 }
 
-// Row `lane` of a 32 x 32 bf16 block = v (rounded to nearest even).
-__device__ __forceinline__ void store32_bf16(bf16* base, size_t ld, int nvalid, uint8_t* tile, int lane,
-                                             const float (&v)[32]) {
+// Row `lane` of a 32 x 32 block of 16-bit type T = v (rounded to nearest even).
+template <typename T>
+__device__ __forceinline__ void store32_h16(T* base, size_t ld, int nvalid, uint8_t* tile, int lane,
+                                            const float (&v)[32]) {
   const int rr = lane >> 2, ch = lane & 3;
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     uint32_t w[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
-      w[e] = *reinterpret_cast<uint32_t*>(&h2);
-    }
+    for (int e = 0; e < 4; ++e) w[e] = H16<T>::pack2(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
     *reinterpret_cast<uint4*>(tile + slot(lane, j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
   __syncwarp();
@@ -138,18 +136,16 @@ __device__ __forceinline__ void async_issue(const CUtensorMap* map, const uint8_
   }
 }
 
-// Row `lane` of a 32 x 32 bf16 box at (column c0, row r0) = v.
-__device__ __forceinline__ void store32_bf16_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int nvalid,
-                                                   int lane, const float (&v)[32]) {
+// Row `lane` of a 32 x 32 box of 16-bit type T at (column c0, row r0) = v.
+template <typename T>
+__device__ __forceinline__ void store32_h16_async(const CUtensorMap* map, AsyncRows& a, int c0, int r0, int nvalid,
+                                                  int lane, const float (&v)[32]) {
   uint8_t* t = async_acquire(a, lane);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     uint32_t w[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
-      w[e] = *reinterpret_cast<uint32_t*>(&h2);
-    }
+    for (int e = 0; e < 4; ++e) w[e] = H16<T>::pack2(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
     *reinterpret_cast<uint4*>(t + slot(lane, j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
   async_issue(map, t, c0, r0, nvalid, lane);

@@ -46,7 +46,8 @@ def test_num_params_matches_blob_format(lib, name):
 
 
 @pytest.mark.parametrize("bad", [dict(window=4), dict(patch=2), dict(dim=96, heads=2), dict(heads=3),
-                                 dict(precision=2), dict(dim=96, heads=3, precision=1), dict(mlp_ratio=0)])
+                                 dict(precision=3), dict(dim=96, heads=3, precision=1),
+                                 dict(dim=96, heads=3, precision=2), dict(mlp_ratio=0)])
 def test_invalid_configs_are_rejected(lib, bad):
     cfg = ModelConfig(**{**dict(dim=128, heads=4, window=8, blocks=2, mlp_ratio=2), **bad})
     with pytest.raises(binding.InpaintError) as e:

@@ -12,7 +12,7 @@ import torch
 
 from oracle import inpaint_oracle as O
 from paper_2509_10466_gb300 import binding, synthetic as S
-from paper_2509_10466_gb300.config import BF16, FP32, ModelConfig
+from paper_2509_10466_gb300.config import BF16, FP16, FP32, ModelConfig
 
 from helpers import TOL_BF16, TOL_FP32, hole_rel_l2, lib
 
@@ -62,7 +62,7 @@ def run_oracle(cfg, weights, x, hole, m):
     return np.stack(outs), masks, mems
 
 
-@pytest.mark.parametrize("precision,tol", [(FP32, TOL_FP32), (BF16, TOL_BF16)])
+@pytest.mark.parametrize("precision,tol", [(FP32, TOL_FP32), (BF16, TOL_BF16), (FP16, TOL_BF16)])
 def test_stream_with_two_memory_slots_matches_oracle(precision, tol):
     cfg = ModelConfig(dim=64, heads=2, window=8, blocks=4, mlp_ratio=2, precision=precision, mem_slots=2)
     weights = S.make_weights(cfg, seed=5, perturb=True)

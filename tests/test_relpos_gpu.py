@@ -6,7 +6,7 @@ import pytest
 import torch
 
 from paper_2509_10466_gb300 import synthetic as S
-from paper_2509_10466_gb300.config import BF16, FP32, ModelConfig
+from paper_2509_10466_gb300.config import BF16, FP16, FP32, ModelConfig
 
 from helpers import TOL_BF16, TOL_FP32, check_parity, inputs
 from test_backward_gpu import compare, gpu_grad, oracle_grad
@@ -16,7 +16,7 @@ from helpers import hole_rel_l2
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,tol", [(FP32, TOL_FP32), (BF16, TOL_BF16)])
+@pytest.mark.parametrize("precision,tol", [(FP32, TOL_FP32), (BF16, TOL_BF16), (FP16, TOL_BF16)])
 @pytest.mark.parametrize("H,W", [(64, 96), (100, 70)])
 def test_forward_with_relative_position_bias(precision, tol, H, W):
     cfg = ModelConfig(dim=64, heads=2, window=8, blocks=3, mlp_ratio=2, precision=precision, pos_bias=1)

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from paper_2509_10466_gb300 import binding, synthetic as S
-from paper_2509_10466_gb300.config import BF16, FP32, ModelConfig
+from paper_2509_10466_gb300.config import BF16, FP16, FP32, ModelConfig
 from paper_2509_10466_gb300.serving import serve
 
 from helpers import lib
@@ -13,7 +13,7 @@ from helpers import lib
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [BF16, FP32])
+@pytest.mark.parametrize("precision", [BF16, FP16, FP32])
 def test_each_result_is_the_same_alone_and_in_the_mix(precision):
     lib()
     cfg = ModelConfig(dim=64, heads=2, window=8, blocks=2, mlp_ratio=2, precision=precision)
