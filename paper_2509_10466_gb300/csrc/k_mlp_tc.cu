@@ -428,7 +428,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         bool ok = true;
         auto pop = [&](int& s) {
           s = g % RING;
-          if (!tc::mbar_wait_cluster(&full[s], (g / RING) & 1, abort_flag)) return false;
+          // weight bytes of both CTAs, counted by the TMA transactions themselves
+          if (!tc::mbar_wait(&full[s], (g / RING) & 1, abort_flag)) return false;
           tc::fence_after_sync();
           ++g;
           return true;
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
           // H buffer free: the previous use's GELU read it (h_done cannot run two phases
           // ahead: its next phase needs this very MMA1), and that use's MMA2, issued
           // before this MMA1, read the 16-bit values before this MMA1 overwrites them
-          if (use >= 1 && !tc::mbar_wait_cluster(&h_done[hb], (use & 1) ^ 1, abort_flag)) return false;
+          if (use >= 1 && !tc::mbar_wait(&h_done[hb], (use & 1) ^ 1, abort_flag)) return false;
           tc::fence_after_sync();
           const uint32_t dt = tmem_base + Cfg::H_COL0 + hb * HC;
           for (int st = 0; st < Cfg::W1_STAGES; ++st) {
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         };
         auto mma2 = [&](uint32_t qq, bool last) {  // OUT += 16-bit H[qq % NB] . W2_chunk^T
           const uint32_t hb = qq % NB, use = qq / NB;
-          if (!tc::mbar_wait_cluster(&h_done[hb], use & 1, abort_flag)) return false;
+          if (!tc::mbar_wait(&h_done[hb], use & 1, abort_flag)) return false;
           tc::fence_after_sync();
           for (int kb = 0; kb < Cfg::KH; ++kb) {
             int s;
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         // P = A . Wp^T into the H columns: the previous tile's MMA2s, issued before, have
         // read them (tcgen05 MMAs run in issue order); its final drain may still read OUT
         auto mma_p = [&](int t) {
-          if (!tc::mbar_wait_cluster(a_full, t & 1, abort_flag)) return false;
+          if (!tc::mbar_wait(a_full, t & 1, abort_flag)) return false;
           tc::fence_after_sync();
           for (int kb = 0; kb < Cfg::KA; ++kb) {
             int s;
@@ -562,7 +563,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         tc::tmem_st_wait();
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive_cluster(lead(&h_done[hb]));
+        // the 16-bit H values are complete in this CTA's tensor memory (tcgen05.wait::st)
+        if (lane == 0) tc::mbar_arrive_remote(lead(&h_done[hb]));
       }
       if (ok) ok = fin(t, p, 1 + cg, d_lo, Cfg::GS, st);
     }
