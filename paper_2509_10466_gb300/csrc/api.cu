@@ -358,12 +358,12 @@ int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, co
       { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, fold ? fold : c->w32 + b.qkvb, nullptr, err, st))); }
       if (temporal) {
         LaunchScope ls(c, st, K_ATTN);
-        TRY(cuda_err(launch_attention_tc_mem<A>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, st, rp, err)));
+        // the kernel also records this block's part of each frame's memory tensor
+        TRY(cuda_err(launch_attention_tc_mem<A>(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, mtab, c->cfg.mem_slots, moff, moff + mkv, mem ? mem->out : nullptr, st, rp, err)));
       } else {
         LaunchScope ls(c, st, K_ATTN);
         TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp, err)));
       }
-      if (temporal) TRY(record_memory(qkv));
       if (c->fold_ln) {
         // projection, residual, LN2 and the whole MLP in one kernel: only the attention
         // output and the residual row come in, only the new residual row and its LN leave

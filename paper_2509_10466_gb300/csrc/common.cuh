@@ -238,11 +238,14 @@ template <typename T>
 cudaError_t launch_attention_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt, int d,
                                  int heads, int offset, const MemTab* tab, int m, size_t off_kv, size_t off_mask,
                                  cudaStream_t st, const float* relpos = nullptr);
+// The tensor-core form also records each frame's own memory tensor of this block: with
+// out (host array [B], null entries skipped) it writes the k | v rows of the frame's tokens
+// and the block's input key mask (v_in) at the same offsets off_kv / off_mask of out[b].
 template <typename T>
 cudaError_t launch_attention_tc_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
                                     int Wt, int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
-                                    size_t off_mask, cudaStream_t st, const float* relpos = nullptr,
-                                    int* err = nullptr);
+                                    size_t off_mask, uint8_t* const* out, cudaStream_t st,
+                                    const float* relpos = nullptr, int* err = nullptr);
 
 // Coloured point cloud (world x, y, z, r, g, b per pixel; NaN coordinates where the depth
 // is not usable) and z-buffered splat into an Ho x Wo image.  cam / view: fx, fy, cx, cy;

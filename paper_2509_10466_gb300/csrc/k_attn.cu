@@ -249,17 +249,7 @@ template cudaError_t launch_attention_mem<f16>(const f16*, const uint8_t*, f16*,
 namespace inpaint {
 namespace {
 
-constexpr int HPC = 2;            // heads per CTA
 constexpr float LOG2E = 1.4426950408889634f;
-constexpr int TC_THREADS = 128 * HPC;
-constexpr int ROWB = 40;  // 16-bit values per staged row: 32 + 8 pad (80 B rows, conflict-free ldmatrix)
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
   const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -498,112 +488,183 @@ bool qkv_map(CUtensorMap* m, const T* qkv, int B, int Ht, int Wt, int d) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Temporal form on tensor cores: key blocks of 64 (the current window, then each memory
-// slot's tokens at the window's positions) are staged one after the other into the same
-// K / V buffers; per block S = Q K^T, the running row maximum is raised, the running sum
-// and O rescaled by 2^(old max - new max), and O += P V.  Blocks without a usable key
-// are skipped.
+// Temporal form on tensor cores, one head per CTA.  Key blocks of 64: the window's
+// current tokens, then each memory slot's tokens at the window's positions.  All staging is
+// issued at once: the current Q, K, V boxes by TMA (as in the spatial kernel) and, for each
+// memory slot, the head slices (64 bytes) of its key rows by 16-byte cp.async copies of all
+// threads into 80-byte rows (conflict-free ldmatrix), one commit group per slot, so that
+// the current block is computed while the slots land.  Rows of keys that are not usable
+// are filled with zeros by the copies themselves (their probability is 0).
+// Per block the running row maximum is raised, the running sum and O rescaled by
+// 2^(old max - new max), and O += P V; blocks without a usable key are skipped.
+constexpr int MROW = 80;                // bytes per staged memory key row: 64 + 16 pad
+constexpr int MTILE = SLOTS * MROW;     // one part (K or V) of one memory slot
+constexpr int MEM_SLOTS_MAX = 4;
+
+// 16 bytes global -> shared, or 16 zero bytes when !valid (the source is then not read)
+__device__ __forceinline__ void cp_async16z(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// at most n (0 .. MEM_SLOTS_MAX - 1) of this thread's committed groups still pending
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+  }
+}
+
 template <bool RP, typename T>
-__global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const T* __restrict__ qkv,
-                                                                 const uint8_t* __restrict__ v_in,
-                                                                 T* __restrict__ o, uint8_t* __restrict__ v_out,
-                                                                 int Ht, int Wt, int d, int offset, int nwx,
-                                                                 const __grid_constant__ MemTab mem_tab, int m,
-                                                                 size_t off_kv, size_t off_mask,
-                                                                 const float* __restrict__ relpos) {
-  __shared__ __align__(16) T Qs[HPC][SLOTS][ROWB];
-  __shared__ float rps[RP ? HPC : 1][RP ? 225 : 1];
-  __shared__ __align__(16) T Ks[HPC][SLOTS][ROWB];
-  __shared__ __align__(16) T Vs[HPC][SLOTS][ROWB];
-  __shared__ int stok[SLOTS];       // token row of each slot, -1 for a void slot
-  __shared__ int sidx[SLOTS];       // token index within the frame, -1 for a void slot
-  __shared__ unsigned okw[2];
-  const int w = blockIdx.x, b = blockIdx.z;
+__global__ void __launch_bounds__(TMA_THREADS, 5) attn_mem_tma_kernel(
+    const __grid_constant__ CUtensorMap tmQKV, const uint8_t* __restrict__ v_in, T* __restrict__ o,
+    uint8_t* __restrict__ v_out, int Ht, int Wt, int d, int offset, int nwx, const __grid_constant__ MemTab mem_tab,
+    int m, size_t off_kv, size_t off_mask, const __grid_constant__ MemTab out_tab, int record,
+    const float* __restrict__ relpos, int* err) {
+  extern __shared__ uint8_t msm_raw[];
+  constexpr int TILE = SLOTS * DH * 2;
+  // Q, K, V boxes [3][TILE] (512-byte aligned for the 64-byte swizzle), then the memory
+  // slots' [m][K, V][MTILE]
+  uint8_t* tiles = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(msm_raw) + 511) & ~uintptr_t(511));
+  uint8_t* mtiles = tiles + 3 * TILE;
+  __shared__ float rps[RP ? 225 : 1];
+  __shared__ int stok[SLOTS], sidx[SLOTS];
+  __shared__ unsigned okw[1 + MEM_SLOTS_MAX][2];  // usable-key bits of each key block
+  __shared__ __align__(8) uint64_t bar;
+  const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
   const int wy = w / nwx, wx = w - (w / nwx) * nwx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Nt = Ht * Wt;
-  const int h0 = HPC * blockIdx.y;
+  auto mK = [&](int j) { return mtiles + (size_t)(2 * j) * MTILE; };
+  auto mV = [&](int j) { return mtiles + (size_t)(2 * j + 1) * MTILE; };
+  auto keymask = [&](int kb) { return (unsigned long long)okw[kb][0] | ((unsigned long long)okw[kb][1] << 32); };
+
   if (RP)
-    for (int e = tid; e < HPC * 225; e += TC_THREADS) rps[e / 225][e % 225] = relpos[(h0 + e / 225) * 225 + e % 225];
+    for (int e = tid; e < 225; e += TMA_THREADS) rps[e] = relpos[h * 225 + e];
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmQKV);
+  }
+  __syncthreads();
   pdl_trigger();
   pdl_wait();
-
+  if (tid == 0) {
+    tc::mbar_expect_tx(&bar, 3 * TILE);
+    for (int part = 0; part < 3; ++part)
+      tc::tma_load_4d(tiles + part * TILE, &tmQKV, &bar, part * d + h * DH, wx * WS - offset, wy * WS - offset, b);
+  }
+  // the window's slots while the boxes land
   if (tid < SLOTS) {
     const int ty = wy * WS - offset + (tid >> 3), tx = wx * WS - offset + (tid & 7);
     const bool real = ty >= 0 && ty < Ht && tx >= 0 && tx < Wt;
     sidx[tid] = real ? ty * Wt + tx : -1;
     stok[tid] = real ? b * Nt + ty * Wt + tx : -1;
-    bool any = real && v_in[b * Nt + ty * Wt + tx] != 0;
-    for (int j = 0; j < m && !any; ++j) {
-      const uint8_t* base = mem_tab.p[b * m + j];
-      any = real && base && base[off_mask + ty * Wt + tx] != 0;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, any);
-    if (lane == 0) okw[warp] = bal;
   }
   __syncthreads();
-  if ((okw[0] | okw[1]) == 0u) {  // no usable key anywhere: the window outputs 0 and stays invalid
-    for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {
-      const int s = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
-      const int t = stok[s];
-      if (t >= 0) {
-        *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) = make_uint4(0, 0, 0, 0);
-        if (h0 == 0 && hh == 0 && ch == 0) v_out[t] = 0;
+  // memory rows of every present slot, all threads, one commit group per slot (committed
+  // for every slot, empty ones too, so that slot j is group j): every real token's row
+  // (recorded k | v values, finite), zeros for void slots; the usable-key masks, read
+  // meanwhile, select the keys in the softmax
+  for (int j = 0; j < m; ++j) {
+    const uint8_t* base = mem_tab.p[b * m + j];
+    if (base) {
+      const uint8_t* kv = base + off_kv;
+      for (int e = tid; e < SLOTS * 8; e += TMA_THREADS) {  // (row, part, 16-byte chunk)
+        const int r = e >> 3, part = (e >> 2) & 1, c = e & 3;
+        const int i = sidx[r];
+        const uint8_t* src = i >= 0 ? kv + (((size_t)i * 2 + part) * d + (size_t)h * DH) * sizeof(T) + c * 16 : kv;
+        cp_async16z((part ? mV(j) : mK(j)) + r * MROW + c * 16, src, i >= 0);
       }
     }
+    cp_async_commit();
+  }
+  if (tid < SLOTS) {
+    const int i = sidx[tid];
+    unsigned bal = __ballot_sync(0xffffffffu, i >= 0 && v_in[b * Nt + i] != 0);
+    if (lane == 0) okw[0][warp] = bal;
+    for (int j = 0; j < m; ++j) {
+      const uint8_t* base = mem_tab.p[b * m + j];
+      bal = __ballot_sync(0xffffffffu, i >= 0 && base && base[off_mask + i] != 0);
+      if (lane == 0) okw[1 + j][warp] = bal;
+    }
+  }
+  __syncthreads();
+  unsigned long long any = 0ull;
+  for (int kb = 0; kb <= m; ++kb) any |= keymask(kb);
+  const bool landed = tc::mbar_wait_timed(&bar, 0);
+  __syncthreads();
+  if (!landed) {
+    if (tid == 0 && err) atomicExch(err, DEV_MBAR_TIMEOUT);
+    cp_async_wait_pending(0);
     return;
   }
-  if (h0 == 0 && tid < SLOTS && stok[tid] >= 0) v_out[stok[tid]] = 1;
-  for (int e = tid; e < SLOTS * 4 * HPC; e += TC_THREADS) {  // Q of both heads (real slots)
-    const int s = e >> 3, hh = (e >> 2) & 1, ch = e & 3;
-    const int t = stok[s];
-    cp_async16(&Qs[hh][s][ch * 8], qkv + (size_t)(t >= 0 ? t : 0) * 3 * d + (h0 + hh) * DH + ch * 8, t >= 0);
+  // this frame's memory tensor of this block: k | v of the window's tokens (this head's
+  // 64-byte slices, from the staged boxes) and the block's input key mask
+  uint8_t* rec = record ? const_cast<uint8_t*>(out_tab.p[b]) : nullptr;
+  if (rec) {
+    for (int e = tid; e < SLOTS * 8; e += TMA_THREADS) {  // (row, part K / V, 16-byte chunk)
+      const int r = e >> 3, part = (e >> 2) & 1, c = e & 3;
+      const int i = sidx[r];
+      if (i >= 0)
+        *reinterpret_cast<uint4*>(rec + off_kv + (((size_t)i * 2 + part) * d + (size_t)h * DH) * sizeof(T) + c * 16) =
+            *reinterpret_cast<const uint4*>(tiles + (1 + part) * TILE + swz64(r, c));
+    }
+    if (h == 0 && tid < SLOTS && sidx[tid] >= 0) rec[off_mask + sidx[tid]] = v_in[b * Nt + sidx[tid]];
   }
+  if (!any) {  // no usable key anywhere: the window outputs 0 and stays invalid
+    for (int e = tid; e < SLOTS * 4; e += TMA_THREADS) {
+      const int sl = e >> 2, ch = e & 3;
+      const int t = stok[sl];
+      if (t >= 0) {
+        *reinterpret_cast<uint4*>(o + (size_t)t * d + h * DH + ch * 8) = make_uint4(0, 0, 0, 0);
+        if (h == 0 && ch == 0) v_out[t] = 0;
+      }
+    }
+    cp_async_wait_pending(0);  // the memory rows land before the CTA's shared memory is released
+    return;
+  }
+  if (h == 0 && tid < SLOTS && stok[tid] >= 0) v_out[stok[tid]] = 1;
 
-  const int hh = warp >> 2, wq = warp & 3;
   const int g = lane >> 2, tq = lane & 3;
-  const int r0 = wq * 16;
+  const int r0 = warp * 16;
+  uint8_t* Qt = tiles;
+  const uint8_t* Kt = tiles + TILE;
+  const uint8_t* Vt = tiles + 2 * TILE;
+  uint32_t qa[2][4];
+  {
+    const int row = r0 + (lane & 15);
+    ldsm_x4(qa[0], Qt + swz64(row, lane >> 4));
+    ldsm_x4(qa[1], Qt + swz64(row, 2 + (lane >> 4)));
+  }
   const float sl2 = 1.4426950408889634f / sqrtf((float)DH);  // scale * log2(e)
   float mx0 = -INFINITY, mx1 = -INFINITY, l0 = 0.f, l1 = 0.f;
   float oc[4][4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
-  uint32_t qa[2][4];
   for (int kb = 0; kb <= m; ++kb) {
-    const uint8_t* base = kb == 0 ? nullptr : mem_tab.p[b * m + kb - 1];
-    if (kb > 0 && !base) continue;  // an empty memory slot (uniform across the CTA)
-    __syncthreads();                // the previous block's K / V are no longer read
-    if (tid < SLOTS) {
-      const int i = sidx[tid];
-      const bool ok = i >= 0 && (kb == 0 ? v_in[b * Nt + i] != 0 : base[off_mask + i] != 0);
-      const unsigned bal = __ballot_sync(0xffffffffu, ok);
-      if (lane == 0) okw[warp] = bal;
+    const unsigned long long km = keymask(kb);
+    if (!km) continue;  // uniform across the CTA
+    if (kb > 0) {  // slot kb - 1's copies (group kb - 1) of every thread have landed
+      cp_async_wait_pending(m - kb);
+      __syncthreads();
     }
-    __syncthreads();
-    const unsigned long long keymask = (unsigned long long)okw[0] | ((unsigned long long)okw[1] << 32);
-    if (keymask == 0ull) continue;
-    for (int e = tid; e < SLOTS * 4 * HPC * 2; e += TC_THREADS) {  // K and V of both heads
-      const int part = e >> 9, r = e & 511;
-      const int s = r >> 3, hh2 = (r >> 2) & 1, ch = r & 3;
-      const bool valid = ((keymask >> s) & 1ull) != 0;
-      const int i = sidx[s] >= 0 ? sidx[s] : 0;
-      const T* src = kb == 0 ? qkv + (size_t)(b * Nt + i) * 3 * d + (1 + part) * d
-                             : reinterpret_cast<const T*>(base + off_kv) + (size_t)i * 2 * d + part * d;
-      cp_async16((part == 0 ? &Ks[hh2][s][0] : &Vs[hh2][s][0]) + ch * 8, src + (h0 + hh2) * DH + ch * 8, valid);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    {
-      const int row = r0 + (lane & 15), col = (lane >> 4) * 8;
-      ldsm_x4(qa[0], &Qs[hh][row][col]);
-      ldsm_x4(qa[1], &Qs[hh][row][col + 16]);
-    }
+    // K / V fragment addresses: the swizzled TMA boxes (current block) or the padded rows
+    auto kaddr = [&](int row, int chunk) -> const uint8_t* {
+      return kb == 0 ? Kt + swz64(row, chunk) : mK(kb - 1) + row * MROW + chunk * 16;
+    };
+    auto vaddr = [&](int row, int chunk) -> const uint8_t* {
+      return kb == 0 ? Vt + swz64(row, chunk) : mV(kb - 1) + row * MROW + chunk * 16;
+    };
     float sc[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       sc[j][0] = sc[j][1] = sc[j][2] = sc[j][3] = 0.f;
       uint32_t kbf[4];
-      ldsm_x4(kbf, &Ks[hh][8 * j + (lane & 7)][(lane >> 3) * 8]);
+      ldsm_x4(kbf, kaddr(8 * j + (lane & 7), lane >> 3));
       mma16816<T>(sc[j], qa[0], kbf[0], kbf[1]);
       mma16816<T>(sc[j], qa[1], kbf[2], kbf[3]);
     }
@@ -613,9 +674,9 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const T* __rest
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const int key = 8 * j + 2 * tq + c;
-        const bool okk = (keymask >> key) & 1ull;
-        const float bb0 = RP ? rps[hh][relpos_index(r0 + g, key)] * LOG2E : 0.f;
-        const float bb1 = RP ? rps[hh][relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
+        const bool okk = (km >> key) & 1ull;
+        const float bb0 = RP ? rps[relpos_index(r0 + g, key)] * LOG2E : 0.f;
+        const float bb1 = RP ? rps[relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
         sc[j][c] = okk ? (RP ? fmaf(sc[j][c], sl2, bb0) : sc[j][c] * sl2) : -INFINITY;
         sc[j][2 + c] = okk ? (RP ? fmaf(sc[j][2 + c], sl2, bb1) : sc[j][2 + c] * sl2) : -INFINITY;
         bm0 = fmaxf(bm0, sc[j][c]);
@@ -657,7 +718,7 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const T* __rest
 #pragma unroll
       for (int nn = 0; nn < 2; ++nn) {
         uint32_t vb[4];
-        ldsm_x4_t(vb, &Vs[hh][16 * kk + (lane & 7) + ((lane >> 3) & 1) * 8][16 * nn + (lane >> 4) * 8]);
+        ldsm_x4_t(vb, vaddr(16 * kk + (lane & 7) + ((lane >> 3) & 1) * 8, 2 * nn + (lane >> 4)));
         mma16816<T>(oc[2 * nn], pa, vb[0], vb[1]);
         mma16816<T>(oc[2 * nn + 1], pa, vb[2], vb[3]);
       }
@@ -669,19 +730,19 @@ __global__ void __launch_bounds__(TC_THREADS) attn_tc_mem_kernel(const T* __rest
   l1 += __shfl_xor_sync(0xffffffffu, l1, 2);
   const float inv0 = 1.f / l0, inv1 = 1.f / l1;
   __syncwarp();
+  // stage this warp's 16 output rows in its own Q rows, then store 16-byte chunks
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g][8 * j + 2 * tq]) = H16<T>::pack2(oc[j][0] * inv0, oc[j][1] * inv0);
-    *reinterpret_cast<uint32_t*>(&Qs[hh][r0 + g + 8][8 * j + 2 * tq]) = H16<T>::pack2(oc[j][2] * inv1, oc[j][3] * inv1);
+    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g, j) + 4 * tq) = H16<T>::pack2(oc[j][0] * inv0, oc[j][1] * inv0);
+    *reinterpret_cast<uint32_t*>(Qt + swz64(r0 + g + 8, j) + 4 * tq) = H16<T>::pack2(oc[j][2] * inv1, oc[j][3] * inv1);
   }
   __syncwarp();
 #pragma unroll
   for (int e = lane; e < 16 * 4; e += 32) {
-    const int s = r0 + (e >> 2), ch = e & 3;
-    const int t = stok[s];
+    const int sl = r0 + (e >> 2), ch = e & 3;
+    const int t = stok[sl];
     if (t >= 0)
-      *reinterpret_cast<uint4*>(o + (size_t)t * d + (h0 + hh) * DH + ch * 8) =
-          *reinterpret_cast<const uint4*>(&Qs[hh][s][ch * 8]);
+      *reinterpret_cast<uint4*>(o + (size_t)t * d + h * DH + ch * 8) = *reinterpret_cast<const uint4*>(Qt + swz64(sl, ch));
   }
 }
 
@@ -707,25 +768,42 @@ cudaError_t launch_attention_tc(const T* qkv, const uint8_t* v_in, T* o, uint8_t
 template <typename T>
 cudaError_t launch_attention_tc_mem(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht, int Wt,
                                     int d, int heads, int offset, const MemTab* tab, int m, size_t off_kv,
-                                    size_t off_mask, cudaStream_t st, const float* relpos, int* err) {
+                                    size_t off_mask, uint8_t* const* out, cudaStream_t st, const float* relpos,
+                                    int* err) {
   const int nwy = (Ht + offset + WS - 1) / WS, nwx = (Wt + offset + WS - 1) / WS;
-  if (heads % HPC) return cudaErrorInvalidValue;
+  if (m < 0 || m > MEM_SLOTS_MAX) return cudaErrorInvalidValue;
+  if (out && B > MEM_TAB_MAX) return cudaErrorInvalidValue;
+  MemTab otab{};
+  if (out)
+    for (int b = 0; b < B; ++b) otab.p[b] = out[b];
   if (tab && (size_t)B * m > (size_t)MEM_TAB_MAX) return cudaErrorInvalidValue;
+  // bulk copies read 16-byte aligned memory rows: buffers are 256-byte aligned, offsets and
+  // row pitches multiples of 16 bytes
+  if ((off_kv | ((size_t)d * sizeof(T))) & 15) return cudaErrorInvalidValue;
+  CUtensorMap map;
+  if (!qkv_map<T>(&map, qkv, B, Ht, Wt, d)) return cudaErrorInvalidValue;
   static const MemTab none{};
-  dim3 grid(nwy * nwx, heads / HPC, B);
-  if (relpos)
-    return launch_pdl(attn_tc_mem_kernel<true, T>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d,
-                      offset, nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, relpos);
-  return launch_pdl(attn_tc_mem_kernel<false, T>, grid, dim3(TC_THREADS), 0, st, qkv, v_in, o, v_out, Ht, Wt, d,
-                    offset, nwx, tab ? *tab : none, tab ? m : 0, off_kv, off_mask, (const float*)nullptr);
+  const int mm = tab ? m : 0;
+  const int smem = 511 + 3 * SLOTS * DH * 2 + mm * 2 * MTILE;
+  auto kern = relpos ? attn_mem_tma_kernel<true, T> : attn_mem_tma_kernel<false, T>;
+  static bool attr[2] = {false, false};
+  if (!attr[relpos ? 1 : 0]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         511 + 3 * SLOTS * DH * 2 + MEM_SLOTS_MAX * 2 * MTILE);
+    if (e != cudaSuccess) return e;
+    attr[relpos ? 1 : 0] = true;
+  }
+  const dim3 grid(nwy * nwx, heads, B);
+  return launch_pdl(kern, grid, dim3(TMA_THREADS), (size_t)smem, st, map, v_in, o, v_out, Ht, Wt, d, offset, nwx,
+                    tab ? *tab : none, mm, off_kv, off_mask, otab, out ? 1 : 0, relpos, err);
 }
 
 #define INSTANTIATE(T)                                                                                              \
   template cudaError_t launch_attention_tc<T>(const T*, const uint8_t*, T*, uint8_t*, int, int, int, int, int, int,  \
                                               cudaStream_t, const float*, int*);                                    \
   template cudaError_t launch_attention_tc_mem<T>(const T*, const uint8_t*, T*, uint8_t*, int, int, int, int, int,   \
-                                                  int, const MemTab*, int, size_t, size_t, cudaStream_t,            \
-                                                  const float*, int*);
+                                                  int, const MemTab*, int, size_t, size_t, uint8_t* const*,         \
+                                                  cudaStream_t, const float*, int*);
 INSTANTIATE(bf16)
 INSTANTIATE(f16)
 #undef INSTANTIATE
