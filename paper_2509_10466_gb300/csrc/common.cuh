@@ -29,7 +29,8 @@ enum Epi {
   EPI_BIAS_GELU = 1,   // C = gelu(acc + bias)               (output type T)
   EPI_BIAS_RESID = 2,  // C(f32) = resid(f32) + acc + bias   (C may alias resid)
   EPI_NONE = 3,        // C(f32) = acc
-  EPI_RESID_LN = 4     // C(f32) = resid + acc + bias, and LayerNorm(C row) -> bf16 (N == tile width)
+  EPI_RESID_LN = 4,    // C(f32) = resid + acc + bias, and LayerNorm(C row) -> bf16 (N == tile width)
+  EPI_BIAS_F32 = 5     // C(f32) = acc + bias
 };
 
 // INPAINT_OK for cudaSuccess; otherwise records `e` as the calling host thread's last CUDA
@@ -190,6 +191,12 @@ cudaError_t launch_gemm_f32(const float* A, int lda, const float* Bm, int ldb, f
 template <typename T>
 cudaError_t launch_gemm_tc(const T* A, const T* Bt, void* C, int ldc, int M, int N, int K,
                            int epi, const float* bias, const float* resid, int* err, cudaStream_t st);
+
+// Split-K form (FP32 partial products): C holds `splits` slices of round_up(M, 128) rows x N
+// (row pitch N); slice s = A[:, ks .. ke) . Bt[:, ks .. ke)^T over its share of the K
+// blocks of 64, to be summed in a fixed order.  1 <= splits <= K / 64.
+cudaError_t launch_gemm_tc_splitk(const bf16* A, const bf16* Bt, float* C, int M, int N, int K, int splits, int* err,
+                                  cudaStream_t st);
 
 // Residual epilogue that also writes LayerNorm(x) (in T) of each finished row: X is
 // updated in place (X = X + A.Bt^T + bias) and ln_out = LN(X; ln_g, ln_b).  N must be

@@ -41,6 +41,59 @@ __global__ void gelu_bwd_kernel(const float* __restrict__ z, float* __restrict__
     g[i] *= gelu_grad(z[i]);
 }
 
+// FP32 products on the tensor cores, accurate to about 1e-5: a value x is split into hi =
+// bf16(x) and lo = bf16(x - hi) (x = hi + lo within 2^-17 |x|), and A . B^T is taken as
+// Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T (the dropped Alo Blo^T is below 2^-16 of a product)
+// in ONE bf16 GEMM with FP32 accumulation over a tripled K: A' = [Ahi | Ahi | Alo],
+// B' = [Bhi | Blo | Bhi].
+// split3_kernel writes such a K-major operand from FP32 X [R][C] (row pitch ld):
+// TRANS = false: out [Ro][3 Kp], row r = row r of X, K along C (Ro >= R, Kp >= C);
+// TRANS = true:  out [Ro][3 Kp], row r = column r of X, K along R (Ro >= C, Kp >= R);
+// part p of a row at columns p Kp .. p Kp + Kp - 1 (b_side: hi, lo, hi; else hi, hi, lo);
+// padding rows and columns are zero.  32 x 32 tiles through shared memory.
+template <bool TRANS>
+__global__ void __launch_bounds__(256) split3_kernel(const float* __restrict__ X, int R, int C, int ld, int Ro,
+                                                     int Kp, int b_side, bf16* __restrict__ out) {
+  __shared__ float t[32][33];
+  const int o0 = blockIdx.y * 32, k0 = blockIdx.x * 32;  // output rows, K positions
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    float v = 0.f;
+    if (TRANS) {  // tile rows = K (rows of X), columns = output rows (columns of X): coalesced reads
+      const int r = k0 + i, cc = o0 + threadIdx.x;
+      if (r < R && cc < C) v = X[(size_t)r * ld + cc];
+      t[i][threadIdx.x] = v;
+    } else {
+      const int r = o0 + i, cc = k0 + threadIdx.x;
+      if (r < R && cc < C) v = X[(size_t)r * ld + cc];
+      t[threadIdx.x][i] = v;  // t[k][o]
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int orow = o0 + i, k = k0 + threadIdx.x;
+    if (orow >= Ro || k >= Kp) continue;
+    const float v = t[threadIdx.x][i];  // X value for (output row orow, K position k)
+    const bf16 hi = __float2bfloat16_rn(v);
+    const bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    bf16* row = out + (size_t)orow * 3 * Kp;
+    row[k] = hi;
+    row[Kp + k] = b_side ? lo : hi;
+    row[2 * (size_t)Kp + k] = b_side ? hi : lo;
+  }
+}
+
+// dst[i][j] = sum_s part[s][i][j], s ascending, for i < m, j < n (slices of m_pad x n_pad).
+__global__ void reduce_part_kernel(const float* __restrict__ part, int splits, int m, int n, int m_pad, int n_pad,
+                                   float* __restrict__ dst) {
+  const size_t total = (size_t)m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    float acc = 0.f;
+    for (int sp = 0; sp < splits; ++sp) acc += part[((size_t)sp * m_pad + i) * n_pad + j];
+    dst[e] = acc;
+  }
+}
+
 // out[i] = sum_s parts[s*n + i], s ascending.
 __global__ void reduce_splits_kernel(const float* __restrict__ parts, int splits, size_t n, float* __restrict__ out) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -364,7 +417,6 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   const int Ht = Hp / 4, Wt = Wp / 4, Nt = Ht * Wt, M = B * Nt;
   const int d = c->d, hid = c->hid, L = c->L, c1 = c->c1, c2 = c->c2;
   const size_t P1 = (size_t)B * 4 * Nt, P2 = (size_t)B * 16 * Nt;   // decoder stage-1 / stage-2 pixels
-  const int SPLIT_MAX = 64;
   const size_t wmax = std::max({(size_t)d * 3 * d, (size_t)d * hid, (size_t)c1 * d, (size_t)c2 * c1, (size_t)d * 64,
                                 (size_t)3 * c2});
   const size_t im2 = std::max({P2 * c2, P2 * c1, P1 * d, (size_t)M * 64});
@@ -382,10 +434,24 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   const size_t oGO = take((size_t)M * d * 4), oGYX = take((size_t)M * d * 4);
   const size_t oZ1 = take(P1 * c1 * 4), oF1 = take(P1 * c1 * 4), oZ2 = take(P2 * c2 * 4), oF2 = take(P2 * c2 * 4);
   const size_t oGP = take(P2 * 3 * 4), oGF2 = take(P2 * c2 * 4), oGU1 = take(P2 * c1 * 4), oGF1 = take(P1 * c1 * 4);
-  const size_t oGU0 = take(P1 * d * 4), oIM = take(im2 * 4), oPART = take((size_t)SPLIT_MAX * wmax * 4);
+  const size_t oGU0 = take(P1 * d * 4), oIM = take(im2 * 4);
   const size_t oCS = take((size_t)CH * nmax * 4), oWF = take((size_t)9 * wmax * 4), oTAP = take((size_t)9 * wmax * 4);
   const int nw_max = ((Ht + 4 + WS - 1) / WS) * ((Wt + 4 + WS - 1) / WS);  // windows of the offset grid (the larger)
   const size_t oRP = take(c->cfg.pos_bias ? (size_t)B * nw_max * c->heads * 225 * 4 : 256);
+  // split operands of the tensor-core products (bf16, three parts along K) and their
+  // split-K partial sums
+  auto r64 = [](size_t v) { return (v + 63) / 64 * 64; };
+  auto r128 = [](size_t v) { return (v + 127) / 128 * 128; };
+  const size_t splitA = 3 * std::max({(size_t)hid * r64(M), (size_t)d * r64(M), (size_t)3 * d * r64(M),
+                                      (size_t)c2 * r64(P2), (size_t)c1 * r64(P1), (size_t)3 * r64(P2),
+                                      (size_t)M * r64(3 * d), (size_t)M * r64(hid)});
+  const size_t splitB = 3 * std::max({r64(hid) * r64(M), r64(3 * d) * r64(M), r64(c1) * r64(P2),
+                                      r64(d) * r64(P1), r64(c2) * r64(P2), (size_t)64 * r64(M),
+                                      r64(d) * r64(hid), r64(hid) * r64(d), r64(d) * r64(3 * d)});
+  constexpr int TC_SPLIT_MAX = 32;
+  const size_t pmax = std::max({r128(d) * r64(3 * d), r128(d) * r64(hid), r128(hid) * r64(d), r128(c1) * r64(d),
+                                r128(c2) * r64(c1), r128(3) * r64(c2), r128(d) * 64});
+  const size_t oSA = take(splitA * 2), oSB = take(splitB * 2), oTP = take((size_t)TC_SPLIT_MAX * pmax * 4);
   int rc = grow(&c->bws, &c->bws_bytes, q, c, c->arena_bytes + c->stage_bytes);
   if (rc != INPAINT_OK) return rc;
   uint8_t* ws = c->bws;
@@ -395,7 +461,7 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   float *y1 = F(oY1), *qkv = F(oQKV), *ao = F(oO), *xm = F(oXM), *y2 = F(oY2), *a = F(oA), *hh = F(oH);
   float *gx = F(oGX), *gxm = F(oGXM), *gh = F(oGH), *gy = F(oGY), *gqkv = F(oGQKV), *go = F(oGO), *gyx = F(oGYX);
   float *z1 = F(oZ1), *f1 = F(oF1), *z2 = F(oZ2), *f2 = F(oF2), *gp = F(oGP), *gf2 = F(oGF2), *gu1 = F(oGU1);
-  float *gf1 = F(oGF1), *gu0 = F(oGU0), *im = F(oIM), *part = F(oPART), *cs = F(oCS), *wf = F(oWF), *tap = F(oTAP);
+  float *gf1 = F(oGF1), *gu0 = F(oGU0), *im = F(oIM), *cs = F(oCS), *wf = F(oWF), *tap = F(oTAP);
   float* rpart = F(oRP);
   const float* w = c->w32;
   auto Xl = [&](int l) { return X + (size_t)l * M * d; };
@@ -412,16 +478,40 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
     { auto ls = K(K_OTHER); reduce_splits_kernel<<<grid1d(n), 256, 0, st>>>(cs, chunks, (size_t)n, dst); }
     ok(cudaGetLastError());
   };
-  // dst[m][n] = sum_r A[r][m] * G[r][n]  (weight gradient X^T G), deterministic split-K
-  auto wgrad = [&](const float* A, int lda, int m, const float* G, int ldg, int n, int rows, float* dst) {
-    int splits = std::min(SPLIT_MAX, std::max(1, rows / 2048));
-    splits = gemm_split_count(rows, splits);
-    { auto ls = K(K_OTHER); ok(launch_gemm_f32_ex(true, false, A, lda, G, ldg, part, n, m, n, rows, splits, EPI_NONE, nullptr, nullptr, st)); }
-    { auto ls = K(K_OTHER); reduce_splits_kernel<<<grid1d((size_t)m * n), 256, 0, st>>>(part, splits, (size_t)m * n, dst); }
+  bf16* sA = reinterpret_cast<bf16*>(ws + oSA);
+  bf16* sB = reinterpret_cast<bf16*>(ws + oSB);
+  float* tpart = F(oTP);
+  auto split3 = [&](bool trans, const float* X, int R, int C, int ld, int Ro, int Kp, bool b_side, bf16* out) {
+    auto ls = K(K_OTHER);
+    const dim3 grid(cdiv(Kp, 32), cdiv(Ro, 32));
+    if (trans) split3_kernel<true><<<grid, dim3(32, 8), 0, st>>>(X, R, C, ld, Ro, Kp, b_side ? 1 : 0, out);
+    else split3_kernel<false><<<grid, dim3(32, 8), 0, st>>>(X, R, C, ld, Ro, Kp, b_side ? 1 : 0, out);
     ok(cudaGetLastError());
   };
-  // out[M][n] = G[M][k] . Wt^T where Wt is [n][k] row-major (a linear weight [in=n][out=k])
+  // dst[m][n] = sum_r A[r][m] * G[r][n]  (weight gradient X^T G) on the tensor cores, split-K
+  // over the rows with a fixed-order reduction
+  auto wgrad = [&](const float* A, int lda, int m, const float* G, int ldg, int n, int rows, float* dst) {
+    const int Kp = (int)r64(rows), n_pad = (int)r64(n), m_pad = (int)r128(m);
+    split3(true, A, rows, m, lda, m, Kp, false, sA);
+    split3(true, G, rows, n, ldg, n_pad, Kp, true, sB);
+    const int bn = n_pad % 256 == 0 ? 256 : (n_pad % 128 == 0 ? 128 : 64);
+    const int tiles = (m_pad / 128) * (n_pad / bn);
+    const int splits = std::max(1, std::min({TC_SPLIT_MAX, 3 * Kp / 64, (2 * 152 + tiles - 1) / tiles}));
+    { auto ls = K(K_OTHER); ok(launch_gemm_tc_splitk(sA, sB, tpart, m, n_pad, 3 * Kp, splits, c->dev_err, st)); }
+    { auto ls = K(K_OTHER); reduce_part_kernel<<<grid1d((size_t)m * n), 256, 0, st>>>(tpart, splits, m, n, m_pad, n_pad, dst); }
+    ok(cudaGetLastError());
+  };
+  // out[M][n] = G[M][k] . Wt^T where Wt is [n][k] row-major (a linear weight [in=n][out=k]):
+  // on the tensor cores when n is a multiple of 64 (the GEMM's tile width), else FP32 SIMT
   auto dgrad = [&](const float* G, int k, const float* Wm, int n, float* out) {
+    if (n % 64 == 0) {
+      const int Kp = (int)r64(k);
+      split3(false, G, M, k, k, M, Kp, false, sA);
+      split3(false, Wm, n, k, k, n, Kp, true, sB);
+      auto ls = K(K_OTHER);
+      ok(launch_gemm_tc<bf16>(sA, sB, out, n, M, n, 3 * Kp, EPI_NONE, nullptr, nullptr, c->dev_err, st));
+      return;
+    }
     auto ls = K(K_OTHER);
     ok(launch_gemm_f32_ex(false, true, G, k, Wm, k, out, n, M, n, k, 1, EPI_NONE, nullptr, nullptr, st));
   };
@@ -452,19 +542,35 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
     colsum(gyx, M, d, gw + gofs);
     colsum(gyv, M, d, gw + bofs);
   };
+  // C[M][N] = epi(X[M][K] . Wl + bias) for a linear weight Wl [K][N] (in, out): on the tensor
+  // cores (split products, FP32 epilogue) when N is a multiple of 64, else FP32 SIMT
+  auto linear = [&](int cls, const float* Xa, int Kd, const float* Wl, int N, float* C, int epi, const float* bias,
+                    const float* resid) {
+    if (N % 64 == 0) {
+      const int Kp = (int)r64(Kd);
+      split3(false, Xa, M, Kd, Kd, M, Kp, false, sA);
+      split3(true, Wl, Kd, N, N, N, Kp, true, sB);  // Wl^T: row n = column n of Wl, K along the inputs
+      auto ls = K(cls);
+      ok(launch_gemm_tc<bf16>(sA, sB, C, N, M, N, 3 * Kp, epi == EPI_BIAS ? EPI_BIAS_F32 : epi, bias, resid,
+                              c->dev_err, st));
+      return;
+    }
+    auto ls = K(cls);
+    ok(launch_gemm_f32(Xa, Kd, Wl, N, C, N, M, N, Kd, epi, bias, resid, st));
+  };
   // block l forward from X[l]; keeps y1, qkv, o, xm, y2, a, h; writes X[l+1] when `out`
   auto block_fwd = [&](int l, bool out) {
     const BlockOff& bo = o.blk[l];
     const int offset = (c->cfg.shift && (l & 1)) ? 4 : 0;
     { auto ls = K(K_LN); ok(launch_layernorm<float>(Xl(l), w + bo.ln1g, w + bo.ln1b, y1, M, d, st)); }
-    { auto ls = K(K_QKV); ok(launch_gemm_f32(y1, d, w + bo.qkvw, 3 * d, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, w + bo.qkvb, nullptr, st)); }
+    linear(K_QKV, y1, d, w + bo.qkvw, 3 * d, qkv, EPI_BIAS, w + bo.qkvb, nullptr);
     const float* rp = c->cfg.pos_bias ? w + bo.relpos : nullptr;
     { auto ls = K(K_ATTN); ok(launch_attention<float>(qkv, masks + (size_t)l * M, ao, masks + (size_t)(l + 1) * M, B, Ht, Wt, d, c->heads, offset, st, rp)); }
-    { auto ls = K(K_PROJ); ok(launch_gemm_f32(ao, d, w + bo.projw, d, xm, d, M, d, d, EPI_BIAS_RESID, w + bo.projb, Xl(l), st)); }
+    linear(K_PROJ, ao, d, w + bo.projw, d, xm, EPI_BIAS_RESID, w + bo.projb, Xl(l));
     { auto ls = K(K_LN); ok(launch_layernorm<float>(xm, w + bo.ln2g, w + bo.ln2b, y2, M, d, st)); }
-    { auto ls = K(K_FC1); ok(launch_gemm_f32(y2, d, w + bo.fc1w, hid, a, hid, M, hid, d, EPI_BIAS, w + bo.fc1b, nullptr, st)); }
+    linear(K_FC1, y2, d, w + bo.fc1w, hid, a, EPI_BIAS, w + bo.fc1b, nullptr);
     { auto ls = K(K_OTHER); gelu_fwd_kernel<<<grid1d((size_t)M * hid), 256, 0, st>>>(a, hh, (size_t)M * hid); }
-    if (out) { auto ls = K(K_FC2); ok(launch_gemm_f32(hh, hid, w + bo.fc2w, d, Xl(l + 1), d, M, d, hid, EPI_BIAS_RESID, w + bo.fc2b, xm, st)); }
+    if (out) linear(K_FC2, hh, hid, w + bo.fc2w, d, Xl(l + 1), EPI_BIAS_RESID, w + bo.fc2b, xm);
     ok(cudaGetLastError());
   };
 

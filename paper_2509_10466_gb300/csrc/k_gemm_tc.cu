@@ -64,6 +64,9 @@ struct GemmArgs {
   const float* ln_b;
   void* ln_out;
   int* err;
+  int splits;  // split-K (EPI_NONE only): work item = (tile, split), split s sums k-blocks
+               // [s nk / splits, (s + 1) nk / splits) into rows s * m_pad + m of C
+  int m_pad;
 };
 
 // scalar loads: parameter vectors sit at any offset of the weight blob
@@ -102,7 +105,17 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = args.M, N = args.N;
-  const int tiles_n = N / BN, tiles = ((M + BM - 1) / BM) * tiles_n, nk = args.K / BK;
+  const int splits = args.splits > 1 ? args.splits : 1;
+  const int tiles_n = N / BN, tiles = ((M + BM - 1) / BM) * tiles_n * splits, nk = args.K / BK;
+  // work item -> output tile (N fastest, so consecutive CTAs share A rows in L2), split, k-blocks
+  auto item = [&](int w, int& m0, int& n0, int& sp, int& kb0, int& kb1) {
+    const int tt = w / splits;
+    sp = w - tt * splits;
+    m0 = (tt / tiles_n) * BM;
+    n0 = (tt % tiles_n) * BN;
+    kb0 = (int)((long long)sp * nk / splits);
+    kb1 = (int)((long long)(sp + 1) * nk / splits);
+  };
   int* err = args.err;
 
   if (threadIdx.x == 0) {
@@ -136,8 +149,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       uint32_t g = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        int m0, n0, sp, kb0, kb1;
+        item(tile, m0, n0, sp, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = g % S;
           if (g >= (uint32_t)S && !tc::mbar_wait(&empty[s], ((g / S) & 1) ^ 1, abort_flag)) {
             ok = false;
@@ -168,7 +182,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (use >= 1 && !tc::mbar_wait(&acc_empty[acc], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
         tc::fence_after_sync();
         const uint32_t dtm = tmem_base + acc * BN;
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        int m0, n0, sp, kb0, kb1;
+        item(tile, m0, n0, sp, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = g % S;
           if (!tc::mbar_wait(&full[s], (g / S) & 1, abort_flag)) { ok = false; break; }
           tc::fence_after_sync();
@@ -177,7 +193,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
           const uint64_t bd = tc::desc_kmajor_sw128(sa + Cfg::A_BYTES);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
-            tc::mma_f16(dtm, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
+            tc::mma_f16(dtm, ad + 2 * kk, bd + 2 * kk, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
           tc::mma_commit(&empty[s]);
         }
         if (ok) tc::mma_commit(&acc_full[acc]);
@@ -202,9 +218,11 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     uint32_t i = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++i) {
       const uint32_t acc = i & 1, use = i >> 1;
-      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      int m0, n0, sp, kb0, kb1;
+      item(tile, m0, n0, sp, kb0, kb1);
       const int row0 = m0 + quarter * 32;    // this warp's 32 rows; the thread owns row0 + lane
       const int nvalid = M - row0;
+      const int crow0 = sp * args.m_pad + row0;  // the row in C (split slices of m_pad rows)
       if (resid && lane < nvalid)  // the residual rows into L2 while the tile's MMAs run
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(args.resid + (size_t)(row0 + lane) * args.ldc +
                                                                         n0 + c_lo),
@@ -236,7 +254,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (epi == EPI_NONE) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = __uint_as_float(r[j]);
-          rows::store32_f32_async(&tmC, st, col, row0, nvalid, lane, f);
+          rows::store32_f32_async(&tmC, st, col, crow0, nvalid, lane, f);
           continue;
         }
         if (bias_smem) {
@@ -260,6 +278,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             for (int j = 0; j < 32; ++j) f[j] = gelu_as(f[j]);
           }
           rows::store32_h16_async<T>(&tmC, st, col, row0, nvalid, lane, f);
+        } else if (epi == EPI_BIAS_F32) {
+          rows::store32_f32_async(&tmC, st, col, row0, nvalid, lane, f);
         } else {  // residual (+ LayerNorm statistics; x stays in TMEM for the normalisation)
 #pragma unroll
           for (int j = 0; j < 32; ++j) f[j] = rv[j] + f[j];
@@ -407,13 +427,15 @@ cudaError_t launch_bn(const T* A, const T* Bt, const GemmArgs& args, cudaStream_
   CUtensorMap ma, mb;
   if (!make_map_2d(&ma, dt, A, (uint64_t)args.K, (uint64_t)args.M, BK, BM)) return cudaErrorInvalidValue;
   if (!make_map_2d(&mb, dt, Bt, (uint64_t)args.K, (uint64_t)args.N, BK, BN)) return cudaErrorInvalidValue;
-  const int tiles = ((args.M + BM - 1) / BM) * (args.N / BN);
+  const int tiles = ((args.M + BM - 1) / BM) * (args.N / BN) * (args.splits > 1 ? args.splits : 1);
   const int grid = tiles < num_sms() ? tiles : num_sms();
   // outputs: C (f32 for the residual epilogues and EPI_NONE, else T) and the LayerNorm output
   CUtensorMap mc, ml;
-  const bool c32 = args.epi == EPI_NONE || args.epi == EPI_BIAS_RESID || args.epi == EPI_RESID_LN;
+  const bool c32 = args.epi == EPI_NONE || args.epi == EPI_BIAS_RESID || args.epi == EPI_RESID_LN ||
+                   args.epi == EPI_BIAS_F32;
   if ((reinterpret_cast<uintptr_t>(args.C) & 15) || (args.ldc * (c32 ? 4 : 2)) % 16) return cudaErrorInvalidValue;
-  if (!make_store_map(&mc, args.C, c32, dt, (uint64_t)args.N, (uint64_t)args.M, (uint64_t)args.ldc))
+  const uint64_t c_rows = args.splits > 1 ? (uint64_t)args.splits * args.m_pad : (uint64_t)args.M;
+  if (!make_store_map(&mc, args.C, c32, dt, (uint64_t)args.N, c_rows, (uint64_t)args.ldc))
     return cudaErrorInvalidValue;
   ml = mc;
   if (args.epi == EPI_RESID_LN &&
@@ -430,6 +452,8 @@ cudaError_t launch_any(const T* A, const T* Bt, const GemmArgs& a, cudaStream_t 
   if (a.M <= 0 || a.N <= 0 || a.K <= 0 || a.K % BK || a.N % 64 || a.ldc % 8) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt)) & 15) return cudaErrorInvalidValue;
   if (a.epi != EPI_NONE && !a.bias) return cudaErrorInvalidValue;
+  if (a.splits > 1 && (a.epi != EPI_NONE || a.m_pad < (a.M + BM - 1) / BM * BM || a.splits > a.K / BK))
+    return cudaErrorInvalidValue;
   if (a.epi == EPI_RESID_LN) {  // a whole row per tile
     if (a.N == 256) return launch_bn<256, T>(A, Bt, a, st);
     if (a.N == 128) return launch_bn<128, T>(A, Bt, a, st);
@@ -448,15 +472,22 @@ bool gemm_tc_ln_supported(int N) { return N == 64 || N == 128 || N == 256; }
 template <typename T>
 cudaError_t launch_gemm_tc(const T* A, const T* Bt, void* C, int ldc, int M, int N, int K, int epi,
                            const float* bias, const float* resid, int* err, cudaStream_t st) {
-  GemmArgs a{C, ldc, M, N, K, epi, bias, resid, nullptr, nullptr, nullptr, err};
+  GemmArgs a{C, ldc, M, N, K, epi, bias, resid, nullptr, nullptr, nullptr, err, 1, 0};
   return launch_any<T>(A, Bt, a, st);
 }
 
 template <typename T>
 cudaError_t launch_gemm_tc_resid_ln(const T* A, const T* Bt, float* X, int M, int N, int K, const float* bias,
                                     const float* ln_g, const float* ln_b, T* ln_out, int* err, cudaStream_t st) {
-  GemmArgs a{X, N, M, N, K, EPI_RESID_LN, bias, X, ln_g, ln_b, ln_out, err};
+  GemmArgs a{X, N, M, N, K, EPI_RESID_LN, bias, X, ln_g, ln_b, ln_out, err, 1, 0};
   return launch_any<T>(A, Bt, a, st);
+}
+
+cudaError_t launch_gemm_tc_splitk(const bf16* A, const bf16* Bt, float* C, int M, int N, int K, int splits, int* err,
+                                  cudaStream_t st) {
+  const int m_pad = (M + BM - 1) / BM * BM;
+  GemmArgs a{C, N, M, N, K, EPI_NONE, nullptr, nullptr, nullptr, nullptr, nullptr, err, splits, m_pad};
+  return launch_any<bf16>(A, Bt, a, st);
 }
 
 #define INSTANTIATE(T)                                                                                           \
