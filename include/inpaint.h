@@ -239,10 +239,11 @@ INPAINT_API int inpaint_sync(inpaint_ctx* ctx, void* stream, int timeout_ms);
  * 0 embed, 1 layernorm, 2 qkv gemm, 3 attention, 4 proj gemm, 5 fc1 gemm, 6 fc2 gemm,
  * 7 decoder stage 1, 8 decoder stage 2, 9 head + composite, 10 other, 11 fused
  * projection + MLP (proj + residual + LN2 + fc1 + GELU + fc2 + residual + LayerNorm in
- * one kernel), 12 point cloud, 13 splat.
+ * one kernel), 12 point cloud, 13 splat, 14 fused QKV + window attention (spatial blocks
+ * of the 16-bit forms).
  * inpaint_profile_read synchronizes and returns total milliseconds and launch
  * counts per class (arrays of INPAINT_PROFILE_CLASSES), then clears them. */
-#define INPAINT_PROFILE_CLASSES 14
+#define INPAINT_PROFILE_CLASSES 15
 INPAINT_API int inpaint_profile_enable(inpaint_ctx* ctx, int on);
 INPAINT_API int inpaint_profile_read(inpaint_ctx* ctx, float* ms, int64_t* launches);
 

@@ -18,9 +18,10 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libinpaint
 _lib = None
 
 INPAINT_OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_STATE, E_DEVICE = range(7)
-PROFILE_CLASSES = 14
+PROFILE_CLASSES = 15
 PROFILE_NAMES = ("embed", "layernorm", "qkv_gemm", "attention", "proj_gemm", "fc1_gemm", "fc2_gemm",
-                 "decoder1", "decoder2", "head_composite", "other", "proj_mlp_fused", "point_cloud", "splat")
+                 "decoder1", "decoder2", "head_composite", "other", "proj_mlp_fused", "point_cloud", "splat",
+                 "qkv_attention")
 
 
 class InpaintError(RuntimeError):

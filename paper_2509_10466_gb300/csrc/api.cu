@@ -355,7 +355,13 @@ int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, co
       const A* wfc2 = wfc1 + (size_t)c->hid * d;
       if (!ln_ready) { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<A>(tok, c->w32 + b.ln1g, c->w32 + b.ln1b, ln, M, d, st))); }
       const float* fold = c->fold_ln ? c->fold_b + (size_t)l * (3 * d + c->hid) : nullptr;
-      { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, fold ? fold : c->w32 + b.qkvb, nullptr, err, st))); }
+      const float* qkv_bias = fold ? fold : c->w32 + b.qkvb;
+      if (!temporal && qkv_attn_supported(d, c->heads)) {
+        // spatial block: Q, K, V computed and consumed on chip, per pair of windows
+        LaunchScope ls(c, st, K_QKV_ATTN);
+        TRY(cuda_err(launch_qkv_attn<A>(ln, wqkv, qkv_bias, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, rp, err, st)));
+      } else {
+      { LaunchScope ls(c, st, K_QKV); TRY(cuda_err(launch_gemm_tc(ln, wqkv, qkv, 3 * d, M, 3 * d, d, EPI_BIAS, qkv_bias, nullptr, err, st))); }
       if (temporal) {
         LaunchScope ls(c, st, K_ATTN);
         // the kernel also records this block's part of each frame's memory tensor
@@ -363,6 +369,7 @@ int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, co
       } else {
         LaunchScope ls(c, st, K_ATTN);
         TRY(cuda_err(launch_attention_tc(qkv, v_in, ao, v_out, p.B, p.Ht, p.Wt, d, c->heads, offset, st, rp, err)));
+      }
       }
       if (c->fold_ln) {
         // projection, residual, LN2 and the whole MLP in one kernel: only the attention

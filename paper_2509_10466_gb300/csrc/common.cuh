@@ -17,7 +17,7 @@ typedef __half f16;
 // Kernel-class ids for event timing (match INPAINT_PROFILE_CLASSES in inpaint.h).
 enum KClass {
   K_EMBED = 0, K_LN = 1, K_QKV = 2, K_ATTN = 3, K_PROJ = 4, K_FC1 = 5, K_FC2 = 6,
-  K_DEC1 = 7, K_DEC2 = 8, K_HEAD = 9, K_OTHER = 10, K_MLP = 11, K_CLOUD = 12, K_SPLAT = 13
+  K_DEC1 = 7, K_DEC2 = 8, K_HEAD = 9, K_OTHER = 10, K_MLP = 11, K_CLOUD = 12, K_SPLAT = 13, K_QKV_ATTN = 14
 };
 
 // Device-side error codes written into the context's error word.
@@ -232,6 +232,16 @@ template <typename T>
 cudaError_t launch_attention_tc(const T* qkv, const uint8_t* v_in, T* o, uint8_t* v_out, int B, int Ht,
                                 int Wt, int d, int heads, int offset, cudaStream_t st,
                                 const float* relpos = nullptr, int* err = nullptr);
+
+// Spatial blocks of the 16-bit forms in one kernel: y (the block's normalized rows, T
+// [B*Nt][d]) -> Q, K, V on tcgen05 (wqkv_t: W_qkv^T [3d][d] in T, bias [3d]) -> the same
+// mask-aware window attention as launch_attention_tc, writing o and v_out; Q, K, V stay
+// on chip.  Supported when d % 64 == 0, heads is even and at most 16 (d = 32 heads).
+bool qkv_attn_supported(int d, int heads);
+template <typename T>
+cudaError_t launch_qkv_attn(const T* y, const T* wqkv_t, const float* bias, const uint8_t* v_in, T* o, uint8_t* v_out,
+                            int B, int Ht, int Wt, int d, int heads, int offset, const float* relpos, int* err,
+                            cudaStream_t st);
 
 // Temporal blocks: as above, plus the keys of m memory slots.  tab->p[b*m + j] is a device
 // pointer to a previous frame's memory buffer (null = empty slot; tab null = no memory);
