@@ -170,7 +170,7 @@ def bytes_per_frame(m, H, W, act_bytes=2):
     }
 
 
-TRAFFIC_HEADERS = ("common.cuh", "tc_primitives.cuh", "warp_rows.cuh")
+TRAFFIC_HEADERS = ("common.cuh", "tc_primitives.cuh", "warp_rows.cuh", "window_attn.cuh")
 
 
 def read_traffic():
