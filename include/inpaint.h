@@ -224,7 +224,10 @@ INPAINT_API int inpaint_l1_hole_loss_noalloc(const float* out, const float* targ
  * grad_weights (device float32, num_params values, overwritten).  Recomputes the
  * forward, keeping only each block's input, and recomputes each block again during
  * the reverse sweep (per-block activation recomputation).  The token masks carry no
- * gradient.  FP32 arithmetic in either precision setting. */
+ * gradient.  FP32-accurate in every precision setting: statistics, adjoints and
+ * accumulation in FP32, every matrix product as three bf16 tensor-core products of the
+ * split x = hi + lo (hi.hi + hi.lo + lo.hi, FP32 accumulation; about 1e-5 relative per
+ * product), reduced in a fixed order (bit-reproducible). */
 INPAINT_API int inpaint_backward(inpaint_ctx* ctx, const float* x, const uint8_t* hole,
                      const float* grad_out, int B, int H, int W, float* grad_weights,
                      void* stream);
