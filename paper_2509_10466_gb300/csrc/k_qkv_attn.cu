@@ -8,8 +8,8 @@
 // pass p computes [q | k | v] of heads 2p, 2p + 1 (192 columns) for all 128 slots on
 // tcgen05 (M = 128, N = 192, FP32 accumulation in tensor memory, two accumulators so that
 // pass p + 1 runs while pass p is consumed).  Sixteen warps take the accumulator of a pass
-// (eight per head: two per TMEM lane quarter, one taking the q and k columns, the other the
-// v columns), add the bias, round to T and write the heads' Q, K, V tiles of both windows
+// (eight per head: two per TMEM lane quarter, one taking the q columns and half of the k
+// columns, the other the rest of k and the v columns), add the bias, round to T and write the heads' Q, K, V tiles of both windows
 // into shared memory in the 64-byte-swizzled layout of the TMA boxes of the separate
 // attention kernel, and run the same masked window softmax on them (one window and 16 query
 // rows per warp, mma.sync), writing the attention output rows.  Q, K and V never reach global
@@ -191,11 +191,11 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
     __syncwarp();
   } else {
     // ---- drain + attention: head hh of every pass for the eight warps of group hh; warp j
-    // of a group drains TMEM lane quarter (warp & 3), the q and k columns (j < 4) or the v
-    // columns, then runs query rows 16 (j & 3) .. + 15 of window j >> 2
+    // of a group drains TMEM lane quarter (warp & 3), the q columns and k channels 0..15
+    // (j < 4) or k channels 16..31 and the v columns, then runs query rows 16 (j & 3) ..
+    // + 15 of window j >> 2
     const int quarter = warp & 3, hh = (warp - 2) >> 3, j = (warp - 2) & 7;
     const int win = quarter >> 1, slot = 32 * (quarter & 1) + lane;  // this thread's accumulator row
-    const int part0 = j < 4 ? 0 : 2, nparts = j < 4 ? 2 : 1;
     const int awin = j >> 2, wq = j & 3;
     const int e = threadIdx.x - 64;  // slot e & 63 of window e >> 6 of a pair, for e < 128
     T* o = static_cast<T*>(args.o);
@@ -234,26 +234,34 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
         if (ok) {
           __syncwarp();
           tc::fence_after_sync();
-          const uint32_t tb = tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * 256;
-          for (int pi = 0; pi < nparts; ++pi) {
-            const int part = part0 + pi;
-            uint32_t v[32];
-            tc::tmem_ld_32x32b_x32(tb + part * 64 + hh * 32, v);
-            tc::tmem_ld_wait();
-            const float* bb = s_bias + part * d + hg * WA_DH;
-            uint8_t* row = tile(hh, win, part);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {  // 16-byte chunk c: channels 8c .. 8c + 7
-              const float4 b0 = *reinterpret_cast<const float4*>(bb + 8 * c);
-              const float4 b1 = *reinterpret_cast<const float4*>(bb + 8 * c + 4);
-              const uint4 w4 = make_uint4(
-                  H16<T>::pack2(__uint_as_float(v[8 * c + 0]) + b0.x, __uint_as_float(v[8 * c + 1]) + b0.y),
-                  H16<T>::pack2(__uint_as_float(v[8 * c + 2]) + b0.z, __uint_as_float(v[8 * c + 3]) + b0.w),
-                  H16<T>::pack2(__uint_as_float(v[8 * c + 4]) + b1.x, __uint_as_float(v[8 * c + 5]) + b1.y),
-                  H16<T>::pack2(__uint_as_float(v[8 * c + 6]) + b1.z, __uint_as_float(v[8 * c + 7]) + b1.w));
-              *reinterpret_cast<uint4*>(row + swz64(slot, c)) = w4;
-            }
+          const uint32_t tb = tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * 256 + hh * 32;
+          // 8 FP32 accumulator values + bias -> T, as 16-byte chunk c of the row of `part`
+          auto put = [&](int part, int c, const uint32_t* v) {
+            const float* bb = s_bias + part * d + hg * WA_DH + 8 * c;
+            const float4 b0 = *reinterpret_cast<const float4*>(bb);
+            const float4 b1 = *reinterpret_cast<const float4*>(bb + 4);
+            *reinterpret_cast<uint4*>(tile(hh, win, part) + swz64(slot, c)) =
+                make_uint4(H16<T>::pack2(__uint_as_float(v[0]) + b0.x, __uint_as_float(v[1]) + b0.y),
+                           H16<T>::pack2(__uint_as_float(v[2]) + b0.z, __uint_as_float(v[3]) + b0.w),
+                           H16<T>::pack2(__uint_as_float(v[4]) + b1.x, __uint_as_float(v[5]) + b1.y),
+                           H16<T>::pack2(__uint_as_float(v[6]) + b1.z, __uint_as_float(v[7]) + b1.w));
+          };
+          // 48 of the head's 96 columns each: q and the first half of k, or the second half
+          // of k and v
+          uint32_t v32[32], v16[16];
+          if (j < 4) {
+            tc::tmem_ld_32x32b_x32(tb, v32);       // q
+            tc::tmem_ld_32x32b_x16(tb + 64, v16);  // k channels 0..15
+          } else {
+            tc::tmem_ld_32x32b_x32(tb + 128, v32);     // v
+            tc::tmem_ld_32x32b_x16(tb + 64 + 16, v16);  // k channels 16..31
           }
+          tc::tmem_ld_wait();
+          const int p32 = j < 4 ? 0 : 2, c16 = j < 4 ? 0 : 2;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) put(p32, c, v32 + 8 * c);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) put(1, c16 + c, v16 + 8 * c);
           tc::fence_before_sync();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);  // the accumulator is free for pass gp + 2
