@@ -159,8 +159,12 @@ INPAINT_API int inpaint_batch_ws(inpaint_ctx* ctx, void* workspace, size_t works
                      float* pred_or_null, void* stream);
 
 /* End-to-end form with HOST buffers: copies x and hole host->device, runs
- * inpaint_batch, copies out device->host and waits for completion.  Pinned host
- * memory gives asynchronous copies; pageable memory works but is slower. */
+ * inpaint_batch, copies out device->host and waits for completion.  The copies run on a
+ * stream of the context, frame by frame, overlapped with the kernels: each frame is
+ * embedded once its inputs have landed and copied back once its output is written.
+ * The forward itself runs on `stream`, which at return has also waited for the copies.
+ * Pinned host memory gives asynchronous copies; pageable memory works but is slower.
+ * Token masks of the call are kept for inpaint_token_masks, as with inpaint_batch. */
 INPAINT_API int inpaint_batch_host(inpaint_ctx* ctx, const float* x_host, const uint8_t* hole_host,
                        int B, int H, int W, float* out_host, void* stream);
 

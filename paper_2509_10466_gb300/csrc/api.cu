@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -284,7 +285,7 @@ int prepare_layouts(inpaint_ctx* c, cudaStream_t st) {
 // type A: float for the FP32 SIMT form, bf16 or f16 for the 16-bit tensor-core forms.
 template <typename A>
 int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, const uint8_t* hole, float* out,
-                  float* pred, cudaStream_t st, const MemArgs* mem) {
+                  float* pred, cudaStream_t st, const MemArgs* mem, const FramePipe* pipe) {
   constexpr bool TC = sizeof(A) == 2;
   const Offsets& o = c->off;
   const int d = c->d, M = p.M;
@@ -293,24 +294,54 @@ int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, co
   int* err = c->dev_err;
   // 16-bit forms: the embedding also writes the first LayerNorm (block 0's LN1, or the
   // final LN when there are no blocks) straight into the 16-bit GEMM operand
-  bool ln_ready = false;
-  {
+  bool ln_ready = TC;
+  // frames f0 .. f0 + nb - 1 (the whole batch, or frame by frame behind the input copies)
+  auto embed = [&](int f0, int nb) -> int {
+    const size_t HW = (size_t)p.H * p.W, nt = (size_t)p.Ht * p.Wt;
+    const float* xf = x + f0 * 3 * HW;
+    const uint8_t* hf = hole + f0 * HW;
+    float* tf = tok + f0 * nt * d;
+    uint8_t* mf = masks + f0 * nt;
     LaunchScope ls(c, st, K_EMBED);
     if constexpr (TC) {
       // with folding, block 0's LN1 affine lives in its QKV weights: normalized rows only
       const float* g0 = c->fold_ln ? nullptr : c->w32 + (c->L ? o.blk[0].ln1g : o.lnfg);
       const float* b0 = c->fold_ln ? nullptr : c->w32 + (c->L ? o.blk[0].ln1b : o.lnfb);
+      A* lf = reinterpret_cast<A*>(ws + p.ln) + f0 * nt * d;
       if (c->embed_w16)
-        TRY(cuda_err(launch_embed_tc<A>(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, reinterpret_cast<const A*>(c->embed_w16),
-                                        c->w32 + o.embb, d, tok, masks, g0, b0, reinterpret_cast<A*>(ws + p.ln), st)));
-      else
-        TRY(cuda_err(launch_embed<A>(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks,
-                                     st, g0, b0, reinterpret_cast<A*>(ws + p.ln))));
-      ln_ready = true;
+        return cuda_err(launch_embed_tc<A>(xf, hf, nb, p.H, p.W, p.Ht, p.Wt, reinterpret_cast<const A*>(c->embed_w16),
+                                           c->w32 + o.embb, d, tf, mf, g0, b0, lf, st));
+      return cuda_err(launch_embed<A>(xf, hf, nb, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tf, mf, st, g0,
+                                      b0, lf));
     } else {
-      TRY(cuda_err(launch_embed(x, hole, p.B, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tok, masks, st)));
+      return cuda_err(launch_embed(xf, hf, nb, p.H, p.W, p.Ht, p.Wt, c->embed_wt, c->w32 + o.embb, d, tf, mf, st));
     }
+  };
+  if (pipe) {
+    for (int f = 0; f < p.B; ++f) {
+      TRY(cuda_err(cudaStreamWaitEvent(st, pipe->in_ready[f], 0)));
+      TRY(embed(f, 1));
+    }
+  } else {
+    TRY(embed(0, p.B));
   }
+  // the 3x3 head + composite + crop, for the whole batch or frame by frame (each frame's
+  // output then announced to the copy stream)
+  auto head = [&](const auto* f2) -> int {
+    using F = std::remove_cv_t<std::remove_pointer_t<decltype(f2)>>;
+    const size_t HW = (size_t)p.H * p.W, fin = (size_t)p.Hp * p.Wp * c->c2;
+    const int nf = pipe ? p.B : 1, nb = pipe ? 1 : p.B;
+    for (int f = 0; f < nf; ++f) {
+      {
+        LaunchScope ls(c, st, K_HEAD);
+        TRY(cuda_err(launch_head_composite<F>(f2 + f * fin, nb, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb,
+                                              x + f * 3 * HW, hole + f * HW, p.H, p.W, out + f * 3 * HW,
+                                              pred ? pred + f * 3 * HW : nullptr, st)));
+      }
+      if (pipe) TRY(cuda_err(cudaEventRecord(pipe->out_ready[f], st)));
+    }
+    return INPAINT_OK;
+  };
   // 16-bit forms: the LayerNorm that follows each residual update is fused into the GEMM
   // epilogue that produces it (proj -> LN2, fc2 -> next LN1 or the final LN) when a
   // tile spans the whole row; `ln_ready` tracks whether `ln` already holds the input
@@ -454,7 +485,7 @@ int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, co
       LaunchScope ls(c, st, K_DEC2);
       TRY(cuda_err(launch_upconv<A>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st)));
     }
-    { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<A>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
+    TRY(head(f2));
   } else {
     float* ln = reinterpret_cast<float*>(ws + p.ln);
     float* f1 = reinterpret_cast<float*>(ws + p.f1);
@@ -462,16 +493,16 @@ int run_forward_t(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, co
     { LaunchScope ls(c, st, K_LN); TRY(cuda_err(launch_layernorm<float>(tok, c->w32 + o.lnfg, c->w32 + o.lnfb, ln, M, d, st))); }
     { LaunchScope ls(c, st, K_DEC1); TRY(cuda_err(launch_upconv<float>(ln, p.B, p.Ht, p.Wt, d, c->dec1_wt, c->w32 + o.d1b, f1, c->c1, st))); }
     { LaunchScope ls(c, st, K_DEC2); TRY(cuda_err(launch_upconv<float>(f1, p.B, 2 * p.Ht, 2 * p.Wt, c->c1, c->dec2_wt, c->w32 + o.d2b, f2, c->c2, st))); }
-    { LaunchScope ls(c, st, K_HEAD); TRY(cuda_err(launch_head_composite<float>(f2, p.B, p.Hp, p.Wp, c->c2, c->w32 + o.hw, c->w32 + o.hb, x, hole, p.H, p.W, out, pred, st))); }
+    TRY(head(f2));
   }
   return INPAINT_OK;
 }
 
 int run_forward(inpaint_ctx* c, uint8_t* ws, const Plan& p, const float* x, const uint8_t* hole, float* out,
-                float* pred, cudaStream_t st, const MemArgs* mem = nullptr) {
-  if (!c->use_tc) return run_forward_t<float>(c, ws, p, x, hole, out, pred, st, mem);
-  if (c->fp16) return run_forward_t<f16>(c, ws, p, x, hole, out, pred, st, mem);
-  return run_forward_t<bf16>(c, ws, p, x, hole, out, pred, st, mem);
+                float* pred, cudaStream_t st, const MemArgs* mem = nullptr, const FramePipe* pipe = nullptr) {
+  if (!c->use_tc) return run_forward_t<float>(c, ws, p, x, hole, out, pred, st, mem, pipe);
+  if (c->fp16) return run_forward_t<f16>(c, ws, p, x, hole, out, pred, st, mem, pipe);
+  return run_forward_t<bf16>(c, ws, p, x, hole, out, pred, st, mem, pipe);
 }
 
 bool bad_shape(int B, int H, int W) {
@@ -539,6 +570,11 @@ void inpaint_destroy(inpaint_ctx* c) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
   }
+  for (cudaEvent_t e : c->in_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->out_ev) cudaEventDestroy(e);
+  if (c->start_ev) cudaEventDestroy(c->start_ev);
+  if (c->done_ev) cudaEventDestroy(c->done_ev);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
 }
 
@@ -748,12 +784,46 @@ int inpaint_batch_host(inpaint_ctx* c, const float* xh, const uint8_t* hh, int B
   float* xd = reinterpret_cast<float*>(c->stage);
   float* od = reinterpret_cast<float*>(c->stage + bx);
   uint8_t* hd = c->stage + 2 * bx;
-  if (cudaMemcpyAsync(xd, xh, nx * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(hd, hh, nh, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return INPAINT_E_CUDA;
-  TRY(inpaint_batch(c, xd, hd, B, H, W, od, nullptr, stream));
-  if (cudaMemcpyAsync(oh, od, nx * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return INPAINT_E_CUDA;
-  return cuda_err(cudaStreamSynchronize(st));
+  // The copies run on the context's copy stream frame by frame: frame f is embedded as
+  // soon as its inputs have landed, and its output is copied back as soon as its head
+  // kernel has written it, while the later frames' copies and kernels proceed.
+  if (!c->copy_stream) TRY(cuda_err(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)));
+  auto events = [&](std::vector<cudaEvent_t>& v) -> int {
+    while ((int)v.size() < B) {
+      cudaEvent_t e;
+      TRY(cuda_err(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)));
+      v.push_back(e);
+    }
+    return INPAINT_OK;
+  };
+  TRY(events(c->in_ev));
+  TRY(events(c->out_ev));
+  if (!c->start_ev) TRY(cuda_err(cudaEventCreateWithFlags(&c->start_ev, cudaEventDisableTiming)));
+  if (!c->done_ev) TRY(cuda_err(cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming)));
+  const Plan p = make_plan(c, B, H, W);
+  TRY(grow(&c->arena, &c->arena_bytes, p.end, c, c->stage_bytes + c->bws_bytes));
+  cudaStream_t cs = c->copy_stream;
+  // the staging buffers are free once the work already queued on `st` is done
+  TRY(cuda_err(cudaEventRecord(c->start_ev, st)));
+  TRY(cuda_err(cudaStreamWaitEvent(cs, c->start_ev, 0)));
+  const size_t HW = (size_t)H * W;
+  for (int f = 0; f < B; ++f) {
+    TRY(cuda_err(cudaMemcpyAsync(xd + f * 3 * HW, xh + f * 3 * HW, 3 * HW * 4, cudaMemcpyHostToDevice, cs)));
+    TRY(cuda_err(cudaMemcpyAsync(hd + f * HW, hh + f * HW, HW, cudaMemcpyHostToDevice, cs)));
+    TRY(cuda_err(cudaEventRecord(c->in_ev[f], cs)));
+  }
+  const FramePipe pipe{c->in_ev.data(), c->out_ev.data()};
+  c->have_masks = false;
+  TRY(run_forward(c, c->arena, p, xd, hd, od, nullptr, st, nullptr, &pipe));
+  c->last = p;
+  c->have_masks = true;
+  for (int f = 0; f < B; ++f) {
+    TRY(cuda_err(cudaStreamWaitEvent(cs, c->out_ev[f], 0)));
+    TRY(cuda_err(cudaMemcpyAsync(oh + f * 3 * HW, od + f * 3 * HW, 3 * HW * 4, cudaMemcpyDeviceToHost, cs)));
+  }
+  TRY(cuda_err(cudaEventRecord(c->done_ev, cs)));
+  TRY(cuda_err(cudaStreamWaitEvent(st, c->done_ev, 0)));  // the caller's stream sees the results
+  return cuda_err(cudaStreamSynchronize(cs));
 }
 
 int inpaint_token_masks(inpaint_ctx* c, uint8_t* host, size_t n) {

@@ -52,6 +52,15 @@ struct EventPair {
   int cls;
 };
 
+// Host-buffer calls: frame f's inputs are on the device once in_ready[f] (recorded on the
+// copy stream) completes; the forward then embeds frame by frame, and records out_ready[f]
+// on the compute stream once frame f's output is written, so that the copies overlap the
+// first and the last kernels.
+struct FramePipe {
+  const cudaEvent_t* in_ready = nullptr;
+  const cudaEvent_t* out_ready = nullptr;
+};
+
 struct inpaint_ctx {
   inpaint_config cfg;
   int d, heads, L, r, c1, c2, hid;
@@ -83,9 +92,12 @@ struct inpaint_ctx {
   // last internal-workspace forward, for inpaint_token_masks
   bool have_masks = false;
   Plan last{};
-  // host e2e staging
+  // host e2e staging, its copy stream and per-frame events
   uint8_t* stage = nullptr;
   size_t stage_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> in_ev, out_ev;
+  cudaEvent_t start_ev = nullptr, done_ev = nullptr;
   // half-resolution buffers of inpaint_fullres
   uint8_t* pp = nullptr;
   size_t pp_bytes = 0;

@@ -4,7 +4,7 @@ import pytest
 import torch
 
 from paper_2509_10466_gb300 import binding, synthetic as S
-from paper_2509_10466_gb300.config import BF16, FP32, ModelConfig, WORKLOAD_A, WORKLOAD_B
+from paper_2509_10466_gb300.config import BF16, FP16, FP32, ModelConfig, WORKLOAD_A, WORKLOAD_B
 
 from helpers import TOL_BF16, TOL_FP32, check_parity, gpu_forward, hole_rel_l2, inputs, lib, oracle_forward
 
@@ -222,6 +222,34 @@ def test_batch_ws_and_host_paths_equal_batch():
         small_ws = torch.empty(nbytes // 2, dtype=torch.uint8, device="cuda")
         with pytest.raises(binding.InpaintError):
             binding.inpaint_batch_ws(inp.ctx, small_ws, xt, ht, out2)
+    finally:
+        inp.close()
+
+
+@pytest.mark.parametrize("precision", [FP32, BF16, FP16])
+def test_host_path_copies_frame_by_frame_equal_the_device_path(precision):
+    """The host-buffer entry point copies and embeds frame by frame and copies each frame
+    back once its head kernel has written it: pageable and pinned host memory, a ragged
+    width, repeated calls and a batch size change give the device path's output bit for
+    bit, and the token masks of the call are kept."""
+    cfg = small(precision)
+    weights = S.make_weights(cfg, seed=9, perturb=True)
+    lib()
+    inp = binding.Inpainter(cfg, weights)
+    try:
+        for B, H, W in [(3, 70, 45), (1, 64, 64), (4, 64, 96)]:
+            x, hole = inputs(B, H, W, "polygons", seed=B + H)
+            ref = inp(torch.from_numpy(x).cuda(), torch.from_numpy(hole).cuda()).cpu()
+            ref_masks = inp.token_masks(B, H, W)
+            for pinned in (False, True):
+                xh, hh = torch.from_numpy(x), torch.from_numpy(hole)
+                out = torch.full(x.shape, float("nan"), dtype=torch.float32)
+                if pinned:
+                    xh, hh, out = xh.pin_memory(), hh.pin_memory(), out.pin_memory()
+                for _ in range(2):
+                    binding.inpaint_batch_host(inp.ctx, xh, hh, out)
+                    assert torch.equal(out, ref)
+                np.testing.assert_array_equal(inp.token_masks(B, H, W), ref_masks)
     finally:
         inp.close()
 
