@@ -110,9 +110,11 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
   }
 }
 
-// Tensor-core form (16-bit forms): 32 tokens per CTA (76 KB of shared memory at d = 256, so
-// three CTAs per SM).  The patch matrix P [32 tok][64] and the embedding weights [d][64]
-// are staged in shared memory in T (rows padded to 144 bytes for conflict-free
+// Tensor-core form (16-bit forms), persistent: a CTA stages the embedding weights [d][64]
+// in shared memory once and takes tiles of 32 tokens (one token row segment; 76 KB of
+// shared memory at d = 256, so three CTAs per SM), loading the next tile's pixels into
+// registers while the current tile is computed and stored.  The patch matrix P [32 tok]
+// [64] and the weights are held in T (rows padded to 144 bytes for conflict-free
 // ldmatrix); warp w computes tokens 16(w%2).. x channels (w/2)*d/4 .. with mma.sync
 // m16n8k16 (K = 64 in 4 steps, FP32 accumulate).  The tile goes through shared memory so
 // the FP32 token rows, the token mask and the fused LayerNorm are written coalesced.  The
@@ -121,12 +123,13 @@ __global__ void __launch_bounds__(256) embed_kernel(const float* __restrict__ x,
 // shared memory in a fixed order, so that the store loop has no reductions left.
 template <int D>
 struct EmbTc {
-  static constexpr int TOK = 32, KP = 72;          // tokens per CTA; padded row length (16-bit) of P and W
+  static constexpr int TOK = 32, KP = 72;          // tokens per tile; padded row length (16-bit) of P and W
   static constexpr int MT = TOK / 16, NQ = 8 / MT;  // warps: MT token tiles x NQ column parts
   static constexpr int P_BYTES = TOK * KP * 2;
   static constexpr int W_BYTES = D * KP * 2;
   static constexpr int OUT_STRIDE = D + 4;         // floats per staged output row
-  static constexpr int SMEM = P_BYTES + W_BYTES + TOK * OUT_STRIDE * 4 + TOK * 4 /*known*/ + 2 * NQ * TOK * 4 /*row statistics*/;
+  static constexpr int SMEM = P_BYTES + W_BYTES + TOK * OUT_STRIDE * 4 + TOK * 4 * 4 /*known, per pixel row*/ +
+                              2 * NQ * TOK * 4 /*row statistics*/;
 };
 
 __device__ __forceinline__ void ldsm_x4_e(uint32_t (&r)[4], const void* p) {
@@ -139,9 +142,50 @@ __device__ __forceinline__ void ldsm_x2_e(uint32_t (&r)[2], const void* p) {
   const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
 }
+
+// One pixel row (4 pixels) of one token: RGB and the known-pixel bits (bit j: pixel j known).
+struct PatchRow {
+  float r[4], g[4], b[4];
+  uint32_t known;
+};
+
+// Pixel row pr of token t of frame b (zeros and no known pixel outside the frame or the grid).
+__device__ __forceinline__ PatchRow load_patch_row(const float* __restrict__ x, const uint8_t* __restrict__ hole,
+                                                   int b, int t, int pr, int H, int W, int Wt, int Nt, bool vec) {
+  PatchRow v;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v.r[j] = v.g[j] = v.b[j] = 0.f;
+  v.known = 0;
+  if (t >= Nt) return v;
+  const int ty = t / Wt, tx = t - (t / Wt) * Wt;
+  const int y = ty * 4 + pr, xx0 = tx * 4;
+  if (y >= H) return v;
+  const size_t HW = (size_t)H * W, q = (size_t)y * W + xx0;
+  const float* xb = x + (size_t)b * 3 * HW + q;
+  const uint8_t* hb = hole + (size_t)b * HW + q;
+  if (vec && xx0 + 3 < W) {  // 16-byte aligned rows: vector loads
+    const float4 r4 = *reinterpret_cast<const float4*>(xb);
+    const float4 g4 = *reinterpret_cast<const float4*>(xb + HW);
+    const float4 b4 = *reinterpret_cast<const float4*>(xb + 2 * HW);
+    const uchar4 h4 = *reinterpret_cast<const uchar4*>(hb);
+    v.r[0] = r4.x; v.r[1] = r4.y; v.r[2] = r4.z; v.r[3] = r4.w;
+    v.g[0] = g4.x; v.g[1] = g4.y; v.g[2] = g4.z; v.g[3] = g4.w;
+    v.b[0] = b4.x; v.b[1] = b4.y; v.b[2] = b4.z; v.b[3] = b4.w;
+    v.known = (h4.x == 0) | ((h4.y == 0) << 1) | ((h4.z == 0) << 2) | ((h4.w == 0) << 3);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (xx0 + j < W) {
+        v.r[j] = xb[j]; v.g[j] = xb[HW + j]; v.b[j] = xb[2 * HW + j];
+        v.known |= (uint32_t)(hb[j] == 0) << j;
+      }
+  }
+  return v;
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__ x, const uint8_t* __restrict__ hole,
-                                                       int H, int W, int Ht, int Wt, const T* __restrict__ we16,
+                                                       int B, int H, int W, int Ht, int Wt, const T* __restrict__ we16,
                                                        const float* __restrict__ be, float* __restrict__ tok,
                                                        uint8_t* __restrict__ v0, const float* __restrict__ ln_g,
                                                        const float* __restrict__ ln_b, T* __restrict__ ln_out) {
@@ -150,160 +194,141 @@ __global__ void __launch_bounds__(256) embed_tc_kernel(const float* __restrict__
   T* P = reinterpret_cast<T*>(esm);                                         // [TOK][KP]
   T* Ws = reinterpret_cast<T*>(esm + C::P_BYTES);                           // [D][KP]
   float* O = reinterpret_cast<float*>(esm + C::P_BYTES + C::W_BYTES);      // [TOK][OUT_STRIDE]
-  int* known = reinterpret_cast<int*>(esm + C::P_BYTES + C::W_BYTES + C::TOK * C::OUT_STRIDE * 4);
-  float* red = reinterpret_cast<float*>(known + C::TOK);  // [TOK][NQ column parts] row sums
-  float* red2 = red + C::NQ * C::TOK;                      // [TOK][NQ] squared deviations
-  const int b = blockIdx.y, t0 = blockIdx.x * C::TOK, Nt = Ht * Wt;
-  const size_t HW = (size_t)H * W;
+  uint32_t* known = reinterpret_cast<uint32_t*>(esm + C::P_BYTES + C::W_BYTES + C::TOK * C::OUT_STRIDE * 4);  // [TOK][4]
+  float* red = reinterpret_cast<float*>(known + 4 * C::TOK);  // [TOK][NQ column parts] row sums
+  float* red2 = red + C::NQ * C::TOK;                          // [TOK][NQ] squared deviations
+  const int Nt = Ht * Wt, tpf = (Nt + C::TOK - 1) / C::TOK, tiles = B * tpf;
   const int tid = threadIdx.x;
-  if (tid < C::TOK) known[tid] = 0;
-  // weights: [D][64] 16-bit rows of 128 B -> padded rows
+  // weights: [D][64] 16-bit rows of 128 B -> padded rows, once per CTA
   for (int e = tid; e < D * 8; e += 256) {
     const int n = e >> 3, ch = e & 7;
     *reinterpret_cast<uint4*>(Ws + n * C::KP + ch * 8) = *reinterpret_cast<const uint4*>(we16 + (size_t)n * 64 + ch * 8);
   }
   pdl_trigger();
   pdl_wait();
-  __syncthreads();
   static_assert(C::TOK * 4 <= 256, "one thread per (token, pixel row)");
-  if (tid < C::TOK * 4) {
-    // thread -> pixel row pr of token tl; a warp covers 32 neighbouring tokens of one
-    // pixel row, so its loads are contiguous 16-byte runs; all loads are independent
-    const int tl = tid & (C::TOK - 1), pr = tid / C::TOK;
-    const int t = t0 + tl;
-    float rv[4] = {0.f, 0.f, 0.f, 0.f}, gv[4] = {0.f, 0.f, 0.f, 0.f}, bv[4] = {0.f, 0.f, 0.f, 0.f};
-    bool kn[4] = {false, false, false, false};
-    if (t < Nt) {
-      const int ty = t / Wt, tx = t - (t / Wt) * Wt;
-      const int y = ty * 4 + pr, xx0 = tx * 4;
-      if (y < H) {
-        const size_t q = (size_t)y * W + xx0;
-        const float* xb = x + (size_t)b * 3 * HW + q;
-        const uint8_t* hb = hole + (size_t)b * HW + q;
-        if ((W & 3) == 0 && xx0 + 3 < W && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(hole)) & 15) == 0) {
-          // 16-byte aligned: vector loads
-          const float4 r4 = *reinterpret_cast<const float4*>(xb);
-          const float4 g4 = *reinterpret_cast<const float4*>(xb + HW);
-          const float4 b4 = *reinterpret_cast<const float4*>(xb + 2 * HW);
-          const uchar4 h4 = *reinterpret_cast<const uchar4*>(hb);
-          rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
-          gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
-          bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
-          kn[0] = h4.x == 0; kn[1] = h4.y == 0; kn[2] = h4.z == 0; kn[3] = h4.w == 0;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (xx0 + j < W) {
-              rv[j] = xb[j]; gv[j] = xb[HW + j]; bv[j] = xb[2 * HW + j];
-              kn[j] = hb[j] == 0;
-            }
-        }
-      }
-    }
-    T* prow = P + tl * C::KP + 4 * pr;
-    bool any = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {  // hole pixels enter as 0 (the mask channel carries them)
-      prow[j] = from_f32<T>(kn[j] ? rv[j] : 0.f);
-      prow[16 + j] = from_f32<T>(kn[j] ? gv[j] : 0.f);
-      prow[32 + j] = from_f32<T>(kn[j] ? bv[j] : 0.f);
-      prow[48 + j] = from_f32<T>(kn[j] ? 1.f : 0.f);
-      any = any || kn[j];
-    }
-    if (any) known[tl] = 1;  // every writer stores the same value
-  }
-  __syncthreads();
+  // thread -> pixel row pr of token tl; a warp covers 32 neighbouring tokens of one pixel
+  // row, so its loads are contiguous 16-byte runs; all loads are independent
+  const bool loader = tid < C::TOK * 4;
+  const int tl_ld = tid & (C::TOK - 1), pr = tid / C::TOK;
+  const bool vec = (W & 3) == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(hole)) & 15) == 0;
+  PatchRow cur{};
+  if (loader && (int)blockIdx.x < tiles)
+    cur = load_patch_row(x, hole, blockIdx.x / tpf, (blockIdx.x % tpf) * C::TOK + tl_ld, pr, H, W, Wt, Nt, vec);
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
   const int m0 = (warp % C::MT) * 16;
-  constexpr int NT = D / 8 / C::NQ;               // n-tiles of 8 per warp (D / NQ columns)
+  constexpr int NT = D / 8 / C::NQ;  // n-tiles of 8 per warp (D / NQ columns)
   const int n0 = (warp / C::MT) * (D / C::NQ);
-  float acc[NT][4];
-#pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-  for (int ks = 0; ks < 4; ++ks) {
-    uint32_t a[4];
-    ldsm_x4_e(a, P + (m0 + (lane & 15)) * C::KP + ks * 16 + (lane >> 4) * 8);
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      uint32_t bb[2];
-      ldsm_x2_e(bb, Ws + (n0 + 8 * j + (lane & 7)) * C::KP + ks * 16 + ((lane >> 3) & 1) * 8);
-      mma16816<T>(acc[j], a, bb[0], bb[1]);
-    }
-  }
-  // bias; this thread's parts of rows m0 + g and m0 + g + 8 (columns n0 + 8j + 2tq, +1)
-  const int half = warp / C::MT;  // this warp's column part
-  float sa = 0.f, sb = 0.f;
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const int c = n0 + 8 * j + 2 * tq;
-    const float b0 = be[c], b1 = be[c + 1];
-    acc[j][0] += b0;
-    acc[j][1] += b1;
-    acc[j][2] += b0;
-    acc[j][3] += b1;
-    sa += acc[j][0] + acc[j][1];
-    sb += acc[j][2] + acc[j][3];
-  }
-  sa += __shfl_xor_sync(0xffffffffu, sa, 1);
-  sa += __shfl_xor_sync(0xffffffffu, sa, 2);
-  sb += __shfl_xor_sync(0xffffffffu, sb, 1);
-  sb += __shfl_xor_sync(0xffffffffu, sb, 2);
-  if (tq == 0) {
-    red[(m0 + g) * C::NQ + half] = sa;
-    red[(m0 + g + 8) * C::NQ + half] = sb;
-  }
-  __syncthreads();
+  const int half = warp / C::MT;     // this warp's column part
   auto part_sum = [&](const float* r, int row) {  // the column parts of a row, in a fixed order
     float v = 0.f;
 #pragma unroll
     for (int k = 0; k < C::NQ; ++k) v += r[row * C::NQ + k];
     return v;
   };
-  const float ma = part_sum(red, m0 + g) * (1.f / D);
-  const float mb = part_sum(red, m0 + g + 8) * (1.f / D);
-  float qa = 0.f, qb = 0.f;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int b = tile / tpf, t0 = (tile - b * tpf) * C::TOK;
+    __syncthreads();  // the previous tile's P, O, known and statistics are no longer read
+    if (loader) {
+      T* prow = P + tl_ld * C::KP + 4 * pr;
 #pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const int c = n0 + 8 * j + 2 * tq;
-    qa = fmaf(acc[j][0] - ma, acc[j][0] - ma, qa);
-    qa = fmaf(acc[j][1] - ma, acc[j][1] - ma, qa);
-    qb = fmaf(acc[j][2] - mb, acc[j][2] - mb, qb);
-    qb = fmaf(acc[j][3] - mb, acc[j][3] - mb, qb);
-    O[(m0 + g) * C::OUT_STRIDE + c] = acc[j][0];
-    O[(m0 + g) * C::OUT_STRIDE + c + 1] = acc[j][1];
-    O[(m0 + g + 8) * C::OUT_STRIDE + c] = acc[j][2];
-    O[(m0 + g + 8) * C::OUT_STRIDE + c + 1] = acc[j][3];
-  }
-  qa += __shfl_xor_sync(0xffffffffu, qa, 1);
-  qa += __shfl_xor_sync(0xffffffffu, qa, 2);
-  qb += __shfl_xor_sync(0xffffffffu, qb, 1);
-  qb += __shfl_xor_sync(0xffffffffu, qb, 2);
-  if (tq == 0) {
-    red2[(m0 + g) * C::NQ + half] = qa;
-    red2[(m0 + g + 8) * C::NQ + half] = qb;
-  }
-  __syncthreads();
-  if (tid < C::TOK && t0 + tid < Nt) v0[(size_t)b * Nt + t0 + tid] = (uint8_t)known[tid];
-  // each warp writes TOK / 8 token rows and their LayerNorm
-#pragma unroll 2
-  for (int i = 0; i < C::TOK / 8; ++i) {
-    const int tl = warp * (C::TOK / 8) + i, t = t0 + tl;
-    if (t >= Nt) break;
-    const float* orow = O + tl * C::OUT_STRIDE;
-    float* trow = tok + ((size_t)b * Nt + t) * D;
-    const float mean = part_sum(red, tl) * (1.f / D);
-    const float rstd = rsqrtf(part_sum(red2, tl) * (1.f / D) + 1e-5f);
-    T* lrow = ln_out + ((size_t)b * Nt + t) * D;
-    for (int c = 2 * lane; c < D; c += 64) {  // two channels per lane: 256-byte warp stores
-      const float2 v = *reinterpret_cast<const float2*>(orow + c);
-      *reinterpret_cast<float2*>(trow + c) = v;
-      float y0 = (v.x - mean) * rstd, y1 = (v.y - mean) * rstd;
-      if (ln_g) {  // else the affine part is folded into the next GEMM
-        y0 = y0 * ln_g[c] + ln_b[c];
-        y1 = y1 * ln_g[c + 1] + ln_b[c + 1];
+      for (int j = 0; j < 4; ++j) {  // hole pixels enter as 0 (the mask channel carries them)
+        const bool kn = (cur.known >> j) & 1u;
+        prow[j] = from_f32<T>(kn ? cur.r[j] : 0.f);
+        prow[16 + j] = from_f32<T>(kn ? cur.g[j] : 0.f);
+        prow[32 + j] = from_f32<T>(kn ? cur.b[j] : 0.f);
+        prow[48 + j] = from_f32<T>(kn ? 1.f : 0.f);
       }
-      *reinterpret_cast<uint32_t*>(lrow + c) = H16<T>::pack2(y0, y1);
+      known[tl_ld * 4 + pr] = cur.known;
+      // the next tile's pixels, in flight while this tile is computed and stored
+      const int nt = tile + gridDim.x;
+      if (nt < tiles) cur = load_patch_row(x, hole, nt / tpf, (nt % tpf) * C::TOK + tl_ld, pr, H, W, Wt, Nt, vec);
+    }
+    __syncthreads();
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      uint32_t a[4];
+      ldsm_x4_e(a, P + (m0 + (lane & 15)) * C::KP + ks * 16 + (lane >> 4) * 8);
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        uint32_t bb[2];
+        ldsm_x2_e(bb, Ws + (n0 + 8 * j + (lane & 7)) * C::KP + ks * 16 + ((lane >> 3) & 1) * 8);
+        mma16816<T>(acc[j], a, bb[0], bb[1]);
+      }
+    }
+    // bias; this thread's parts of rows m0 + g and m0 + g + 8 (columns n0 + 8j + 2tq, +1)
+    float sa = 0.f, sb = 0.f;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int c = n0 + 8 * j + 2 * tq;
+      const float b0 = be[c], b1 = be[c + 1];
+      acc[j][0] += b0;
+      acc[j][1] += b1;
+      acc[j][2] += b0;
+      acc[j][3] += b1;
+      sa += acc[j][0] + acc[j][1];
+      sb += acc[j][2] + acc[j][3];
+    }
+    sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+    sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+    sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+    sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+    if (tq == 0) {
+      red[(m0 + g) * C::NQ + half] = sa;
+      red[(m0 + g + 8) * C::NQ + half] = sb;
+    }
+    __syncthreads();
+    const float ma = part_sum(red, m0 + g) * (1.f / D);
+    const float mb = part_sum(red, m0 + g + 8) * (1.f / D);
+    float qa = 0.f, qb = 0.f;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int c = n0 + 8 * j + 2 * tq;
+      qa = fmaf(acc[j][0] - ma, acc[j][0] - ma, qa);
+      qa = fmaf(acc[j][1] - ma, acc[j][1] - ma, qa);
+      qb = fmaf(acc[j][2] - mb, acc[j][2] - mb, qb);
+      qb = fmaf(acc[j][3] - mb, acc[j][3] - mb, qb);
+      O[(m0 + g) * C::OUT_STRIDE + c] = acc[j][0];
+      O[(m0 + g) * C::OUT_STRIDE + c + 1] = acc[j][1];
+      O[(m0 + g + 8) * C::OUT_STRIDE + c] = acc[j][2];
+      O[(m0 + g + 8) * C::OUT_STRIDE + c + 1] = acc[j][3];
+    }
+    qa += __shfl_xor_sync(0xffffffffu, qa, 1);
+    qa += __shfl_xor_sync(0xffffffffu, qa, 2);
+    qb += __shfl_xor_sync(0xffffffffu, qb, 1);
+    qb += __shfl_xor_sync(0xffffffffu, qb, 2);
+    if (tq == 0) {
+      red2[(m0 + g) * C::NQ + half] = qa;
+      red2[(m0 + g + 8) * C::NQ + half] = qb;
+    }
+    __syncthreads();
+    if (tid < C::TOK && t0 + tid < Nt) {
+      const uint32_t* kw = known + tid * 4;
+      v0[(size_t)b * Nt + t0 + tid] = (uint8_t)((kw[0] | kw[1] | kw[2] | kw[3]) != 0u);
+    }
+    // each warp writes TOK / 8 token rows and their LayerNorm
+#pragma unroll 2
+    for (int i = 0; i < C::TOK / 8; ++i) {
+      const int tl = warp * (C::TOK / 8) + i, t = t0 + tl;
+      if (t >= Nt) break;
+      const float* orow = O + tl * C::OUT_STRIDE;
+      float* trow = tok + ((size_t)b * Nt + t) * D;
+      const float mean = part_sum(red, tl) * (1.f / D);
+      const float rstd = rsqrtf(part_sum(red2, tl) * (1.f / D) + 1e-5f);
+      T* lrow = ln_out + ((size_t)b * Nt + t) * D;
+      for (int c = 2 * lane; c < D; c += 64) {  // two channels per lane: 256-byte warp stores
+        const float2 v = *reinterpret_cast<const float2*>(orow + c);
+        *reinterpret_cast<float2*>(trow + c) = v;
+        float y0 = (v.x - mean) * rstd, y1 = (v.y - mean) * rstd;
+        if (ln_g) {  // else the affine part is folded into the next GEMM
+          y0 = y0 * ln_g[c] + ln_b[c];
+          y1 = y1 * ln_g[c + 1] + ln_b[c + 1];
+        }
+        *reinterpret_cast<uint32_t*>(lrow + c) = H16<T>::pack2(y0, y1);
+      }
     }
   }
 }
@@ -467,9 +492,18 @@ cudaError_t launch_embed_tc_d(const float* x, const uint8_t* hole, int B, int H,
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(cdiv(Ht * Wt, EmbTc<D>::TOK), B);
-  return launch_pdl(embed_tc_kernel<D, T>, grid, dim3(256), EmbTc<D>::SMEM, st, x, hole, H, W, Ht, Wt, we16, be, tok, v0,
-                    ln_g, ln_b, ln_out);
+  // persistent: three CTAs per SM (the shared memory of a tile allows three)
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  const int tiles = B * cdiv(Ht * Wt, EmbTc<D>::TOK);
+  dim3 grid(tiles < 3 * sms ? tiles : 3 * sms);
+  return launch_pdl(embed_tc_kernel<D, T>, grid, dim3(256), EmbTc<D>::SMEM, st, x, hole, B, H, W, Ht, Wt, we16, be, tok,
+                    v0, ln_g, ln_b, ln_out);
 }
 
 template <typename T>
