@@ -50,35 +50,42 @@ __global__ void gelu_bwd_kernel(const float* __restrict__ z, float* __restrict__
 // TRANS = false: out [Ro][3 Kp], row r = row r of X, K along C (Ro >= R, Kp >= C);
 // TRANS = true:  out [Ro][3 Kp], row r = column r of X, K along R (Ro >= C, Kp >= R);
 // part p of a row at columns p Kp .. p Kp + Kp - 1 (b_side: hi, lo, hi; else hi, hi, lo);
-// padding rows and columns are zero.  32 x 32 tiles through shared memory.
+// padding rows and columns are zero.  32 x 64 tiles through shared memory, two K positions
+// per 32-bit store.
 template <bool TRANS>
 __global__ void __launch_bounds__(256) split3_kernel(const float* __restrict__ X, int R, int C, int ld, int Ro,
                                                      int Kp, int b_side, bf16* __restrict__ out) {
-  __shared__ float t[32][33];
-  const int o0 = blockIdx.y * 32, k0 = blockIdx.x * 32;  // output rows, K positions
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    float v = 0.f;
-    if (TRANS) {  // tile rows = K (rows of X), columns = output rows (columns of X): coalesced reads
+  // tile: 32 output rows x 64 K positions, t[o][k] (row pitch 66 floats: 8-byte aligned pairs)
+  __shared__ float t[32][66];
+  const int o0 = blockIdx.y * 32, k0 = blockIdx.x * 64;  // output rows, K positions
+  if (TRANS) {  // rows of X = K positions, columns of X = output rows: coalesced reads along o
+    for (int i = threadIdx.y; i < 64; i += 8) {
       const int r = k0 + i, cc = o0 + threadIdx.x;
-      if (r < R && cc < C) v = X[(size_t)r * ld + cc];
-      t[i][threadIdx.x] = v;
-    } else {
-      const int r = o0 + i, cc = k0 + threadIdx.x;
-      if (r < R && cc < C) v = X[(size_t)r * ld + cc];
-      t[threadIdx.x][i] = v;  // t[k][o]
+      t[threadIdx.x][i] = r < R && cc < C ? X[(size_t)r * ld + cc] : 0.f;
+    }
+  } else {  // rows of X = output rows, columns = K positions: coalesced reads along k
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int r = o0 + i;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cc = k0 + 32 * h + threadIdx.x;
+        t[i][32 * h + threadIdx.x] = r < R && cc < C ? X[(size_t)r * ld + cc] : 0.f;
+      }
     }
   }
   __syncthreads();
+  // K positions k, k + 1 of output row orow per thread: one 32-bit store per part
   for (int i = threadIdx.y; i < 32; i += 8) {
-    const int orow = o0 + i, k = k0 + threadIdx.x;
+    const int orow = o0 + i, k = k0 + 2 * threadIdx.x;
     if (orow >= Ro || k >= Kp) continue;
-    const float v = t[threadIdx.x][i];  // X value for (output row orow, K position k)
-    const bf16 hi = __float2bfloat16_rn(v);
-    const bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const float2 v = *reinterpret_cast<const float2*>(&t[i][2 * threadIdx.x]);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+    const float2 hf = __bfloat1622float2(hi);
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
     bf16* row = out + (size_t)orow * 3 * Kp;
-    row[k] = hi;
-    row[Kp + k] = b_side ? lo : hi;
-    row[2 * (size_t)Kp + k] = b_side ? hi : lo;
+    *reinterpret_cast<__nv_bfloat162*>(row + k) = hi;
+    *reinterpret_cast<__nv_bfloat162*>(row + Kp + k) = b_side ? lo : hi;
+    *reinterpret_cast<__nv_bfloat162*>(row + 2 * (size_t)Kp + k) = b_side ? hi : lo;
   }
 }
 
@@ -483,7 +490,7 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   float* tpart = F(oTP);
   auto split3 = [&](bool trans, const float* X, int R, int C, int ld, int Ro, int Kp, bool b_side, bf16* out) {
     auto ls = K(K_OTHER);
-    const dim3 grid(cdiv(Kp, 32), cdiv(Ro, 32));
+    const dim3 grid(cdiv(Kp, 64), cdiv(Ro, 32));  // Kp: a multiple of 64
     if (trans) split3_kernel<true><<<grid, dim3(32, 8), 0, st>>>(X, R, C, ld, Ro, Kp, b_side ? 1 : 0, out);
     else split3_kernel<false><<<grid, dim3(32, 8), 0, st>>>(X, R, C, ld, Ro, Kp, b_side ? 1 : 0, out);
     ok(cudaGetLastError());
