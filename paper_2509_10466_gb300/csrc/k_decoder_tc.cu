@@ -236,8 +236,8 @@ __global__ void subpixel_weights_kernel(const float* __restrict__ w, int Cout, i
 
 // ---------------------------------------------------------------------------------
 // Transposed form for Cout = 32 or 64, with the parities stacked on the MMA's M side.
-// A tcgen05.mma takes as long for N = 32 or 64 as for N = 256, so the form above (M =
-// pixels, N = Cout) runs its tensor core at Cout / 256 of its rate.  Here a tile is a
+// The form above (M = pixels, N = Cout) issues narrow MMAs (N = 32 or 64), which keep
+// the tensor core below its rate and need many more instructions per output.  Here a tile is a
 // 16 x 16 block of input pixels (N = 256, pixel q = 16 py + px) and the accumulator row
 // g * Cout + co holds output channel co of parity g of a group of NG = 128 / Cout parities
 // (all four at Cout = 32; the two of output-row parity a at Cout = 64):

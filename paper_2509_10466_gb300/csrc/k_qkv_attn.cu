@@ -9,12 +9,14 @@
 // tcgen05 (M = 128, N = 192, FP32 accumulation in tensor memory, two accumulators so that
 // pass p + 1 runs while pass p is consumed).  Sixteen warps take the accumulator of a pass
 // (eight per head: two per TMEM lane quarter, one taking the q columns and half of the k
-// columns, the other the rest of k and the v columns), add the bias, round to T and write the heads' Q, K, V tiles of both windows
-// into shared memory in the 64-byte-swizzled layout of the TMA boxes of the separate
-// attention kernel, and run the same masked window softmax on them (one window and 16 query
-// rows per warp, mma.sync), writing the attention output rows.  Q, K and V never reach global
-// memory; the weights stream through a ring of 24 KB stages (three 64-row boxes: the q, k
-// and v rows of the pass's heads).
+// columns, the other the rest of k and the v columns), add the bias, round to T and write
+// the heads' Q, K, V tiles of both windows into shared memory in the 64-byte-swizzled
+// layout of the TMA boxes of the separate attention kernel, and run the same masked window
+// softmax on them (one window and 16 query rows per warp, mma.sync), writing the attention
+// output rows.  The tiles are double-buffered by pass parity, so a warp drains pass p + 1
+// while the other warps of its head still attend pass p.  Q, K and V never reach global
+// memory; the weights stream through a two-stage ring of 24 KB stages (three 64-row boxes:
+// the q, k and v rows of the pass's heads).
 //
 // Warps: 0 TMA producer, 1 TMEM owner + MMA issuer, 2..17 drain + attention.
 #include <cuda.h>
@@ -28,7 +30,7 @@ namespace inpaint {
 
 namespace {
 
-constexpr int QA_BM = 128, QA_BK = 64, QA_N = 192, QA_RING = 4;
+constexpr int QA_BM = 128, QA_BK = 64, QA_N = 192, QA_RING = 2;
 constexpr int QA_ATT_WARPS = 16;                    // drain + attention warps (8 per head of a pass)
 constexpr int QA_THREADS = 64 + 32 * QA_ATT_WARPS;
 constexpr int QA_STAGE = QA_N * QA_BK * 2;            // 24 KB: q, k, v rows of two heads, one k-block
@@ -37,7 +39,7 @@ constexpr int QA_MAX_HEADS = 16;
 
 __host__ __device__ constexpr int qa_smem_bytes(int d, int heads) {
   return 1024 /*alignment*/ + (d / QA_BK) * QA_BM * QA_BK * 2 /*Y*/ + QA_RING * QA_STAGE +
-         2 * 2 * 3 * QA_TILE /*Q, K, V tiles of two heads x two windows*/ + heads * 225 * 4 /*bias tables*/ +
+         2 * 2 * 2 * 3 * QA_TILE /*Q, K, V tiles of two passes x two heads x two windows*/ + heads * 225 * 4 /*bias tables*/ +
          3 * d * 4 /*QKV bias*/;
 }
 
@@ -76,8 +78,8 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
   const int pairs = (args.nwin + 1) / 2;
   uint8_t* sY = smem;                                   // [KA][128 rows x 128 B]: window 0 rows, then window 1
   uint8_t* sW = sY + KA * QA_BM * QA_BK * 2;            // [RING][192 rows x 128 B]
-  uint8_t* sT = sW + QA_RING * QA_STAGE;                // [head 0, 1][window 0, 1][Q, K, V][64 x 64 B]
-  float* s_bias = reinterpret_cast<float*>(sT + 12 * QA_TILE);  // [3d], 16-byte aligned
+  uint8_t* sT = sW + QA_RING * QA_STAGE;  // [pass parity][head 0, 1][window 0, 1][Q, K, V][64 x 64 B]
+  float* s_bias = reinterpret_cast<float*>(sT + 24 * QA_TILE);  // [3d], 16-byte aligned
   float* s_rp = s_bias + 3 * d;                                 // [heads][225]
   __shared__ __align__(8) uint64_t full[QA_RING], empty[QA_RING], a_full, y_empty, acc_full[2], acc_empty[2],
       teardown;
@@ -85,7 +87,9 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
   __shared__ int abort_flag;
   __shared__ int stok[2][WA_SLOTS];
   __shared__ unsigned okw[2][2];
-  auto tile = [&](int hh, int win, int part) { return sT + ((hh * 2 + win) * 3 + part) * QA_TILE; };
+  auto tile = [&](uint32_t buf, int hh, int win, int part) {
+    return sT + (((buf * 2 + hh) * 2 + win) * 3 + part) * QA_TILE;
+  };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int* err = args.err;
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
             const float* bb = s_bias + part * d + hg * WA_DH + 8 * c;
             const float4 b0 = *reinterpret_cast<const float4*>(bb);
             const float4 b1 = *reinterpret_cast<const float4*>(bb + 4);
-            *reinterpret_cast<uint4*>(tile(hh, win, part) + swz64(slot, c)) =
+            *reinterpret_cast<uint4*>(tile(buf, hh, win, part) + swz64(slot, c)) =
                 make_uint4(H16<T>::pack2(__uint_as_float(v[0]) + b0.x, __uint_as_float(v[1]) + b0.y),
                            H16<T>::pack2(__uint_as_float(v[2]) + b0.z, __uint_as_float(v[3]) + b0.w),
                            H16<T>::pack2(__uint_as_float(v[4]) + b1.x, __uint_as_float(v[5]) + b1.y),
@@ -266,7 +270,9 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);  // the accumulator is free for pass gp + 2
         }
-        named_sync(1 + hh, 256);  // the head's Q, K, V tiles of both windows are complete
+        // the head's Q, K, V tiles of both windows are complete; the group's warps have also
+        // left pass gp - 1's attention, so pass gp + 1 may drain into that pass's tiles
+        named_sync(1 + hh, 256);
         if (ok && awin < nh) {
           const unsigned long long keymask =
               (unsigned long long)okw[awin][0] | ((unsigned long long)okw[awin][1] << 32);
@@ -277,12 +283,11 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
                 *reinterpret_cast<uint4*>(o + (size_t)t * d + hg * WA_DH + (x & 3) * 8) = make_uint4(0, 0, 0, 0);
             }
           } else {
-            window_attention_rows<RP, T>(tile(hh, awin, 0), tile(hh, awin, 1), tile(hh, awin, 2), keymask,
+            window_attention_rows<RP, T>(tile(buf, hh, awin, 0), tile(buf, hh, awin, 1), tile(buf, hh, awin, 2), keymask,
                                          RP ? s_rp + hg * 225 : nullptr, stok[awin], o, d, hg * WA_DH, 16 * wq,
                                          lane);
           }
         }
-        named_sync(1 + hh, 256);  // the tiles are read before the next pass overwrites them
       }
     }
     if (!ok) {
