@@ -151,7 +151,9 @@ def bytes_per_frame(m, H, W, act_bytes=2):
     d, r, L = m.dim, m.mlp_ratio, m.blocks
     a = act_bytes
     return {
-        "embed": 13 * H * W + N * d * 4 + N,
+        # frame + hole in; the FP32 token row, the token mask and (16-bit forms) the first
+        # block's normalized row out
+        "embed": 13 * H * W + N * d * 4 + N + (N * d * a if a == 2 else 0),
         "layernorm": (2 * L + 1) * N * d * (4 + a),
         "qkv_gemm": L * N * (d * a + 3 * d * a),
         "attention": L * N * (3 * d * a + d * a + 2),
