@@ -335,12 +335,19 @@ INPAINT_API int inpaint_test_gemm_bf16(const void* A, const void* Bt, float* C, 
  * clears the word.  Errors: E_INVAL, E_CUDA. */
 INPAINT_API int inpaint_test_wait_expiry(inpaint_ctx* ctx, int limit_us, void* stream);
 
-/* The two GELU evaluations of the library on device floats x[n]: y_bf16_form[i] as the
- * BF16 tensor-core epilogues compute it (0.5 x (1 + tanh(x P(x^2))) with a fitted degree-4
+/* Two GELU evaluations of the library on device floats x[n]: y_bf16_form[i] as the
+ * 16-bit forms' decoder epilogues compute it (0.5 x (1 + tanh(x P(x^2))) with a fitted degree-4
  * P and the approximate hardware tanh: |error| <= 6e-6 + 2.5e-4 |x| absolute on [-12, 12],
  * saturating beyond) and y_fp32_form[i] with CUDA's erff (the FP32 form). */
 INPAINT_API int inpaint_test_gelu(const float* x, float* y_bf16_form, float* y_fp32_form, int n,
                                   void* stream);
+
+/* The GELU of the 16-bit forms' hidden activations (the fused projection + MLP kernel), on
+ * device floats x[n]: the same 0.5 x (1 + tanh(x P(x^2))) evaluated in FP16 arithmetic on
+ * pairs (x rounded to FP16 saturating at +-65504, packed FP16 multiply-adds, the
+ * approximate FP16 tanh), y[i] its FP16 result as a float.  The kernel rounds that result
+ * to the operand type.  Errors: E_INVAL, E_CUDA. */
+INPAINT_API int inpaint_test_gelu_h16(const float* x, float* y, int n, void* stream);
 
 #ifdef __cplusplus
 }

@@ -78,6 +78,7 @@ _SIGS = {
     "inpaint_destroy": (None, [_P]),
     "inpaint_test_gemm_bf16": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "inpaint_test_gelu": (_I, [_P, _P, _P, _I, _P]),
+    "inpaint_test_gelu_h16": (_I, [_P, _P, _I, _P]),
     "inpaint_test_wait_expiry": (_I, [_P, _I, _P]),
     "inpaint_default_weights": (_I, [ctypes.POINTER(InpaintConfig), ctypes.c_uint64, _P, ctypes.c_size_t]),
 }
@@ -332,6 +333,10 @@ def inpaint_test_gemm_bf16(A, Bt, C, stream=None):
 
 def inpaint_test_wait_expiry(ctx, limit_us: int, stream=None):
     _check(load().inpaint_test_wait_expiry(ctx, limit_us, _stream(stream)), "inpaint_test_wait_expiry")
+
+
+def inpaint_test_gelu_h16(x, y, stream=None):
+    _check(load().inpaint_test_gelu_h16(_ptr(x), _ptr(y), x.numel(), _stream(stream)), "inpaint_test_gelu_h16")
 
 
 def inpaint_test_gelu(x, y_bf16_form, y_fp32_form, stream=None):

@@ -948,6 +948,15 @@ __global__ void gelu_pair_kernel(const float* __restrict__ x, float* __restrict_
     y_fp32_form[i] = gelu_erf(x[i]);
   }
 }
+__global__ void gelu_h16_kernel(const float* __restrict__ x, float* __restrict__ y, int n) {
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i < n) {
+    const float a = x[i], b = i + 1 < n ? x[i + 1] : 0.f;
+    const float2 r = __half22float2(gelu_h2(f32x2_to_h2_satfinite(a, b)));
+    y[i] = r.x;
+    if (i + 1 < n) y[i + 1] = r.y;
+  }
+}
 }  // namespace
 
 extern "C" {
@@ -963,6 +972,13 @@ int inpaint_test_gelu(const float* x, float* y_bf16_form, float* y_fp32_form, in
   if (!x || !y_bf16_form || !y_fp32_form || n < 0) return INPAINT_E_INVAL;
   if (n == 0) return INPAINT_OK;
   gelu_pair_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, y_bf16_form, y_fp32_form, n);
+  return cuda_err(cudaGetLastError());
+}
+
+int inpaint_test_gelu_h16(const float* x, float* y, int n, void* stream) {
+  if (!x || !y || n < 0) return INPAINT_E_INVAL;
+  if (n == 0) return INPAINT_OK;
+  gelu_h16_kernel<<<((n + 1) / 2 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, y, n);
   return cuda_err(cudaGetLastError());
 }
 

@@ -100,6 +100,22 @@ __device__ __forceinline__ float gelu_as(float x) {
   return fmaf(hx, tanh_approx(x * p), hx);
 }
 
+// The same GELU on a pair of values in FP16 arithmetic (packed: one instruction per pair
+// for each step, one MUFU tanh per pair), for the 16-bit forms' hidden activations, whose
+// result is rounded to a 16-bit type anyway.  Large |x| saturate through tanh(+-inf).
+__device__ __forceinline__ __half2 gelu_h2(__half2 x) {
+  const __half2 x2 = __hmul2(x, x);
+  __half2 p = __hfma2(__float2half2_rn(9.163219942820433e-07f), x2, __float2half2_rn(-2.670336834853515e-05f));
+  p = __hfma2(p, x2, __float2half2_rn(-1.468761620344594e-04f));
+  p = __hfma2(p, x2, __float2half2_rn(3.6510955542325974e-02f));
+  p = __hfma2(p, x2, __float2half2_rn(7.97806978225708e-01f));
+  const __half2 hx = __hmul2(__float2half2_rn(0.5f), x);
+  const __half2 z = __hmul2(x, p);
+  uint32_t zi = *reinterpret_cast<const uint32_t*>(&z), ti;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(ti) : "r"(zi));
+  return __hfma2(hx, *reinterpret_cast<const __half2*>(&ti), hx);
+}
+
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(bf16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float to_f32(f16 v) { return __half2float(v); }
@@ -133,6 +149,25 @@ template <> struct H16<f16> {
     return __half22float2(*reinterpret_cast<const __half2*>(&v));
   }
 };
+
+// A pair of FP32 values rounded to FP16 (a in the low half), saturating at +-65504.
+__device__ __forceinline__ __half2 f32x2_to_h2_satfinite(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return *reinterpret_cast<const __half2*>(&r);
+}
+
+// GELU of a pair of FP32 values (evaluated by gelu_h2), packed in the 16-bit type T.
+template <typename T>
+__device__ __forceinline__ uint32_t gelu2_pack(float a, float b) {
+  const __half2 r = gelu_h2(f32x2_to_h2_satfinite(a, b));
+  if constexpr (sizeof(T) == 2 && H16<T>::kMmaFmt == 0) {
+    return *reinterpret_cast<const uint32_t*>(&r);
+  } else {
+    const float2 f = __half22float2(r);
+    return H16<T>::pack2(f.x, f.y);
+  }
+}
 
 // D(16x8, f32) += A(16x16) . B(16x8) on the warp-level tensor-core instruction, with A and
 // B in 16-bit type T (register fragments of mma.m16n8k16, row.col).

@@ -555,8 +555,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
           for (int k = 0; k < 16; k += 2) {
             const float4 b4 = *reinterpret_cast<const float4*>(bp + 2 * k);
             const uint32_t* x = &v[l][2 * k];
-            pk[k] = H16<T>::pack2(gelu_as(__uint_as_float(x[0]) + b4.x), gelu_as(__uint_as_float(x[1]) + b4.y));
-            pk[k + 1] = H16<T>::pack2(gelu_as(__uint_as_float(x[2]) + b4.z), gelu_as(__uint_as_float(x[3]) + b4.w));
+            pk[k] = gelu2_pack<T>(__uint_as_float(x[0]) + b4.x, __uint_as_float(x[1]) + b4.y);
+            pk[k + 1] = gelu2_pack<T>(__uint_as_float(x[2]) + b4.z, __uint_as_float(x[3]) + b4.w);
           }
           tc::tmem_st_32x32b_x16(lane_base + Cfg::H_COL0 + hb * HC + cb + 16 * l, pk);
         }

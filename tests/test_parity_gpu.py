@@ -66,6 +66,39 @@ def test_gelu_of_the_bf16_form_matches_erff():
     assert torch.equal(ya.cpu()[3:], big.cpu()[3:]) and float(ya.cpu()[:3].abs().max()) == 0.0
 
 
+def test_gelu_of_the_hidden_activations_in_fp16():
+    """The 16-bit forms' hidden-activation GELU, the same 0.5 x (1 + tanh(x P(x^2))) in packed
+    FP16 arithmetic: over [-12, 12] within 2e-3 |GELU(x)| + 1e-4 of the FP64 closed form
+    for x > 0.5 (the input and each step rounded to FP16, 2^-11 relative, and the FP16
+    tanh; measured 1.25e-3 relative), within 2e-3 + 1e-4 |x| absolute below (near 0 the
+    output is small and the error absolute; measured 1.24e-3); every value then rounds to
+    the bf16 step (2^-9 relative) or the fp16 one.  Saturation: x for large x, 0 for large
+    negative x, no NaN or inf up to +-1e6."""
+    lib()
+    x = torch.linspace(-12, 12, 200001, dtype=torch.float32)
+    y = torch.empty_like(x).cuda()
+    binding.inpaint_test_gelu_h16(x.cuda(), y)
+    torch.cuda.synchronize()
+    yd = y.cpu().double()
+    ref = 0.5 * x.double() * (1 + torch.erf(x.double() / 2 ** 0.5))
+    err = (yd - ref).abs()
+    pos = x > 0.5
+    rel_pos = float((err[pos] / ref[pos].abs()).max())
+    abs_neg = float((err[~pos] - 1e-4 * x.double().abs()[~pos]).max())
+    print(f"fp16 GELU: max relative error (x > 0.5) {rel_pos:.3e}, max absolute error (x <= 0.5) "
+          f"{float(err[~pos].max()):.3e}")
+    assert bool((err[pos] <= 2e-3 * ref[pos].abs() + 1e-4).all()), rel_pos
+    assert bool((err[~pos] <= 2e-3 + 1e-4 * x.double().abs()[~pos]).all()), abs_neg
+    big = torch.tensor([-1e6, -1e4, -100.0, -30.0, 30.0, 100.0, 1e4, 1e6]).cuda()
+    yb = torch.empty_like(big)
+    binding.inpaint_test_gelu_h16(big, yb)
+    torch.cuda.synchronize()
+    yb = yb.cpu()
+    assert torch.isfinite(yb).all()
+    assert float(yb[:4].abs().max()) == 0.0
+    assert torch.equal(yb[4:7], big.cpu()[4:7]) and float(yb[7]) == 65504.0
+
+
 # ----------------------------------------------------------------------------- FP32 form
 
 def test_fp32_plain_256_matches_oracle():
