@@ -60,3 +60,24 @@ def test_argument_increasing_and_saturation():
     big = np.array([30.0, 100.0, 1e4])
     assert np.allclose(form(big, c), big, rtol=0, atol=0)
     assert np.all(form(-big, c) == 0.0)
+
+
+
+def h2_coefficients():
+    """The polynomial of the FP16 hidden-activation GELU (gelu_h2), highest degree first."""
+    body = open(SRC).read()
+    body = body[body.index("__half2 gelu_h2(__half2 x)"):]
+    body = body[:body.index("\n}")]
+    c = []
+    for lead, const in re.findall(
+            r"__hfma2\((?:p|__float2half2_rn\(([-+0-9.eE]+)f\)), x2, __float2half2_rn\(([-+0-9.eE]+)f\)\)", body):
+        if lead:
+            c.append(float(lead))
+        c.append(float(const))
+    return np.array(c, dtype=np.float32).astype(np.float64)
+
+
+def test_fp16_form_uses_the_pinned_fit():
+    """The FP16 hidden-activation GELU evaluates the same fitted polynomial as the FP32 one
+    (whose fit the tests above pin); only the arithmetic differs (covered on the GPU)."""
+    assert np.array_equal(h2_coefficients(), coefficients())
