@@ -280,9 +280,10 @@ def hd_leg(binding, S, dev, flush, peaks, steps=8):
 
 
 def train_leg(binding, S, dev, flush, steps=5):
-    """The differentiation form: one training step = forward (inpaint_batch with pred) +
-    hole-L1 loss and its gradient + weight gradient (inpaint_backward, per-block
-    recomputation), 8 frames of 256x256, d192 h6, 6 blocks, MLP ratio 4, FP32."""
+    """The differentiation form: one training step = forward + hole-L1 loss and its gradient +
+    weight gradient with per-block recomputation, through inpaint_train_step (one call; the
+    forward runs once, in the backward's FP32-accurate form), 8 frames of 256x256, d192 h6,
+    6 blocks, MLP ratio 4, FP32."""
     import torch
     from paper_2509_10466_gb300.config import WORKLOAD_C as w
     cfg = w.model
@@ -290,16 +291,12 @@ def train_leg(binding, S, dev, flush, steps=5):
     hole = torch.from_numpy(S.make_hole(w.batch, w.height, w.width, w.mask_kind, seed=5)).to(dev)
     tgt = torch.from_numpy(S.make_target(w.batch, w.height, w.width, seed=5)).to(dev)
     inp = binding.Inpainter(cfg, S.make_weights(cfg, seed=0))
-    out = torch.empty_like(x)
     loss = torch.zeros(1, device=dev)
-    gout = torch.empty_like(x)
     gw = torch.empty(inp.n_params, device=dev)
     stream = torch.cuda.current_stream()
 
     def step():
-        binding.inpaint_batch(inp.ctx, x, hole, out, None, stream)
-        binding.inpaint_l1_hole_loss(inp.ctx, out, tgt, hole, loss, gout, stream)
-        binding.inpaint_backward(inp.ctx, x, hole, gout, gw, stream)
+        binding.inpaint_train_step(inp.ctx, x, hole, tgt, loss, gw, None, stream)
 
     for _ in range(2):
         step()
@@ -320,7 +317,8 @@ def train_leg(binding, S, dev, flush, steps=5):
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     ach = 3 * fwd / (ms / 1000.0) / 1e12
     return {"workload": f"{w.name}: {w.batch}x{w.height}x{w.width}, d{cfg.dim} h{cfg.heads} L{cfg.blocks} "
-                        f"r{cfg.mlp_ratio}, FP32, forward + hole-L1 loss + backward with per-block recomputation",
+                        f"r{cfg.mlp_ratio}, FP32, forward + hole-L1 loss + backward with per-block recomputation "
+                        f"(inpaint_train_step)",
             "steps_per_s": 1000.0 / ms, "frames_per_s": w.batch * 1000.0 / ms, "ms_per_step": ms,
             "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": ach / fp32_peak, "kernel": "whole training step",

@@ -236,6 +236,18 @@ INPAINT_API int inpaint_backward(inpaint_ctx* ctx, const float* x, const uint8_t
                      const float* grad_out, int B, int H, int W, float* grad_weights,
                      void* stream);
 
+/* One fine-tuning step's gradient in one call (the paper fine-tunes with an L1 loss that
+ * weights the masked region, "Training structure"): the forward in the backward's own
+ * FP32-accurate form, keeping each block's input, the hole-L1 loss of its output against
+ * target (as inpaint_l1_hole_loss), and the gradient of that loss with respect to the
+ * weight blob (as inpaint_backward with grad_out = dloss/dout); the forward is not run a
+ * second time.  target: device [B,3,H,W] float32; loss_dev: one device float;
+ * grad_weights: device float32, num_params values (overwritten); out_or_null: device
+ * [B,3,H,W] float32 receiving the forward's output, or NULL. */
+INPAINT_API int inpaint_train_step(inpaint_ctx* ctx, const float* x, const uint8_t* hole, const float* target,
+                                   int B, int H, int W, float* loss_dev, float* grad_weights,
+                                   float* out_or_null, void* stream);
+
 /* Wait for `stream` with a host deadline (timeout_ms < 0: wait forever), then check
  * the context's device error flag.  E_TIMEOUT if the deadline passed (the work keeps
  * running), E_DEVICE if a kernel raised the flag (the flag is then cleared). */

@@ -79,6 +79,7 @@ _SIGS = {
     "inpaint_test_gemm_bf16": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "inpaint_test_gelu": (_I, [_P, _P, _P, _I, _P]),
     "inpaint_test_gelu_h16": (_I, [_P, _P, _I, _P]),
+    "inpaint_train_step": (_I, [_P, _P, _P, _P, _I, _I, _I, _P, _P, _P, _P]),
     "inpaint_test_wait_expiry": (_I, [_P, _I, _P]),
     "inpaint_default_weights": (_I, [ctypes.POINTER(InpaintConfig), ctypes.c_uint64, _P, ctypes.c_size_t]),
 }
@@ -333,6 +334,14 @@ def inpaint_test_gemm_bf16(A, Bt, C, stream=None):
 
 def inpaint_test_wait_expiry(ctx, limit_us: int, stream=None):
     _check(load().inpaint_test_wait_expiry(ctx, limit_us, _stream(stream)), "inpaint_test_wait_expiry")
+
+
+def inpaint_train_step(ctx, x, hole, target, loss, grad_weights, out=None, stream=None):
+    """Forward + hole-L1 loss + weight gradient in one call (device tensors)."""
+    B, H, W = hole.shape
+    _check(load().inpaint_train_step(ctx, _ptr(x), _ptr(hole), _ptr(target), B, H, W, _ptr(loss),
+                                     _ptr(grad_weights), _ptr(out) if out is not None else None, _stream(stream)),
+           "inpaint_train_step")
 
 
 def inpaint_test_gelu_h16(x, y, stream=None):

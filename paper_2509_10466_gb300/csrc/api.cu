@@ -14,7 +14,8 @@
 
 namespace inpaint {
 int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* grad_out, int B, int H, int W,
-                  float* grad_w, cudaStream_t st);
+                  float* grad_w, cudaStream_t st, const float* target = nullptr, float* loss = nullptr,
+                  float* out = nullptr);
 }  // namespace inpaint
 
 using namespace inpaint;
@@ -872,6 +873,12 @@ int inpaint_backward(inpaint_ctx* c, const float* x, const uint8_t* hole, const 
                      float* grad_w, void* stream) {
   if (!c || !x || !hole || !grad_out || !grad_w || bad_shape(B, H, W)) return INPAINT_E_INVAL;
   return backward_impl(c, x, hole, grad_out, B, H, W, grad_w, (cudaStream_t)stream);
+}
+
+int inpaint_train_step(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* target, int B, int H, int W,
+                       float* loss, float* grad_w, float* out, void* stream) {
+  if (!c || !x || !hole || !target || !loss || !grad_w || bad_shape(B, H, W)) return INPAINT_E_INVAL;
+  return backward_impl(c, x, hole, nullptr, B, H, W, grad_w, (cudaStream_t)stream, target, loss, out);
 }
 
 int inpaint_sync(inpaint_ctx* c, void* stream, int timeout_ms) {

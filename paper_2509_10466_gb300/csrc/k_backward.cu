@@ -417,8 +417,11 @@ inline unsigned grid1d(size_t n) {
 
 }  // namespace
 
+// gout: dL/dout from the caller; or, with gout null, the loss is taken here: the forward
+// also runs the head and composite (into out, or scratch when out is null), then the
+// hole-L1 loss against target into *loss and its gradient, which the sweep then uses.
 int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const float* gout, int B, int H, int W,
-                  float* gw, cudaStream_t st) {
+                  float* gw, cudaStream_t st, const float* target, float* loss, float* out) {
   const Offsets& o = c->off;
   const int Hp = (H + 31) / 32 * 32, Wp = (W + 31) / 32 * 32;
   const int Ht = Hp / 4, Wt = Wp / 4, Nt = Ht * Wt, M = B * Nt;
@@ -459,6 +462,12 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   const size_t pmax = std::max({r128(d) * r64(3 * d), r128(d) * r64(hid), r128(hid) * r64(d), r128(c1) * r64(d),
                                 r128(c2) * r64(c1), r128(3) * r64(c2), r128(d) * 64});
   const size_t oSA = take(splitA * 2), oSB = take(splitB * 2), oTP = take((size_t)TC_SPLIT_MAX * pmax * 4);
+  // the loss taken here: the output frame (unless the caller's), dL/dout, the partial sums
+  const bool own_loss = gout == nullptr;
+  const size_t frame = (size_t)B * 3 * H * W;
+  const int nbl = own_loss ? loss_partials(B, H, W) : 0;
+  const size_t oOUT = take(own_loss && !out ? frame * 4 : 0), oGOUT = take(own_loss ? frame * 4 : 0);
+  const size_t oLP = take((size_t)nbl * 4), oLC = take((size_t)nbl * 4);
   int rc = grow(&c->bws, &c->bws_bytes, q, c, c->arena_bytes + c->stage_bytes);
   if (rc != INPAINT_OK) return rc;
   uint8_t* ws = c->bws;
@@ -598,6 +607,16 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
   { auto ls = K(K_DEC1); ok(launch_conv3x3_f32(yf, B, Ht, Wt, d, true, c->dec1_wt, w + o.d1b, 1, f1, z1, c1, st)); }
   { auto ls = K(K_DEC2); ok(launch_conv3x3_f32(f1, B, 2 * Ht, 2 * Wt, c1, true, c->dec2_wt, w + o.d2b, 1, f2, z2, c2, st)); }
 
+  if (own_loss) {  // the head and composite of the forward, then the hole-L1 loss and dL/dout
+    float* of = out ? out : F(oOUT);
+    float* g = F(oGOUT);
+    { auto ls = K(K_HEAD); ok(launch_head_composite<float>(f2, B, Hp, Wp, c2, w + o.hw, w + o.hb, x, hole, H, W, of, nullptr, st)); }
+    {
+      auto ls = K(K_OTHER);
+      ok(launch_l1_hole_loss(of, target, hole, B, H, W, F(oLP), reinterpret_cast<unsigned*>(ws + oLC), loss, g, st));
+    }
+    gout = g;
+  }
   // ---- head conv and composite
   { auto ls = K(K_OTHER); pred_grad_kernel<<<grid1d(P2), 256, 0, st>>>(gout, hole, B, H, W, Hp, Wp, gp); }
   conv_wgrad(gp, 3, f2, Hp, Wp, c2, false, P2, o.hw, o.hb);

@@ -127,3 +127,41 @@ def test_autograd_finetune_lowers_loss():
         assert torch.isfinite(g_auto).all() and float(g_auto.abs().sum()) > 0
     finally:
         ft.close()
+
+
+def test_train_step_equals_forward_loss_and_backward():
+    """inpaint_train_step (forward once, in the backward's FP32-accurate form, then the hole-L1
+    loss and the weight gradient) against the separate calls: the same output, loss and
+    gradient within the FP32 tolerances (1e-5 relative on the output, 1e-5 on the loss,
+    1e-4 on the gradient, which the separate path meets against FP64), with and without an
+    output buffer."""
+    cfg = ModelConfig(dim=64, heads=2, window=8, blocks=2, mlp_ratio=2, precision=FP32)
+    weights = S.make_weights(cfg, seed=4, perturb=True)
+    B, H, W = 2, 64, 96
+    x = torch.from_numpy(S.make_frames(B, H, W, seed=4)).cuda()
+    hole = torch.from_numpy(S.make_hole(B, H, W, "ellipse_strokes", seed=4)).cuda()
+    tgt = torch.from_numpy(S.make_target(B, H, W, seed=4)).cuda()
+    binding.load()
+    inp = binding.Inpainter(cfg, weights)
+    try:
+        out = torch.empty_like(x)
+        loss = torch.zeros(1, device="cuda")
+        gout = torch.empty_like(x)
+        gw = torch.empty(inp.n_params, device="cuda")
+        binding.inpaint_batch(inp.ctx, x, hole, out)
+        binding.inpaint_l1_hole_loss(inp.ctx, out, tgt, hole, loss, gout)
+        binding.inpaint_backward(inp.ctx, x, hole, gout, gw)
+        out2 = torch.empty_like(x)
+        loss2 = torch.zeros(1, device="cuda")
+        gw2 = torch.empty(inp.n_params, device="cuda")
+        binding.inpaint_train_step(inp.ctx, x, hole, tgt, loss2, gw2, out2)
+        loss3 = torch.zeros(1, device="cuda")
+        gw3 = torch.empty(inp.n_params, device="cuda")
+        binding.inpaint_train_step(inp.ctx, x, hole, tgt, loss3, gw3)
+        torch.cuda.synchronize()
+        assert float((out2 - out).norm() / out.norm()) < 1e-5
+        assert abs(float(loss2) - float(loss)) <= 1e-5 * abs(float(loss))
+        assert float((gw2 - gw).norm() / gw.norm()) < 1e-4
+        assert torch.equal(loss2, loss3) and torch.equal(gw2, gw3)
+    finally:
+        inp.close()
