@@ -250,7 +250,8 @@ __global__ void subpixel_weights_kernel(const float* __restrict__ w, int Cout, i
 // transposes them through a 2 KB shared tile (32 pixels x 32 channels) and stores 16-byte
 // channel chunks of each output pixel (2 (i0 + py) + a, 2 (j0 + px) + b).
 constexpr int TQ = 16;            // tile = TQ x TQ input pixels
-constexpr int T_STAGES = 4;
+constexpr int TB_ROWS = TQ + 2;   // a column-shifted pixel box spans the three row shifts
+constexpr int A_STAGES = 4, B_STAGES = 2;
 constexpr int T_THREADS = 320;    // warp 0 TMA, warp 1 MMA, warps 2-5 and 6-9: one epilogue group per accumulator
 
 template <int COUT>
@@ -258,10 +259,10 @@ struct DecTCfg {
   static constexpr int NG = 128 / COUT;                 // parities per group (stacked on M)
   static constexpr int GROUPS = 4 / NG;
   static constexpr int NSH = NG == 4 ? 9 : 6;           // input shifts per group
+  static constexpr int NY = NSH / 3;                    // row shifts per group (3 column shifts each)
   static constexpr int A_BYTES = 128 * BK * 2;          // stacked weights of one (shift, chunk)
-  static constexpr int B_BYTES = TQ * TQ * BK * 2;      // the shifted pixel block
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int SMEM_BYTES = T_STAGES * STAGE_BYTES + 1024 + 256 + 8 * 2048;
+  static constexpr int B_BYTES = TB_ROWS * TQ * BK * 2; // pixel rows i0 - 1 .. i0 + TQ at one column shift
+  static constexpr int SMEM_BYTES = A_STAGES * A_BYTES + B_STAGES * B_BYTES + 1024 + 256 + 8 * 2048;
   static_assert(COUT == 32 || COUT == 64, "stacked parities need Cout = 32 or 64");
   static_assert(SMEM_BYTES <= 232448, "exceeds the 227 KB dynamic shared memory of an sm_100-family CTA");
 };
@@ -300,31 +301,42 @@ __global__ void stacked_weights_kernel(const float* __restrict__ w, int Cout, in
   }
 }
 
+// Per tile and 64-channel chunk, the pixel boxes are loaded once per column shift sx, 18
+// rows high (rows i0 - 1 .. i0 + 16); the product of row shift sy reads the 16 x 16 block
+// starting (sy + 1) pixel rows into the box, a contiguous run of 256 K-major rows, so
+// the three (or two) row shifts share one box.  Stacked weights and pixel boxes stream
+// through separate rings.
 template <int COUT, typename T>
 __global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_constant__ CUtensorMap tmIn,
                                                                 const __grid_constant__ CUtensorMap tmW, T* out,
                                                                 int B, int Hi, int Wi, int Cin,
                                                                 const float* __restrict__ bias, int* err) {
   using Cfg = DecTCfg<COUT>;
-  constexpr int NG = Cfg::NG, GROUPS = Cfg::GROUPS, NSH = Cfg::NSH;
+  constexpr int NG = Cfg::NG, GROUPS = Cfg::GROUPS, NSH = Cfg::NSH, NY = Cfg::NY;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + T_STAGES * Cfg::STAGE_BYTES);
-  uint64_t* empty = full + T_STAGES;
-  uint64_t* acc_full = empty + T_STAGES;
+  uint8_t* sA = smem;                                // [A_STAGES][128 x 64] stacked weights
+  uint8_t* sB = smem + A_STAGES * Cfg::A_BYTES;      // [B_STAGES][18 x 16 pixels x 64]
+  uint64_t* afull = reinterpret_cast<uint64_t*>(sB + B_STAGES * Cfg::B_BYTES);
+  uint64_t* aempty = afull + A_STAGES;
+  uint64_t* bfull = aempty + A_STAGES;
+  uint64_t* bempty = bfull + B_STAGES;
+  uint64_t* acc_full = bempty + B_STAGES;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* teardown = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(teardown + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  uint8_t* stage_tiles = smem + T_STAGES * Cfg::STAGE_BYTES + 256;  // [8 epilogue warps][32 pixels][64 B]
+  uint8_t* stage_tiles = sB + B_STAGES * Cfg::B_BYTES + 256;  // [8 epilogue warps][32 pixels][64 B]
+  static_assert((2 * A_STAGES + 2 * B_STAGES + 5) * 8 + 8 <= 256, "barrier area");
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bx_n = (Wi + TQ - 1) / TQ, by_n = (Hi + TQ - 1) / TQ;
   const int tiles = B * by_n * bx_n * GROUPS;
-  const int kc = Cin / BK, nk = NSH * kc;
+  const int kc = Cin / BK;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < T_STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    for (int s = 0; s < A_STAGES; ++s) { tc::mbar_init(&afull[s], 1); tc::mbar_init(&aempty[s], 1); }
+    for (int s = 0; s < B_STAGES; ++s) { tc::mbar_init(&bfull[s], 1); tc::mbar_init(&bempty[s], 1); }
     for (int a = 0; a < 2; ++a) { tc::mbar_init(&acc_full[a], 1); tc::mbar_init(&acc_empty[a], 4); }
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
@@ -355,28 +367,41 @@ __global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_con
 
   if (warp == 0) {
     if (lane == 0) {
-      uint32_t g = 0;
+      uint32_t ga = 0, gb = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
         int grp, j0, i0, img;
         decode(tile, grp, j0, i0, img);
-        for (int kb = 0; kb < nk; ++kb, ++g) {
-          const int s = g % T_STAGES;
-          if (g >= (uint32_t)T_STAGES && !tc::mbar_wait(&empty[s], ((g / T_STAGES) & 1) ^ 1, abort_flag)) {
-            ok = false;
-            break;
+        for (int ck = 0; ck < kc && ok; ++ck)
+          for (int sxi = 0; sxi < 3 && ok; ++sxi) {
+            const int c0 = ck * BK;
+            {  // the pixel box of column shift sxi - 1
+              const int s = gb % B_STAGES;
+              if (gb >= (uint32_t)B_STAGES && !tc::mbar_wait(&bempty[s], ((gb / B_STAGES) & 1) ^ 1, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc::mbar_expect_tx(&bfull[s], Cfg::B_BYTES);
+              tc::tma_load_4d(sB + s * Cfg::B_BYTES, &tmIn, &bfull[s], c0, j0 + sxi - 1, i0 - 1, img);
+              ++gb;
+            }
+            for (int yi = 0; yi < NY; ++yi) {  // the stacked weights of shift (row shift yi, column shift sxi)
+              const int s = ga % A_STAGES;
+              if (ga >= (uint32_t)A_STAGES && !tc::mbar_wait(&aempty[s], ((ga / A_STAGES) & 1) ^ 1, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc::mbar_expect_tx(&afull[s], Cfg::A_BYTES);
+              tc::tma_load_2d(sA + s * Cfg::A_BYTES, &tmW, &afull[s], c0, (grp * NSH + yi * 3 + sxi) * 128);
+              ++ga;
+            }
           }
-          const int sh = kb / kc, c0 = (kb - sh * kc) * BK;
-          int sy, sx;
-          group_shift(NG, grp, sh, sy, sx);
-          uint8_t* sa = smem + s * Cfg::STAGE_BYTES;
-          tc::mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
-          tc::tma_load_2d(sa, &tmW, &full[s], c0, (grp * NSH + sh) * 128);
-          tc::tma_load_4d(sa + Cfg::A_BYTES, &tmIn, &full[s], c0, j0 + sx, i0 + sy, img);
-        }
       }
-      for (uint32_t h = (g > (uint32_t)T_STAGES ? g - T_STAGES : 0); h < g; ++h)
-        if (!tc::mbar_wait_timed(&full[h % T_STAGES], (h / T_STAGES) & 1)) break;
+      // the loads land before the CTA may exit
+      for (uint32_t h = (ga > (uint32_t)A_STAGES ? ga - A_STAGES : 0); h < ga; ++h)
+        if (!tc::mbar_wait_timed(&afull[h % A_STAGES], (h / A_STAGES) & 1)) break;
+      for (uint32_t h = (gb > (uint32_t)B_STAGES ? gb - B_STAGES : 0); h < gb; ++h)
+        if (!tc::mbar_wait_timed(&bfull[h % B_STAGES], (h / B_STAGES) & 1)) break;
       if (!ok) {
         if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
         *abort_flag = 1;
@@ -386,24 +411,40 @@ __global__ void __launch_bounds__(T_THREADS, 1) upconv_t_kernel(const __grid_con
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_f32acc(H16<T>::kMmaFmt, 128, TQ * TQ);
-      uint32_t g = 0, i = 0;
+      uint32_t ga = 0, gb = 0, i = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++i) {
+        int grp, j0, i0, img;
+        decode(tile, grp, j0, i0, img);
         const uint32_t acc = i & 1, use = i >> 1;
         if (use >= 1 && !tc::mbar_wait(&acc_empty[acc], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
         tc::fence_after_sync();
         const uint32_t dtm = tmem_base + acc * (TQ * TQ);
-        for (int kb = 0; kb < nk; ++kb, ++g) {
-          const int s = g % T_STAGES;
-          if (!tc::mbar_wait(&full[s], (g / T_STAGES) & 1, abort_flag)) { ok = false; break; }
-          tc::fence_after_sync();
-          const uint32_t sa = tc::smem_u32(smem + s * Cfg::STAGE_BYTES);
-          const uint64_t ad = tc::desc_kmajor_sw128(sa);
-          const uint64_t bd = tc::desc_kmajor_sw128(sa + Cfg::A_BYTES);
+        bool first = true;
+        for (int ck = 0; ck < kc && ok; ++ck)
+          for (int sxi = 0; sxi < 3 && ok; ++sxi) {
+            const int sb = gb % B_STAGES;
+            if (!tc::mbar_wait(&bfull[sb], (gb / B_STAGES) & 1, abort_flag)) { ok = false; break; }
+            ++gb;
+            for (int yi = 0; yi < NY; ++yi) {
+              const int sa = ga % A_STAGES;
+              if (!tc::mbar_wait(&afull[sa], (ga / A_STAGES) & 1, abort_flag)) { ok = false; break; }
+              ++ga;
+              tc::fence_after_sync();
+              // row shift sy = yi - 1 (four parities) or grp - 1 + yi (two): the block starts
+              // sy + 1 pixel rows (of 16 x 128 B) into the box
+              const int r0 = NG == 4 ? yi : grp + yi;
+              const uint64_t ad = tc::desc_kmajor_sw128(tc::smem_u32(sA + sa * Cfg::A_BYTES));
+              const uint64_t bd = tc::desc_kmajor_sw128(tc::smem_u32(sB + sb * Cfg::B_BYTES + r0 * TQ * 128));
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) tc::mma_f16(dtm, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
-          tc::mma_commit(&empty[s]);
-        }
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                tc::mma_f16(dtm, ad + 2 * kk, bd + 2 * kk, idesc, first ? 0u : 1u);
+                first = false;
+              }
+              tc::mma_commit(&aempty[sa]);
+            }
+            tc::mma_commit(&bempty[sb]);
+          }
         if (ok) tc::mma_commit(&acc_full[acc]);
       }
       if (!ok) {
@@ -560,7 +601,7 @@ cudaError_t launch_t_cout(const T* in, int B, int Hi, int Wi, int Cin, const T* 
   {
     cuuint64_t dims[4] = {(cuuint64_t)Cin, (cuuint64_t)Wi, (cuuint64_t)Hi, (cuuint64_t)B};
     cuuint64_t strides[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)Wi * Cin * 2, (cuuint64_t)Hi * Wi * Cin * 2};
-    cuuint32_t box[4] = {BK, TQ, TQ, 1};
+    cuuint32_t box[4] = {BK, TQ, TB_ROWS, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     if (fn(&mi, tc::tma_dtype<T>(), 4, const_cast<T*>(in), dims, strides, box, es,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
