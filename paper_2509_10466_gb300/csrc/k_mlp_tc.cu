@@ -39,8 +39,10 @@
 // so three warps per lane quarter share both drains by columns (at D = 256: 64 columns
 // for the final warp, 96 for each GELU warp; at D = 128: half and two quarters).  The three exchange per-row
 // partial statistics (Welford) through shared memory and merge them in one fixed order.
-// Residual rows are prefetched to L2 a tile ahead, then loaded one 32-column block ahead;
-// rows move in whole 64-byte segments (warp_rows.cuh) and leave by TMA stores.
+// Residual rows are prefetched to L2 a tile ahead; the first 32-column block of each GELU
+// warp's slice (all 128 rows of the CTA) is loaded by TMA into shared memory a tile ahead,
+// the other blocks one block ahead into registers; rows move in whole 64-byte segments
+// (warp_rows.cuh) and leave by TMA stores.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -88,18 +90,22 @@ struct MlpCfg {
   static constexpr int W2_BOX = (D / 2) * BK * 2;             // this CTA's half of a Wp or W2 k-block (D/2 rows)
   static constexpr int PARAM_FLOATS = 1024 + 2 * D;          // b1 (hid <= 1024), b2, bp
   // 16 KB weight stages: as many as fit (up to two chunks' worth; four, one chunk, at D = 256)
-  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 2 * D) * 4 +
-                                     1024 /*tile alignment*/ + DRAIN_TILES * rows::TILE_BYTES + 3 * BM * 2 * 4;
-  static constexpr int RING_FIT = (232448 - FIXED_BYTES) / STAGE_BYTES;
-  static constexpr int RING = RING_FIT < 8 ? RING_FIT : 8;
-  static_assert(RING >= 4, "weight ring too shallow");
-  static constexpr int SMEM_BYTES = A_BYTES + RING * STAGE_BYTES + 1024 /*align slack*/ +
-                                    512 /*barriers*/ + PARAM_FLOATS * 4 + 1024 /*tile alignment*/ +
-                                    DRAIN_TILES * rows::TILE_BYTES /*staging tiles of the drain warps*/ +
-                                    3 * BM * 2 * 4 /*partial row statistics of the three drain slices*/;
   // Drain column slices, in 32-column blocks: the final warp takes the first FS blocks,
   // each GELU warp GS blocks (none when D = 64), as even as 32-column blocks allow.
   static constexpr int NCH = D / 32, GS = NCH == 8 ? 3 : NCH / 4, FS = NCH - 2 * GS;
+  // the first residual block of each GELU warp's slice (all 128 rows), loaded by TMA a tile
+  // ahead: two blocks of 128 rows x 32 FP32 columns
+  static constexpr int RES_BYTES = GS > 0 ? 2 * BM * 32 * 4 : 0;
+  static constexpr int FIXED_BYTES = A_BYTES + 1024 /*align slack*/ + 512 /*barriers*/ + (1024 + 2 * D) * 4 +
+                                     1024 /*tile alignment*/ + DRAIN_TILES * rows::TILE_BYTES + 3 * BM * 2 * 4 +
+                                     RES_BYTES;
+  static constexpr int RING_FIT = (232448 - FIXED_BYTES) / STAGE_BYTES;
+  static constexpr int RING = RING_FIT < 8 ? RING_FIT : 8;
+  static_assert(RING >= 4, "weight ring too shallow");
+  static constexpr int SMEM_BYTES = A_BYTES + RING * STAGE_BYTES + RES_BYTES + 1024 /*align slack*/ +
+                                    512 /*barriers*/ + PARAM_FLOATS * 4 + 1024 /*tile alignment*/ +
+                                    DRAIN_TILES * rows::TILE_BYTES /*staging tiles of the drain warps*/ +
+                                    3 * BM * 2 * 4 /*partial row statistics of the three drain slices*/;
   static constexpr int H_COL0 = 256;                          // H buffers at TMEM columns 256 + HC b
   static_assert(H_COL0 + D <= 512 && NB * HC >= D, "MMA_P's accumulator lives in the H buffers' columns");
   static_assert(W1_KB * W1_BOX <= STAGE_BYTES && W2_BOX <= STAGE_BYTES, "stage too small");
@@ -126,6 +132,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
                                                             const __grid_constant__ CUtensorMap tmW2,
                                                             const __grid_constant__ CUtensorMap tmX,
                                                             const __grid_constant__ CUtensorMap tmLN,
+                                                            const __grid_constant__ CUtensorMap tmXr,
                                                             const MlpArgs args) {
   using Cfg = MlpCfg<D>;
   constexpr int RING = Cfg::RING;
@@ -133,7 +140,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sR = sA + Cfg::A_BYTES;                      // ring
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sR + RING * Cfg::STAGE_BYTES);
+  uint8_t* s_res = sR + RING * Cfg::STAGE_BYTES;       // [2][128 rows x 128 B], 128-byte swizzle
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_res + Cfg::RES_BYTES);
   uint64_t* full = bar;                 // [RING]  even CTA: both CTAs' weight bytes
   uint64_t* empty = full + RING;        // [RING]  both: stage consumed by the pair's MMAs
   uint64_t* a_full = empty + RING;      //         even CTA: both CTAs' A bytes
@@ -145,7 +153,9 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   uint64_t* o_full = h_done + NB;       //         both: OUT complete
   uint64_t* teardown = o_full + 1;
   uint64_t* stat_bar = teardown + 1;    // [4]     per lane quarter: the three drain slices' statistics
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(stat_bar + 4);
+  uint64_t* res_full = stat_bar + 4;    //         this CTA: the GELU warps' first residual blocks landed
+  uint64_t* res_empty = res_full + 1;   //         this CTA: the GELU warps read them
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(res_empty + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* s_b1 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bar) + 512);  // [hid]
   float* s_b2 = s_b1 + 1024;                                                      // [D]
@@ -178,6 +188,8 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     }
     tc::mbar_init(o_full, 1);
     for (int k = 0; k < 4; ++k) tc::mbar_init(&stat_bar[k], 3 * 32);
+    tc::mbar_init(res_full, 1);
+    tc::mbar_init(res_empty, EPI_WARPS);
     tc::mbar_init(teardown, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -185,6 +197,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     tc::prefetch_tmap(&tmWp);
     tc::prefetch_tmap(&tmW1);
     tc::prefetch_tmap(&tmW2);
+    tc::prefetch_tmap(&tmXr);
   }
   if (warp == 1) {  // one warp of each CTA allocates the pair's TMEM together
     tc::tmem_alloc_pair(tmem_slot, 512);
@@ -262,8 +275,11 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
     const int row0 = (2 * p + rank) * BM + quarter * 32;
     const int nvalid = M - row0;
     const float* xb = args.X + (size_t)row0 * D;
-    float4 gn[8];  // the next block's residual, loaded one block ahead (the first while MMA_P runs)
-    if (nch > 0) rows::load32_issue(xb + c_lo, D, nvalid, lane, gn);
+    // a GELU warp's first block comes from the TMA-loaded residual tile; the next block's
+    // residual is loaded one block ahead (the first of them while MMA_P runs)
+    const bool pre = Cfg::GS > 0 && role > 0;
+    float4 gn[8];
+    if (nch > (pre ? 1 : 0)) rows::load32_issue(xb + c_lo + (pre ? 32 : 0), D, nvalid, lane, gn);
     if (lane == 0) tc::bulk_wait_read<0>();  // the previous tile's stores are done with `tl`
     if (!tc::mbar_wait(p_full, t & 1, abort_flag)) return false;
     __syncwarp();
@@ -275,8 +291,20 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         uint32_t v[32];
         tc::tmem_ld_32x32b_x32(lane_base + Cfg::H_COL0 + c0, v);
         float f[32];
-        rows::load32_finish(tl, lane, gn, f);
-        if (c0 + 32 < c_lo + 32 * nch) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
+        if (pre && c0 == c_lo) {  // row r of the prefetched block (128-byte rows, 128-byte swizzle)
+          if (!tc::mbar_wait(res_full, t & 1, abort_flag)) return false;
+          const uint8_t* rb = s_res + (role - 1) * (BM * 128) + r * 128;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 q4 = *reinterpret_cast<const float4*>(rb + ((c ^ (r & 7)) << 4));
+            f[4 * c] = q4.x; f[4 * c + 1] = q4.y; f[4 * c + 2] = q4.z; f[4 * c + 3] = q4.w;
+          }
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(res_empty);  // read: the next tile's block may land
+        } else {
+          rows::load32_finish(tl, lane, gn, f);
+          if (c0 + 32 < c_lo + 32 * nch) rows::load32_issue(xb + c0 + 32, D, nvalid, lane, gn);
+        }
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; k += 4) {
@@ -398,6 +426,16 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
           if (m0 < M)
             for (int kb = 0; kb < Cfg::KA; ++kb)
               tc::tma_load_2d_pair(sA + kb * (BM * BK * 2), &tmA, lead(a_full), kb * BK, m0);
+          if constexpr (Cfg::GS > 0) {  // the GELU warps' first residual blocks of this tile
+            if (t >= 1 && !tc::mbar_wait(res_empty, (t - 1) & 1, abort_flag)) { ok = false; break; }
+            if (m0 < M) {
+              tc::mbar_expect_tx(res_full, Cfg::RES_BYTES);
+              for (int g = 0; g < 2; ++g)
+                tc::tma_load_2d(s_res + g * (BM * 128), &tmXr, res_full, 32 * (Cfg::FS + g * Cfg::GS), m0);
+            } else {
+              tc::mbar_arrive(res_full);  // no rows: the phase completes without bytes
+            }
+          }
           for (int kb = 0; kb < Cfg::KA && ok; ++kb)  // the projection's k-blocks first
             ok = push(&tmWp, 1, kb * BK, rank * (D / 2), Cfg::W2_BOX);
           for (int j = 0; j < NJ + LOOK && ok; ++j) {  // the MMA warp's consumption order
@@ -414,6 +452,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         for (uint32_t h = (g > (uint32_t)RING ? g - RING : 0); h < g; ++h)
           if (!tc::mbar_wait_timed(&empty[h % RING], (h / RING) & 1)) break;
         if (t >= 1) tc::mbar_wait_timed(a_empty, (t - 1) & 1);
+        if (Cfg::GS > 0 && t >= 1) tc::mbar_wait_timed(res_full, (t - 1) & 1);
         if (!ok) {
           if (err) atomicExch(err, DEV_MBAR_TIMEOUT);
           *abort_flag = 1;
@@ -651,6 +690,20 @@ bool store_map(CUtensorMap* m, const void* base, bool f32, CUtensorMapDataType d
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Load map of the FP32 residual stream [rows][inner]: boxes of 32 columns (128 bytes) x 128
+// rows, 128-byte swizzle (the GELU warps' prefetched first residual block).
+bool residual_map(CUtensorMap* m, const float* base, uint64_t inner, uint64_t rows) {
+  auto fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 4};
+  cuuint32_t box[2] = {32, BM};
+  cuuint32_t ess[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, ess,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -690,17 +743,18 @@ cudaError_t launch_d(const T* A, const T* Wpt, const T* W1t, const T* W2t, const
     if (e != cudaSuccess) return e;
     max_pairs = n > 0 ? n : 1;
   }
-  CUtensorMap ma, mp, m1, m2, mx, mln;
+  CUtensorMap ma, mp, m1, m2, mx, mln, mxr;
   if (!map2d(&ma, dt, A, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
   if (!map2d(&mp, dt, Wpt, D, D, BK, D / 2)) return cudaErrorInvalidValue;
   if (!store_map(&mx, a.X, true, dt, D, (uint64_t)a.M) || !store_map(&mln, a.ln_out, false, dt, D, (uint64_t)a.M))
     return cudaErrorInvalidValue;
   if (!map2d(&m1, dt, W1t, D, (uint64_t)a.hid, BK, HC / 2)) return cudaErrorInvalidValue;
   if (!map2d(&m2, dt, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;
+  if (!residual_map(&mxr, a.X, D, (uint64_t)a.M)) return cudaErrorInvalidValue;
   const int pairs = ((a.M + BM - 1) / BM + 1) / 2;
   lc.gridDim = dim3((pairs < max_pairs ? pairs : max_pairs) * 2);
   lc.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&lc, kern, ma, mp, m1, m2, mx, mln, a);
+  cudaError_t e = cudaLaunchKernelEx(&lc, kern, ma, mp, m1, m2, mx, mln, mxr, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
