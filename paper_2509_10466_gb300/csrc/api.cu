@@ -808,23 +808,32 @@ int inpaint_batch_host(inpaint_ctx* c, const float* xh, const uint8_t* hh, int B
   TRY(cuda_err(cudaEventRecord(c->start_ev, st)));
   TRY(cuda_err(cudaStreamWaitEvent(cs, c->start_ev, 0)));
   const size_t HW = (size_t)H * W;
-  for (int f = 0; f < B; ++f) {
-    TRY(cuda_err(cudaMemcpyAsync(xd + f * 3 * HW, xh + f * 3 * HW, 3 * HW * 4, cudaMemcpyHostToDevice, cs)));
-    TRY(cuda_err(cudaMemcpyAsync(hd + f * HW, hh + f * HW, HW, cudaMemcpyHostToDevice, cs)));
-    TRY(cuda_err(cudaEventRecord(c->in_ev[f], cs)));
-  }
-  const FramePipe pipe{c->in_ev.data(), c->out_ev.data()};
   c->have_masks = false;
-  TRY(run_forward(c, c->arena, p, xd, hd, od, nullptr, st, nullptr, &pipe));
+  auto run = [&]() -> int {
+    for (int f = 0; f < B; ++f) {
+      TRY(cuda_err(cudaMemcpyAsync(xd + f * 3 * HW, xh + f * 3 * HW, 3 * HW * 4, cudaMemcpyHostToDevice, cs)));
+      TRY(cuda_err(cudaMemcpyAsync(hd + f * HW, hh + f * HW, HW, cudaMemcpyHostToDevice, cs)));
+      TRY(cuda_err(cudaEventRecord(c->in_ev[f], cs)));
+    }
+    const FramePipe pipe{c->in_ev.data(), c->out_ev.data()};
+    TRY(run_forward(c, c->arena, p, xd, hd, od, nullptr, st, nullptr, &pipe));
+    for (int f = 0; f < B; ++f) {
+      TRY(cuda_err(cudaStreamWaitEvent(cs, c->out_ev[f], 0)));
+      TRY(cuda_err(cudaMemcpyAsync(oh + f * 3 * HW, od + f * 3 * HW, 3 * HW * 4, cudaMemcpyDeviceToHost, cs)));
+    }
+    TRY(cuda_err(cudaEventRecord(c->done_ev, cs)));
+    TRY(cuda_err(cudaStreamWaitEvent(st, c->done_ev, 0)));  // the caller's stream sees the results
+    return cuda_err(cudaStreamSynchronize(cs));
+  };
+  const int rc = run();
+  if (rc != INPAINT_OK) {  // no copy of the caller's host buffers may still be in flight
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(st);
+    return rc;
+  }
   c->last = p;
   c->have_masks = true;
-  for (int f = 0; f < B; ++f) {
-    TRY(cuda_err(cudaStreamWaitEvent(cs, c->out_ev[f], 0)));
-    TRY(cuda_err(cudaMemcpyAsync(oh + f * 3 * HW, od + f * 3 * HW, 3 * HW * 4, cudaMemcpyDeviceToHost, cs)));
-  }
-  TRY(cuda_err(cudaEventRecord(c->done_ev, cs)));
-  TRY(cuda_err(cudaStreamWaitEvent(st, c->done_ev, 0)));  // the caller's stream sees the results
-  return cuda_err(cudaStreamSynchronize(cs));
+  return INPAINT_OK;
 }
 
 int inpaint_token_masks(inpaint_ctx* c, uint8_t* host, size_t n) {
