@@ -116,6 +116,13 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem_base = tmem_slot;
+  // this CTA's contiguous share of the (window pair, head pass) items, pair-major: pairs
+  // u_lo .. u_hi, from pass p_lo(u_lo) of the first to pass p_hi(u_hi) - 1 of the last
+  const long long items = (long long)args.units * P;
+  const int lo = (int)(items * blockIdx.x / gridDim.x), hi = (int)(items * (blockIdx.x + 1) / gridDim.x);
+  const int u_lo = lo / P, u_hi = (hi - 1) / P;
+  auto p_lo = [&](int u) { return u == u_lo ? lo - u * P : 0; };
+  auto p_hi = [&](int u) { return u == u_hi ? hi - u * P : P; };
   pdl_trigger();
   pdl_wait();
 
@@ -123,7 +130,7 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
     if (lane == 0) {
       bool ok = true;
       uint32_t g = 0, i = 0;
-      for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x, ++i) {
+      for (int u = u_lo; u <= u_hi && ok; ++u, ++i) {
         const int b = u / pairs, w0 = 2 * (u - b * pairs), nh = w0 + 1 < args.nwin ? 2 : 1;
         // Y boxes of the pair: k-block kb of window k at rows 64k of tile kb, once the
         // previous pair's MMAs have read sY
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
             tc::tma_load_4d(sY + kb * QA_BM * QA_BK * 2 + k * WA_SLOTS * QA_BK * 2, &tmY, &a_full, kb * QA_BK,
                             wx * 8 - args.offset, wy * 8 - args.offset, b);
         }
-        for (int p = 0; p < P && ok; ++p)
+        for (int p = p_lo(u); p < p_hi(u) && ok; ++p)
           for (int kb = 0; kb < KA; ++kb, ++g) {
             const int s = g % QA_RING;
             if (g >= (uint32_t)QA_RING && !tc::mbar_wait(&empty[s], ((g / QA_RING) & 1) ^ 1, &abort_flag)) {
@@ -163,10 +170,10 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
       const uint32_t idesc = tc::idesc_f32acc(H16<T>::kMmaFmt, QA_BM, QA_N);
       bool ok = true;
       uint32_t g = 0, gp = 0, i = 0;
-      for (int u = blockIdx.x; u < args.units && ok; u += gridDim.x, ++i) {
+      for (int u = u_lo; u <= u_hi && ok; ++u, ++i) {
         if (!tc::mbar_wait(&a_full, i & 1, &abort_flag)) { ok = false; break; }
         tc::fence_after_sync();
-        for (int p = 0; p < P && ok; ++p, ++gp) {
+        for (int p = p_lo(u); p < p_hi(u) && ok; ++p, ++gp) {
           const uint32_t buf = gp & 1, use = gp >> 1;
           if (use >= 1 && !tc::mbar_wait(&acc_empty[buf], (use & 1) ^ 1, &abort_flag)) { ok = false; break; }
           tc::fence_after_sync();
@@ -215,12 +222,12 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
         if (t_next >= 0) ok_next = args.v_in[t_next] != 0;
       }
     };
-    fetch(blockIdx.x);
+    fetch(u_lo);
     // every attention warp passes every named barrier of every pair, also after a failed
     // wait (then skipping the work), so that no warp waits for a peer that has left
     bool ok = true;
     uint32_t gp = 0;
-    for (int u = blockIdx.x; u < args.units; u += gridDim.x) {
+    for (int u = u_lo; u <= u_hi; ++u) {
       const int b = u / pairs, nh = 2 * (u - b * pairs) + 1 < args.nwin ? 2 : 1;
       named_sync(3, 32 * QA_ATT_WARPS);  // the previous pair's windows are no longer read
       if (e < 2 * WA_SLOTS) {
@@ -229,9 +236,11 @@ __global__ void __launch_bounds__(QA_THREADS, 1) qkv_attn_kernel(const __grid_co
         if (lane == 0) okw[e >> 6][(e >> 5) & 1] = bal;
       }
       named_sync(3, 32 * QA_ATT_WARPS);
-      if (e < 2 * WA_SLOTS && t_next >= 0) args.v_out[t_next] = (okw[e >> 6][0] | okw[e >> 6][1]) != 0u;
-      fetch(u + gridDim.x);
-      for (int p = 0; p < P; ++p, ++gp) {
+      // the next block's token mask of the pair: written by the CTA that runs its first pass
+      if (p_lo(u) == 0 && e < 2 * WA_SLOTS && t_next >= 0)
+        args.v_out[t_next] = (okw[e >> 6][0] | okw[e >> 6][1]) != 0u;
+      fetch(u < u_hi ? u + 1 : args.units);
+      for (int p = p_lo(u); p < p_hi(u); ++p, ++gp) {
         const uint32_t buf = gp & 1, use = gp >> 1;
         const int hg = 2 * p + hh;
         if (ok && !tc::mbar_wait(&acc_full[buf], use & 1, &abort_flag)) ok = false;
@@ -336,7 +345,8 @@ cudaError_t launch_t(const CUtensorMap& my, const CUtensorMap& mw, const QaArgs&
     if (e != cudaSuccess) return e;
     attr = smem;
   }
-  const dim3 grid(a.units < num_sms() ? a.units : num_sms());
+  const int items = a.units * (a.heads / 2);  // (window pair, head pass) items
+  const dim3 grid(items < num_sms() ? items : num_sms());
   return launch_pdl(qkv_attn_kernel<RP, T>, grid, dim3(QA_THREADS), (size_t)smem, st, my, mw, a);
 }
 
