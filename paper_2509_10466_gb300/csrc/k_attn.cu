@@ -444,27 +444,43 @@ __global__ void __launch_bounds__(TMA_THREADS, 5) attn_mem_tma_kernel(
   // for every slot, empty ones too, so that slot j is group j): every real token's row
   // (recorded k | v values, finite), zeros for void slots; the usable-key masks, read
   // meanwhile, select the keys in the softmax
+  // (row, part, 16-byte chunk) e = tid + 128 q of every slot: the rows' byte offsets and
+  // validity, the same for every slot
+  constexpr int CP_PER_THREAD = SLOTS * 8 / TMA_THREADS;
+  static_assert(SLOTS * 8 % TMA_THREADS == 0, "memory row copies per thread");
+  const int cpart = (tid >> 2) & 1, cc = tid & 3;
+  size_t src_off[CP_PER_THREAD];
+  bool src_ok[CP_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < CP_PER_THREAD; ++q) {
+    const int i = sidx[(tid + q * TMA_THREADS) >> 3];
+    src_ok[q] = i >= 0;
+    src_off[q] = i >= 0 ? (((size_t)i * 2 + cpart) * d + (size_t)h * DH) * sizeof(T) + cc * 16 : 0;
+  }
   for (int j = 0; j < m; ++j) {
     const uint8_t* base = mem_tab.p[b * m + j];
     if (base) {
       const uint8_t* kv = base + off_kv;
-      for (int e = tid; e < SLOTS * 8; e += TMA_THREADS) {  // (row, part, 16-byte chunk)
-        const int r = e >> 3, part = (e >> 2) & 1, c = e & 3;
-        const int i = sidx[r];
-        const uint8_t* src = i >= 0 ? kv + (((size_t)i * 2 + part) * d + (size_t)h * DH) * sizeof(T) + c * 16 : kv;
-        cp_async16z((part ? mV(j) : mK(j)) + r * MROW + c * 16, src, i >= 0);
-      }
+      uint8_t* dst = (cpart ? mV(j) : mK(j)) + cc * 16;
+#pragma unroll
+      for (int q = 0; q < CP_PER_THREAD; ++q)
+        cp_async16z(dst + ((tid + q * TMA_THREADS) >> 3) * MROW, kv + src_off[q], src_ok[q]);
     }
     cp_async_commit();
   }
-  if (tid < SLOTS) {
+  if (tid < SLOTS) {  // every mask byte is loaded before the first ballot
     const int i = sidx[tid];
-    unsigned bal = __ballot_sync(0xffffffffu, i >= 0 && v_in[b * Nt + i] != 0);
-    if (lane == 0) okw[0][warp] = bal;
-    for (int j = 0; j < m; ++j) {
-      const uint8_t* base = mem_tab.p[b * m + j];
-      bal = __ballot_sync(0xffffffffu, i >= 0 && base && base[off_mask + i] != 0);
-      if (lane == 0) okw[1 + j][warp] = bal;
+    bool use[1 + MEM_SLOTS_MAX];
+    use[0] = i >= 0 && v_in[b * Nt + i] != 0;
+#pragma unroll
+    for (int j = 0; j < MEM_SLOTS_MAX; ++j) {
+      const uint8_t* base = j < m ? mem_tab.p[b * m + j] : nullptr;
+      use[1 + j] = i >= 0 && base && base[off_mask + i] != 0;
+    }
+#pragma unroll
+    for (int j = 0; j <= MEM_SLOTS_MAX; ++j) {
+      const unsigned bal = __ballot_sync(0xffffffffu, use[j]);
+      if (lane == 0 && j <= m) okw[j][warp] = bal;
     }
   }
   __syncthreads();
@@ -516,8 +532,15 @@ __global__ void __launch_bounds__(TMA_THREADS, 5) attn_mem_tma_kernel(
     ldsm_x4(qa[1], Qt + swz64(row, 2 + (lane >> 4)));
   }
   const float sl2 = 1.4426950408889634f / sqrtf((float)DH);  // scale * log2(e)
-  float mx0 = -INFINITY, mx1 = -INFINITY, l0 = 0.f, l1 = 0.f;
-  float oc[4][4];
+  // Without the relative-position bias the running maxima are taken on the raw scores (the
+  // scale is positive) and the scale enters with the maximum in one FMA in the exponent;
+  // with it the scores are scaled and biased first (sx = 1).  The running row sums are
+  // those of the 16-bit probabilities, by one more MMA against ones per block (every
+  // column of `ls` holds its row's sum).
+  const float sx = RP ? 1.f : sl2;
+  const uint32_t ones = H16<T>::pack2(1.f, 1.f);
+  float mx0 = -INFINITY, mx1 = -INFINITY;
+  float oc[4][4], ls[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int j = 0; j < 4; ++j) oc[j][0] = oc[j][1] = oc[j][2] = oc[j][3] = 0.f;
   for (int kb = 0; kb <= m; ++kb) {
@@ -544,43 +567,54 @@ __global__ void __launch_bounds__(TMA_THREADS, 5) attn_mem_tma_kernel(
       mma16816<T>(sc[j], qa[1], kbf[2], kbf[3]);
     }
     float bm0 = -INFINITY, bm1 = -INFINITY;
+    const unsigned long long kq = km >> (2 * tq);  // bit 8j + c: key 8j + 2tq + c
+    auto mask_and_max = [&](auto masked) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < 8; ++j) {
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int key = 8 * j + 2 * tq + c;
-        const bool okk = (km >> key) & 1ull;
-        const float bb0 = RP ? rps[relpos_index(r0 + g, key)] * LOG2E : 0.f;
-        const float bb1 = RP ? rps[relpos_index(r0 + g + 8, key)] * LOG2E : 0.f;
-        sc[j][c] = okk ? (RP ? fmaf(sc[j][c], sl2, bb0) : sc[j][c] * sl2) : -INFINITY;
-        sc[j][2 + c] = okk ? (RP ? fmaf(sc[j][2 + c], sl2, bb1) : sc[j][2 + c] * sl2) : -INFINITY;
-        bm0 = fmaxf(bm0, sc[j][c]);
-        bm1 = fmaxf(bm1, sc[j][2 + c]);
+        for (int c = 0; c < 2; ++c) {
+          const bool okk = (kq >> (8 * j + c)) & 1ull;
+          if constexpr (RP) {
+            const int key = 8 * j + 2 * tq + c;
+            const float bb0 = rps[relpos_index(r0 + g, key)] * LOG2E;
+            const float bb1 = rps[relpos_index(r0 + g + 8, key)] * LOG2E;
+            sc[j][c] = okk ? fmaf(sc[j][c], sl2, bb0) : -INFINITY;
+            sc[j][2 + c] = okk ? fmaf(sc[j][2 + c], sl2, bb1) : -INFINITY;
+          } else if constexpr (decltype(masked)::value) {
+            sc[j][c] = okk ? sc[j][c] : -INFINITY;
+            sc[j][2 + c] = okk ? sc[j][2 + c] : -INFINITY;
+          }
+          bm0 = fmaxf(bm0, sc[j][c]);
+          bm1 = fmaxf(bm1, sc[j][2 + c]);
+        }
       }
-    }
+    };
+    // a block whose 64 keys are all usable skips the selects
+    if (RP || km != ~0ull) mask_and_max(BoolTag<true>{});
+    else mask_and_max(BoolTag<false>{});
     bm0 = fmaxf(bm0, __shfl_xor_sync(0xffffffffu, bm0, 1));
     bm0 = fmaxf(bm0, __shfl_xor_sync(0xffffffffu, bm0, 2));
     bm1 = fmaxf(bm1, __shfl_xor_sync(0xffffffffu, bm1, 1));
     bm1 = fmaxf(bm1, __shfl_xor_sync(0xffffffffu, bm1, 2));
+    // every row sees a usable key of this block (km != 0), so the new maxima are finite
     const float n0 = fmaxf(mx0, bm0), n1 = fmaxf(mx1, bm1);
-    const float a0 = ex2_approx(mx0 - n0), a1 = ex2_approx(mx1 - n1);  // 0 on the first usable block
+    const float a0 = ex2_approx((mx0 - n0) * sx), a1 = ex2_approx((mx1 - n1) * sx);  // 0 on the first usable block
     mx0 = n0;
     mx1 = n1;
-    l0 *= a0;
-    l1 *= a1;
+    ls[0] *= a0; ls[1] *= a0;
+    ls[2] *= a1; ls[3] *= a1;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       oc[j][0] *= a0; oc[j][1] *= a0;
       oc[j][2] *= a1; oc[j][3] *= a1;
     }
+    const float o0 = -n0 * sx, o1 = -n1 * sx;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        sc[j][c] = ex2_approx(sc[j][c] - mx0);
-        sc[j][2 + c] = ex2_approx(sc[j][2 + c] - mx1);
-        l0 += sc[j][c];
-        l1 += sc[j][2 + c];
+        sc[j][c] = ex2_approx(fmaf(sc[j][c], sx, o0));
+        sc[j][2 + c] = ex2_approx(fmaf(sc[j][2 + c], sx, o1));
       }
     }
 #pragma unroll
@@ -597,12 +631,10 @@ __global__ void __launch_bounds__(TMA_THREADS, 5) attn_mem_tma_kernel(
         mma16816<T>(oc[2 * nn], pa, vb[0], vb[1]);
         mma16816<T>(oc[2 * nn + 1], pa, vb[2], vb[3]);
       }
+      mma16816<T>(ls, pa, ones, ones);
     }
   }
-  l0 += __shfl_xor_sync(0xffffffffu, l0, 1);
-  l0 += __shfl_xor_sync(0xffffffffu, l0, 2);
-  l1 += __shfl_xor_sync(0xffffffffu, l1, 1);
-  l1 += __shfl_xor_sync(0xffffffffu, l1, 2);
+  const float l0 = ls[0], l1 = ls[2];
   const float inv0 = 1.f / l0, inv1 = 1.f / l1;
   __syncwarp();
   // stage this warp's 16 output rows in its own Q rows, then store 16-byte chunks
