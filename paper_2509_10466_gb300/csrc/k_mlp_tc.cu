@@ -122,6 +122,7 @@ struct MlpArgs {
   const float* ln_b;
   int M, hid;
   int* err;
+  unsigned stagger_ns;   // start delay of the CTA pairs that get one tile fewer than the others
 };
 
 
@@ -215,6 +216,14 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
   const uint32_t tmem_base = *tmem_slot;
   pdl_trigger();
   pdl_wait();
+  // Every pair runs the same sequence of phases, and the drains (tensor core idle, all of the
+  // tile's HBM traffic) would otherwise start on every SM at the same moment.  The pairs that
+  // get one tile fewer than the others start about half a tile late: that costs them nothing
+  // (they still finish before the others) and puts their drains between those of the others.
+  if (args.stagger_ns && pairs % ncl != 0 && cid >= pairs % ncl) {
+    const uint64_t t0 = tc::globaltimer();
+    while (tc::globaltimer() - t0 < args.stagger_ns) __nanosleep(256);
+  }
 
   // Both drains of pair p's tile (the t-th of this CTA) run in three warps per lane
   // quarter (warp & 3, 32 rows, the thread owning row row0 + lane), each over its slice of
@@ -773,7 +782,10 @@ cudaError_t launch_proj_mlp_tc(const T* A, const T* Wpt, const float* bp, const 
        reinterpret_cast<uintptr_t>(W2t) | reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(ln_out)) & 15)
     return cudaErrorInvalidValue;
   if ((ln_g == nullptr) != (ln_b == nullptr)) return cudaErrorInvalidValue;
-  MlpArgs a{X, ln_out, bp, b1, b2, ln_g, ln_b, M, hid, err};
+  // about half of a tile's time: 256 rows x D x (D + 2 hid) multiply-adds at 10.8 TFLOP/s
+  // per CTA pair, the rate that the D = 256, hid = 1024 tiles reach
+  const unsigned stagger = (unsigned)(2.0 * 256 * d * (d + 2.0 * hid) / 10.8e12 * 0.5 * 1e9);
+  MlpArgs a{X, ln_out, bp, b1, b2, ln_g, ln_b, M, hid, err, stagger};
   if (d == 256) return launch_d<256, T>(A, Wpt, W1t, W2t, a, st);
   if (d == 128) return launch_d<128, T>(A, Wpt, W1t, W2t, a, st);
   return launch_d<64, T>(A, Wpt, W1t, W2t, a, st);
