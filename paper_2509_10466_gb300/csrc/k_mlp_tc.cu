@@ -42,7 +42,9 @@
 // Residual rows are prefetched to L2 a tile ahead; the first 32-column block of each GELU
 // warp's slice (all 128 rows of the CTA) is loaded by TMA into shared memory a tile ahead,
 // the other blocks one block ahead into registers; rows move in whole 64-byte segments
-// (warp_rows.cuh) and leave by TMA stores.
+// (warp_rows.cuh) and leave by TMA stores.  CTA pairs that get one tile fewer than the
+// others start about half a tile late, so that their drains (all of a tile's HBM traffic)
+// fall between those of the other pairs rather than on every SM at once.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
