@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(THREADS, 1) proj_mlp_tc_kernel(const __grid_co
         f[k + 2] = __uint_as_float(v[k + 2]) + b.z;
         f[k + 3] = __uint_as_float(v[k + 3]) + b.w;
       }
-      rows::store32_f32_async(&tmX, st, c0, row0, nvalid, lane, f);
+      rows::store32_f32_async_wide(&tmX, st, c0, row0, nvalid, lane, f);
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] = __float_as_uint(f[k]);
       tc::tmem_st_32x32b_x32(lane_base + c0, v);
@@ -687,17 +687,19 @@ bool map2d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t in
 }
 
 // Store map of a dense [rows][inner] matrix: 32-row boxes of 64 bytes, 64-byte swizzle
-// (the layout of the drain warps' staging tiles).
-bool store_map(CUtensorMap* m, const void* base, bool f32, CUtensorMapDataType dt16, uint64_t inner, uint64_t rows) {
+// (the layout of the drain warps' staging tiles), or with `wide` 32-row boxes of 128 bytes,
+// 128-byte swizzle (a wide box over both tiles).
+bool store_map(CUtensorMap* m, const void* base, bool f32, CUtensorMapDataType dt16, uint64_t inner, uint64_t rows,
+               bool wide = false) {
   auto fn = encode_fn();
   if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
   const uint32_t es = f32 ? 4 : 2;
   cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {inner * es};
-  cuuint32_t box[2] = {64 / es, 32};
+  cuuint32_t box[2] = {(wide ? 128u : 64u) / es, 32};
   cuuint32_t ess[2] = {1, 1};
   return fn(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : dt16, 2, const_cast<void*>(base), dims,
-            strides, box, ess, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            strides, box, ess, CU_TENSOR_MAP_INTERLEAVE_NONE, wide ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -757,7 +759,7 @@ cudaError_t launch_d(const T* A, const T* Wpt, const T* W1t, const T* W2t, const
   CUtensorMap ma, mp, m1, m2, mx, mln, mxr;
   if (!map2d(&ma, dt, A, D, (uint64_t)a.M, BK, BM)) return cudaErrorInvalidValue;
   if (!map2d(&mp, dt, Wpt, D, D, BK, D / 2)) return cudaErrorInvalidValue;
-  if (!store_map(&mx, a.X, true, dt, D, (uint64_t)a.M) || !store_map(&mln, a.ln_out, false, dt, D, (uint64_t)a.M))
+  if (!store_map(&mx, a.X, true, dt, D, (uint64_t)a.M, true) || !store_map(&mln, a.ln_out, false, dt, D, (uint64_t)a.M))
     return cudaErrorInvalidValue;
   if (!map2d(&m1, dt, W1t, D, (uint64_t)a.hid, BK, HC / 2)) return cudaErrorInvalidValue;
   if (!map2d(&m2, dt, W2t, (uint64_t)a.hid, D, BK, D / 2)) return cudaErrorInvalidValue;

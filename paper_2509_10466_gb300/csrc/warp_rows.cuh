@@ -114,14 +114,19 @@ __device__ __forceinline__ void store32_h16(T* base, size_t ld, int nvalid, uint
 // no row inside it (nvalid <= 0) is not issued at all; it still commits a (then empty)
 // bulk group, so that the group count behind each tile stays the box count.
 struct AsyncRows {
-  uint8_t* tiles;  // 2 x TILE_BYTES, 512-byte aligned
+  uint8_t* tiles;  // 2 x TILE_BYTES, 512-byte aligned (1024-byte aligned for the wide boxes)
   int k;
+  int wide = 0;    // the last store was a wide box over both tiles
 };
 
 __device__ __forceinline__ uint8_t* async_acquire(AsyncRows& a, int lane) {
   uint8_t* t = a.tiles + (a.k & 1) * TILE_BYTES;
   ++a.k;
-  if (lane == 0) tc::bulk_wait_read<1>();
+  if (lane == 0) {
+    if (a.wide) tc::bulk_wait_read<0>();  // a wide box covers both tiles
+    else tc::bulk_wait_read<1>();
+  }
+  a.wide = 0;
   __syncwarp();
   return t;
 }
@@ -163,6 +168,23 @@ __device__ __forceinline__ void store32_f32_async(const CUtensorMap* map, AsyncR
           make_float4(v[16 * h + 4 * j], v[16 * h + 4 * j + 1], v[16 * h + 4 * j + 2], v[16 * h + 4 * j + 3]);
     async_issue(map, t, c0 + 16 * h, r0, nvalid, lane);
   }
+}
+
+// Row `lane` of a 32 x 32 FP32 block at (column c0, row r0) = v, as one box of 32 rows x
+// 128 bytes staged over both tiles (128-byte swizzle: 16-byte chunk c of row r at
+// c ^ (r % 8); the tiles must be 1024-byte aligned): half the TMA row requests of two
+// 64-byte boxes.  Waits until every earlier store of the warp has read its tile.
+__device__ __forceinline__ void store32_f32_async_wide(const CUtensorMap* map, AsyncRows& a, int c0, int r0,
+                                                       int nvalid, int lane, const float (&v)[32]) {
+  if (lane == 0) tc::bulk_wait_read<0>();
+  __syncwarp();
+  uint8_t* t = a.tiles;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    *reinterpret_cast<float4*>(t + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+        make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  a.wide = 1;
+  async_issue(map, t, c0, r0, nvalid, lane);
 }
 
 // All of this warp's stores complete (before the CTA exits).
