@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-memory-sweep", action="store_true",
                     help="skip the temporal-memory leg (one 640x360 stream, m = 0, 2, 3, 4 slots)")
+    ap.add_argument("--memory-sweep-only", action="store_true",
+                    help="run only the temporal-memory leg and print its JSON (ncu captures of its kernels)")
     ap.add_argument("--serving-seconds", type=float, default=20.0,
                     help="length of the serving run (4 collaborators, 30 fps each); 0 skips it")
     return ap.parse_args()
@@ -371,6 +373,42 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- our arm
 
+def memory_leg(binding, S, cfg, weights, dev):
+    """Temporal memory: one 640x360 stream (the paper's inference size), frame by frame, with
+    m = 0, 2, 3, 4 memory slots; per-frame device time with CUDA events."""
+    import torch
+    from dataclasses import replace as _replace
+    Hm, Wm = 360, 640
+    xm = torch.from_numpy(S.make_frames(1, Hm, Wm, seed=7)).to(dev)
+    hm = torch.from_numpy(S.make_hole(1, Hm, Wm, "polygons", seed=7)).to(dev)
+    memory_sweep = {"workload": "one 640x360 stream (padded to 640x384), d256 h8 L8 r4 BF16, batch 1, "
+                                "frame by frame; odd blocks temporal when m > 0",
+                    "paper_context_ms": {"2": 14.7, "3": 18.6, "4": 23.0,
+                                         "note": "RTX 3070 TensorRT FP16 modified DSTT, frame time per the "
+                                                 "paper's memory-slot table; another model and GPU"}}
+    for m in (0, 2, 3, 4):
+        cfg_m = _replace(cfg, mem_slots=m)
+        inp_m = binding.Inpainter(cfg_m, weights)
+        bufs = [inp_m.memory_buffer(Hm, Wm) for _ in range(m + 1)] if m else []
+        ev = []
+        for k in range(23):
+            slots = [[bufs[(k - 1 - j) % (m + 1)] if k - 1 - j >= 0 else None for j in range(m)]] if m else None
+            outs = [bufs[k % (m + 1)]] if m else None
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if m:
+                inp_m.with_memory(xm, hm, slots, outs)
+            else:
+                inp_m(xm, hm)
+            b2.record()
+            ev.append((a, b2))
+        torch.cuda.synchronize()
+        times = sorted(x.elapsed_time(y) for x, y in ev[3:])
+        memory_sweep[f"m={m}"] = {"ms_per_frame_p50": times[len(times) // 2], "ms_per_frame_min": times[0]}
+        inp_m.close()
+    return memory_sweep
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -402,6 +440,9 @@ def main():
     x_np = S.make_frames(B, H, W, seed=frame_seed(rank))
     hole_np = S.make_hole(B, H, W, w.mask_kind, seed=frame_seed(rank))
     dev = torch.device("cuda", local)
+    if args.memory_sweep_only:
+        print(json.dumps({"leg": "memory_sweep", **memory_leg(binding, S, cfg, weights, dev)}))
+        return
     x = torch.from_numpy(x_np).to(dev)
     hole = torch.from_numpy(hole_np).to(dev)
     out = torch.empty_like(x)
@@ -572,35 +613,7 @@ def main():
     # with m = 0, 2, 3, 4 memory slots; per-frame device time with CUDA events
     memory_sweep = None
     if not args.no_memory_sweep and args.batch is None and args.size is None:
-        from dataclasses import replace as _replace
-        Hm, Wm = 360, 640
-        xm = torch.from_numpy(S.make_frames(1, Hm, Wm, seed=7)).to(dev)
-        hm = torch.from_numpy(S.make_hole(1, Hm, Wm, "polygons", seed=7)).to(dev)
-        memory_sweep = {"workload": "one 640x360 stream (padded to 640x384), d256 h8 L8 r4 BF16, batch 1, "
-                                    "frame by frame; odd blocks temporal when m > 0",
-                        "paper_context_ms": {"2": 14.7, "3": 18.6, "4": 23.0,
-                                             "note": "RTX 3070 TensorRT FP16 modified DSTT, frame time per the "
-                                                     "paper's memory-slot table; another model and GPU"}}
-        for m in (0, 2, 3, 4):
-            cfg_m = _replace(cfg, mem_slots=m)
-            inp_m = binding.Inpainter(cfg_m, weights)
-            bufs = [inp_m.memory_buffer(Hm, Wm) for _ in range(m + 1)] if m else []
-            ev = []
-            for k in range(23):
-                slots = [[bufs[(k - 1 - j) % (m + 1)] if k - 1 - j >= 0 else None for j in range(m)]] if m else None
-                outs = [bufs[k % (m + 1)]] if m else None
-                a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                if m:
-                    inp_m.with_memory(xm, hm, slots, outs)
-                else:
-                    inp_m(xm, hm)
-                b2.record()
-                ev.append((a, b2))
-            torch.cuda.synchronize()
-            times = sorted(x.elapsed_time(y) for x, y in ev[3:])
-            memory_sweep[f"m={m}"] = {"ms_per_frame_p50": times[len(times) // 2], "ms_per_frame_min": times[0]}
-            inp_m.close()
+        memory_sweep = memory_leg(binding, S, cfg, weights, dev)
 
     # ---- point cloud + headless splat of a 720p frame into a rotated 720p view
     splat = None
