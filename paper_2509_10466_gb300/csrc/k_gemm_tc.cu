@@ -44,8 +44,9 @@ struct TcCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int STAGES = (BN == 256) ? 3 : (BN == 128 ? 5 : 6);
-  static constexpr int TMEM_COLS = 2 * BN;
+  static constexpr int STAGES = (BN == 256) ? 3 : (BN == 192 ? 4 : (BN == 128 ? 5 : 6));
+  // two accumulators of BN columns, in an allocation of a power of two columns
+  static constexpr int TMEM_COLS = 2 * BN <= 128 ? 2 * BN : (2 * BN <= 256 ? 256 : 512);
   static constexpr int COLS_PER_WARP = BN / EW;
   static constexpr int PARAM_FLOATS = 1024 + 2 * BN;       // bias (N <= 1024) and LayerNorm scale/shift
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/ +
@@ -462,6 +463,7 @@ cudaError_t launch_any(const T* A, const T* Bt, const GemmArgs& a, cudaStream_t 
   }
   if (a.N % 256 == 0) return launch_bn<256, T>(A, Bt, a, st);
   if (a.N % 128 == 0) return launch_bn<128, T>(A, Bt, a, st);
+  if (a.N % 192 == 0) return launch_bn<192, T>(A, Bt, a, st);  // d = 192 models: 192, 576
   return launch_bn<64, T>(A, Bt, a, st);
 }
 
