@@ -510,7 +510,8 @@ int backward_impl(inpaint_ctx* c, const float* x, const uint8_t* hole, const flo
     const int Kp = (int)r64(rows), n_pad = (int)r64(n), m_pad = (int)r128(m);
     split3(true, A, rows, m, lda, m, Kp, false, sA);
     split3(true, G, rows, n, ldg, n_pad, Kp, true, sB);
-    const int bn = n_pad % 256 == 0 ? 256 : (n_pad % 128 == 0 ? 128 : 64);
+    // the GEMM's tile width for this n (its launcher's rule)
+    const int bn = n_pad % 256 == 0 ? 256 : (n_pad % 128 == 0 ? 128 : (n_pad % 192 == 0 ? 192 : 64));
     const int tiles = (m_pad / 128) * (n_pad / bn);
     const int splits = std::max(1, std::min({TC_SPLIT_MAX, 3 * Kp / 64, (2 * 152 + tiles - 1) / tiles}));
     { auto ls = K(K_OTHER); ok(launch_gemm_tc_splitk(sA, sB, tpart, m, n_pad, 3 * Kp, splits, c->dev_err, st)); }
