@@ -284,11 +284,16 @@ struct AttnBwdSmem {
   float Q[SLOTS][DH + 1], K[SLOTS][DH + 1], V[SLOTS][DH + 1], GO[SLOTS][DH + 1];
   float P[SLOTS][SLOTS + 1], GS[SLOTS][SLOTS + 1];
   float rp[225];
-  int ok[SLOTS];
+  int ok[SLOTS], tok[SLOTS];
 };
 
 __device__ __forceinline__ int relpos_idx(int s, int k) { return ((k >> 3) - (s >> 3) + 7) * 15 + ((k & 7) - (s & 7) + 7); }
 
+// One CTA per (window, head), thread s = slot s: the query-side gradients of row s, then the
+// key-side gradients of key s.  Rows move between global and shared memory a whole 32-value
+// head slice per warp instruction (lane = channel); the scores are computed once and kept in
+// P; dot products run four keys at a time (independent FMA chains, each in ascending channel
+// order, so every value equals the one-key-at-a-time evaluation).
 __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict__ qkv, const uint8_t* __restrict__ v_in,
                                                          const float* __restrict__ go, float* __restrict__ gqkv, int Ht,
                                                          int Wt, int d, int offset, int nwx,
@@ -296,6 +301,8 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
   extern __shared__ __align__(16) uint8_t smem_raw[];
   AttnBwdSmem& sm = *reinterpret_cast<AttnBwdSmem*>(smem_raw);
   const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = SLOTS / 32;  // warps
   // this CTA's partial gradient of the relative-position table: [frame][window][head][225]
   float* gb = gbias ? gbias + (((size_t)b * gridDim.x + w) * gridDim.y + h) * 225 : nullptr;
   for (int e = threadIdx.x; e < 225; e += SLOTS) sm.rp[e] = relpos ? relpos[h * 225 + e] : 0.f;
@@ -306,17 +313,20 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
   const size_t t = real ? (size_t)b * Ht * Wt + (size_t)ty * Wt + tx : 0;
   const bool ok = real && v_in[t] != 0;
   sm.ok[s] = ok;
-  const float* row = qkv + t * 3 * d;
-  const float* grow_ = go + t * d + h * DH;
-  for (int i = 0; i < DH; ++i) {
-    sm.Q[s][i] = real ? row[h * DH + i] : 0.f;
-    sm.K[s][i] = ok ? row[d + h * DH + i] : 0.f;
-    sm.V[s][i] = ok ? row[2 * d + h * DH + i] : 0.f;
-    sm.GO[s][i] = real ? grow_[i] : 0.f;
+  sm.tok[s] = real ? (int)t : -1;
+  __syncthreads();
+  for (int sl = warp; sl < SLOTS; sl += NW) {  // the window's head slices, one row per warp step
+    const int ts = sm.tok[sl];
+    const bool oks = sm.ok[sl];
+    const float* row = qkv + (size_t)(ts < 0 ? 0 : ts) * 3 * d + h * DH + lane;
+    sm.Q[sl][lane] = ts >= 0 ? row[0] : 0.f;
+    sm.K[sl][lane] = oks ? row[d] : 0.f;
+    sm.V[sl][lane] = oks ? row[2 * d] : 0.f;
+    sm.GO[sl][lane] = ts >= 0 ? go[(size_t)ts * d + h * DH + lane] : 0.f;
   }
   const int any = __syncthreads_or(ok);
-  float* gq = gqkv + t * 3 * d + h * DH;
   if (!any) {
+    float* gq = gqkv + t * 3 * d + h * DH;
     if (real)
       for (int i = 0; i < DH; ++i) { gq[i] = 0.f; gq[d + i] = 0.f; gq[2 * d + i] = 0.f; }
     if (gb)
@@ -325,37 +335,51 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
   }
   const float scale = 1.0f / sqrtf((float)DH);
   // query side: probabilities, score gradients, dQ
+  float acc[DH];
   if (real) {
     float mx = -INFINITY;
-    for (int k = 0; k < SLOTS; ++k) {
-      if (!sm.ok[k]) continue;
-      float sc = 0.f;
-      for (int i = 0; i < DH; ++i) sc = fmaf(sm.Q[s][i], sm.K[k][i], sc);
-      mx = fmaxf(mx, sc * scale + sm.rp[relpos_idx(s, k)]);
+    for (int k0 = 0; k0 < SLOTS; k0 += 4) {  // scores (with bias) into P, -inf for excluded keys
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < DH; ++i) {
+        const float qi = sm.Q[s][i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = fmaf(qi, sm.K[k0 + j][i], a[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + j;
+        const float z = sm.ok[k] ? a[j] * scale + sm.rp[relpos_idx(s, k)] : -INFINITY;
+        sm.P[s][k] = z;
+        mx = fmaxf(mx, z);
+      }
     }
     float l = 0.f;
     for (int k = 0; k < SLOTS; ++k) {
-      float p = 0.f;
-      if (sm.ok[k]) {
-        float sc = 0.f;
-        for (int i = 0; i < DH; ++i) sc = fmaf(sm.Q[s][i], sm.K[k][i], sc);
-        p = expf(sc * scale + sm.rp[relpos_idx(s, k)] - mx);
-      }
+      const float p = sm.ok[k] ? expf(sm.P[s][k] - mx) : 0.f;
       sm.P[s][k] = p;
       l += p;
     }
     const float inv = 1.f / l;
     float D = 0.f;
-    for (int k = 0; k < SLOTS; ++k) {
-      const float p = sm.P[s][k] * inv;
-      sm.P[s][k] = p;
-      float gp = 0.f;
-      if (sm.ok[k])
-        for (int i = 0; i < DH; ++i) gp = fmaf(sm.GO[s][i], sm.V[k][i], gp);
-      sm.GS[s][k] = gp;
-      D = fmaf(p, gp, D);
+    for (int k0 = 0; k0 < SLOTS; k0 += 4) {  // dO . V for four keys at a time
+      float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < DH; ++i) {
+        const float gi = sm.GO[s][i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g[j] = fmaf(gi, sm.V[k0 + j][i], g[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + j;
+        const float p = sm.P[s][k] * inv;
+        sm.P[s][k] = p;
+        const float gp = sm.ok[k] ? g[j] : 0.f;
+        sm.GS[s][k] = gp;
+        D = fmaf(p, gp, D);
+      }
     }
-    float acc[DH];
     for (int i = 0; i < DH; ++i) acc[i] = 0.f;
     for (int k = 0; k < SLOTS; ++k) {
       const float gs = sm.P[s][k] * (sm.GS[s][k] - D);
@@ -363,40 +387,50 @@ __global__ void __launch_bounds__(SLOTS) attn_bwd_kernel(const float* __restrict
       if (sm.ok[k])
         for (int i = 0; i < DH; ++i) acc[i] = fmaf(gs, sm.K[k][i], acc[i]);
     }
-    for (int i = 0; i < DH; ++i) gq[i] = acc[i] * scale;
   } else {
     for (int k = 0; k < SLOTS; ++k) { sm.P[s][k] = 0.f; sm.GS[s][k] = 0.f; }
   }
   __syncthreads();
+  // V is no longer read: it takes dQ
+  if (real)
+    for (int i = 0; i < DH; ++i) sm.V[s][i] = acc[i] * scale;
   // relative-position table: d score / d table entry = 1, so its gradient is the sum of the
   // score gradients over the (query, key) slot pairs at that offset (fixed order)
   if (gb)
     for (int e = s; e < 225; e += SLOTS) {
       const int dy = e / 15 - 7, dx = e % 15 - 7;
-      float acc = 0.f;
+      float a = 0.f;
       for (int q = 0; q < SLOTS; ++q) {
         const int ky = (q >> 3) + dy, kx = (q & 7) + dx;
-        if (ky >= 0 && ky < 8 && kx >= 0 && kx < 8) acc += sm.GS[q][ky * 8 + kx];
+        if (ky >= 0 && ky < 8 && kx >= 0 && kx < 8) a += sm.GS[q][ky * 8 + kx];
       }
-      gb[e] = acc;
+      gb[e] = a;
     }
   // key side: dK = scale * GS^T Q, dV = P^T dO
-  if (real) {
-    float gk[DH], gv[DH];
-    for (int i = 0; i < DH; ++i) { gk[i] = 0.f; gv[i] = 0.f; }
-    if (ok) {
-      for (int q = 0; q < SLOTS; ++q) {
-        const float gs = sm.GS[q][s], p = sm.P[q][s];
-        for (int i = 0; i < DH; ++i) {
-          gk[i] = fmaf(gs, sm.Q[q][i], gk[i]);
-          gv[i] = fmaf(p, sm.GO[q][i], gv[i]);
-        }
+  float gk[DH], gv[DH];
+  for (int i = 0; i < DH; ++i) { gk[i] = 0.f; gv[i] = 0.f; }
+  if (ok) {
+    for (int q = 0; q < SLOTS; ++q) {
+      const float gs = sm.GS[q][s], p = sm.P[q][s];
+      for (int i = 0; i < DH; ++i) {
+        gk[i] = fmaf(gs, sm.Q[q][i], gk[i]);
+        gv[i] = fmaf(p, sm.GO[q][i], gv[i]);
       }
     }
-    for (int i = 0; i < DH; ++i) {
-      gq[d + i] = gk[i] * scale;
-      gq[2 * d + i] = gv[i];
-    }
+  }
+  __syncthreads();  // K and dO are no longer read: they take dK and dV
+  for (int i = 0; i < DH; ++i) {
+    sm.K[s][i] = gk[i] * scale;
+    sm.GO[s][i] = gv[i];
+  }
+  __syncthreads();
+  for (int sl = warp; sl < SLOTS; sl += NW) {  // the gradient rows of the window's real slots
+    const int ts = sm.tok[sl];
+    if (ts < 0) continue;
+    float* gq = gqkv + (size_t)ts * 3 * d + h * DH + lane;
+    gq[0] = sm.V[sl][lane];
+    gq[d] = sm.K[sl][lane];
+    gq[2 * d] = sm.GO[sl][lane];
   }
 }
 
