@@ -27,16 +27,22 @@ constexpr int SLOTS = 64;  // WS * WS
 constexpr int DH = 32;     // head dim
 
 
+// One CTA per (window, head), thread s = slot s.  Rows move a whole 32-value head slice per
+// warp instruction (lane = channel) between global and shared memory; the scores are dot
+// products four keys at a time (independent FMA chains, each in ascending channel order, so
+// every value equals the one-key-at-a-time evaluation); excluded keys add exact zeros.
 template <typename T>
 __global__ void __launch_bounds__(SLOTS) attn_simt_kernel(const T* __restrict__ qkv, const uint8_t* __restrict__ v_in,
                                                           T* __restrict__ o, uint8_t* __restrict__ v_out, int Ht,
                                                           int Wt, int d, int offset, int nwx,
                                                           const float* __restrict__ relpos) {
+  __shared__ float Qs[SLOTS][DH + 1];
   __shared__ float Ks[SLOTS][DH + 1];
   __shared__ float Vs[SLOTS][DH + 1];
-  __shared__ int okS[SLOTS];
+  __shared__ int okS[SLOTS], tokS[SLOTS];
   __shared__ float rp[225];
   const int w = blockIdx.x, h = blockIdx.y, b = blockIdx.z;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int e = threadIdx.x; e < 225; e += SLOTS) rp[e] = relpos ? relpos[h * 225 + e] : 0.f;
   const int wy = w / nwx, wx = w - (w / nwx) * nwx;
   const int s = threadIdx.x;
@@ -46,50 +52,76 @@ __global__ void __launch_bounds__(SLOTS) attn_simt_kernel(const T* __restrict__ 
   const size_t t = real ? (size_t)b * Nt + (size_t)ty * Wt + tx : 0;
   const bool ok = real && v_in[t] != 0;
   okS[s] = ok;
-  const T* row = qkv + t * 3 * d;
-#pragma unroll 8
-  for (int i = 0; i < DH; ++i) {
-    Ks[s][i] = ok ? to_f32(row[d + h * DH + i]) : 0.f;
-    Vs[s][i] = ok ? to_f32(row[2 * d + h * DH + i]) : 0.f;
+  tokS[s] = real ? (int)t : -1;
+  __syncthreads();
+  for (int sl = warp; sl < SLOTS; sl += SLOTS / 32) {  // the window's head slices
+    const int ts = tokS[sl];
+    const bool oks = okS[sl];
+    const T* row = qkv + (size_t)(ts < 0 ? 0 : ts) * 3 * d + h * DH + lane;
+    Qs[sl][lane] = ts >= 0 ? to_f32(row[0]) : 0.f;
+    Ks[sl][lane] = oks ? to_f32(row[d]) : 0.f;
+    Vs[sl][lane] = oks ? to_f32(row[2 * d]) : 0.f;
   }
   const int any = __syncthreads_or(ok);
-  if (!real) return;
-  T* orow = o + t * d + h * DH;
-  if (!any) {
+  if (!any) {  // the same for every thread of the CTA
+    if (real) {
+      T* orow = o + t * d + h * DH;
 #pragma unroll 8
-    for (int i = 0; i < DH; ++i) orow[i] = from_f32<T>(0.f);
-    if (h == 0) v_out[t] = 0;
+      for (int i = 0; i < DH; ++i) orow[i] = from_f32<T>(0.f);
+      if (h == 0) v_out[t] = 0;
+    }
     return;
   }
-  if (h == 0) v_out[t] = 1;
-  float q[DH];
+  if (real && h == 0) v_out[t] = 1;
+  float acc[DH], inv = 0.f;
+  if (real) {
+    float q[DH];
 #pragma unroll
-  for (int i = 0; i < DH; ++i) q[i] = to_f32(row[h * DH + i]);
-  const float scale = 1.0f / sqrtf((float)DH);
-  float mx = -INFINITY;
-  for (int k = 0; k < SLOTS; ++k) {
-    if (!okS[k]) continue;
-    float sc = 0.f;
+    for (int i = 0; i < DH; ++i) q[i] = Qs[s][i];
+    const float scale = 1.0f / sqrtf((float)DH);
+    float mx = -INFINITY;
+    for (int k0 = 0; k0 < SLOTS; k0 += 4) {
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < DH; ++i) sc = fmaf(q[i], Ks[k][i], sc);
-    mx = fmaxf(mx, sc * scale + rp[relpos_index(s, k)]);
+      for (int i = 0; i < DH; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = fmaf(q[i], Ks[k0 + j][i], a[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (okS[k0 + j]) mx = fmaxf(mx, a[j] * scale + rp[relpos_index(s, k0 + j)]);
+    }
+    float l = 0.f;
+#pragma unroll
+    for (int i = 0; i < DH; ++i) acc[i] = 0.f;
+    for (int k0 = 0; k0 < SLOTS; k0 += 4) {
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < DH; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = fmaf(q[i], Ks[k0 + j][i], a[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + j;
+        if (!okS[k]) continue;
+        const float p = expf(a[j] * scale + rp[relpos_index(s, k)] - mx);
+        l += p;
+#pragma unroll
+        for (int i = 0; i < DH; ++i) acc[i] = fmaf(p, Vs[k][i], acc[i]);
+      }
+    }
+    inv = 1.f / l;
   }
-  float l = 0.f, acc[DH];
+  __syncthreads();  // K is no longer read: it takes the output rows
+  if (real)
 #pragma unroll
-  for (int i = 0; i < DH; ++i) acc[i] = 0.f;
-  for (int k = 0; k < SLOTS; ++k) {
-    if (!okS[k]) continue;
-    float sc = 0.f;
-#pragma unroll
-    for (int i = 0; i < DH; ++i) sc = fmaf(q[i], Ks[k][i], sc);
-    const float p = expf(sc * scale + rp[relpos_index(s, k)] - mx);
-    l += p;
-#pragma unroll
-    for (int i = 0; i < DH; ++i) acc[i] = fmaf(p, Vs[k][i], acc[i]);
+    for (int i = 0; i < DH; ++i) Ks[s][i] = acc[i] * inv;
+  __syncthreads();
+  for (int sl = warp; sl < SLOTS; sl += SLOTS / 32) {
+    const int ts = tokS[sl];
+    if (ts >= 0) o[(size_t)ts * d + h * DH + lane] = from_f32<T>(Ks[sl][lane]);
   }
-  const float inv = 1.f / l;
-#pragma unroll
-  for (int i = 0; i < DH; ++i) orow[i] = from_f32<T>(acc[i] * inv);
 }
 
 // Temporal form: the window's keys are its usable current tokens and, for each of the m
